@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark: certified subdomain-bounds per second at a fixed iteration count.
+
+Workload (default): ReLU MLP 784-256x6-10, 1024 branch-and-bound subdomains
+(1-8 neuron splits each) x 9 spec rows, 200 sparse cuts over 2-8 variables,
+100 Adam ascent iterations on (alpha, beta, gamma) in the FP32 chain, then
+the FP64 outward-rounded certification pass. One step = that whole hot path
+for the batch; one unit = one subdomain with all its spec rows optimised and
+certified. Inputs are seeded synthetic data of the paper's shapes.
+
+value  : device-timed (CUDA events on the library's stream), inputs resident.
+e2e    : the same through the public C ABI from host buffers: every step
+         creates the batch from host split arrays (uploads splits and cuts),
+         optimises, certifies, copies bounds back and frees the batch.
+--impl reference : the FP64 CPU oracle on a bounded sample of the workload.
+Multi-GPU (torchrun): every rank runs its own batch (weak scaling, no
+collective on the data path); value = all ranks' subdomains / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "certified subdomain-bounds/sec at fixed iters; p50/p99 latency; bound err vs FP64"
+UNIT = "subdomain-bounds/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gcp", "reference"], default="gcp")
+    ap.add_argument("--prec", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--iters", type=int, default=100)
+    ap.add_argument("--n-sub", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-all", action="store_true", help="print every kernel's share (untimed step)")
+    return ap.parse_args()
+
+
+def workload_config(a, n_gpus):
+    return {"workload": "mlp_784_256x6_10", "n_subdomains_per_gpu": a.n_sub, "spec_rows": 9, "rows_per_gpu": a.n_sub * 9,
+            "cuts": 200, "splits_per_subdomain": "1-8", "iters": a.iters, "optimizer": "adam",
+            "lr": [0.1, 0.02, 0.02], "lr_decay": 0.98, "chain": a.prec, "certify": "fp64_outward_rounded",
+            "intermediate_bounds": "interval (IBP)", "l2": "flushed between steps (256 MiB write)",
+            "parallelism": f"replicas{n_gpus}" if n_gpus > 1 else "single_gpu"}
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        rows = []
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        mhz = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower().startswith("active")})
+        return {"sm_mhz": mhz[len(mhz) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- peaks
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+def kernel_peak(name, peaks, src):
+    """(bound, peak, unit, note) for a kernel class.
+
+    FP32 SIMT contractions: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock.
+    FP64 SIMT contractions: 152 SMs x 2 FP64 lanes x 2 flop x max SM clock
+    (the nominal 1.25 TFLOP/s of GB300's FP64 units). Per-neuron kernels: HBM.
+    """
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    if name.startswith(("gemm_simt_f32", "conv_fwd_f32", "conv_T_f32")):
+        return "alu", 152 * 128 * 2 * mhz * 1e6 / 1e12, "TFLOP/s", f"FFMA peak from unit counts and {mhz:.0f} MHz"
+    if name.startswith(("gemm_simt_f64", "conv_T_f64", "conv_fwd_f64")):
+        return "alu", 152 * 2 * 2 * mhz * 1e6 / 1e12, "TFLOP/s", f"DFMA peak from unit counts and {mhz:.0f} MHz"
+    if name.startswith(("gemm_tc_bf16", "conv_tc_bf16")):
+        return "tensor", float(peaks["bf16_tflops_sustained"]), "TFLOP/s", f"bf16 sustained ({src})"
+    return "hbm", float(peaks["hbm_gbs"]), "GB/s", f"copy bandwidth ({src})"
+
+
+def traffic_for(name, workload):
+    """Per-launch DRAM bytes of an ncu capture, if the kernel source is unchanged since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            tab = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = tab.get(f"{workload}:{name}")
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2208_05740_gb300", "csrc", ent["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return ent["bytes_per_launch"] if h == ent["source_sha"] else None
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def oracle_sample(inst, n_sub, iters, seconds_cap=25.0):
+    """Time the FP64 oracle on the first n_sub subdomains: a few Adam steps and
+    the two evaluations (final bound and certification), extrapolated to
+    `iters` steps. Returns (subdomains per second, description)."""
+    import numpy as np
+    from oracle import gcp_oracle as O
+    from paper_2208_05740_gb300 import synth
+    sub = synth.restrict(inst, n_sub)
+    P = O.build_problem(sub)
+    D = O.default_duals(P)
+    t0 = time.perf_counter()
+    O.evaluate(P, D)
+    t_eval = time.perf_counter() - t0
+    # probe one step, then time k contiguous steps (k fits the cap); optimize()
+    # ends with one evaluation, which is subtracted
+    t0 = time.perf_counter()
+    O.optimize(P, D, 1, 0.1, 0.02, 0.02, optimizer="adam", lr_decay=0.98)
+    t1 = max(time.perf_counter() - t0 - t_eval, 1e-6)
+    k = int(max(1, min(iters, seconds_cap / t1)))
+    t0 = time.perf_counter()
+    O.optimize(P, D, k, 0.1, 0.02, 0.02, optimizer="adam", lr_decay=0.98)
+    t_it = max(time.perf_counter() - t0 - t_eval, 1e-9) / k
+    per_batch = t_it * iters + 2 * t_eval
+    return n_sub / per_batch, f"{n_sub} subdomains x 9 rows, {k} timed Adam steps + 1 evaluation, " \
+                              f"extrapolated to {iters} steps + 2 evaluations"
+
+
+def run_reference(a):
+    import numpy as np
+    from paper_2208_05740_gb300 import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    inst = synth.mlp_256x6()
+    n_sub = 4
+    cfg = workload_config(a, a.gpus)
+    for _ in range(a.warmup):
+        oracle_sample(inst, n_sub, a.iters, seconds_cap=2.0)
+    vals = []
+    for _ in range(a.steps):
+        v, desc = oracle_sample(inst, n_sub, a.iters, seconds_cap=8.0)
+        vals.append(v)
+    value = float(np.median(vals))
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1000.0 * n_sub / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------- GPU arm
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    import numpy as np
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_2208_05740_gb300 import build, gcp, synth
+    build.build()
+    dev = local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    prec = gcp.GCP_FP32 if a.prec == "fp32" else gcp.GCP_BF16
+    inst = synth.mlp_256x6(n_sub=a.n_sub)
+    ctx = gcp.Context(dev)
+    ctx.set_stream(stream.cuda_stream)
+    net_id, cs = ctx.load_instance(inst)
+    params = gcp.opt_params(a.iters, gcp.GCP_ADAM, prec, 1, 0.1, 0.02, 0.02, 0.98)
+    D = ctx.duals_create(net_id, cs, inst.sub, gcp.GCP_FP32)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")
+
+    def step():
+        ctx.duals_import(D)                       # default duals: same work every step
+        return ctx.optimize_batch(D, params)      # 100 iterations + final bound + FP64 certify
+
+    for _ in range(a.warmup):
+        bound, cert, err = step()
+    # shares of every kernel in one untimed step, to pick the dominant one
+    gcp.profile_start("*")
+    step()
+    rep = gcp.profile_report()
+    gcp.profile_stop()
+    dominant = max(rep, key=lambda k: rep[k][2])
+    total_ms = sum(v[2] for v in rep.values())
+    if a.profile_all and rank == 0:
+        for k, v in sorted(rep.items(), key=lambda kv: -kv[1][2]):
+            print(f"# {k:28s} launches {v[0]:6d} ms {v[2]:9.3f} share {100 * v[2] / total_ms:5.1f}%", file=sys.stderr)
+
+    # ---- timed region: device time per step, dominant kernel timed live
+    sampler = ClockSampler(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    gcp.profile_start(dominant)
+    times = []
+    for _ in range(a.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bound, cert, err = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    launches_all = gcp.profile_query(None)[0]
+    n_dom, ms_dom, fl_dom, by_dom = gcp.profile_query(dominant)
+    gcp.profile_stop()
+    clocks = sampler.stop()
+    total_s = sum(times) / 1000.0
+    if world > 1:
+        t = torch.tensor([total_s], device=f"cuda:{dev}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * a.n_sub * a.steps / total_s
+
+    # ---- end to end through the C ABI from host buffers
+    sub = inst.sub
+    h2d = sub.ptr.nbytes + sub.layer.nbytes + sub.index.nbytes + sub.sign.nbytes
+    c = inst.cuts
+    nnz = len(c.coef)
+    h2d += (c.n + 1) * 4 + c.n * 12 + sum(d + 1 for d in inst.net.dims[:-1]) * 4 + nnz * (4 + 1 + 8 + 4 + 4 + 4)
+    d2h = 3 * 8 * inst.n_rows
+    e2e_t = []
+    for _ in range(a.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        D2 = ctx.duals_create(net_id, cs, sub, gcp.GCP_FP32)
+        b2, c2, r2 = ctx.optimize_batch(D2, params)
+        ctx.duals_free(D2)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_t)
+    if world > 1:
+        t = torch.tensor([e2e_s], device=f"cuda:{dev}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * a.n_sub * a.steps / e2e_s
+
+    if rank != 0:
+        return
+    peaks, src = measured_peaks()
+    bound_kind, peak, unit, note = kernel_peak(dominant, peaks, src)
+    per_launch_ms = ms_dom / max(n_dom, 1)
+    if unit == "TFLOP/s":
+        achieved = (fl_dom / max(n_dom, 1)) / (per_launch_ms / 1e3) / 1e12
+    else:
+        achieved = (by_dom / max(n_dom, 1)) / (per_launch_ms / 1e3) / 1e9
+    lat = np.array(times)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": float(np.mean(times)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if a.prec == "fp32" else "bf16", "data": "synthetic", "config": workload_config(a, world),
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "bound": {"mean_certified": float(np.mean(cert)), "max_err_vs_fp64": float(np.max(err)),
+                  "max_rel_err_vs_fp64": float(np.max(err / np.maximum(1.0, np.abs(cert))))},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches_all),
+        "roofline": {"kernel": dominant, "bound": bound_kind, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": achieved / peak, "traffic": traffic_for(dominant, "mlp_784_256x6_10"),
+                     "peak_source": note, "launches": int(n_dom), "ms_per_launch": per_launch_ms,
+                     "share_of_step": rep[dominant][2] / total_ms},
+        "clocks": clocks,
+    }
+    if world == 1 and not a.no_cpu_baseline:
+        v, desc = oracle_sample(inst, 4, a.iters)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
+    print(json.dumps(line))
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,276 @@
+/*
+ * gcp.h -- C ABI of libgcp: batched GCP-CROWN bound propagation on one GB300.
+ *
+ * GCP-CROWN (Zhang et al., "General Cutting Planes for Bound-Propagation-Based
+ * Neural Network Verification", arXiv 2208.05740) lower-bounds
+ *     f* = min_{x in C} c^T f(x),  C = {x : x_lo <= x <= x_hi}        (Sec. 2, Eq. 1)
+ * for a ReLU network under general cutting planes
+ *     sum_i H^(i) x^(i) + G^(i) xhat^(i) + Q^(i) z^(i) <= d               (Sec. 3.1, Eq. 15)
+ * by propagating nu^(L) = -c backwards through every layer with the closed
+ * form of Theorem 3.1 (App. A, Lemma A.1), then optimising the duals
+ * alpha (ReLU lower slopes), beta (neuron-split multipliers) and gamma
+ * (general-cut multipliers) by projected gradient ascent (Sec. 3.1 after
+ * Theorem 3.1; App. C.1).
+ *
+ * Conventions shared by every call
+ *  - Every call returns a gcp_status; nothing throws or aborts across the ABI.
+ *    On error the call leaves its outputs untouched and gcp_last_error()
+ *    describes the failure.
+ *  - Host arrays passed in are copied; the caller keeps ownership and may free
+ *    them when the call returns. Output arrays are caller-allocated.
+ *  - "rows": a batch of S subdomains and K spec rows has R = S*K rows ordered
+ *    r = s*K + k. Each row has its own alpha, beta, gamma (one dual point per
+ *    subdomain and spec row).
+ *  - A context owns one CUDA device and one stream; calls on one context are
+ *    serialised by an internal mutex (thread-safe), calls on different
+ *    contexts are independent.
+ *  - Device-side failures (a kernel's bounds check or error word) surface as
+ *    GCP_EDEVICE with a message; CUDA runtime errors as GCP_ECUDA.
+ */
+#ifndef GCP_H_
+#define GCP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GCP_API __attribute__((visibility("default")))
+#else
+#define GCP_API
+#endif
+
+typedef struct gcp_ctx gcp_ctx;
+typedef int32_t gcp_status;
+
+enum {
+  GCP_OK = 0,
+  GCP_PENDING = 1,      /* gcp_serve_poll: request still in flight */
+  GCP_EINVAL = -1,      /* malformed argument (shape, index, sign, NaN) */
+  GCP_ENOMEM = -2,      /* device or host allocation failed */
+  GCP_ECUDA = -3,       /* CUDA runtime error */
+  GCP_ETIMEOUT = -4,    /* a bounded wait expired */
+  GCP_EBUDGET = -5,     /* request larger than the context's HBM budget */
+  GCP_ENOTFOUND = -6,   /* unknown net / cut set / duals / ticket */
+  GCP_EDEVICE = -7      /* a kernel reported an error word */
+};
+
+enum { GCP_DENSE = 0, GCP_CONV2D = 1 };
+/* cut variable kinds: pre-activation x, post-activation xhat, ReLU indicator z (Eq. 15) */
+enum { GCP_VAR_X = 0, GCP_VAR_XHAT = 1, GCP_VAR_Z = 2 };
+/* arithmetic of the propagation chain */
+enum { GCP_FP64 = 0, GCP_FP32 = 1, GCP_BF16 = 2 };
+enum { GCP_PGA = 0, GCP_ADAM = 1 };
+
+/* One affine layer x^(i) = W^(i) xhat^(i-1) + b^(i) (Sec. 2).
+ * dense : W is [d_out, d_in] row-major.
+ * conv2d: W is [c_out, c_in, k, k] (OIHW), cross-correlation with the given
+ *         stride and zero padding; activations are CHW-flattened, so
+ *         d_in = c_in*h_in*w_in and d_out = c_out*h_out*w_out.
+ * b has d_out entries (per output element, CHW order for conv2d). */
+typedef struct {
+  int32_t kind;
+  int32_t d_in, d_out;
+  int32_t c_in, h_in, w_in, c_out, h_out, w_out, k, stride, pad;
+  const double* W;
+  const double* b;
+} gcp_layer_desc;
+
+/* Branch-and-bound subdomains as neuron split sets (App. B), CSR by
+ * subdomain: subdomain s owns entries split_ptr[s] .. split_ptr[s+1]-1.
+ * split_layer in 1..L-1, split_index < d_layer, split_sign +1 for the branch
+ * x >= 0 and -1 for x <= 0. A split is the cut row -x <= 0 (resp. x <= 0) with
+ * its own multiplier beta (Sec. 3.1, beta-CROWN as a special case) and clamps
+ * the neuron's bound l := max(l,0) (resp. u := min(u,0)). */
+typedef struct {
+  int32_t n_sub;
+  const int32_t* split_ptr;
+  const int16_t* split_layer;
+  const int32_t* split_index;
+  const int8_t* split_sign;
+} gcp_subdomains;
+
+/* Optimiser settings. iters: gradient-ascent steps. optimizer: GCP_PGA
+ * (x <- proj(x + lr*grad)) or GCP_ADAM (App. C.1; moments 0.9/0.999, eps 1e-8).
+ * Learning rate at step t is lr * lr_decay^t. prec: chain arithmetic
+ * (GCP_FP64 needs duals created with GCP_FP64; GCP_FP32 / GCP_BF16 need
+ * GCP_FP32 duals). certify != 0: also run the FP64 outward-rounded
+ * certification pass at the final duals. */
+typedef struct {
+  int32_t iters, optimizer, prec, certify;
+  double lr_alpha, lr_beta, lr_gamma, lr_decay;
+} gcp_opt_params;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`. hbm_budget_bytes caps the device
+ * memory this context allocates (0 = no cap); exceeding it yields GCP_EBUDGET.
+ * *out receives the context (owned by the caller, freed by gcp_destroy). */
+GCP_API gcp_status gcp_create(gcp_ctx** out, int32_t device, uint64_t hbm_budget_bytes);
+/* Free every net, cut set, duals object and the serving loop of the context. */
+GCP_API gcp_status gcp_destroy(gcp_ctx* ctx);
+/* Message of the last failing call on this context (static storage of the
+ * context; valid until the next call). Never NULL. */
+GCP_API const char* gcp_last_error(const gcp_ctx* ctx);
+/* Use `stream` (a cudaStream_t passed as void*, NULL = the context's own
+ * stream) for subsequent work of this context. The caller keeps ownership. */
+GCP_API gcp_status gcp_set_stream(gcp_ctx* ctx, void* stream);
+/* Device bytes currently held by the context. */
+GCP_API gcp_status gcp_mem_used(const gcp_ctx* ctx, uint64_t* bytes);
+
+/* ---------------------------------------------------------- problem inputs */
+
+/* Register a network, its input box and spec (Sec. 2): layers[0..n_layers-1]
+ * are W^(1)..W^(L); x_lo/x_hi [d_0] the input box (x0 -/+ eps for the
+ * L-infinity ball); spec_c [n_spec, d_L] row-major, the spec rows folded in as
+ * the last linear layer (nu^(L) = -c); inter_lo/inter_hi: sound pre-activation
+ * bounds of hidden layers 1..L-1 concatenated ([sum d_i], Sec. 2, "sound
+ * pre-activation bounds"), lo <= hi elementwise. *net_id receives the id.
+ * Errors: GCP_EINVAL for inconsistent shapes, lo > hi or non-finite values. */
+GCP_API gcp_status gcp_init_net(gcp_ctx* ctx, const gcp_layer_desc* layers, int32_t n_layers,
+                                const double* x_lo, const double* x_hi,
+                                const double* spec_c, int32_t n_spec,
+                                const double* inter_lo, const double* inter_hi, int32_t* net_id);
+
+/* Append n_cuts general cutting planes (Eq. 15) to a cut set of net_id:
+ *   sum_{e in row_ptr[c]..row_ptr[c+1]-1} coef[e] * var(layer[e], kind[e], index[e]) <= d[c]
+ * layer 0 is the network input (kind must be GCP_VAR_X); layers 1..L-1 are
+ * hidden with kind X, XHAT or Z. *cutset_id: -1 creates a new cut set (id
+ * returned in it), otherwise cuts are appended to that set (append-only, the
+ * way cuts arrive from a MIP solver while branch and bound runs, Sec. 3.2).
+ * *first_cut receives the index of the first appended cut. Duals created
+ * later see all cuts; existing duals objects keep the cut count they had.
+ * Errors: GCP_EINVAL for bad indices/kinds/non-finite values,
+ * GCP_ENOTFOUND for unknown ids. */
+GCP_API gcp_status gcp_add_cuts(gcp_ctx* ctx, int32_t net_id, int32_t n_cuts, const int64_t* row_ptr,
+                                const int16_t* layer, const int8_t* kind, const int32_t* index,
+                                const double* coef, const double* d, int32_t* cutset_id,
+                                int32_t* first_cut);
+
+/* ------------------------------------------------------------------- duals */
+
+/* Create device-resident state for a batch of subdomains of net_id under
+ * cut set cutset_id (-1 = no cuts): the duals alpha [R, sum_i d_i] (hidden
+ * neurons, layer-major columns), beta [R, max_splits], gamma [R, N], the
+ * split sets, and the workspace of the chain. dual_prec: GCP_FP64 (duals and
+ * chain in float64) or GCP_FP32 (float32 duals; chain FP32 or BF16).
+ * Default initial duals: alpha = 1 where u >= -l else 0, beta = gamma = 0.
+ * *duals receives an opaque handle owned by the context. */
+GCP_API gcp_status gcp_duals_create(gcp_ctx* ctx, int32_t net_id, int32_t cutset_id,
+                                    const gcp_subdomains* sub, int32_t dual_prec, void** duals);
+/* Shape of a duals object: rows R, alpha columns sum_i d_i, max_splits, cuts N. */
+GCP_API gcp_status gcp_duals_shape(gcp_ctx* ctx, void* duals, int64_t* rows, int64_t* n_alpha,
+                                   int32_t* max_splits, int32_t* n_cuts);
+/* Copy the duals to host arrays (row-major [R, *]); NULL skips a group. */
+GCP_API gcp_status gcp_duals_export(gcp_ctx* ctx, void* duals, double* alpha, double* beta, double* gamma);
+/* Set the duals from host arrays (row-major [R, *]); NULL restores that
+ * group's default initial value. Values are used as given (no projection). */
+GCP_API gcp_status gcp_duals_import(gcp_ctx* ctx, void* duals, const double* alpha, const double* beta,
+                                   const double* gamma);
+GCP_API gcp_status gcp_duals_free(gcp_ctx* ctx, void* duals);
+
+/* ------------------------------------------------------------------ bounds */
+
+/* Evaluate g(alpha, beta, gamma) of Theorem 3.1 at the current duals for all
+ * R rows in chain arithmetic `prec` -> out_bound [R]. certify != 0 also runs
+ * the certification pass -> out_certified [R]: the Lagrangian of Eq. 16 at
+ * the dual point reached, evaluated in float64 with outward rounding and every
+ * rounding residual charged over the variables' boxes, hence a rigorous lower
+ * bound of the subdomain's optimum given sound intermediate bounds and valid
+ * cuts (weak duality, App. A). out_certified may be NULL when certify == 0. */
+GCP_API gcp_status gcp_bound_batch(gcp_ctx* ctx, void* duals, int32_t prec, int32_t certify,
+                                   double* out_bound, double* out_certified);
+
+/* Bound and its gradient d g / d(alpha, beta, gamma) at the current duals
+ * (reverse mode of Theorem 3.1, computed by the adjoint kernels); outputs in
+ * the export layouts. Any output may be NULL. */
+GCP_API gcp_status gcp_grad_batch(gcp_ctx* ctx, void* duals, int32_t prec, double* out_bound,
+                                  double* g_alpha, double* g_beta, double* g_gamma);
+
+/* Run p->iters projected ascent steps on the duals in place (Sec. 3.1; App.
+ * C.1), then evaluate at the final duals: out_bound [R] in p->prec; with
+ * p->certify, out_certified [R] (FP64, outward rounded) and out_err_vs_fp64
+ * [R] = |out_bound - out_certified|. Either of the last two may be NULL. */
+GCP_API gcp_status gcp_optimize_batch(gcp_ctx* ctx, void* duals, const gcp_opt_params* p,
+                                      double* out_bound, double* out_certified, double* out_err_vs_fp64);
+
+/* Device-pointer entry points behind the PyTorch autograd wrapper.
+ * alpha/beta/gamma are float32 device arrays in the export layouts; they
+ * replace the duals object's values (copied in). gcp_bound_device writes the
+ * FP32/BF16 bound [R] to out (device). gcp_grad_device runs the adjoint with
+ * the per-row seed grad_out [R] (device) and writes vector-Jacobian products
+ * into g_alpha/g_beta/g_gamma (device, export layouts). Work is enqueued on
+ * `stream` (cudaStream_t as void*; NULL = the context stream) and the call
+ * returns without synchronising. */
+GCP_API gcp_status gcp_bound_device(gcp_ctx* ctx, void* duals, int32_t prec, const float* alpha,
+                                    const float* beta, const float* gamma, float* out, void* stream);
+GCP_API gcp_status gcp_grad_device(gcp_ctx* ctx, void* duals, int32_t prec, const float* alpha,
+                                   const float* beta, const float* gamma, const float* grad_out,
+                                   float* g_alpha, float* g_beta, float* g_gamma, void* stream);
+
+/* --------------------------------------------------------------- profiling */
+
+/* Launch accounting (process-wide, all contexts). Not a step of the paper's
+ * method: instrumentation for measuring it. After gcp_profile_start every
+ * kernel launch of the library is counted with its algorithmic flops and
+ * bytes (the minimum the launch must compute and move, from its shapes);
+ * launches whose kernel name starts with kernel_prefix ("*" = all, NULL or ""
+ * = none) are also bracketed by CUDA events on their own stream. */
+GCP_API gcp_status gcp_profile_start(const char* kernel_prefix);
+GCP_API gcp_status gcp_profile_stop(void);
+/* Totals since gcp_profile_start for the kernel called `name` (NULL = all):
+ * launches, device time of the timed launches (ms), flops, bytes. Waits for
+ * the timed launches to finish. */
+GCP_API gcp_status gcp_profile_query(const char* name, int64_t* launches, double* total_ms, double* flops,
+                                     double* bytes);
+/* One line per kernel, "name launches timed_launches ms flops bytes\n", into
+ * buf (cap bytes, NUL-terminated); GCP_EINVAL if truncated. */
+GCP_API gcp_status gcp_profile_report(char* buf, int64_t cap);
+
+/* ----------------------------------------------------------------- serving */
+
+/* A verification query for continuous batching: its subdomains (copied),
+ * the optimiser settings of every round, and the number of branch-and-bound
+ * rounds. Each round after the first replaces every subdomain by one child
+ * (one more split on a root-unstable neuron chosen by the request's seed, on
+ * a random side; App. B) and warm-starts its duals from the parent. */
+typedef struct {
+  int32_t net_id, cutset_id, rounds;
+  uint64_t seed;
+  gcp_subdomains sub;
+  gcp_opt_params p;
+} gcp_request;
+
+/* Result of a finished request. certified (caller-allocated, >= rows of the
+ * last round) receives the certified bounds of the last round; min_certified
+ * the minimum over them; latency_ms = completion - submission. */
+typedef struct {
+  gcp_status status;
+  int32_t rows;
+  double* certified;
+  double min_certified;
+  double latency_ms;
+  double max_err_vs_fp64;
+} gcp_result;
+
+/* Start the serving loop: a host scheduler thread admits submitted requests
+ * while at most max_inflight run and their device memory fits the context's
+ * budget, runs each admitted request's rounds on its own stream (requests
+ * overlap on the device), and frees memory as requests finish. */
+GCP_API gcp_status gcp_serve_start(gcp_ctx* ctx, int32_t max_inflight);
+/* Enqueue a request; *ticket identifies it. GCP_EBUDGET if it can never fit. */
+GCP_API gcp_status gcp_serve_submit(gcp_ctx* ctx, const gcp_request* req, uint64_t* ticket);
+/* GCP_PENDING while in flight; otherwise fills *res and forgets the ticket. */
+GCP_API gcp_status gcp_serve_poll(gcp_ctx* ctx, uint64_t ticket, gcp_result* res);
+/* Like poll but waits up to timeout_ms (GCP_ETIMEOUT if still pending). */
+GCP_API gcp_status gcp_serve_wait(gcp_ctx* ctx, uint64_t ticket, int32_t timeout_ms, gcp_result* res);
+/* Stop admitting, finish in-flight requests, join the scheduler thread. */
+GCP_API gcp_status gcp_serve_stop(gcp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GCP_H_ */

@@ -1,0 +1,1372 @@
+// Host implementation of the C ABI in include/gcp.h.
+//
+// Owns device memory (budgeted per context), validates every argument on the
+// host (the kernels trust indices), and sequences the kernels of
+//   eval     : Theorem 3.1 backwards from nu^(L) = -c to the input box,
+//   adjoint  : its reverse-mode derivative (forward through W^(i)),
+//   update   : projected ascent on (alpha, beta, gamma),
+//   certify  : the float64 outward-rounded Lagrangian at the reached duals.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <numeric>
+#include <type_traits>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "gcp_ctx.h"
+
+namespace gcp {
+
+// ------------------------------------------------------------------ errors
+gcp_status Ctx::fail(gcp_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  err = buf;
+  return st;
+}
+
+gcp_status Ctx::cuda(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return GCP_OK;
+  return fail(GCP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void* Ctx::alloc(size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (budget && used + bytes > budget) {
+    over_budget = true;
+    return nullptr;
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  sizes[p] = bytes;
+  used += bytes;
+  reg_alloc(p, bytes);
+  return p;
+}
+
+void Ctx::release(void* p) {
+  if (!p) return;
+  auto it = sizes.find(p);
+  if (it != sizes.end()) {
+    used -= it->second;
+    sizes.erase(it);
+  }
+  reg_free(p);
+  cudaFree(p);
+}
+
+template <typename T>
+T* upload(Ctx& c, const T* host, size_t n, gcp_status* st) {
+  T* d = static_cast<T*>(c.alloc(n * sizeof(T)));
+  if (!d) {
+    *st = c.over_budget ? c.fail(GCP_EBUDGET, "device memory budget exceeded")
+                        : c.fail(GCP_ENOMEM, "cudaMalloc of %zu bytes failed", n * sizeof(T));
+    return nullptr;
+  }
+  if (n && host) {
+    cudaError_t e = cudaMemcpy(d, host, n * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      *st = c.cuda(e, "upload");
+      return nullptr;
+    }
+  }
+  *st = GCP_OK;
+  return d;
+}
+
+static std::vector<float> to_f32(const double* p, size_t n) {
+  std::vector<float> v(n);
+  for (size_t i = 0; i < n; ++i) v[i] = (float)p[i];
+  return v;
+}
+static std::vector<__nv_bfloat16> to_bf16(const double* p, size_t n) {
+  std::vector<__nv_bfloat16> v(n);
+  for (size_t i = 0; i < n; ++i) v[i] = __float2bfloat16_rn((float)p[i]);
+  return v;
+}
+
+Net::~Net() {
+  for (void* p : owned) ctx->release(p);
+}
+CutDev::~CutDev() {
+  for (void* p : owned) ctx->release(p);
+}
+Batch::~Batch() {
+  for (void* p : owned) ctx->release(p);
+  for (auto& kv : lazy) ctx->release(kv.second);
+}
+
+void* Batch::ws(const std::string& name, size_t bytes, gcp_status* st) {
+  auto it = lazy.find(name);
+  if (it != lazy.end()) {
+    if (lazy_bytes[name] >= bytes) return it->second;
+    ctx->release(it->second);
+    lazy.erase(it);
+  }
+  void* p = ctx->alloc(bytes);
+  if (!p) {
+    *st = ctx->over_budget ? ctx->fail(GCP_EBUDGET, "device memory budget exceeded (%s)", name.c_str())
+                           : ctx->fail(GCP_ENOMEM, "cudaMalloc of %zu bytes failed (%s)", bytes, name.c_str());
+    return nullptr;
+  }
+  lazy[name] = p;
+  lazy_bytes[name] = bytes;
+  return p;
+}
+
+// Launch-check problems (a skipped launch) and CUDA launch errors of a sequence.
+gcp_status launch_status(Ctx& c, const char* what) {
+  std::string e = reg_take_error();
+  if (!e.empty()) return c.fail(GCP_EDEVICE, "%s: %s", what, e.c_str());
+  return c.cuda(cudaGetLastError(), what);
+}
+
+// Synchronise and report CUDA errors, then failed in-kernel index checks.
+gcp_status sync_check(Ctx& c, cudaStream_t st, const char* what) {
+  gcp_status s = c.cuda(cudaStreamSynchronize(st), what);
+  if (s) return s;
+  std::string e = take_device_error(st);
+  if (!e.empty()) return c.fail(GCP_EDEVICE, "%s: %s", what, e.c_str());
+  return GCP_OK;
+}
+
+// Higham's gamma_n = n u / (1 - n u) with a safety factor for the host rounding.
+static double gamma_n_host(int64_t n) {
+  const double u = std::ldexp(1.0, -53);
+  const double nu = (double)n * u;
+  return nu / (1.0 - nu) * (1.0 + std::ldexp(1.0, -30));
+}
+
+// reduction length of y^(i-1) = W^(i)^T nu^(i) (the K of the backward product)
+static int64_t red_len(const LayerGeom& g) {
+  return g.kind == GCP_DENSE ? g.d_out : (int64_t)g.c_out * g.k * g.k;
+}
+
+// ------------------------------------------------------------------ net
+gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const double* x_lo, const double* x_hi,
+                    const double* spec_c, int n_spec, const double* inter_lo, const double* inter_hi, int* out_id) {
+  if (!layers || n_layers < 1 || !x_lo || !x_hi || !spec_c || n_spec < 1 || !out_id)
+    return c.fail(GCP_EINVAL, "gcp_init_net: null argument or empty network/spec");
+  auto net = std::make_unique<Net>();
+  net->ctx = &c;
+  net->L = n_layers;
+  net->K = n_spec;
+  for (int i = 0; i < n_layers; ++i) {
+    const gcp_layer_desc& d = layers[i];
+    LayerGeom g{};
+    g.kind = d.kind;
+    g.d_in = d.d_in;
+    g.d_out = d.d_out;
+    if (d.kind == GCP_DENSE) {
+      if (d.d_in <= 0 || d.d_out <= 0) return c.fail(GCP_EINVAL, "layer %d: bad dense shape", i + 1);
+    } else if (d.kind == GCP_CONV2D) {
+      g.c_in = d.c_in; g.h_in = d.h_in; g.w_in = d.w_in; g.c_out = d.c_out; g.h_out = d.h_out;
+      g.w_out = d.w_out; g.k = d.k; g.stride = d.stride; g.pad = d.pad;
+      if (d.c_in <= 0 || d.h_in <= 0 || d.w_in <= 0 || d.c_out <= 0 || d.k <= 0 || d.stride <= 0 || d.pad < 0 ||
+          d.h_out != (d.h_in + 2 * d.pad - d.k) / d.stride + 1 || d.w_out != (d.w_in + 2 * d.pad - d.k) / d.stride + 1 ||
+          d.d_in != d.c_in * d.h_in * d.w_in || d.d_out != d.c_out * d.h_out * d.w_out || d.h_out <= 0 || d.w_out <= 0)
+        return c.fail(GCP_EINVAL, "layer %d: inconsistent conv2d geometry", i + 1);
+      if (i == n_layers - 1) return c.fail(GCP_EINVAL, "the last (spec) layer must be dense");
+    } else {
+      return c.fail(GCP_EINVAL, "layer %d: unknown kind %d", i + 1, d.kind);
+    }
+    if (i > 0 && d.d_in != layers[i - 1].d_out) return c.fail(GCP_EINVAL, "layer %d: d_in mismatch", i + 1);
+    if (!d.W || !d.b) return c.fail(GCP_EINVAL, "layer %d: null W or b", i + 1);
+    net->geom.push_back(g);
+  }
+  net->dims.push_back(layers[0].d_in);
+  for (int i = 0; i < n_layers; ++i) net->dims.push_back(layers[i].d_out);
+  const int L = n_layers;
+  const int d0 = net->dims[0], dL = net->dims[L];
+  int64_t nh = 0;
+  for (int i = 1; i < L; ++i) nh += net->dims[i];
+  if (nh > 0 && (!inter_lo || !inter_hi)) return c.fail(GCP_EINVAL, "intermediate bounds required");
+  for (int j = 0; j < d0; ++j)
+    if (!(x_lo[j] <= x_hi[j]) || !std::isfinite(x_lo[j]) || !std::isfinite(x_hi[j]))
+      return c.fail(GCP_EINVAL, "input box: x_lo > x_hi or non-finite at %d", j);
+  for (int64_t j = 0; j < nh; ++j)
+    if (!(inter_lo[j] <= inter_hi[j]) || !std::isfinite(inter_lo[j]) || !std::isfinite(inter_hi[j]))
+      return c.fail(GCP_EINVAL, "intermediate bounds: lo > hi or non-finite at %lld", (long long)j);
+  for (int64_t j = 0; j < (int64_t)n_spec * dL; ++j)
+    if (!std::isfinite(spec_c[j])) return c.fail(GCP_EINVAL, "spec: non-finite entry");
+  gcp_status st = GCP_OK;
+#define UP(dst, T, host, n)                    \
+  do {                                         \
+    dst = upload<T>(c, host, n, &st);          \
+    if (!dst) return st;                       \
+    net->owned.push_back((void*)dst);          \
+  } while (0)
+  for (int i = 0; i < L; ++i) {
+    const gcp_layer_desc& d = layers[i];
+    const LayerGeom& g = net->geom[i];
+    size_t nw = g.kind == GCP_DENSE ? (size_t)g.d_out * g.d_in : (size_t)g.c_out * g.c_in * g.k * g.k;
+    for (size_t q = 0; q < nw; ++q)
+      if (!std::isfinite(d.W[q])) return c.fail(GCP_EINVAL, "layer %d: non-finite weight", i + 1);
+    for (int q = 0; q < g.d_out; ++q)
+      if (!std::isfinite(d.b[q])) return c.fail(GCP_EINVAL, "layer %d: non-finite bias", i + 1);
+    double *w64, *wt64 = nullptr, *b64;
+    float *w32, *wt32 = nullptr, *b32;
+    __nv_bfloat16 *w16, *wt16 = nullptr;
+    UP(w64, double, d.W, nw);
+    auto wf = to_f32(d.W, nw);
+    UP(w32, float, wf.data(), nw);
+    auto wh = to_bf16(d.W, nw);
+    UP(w16, __nv_bfloat16, wh.data(), nw);
+    if (g.kind == GCP_DENSE) {
+      std::vector<double> t(nw);
+      for (int o = 0; o < g.d_out; ++o)
+        for (int q = 0; q < g.d_in; ++q) t[(size_t)q * g.d_out + o] = d.W[(size_t)o * g.d_in + q];
+      UP(wt64, double, t.data(), nw);
+      auto tf = to_f32(t.data(), nw);
+      UP(wt32, float, tf.data(), nw);
+      auto th = to_bf16(t.data(), nw);
+      UP(wt16, __nv_bfloat16, th.data(), nw);
+    }
+    UP(b64, double, d.b, g.d_out);
+    auto bf = to_f32(d.b, g.d_out);
+    UP(b32, float, bf.data(), g.d_out);
+    net->W64.push_back(w64); net->WT64.push_back(wt64); net->b64.push_back(b64);
+    net->W32.push_back(w32); net->WT32.push_back(wt32); net->b32.push_back(b32);
+    net->W16.push_back(w16); net->WT16.push_back(wt16);
+  }
+  UP(net->xlo64, double, x_lo, d0);
+  UP(net->xhi64, double, x_hi, d0);
+  auto xl = to_f32(x_lo, d0), xh = to_f32(x_hi, d0);
+  UP(net->xlo32, float, xl.data(), d0);
+  UP(net->xhi32, float, xh.data(), d0);
+  UP(net->C64, double, spec_c, (size_t)n_spec * dL);
+  std::vector<double> negc((size_t)n_spec * dL);
+  for (size_t q = 0; q < negc.size(); ++q) negc[q] = -spec_c[q];
+  UP(net->negC64, double, negc.data(), negc.size());
+  // y^(L-1) = W^(L)^T nu^(L) = -W^(L)^T c_k and c_k^T b^(L), per spec row
+  const gcp_layer_desc& last = layers[L - 1];
+  const int dl1 = net->dims[L - 1];
+  std::vector<double> yl((size_t)n_spec * dl1, 0.0), cb(n_spec, 0.0);
+  for (int k = 0; k < n_spec; ++k) {
+    for (int q = 0; q < dL; ++q) {
+      const double cv = spec_c[(size_t)k * dL + q];
+      cb[k] += cv * last.b[q];
+      for (int j = 0; j < dl1; ++j) yl[(size_t)k * dl1 + j] -= cv * last.W[(size_t)q * dl1 + j];
+    }
+  }
+  UP(net->YL64, double, yl.data(), yl.size());
+  auto ylf = to_f32(yl.data(), yl.size());
+  UP(net->YL32, float, ylf.data(), ylf.size());
+  UP(net->cb64, double, cb.data(), n_spec);
+  auto cbf = to_f32(cb.data(), n_spec);
+  UP(net->cb32, float, cbf.data(), n_spec);
+  UP(net->bL64, double, last.b, dL);
+  int64_t off = 0;
+  for (int i = 1; i < L; ++i) {
+    const int di = net->dims[i];
+    double *lo, *hi;
+    float *lof, *hif;
+    UP(lo, double, inter_lo + off, di);
+    UP(hi, double, inter_hi + off, di);
+    auto a = to_f32(inter_lo + off, di), b = to_f32(inter_hi + off, di);
+    // float copies rounded outwards so that float classification never
+    // treats an unstable neuron as stable
+    for (int j = 0; j < di; ++j) {
+      if ((double)a[j] > inter_lo[off + j]) a[j] = std::nextafter(a[j], -INFINITY);
+      if ((double)b[j] < inter_hi[off + j]) b[j] = std::nextafter(b[j], INFINITY);
+    }
+    UP(lof, float, a.data(), di);
+    UP(hif, float, b.data(), di);
+    net->lo64.push_back(lo); net->hi64.push_back(hi); net->lo32.push_back(lof); net->hi32.push_back(hif);
+    off += di;
+  }
+#undef UP
+  int id = c.next_id++;
+  c.nets[id] = std::move(net);
+  *out_id = id;
+  return GCP_OK;
+}
+
+// ------------------------------------------------------------------ cuts
+gcp_status add_cuts(Ctx& c, int net_id, int n_cuts, const int64_t* row_ptr, const int16_t* layer, const int8_t* kind,
+                    const int32_t* index, const double* coef, const double* d, int* cutset_id, int* first_cut) {
+  auto it = c.nets.find(net_id);
+  if (it == c.nets.end()) return c.fail(GCP_ENOTFOUND, "unknown net %d", net_id);
+  if (!cutset_id || n_cuts < 0 || (n_cuts > 0 && (!row_ptr || !d))) return c.fail(GCP_EINVAL, "gcp_add_cuts: bad arguments");
+  Net& net = *it->second;
+  CutSet* cs = nullptr;
+  if (*cutset_id < 0) {
+    auto p = std::make_unique<CutSet>();
+    p->net_id = net_id;
+    p->ptr.push_back(0);
+    int id = c.next_id++;
+    cs = p.get();
+    c.cutsets[id] = std::move(p);
+    *cutset_id = id;
+  } else {
+    auto ci = c.cutsets.find(*cutset_id);
+    if (ci == c.cutsets.end()) return c.fail(GCP_ENOTFOUND, "unknown cut set %d", *cutset_id);
+    cs = ci->second.get();
+    if (cs->net_id != net_id) return c.fail(GCP_EINVAL, "cut set %d belongs to net %d", *cutset_id, cs->net_id);
+  }
+  if (n_cuts > 0) {
+    if (row_ptr[0] != 0) return c.fail(GCP_EINVAL, "row_ptr[0] must be 0");
+    const int64_t nnz = row_ptr[n_cuts];
+    if (nnz > 0 && (!layer || !kind || !index || !coef)) return c.fail(GCP_EINVAL, "null cut entry arrays");
+    for (int k = 0; k < n_cuts; ++k) {
+      if (row_ptr[k + 1] < row_ptr[k]) return c.fail(GCP_EINVAL, "row_ptr not monotone at cut %d", k);
+      if (!std::isfinite(d[k])) return c.fail(GCP_EINVAL, "cut %d: non-finite d", k);
+    }
+    for (int64_t e = 0; e < nnz; ++e) {
+      const int li = layer[e];
+      if (li < 0 || li >= net.L) return c.fail(GCP_EINVAL, "entry %lld: layer %d out of range", (long long)e, li);
+      if (kind[e] < 0 || kind[e] > 2) return c.fail(GCP_EINVAL, "entry %lld: bad kind", (long long)e);
+      if (li == 0 && kind[e] != GCP_VAR_X) return c.fail(GCP_EINVAL, "entry %lld: input variables have kind X", (long long)e);
+      if (index[e] < 0 || index[e] >= net.dims[li]) return c.fail(GCP_EINVAL, "entry %lld: index out of range", (long long)e);
+      if (!std::isfinite(coef[e])) return c.fail(GCP_EINVAL, "entry %lld: non-finite coef", (long long)e);
+    }
+    if ((int64_t)cs->d.size() + n_cuts > 65535) return c.fail(GCP_EINVAL, "at most 65535 cuts per set");
+    const int64_t base = cs->ptr.back();
+    if (first_cut) *first_cut = (int)cs->d.size();
+    for (int k = 0; k < n_cuts; ++k) {
+      cs->d.push_back(d[k]);
+      cs->ptr.push_back(base + row_ptr[k + 1]);
+    }
+    cs->layer.insert(cs->layer.end(), layer, layer + nnz);
+    cs->kind.insert(cs->kind.end(), kind, kind + nnz);
+    cs->index.insert(cs->index.end(), index, index + nnz);
+    cs->coef.insert(cs->coef.end(), coef, coef + nnz);
+  } else if (first_cut) {
+    *first_cut = (int)cs->d.size();
+  }
+  return GCP_OK;
+}
+
+// Device copy of a cut set: CSR by cut for the gather, CSC by (layer, neuron).
+gcp_status build_cutdev(Ctx& c, const Net& net, const CutSet* cs, CutDev& out) {
+  out.ctx = &c;
+  const int L = net.L;
+  out.N = cs ? (int)cs->d.size() : 0;
+  out.nnz = cs ? (int64_t)cs->coef.size() : 0;
+  std::vector<int64_t> poff(L + 1, 0);
+  for (int i = 0; i < L; ++i) poff[i + 1] = poff[i] + net.dims[i] + 1;
+  out.poff = poff;
+  std::vector<int32_t> cut_of(out.nnz);
+  for (int k = 0; k < out.N; ++k)
+    for (int64_t e = cs->ptr[k]; e < cs->ptr[k + 1]; ++e) cut_of[e] = k;
+  std::vector<int64_t> order(out.nnz);
+  std::iota(order.begin(), order.end(), 0);
+  if (out.nnz)
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+      if (cs->layer[a] != cs->layer[b]) return cs->layer[a] < cs->layer[b];
+      return cs->index[a] < cs->index[b];
+    });
+  std::vector<int32_t> cptr(poff[L], 0), ccut(out.nnz), ceid(out.nnz);
+  std::vector<int8_t> ckind(out.nnz);
+  std::vector<double> ccoef(out.nnz);
+  std::vector<int64_t> cnt(poff[L], 0);
+  for (int64_t e = 0; e < out.nnz; ++e) cnt[poff[cs->layer[e]] + cs->index[e]]++;
+  out.layer_nnz.assign(L, 0);
+  for (int64_t e = 0; e < out.nnz; ++e) out.layer_nnz[cs->layer[e]]++;
+  for (int i = 0; i < L; ++i) {
+    int64_t run = 0;
+    // entries of layer i start after all entries of layers < i
+    for (int q = 0; q < i; ++q)
+      for (int j = 0; j < net.dims[q]; ++j) run += cnt[poff[q] + j];
+    for (int j = 0; j <= net.dims[i]; ++j) {
+      cptr[poff[i] + j] = (int32_t)run;
+      if (j < net.dims[i]) run += cnt[poff[i] + j];
+    }
+  }
+  for (int64_t q = 0; q < out.nnz; ++q) {
+    const int64_t e = order[q];
+    ccut[q] = cut_of[e];
+    ckind[q] = cs->kind[e];
+    ccoef[q] = cs->coef[e];
+    ceid[q] = (int32_t)e;
+  }
+  std::vector<int32_t> cp32(out.N + 1, 0);
+  for (int k = 0; k <= out.N; ++k) cp32[k] = (int32_t)(cs ? cs->ptr[k] : 0);
+  std::vector<double> dd = cs ? cs->d : std::vector<double>();
+  gcp_status st = GCP_OK;
+#define UPC(dst, T, host, n)                   \
+  do {                                         \
+    dst = upload<T>(c, host, n, &st);          \
+    if (!dst) return st;                       \
+    out.owned.push_back((void*)dst);           \
+  } while (0)
+  UPC(out.cut_ptr, int32_t, cp32.data(), cp32.size());
+  UPC(out.d64, double, dd.data(), dd.size());
+  auto df = to_f32(dd.data(), dd.size());
+  UPC(out.d32, float, df.data(), df.size());
+  UPC(out.csc_ptr, int32_t, cptr.data(), cptr.size());
+  UPC(out.csc_cut, int32_t, ccut.data(), ccut.size());
+  UPC(out.csc_kind, int8_t, ckind.data(), ckind.size());
+  UPC(out.csc_coef64, double, ccoef.data(), ccoef.size());
+  auto cf = to_f32(ccoef.data(), ccoef.size());
+  UPC(out.csc_coef32, float, cf.data(), cf.size());
+  UPC(out.csc_eid, int32_t, ceid.data(), ceid.size());
+#undef UPC
+  return GCP_OK;
+}
+
+// ------------------------------------------------------------------ duals
+gcp_status duals_create(Ctx& c, int net_id, int cutset_id, const gcp_subdomains* sub, int dual_prec, Batch** out) {
+  auto it = c.nets.find(net_id);
+  if (it == c.nets.end()) return c.fail(GCP_ENOTFOUND, "unknown net %d", net_id);
+  if (!sub || !out || sub->n_sub < 0) return c.fail(GCP_EINVAL, "gcp_duals_create: bad arguments");
+  if (dual_prec != GCP_FP64 && dual_prec != GCP_FP32) return c.fail(GCP_EINVAL, "dual_prec must be FP64 or FP32");
+  Net& net = *it->second;
+  const CutSet* cs = nullptr;
+  if (cutset_id >= 0) {
+    auto ci = c.cutsets.find(cutset_id);
+    if (ci == c.cutsets.end()) return c.fail(GCP_ENOTFOUND, "unknown cut set %d", cutset_id);
+    if (ci->second->net_id != net_id) return c.fail(GCP_EINVAL, "cut set of another net");
+    cs = ci->second.get();
+  }
+  const int S = sub->n_sub;
+  if (S > 0 && !sub->split_ptr) return c.fail(GCP_EINVAL, "null split_ptr");
+  std::vector<int32_t> sptr(S + 1, 0);
+  int M = 0;
+  if (S > 0) {
+    if (sub->split_ptr[0] != 0) return c.fail(GCP_EINVAL, "split_ptr[0] must be 0");
+    for (int s = 0; s < S; ++s) {
+      const int n = sub->split_ptr[s + 1] - sub->split_ptr[s];
+      if (n < 0 || n > kMaxSplits) return c.fail(GCP_EINVAL, "subdomain %d: 0..%d splits allowed", s, kMaxSplits);
+      M = std::max(M, n);
+    }
+    std::copy(sub->split_ptr, sub->split_ptr + S + 1, sptr.begin());
+  }
+  const int64_t nsp = sptr[S];
+  if (nsp > 0 && (!sub->split_layer || !sub->split_index || !sub->split_sign)) return c.fail(GCP_EINVAL, "null split arrays");
+  for (int s = 0; s < S; ++s)
+    for (int q = sptr[s]; q < sptr[s + 1]; ++q) {
+      const int li = sub->split_layer[q];
+      if (li < 1 || li >= net.L) return c.fail(GCP_EINVAL, "split %d: layer %d not hidden", q, li);
+      if (sub->split_index[q] < 0 || sub->split_index[q] >= net.dims[li]) return c.fail(GCP_EINVAL, "split %d: index out of range", q);
+      if (sub->split_sign[q] != 1 && sub->split_sign[q] != -1) return c.fail(GCP_EINVAL, "split %d: sign must be +-1", q);
+      for (int q2 = sptr[s]; q2 < q; ++q2)
+        if (sub->split_layer[q2] == li && sub->split_index[q2] == sub->split_index[q])
+          return c.fail(GCP_EINVAL, "subdomain %d splits a neuron twice", s);
+    }
+  auto b = std::make_unique<Batch>();
+  b->ctx = &c;
+  b->net = &net;
+  b->net_id = net_id;
+  b->S = S;
+  b->K = net.K;
+  b->R = (int64_t)S * net.K;
+  b->M = M;
+  b->fp64 = dual_prec == GCP_FP64;
+  gcp_status st = build_cutdev(c, net, cs, b->cuts);
+  if (st) return st;
+  b->N = b->cuts.N;
+  b->nnz = b->cuts.nnz;
+  b->nsp = nsp;
+#define UPB(dst, T, host, n)                   \
+  do {                                         \
+    dst = upload<T>(c, host, n, &st);          \
+    if (!dst) return st;                       \
+    b->owned.push_back((void*)dst);            \
+  } while (0)
+  UPB(b->sp_ptr, int32_t, sptr.data(), S + 1);
+  UPB(b->sp_layer, int16_t, sub->split_layer, nsp);
+  UPB(b->sp_index, int32_t, sub->split_index, nsp);
+  UPB(b->sp_sign, int8_t, sub->split_sign, nsp);
+  const size_t es = b->fp64 ? 8 : 4;
+  for (int i = 1; i < net.L; ++i) {
+    void* p = c.alloc((size_t)b->R * net.dims[i] * es);
+    if (!p) return c.fail(c.over_budget ? GCP_EBUDGET : GCP_ENOMEM, "alpha allocation failed");
+    b->owned.push_back(p);
+    b->alpha.push_back(p);
+  }
+  b->beta = c.alloc((size_t)std::max(M, 1) * b->R * es);
+  if (!b->beta) return c.fail(c.over_budget ? GCP_EBUDGET : GCP_ENOMEM, "beta allocation failed");
+  b->owned.push_back(b->beta);
+  b->gamma = c.alloc((size_t)std::max(b->N, 1) * b->R * es);
+  if (!b->gamma) return c.fail(c.over_budget ? GCP_EBUDGET : GCP_ENOMEM, "gamma allocation failed");
+  b->owned.push_back(b->gamma);
+#undef UPB
+  st = reset_duals(c, *b, true, true, true);
+  if (st) return st;
+  *out = b.get();
+  c.batches[b.get()] = std::move(b);
+  return GCP_OK;
+}
+
+gcp_status reset_duals(Ctx& c, Batch& b, bool a, bool be, bool g) {
+  cudaStream_t st = c.stream;
+  const Net& net = *b.net;
+  const size_t es = b.fp64 ? 8 : 4;
+  SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp};
+  if (a)
+    for (int i = 1; i < net.L; ++i) {
+      if (b.fp64)
+        default_alpha<double>(st, b.R, b.K, net.dims[i], i, net.lo64[i - 1], net.hi64[i - 1], sp, (double*)b.alpha[i - 1]);
+      else
+        default_alpha<float>(st, b.R, b.K, net.dims[i], i, net.lo32[i - 1], net.hi32[i - 1], sp, (float*)b.alpha[i - 1]);
+    }
+  if (be) cudaMemsetAsync(b.beta, 0, (size_t)std::max(b.M, 1) * b.R * es, st);
+  if (g) cudaMemsetAsync(b.gamma, 0, (size_t)std::max(b.N, 1) * b.R * es, st);
+  {
+    std::string e = reg_take_error();
+    if (!e.empty()) return c.fail(GCP_EDEVICE, "reset duals: %s", e.c_str());
+  }
+  // Adam moments restart with the duals
+  for (const char* nm : {"m_alpha", "v_alpha", "m_beta", "v_beta", "m_gamma", "v_gamma"}) {
+    auto it = b.lazy.find(nm);
+    if (it != b.lazy.end()) cudaMemsetAsync(it->second, 0, b.lazy_bytes[nm], st);
+  }
+  return c.cuda(cudaGetLastError(), "reset duals");
+}
+
+// ------------------------------------------------------------------ chain drivers
+template <typename T>
+struct TSel;
+template <>
+struct TSel<double> {
+  static const double* lo(const Net& n, int i) { return n.lo64[i - 1]; }
+  static const double* hi(const Net& n, int i) { return n.hi64[i - 1]; }
+  static const double* b(const Net& n, int i) { return n.b64[i - 1]; }
+  static const double* xlo(const Net& n) { return n.xlo64; }
+  static const double* xhi(const Net& n) { return n.xhi64; }
+  static const double* YL(const Net& n) { return n.YL64; }
+  static const double* cb(const Net& n) { return n.cb64; }
+  static const double* coef(const CutDev& c) { return c.csc_coef64; }
+  static const double* d(const CutDev& c) { return c.d64; }
+};
+template <>
+struct TSel<float> {
+  static const float* lo(const Net& n, int i) { return n.lo32[i - 1]; }
+  static const float* hi(const Net& n, int i) { return n.hi32[i - 1]; }
+  static const float* b(const Net& n, int i) { return n.b32[i - 1]; }
+  static const float* xlo(const Net& n) { return n.xlo32; }
+  static const float* xhi(const Net& n) { return n.xhi32; }
+  static const float* YL(const Net& n) { return n.YL32; }
+  static const float* cb(const Net& n) { return n.cb32; }
+  static const float* coef(const CutDev& c) { return c.csc_coef32; }
+  static const float* d(const CutDev& c) { return c.d32; }
+};
+template <typename Top>
+struct WSel;
+template <>
+struct WSel<double> {
+  static const double* W(const Net& n, int i) { return n.W64[i - 1]; }
+  static const double* WT(const Net& n, int i) { return n.WT64[i - 1]; }
+};
+template <>
+struct WSel<float> {
+  static const float* W(const Net& n, int i) { return n.W32[i - 1]; }
+  static const float* WT(const Net& n, int i) { return n.WT32[i - 1]; }
+};
+template <>
+struct WSel<__nv_bfloat16> {
+  static const __nv_bfloat16* W(const Net& n, int i) { return n.W16[i - 1]; }
+  static const __nv_bfloat16* WT(const Net& n, int i) { return n.WT16[i - 1]; }
+};
+
+template <typename T>
+CutCSC<T> csc_of(const Batch& b, int layer) {
+  const CutDev& c = b.cuts;
+  return CutCSC<T>{c.csc_ptr + c.poff[layer], c.csc_cut, c.csc_kind, TSel<T>::coef(c), c.csc_eid,
+                   c.layer_nnz.empty() ? 0 : c.layer_nnz[layer], c.nnz};
+}
+
+int64_t Batch::dmax() const {
+  int64_t m = 1;
+  for (int i = 0; i < net->L; ++i) m = std::max<int64_t>(m, net->dims[i]);
+  return m;
+}
+int Batch::n_partials() const {
+  int p = 0;
+  for (int i = 0; i < net->L; ++i) p += (net->dims[i] + kChunk - 1) / kChunk;
+  return p;
+}
+
+// Linear backward step y^(i-1) = W^(i)^T nu^(i) for all rows.
+template <typename Top, typename T>
+static void lin_backward(cudaStream_t st, const Net& net, int i, int64_t R, const Top* nu, T* y) {
+  const LayerGeom& g = net.geom[i - 1];
+  if (g.kind == GCP_DENSE) gemm_nt<Top, T>(st, R, g.d_in, g.d_out, nu, 0, WSel<Top>::WT(net, i), y);
+  else conv_T<Top, T>(st, R, g, WSel<Top>::W(net, i), nu, y);
+}
+// Linear forward step nubar^(i) = W^(i) a for all rows.
+template <typename Top, typename T>
+static void lin_forward(cudaStream_t st, const Net& net, int i, int64_t R, const Top* a, T* out) {
+  const LayerGeom& g = net.geom[i - 1];
+  if (g.kind == GCP_DENSE) gemm_nt<Top, T>(st, R, g.d_out, g.d_in, a, 0, WSel<Top>::W(net, i), out);
+  else conv_fwd<Top, T>(st, R, g, WSel<Top>::W(net, i), a, out);
+}
+
+// Evaluate g for all rows at the batch's duals. with_adjoint_start: also write
+// a0 = -seed*x* into the operand buffer and the input-layer cut entries into E.
+template <typename T, typename Top>
+gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, const T* seed) {
+  const Net& net = *b.net;
+  const int L = net.L;
+  const int64_t R = b.R;
+  gcp_status s = GCP_OK;
+  Top* nu = (Top*)b.ws("nu", (size_t)R * b.dmax() * sizeof(Top), &s);
+  if (!nu) return s;
+  T* y = (T*)b.ws("y", (size_t)R * b.dmax() * sizeof(T), &s);
+  if (!y) return s;
+  T* part = (T*)b.ws("obj_part", (size_t)b.n_partials() * R * sizeof(T), &s);
+  if (!part) return s;
+  T* g = (T*)b.ws("g", (size_t)std::max<int64_t>(R, 1) * sizeof(T), &s);
+  if (!g) return s;
+  T* E = nullptr;
+  if (with_adjoint_start && b.nnz) {
+    E = (T*)b.ws("E", (size_t)b.nnz * R * sizeof(T), &s);
+    if (!E) return s;
+  }
+  SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp};
+  int poff = 0;
+  for (int i = L - 1; i >= 1; --i) {
+    T* nuhat = (T*)b.ws("nuhat" + std::to_string(i), (size_t)R * net.dims[i] * sizeof(T), &s);
+    if (!nuhat) return s;
+    RelaxArgs<T, Top> a{};
+    a.R = R; a.K = b.K; a.d = net.dims[i]; a.layer = i; a.M = b.M; a.N = b.N;
+    a.y = (i == L - 1) ? TSel<T>::YL(net) : y;
+    a.y_per_spec = (i == L - 1);
+    a.lo = TSel<T>::lo(net, i); a.hi = TSel<T>::hi(net, i); a.bias = TSel<T>::b(net, i);
+    a.alpha = (const T*)b.alpha[i - 1];
+    a.beta = (const T*)b.beta;
+    a.gamma = (const T*)b.gamma;
+    a.sp = sp;
+    a.csc = csc_of<T>(b, i);
+    a.nu_out = nu;
+    a.nuhat_out = nuhat;
+    a.obj_part = part + (int64_t)poff * R;
+    relax_eval<T, Top>(st, a);
+    poff += (net.dims[i] + kChunk - 1) / kChunk;
+    lin_backward<Top, T>(st, net, i, R, nu, y);
+  }
+  ConcArgs<T, Top> ca{};
+  ca.R = R; ca.K = b.K; ca.d0 = net.dims[0]; ca.N = b.N;
+  ca.y0 = y;
+  ca.x_lo = TSel<T>::xlo(net); ca.x_hi = TSel<T>::xhi(net);
+  ca.gamma = (const T*)b.gamma;
+  ca.seed = seed;
+  ca.csc = csc_of<T>(b, 0);
+  ca.a0_out = with_adjoint_start ? nu : nullptr;
+  ca.E = E;
+  ca.obj_part = part + (int64_t)poff * R;
+  concretize<T, Top>(st, ca);
+  poff += (net.dims[0] + kChunk - 1) / kChunk;
+  FinalArgs<T> fa{R, b.K, b.N, poff, TSel<T>::cb(net), TSel<T>::d(b.cuts), (const T*)b.gamma, part, g};
+  finalize_bound<T>(st, fa);
+  return launch_status(c, "eval");
+}
+
+// Reverse pass after run_eval(with_adjoint_start): gradients or an update step.
+template <typename T, typename Top>
+gcp_status run_adjoint(Ctx& c, Batch& b, cudaStream_t st, const StepArgs<T>& step, const T* seed, T* gal, T* gbe,
+                       T* gga) {
+  const Net& net = *b.net;
+  const int L = net.L;
+  const int64_t R = b.R;
+  gcp_status s = GCP_OK;
+  Top* abuf = (Top*)b.ws("nu", (size_t)R * b.dmax() * sizeof(Top), &s);
+  T* y = (T*)b.ws("y", (size_t)R * b.dmax() * sizeof(T), &s);
+  if (!abuf || !y) return s;
+  T* E = b.nnz ? (T*)b.ws("E", (size_t)b.nnz * R * sizeof(T), &s) : nullptr;
+  if (b.nnz && !E) return s;
+  T *ma = nullptr, *va = nullptr, *mb = nullptr, *vb = nullptr, *mg = nullptr, *vg = nullptr;
+  int64_t nal = 0;
+  for (int i = 1; i < L; ++i) nal += (int64_t)R * net.dims[i];
+  if (step.mode == 2) {
+    const size_t ab = (size_t)nal * sizeof(T), bb = (size_t)std::max(b.M, 1) * R * sizeof(T),
+                 gb = (size_t)std::max(b.N, 1) * R * sizeof(T);
+    bool fresh = b.lazy.find("m_alpha") == b.lazy.end();
+    ma = (T*)b.ws("m_alpha", ab, &s); va = (T*)b.ws("v_alpha", ab, &s);
+    mb = (T*)b.ws("m_beta", bb, &s); vb = (T*)b.ws("v_beta", bb, &s);
+    mg = (T*)b.ws("m_gamma", gb, &s); vg = (T*)b.ws("v_gamma", gb, &s);
+    if (!ma || !va || !mb || !vb || !mg || !vg) return s;
+    if (fresh) {
+      cudaMemsetAsync(ma, 0, ab, st); cudaMemsetAsync(va, 0, ab, st);
+      cudaMemsetAsync(mb, 0, bb, st); cudaMemsetAsync(vb, 0, bb, st);
+      cudaMemsetAsync(mg, 0, gb, st); cudaMemsetAsync(vg, 0, gb, st);
+    }
+  }
+  SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp};
+  int64_t aoff = 0;
+  for (int i = 1; i < L; ++i) {
+    lin_forward<Top, T>(st, net, i, R, abuf, y);
+    const T* nuhat = (const T*)b.lazy["nuhat" + std::to_string(i)];
+    AdjArgs<T, Top> a{};
+    a.R = R; a.K = b.K; a.d = net.dims[i]; a.layer = i; a.M = b.M; a.N = b.N;
+    a.nubar = y; a.seed = seed;
+    a.lo = TSel<T>::lo(net, i); a.hi = TSel<T>::hi(net, i); a.bias = TSel<T>::b(net, i);
+    a.alpha = (T*)b.alpha[i - 1];
+    a.beta = (T*)b.beta;
+    a.gamma = (const T*)b.gamma;
+    a.nuhat = nuhat;
+    a.sp = sp;
+    a.csc = csc_of<T>(b, i);
+    a.a_out = (i < L - 1) ? abuf : nullptr;
+    a.E = E;
+    a.g_alpha = gal ? gal + aoff : nullptr;
+    a.g_beta = gbe;
+    if (ma) { a.m_alpha = ma + aoff; a.v_alpha = va + aoff; a.m_beta = mb; a.v_beta = vb; }
+    a.st = step;
+    relax_adjoint<T, Top>(st, a);
+    aoff += (int64_t)R * net.dims[i];
+  }
+  if (b.N > 0) {
+    GatherArgs<T> ga{R, b.N, b.cuts.cut_ptr, E, TSel<T>::d(b.cuts), seed, (T*)b.gamma, gga, mg, vg, step, b.nnz};
+    gather_gamma<T>(st, ga);
+  }
+  return launch_status(c, "adjoint");
+}
+
+// Float64 certification pass with outward rounding (rigorous lower bound).
+template <typename Td>
+gcp_status run_certify(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
+  const Net& net = *b.net;
+  const int L = net.L;
+  const int64_t R = b.R;
+  gcp_status s = GCP_OK;
+  double* nu = (double*)b.ws("c_nu", (size_t)R * b.dmax() * 8, &s);
+  double* y = (double*)b.ws("c_y", (size_t)R * b.dmax() * 8, &s);
+  float* ya = (float*)b.ws("c_yabs", (size_t)R * b.dmax() * 4, &s);
+  double* part = (double*)b.ws("c_part", (size_t)b.n_partials() * R * 8, &s);
+  if (!nu || !y || !ya || !part) return s;
+  SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp};
+  // y^(L-1) = W^(L)^T (-c_k), one row per spec row
+  const LayerGeom& gl = net.geom[L - 1];
+  gemm_nt_abs(st, b.K, gl.d_in, gl.d_out, net.negC64, 0, net.WT64[L - 1], y, ya);
+  int poff = 0;
+  for (int i = L - 1; i >= 1; --i) {
+    CertArgs<Td> a{};
+    a.R = R; a.K = b.K; a.d = net.dims[i]; a.layer = i; a.M = b.M; a.N = b.N;
+    a.y = y; a.yabs = ya; a.y_per_spec = (i == L - 1);
+    a.gamma_n = gamma_n_host(red_len(net.geom[i]));
+    a.lo = net.lo64[i - 1]; a.hi = net.hi64[i - 1]; a.bias = net.b64[i - 1];
+    a.alpha = (const Td*)b.alpha[i - 1];
+    a.beta = (const Td*)b.beta;
+    a.gamma = (const Td*)b.gamma;
+    a.sp = sp;
+    a.csc = csc_of<double>(b, i);
+    a.nu_out = nu;
+    a.obj_part = part + (int64_t)poff * R;
+    certify_relax<Td>(st, a);
+    poff += (net.dims[i] + kChunk - 1) / kChunk;
+    const LayerGeom& g = net.geom[i - 1];
+    if (g.kind == GCP_DENSE) gemm_nt_abs(st, R, g.d_in, g.d_out, nu, 0, net.WT64[i - 1], y, ya);
+    else conv_T_abs(st, R, g, net.W64[i - 1], nu, y, ya);
+  }
+  certify_concretize<Td>(st, R, b.K, b.N, net.dims[0], y, ya, gamma_n_host(red_len(net.geom[0])), net.xlo64, net.xhi64,
+                         (const Td*)b.gamma, csc_of<double>(b, 0), part + (int64_t)poff * R);
+  poff += (net.dims[0] + kChunk - 1) / kChunk;
+  certify_finalize<Td>(st, R, b.K, b.N, poff, net.C64, net.bL64, net.dims[L], b.cuts.d64, (const Td*)b.gamma, part,
+                       out_dev);
+  return launch_status(c, "certify");
+}
+
+template <typename T>
+static StepArgs<T> make_step(const gcp_opt_params& p, int it) {
+  StepArgs<T> s{};
+  s.mode = p.optimizer == GCP_ADAM ? 2 : 1;
+  const double f = std::pow(p.lr_decay, (double)it);
+  s.lr_a = (T)(p.lr_alpha * f);
+  s.lr_b = (T)(p.lr_beta * f);
+  s.lr_g = (T)(p.lr_gamma * f);
+  s.b1 = (T)0.9;
+  s.b2 = (T)0.999;
+  s.eps = (T)1e-8;
+  s.c1 = (T)(1.0 - std::pow(0.9, it + 1));
+  s.c2 = (T)(1.0 - std::pow(0.999, it + 1));
+  return s;
+}
+
+template <typename T, typename Top>
+gcp_status optimize_steps(Ctx& c, Batch& b, cudaStream_t st, const gcp_opt_params& p) {
+  for (int it = 0; it < p.iters; ++it) {
+    gcp_status s = run_eval<T, Top>(c, b, st, true, nullptr);
+    if (s) return s;
+    s = run_adjoint<T, Top>(c, b, st, make_step<T>(p, it), nullptr, nullptr, nullptr, nullptr);
+    if (s) return s;
+  }
+  return GCP_OK;
+}
+
+gcp_status check_prec(Ctx& c, const Batch& b, int prec) {
+  if (prec == GCP_FP64 && !b.fp64) return c.fail(GCP_EINVAL, "FP64 chain needs duals created with GCP_FP64");
+  if ((prec == GCP_FP32 || prec == GCP_BF16) && b.fp64) return c.fail(GCP_EINVAL, "FP32/BF16 chain needs GCP_FP32 duals");
+  if (prec < 0 || prec > 2) return c.fail(GCP_EINVAL, "unknown precision %d", prec);
+  return GCP_OK;
+}
+
+// Copy the chain bound (T on device) to host doubles.
+static gcp_status fetch_bound(Ctx& c, Batch& b, cudaStream_t st, double* out) {
+  if (!out || b.R == 0) return GCP_OK;
+  gcp_status s = GCP_OK;
+  if (b.fp64) {
+    cudaError_t e = cudaMemcpyAsync(out, b.lazy["g"], b.R * 8, cudaMemcpyDeviceToHost, st);
+    if (e) return c.cuda(e, "copy bound");
+  } else {
+    double* tmp = (double*)b.ws("g64", b.R * 8, &s);
+    if (!tmp) return s;
+    cast_copy<float, double>(st, b.R, (const float*)b.lazy["g"], tmp);
+    cudaError_t e = cudaMemcpyAsync(out, tmp, b.R * 8, cudaMemcpyDeviceToHost, st);
+    if (e) return c.cuda(e, "copy bound");
+  }
+  return GCP_OK;
+}
+
+gcp_status eval_dispatch(Ctx& c, Batch& b, cudaStream_t st, int prec, bool adj_start, const void* seed) {
+  if (prec == GCP_FP64) return run_eval<double, double>(c, b, st, adj_start, (const double*)seed);
+  if (prec == GCP_FP32) return run_eval<float, float>(c, b, st, adj_start, (const float*)seed);
+  return run_eval<float, __nv_bfloat16>(c, b, st, adj_start, (const float*)seed);
+}
+
+gcp_status certify_dispatch(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
+  return b.fp64 ? run_certify<double>(c, b, st, out_dev) : run_certify<float>(c, b, st, out_dev);
+}
+
+gcp_status bound_batch(Ctx& c, Batch& b, int prec, int certify, double* out_bound, double* out_cert) {
+  gcp_status s = check_prec(c, b, prec);
+  if (s) return s;
+  cudaStream_t st = c.stream;
+  if (b.R == 0) return GCP_OK;
+  s = eval_dispatch(c, b, st, prec, false, nullptr);
+  if (s) return s;
+  s = fetch_bound(c, b, st, out_bound);
+  if (s) return s;
+  if (certify) {
+    double* cd = (double*)b.ws("cert", b.R * 8, &s);
+    if (!cd) return s;
+    s = certify_dispatch(c, b, st, cd);
+    if (s) return s;
+    if (out_cert) {
+      cudaError_t e = cudaMemcpyAsync(out_cert, cd, b.R * 8, cudaMemcpyDeviceToHost, st);
+      if (e) return c.cuda(e, "copy certified");
+    }
+  }
+  return sync_check(c, st, "bound_batch");
+}
+
+template <typename T>
+static gcp_status grad_impl(Ctx& c, Batch& b, int prec, double* out_bound, double* ga, double* gb, double* gg) {
+  cudaStream_t st = c.stream;
+  const Net& net = *b.net;
+  gcp_status s = GCP_OK;
+  int64_t nal = 0;
+  for (int i = 1; i < net.L; ++i) nal += (int64_t)b.R * net.dims[i];
+  T* gal = (T*)b.ws("g_alpha", (size_t)nal * sizeof(T), &s);
+  T* gbe = (T*)b.ws("g_beta", (size_t)std::max(b.M, 1) * b.R * sizeof(T), &s);
+  T* gga = (T*)b.ws("g_gamma", (size_t)std::max(b.N, 1) * b.R * sizeof(T), &s);
+  if (!gal || !gbe || !gga) return s;
+  cudaMemsetAsync(gbe, 0, (size_t)std::max(b.M, 1) * b.R * sizeof(T), st);
+  s = eval_dispatch(c, b, st, prec, true, nullptr);
+  if (s) return s;
+  StepArgs<T> step{};
+  step.mode = 0;
+  if constexpr (std::is_same<T, double>::value) {
+    s = run_adjoint<double, double>(c, b, st, step, nullptr, gal, gbe, gga);
+  } else {
+    s = prec == GCP_FP32 ? run_adjoint<float, float>(c, b, st, step, nullptr, gal, gbe, gga)
+                         : run_adjoint<float, __nv_bfloat16>(c, b, st, step, nullptr, gal, gbe, gga);
+  }
+  if (s) return s;
+  s = fetch_bound(c, b, st, out_bound);
+  if (s) return s;
+  // export layouts: alpha [R, sum d] (layer blocks), beta [R, M], gamma [R, N]
+  std::vector<T> h;
+  s = sync_check(c, st, "grad_batch");
+  if (s) return s;
+  cudaError_t e = cudaSuccess;
+  if (ga) {
+    h.resize(nal);
+    e = cudaMemcpy(h.data(), gal, nal * sizeof(T), cudaMemcpyDeviceToHost);
+    if (e) return c.cuda(e, "copy g_alpha");
+    int64_t cols = 0, off = 0;
+    for (int i = 1; i < net.L; ++i) cols += net.dims[i];
+    int64_t coff = 0;
+    for (int i = 1; i < net.L; ++i) {
+      const int di = net.dims[i];
+      for (int64_t r = 0; r < b.R; ++r)
+        for (int j = 0; j < di; ++j) ga[r * cols + coff + j] = (double)h[off + r * di + j];
+      off += b.R * di;
+      coff += di;
+    }
+  }
+  if (gb && b.M > 0) {
+    h.resize((size_t)b.M * b.R);
+    e = cudaMemcpy(h.data(), gbe, h.size() * sizeof(T), cudaMemcpyDeviceToHost);
+    if (e) return c.cuda(e, "copy g_beta");
+    for (int64_t r = 0; r < b.R; ++r)
+      for (int m = 0; m < b.M; ++m) gb[r * b.M + m] = (double)h[(size_t)m * b.R + r];
+  }
+  if (gg && b.N > 0) {
+    h.resize((size_t)b.N * b.R);
+    e = cudaMemcpy(h.data(), gga, h.size() * sizeof(T), cudaMemcpyDeviceToHost);
+    if (e) return c.cuda(e, "copy g_gamma");
+    for (int64_t r = 0; r < b.R; ++r)
+      for (int n = 0; n < b.N; ++n) gg[r * b.N + n] = (double)h[(size_t)n * b.R + r];
+  }
+  return GCP_OK;
+}
+
+gcp_status grad_batch(Ctx& c, Batch& b, int prec, double* out_bound, double* ga, double* gb, double* gg) {
+  gcp_status s = check_prec(c, b, prec);
+  if (s) return s;
+  if (b.R == 0) return GCP_OK;
+  return b.fp64 ? grad_impl<double>(c, b, prec, out_bound, ga, gb, gg) : grad_impl<float>(c, b, prec, out_bound, ga, gb, gg);
+}
+
+gcp_status optimize_on(Ctx& c, Batch& b, const gcp_opt_params& p, cudaStream_t st, double* cert_dev) {
+  gcp_status s = check_prec(c, b, p.prec);
+  if (s) return s;
+  if (p.iters < 0 || (p.optimizer != GCP_PGA && p.optimizer != GCP_ADAM) || !(p.lr_decay > 0))
+    return c.fail(GCP_EINVAL, "bad optimiser parameters");
+  if (b.R == 0) return GCP_OK;
+  if (p.prec == GCP_FP64) s = optimize_steps<double, double>(c, b, st, p);
+  else if (p.prec == GCP_FP32) s = optimize_steps<float, float>(c, b, st, p);
+  else s = optimize_steps<float, __nv_bfloat16>(c, b, st, p);
+  if (s) return s;
+  s = eval_dispatch(c, b, st, p.prec, false, nullptr);
+  if (s) return s;
+  if (p.certify && cert_dev) s = certify_dispatch(c, b, st, cert_dev);
+  return s;
+}
+
+gcp_status optimize_batch(Ctx& c, Batch& b, const gcp_opt_params* p, double* out_bound, double* out_cert,
+                          double* out_err) {
+  if (!p) return c.fail(GCP_EINVAL, "null params");
+  cudaStream_t st = c.stream;
+  gcp_status s = GCP_OK;
+  double* cd = nullptr;
+  if (p->certify && b.R > 0) {
+    cd = (double*)b.ws("cert", b.R * 8, &s);
+    if (!cd) return s;
+  }
+  s = optimize_on(c, b, *p, st, cd);
+  if (s) return s;
+  if (b.R == 0) return GCP_OK;
+  s = fetch_bound(c, b, st, out_bound);
+  if (s) return s;
+  std::vector<double> cert;
+  if (cd && (out_cert || out_err)) {
+    cert.resize(b.R);
+    cudaError_t e = cudaMemcpyAsync(cert.data(), cd, b.R * 8, cudaMemcpyDeviceToHost, st);
+    if (e) return c.cuda(e, "copy certified");
+  }
+  std::vector<double> bnd;
+  if (out_err && !out_bound) {
+    bnd.resize(b.R);
+    s = fetch_bound(c, b, st, bnd.data());
+    if (s) return s;
+  }
+  s = sync_check(c, st, "optimize_batch");
+  if (s) return s;
+  if (cd) {
+    if (out_cert) std::copy(cert.begin(), cert.end(), out_cert);
+    if (out_err) {
+      const double* gb = out_bound ? out_bound : bnd.data();
+      for (int64_t r = 0; r < b.R; ++r) out_err[r] = std::fabs(gb[r] - cert[r]);
+    }
+  }
+  return GCP_OK;
+}
+
+// ------------------------------------------------------------------ dual import / export
+gcp_status duals_export(Ctx& c, Batch& b, double* alpha, double* beta, double* gamma) {
+  const Net& net = *b.net;
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e) return c.cuda(e, "export sync");
+  const size_t es = b.fp64 ? 8 : 4;
+  std::vector<char> h;
+  auto rd = [&](const char* p, size_t i) -> double {
+    return b.fp64 ? ((const double*)p)[i] : (double)((const float*)p)[i];
+  };
+  if (alpha) {
+    int64_t cols = 0;
+    for (int i = 1; i < net.L; ++i) cols += net.dims[i];
+    int64_t coff = 0;
+    for (int i = 1; i < net.L; ++i) {
+      const int di = net.dims[i];
+      h.resize((size_t)b.R * di * es);
+      e = cudaMemcpy(h.data(), b.alpha[i - 1], h.size(), cudaMemcpyDeviceToHost);
+      if (e) return c.cuda(e, "export alpha");
+      for (int64_t r = 0; r < b.R; ++r)
+        for (int j = 0; j < di; ++j) alpha[r * cols + coff + j] = rd(h.data(), (size_t)r * di + j);
+      coff += di;
+    }
+  }
+  if (beta && b.M > 0) {
+    h.resize((size_t)b.M * b.R * es);
+    e = cudaMemcpy(h.data(), b.beta, h.size(), cudaMemcpyDeviceToHost);
+    if (e) return c.cuda(e, "export beta");
+    for (int64_t r = 0; r < b.R; ++r)
+      for (int m = 0; m < b.M; ++m) beta[r * b.M + m] = rd(h.data(), (size_t)m * b.R + r);
+  }
+  if (gamma && b.N > 0) {
+    h.resize((size_t)b.N * b.R * es);
+    e = cudaMemcpy(h.data(), b.gamma, h.size(), cudaMemcpyDeviceToHost);
+    if (e) return c.cuda(e, "export gamma");
+    for (int64_t r = 0; r < b.R; ++r)
+      for (int n = 0; n < b.N; ++n) gamma[r * b.N + n] = rd(h.data(), (size_t)n * b.R + r);
+  }
+  return GCP_OK;
+}
+
+gcp_status duals_import(Ctx& c, Batch& b, const double* alpha, const double* beta, const double* gamma) {
+  const Net& net = *b.net;
+  gcp_status s = reset_duals(c, b, !alpha, !beta, !gamma);
+  if (s) return s;
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e) return c.cuda(e, "import sync");
+  const size_t es = b.fp64 ? 8 : 4;
+  std::vector<char> h;
+  auto wr = [&](char* p, size_t i, double v) {
+    if (b.fp64) ((double*)p)[i] = v; else ((float*)p)[i] = (float)v;
+  };
+  if (alpha) {
+    int64_t cols = 0;
+    for (int i = 1; i < net.L; ++i) cols += net.dims[i];
+    int64_t coff = 0;
+    for (int i = 1; i < net.L; ++i) {
+      const int di = net.dims[i];
+      h.resize((size_t)b.R * di * es);
+      for (int64_t r = 0; r < b.R; ++r)
+        for (int j = 0; j < di; ++j) wr(h.data(), (size_t)r * di + j, alpha[r * cols + coff + j]);
+      e = cudaMemcpy(b.alpha[i - 1], h.data(), h.size(), cudaMemcpyHostToDevice);
+      if (e) return c.cuda(e, "import alpha");
+      coff += di;
+    }
+  }
+  if (beta && b.M > 0) {
+    h.resize((size_t)b.M * b.R * es);
+    for (int64_t r = 0; r < b.R; ++r)
+      for (int m = 0; m < b.M; ++m) wr(h.data(), (size_t)m * b.R + r, beta[r * b.M + m]);
+    e = cudaMemcpy(b.beta, h.data(), h.size(), cudaMemcpyHostToDevice);
+    if (e) return c.cuda(e, "import beta");
+  }
+  if (gamma && b.N > 0) {
+    h.resize((size_t)b.N * b.R * es);
+    for (int64_t r = 0; r < b.R; ++r)
+      for (int n = 0; n < b.N; ++n) wr(h.data(), (size_t)n * b.R + r, gamma[r * b.N + n]);
+    e = cudaMemcpy(b.gamma, h.data(), h.size(), cudaMemcpyHostToDevice);
+    if (e) return c.cuda(e, "import gamma");
+  }
+  return GCP_OK;
+}
+
+// Caller-owned device arrays of the device entry points take part in the launch
+// checks for the duration of the call (registered with their documented sizes).
+struct ForeignArrays {
+  std::vector<const void*> regs;
+  gcp_status add(Ctx& c, const void* p, size_t bytes, const char* what) {
+    if (!p || bytes == 0) return GCP_OK;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+      cudaGetLastError();
+      return c.fail(GCP_EINVAL, "%s is not a device pointer", what);
+    }
+    reg_alloc(p, bytes);
+    regs.push_back(p);
+    return GCP_OK;
+  }
+  ~ForeignArrays() {
+    for (const void* p : regs) reg_free(p);
+  }
+};
+
+static int64_t alpha_cols(const Net& net) {
+  int64_t cols = 0;
+  for (int i = 1; i < net.L; ++i) cols += net.dims[i];
+  return cols;
+}
+
+// Device-pointer variants (float duals in export layouts).
+gcp_status load_device_duals(Ctx& c, Batch& b, cudaStream_t st, const float* alpha, const float* beta,
+                             const float* gamma) {
+  if (b.fp64) return c.fail(GCP_EINVAL, "device entry points need GCP_FP32 duals");
+  const Net& net = *b.net;
+  int64_t cols = 0;
+  for (int i = 1; i < net.L; ++i) cols += net.dims[i];
+  int64_t coff = 0;
+  for (int i = 1; i < net.L; ++i) {
+    const int di = net.dims[i];
+    if (alpha && b.R > 0) {
+      cudaError_t e = cudaMemcpy2DAsync(b.alpha[i - 1], di * 4, alpha + coff, cols * 4, di * 4, b.R,
+                                        cudaMemcpyDeviceToDevice, st);
+      if (e) return c.cuda(e, "alpha in");
+    }
+    coff += di;
+  }
+  if (beta && b.M > 0) transpose_cast<float, float>(st, b.R, b.M, beta, (float*)b.beta);
+  if (gamma && b.N > 0) transpose_cast<float, float>(st, b.R, b.N, gamma, (float*)b.gamma);
+  return launch_status(c, "load duals");
+}
+
+gcp_status bound_device(Ctx& c, Batch& b, int prec, const float* alpha, const float* beta, const float* gamma,
+                        float* out, cudaStream_t st) {
+  gcp_status s = check_prec(c, b, prec);
+  if (s) return s;
+  if (prec == GCP_FP64) return c.fail(GCP_EINVAL, "device entry points run FP32 or BF16");
+  ForeignArrays fa;
+  const size_t R4 = (size_t)b.R * 4;
+  if ((s = fa.add(c, alpha, R4 * alpha_cols(*b.net), "alpha")) || (s = fa.add(c, beta, R4 * b.M, "beta")) ||
+      (s = fa.add(c, gamma, R4 * b.N, "gamma")) || (s = fa.add(c, out, R4, "out")))
+    return s;
+  s = load_device_duals(c, b, st, alpha, beta, gamma);
+  if (s) return s;
+  if (b.R == 0) return GCP_OK;
+  s = eval_dispatch(c, b, st, prec, false, nullptr);
+  if (s) return s;
+  return c.cuda(cudaMemcpyAsync(out, b.lazy["g"], (size_t)b.R * 4, cudaMemcpyDeviceToDevice, st), "bound out");
+}
+
+gcp_status grad_device(Ctx& c, Batch& b, int prec, const float* alpha, const float* beta, const float* gamma,
+                       const float* grad_out, float* g_alpha, float* g_beta, float* g_gamma, cudaStream_t st) {
+  gcp_status s = check_prec(c, b, prec);
+  if (s) return s;
+  if (prec == GCP_FP64) return c.fail(GCP_EINVAL, "device entry points run FP32 or BF16");
+  ForeignArrays fa;
+  const size_t R4 = (size_t)b.R * 4, na = (size_t)alpha_cols(*b.net);
+  if ((s = fa.add(c, alpha, R4 * na, "alpha")) || (s = fa.add(c, beta, R4 * b.M, "beta")) ||
+      (s = fa.add(c, gamma, R4 * b.N, "gamma")) || (s = fa.add(c, grad_out, R4, "grad_out")) ||
+      (s = fa.add(c, g_alpha, R4 * na, "g_alpha")) || (s = fa.add(c, g_beta, R4 * b.M, "g_beta")) ||
+      (s = fa.add(c, g_gamma, R4 * b.N, "g_gamma")))
+    return s;
+  s = load_device_duals(c, b, st, alpha, beta, gamma);
+  if (s) return s;
+  if (b.R == 0) return GCP_OK;
+  const Net& net = *b.net;
+  int64_t nal = 0;
+  for (int i = 1; i < net.L; ++i) nal += (int64_t)b.R * net.dims[i];
+  float* gal = (float*)b.ws("g_alpha", (size_t)nal * 4, &s);
+  float* gbe = (float*)b.ws("g_beta", (size_t)std::max(b.M, 1) * b.R * 4, &s);
+  float* gga = (float*)b.ws("g_gamma", (size_t)std::max(b.N, 1) * b.R * 4, &s);
+  if (!gal || !gbe || !gga) return s;
+  cudaMemsetAsync(gbe, 0, (size_t)std::max(b.M, 1) * b.R * 4, st);
+  s = eval_dispatch(c, b, st, prec, true, grad_out);
+  if (s) return s;
+  StepArgs<float> step{};
+  step.mode = 0;
+  s = prec == GCP_FP32 ? run_adjoint<float, float>(c, b, st, step, grad_out, gal, gbe, gga)
+                       : run_adjoint<float, __nv_bfloat16>(c, b, st, step, grad_out, gal, gbe, gga);
+  if (s) return s;
+  int64_t cols = 0;
+  for (int i = 1; i < net.L; ++i) cols += net.dims[i];
+  int64_t coff = 0, off = 0;
+  for (int i = 1; i < net.L; ++i) {
+    const int di = net.dims[i];
+    if (g_alpha) {
+      cudaError_t e = cudaMemcpy2DAsync(g_alpha + coff, cols * 4, gal + off, di * 4, di * 4, b.R,
+                                        cudaMemcpyDeviceToDevice, st);
+      if (e) return c.cuda(e, "g_alpha out");
+    }
+    coff += di;
+    off += (int64_t)b.R * di;
+  }
+  if (g_beta && b.M > 0) transpose_cast<float, float>(st, b.M, b.R, gbe, g_beta);
+  if (g_gamma && b.N > 0) transpose_cast<float, float>(st, b.N, b.R, gga, g_gamma);
+  return launch_status(c, "grad out");
+}
+
+}  // namespace gcp
+
+// ====================================================================== C ABI
+using gcp::Ctx;
+
+#define CTX_GUARD(ctx)                                   \
+  if (!(ctx)) return GCP_EINVAL;                         \
+  std::lock_guard<std::recursive_mutex> _lk((ctx)->mu);  \
+  cudaSetDevice((ctx)->device);
+
+extern "C" {
+
+gcp_status gcp_create(gcp_ctx** out, int32_t device, uint64_t budget) {
+  if (!out) return GCP_EINVAL;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return GCP_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return GCP_ECUDA;
+  Ctx* c = new (std::nothrow) Ctx();
+  if (!c) return GCP_ENOMEM;
+  c->device = device;
+  c->budget = budget;
+  if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return GCP_ECUDA;
+  }
+  c->stream = c->own_stream;
+  *out = reinterpret_cast<gcp_ctx*>(c);
+  return GCP_OK;
+}
+
+gcp_status gcp_destroy(gcp_ctx* h) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  if (!c) return GCP_EINVAL;
+  gcp::serve_shutdown(*c);
+  {
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    c->batches.clear();
+    c->cutsets.clear();
+    c->nets.clear();
+    cudaStreamDestroy(c->own_stream);
+  }
+  delete c;
+  return GCP_OK;
+}
+
+const char* gcp_last_error(const gcp_ctx* h) {
+  const Ctx* c = reinterpret_cast<const Ctx*>(h);
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+gcp_status gcp_set_stream(gcp_ctx* h, void* stream) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  CTX_GUARD(c);
+  c->stream = stream ? (cudaStream_t)stream : c->own_stream;
+  return GCP_OK;
+}
+
+gcp_status gcp_mem_used(const gcp_ctx* h, uint64_t* bytes) {
+  const Ctx* c = reinterpret_cast<const Ctx*>(h);
+  if (!c || !bytes) return GCP_EINVAL;
+  *bytes = c->used;
+  return GCP_OK;
+}
+
+gcp_status gcp_init_net(gcp_ctx* h, const gcp_layer_desc* layers, int32_t n_layers, const double* x_lo,
+                        const double* x_hi, const double* spec_c, int32_t n_spec, const double* inter_lo,
+                        const double* inter_hi, int32_t* net_id) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  CTX_GUARD(c);
+  return gcp::init_net(*c, layers, n_layers, x_lo, x_hi, spec_c, n_spec, inter_lo, inter_hi, net_id);
+}
+
+gcp_status gcp_add_cuts(gcp_ctx* h, int32_t net_id, int32_t n_cuts, const int64_t* row_ptr, const int16_t* layer,
+                        const int8_t* kind, const int32_t* index, const double* coef, const double* d,
+                        int32_t* cutset_id, int32_t* first_cut) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  CTX_GUARD(c);
+  return gcp::add_cuts(*c, net_id, n_cuts, row_ptr, layer, kind, index, coef, d, cutset_id, first_cut);
+}
+
+static gcp::Batch* find_batch(Ctx* c, void* duals) {
+  auto it = c->batches.find((gcp::Batch*)duals);
+  return it == c->batches.end() ? nullptr : it->second.get();
+}
+
+gcp_status gcp_duals_create(gcp_ctx* h, int32_t net_id, int32_t cutset_id, const gcp_subdomains* sub,
+                            int32_t dual_prec, void** duals) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  CTX_GUARD(c);
+  gcp::Batch* b = nullptr;
+  gcp_status s = gcp::duals_create(*c, net_id, cutset_id, sub, dual_prec, &b);
+  if (s == GCP_OK) {
+    s = gcp::sync_check(*c, c->stream, "duals_create");
+    if (s == GCP_OK) *duals = b;
+  }
+  return s;
+}
+
+gcp_status gcp_duals_shape(gcp_ctx* h, void* duals, int64_t* rows, int64_t* n_alpha, int32_t* max_splits,
+                           int32_t* n_cuts) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  CTX_GUARD(c);
+  gcp::Batch* b = find_batch(c, duals);
+  if (!b) return c->fail(GCP_ENOTFOUND, "unknown duals");
+  int64_t na = 0;
+  for (int i = 1; i < b->net->L; ++i) na += b->net->dims[i];
+  if (rows) *rows = b->R;
+  if (n_alpha) *n_alpha = na;
+  if (max_splits) *max_splits = b->M;
+  if (n_cuts) *n_cuts = b->N;
+  return GCP_OK;
+}
+
+gcp_status gcp_duals_export(gcp_ctx* h, void* duals, double* a, double* be, double* g) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  CTX_GUARD(c);
+  gcp::Batch* b = find_batch(c, duals);
+  if (!b) return c->fail(GCP_ENOTFOUND, "unknown duals");
+  return gcp::duals_export(*c, *b, a, be, g);
+}
+
+gcp_status gcp_duals_import(gcp_ctx* h, void* duals, const double* a, const double* be, const double* g) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  CTX_GUARD(c);
+  gcp::Batch* b = find_batch(c, duals);
+  if (!b) return c->fail(GCP_ENOTFOUND, "unknown duals");
+  return gcp::duals_import(*c, *b, a, be, g);
+}
+
+gcp_status gcp_duals_free(gcp_ctx* h, void* duals) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  CTX_GUARD(c);
+  auto it = c->batches.find((gcp::Batch*)duals);
+  if (it == c->batches.end()) return c->fail(GCP_ENOTFOUND, "unknown duals");
+  cudaStreamSynchronize(c->stream);
+  c->batches.erase(it);
+  return GCP_OK;
+}
+
+gcp_status gcp_bound_batch(gcp_ctx* h, void* duals, int32_t prec, int32_t certify, double* out_bound,
+                           double* out_cert) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  CTX_GUARD(c);
+  gcp::Batch* b = find_batch(c, duals);
+  if (!b) return c->fail(GCP_ENOTFOUND, "unknown duals");
+  return gcp::bound_batch(*c, *b, prec, certify, out_bound, out_cert);
+}
+
+gcp_status gcp_grad_batch(gcp_ctx* h, void* duals, int32_t prec, double* out_bound, double* ga, double* gb,
+                          double* gg) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  CTX_GUARD(c);
+  gcp::Batch* b = find_batch(c, duals);
+  if (!b) return c->fail(GCP_ENOTFOUND, "unknown duals");
+  return gcp::grad_batch(*c, *b, prec, out_bound, ga, gb, gg);
+}
+
+gcp_status gcp_optimize_batch(gcp_ctx* h, void* duals, const gcp_opt_params* p, double* out_bound,
+                              double* out_cert, double* out_err) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  CTX_GUARD(c);
+  gcp::Batch* b = find_batch(c, duals);
+  if (!b) return c->fail(GCP_ENOTFOUND, "unknown duals");
+  return gcp::optimize_batch(*c, *b, p, out_bound, out_cert, out_err);
+}
+
+gcp_status gcp_bound_device(gcp_ctx* h, void* duals, int32_t prec, const float* alpha, const float* beta,
+                            const float* gamma, float* out, void* stream) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  CTX_GUARD(c);
+  gcp::Batch* b = find_batch(c, duals);
+  if (!b) return c->fail(GCP_ENOTFOUND, "unknown duals");
+  return gcp::bound_device(*c, *b, prec, alpha, beta, gamma, out, stream ? (cudaStream_t)stream : c->stream);
+}
+
+gcp_status gcp_grad_device(gcp_ctx* h, void* duals, int32_t prec, const float* alpha, const float* beta,
+                           const float* gamma, const float* grad_out, float* g_alpha, float* g_beta, float* g_gamma,
+                           void* stream) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  CTX_GUARD(c);
+  gcp::Batch* b = find_batch(c, duals);
+  if (!b) return c->fail(GCP_ENOTFOUND, "unknown duals");
+  return gcp::grad_device(*c, *b, prec, alpha, beta, gamma, grad_out, g_alpha, g_beta, g_gamma,
+                          stream ? (cudaStream_t)stream : c->stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,123 @@
+// Host-side object model of a libgcp context: nets, cut sets, duals batches.
+#pragma once
+
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "gcp_internal.cuh"
+
+namespace gcp {
+
+struct Ctx;
+
+struct Net {
+  Ctx* ctx = nullptr;
+  int L = 0, K = 0;
+  std::vector<int> dims;             // d_0 .. d_L
+  std::vector<LayerGeom> geom;       // layer i at index i-1
+  std::vector<double*> W64, WT64, b64;
+  std::vector<float*> W32, WT32, b32;
+  std::vector<__nv_bfloat16*> W16, WT16;
+  double *xlo64 = nullptr, *xhi64 = nullptr;
+  float *xlo32 = nullptr, *xhi32 = nullptr;
+  double *C64 = nullptr, *negC64 = nullptr, *bL64 = nullptr;
+  double* YL64 = nullptr;            // [K, d_{L-1}] = -W^(L)^T c_k
+  float* YL32 = nullptr;
+  double* cb64 = nullptr;            // [K] = c_k^T b^(L)
+  float* cb32 = nullptr;
+  std::vector<double*> lo64, hi64;   // hidden layer i at index i-1
+  std::vector<float*> lo32, hi32;    // rounded outwards
+  std::vector<void*> owned;
+  ~Net();
+};
+
+struct CutSet {
+  int net_id = 0;
+  std::vector<int64_t> ptr;
+  std::vector<int16_t> layer;
+  std::vector<int8_t> kind;
+  std::vector<int32_t> index;
+  std::vector<double> coef, d;
+};
+
+struct CutDev {
+  Ctx* ctx = nullptr;
+  int N = 0;
+  int64_t nnz = 0;
+  int32_t* cut_ptr = nullptr;        // [N+1] CSR by cut (entry ids)
+  double* d64 = nullptr;
+  float* d32 = nullptr;
+  int32_t* csc_ptr = nullptr;        // per layer segments of d_i + 1 offsets
+  int32_t* csc_cut = nullptr;
+  int8_t* csc_kind = nullptr;
+  double* csc_coef64 = nullptr;
+  float* csc_coef32 = nullptr;
+  int32_t* csc_eid = nullptr;
+  std::vector<int64_t> poff;         // segment start of layer i in csc_ptr
+  std::vector<int64_t> layer_nnz;    // entries per layer
+  std::vector<void*> owned;
+  ~CutDev();
+};
+
+struct Batch {
+  Ctx* ctx = nullptr;
+  Net* net = nullptr;
+  int net_id = 0;
+  int S = 0, K = 0, M = 0, N = 0;
+  int64_t R = 0, nnz = 0, nsp = 0;
+  bool fp64 = false;
+  CutDev cuts;
+  int32_t* sp_ptr = nullptr;
+  int16_t* sp_layer = nullptr;
+  int32_t* sp_index = nullptr;
+  int8_t* sp_sign = nullptr;
+  std::vector<void*> alpha;          // hidden layer i at index i-1, [R, d_i]
+  void* beta = nullptr;              // [M, R]
+  void* gamma = nullptr;             // [N, R]
+  std::vector<void*> owned;
+  std::map<std::string, void*> lazy; // workspace by name
+  std::map<std::string, size_t> lazy_bytes;
+  void* ws(const std::string& name, size_t bytes, gcp_status* st);
+  int64_t dmax() const;
+  int n_partials() const;
+  ~Batch();
+};
+
+struct Serve;
+
+struct Ctx {
+  int device = 0;
+  uint64_t budget = 0, used = 0;
+  bool over_budget = false;
+  cudaStream_t own_stream = nullptr, stream = nullptr;
+  std::recursive_mutex mu;
+  std::string err;
+  int next_id = 1;
+  std::map<int, std::unique_ptr<Net>> nets;
+  std::map<int, std::unique_ptr<CutSet>> cutsets;
+  std::map<Batch*, std::unique_ptr<Batch>> batches;
+  std::unordered_map<void*, size_t> sizes;
+  Serve* serve = nullptr;
+
+  gcp_status fail(gcp_status st, const char* fmt, ...);
+  gcp_status cuda(cudaError_t e, const char* what);
+  void* alloc(size_t bytes);
+  void release(void* p);
+};
+
+// shared by api.cu and serve.cu
+gcp_status duals_create(Ctx& c, int net_id, int cutset_id, const gcp_subdomains* sub, int dual_prec, Batch** out);
+gcp_status reset_duals(Ctx& c, Batch& b, bool a, bool be, bool g);
+gcp_status optimize_on(Ctx& c, Batch& b, const gcp_opt_params& p, cudaStream_t st, double* cert_dev);
+gcp_status eval_dispatch(Ctx& c, Batch& b, cudaStream_t st, int prec, bool adj_start, const void* seed);
+gcp_status certify_dispatch(Ctx& c, Batch& b, cudaStream_t st, double* out_dev);
+void serve_shutdown(Ctx& c);
+
+}  // namespace gcp

@@ -1,0 +1,233 @@
+// Internal declarations shared by the libgcp translation units.
+//
+// Data layout on the device (R rows = subdomains x spec rows, r = s*K + k):
+//   chain operands nu / a          [R, d_i]  row-major, operand dtype
+//   GEMM outputs y / nubar         [R, d_i]  row-major, epilogue dtype T
+//   alpha^(i), nuhat^(i)           [R, d_i]  row-major, T
+//   beta                           [M, R]    (split slot major, rows contiguous)
+//   gamma                          [N, R]    (cut major, rows contiguous)
+//   E (cut-entry values)           [nnz, R]
+//   objective partials             [P, R]
+// Cut-major / slot-major layouts make the per-row gathers of the epilogues
+// coalesced: a warp handles 32 consecutive rows of the same neuron.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gcp.h"
+
+namespace gcp {
+
+constexpr int kMaxSplits = 64;     // per subdomain (validated on the host)
+constexpr int kChunk = 32;         // neurons per epilogue block column
+constexpr int kRowsPerBlock = 128; // rows per epilogue block
+
+struct LayerGeom {
+  int kind, d_in, d_out;
+  int c_in, h_in, w_in, c_out, h_out, w_out, k, stride, pad;
+};
+
+// Cut entries of one layer in CSC order (per neuron), pointers already offset.
+template <typename T>
+struct CutCSC {
+  const int32_t* ptr;   // [d+1] global entry offsets
+  const int32_t* cut;   // cut id per entry
+  const int8_t* kind;   // GCP_VAR_*
+  const T* coef;
+  const int32_t* eid;   // row of E written for this entry
+  int64_t n_entries;    // entries of this layer (host-side accounting only)
+  int64_t n_total;      // entries of all layers (host-side validation only)
+};
+
+struct SplitsDev {
+  const int32_t* ptr;   // [S+1]
+  const int16_t* layer;
+  const int32_t* index;
+  const int8_t* sign;
+  int64_t n;            // total split entries (host-side validation only)
+};
+
+// Optimiser step applied inside the adjoint epilogues / cut gather.
+// mode 0: write gradients (no update); 1: projected gradient ascent; 2: Adam.
+template <typename T>
+struct StepArgs {
+  int mode;
+  T lr_a, lr_b, lr_g;
+  T b1, b2, eps, c1, c2;  // Adam moments and bias corrections 1-b1^t, 1-b2^t
+};
+
+template <typename T, typename Top>
+struct RelaxArgs {
+  int64_t R;
+  int K, d, layer;
+  int M, N;             // split slots and cuts (extents of beta / gamma)
+  const T* y;           // [R, d] or [K, d] when y_per_spec
+  int y_per_spec;
+  const T* lo;          // root bounds [d]
+  const T* hi;
+  const T* bias;        // b^(layer) [d]
+  const T* alpha;       // [R, d]
+  const T* beta;        // [M, R]
+  const T* gamma;       // [N, R]
+  SplitsDev sp;
+  CutCSC<T> csc;
+  Top* nu_out;          // [R, d]
+  T* nuhat_out;         // [R, d]
+  T* obj_part;          // [ceil(d/kChunk), R]
+};
+
+template <typename T, typename Top>
+struct AdjArgs {
+  int64_t R;
+  int K, d, layer;
+  int M, N;
+  const T* nubar;       // [R, d]  (W^(i) a, bias not yet subtracted)
+  const T* seed;        // per-row seed of the reverse pass, nullptr = 1
+  const T* lo;
+  const T* hi;
+  const T* bias;
+  T* alpha;             // [R, d], updated in place when mode != 0
+  T* beta;              // [M, R], updated in place when mode != 0
+  const T* gamma;       // [N, R]
+  const T* nuhat;       // [R, d]
+  SplitsDev sp;
+  CutCSC<T> csc;
+  Top* a_out;           // [R, d] dg/dnuhat (nullptr for the last hidden layer)
+  T* E;                 // [nnz, R]
+  T* g_alpha;           // [R, d]  (mode 0)
+  T* g_beta;            // [M, R]  (mode 0)
+  T* m_alpha; T* v_alpha; T* m_beta; T* v_beta;  // Adam state (mode 2)
+  StepArgs<T> st;
+};
+
+template <typename T, typename Top>
+struct ConcArgs {
+  int64_t R;
+  int K, d0;
+  int N;
+  const T* y0;          // [R, d0]
+  const T* x_lo;
+  const T* x_hi;
+  const T* gamma;
+  const T* seed;
+  CutCSC<T> csc;        // layer 0 entries (kind X only)
+  Top* a0_out;          // [R, d0] = -seed * x*  (start of the reverse pass)
+  T* E;
+  T* obj_part;          // [ceil(d0/kChunk), R]
+};
+
+template <typename T>
+struct FinalArgs {
+  int64_t R;
+  int K, N, P;
+  const T* cb;          // [K]  c_k^T b^(L)
+  const T* d;           // [N]
+  const T* gamma;       // [N, R]
+  const T* obj_part;    // [P, R]
+  T* g;                 // [R]
+};
+
+template <typename T>
+struct GatherArgs {
+  int64_t R;
+  int N;
+  const int32_t* cut_ptr;  // [N+1]
+  const T* E;
+  const T* d;
+  const T* seed;
+  T* gamma;             // [N, R] updated when mode != 0
+  T* g_gamma;           // [N, R] mode 0
+  T* m_gamma; T* v_gamma;
+  StepArgs<T> st;
+  int64_t nnz;          // cut entries (host-side accounting only)
+};
+
+// Certification pass (float64, outward rounding). Td: dual storage type.
+template <typename Td>
+struct CertArgs {
+  int64_t R;
+  int K, d, layer;
+  int M, N;
+  const double* y;       // [R, d] or [K, d]
+  const float* yabs;     // sum |W||nu| rounded up, same layout as y
+  int y_per_spec;
+  double gamma_n;        // Higham's gamma_n for the GEMM's reduction length
+  const double* lo;
+  const double* hi;
+  const double* bias;
+  const Td* alpha;
+  const Td* beta;
+  const Td* gamma;
+  SplitsDev sp;
+  CutCSC<double> csc;
+  double* nu_out;        // [R, d]
+  double* obj_part;      // [ceil(d/kChunk), R] rounded-down partial sums
+};
+
+// ---------------------------------------------------------------- launch validation
+// Every device allocation of the library is registered; before each launch the
+// launcher checks, on the host, that each pointer argument lies inside a live
+// allocation with room for the largest extent the kernel can touch. A launch
+// that fails the check is skipped and the problem is recorded for the API
+// call to report (GCP_EDEVICE), so a bad argument never reaches the GPU.
+void reg_alloc(const void* p, size_t bytes);
+void reg_free(const void* p);
+bool reg_check(const void* p, double bytes, const char* what);
+// first recorded problem since the last call (empty if none); clears it
+std::string reg_take_error();
+// first failed in-kernel index check since the last call (synchronises st)
+std::string take_device_error(cudaStream_t st);
+
+// ---------------------------------------------------------------- profiling
+// Count a launch and, if its kernel is selected, bracket it with CUDA events.
+int prof_begin(cudaStream_t st, const char* name, double flops, double bytes);
+void prof_end(cudaStream_t st, int token);
+
+// ---------------------------------------------------------------- launchers
+// GEMM: C[M,N] = A[M,K] * B[N,K]^T, A row m read from row (a_mod ? m % a_mod : m).
+template <typename Tin, typename Tacc>
+void gemm_nt(cudaStream_t st, int64_t M, int N, int K, const Tin* A, int a_mod, const Tin* B, Tacc* C);
+void gemm_nt_abs(cudaStream_t st, int64_t M, int N, int K, const double* A, int a_mod, const double* B,
+                 double* C, float* Cabs);
+template <typename Tin, typename Tacc>
+void conv_fwd(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const Tin* in, Tacc* out);
+template <typename Tin, typename Tacc>
+void conv_T(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const Tin* in, Tacc* out);
+void conv_T_abs(cudaStream_t st, int64_t R, const LayerGeom& g, const double* W, const double* in, double* out,
+                float* outabs);
+
+template <typename T, typename Top>
+void relax_eval(cudaStream_t st, const RelaxArgs<T, Top>& a);
+template <typename T, typename Top>
+void relax_adjoint(cudaStream_t st, const AdjArgs<T, Top>& a);
+template <typename T, typename Top>
+void concretize(cudaStream_t st, const ConcArgs<T, Top>& a);
+template <typename T>
+void finalize_bound(cudaStream_t st, const FinalArgs<T>& a);
+template <typename T>
+void gather_gamma(cudaStream_t st, const GatherArgs<T>& a);
+
+template <typename Td>
+void certify_relax(cudaStream_t st, const CertArgs<Td>& a);
+template <typename Td>
+void certify_concretize(cudaStream_t st, int64_t R, int K, int N, int d0, const double* y0, const float* y0abs,
+                        double gamma_n, const double* x_lo, const double* x_hi, const Td* gamma,
+                        CutCSC<double> csc, double* obj_part);
+template <typename Td>
+void certify_finalize(cudaStream_t st, int64_t R, int K, int N, int P, const double* C, const double* bL, int dL,
+                      const double* d, const Td* gamma, const double* obj_part, double* out);
+
+// layout helpers
+template <typename Ts, typename Td>
+void transpose_cast(cudaStream_t st, int64_t rows, int64_t cols, const Ts* src, Td* dst);  // dst[c,r] = src[r,c]
+template <typename Ts, typename Td>
+void cast_copy(cudaStream_t st, int64_t n, const Ts* src, Td* dst);
+template <typename T>
+void default_alpha(cudaStream_t st, int64_t R, int K, int d, int layer, const T* lo, const T* hi, SplitsDev sp,
+                   T* alpha);
+
+}  // namespace gcp

@@ -1,0 +1,286 @@
+// Linear operators of the propagation chain (SIMT versions).
+//
+// Backward step of Theorem 3.1:  y^(i-1) = W^(i)^T nu^(i)   (dense: gemm_nt with
+//   B = W^(i)^T stored [d_{i-1}, d_i]; conv: conv_T, the transposed convolution).
+// Reverse-mode step (adjoint):  nubar^(i) = W^(i) a        (dense: gemm_nt with
+//   B = W^(i) stored [d_i, d_{i-1}]; conv: conv_fwd).
+// Certification: the same products in float64 plus sum |W||nu| rounded up, the
+//   quantity in Higham's bound |fl(y) - y| <= gamma_n * sum |W||nu|.
+#include <cstdio>
+
+#include "gcp_internal.cuh"
+
+namespace gcp {
+
+namespace {
+
+template <typename Tacc, typename Tin>
+__device__ __forceinline__ Tacc load_as(const Tin* p) { return static_cast<Tacc>(*p); }
+template <>
+__device__ __forceinline__ float load_as<float, __nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+// 64x64 output tile per 256-thread block; each thread owns rows ty+16i, cols tx+16j.
+template <typename Tin, typename Tacc, bool ABS>
+__global__ void __launch_bounds__(256) k_gemm_nt(int64_t M, int N, int K, const Tin* __restrict__ A, int a_mod,
+                                                 const Tin* __restrict__ B, Tacc* __restrict__ C,
+                                                 float* __restrict__ Cabs) {
+  __shared__ Tacc As[BK][BM + 1];
+  __shared__ Tacc Bs[BK][BN + 1];
+  __shared__ float Aa[ABS ? BK : 1][ABS ? BM + 1 : 1];
+  __shared__ float Ba[ABS ? BK : 1][ABS ? BN + 1 : 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t m0 = (int64_t)blockIdx.y * BM;
+  const int n0 = blockIdx.x * BN;
+  Tacc acc[4][4];
+  float aacc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { acc[i][j] = Tacc(0); aacc[i][j] = 0.f; }
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int idx = tid + 256 * q, row = idx >> 4, kk = idx & 15;
+      int64_t gm = m0 + row;
+      int gk = k0 + kk;
+      Tacc va = Tacc(0), vb = Tacc(0);
+      if (gm < M && gk < K) {
+        int64_t ar = a_mod ? (gm % a_mod) : gm;
+        va = load_as<Tacc>(A + ar * K + gk);
+      }
+      int gn = n0 + row;
+      if (gn < N && gk < K) vb = load_as<Tacc>(B + (int64_t)gn * K + gk);
+      As[kk][row] = va;
+      Bs[kk][row] = vb;
+      if constexpr (ABS) {
+        Aa[kk][row] = __double2float_ru(fabs((double)va));
+        Ba[kk][row] = __double2float_ru(fabs((double)vb));
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      Tacc a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      if constexpr (ABS) {
+        float aa[4], bb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) aa[i] = Aa[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bb[j] = Ba[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) aacc[i][j] = __fmaf_ru(aa[i], bb[j], aacc[i][j]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int64_t gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gn = n0 + tx + 16 * j;
+      if (gn < N) {
+        C[gm * N + gn] = acc[i][j];
+        if constexpr (ABS) Cabs[gm * N + gn] = aacc[i][j];
+      }
+    }
+  }
+}
+
+// out[r,o,oh,ow] = sum_{c,kh,kw} W[o,c,kh,kw] in[r,c,oh*s+kh-p,ow*s+kw-p]
+template <typename Tin, typename Tacc>
+__global__ void k_conv_fwd(int64_t R, LayerGeom g, const Tin* __restrict__ W, const Tin* __restrict__ in,
+                           Tacc* __restrict__ out) {
+  int64_t n = R * (int64_t)g.d_out;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = idx / g.d_out;
+    int rem = (int)(idx - r * g.d_out);
+    int o = rem / (g.h_out * g.w_out);
+    int p2 = rem - o * g.h_out * g.w_out;
+    int oh = p2 / g.w_out, ow = p2 - oh * g.w_out;
+    const Tin* ir = in + r * g.d_in;
+    Tacc acc = Tacc(0);
+    for (int c = 0; c < g.c_in; ++c)
+      for (int kh = 0; kh < g.k; ++kh) {
+        int ih = oh * g.stride + kh - g.pad;
+        if (ih < 0 || ih >= g.h_in) continue;
+        for (int kw = 0; kw < g.k; ++kw) {
+          int iw = ow * g.stride + kw - g.pad;
+          if (iw < 0 || iw >= g.w_in) continue;
+          acc = fma(load_as<Tacc>(W + ((o * g.c_in + c) * g.k + kh) * g.k + kw),
+                    load_as<Tacc>(ir + (c * g.h_in + ih) * g.w_in + iw), acc);
+        }
+      }
+    out[idx] = acc;
+  }
+}
+
+// out[r,c,ih,iw] = sum over (o,kh,kw) with ih = oh*s+kh-p, iw = ow*s+kw-p of W[o,c,kh,kw] in[r,o,oh,ow]
+template <typename Tin, typename Tacc, bool ABS>
+__global__ void k_conv_T(int64_t R, LayerGeom g, const Tin* __restrict__ W, const Tin* __restrict__ in,
+                         Tacc* __restrict__ out, float* __restrict__ outabs) {
+  int64_t n = R * (int64_t)g.d_in;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = idx / g.d_in;
+    int rem = (int)(idx - r * g.d_in);
+    int c = rem / (g.h_in * g.w_in);
+    int p2 = rem - c * g.h_in * g.w_in;
+    int ih = p2 / g.w_in, iw = p2 - ih * g.w_in;
+    const Tin* ir = in + r * g.d_out;
+    Tacc acc = Tacc(0);
+    float aacc = 0.f;
+    for (int kh = 0; kh < g.k; ++kh) {
+      int th = ih + g.pad - kh;
+      if (th < 0 || th % g.stride) continue;
+      int oh = th / g.stride;
+      if (oh >= g.h_out) continue;
+      for (int kw = 0; kw < g.k; ++kw) {
+        int tw = iw + g.pad - kw;
+        if (tw < 0 || tw % g.stride) continue;
+        int ow = tw / g.stride;
+        if (ow >= g.w_out) continue;
+        for (int o = 0; o < g.c_out; ++o) {
+          Tacc wv = load_as<Tacc>(W + ((o * g.c_in + c) * g.k + kh) * g.k + kw);
+          Tacc xv = load_as<Tacc>(ir + (o * g.h_out + oh) * g.w_out + ow);
+          acc = fma(wv, xv, acc);
+          if constexpr (ABS)
+            aacc = __fmaf_ru(__double2float_ru(fabs((double)wv)), __double2float_ru(fabs((double)xv)), aacc);
+        }
+      }
+    }
+    out[idx] = acc;
+    if constexpr (ABS) outabs[idx] = aacc;
+  }
+}
+
+template <typename T>
+const char* tname();
+template <>
+const char* tname<double>() { return "f64"; }
+template <>
+const char* tname<float>() { return "f32"; }
+template <>
+const char* tname<__nv_bfloat16>() { return "bf16"; }
+
+// multiply-adds of one row of a convolution (padding taps excluded)
+double conv_macs(const LayerGeom& g) {
+  auto taps = [&](int n_out, int n_in) {
+    int64_t t = 0;
+    for (int o = 0; o < n_out; ++o)
+      for (int k = 0; k < g.k; ++k) {
+        int i = o * g.stride + k - g.pad;
+        t += (i >= 0 && i < n_in);
+      }
+    return (double)t;
+  };
+  return (double)g.c_out * g.c_in * taps(g.h_out, g.h_in) * taps(g.w_out, g.w_in);
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 152 * 64) b = 152 * 64;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+template <typename Tin, typename Tacc>
+void gemm_nt(cudaStream_t st, int64_t M, int N, int K, const Tin* A, int a_mod, const Tin* B, Tacc* C) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid((N + BN - 1) / BN, (unsigned)((M + BM - 1) / BM));
+  char nm[32];
+  snprintf(nm, sizeof nm, "gemm_simt_%s", tname<Tin>());
+  const double arows = a_mod ? (double)a_mod : (double)M;
+  if (!(reg_check(A, arows * K * sizeof(Tin), "gemm A") & reg_check(B, (double)N * K * sizeof(Tin), "gemm B") &
+        reg_check(C, (double)M * N * sizeof(Tacc), "gemm C")))
+    return;
+  int tk = prof_begin(st, nm, 2.0 * M * N * K, (arows * K + (double)N * K) * sizeof(Tin) + (double)M * N * sizeof(Tacc));
+  k_gemm_nt<Tin, Tacc, false><<<grid, 256, 0, st>>>(M, N, K, A, a_mod, B, C, nullptr);
+  prof_end(st, tk);
+}
+
+void gemm_nt_abs(cudaStream_t st, int64_t M, int N, int K, const double* A, int a_mod, const double* B,
+                 double* C, float* Cabs) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid((N + BN - 1) / BN, (unsigned)((M + BM - 1) / BM));
+  const double arows = a_mod ? (double)a_mod : (double)M;
+  if (!(reg_check(A, arows * K * 8.0, "gemm A") & reg_check(B, (double)N * K * 8.0, "gemm B") &
+        reg_check(C, (double)M * N * 8.0, "gemm C") & reg_check(Cabs, (double)M * N * 4.0, "gemm Cabs")))
+    return;
+  int tk = prof_begin(st, "gemm_simt_f64_certify", 2.0 * M * N * K, (arows * K + (double)N * K) * 8.0 + (double)M * N * 12.0);
+  k_gemm_nt<double, double, true><<<grid, 256, 0, st>>>(M, N, K, A, a_mod, B, C, Cabs);
+  prof_end(st, tk);
+}
+
+template <typename Tin, typename Tacc>
+void conv_fwd(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const Tin* in, Tacc* out) {
+  int64_t n = R * (int64_t)g.d_out;
+  if (n <= 0) return;
+  const double nw = (double)g.c_out * g.c_in * g.k * g.k;
+  if (!(reg_check(W, nw * sizeof(Tin), "conv W") & reg_check(in, (double)R * g.d_in * sizeof(Tin), "conv in") &
+        reg_check(out, (double)R * g.d_out * sizeof(Tacc), "conv out")))
+    return;
+  char nm[32];
+  snprintf(nm, sizeof nm, "conv_fwd_%s", tname<Tin>());
+  int tk = prof_begin(st, nm, 2.0 * R * conv_macs(g), (double)R * (g.d_in * sizeof(Tin) + g.d_out * sizeof(Tacc)));
+  k_conv_fwd<Tin, Tacc><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out);
+  prof_end(st, tk);
+}
+
+template <typename Tin, typename Tacc>
+void conv_T(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const Tin* in, Tacc* out) {
+  int64_t n = R * (int64_t)g.d_in;
+  if (n <= 0) return;
+  const double nw = (double)g.c_out * g.c_in * g.k * g.k;
+  if (!(reg_check(W, nw * sizeof(Tin), "convT W") & reg_check(in, (double)R * g.d_out * sizeof(Tin), "convT in") &
+        reg_check(out, (double)R * g.d_in * sizeof(Tacc), "convT out")))
+    return;
+  char nm[32];
+  snprintf(nm, sizeof nm, "conv_T_%s", tname<Tin>());
+  int tk = prof_begin(st, nm, 2.0 * R * conv_macs(g), (double)R * (g.d_out * sizeof(Tin) + g.d_in * sizeof(Tacc)));
+  k_conv_T<Tin, Tacc, false><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, nullptr);
+  prof_end(st, tk);
+}
+
+void conv_T_abs(cudaStream_t st, int64_t R, const LayerGeom& g, const double* W, const double* in, double* out,
+                float* outabs) {
+  int64_t n = R * (int64_t)g.d_in;
+  if (n <= 0) return;
+  const double nw = (double)g.c_out * g.c_in * g.k * g.k;
+  if (!(reg_check(W, nw * 8.0, "convT W") & reg_check(in, (double)R * g.d_out * 8.0, "convT in") &
+        reg_check(out, (double)R * g.d_in * 8.0, "convT out") & reg_check(outabs, (double)R * g.d_in * 4.0, "convT abs")))
+    return;
+  int tk = prof_begin(st, "conv_T_f64_certify", 2.0 * R * conv_macs(g), (double)R * (g.d_out * 8.0 + g.d_in * 12.0));
+  k_conv_T<double, double, true><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, outabs);
+  prof_end(st, tk);
+}
+
+template void gemm_nt<double, double>(cudaStream_t, int64_t, int, int, const double*, int, const double*, double*);
+template void gemm_nt<float, float>(cudaStream_t, int64_t, int, int, const float*, int, const float*, float*);
+template void gemm_nt<__nv_bfloat16, float>(cudaStream_t, int64_t, int, int, const __nv_bfloat16*, int,
+                                            const __nv_bfloat16*, float*);
+template void conv_fwd<double, double>(cudaStream_t, int64_t, const LayerGeom&, const double*, const double*, double*);
+template void conv_fwd<float, float>(cudaStream_t, int64_t, const LayerGeom&, const float*, const float*, float*);
+template void conv_fwd<__nv_bfloat16, float>(cudaStream_t, int64_t, const LayerGeom&, const __nv_bfloat16*,
+                                             const __nv_bfloat16*, float*);
+template void conv_T<double, double>(cudaStream_t, int64_t, const LayerGeom&, const double*, const double*, double*);
+template void conv_T<float, float>(cudaStream_t, int64_t, const LayerGeom&, const float*, const float*, float*);
+template void conv_T<__nv_bfloat16, float>(cudaStream_t, int64_t, const LayerGeom&, const __nv_bfloat16*,
+                                           const __nv_bfloat16*, float*);
+
+}  // namespace gcp
