@@ -905,15 +905,13 @@ static gcp_status grad_impl(Ctx& c, Batch& b, int prec, double* out_bound, doubl
     h.resize((size_t)b.M * b.R);
     e = cudaMemcpy(h.data(), gbe, h.size() * sizeof(T), cudaMemcpyDeviceToHost);
     if (e) return c.cuda(e, "copy g_beta");
-    for (int64_t r = 0; r < b.R; ++r)
-      for (int m = 0; m < b.M; ++m) gb[r * b.M + m] = (double)h[(size_t)m * b.R + r];
+    for (size_t q = 0; q < h.size(); ++q) gb[q] = (double)h[q];
   }
   if (gg && b.N > 0) {
     h.resize((size_t)b.N * b.R);
     e = cudaMemcpy(h.data(), gga, h.size() * sizeof(T), cudaMemcpyDeviceToHost);
     if (e) return c.cuda(e, "copy g_gamma");
-    for (int64_t r = 0; r < b.R; ++r)
-      for (int n = 0; n < b.N; ++n) gg[r * b.N + n] = (double)h[(size_t)n * b.R + r];
+    for (size_t q = 0; q < h.size(); ++q) gg[q] = (double)h[q];
   }
   return GCP_OK;
 }
@@ -1008,15 +1006,13 @@ gcp_status duals_export(Ctx& c, Batch& b, double* alpha, double* beta, double* g
     h.resize((size_t)b.M * b.R * es);
     e = cudaMemcpy(h.data(), b.beta, h.size(), cudaMemcpyDeviceToHost);
     if (e) return c.cuda(e, "export beta");
-    for (int64_t r = 0; r < b.R; ++r)
-      for (int m = 0; m < b.M; ++m) beta[r * b.M + m] = rd(h.data(), (size_t)m * b.R + r);
+    for (size_t q = 0; q < (size_t)b.M * b.R; ++q) beta[q] = rd(h.data(), q);
   }
   if (gamma && b.N > 0) {
     h.resize((size_t)b.N * b.R * es);
     e = cudaMemcpy(h.data(), b.gamma, h.size(), cudaMemcpyDeviceToHost);
     if (e) return c.cuda(e, "export gamma");
-    for (int64_t r = 0; r < b.R; ++r)
-      for (int n = 0; n < b.N; ++n) gamma[r * b.N + n] = rd(h.data(), (size_t)n * b.R + r);
+    for (size_t q = 0; q < (size_t)b.N * b.R; ++q) gamma[q] = rd(h.data(), q);
   }
   return GCP_OK;
 }
@@ -1048,15 +1044,13 @@ gcp_status duals_import(Ctx& c, Batch& b, const double* alpha, const double* bet
   }
   if (beta && b.M > 0) {
     h.resize((size_t)b.M * b.R * es);
-    for (int64_t r = 0; r < b.R; ++r)
-      for (int m = 0; m < b.M; ++m) wr(h.data(), (size_t)m * b.R + r, beta[r * b.M + m]);
+    for (size_t q = 0; q < (size_t)b.M * b.R; ++q) wr(h.data(), q, beta[q]);
     e = cudaMemcpy(b.beta, h.data(), h.size(), cudaMemcpyHostToDevice);
     if (e) return c.cuda(e, "import beta");
   }
   if (gamma && b.N > 0) {
     h.resize((size_t)b.N * b.R * es);
-    for (int64_t r = 0; r < b.R; ++r)
-      for (int n = 0; n < b.N; ++n) wr(h.data(), (size_t)n * b.R + r, gamma[r * b.N + n]);
+    for (size_t q = 0; q < (size_t)b.N * b.R; ++q) wr(h.data(), q, gamma[q]);
     e = cudaMemcpy(b.gamma, h.data(), h.size(), cudaMemcpyHostToDevice);
     if (e) return c.cuda(e, "import gamma");
   }
@@ -1106,8 +1100,10 @@ gcp_status load_device_duals(Ctx& c, Batch& b, cudaStream_t st, const float* alp
     }
     coff += di;
   }
-  if (beta && b.M > 0) transpose_cast<float, float>(st, b.R, b.M, beta, (float*)b.beta);
-  if (gamma && b.N > 0) transpose_cast<float, float>(st, b.R, b.N, gamma, (float*)b.gamma);
+  cudaError_t e = cudaSuccess;
+  if (beta && b.M > 0) e = cudaMemcpyAsync(b.beta, beta, (size_t)b.R * b.M * 4, cudaMemcpyDeviceToDevice, st);
+  if (!e && gamma && b.N > 0) e = cudaMemcpyAsync(b.gamma, gamma, (size_t)b.R * b.N * 4, cudaMemcpyDeviceToDevice, st);
+  if (e) return c.cuda(e, "load duals");
   return launch_status(c, "load duals");
 }
 
@@ -1172,8 +1168,10 @@ gcp_status grad_device(Ctx& c, Batch& b, int prec, const float* alpha, const flo
     coff += di;
     off += (int64_t)b.R * di;
   }
-  if (g_beta && b.M > 0) transpose_cast<float, float>(st, b.M, b.R, gbe, g_beta);
-  if (g_gamma && b.N > 0) transpose_cast<float, float>(st, b.N, b.R, gga, g_gamma);
+  cudaError_t e = cudaSuccess;
+  if (g_beta && b.M > 0) e = cudaMemcpyAsync(g_beta, gbe, (size_t)b.R * b.M * 4, cudaMemcpyDeviceToDevice, st);
+  if (!e && g_gamma && b.N > 0) e = cudaMemcpyAsync(g_gamma, gga, (size_t)b.R * b.N * 4, cudaMemcpyDeviceToDevice, st);
+  if (e) return c.cuda(e, "grad out");
   return launch_status(c, "grad out");
 }
 

@@ -79,8 +79,8 @@ struct Batch {
   int32_t* sp_index = nullptr;
   int8_t* sp_sign = nullptr;
   std::vector<void*> alpha;          // hidden layer i at index i-1, [R, d_i]
-  void* beta = nullptr;              // [M, R]
-  void* gamma = nullptr;             // [N, R]
+  void* beta = nullptr;              // [R, M]
+  void* gamma = nullptr;             // [R, N]
   std::vector<void*> owned;
   std::map<std::string, void*> lazy; // workspace by name
   std::map<std::string, size_t> lazy_bytes;

@@ -4,12 +4,13 @@
 //   chain operands nu / a          [R, d_i]  row-major, operand dtype
 //   GEMM outputs y / nubar         [R, d_i]  row-major, epilogue dtype T
 //   alpha^(i), nuhat^(i)           [R, d_i]  row-major, T
-//   beta                           [M, R]    (split slot major, rows contiguous)
-//   gamma                          [N, R]    (cut major, rows contiguous)
-//   E (cut-entry values)           [nnz, R]
+//   beta                           [R, M]    (split slot m of the row's subdomain)
+//   gamma                          [R, N]
+//   E (cut-entry values)           [R, nnz]
 //   objective partials             [P, R]
-// Cut-major / slot-major layouts make the per-row gathers of the epilogues
-// coalesced: a warp handles 32 consecutive rows of the same neuron.
+// A warp of the per-neuron kernels handles 32 consecutive neurons of one row,
+// so dense arrays move whole lines and the sparse cut gathers of a warp stay
+// inside that row's gamma / E vectors.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -24,7 +25,6 @@ namespace gcp {
 
 constexpr int kMaxSplits = 64;     // per subdomain (validated on the host)
 constexpr int kChunk = 32;         // neurons per epilogue block column
-constexpr int kRowsPerBlock = 128; // rows per epilogue block
 
 struct LayerGeom {
   int kind, d_in, d_out;
@@ -71,8 +71,8 @@ struct RelaxArgs {
   const T* hi;
   const T* bias;        // b^(layer) [d]
   const T* alpha;       // [R, d]
-  const T* beta;        // [M, R]
-  const T* gamma;       // [N, R]
+  const T* beta;        // [R, M]
+  const T* gamma;       // [R, N]
   SplitsDev sp;
   CutCSC<T> csc;
   Top* nu_out;          // [R, d]
@@ -91,15 +91,15 @@ struct AdjArgs {
   const T* hi;
   const T* bias;
   T* alpha;             // [R, d], updated in place when mode != 0
-  T* beta;              // [M, R], updated in place when mode != 0
-  const T* gamma;       // [N, R]
+  T* beta;              // [R, M], updated in place when mode != 0
+  const T* gamma;       // [R, N]
   const T* nuhat;       // [R, d]
   SplitsDev sp;
   CutCSC<T> csc;
   Top* a_out;           // [R, d] dg/dnuhat (nullptr for the last hidden layer)
-  T* E;                 // [nnz, R]
+  T* E;                 // [R, nnz]
   T* g_alpha;           // [R, d]  (mode 0)
-  T* g_beta;            // [M, R]  (mode 0)
+  T* g_beta;            // [R, M]  (mode 0)
   T* m_alpha; T* v_alpha; T* m_beta; T* v_beta;  // Adam state (mode 2)
   StepArgs<T> st;
 };
@@ -126,7 +126,7 @@ struct FinalArgs {
   int K, N, P;
   const T* cb;          // [K]  c_k^T b^(L)
   const T* d;           // [N]
-  const T* gamma;       // [N, R]
+  const T* gamma;       // [R, N]
   const T* obj_part;    // [P, R]
   T* g;                 // [R]
 };
@@ -139,8 +139,8 @@ struct GatherArgs {
   const T* E;
   const T* d;
   const T* seed;
-  T* gamma;             // [N, R] updated when mode != 0
-  T* g_gamma;           // [N, R] mode 0
+  T* gamma;             // [R, N] updated when mode != 0
+  T* g_gamma;           // [R, N] mode 0
   T* m_gamma; T* v_gamma;
   StepArgs<T> st;
   int64_t nnz;          // cut entries (host-side accounting only)

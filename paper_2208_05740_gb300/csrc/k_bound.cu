@@ -1,10 +1,12 @@
 // Per-neuron kernels of the GCP-CROWN chain (Theorem 3.1, Lemma A.1, App. A).
 //
-// Thread mapping: one thread per row, a block covers kRowsPerBlock consecutive
-// rows and kChunk consecutive neurons of one layer; every cut / split gather of
-// a warp reads 32 consecutive rows of the same cut (coalesced, see layout note
-// in gcp_internal.cuh). Per-row objective partials are written per neuron
-// chunk and summed in a fixed order (deterministic results).
+// Thread mapping: a warp owns one row and 32 consecutive neurons of one layer
+// (lane = neuron), so every per-(row, neuron) array is read and written as
+// whole 128-byte lines. Cut multipliers gamma [R, N], split multipliers
+// beta [R, M] and cut-entry values E [R, nnz] are row-major, so the sparse
+// gathers of a warp stay inside one row's vector. Per-row objective partials
+// are reduced across the warp in a fixed shuffle order and written per neuron
+// chunk, then summed in a fixed order (deterministic results).
 #include <cstdio>
 
 #include "gcp_internal.cuh"
@@ -17,6 +19,8 @@ __device__ unsigned long long g_dev_err[3];
 
 namespace {
 
+constexpr int kWarpsPerBlock = 8;
+
 __device__ __noinline__ void dev_error(unsigned long long code, long long idx, long long lim) {
   if (atomicCAS(&g_dev_err[0], 0ull, code) == 0ull) {
     g_dev_err[1] = (unsigned long long)idx;
@@ -26,15 +30,13 @@ __device__ __noinline__ void dev_error(unsigned long long code, long long idx, l
 
 // entry range of neuron j, checked against the entry count
 template <typename T>
-__device__ __forceinline__ bool csc_range(const CutCSC<T>& c, int j, int& e0, int& e1) {
+__device__ __forceinline__ void csc_range(const CutCSC<T>& c, int j, int& e0, int& e1) {
   e0 = c.ptr[j];
   e1 = c.ptr[j + 1];
   if (e0 < 0 || e1 < e0 || (int64_t)e1 > c.n_total) {
     dev_error(1, j, c.n_total);
     e0 = e1 = 0;
-    return false;
   }
-  return true;
 }
 
 // split entries of subdomain s, checked against the entry count and slots
@@ -57,28 +59,48 @@ __device__ __forceinline__ Top cvt_out(T v) { return static_cast<Top>(v); }
 template <>
 __device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
 
-// mask of neurons in [j0, j0+32) split in this row's subdomain on `layer`
-__device__ __forceinline__ uint32_t split_mask(const SplitsDev& sp, int q0, int q1, int layer, int j0, int jend) {
-  uint32_t m = 0;
-  for (int q = q0; q < q1; ++q) {
-    int j = sp.index[q];
-    if (sp.layer[q] == layer && j >= j0 && j < jend) m |= 1u << (j - j0);
-  }
-  return m;
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_rd(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = __dadd_rd(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
 }
 
-// Sparse cut sums for neuron j of this row: t = H^T gamma, g = G^T gamma, s = Q^T gamma.
-template <typename T>
-__device__ __forceinline__ void cut_sums(const CutCSC<T>& c, const T* gamma, int64_t R, int N, int64_t r, int j,
-                                         T& t, T& g, T& s) {
+// Warp coordinates: (row r, neuron chunk c, neuron j = 32c + lane). Returns
+// false for warps past the end (the whole warp leaves together).
+struct WarpPos {
+  int64_t r;
+  int c, j, lane;
+  bool on;
+};
+__device__ __forceinline__ bool warp_pos(int64_t R, int d, WarpPos& p) {
+  const int nch = (d + 31) >> 5;
+  const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (w >= R * nch) return false;
+  p.r = w / nch;
+  p.c = (int)(w - p.r * nch);
+  p.lane = threadIdx.x & 31;
+  p.j = p.c * 32 + p.lane;
+  p.on = p.j < d;
+  return true;
+}
+
+// Sparse cut sums for neuron j of row r: t = H^T gamma, g = G^T gamma, s = Q^T gamma.
+template <typename T, typename Tg>
+__device__ __forceinline__ void cut_sums(const CutCSC<T>& c, const Tg* grow, int N, int j, T& t, T& g, T& s) {
   t = T(0); g = T(0); s = T(0);
   int e0, e1;
   csc_range(c, j, e0, e1);
   for (int e = e0; e < e1; ++e) {
     const int k = c.cut[e];
     if (k < 0 || k >= N) { dev_error(2, e, N); continue; }
-    T v = c.coef[e] * gamma[(int64_t)k * R + r];
-    int kd = c.kind[e];
+    const T v = c.coef[e] * (T)grow[k];
+    const int kd = c.kind[e];
     if (kd == GCP_VAR_X) t += v;
     else if (kd == GCP_VAR_XHAT) g += v;
     else s += v;
@@ -97,33 +119,29 @@ __device__ __forceinline__ T step_apply(const StepArgs<T>& st, T x, T grad, T lr
 
 // ------------------------------------------------------------------ eval
 template <typename T, typename Top>
-__global__ void __launch_bounds__(kRowsPerBlock) k_relax_eval(RelaxArgs<T, Top> a) {
-  const int64_t r = (int64_t)blockIdx.x * kRowsPerBlock + threadIdx.x;
-  if (r >= a.R) return;
-  const int j0 = blockIdx.y * kChunk, jend = min(j0 + kChunk, a.d);
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_eval(RelaxArgs<T, Top> a) {
+  WarpPos p;
+  if (!warp_pos(a.R, a.d, p)) return;
+  const int64_t r = p.r;
+  const int j = p.j;
   const int s = (int)(r / a.K), k = (int)(r - (int64_t)s * a.K);
-  const T* yrow = a.y + (a.y_per_spec ? (int64_t)k : r) * a.d;
-  int sp0, sp1;
-  split_range(a.sp, s, a.M, sp0, sp1);
-  const uint32_t smask = split_mask(a.sp, sp0, sp1, a.layer, j0, jend);
-  T acc = T(0);
-  for (int j = j0; j < jend; ++j) {
+  T term = T(0);
+  if (p.on) {
     T t, gg, sq;
-    cut_sums(a.csc, a.gamma, a.R, a.N, r, j, t, gg, sq);
+    cut_sums(a.csc, a.gamma + r * a.N, a.N, j, t, gg, sq);
     T lo = a.lo[j], hi = a.hi[j];
-    if ((smask >> (j - j0)) & 1u) {
-      for (int q = sp0; q < sp1; ++q)
-        if (a.sp.layer[q] == a.layer && a.sp.index[q] == j) {
-          const T bv = a.beta[(int64_t)(q - sp0) * a.R + r];
-          if (a.sp.sign[q] > 0) { t -= bv; lo = tmax(lo, T(0)); }   // row -x <= 0
-          else { t += bv; hi = tmin(hi, T(0)); }                    // row  x <= 0
-        }
-    }
-    const T nh = yrow[j] - gg;
-    T nu, term;
+    int q0, q1;
+    split_range(a.sp, s, a.M, q0, q1);
+    for (int q = q0; q < q1; ++q)
+      if (a.sp.layer[q] == a.layer && a.sp.index[q] == j) {
+        const T bv = a.beta[r * a.M + (q - q0)];
+        if (a.sp.sign[q] > 0) { t -= bv; lo = tmax(lo, T(0)); }   // row -x <= 0
+        else { t += bv; hi = tmin(hi, T(0)); }                    // row  x <= 0
+      }
+    const T nh = a.y[(a.y_per_spec ? (int64_t)k : r) * a.d + j] - gg;
+    T nu;
     if (hi <= T(0)) {            // inactive: xhat = 0, z = 0
       nu = -t;
-      term = T(0);
     } else if (lo >= T(0)) {     // active: xhat = x, z = 1
       nu = nh - t;
       term = sq;
@@ -131,166 +149,167 @@ __global__ void __launch_bounds__(kRowsPerBlock) k_relax_eval(RelaxArgs<T, Top> 
       const T C = tmax(nh, T(0));
       const T p0 = (hi * C - sq) / (hi - lo);
       const T pi = tmin(tmax(p0, T(0)), C);
-      const T h = lo * pi - tmax(T(0), hi * (C - pi) + lo * pi - sq);
+      term = lo * pi - tmax(T(0), hi * (C - pi) + lo * pi - sq);
       const T tau = a.alpha[r * a.d + j] * tmax(-nh, T(0));
       nu = pi - tau - t;
-      term = h;
     }
-    acc += term - nu * a.bias[j];
+    term -= nu * a.bias[j];
     a.nu_out[r * a.d + j] = cvt_out<Top>(nu);
     a.nuhat_out[r * a.d + j] = nh;
   }
-  a.obj_part[(int64_t)blockIdx.y * a.R + r] = acc;
+  term = warp_sum(term);
+  if (p.lane == 0) a.obj_part[(int64_t)p.c * a.R + r] = term;
 }
 
 // ------------------------------------------------------------------ adjoint
 template <typename T, typename Top>
-__global__ void __launch_bounds__(kRowsPerBlock) k_relax_adj(AdjArgs<T, Top> a) {
-  const int64_t r = (int64_t)blockIdx.x * kRowsPerBlock + threadIdx.x;
-  if (r >= a.R) return;
-  const int j0 = blockIdx.y * kChunk, jend = min(j0 + kChunk, a.d);
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_adj(AdjArgs<T, Top> a) {
+  WarpPos p;
+  if (!warp_pos(a.R, a.d, p) || !p.on) return;
+  const int64_t r = p.r;
+  const int j = p.j;
   const int s = (int)(r / a.K);
-  int sp0, sp1;
-  split_range(a.sp, s, a.M, sp0, sp1);
-  const uint32_t smask = split_mask(a.sp, sp0, sp1, a.layer, j0, jend);
   const T w = a.seed ? a.seed[r] : T(1);
-  for (int j = j0; j < jend; ++j) {
-    const T nb = a.nubar[r * a.d + j] - w * a.bias[j];   // dg/dnu^(i)
-    T t, gg, sq;
-    cut_sums(a.csc, a.gamma, a.R, a.N, r, j, t, gg, sq);
-    T lo = a.lo[j], hi = a.hi[j];
-    const bool split = (smask >> (j - j0)) & 1u;
-    if (split) {
-      for (int q = sp0; q < sp1; ++q)
-        if (a.sp.layer[q] == a.layer && a.sp.index[q] == j) {
-          if (a.sp.sign[q] > 0) lo = tmax(lo, T(0)); else hi = tmin(hi, T(0));
-        }
+  const int64_t ij = r * a.d + j;
+  const T nb = a.nubar[ij] - w * a.bias[j];   // dg/dnu^(i)
+  T t, gg, sq;
+  cut_sums(a.csc, a.gamma + r * a.N, a.N, j, t, gg, sq);
+  T lo = a.lo[j], hi = a.hi[j];
+  int q0, q1;
+  split_range(a.sp, s, a.M, q0, q1);
+  int split_q = -1;
+  for (int q = q0; q < q1; ++q)
+    if (a.sp.layer[q] == a.layer && a.sp.index[q] == j) {
+      split_q = q;
+      if (a.sp.sign[q] > 0) lo = tmax(lo, T(0)); else hi = tmin(hi, T(0));
     }
-    T dnu_dnh = T(0), dh_dnh = T(0), dnu_ds = T(0), dh_ds = T(0), g_alpha = T(0);
-    const bool unstable = !(hi <= T(0)) && !(lo >= T(0));
-    if (!unstable) {
-      if (!(hi <= T(0))) { dnu_dnh = T(1); dh_ds = w; }     // active
+  T dnu_dnh = T(0), dh_dnh = T(0), dnu_ds = T(0), dh_ds = T(0);
+  const bool unstable = !(hi <= T(0)) && !(lo >= T(0));
+  if (!unstable) {
+    if (!(hi <= T(0))) { dnu_dnh = T(1); dh_ds = w; }     // active
+    if (a.st.mode == 0) a.g_alpha[ij] = T(0);
+  } else {
+    const T nh = a.nuhat[ij];
+    const T al = a.alpha[ij];
+    if (nh > T(0)) {
+      const T ul = hi - lo;
+      const T p0 = (hi * nh - sq) / ul;
+      if (p0 > T(0) && p0 < nh) {          // pi* = p0
+        dnu_dnh = hi / ul;
+        dh_dnh = w * lo * hi / ul;
+        dnu_ds = -T(1) / ul;
+        dh_ds = -w * lo / ul;
+      } else if (p0 >= nh) {               // pi* = C, h = s when l C - s > 0
+        dnu_dnh = T(1);
+        dh_ds = (lo * nh - sq > T(0)) ? w : T(0);
+      }
     } else {
-      const T nh = a.nuhat[r * a.d + j];
-      const T al = a.alpha[r * a.d + j];
-      if (nh > T(0)) {
-        const T ul = hi - lo;
-        const T p0 = (hi * nh - sq) / ul;
-        if (p0 > T(0) && p0 < nh) {          // pi* = p0
-          dnu_dnh = hi / ul;
-          dh_dnh = w * lo * hi / ul;
-          dnu_ds = -T(1) / ul;
-          dh_ds = -w * lo / ul;
-        } else if (p0 >= nh) {               // pi* = C, h = s when l C - s > 0
-          dnu_dnh = T(1);
-          dh_ds = (lo * nh - sq > T(0)) ? w : T(0);
-        }
-      } else {
-        if (nh < T(0)) dnu_dnh = al;         // nu = alpha * nuhat
-        dh_ds = (sq < T(0)) ? w : T(0);      // h = min(s, 0)
-      }
-      g_alpha = nb * (-tmax(-nh, T(0)));
-      if (a.st.mode == 0) {
-        a.g_alpha[r * a.d + j] = g_alpha;
-      } else {
-        T na = step_apply(a.st, al, g_alpha, a.st.lr_a, a.m_alpha ? a.m_alpha + r * a.d + j : nullptr,
-                          a.v_alpha ? a.v_alpha + r * a.d + j : nullptr);
-        a.alpha[r * a.d + j] = tmin(tmax(na, T(0)), T(1));
-      }
+      if (nh < T(0)) dnu_dnh = al;         // nu = alpha * nuhat
+      dh_ds = (sq < T(0)) ? w : T(0);      // h = min(s, 0)
     }
-    if (!unstable && a.st.mode == 0) a.g_alpha[r * a.d + j] = T(0);
-    const T dg_dnh = nb * dnu_dnh + dh_dnh;
-    const T dg_ds = nb * dnu_ds + dh_ds;
-    const T dg_dt = -nb;
-    if (a.a_out) a.a_out[r * a.d + j] = cvt_out<Top>(dg_dnh);
-    int e0, e1;
-    csc_range(a.csc, j, e0, e1);
-    for (int e = e0; e < e1; ++e) {
-      const int kd = a.csc.kind[e];
-      const T v = kd == GCP_VAR_X ? dg_dt : (kd == GCP_VAR_XHAT ? -dg_dnh : dg_ds);
-      const int row = a.csc.eid[e];
-      if (row < 0 || (int64_t)row >= a.csc.n_total) { dev_error(4, e, a.csc.n_total); continue; }
-      a.E[(int64_t)row * a.R + r] = a.csc.coef[e] * v;
+    const T g_alpha = nb * (-tmax(-nh, T(0)));
+    if (a.st.mode == 0) {
+      a.g_alpha[ij] = g_alpha;
+    } else {
+      T na = step_apply(a.st, al, g_alpha, a.st.lr_a, a.m_alpha ? a.m_alpha + ij : nullptr,
+                        a.v_alpha ? a.v_alpha + ij : nullptr);
+      a.alpha[ij] = tmin(tmax(na, T(0)), T(1));
     }
-    if (split) {
-      for (int q = sp0; q < sp1; ++q)
-        if (a.sp.layer[q] == a.layer && a.sp.index[q] == j) {
-          const int64_t bi = (int64_t)(q - sp0) * a.R + r;
-          const T gb = (a.sp.sign[q] > 0 ? T(-1) : T(1)) * dg_dt;
-          if (a.st.mode == 0) {
-            a.g_beta[bi] = gb;
-          } else {
-            T nbv = step_apply(a.st, a.beta[bi], gb, a.st.lr_b, a.m_beta ? a.m_beta + bi : nullptr,
-                               a.v_beta ? a.v_beta + bi : nullptr);
-            a.beta[bi] = tmax(nbv, T(0));
-          }
-        }
+  }
+  const T dg_dnh = nb * dnu_dnh + dh_dnh;
+  const T dg_ds = nb * dnu_ds + dh_ds;
+  const T dg_dt = -nb;
+  if (a.a_out) a.a_out[ij] = cvt_out<Top>(dg_dnh);
+  int e0, e1;
+  csc_range(a.csc, j, e0, e1);
+  for (int e = e0; e < e1; ++e) {
+    const int kd = a.csc.kind[e];
+    const T v = kd == GCP_VAR_X ? dg_dt : (kd == GCP_VAR_XHAT ? -dg_dnh : dg_ds);
+    const int row = a.csc.eid[e];
+    if (row < 0 || (int64_t)row >= a.csc.n_total) { dev_error(4, e, a.csc.n_total); continue; }
+    a.E[r * a.csc.n_total + row] = a.csc.coef[e] * v;
+  }
+  if (split_q >= 0) {
+    const int64_t bi = r * a.M + (split_q - q0);
+    const T gb = (a.sp.sign[split_q] > 0 ? T(-1) : T(1)) * dg_dt;
+    if (a.st.mode == 0) {
+      a.g_beta[bi] = gb;
+    } else {
+      T nbv = step_apply(a.st, a.beta[bi], gb, a.st.lr_b, a.m_beta ? a.m_beta + bi : nullptr,
+                         a.v_beta ? a.v_beta + bi : nullptr);
+      a.beta[bi] = tmax(nbv, T(0));
     }
   }
 }
 
 // ------------------------------------------------------------------ concretization
 template <typename T, typename Top>
-__global__ void __launch_bounds__(kRowsPerBlock) k_concretize(ConcArgs<T, Top> a) {
-  const int64_t r = (int64_t)blockIdx.x * kRowsPerBlock + threadIdx.x;
-  if (r >= a.R) return;
-  const int j0 = blockIdx.y * kChunk, jend = min(j0 + kChunk, a.d0);
-  const T w = a.seed ? a.seed[r] : T(1);
-  T acc = T(0);
-  for (int j = j0; j < jend; ++j) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_concretize(ConcArgs<T, Top> a) {
+  WarpPos p;
+  if (!warp_pos(a.R, a.d0, p)) return;
+  const int64_t r = p.r;
+  const int j = p.j;
+  T term = T(0);
+  if (p.on) {
+    const T w = a.seed ? a.seed[r] : T(1);
+    const T* grow = a.gamma + r * a.N;
     T h0 = T(0);
     int e0, e1;
     csc_range(a.csc, j, e0, e1);
     for (int e = e0; e < e1; ++e) {
       const int kc = a.csc.cut[e];
       if (kc < 0 || kc >= a.N) { dev_error(2, e, a.N); continue; }
-      h0 += a.csc.coef[e] * a.gamma[(int64_t)kc * a.R + r];
+      h0 += a.csc.coef[e] * grow[kc];
     }
     const T c0 = -a.y0[r * a.d0 + j] + h0;
     const T xl = a.x_lo[j], xh = a.x_hi[j];
-    acc += tmin(c0 * xl, c0 * xh);
+    term = tmin(c0 * xl, c0 * xh);
     const T xs = c0 > T(0) ? xl : (c0 < T(0) ? xh : T(0.5) * (xl + xh));
     if (a.a0_out) a.a0_out[r * a.d0 + j] = cvt_out<Top>(-w * xs);
     if (a.E)
       for (int e = e0; e < e1; ++e) {
         const int row = a.csc.eid[e];
         if (row < 0 || (int64_t)row >= a.csc.n_total) { dev_error(4, e, a.csc.n_total); continue; }
-        a.E[(int64_t)row * a.R + r] = a.csc.coef[e] * w * xs;
+        a.E[r * a.csc.n_total + row] = a.csc.coef[e] * w * xs;
       }
   }
-  a.obj_part[(int64_t)blockIdx.y * a.R + r] = acc;
+  term = warp_sum(term);
+  if (p.lane == 0) a.obj_part[(int64_t)p.c * a.R + r] = term;
 }
 
+// g[r] = c_k^T b^(L) - gamma_r^T d + sum of the partials; one warp per row.
 template <typename T>
-__global__ void k_finalize(FinalArgs<T> a) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_finalize(FinalArgs<T> a) {
+  const int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (r >= a.R) return;
-  const int k = (int)(r % a.K);
-  T g = a.cb[k];
-  for (int n = 0; n < a.N; ++n) g -= a.gamma[(int64_t)n * a.R + r] * a.d[n];
-  for (int p = 0; p < a.P; ++p) g += a.obj_part[(int64_t)p * a.R + r];
-  a.g[r] = g;
+  const int lane = threadIdx.x & 31;
+  T g = T(0);
+  for (int n = lane; n < a.N; n += 32) g -= a.gamma[r * a.N + n] * a.d[n];
+  for (int q = lane; q < a.P; q += 32) g += a.obj_part[(int64_t)q * a.R + r];
+  g = warp_sum(g);
+  if (lane == 0) a.g[r] = g + a.cb[(int)(r % a.K)];
 }
 
 // dg/dgamma_k = -d_k + sum of the cut's entry values (violation of cut k at the
 // primal point implied by the duals), then the projected step on gamma.
 template <typename T>
 __global__ void k_gather(GatherArgs<T> a) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = blockIdx.y;
-  if (r >= a.R) return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.R * a.N) return;
+  const int64_t r = i / a.N;
+  const int n = (int)(i - r * a.N);
   const T w = a.seed ? a.seed[r] : T(1);
   T grad = -w * a.d[n];
   int e0 = a.cut_ptr[n], e1 = a.cut_ptr[n + 1];
   if (e0 < 0 || e1 < e0 || (int64_t)e1 > a.nnz) { dev_error(5, n, a.nnz); e0 = e1 = 0; }
-  for (int e = e0; e < e1; ++e) grad += a.E[(int64_t)e * a.R + r];
-  const int64_t gi = (int64_t)n * a.R + r;
+  const T* Er = a.E + r * a.nnz;
+  for (int e = e0; e < e1; ++e) grad += Er[e];
   if (a.st.mode == 0) {
-    a.g_gamma[gi] = grad;
+    a.g_gamma[i] = grad;
   } else {
-    T x = step_apply(a.st, a.gamma[gi], grad, a.st.lr_g, a.m_gamma ? a.m_gamma + gi : nullptr,
-                     a.v_gamma ? a.v_gamma + gi : nullptr);
-    a.gamma[gi] = tmax(x, T(0));
+    T x = step_apply(a.st, a.gamma[i], grad, a.st.lr_g, a.m_gamma ? a.m_gamma + i : nullptr,
+                     a.v_gamma ? a.v_gamma + i : nullptr);
+    a.gamma[i] = tmax(x, T(0));
   }
 }
 
@@ -307,17 +326,16 @@ __device__ __forceinline__ double gamma_of(int n) {
 }
 
 template <typename Td>
-__global__ void __launch_bounds__(kRowsPerBlock) k_certify_relax(CertArgs<Td> a) {
-  const int64_t r = (int64_t)blockIdx.x * kRowsPerBlock + threadIdx.x;
-  if (r >= a.R) return;
-  const int j0 = blockIdx.y * kChunk, jend = min(j0 + kChunk, a.d);
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_relax(CertArgs<Td> a) {
+  WarpPos p;
+  if (!warp_pos(a.R, a.d, p)) return;
+  const int64_t r = p.r;
+  const int j = p.j;
   const int s = (int)(r / a.K), k = (int)(r - (int64_t)s * a.K);
-  const int64_t yr = (a.y_per_spec ? (int64_t)k : r) * a.d;
-  int sp0, sp1;
-  split_range(a.sp, s, a.M, sp0, sp1);
-  const uint32_t smask = split_mask(a.sp, sp0, sp1, a.layer, j0, jend);
-  double acc = 0.0;
-  for (int j = j0; j < jend; ++j) {
+  double part = 0.0;
+  if (p.on) {
+    const int64_t yi = (a.y_per_spec ? (int64_t)k : r) * a.d + j;
+    const Td* grow = a.gamma + r * a.N;
     // sparse sums in round-to-nearest with their Higham error bounds
     double t = 0, gg = 0, sq = 0, ta = 0, ga = 0, sa = 0;
     int nt = 0, ng = 0, ns = 0;
@@ -326,7 +344,7 @@ __global__ void __launch_bounds__(kRowsPerBlock) k_certify_relax(CertArgs<Td> a)
     for (int e = e0; e < e1; ++e) {
       const int kc = a.csc.cut[e];
       if (kc < 0 || kc >= a.N) { dev_error(2, e, a.N); continue; }
-      const double gv = (double)a.gamma[(int64_t)kc * a.R + r];
+      const double gv = (double)grow[kc];
       const double v = a.csc.coef[e] * gv;
       const double av = __dmul_ru(fabs(a.csc.coef[e]), fabs(gv));
       const int kd = a.csc.kind[e];
@@ -335,28 +353,28 @@ __global__ void __launch_bounds__(kRowsPerBlock) k_certify_relax(CertArgs<Td> a)
       else { sq += v; sa = __dadd_ru(sa, av); ++ns; }
     }
     double lo = a.lo[j], hi = a.hi[j];
-    if ((smask >> (j - j0)) & 1u) {
-      for (int q = sp0; q < sp1; ++q)
-        if (a.sp.layer[q] == a.layer && a.sp.index[q] == j) {
-          const double bv = (double)a.beta[(int64_t)(q - sp0) * a.R + r];
-          if (a.sp.sign[q] > 0) { t -= bv; lo = fmax(lo, 0.0); }
-          else { t += bv; hi = fmin(hi, 0.0); }
-          ta = __dadd_ru(ta, fabs(bv));
-          ++nt;
-        }
-    }
+    int q0, q1;
+    split_range(a.sp, s, a.M, q0, q1);
+    for (int q = q0; q < q1; ++q)
+      if (a.sp.layer[q] == a.layer && a.sp.index[q] == j) {
+        const double bv = (double)a.beta[r * a.M + (q - q0)];
+        if (a.sp.sign[q] > 0) { t -= bv; lo = fmax(lo, 0.0); }
+        else { t += bv; hi = fmin(hi, 0.0); }
+        ta = __dadd_ru(ta, fabs(bv));
+        ++nt;
+      }
     const double et = __dmul_ru(gamma_of(nt), ta);
     const double eg = __dmul_ru(gamma_of(ng), ga);
     const double es = __dmul_ru(gamma_of(ns), sa);
-    const double y = a.y[yr + j];
-    const double ey = __dmul_ru(a.gamma_n, (double)a.yabs[yr + j]);
+    const double y = a.y[yi];
+    const double ey = __dmul_ru(a.gamma_n, (double)a.yabs[yi]);
     const double nh = y - gg;
     // enclosures of the exact t, y, g, s
     const double t_lo = __dsub_rd(t, et), t_hi = __dadd_ru(t, et);
     const double y_lo = __dsub_rd(y, ey), y_hi = __dadd_ru(y, ey);
     const double g_lo = __dsub_rd(gg, eg), g_hi = __dadd_ru(gg, eg);
     const double s_lo = __dsub_rd(sq, es);
-    double nu, part = 0.0;
+    double nu;
     if (hi <= 0.0) {
       // inactive: xhat = z = 0; Lagrangian term (nu + t) x over x in [lo, hi]
       nu = -t;
@@ -369,13 +387,13 @@ __global__ void __launch_bounds__(kRowsPerBlock) k_certify_relax(CertArgs<Td> a)
       part = __dadd_rd(box_min_rd(klo, khi, lo, hi), s_lo);
     } else {
       // unstable: explicit duals pi, gamma_r = C - pi, tau, mu = M - tau (all >= 0)
-      const double C = fmax(nh, 0.0), M = fmax(-nh, 0.0);
+      const double C = fmax(nh, 0.0), Mm = fmax(-nh, 0.0);
       const double p0 = (hi * C - sq) / (hi - lo);
       const double pi = fmin(fmax(p0, 0.0), C);
       const double gr = C - pi;
       const double al = fmin(fmax((double)a.alpha[r * a.d + j], 0.0), 1.0);
-      const double tau = al * M;
-      const double mu = M - tau;
+      const double tau = al * Mm;
+      const double mu = Mm - tau;
       nu = (pi - tau) - t;
       // x: (nu + t + tau - pi) x over [lo, hi]
       const double kx_lo = __dsub_rd(__dadd_rd(__dadd_rd(nu, t_lo), tau), pi);
@@ -391,23 +409,25 @@ __global__ void __launch_bounds__(kRowsPerBlock) k_certify_relax(CertArgs<Td> a)
       part = __dadd_rd(part, __dmul_rd(pi, lo));
     }
     part = __dadd_rd(part, __dmul_rd(-nu, a.bias[j]));
-    acc = __dadd_rd(acc, part);
     a.nu_out[r * a.d + j] = nu;
   }
-  a.obj_part[(int64_t)blockIdx.y * a.R + r] = acc;
+  part = warp_sum_rd(part);
+  if (p.lane == 0) a.obj_part[(int64_t)p.c * a.R + r] = part;
 }
 
 template <typename Td>
-__global__ void __launch_bounds__(kRowsPerBlock) k_certify_conc(int64_t R, int K, int N, int d0, const double* y0,
-                                                                const float* y0abs, double gamma_n,
-                                                                const double* x_lo, const double* x_hi,
-                                                                const Td* gamma, CutCSC<double> csc,
-                                                                double* obj_part) {
-  const int64_t r = (int64_t)blockIdx.x * kRowsPerBlock + threadIdx.x;
-  if (r >= R) return;
-  const int j0 = blockIdx.y * kChunk, jend = min(j0 + kChunk, d0);
-  double acc = 0.0;
-  for (int j = j0; j < jend; ++j) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_conc(int64_t R, int K, int N, int d0,
+                                                                       const double* y0, const float* y0abs,
+                                                                       double gamma_n, const double* x_lo,
+                                                                       const double* x_hi, const Td* gamma,
+                                                                       CutCSC<double> csc, double* obj_part) {
+  WarpPos p;
+  if (!warp_pos(R, d0, p)) return;
+  const int64_t r = p.r;
+  const int j = p.j;
+  double part = 0.0;
+  if (p.on) {
+    const Td* grow = gamma + r * N;
     double h = 0, ha = 0;
     int n = 0;
     int e0, e1;
@@ -415,7 +435,7 @@ __global__ void __launch_bounds__(kRowsPerBlock) k_certify_conc(int64_t R, int K
     for (int e = e0; e < e1; ++e) {
       const int kc = csc.cut[e];
       if (kc < 0 || kc >= N) { dev_error(2, e, N); continue; }
-      const double gv = (double)gamma[(int64_t)kc * R + r];
+      const double gv = (double)grow[kc];
       h += csc.coef[e] * gv;
       ha = __dadd_ru(ha, __dmul_ru(fabs(csc.coef[e]), fabs(gv)));
       ++n;
@@ -425,22 +445,27 @@ __global__ void __launch_bounds__(kRowsPerBlock) k_certify_conc(int64_t R, int K
     const double ey = __dmul_ru(gamma_n, (double)y0abs[r * d0 + j]);
     const double c_lo = __dadd_rd(__dsub_rd(-y, ey), __dsub_rd(h, eh));
     const double c_hi = __dadd_ru(__dadd_ru(-y, ey), __dadd_ru(h, eh));
-    acc = __dadd_rd(acc, box_min_rd(c_lo, c_hi, x_lo[j], x_hi[j]));
+    part = box_min_rd(c_lo, c_hi, x_lo[j], x_hi[j]);
   }
-  obj_part[(int64_t)blockIdx.y * R + r] = acc;
+  part = warp_sum_rd(part);
+  if (p.lane == 0) obj_part[(int64_t)p.c * R + r] = part;
 }
 
 template <typename Td>
-__global__ void k_certify_final(int64_t R, int K, int N, int P, const double* C, const double* bL, int dL,
-                                const double* d, const Td* gamma, const double* obj_part, double* out) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_final(int64_t R, int K, int N, int P, const double* C,
+                                                                       const double* bL, int dL, const double* d,
+                                                                       const Td* gamma, const double* obj_part,
+                                                                       double* out) {
+  const int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (r >= R) return;
+  const int lane = threadIdx.x & 31;
   const int k = (int)(r % K);
   double g = 0.0;
-  for (int q = 0; q < dL; ++q) g = __dadd_rd(g, __dmul_rd(C[(int64_t)k * dL + q], bL[q]));  // -nu^(L)^T b^(L)
-  for (int n = 0; n < N; ++n) g = __dadd_rd(g, __dmul_rd(-(double)gamma[(int64_t)n * R + r], d[n]));
-  for (int p = 0; p < P; ++p) g = __dadd_rd(g, obj_part[(int64_t)p * R + r]);
-  out[r] = g;
+  for (int q = lane; q < dL; q += 32) g = __dadd_rd(g, __dmul_rd(C[(int64_t)k * dL + q], bL[q]));  // -nu^(L)^T b^(L)
+  for (int n = lane; n < N; n += 32) g = __dadd_rd(g, __dmul_rd(-(double)gamma[r * N + n], d[n]));
+  for (int q = lane; q < P; q += 32) g = __dadd_rd(g, obj_part[(int64_t)q * R + r]);
+  g = warp_sum_rd(g);
+  if (lane == 0) out[r] = g;
 }
 
 // ------------------------------------------------------------------ layout helpers
@@ -484,9 +509,12 @@ __global__ void k_default_alpha(int64_t R, int K, int d, int layer, const T* lo,
   }
 }
 
-inline dim3 epi_grid(int64_t R, int d) {
-  return dim3((unsigned)((R + kRowsPerBlock - 1) / kRowsPerBlock), (unsigned)((d + kChunk - 1) / kChunk));
+// one warp per (row, 32-neuron chunk)
+inline unsigned warp_blocks(int64_t R, int d) {
+  const int64_t warps = R * (int64_t)((d + 31) / 32);
+  return (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
 }
+inline unsigned row_blocks(int64_t R) { return (unsigned)((R + kWarpsPerBlock - 1) / kWarpsPerBlock); }
 inline int flat_grid(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 32) b = 152 * 32;
@@ -530,7 +558,7 @@ void relax_eval(cudaStream_t st, const RelaxArgs<T, Top>& a) {
         reg_check(a.nuhat_out, Rd * tb, "nuhat out") & reg_check(a.obj_part, chunks(a.d) * a.R * tb, "obj part")))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
-  k_relax_eval<T, Top><<<epi_grid(a.R, a.d), kRowsPerBlock, 0, st>>>(a);
+  k_relax_eval<T, Top><<<warp_blocks(a.R, a.d), kWarpsPerBlock * 32, 0, st>>>(a);
   prof_end(st, tk);
 }
 template <typename T, typename Top>
@@ -556,7 +584,7 @@ void relax_adjoint(cudaStream_t st, const AdjArgs<T, Top>& a) {
         reg_check(a.v_beta, m2 ? (double)a.M * a.R * tb : 0.0, "v_beta")))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
-  k_relax_adj<T, Top><<<epi_grid(a.R, a.d), kRowsPerBlock, 0, st>>>(a);
+  k_relax_adj<T, Top><<<warp_blocks(a.R, a.d), kWarpsPerBlock * 32, 0, st>>>(a);
   prof_end(st, tk);
 }
 template <typename T, typename Top>
@@ -575,7 +603,7 @@ void concretize(cudaStream_t st, const ConcArgs<T, Top>& a) {
         reg_check(a.obj_part, chunks(a.d0) * a.R * tb, "obj part")))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
-  k_concretize<T, Top><<<epi_grid(a.R, a.d0), kRowsPerBlock, 0, st>>>(a);
+  k_concretize<T, Top><<<warp_blocks(a.R, a.d0), kWarpsPerBlock * 32, 0, st>>>(a);
   prof_end(st, tk);
 }
 template <typename T>
@@ -588,7 +616,7 @@ void finalize_bound(cudaStream_t st, const FinalArgs<T>& a) {
     return;
   int tk = prof_begin(st, sizeof(T) == 8 ? "finalize_f64" : "finalize_f32", 0.0,
                       (double)a.R * (a.N + a.P + 1) * sizeof(T));
-  k_finalize<T><<<(unsigned)((a.R + 255) / 256), 256, 0, st>>>(a);
+  k_finalize<T><<<row_blocks(a.R), kWarpsPerBlock * 32, 0, st>>>(a);
   prof_end(st, tk);
 }
 template <typename T>
@@ -603,7 +631,7 @@ void gather_gamma(cudaStream_t st, const GatherArgs<T>& a) {
     return;
   int tk = prof_begin(st, sizeof(T) == 8 ? "gather_gamma_f64" : "gather_gamma_f32", 0.0,
                       (double)a.R * (a.nnz + 2.0 * a.N) * sizeof(T));
-  k_gather<T><<<dim3((unsigned)((a.R + 255) / 256), a.N), 256, 0, st>>>(a);
+  k_gather<T><<<(unsigned)((a.R * a.N + 255) / 256), 256, 0, st>>>(a);
   prof_end(st, tk);
 }
 template <typename Td>
@@ -620,7 +648,7 @@ void certify_relax(cudaStream_t st, const CertArgs<Td>& a) {
         reg_check(a.obj_part, chunks(a.d) * a.R * 8.0, "cert part")))
     return;
   int tk = prof_begin(st, "certify_relax_f64", 0.0, bytes);
-  k_certify_relax<Td><<<epi_grid(a.R, a.d), kRowsPerBlock, 0, st>>>(a);
+  k_certify_relax<Td><<<warp_blocks(a.R, a.d), kWarpsPerBlock * 32, 0, st>>>(a);
   prof_end(st, tk);
 }
 template <typename Td>
@@ -633,7 +661,7 @@ void certify_concretize(cudaStream_t st, int64_t R, int K, int N, int d0, const 
         reg_check(obj_part, chunks(d0) * R * 8.0, "cert part")))
     return;
   int tk = prof_begin(st, "certify_conc_f64", 0.0, (double)R * d0 * 12.0);
-  k_certify_conc<Td><<<epi_grid(R, d0), kRowsPerBlock, 0, st>>>(R, K, N, d0, y0, y0abs, gamma_n, x_lo, x_hi,
+  k_certify_conc<Td><<<warp_blocks(R, d0), kWarpsPerBlock * 32, 0, st>>>(R, K, N, d0, y0, y0abs, gamma_n, x_lo, x_hi,
                                                                     gamma, csc, obj_part);
   prof_end(st, tk);
 }
@@ -646,7 +674,7 @@ void certify_finalize(cudaStream_t st, int64_t R, int K, int N, int P, const dou
         reg_check(out, R * 8.0, "cert out")))
     return;
   int tk = prof_begin(st, "certify_final_f64", 0.0, (double)R * (N * sizeof(Td) + P * 8.0 + 8.0));
-  k_certify_final<Td><<<(unsigned)((R + 255) / 256), 256, 0, st>>>(R, K, N, P, C, bL, dL, d, gamma, obj_part, out);
+  k_certify_final<Td><<<row_blocks(R), kWarpsPerBlock * 32, 0, st>>>(R, K, N, P, C, bL, dL, d, gamma, obj_part, out);
   prof_end(st, tk);
 }
 template <typename Ts, typename Td>
