@@ -211,6 +211,39 @@ GCP_API gcp_status gcp_grad_device(gcp_ctx* ctx, void* duals, int32_t prec, cons
                                    const float* beta, const float* gamma, const float* grad_out,
                                    float* g_alpha, float* g_beta, float* g_gamma, void* stream);
 
+/* ------------------------------------------------------- no-allocation bound */
+
+/* The FP32 bound g(alpha) of dense ReLU networks without cuts or splits,
+ * enqueued on `stream` with no device allocation at all. The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory -- work recorded into a CUDA graph under stream capture,
+ * processes that reserve the whole GPU for their own pool up front, loops
+ * that cannot afford cudaMalloc's implicit synchronisation.
+ *
+ * Every argument is the caller's and stays the caller's: dims (host,
+ * d_0..d_L); WT, bias, lo, hi, alpha (host arrays of L-1 device pointers,
+ * entry i-1 for layer i): WT = W^(i) transposed, float [d_{i-1}, d_i];
+ * bias [d_i]; lo/hi the pre-activation bounds of hidden layer i [d_i];
+ * alpha [R, d_i]; x_lo/x_hi [d_0] the input box; y_last [K, d_{L-1}] =
+ * -W^(L)^T c_k and cb [K] = c_k^T b^(L) for the K spec rows; out [R]
+ * receives the bound of row r = s*K + k. All device arrays are float32.
+ *
+ * The chain's scratch (its coefficients, one layer's product and the
+ * objective partials: 3*R*max(d_0..d_{L-1}) + R*sum_i ceil(d_i/32) floats
+ * plus offsets) lives in one 32 MiB device array of the library that every
+ * GPU loading the library holds until the process exits; a batch that needs
+ * more returns GCP_EBUDGET. The first call on each device looks up that
+ * array's address (once, with the device current): make the first call
+ * before any stream capture. Every call uses the same array, so calls whose
+ * work overlaps on the GPU race and corrupt each other's results; serialise
+ * them (one stream, or events). Returns without synchronising; GCP_EINVAL
+ * for bad shapes or a pointer that is not device memory. */
+GCP_API gcp_status gcp_bound_dense_noalloc(int32_t n_layers, const int32_t* dims, const float* const* WT,
+                                           const float* const* bias, const float* const* lo,
+                                           const float* const* hi, const float* const* alpha,
+                                           const float* x_lo, const float* x_hi, const float* y_last,
+                                           const float* cb, int32_t K, int64_t R, float* out, void* stream);
+
 /* --------------------------------------------------------------- profiling */
 
 /* Launch accounting (process-wide, all contexts). Not a step of the paper's

@@ -26,7 +26,7 @@ GCP_PGA, GCP_ADAM = 0, 1
 EXPORTED = ["gcp_create", "gcp_destroy", "gcp_last_error", "gcp_set_stream", "gcp_mem_used", "gcp_init_net",
             "gcp_add_cuts", "gcp_duals_create", "gcp_duals_shape", "gcp_duals_export", "gcp_duals_import",
             "gcp_duals_free", "gcp_bound_batch", "gcp_grad_batch", "gcp_optimize_batch", "gcp_bound_device",
-            "gcp_grad_device", "gcp_profile_start", "gcp_profile_stop", "gcp_profile_query", "gcp_profile_report",
+            "gcp_grad_device", "gcp_bound_dense_noalloc", "gcp_profile_start", "gcp_profile_stop", "gcp_profile_query", "gcp_profile_report",
             "gcp_serve_start", "gcp_serve_submit", "gcp_serve_poll", "gcp_serve_wait",
             "gcp_serve_stop"]
 
@@ -95,6 +95,8 @@ def lib():
             "gcp_optimize_batch": [P, P, C.POINTER(OptParams), pd, pd, pd],
             "gcp_bound_device": [P, P, I32, P, P, P, P, P],
             "gcp_grad_device": [P, P, I32, P, P, P, P, P, P, P, P],
+            "gcp_bound_dense_noalloc": [I32, C.POINTER(I32), C.POINTER(P), C.POINTER(P), C.POINTER(P),
+                                        C.POINTER(P), C.POINTER(P), P, P, P, P, I32, I64, P, P],
             "gcp_profile_start": [C.c_char_p],
             "gcp_profile_stop": [],
             "gcp_profile_query": [C.c_char_p, C.POINTER(I64), pd, pd, pd],
@@ -318,6 +320,26 @@ class Context:
 
     def serve_stop(self):
         self._check(lib().gcp_serve_stop(self.h))
+
+
+def bound_dense_noalloc(dims, WT, bias, lo, hi, alpha, x_lo, x_hi, y_last, cb, K, out, stream: int) -> int:
+    """gcp_bound_dense_noalloc on float32 CUDA tensors; returns the status.
+
+    WT, bias, lo, hi, alpha: lists over hidden layers i = 1..L-1 (entry i-1).
+    """
+    nl = len(dims) - 1
+    dd = (C.c_int32 * len(dims))(*dims)
+
+    def arr(ts):
+        a = (C.c_void_p * max(len(ts), 1))()
+        for q, t in enumerate(ts):
+            a[q] = t.data_ptr()
+        return a
+    R = out.numel()
+    return lib().gcp_bound_dense_noalloc(nl, dd, arr(WT), arr(bias), arr(lo), arr(hi), arr(alpha),
+                                         C.c_void_p(x_lo.data_ptr()), C.c_void_p(x_hi.data_ptr()),
+                                         C.c_void_p(y_last.data_ptr()), C.c_void_p(cb.data_ptr()), K, R,
+                                         C.c_void_p(out.data_ptr()), C.c_void_p(stream))
 
 
 def profile_start(kernel_prefix: Optional[str] = None):
