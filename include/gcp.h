@@ -244,6 +244,17 @@ GCP_API gcp_status gcp_bound_dense_noalloc(int32_t n_layers, const int32_t* dims
                                            const float* x_lo, const float* x_hi, const float* y_last,
                                            const float* cb, int32_t K, int64_t R, float* out, void* stream);
 
+/* ------------------------------------------------------------- self-test */
+
+/* Not a step of the paper's method: runs one GEMM of the chain on the current
+ * device, C[M, N] = A[M, K] * B[N, K]^T (row-major float host arrays, copied
+ * in and out), through kind 0 = tcgen05 bf16 (operands rounded to bfloat16),
+ * 1 = tcgen05 three-pass tf32, 2 = the SIMT float kernel. For tests. Returns
+ * GCP_EINVAL for a shape the kernel does not take (tensor-core kinds need
+ * K % 8 == 0 for bf16, K % 4 == 0 for tf32). */
+GCP_API gcp_status gcp_selftest_gemm(int32_t kind, int64_t M, int32_t N, int32_t K, const float* A, const float* B,
+                                     float* C);
+
 /* --------------------------------------------------------------- profiling */
 
 /* Launch accounting (process-wide, all contexts). Not a step of the paper's

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -94,6 +95,26 @@ static std::vector<float> to_f32(const double* p, size_t n) {
   for (size_t i = 0; i < n; ++i) v[i] = (float)p[i];
   return v;
 }
+// x = hi + lo, hi = x rounded to tf32 (10-bit mantissa) to nearest, ties away
+// from zero; lo = x - hi is exact in float.
+static float tf32_hi_host(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return x;
+  u = (u + 0x1000u) & 0xffffe000u;
+  float h;
+  std::memcpy(&h, &u, 4);
+  return h;
+}
+static void tf32_split(const std::vector<float>& v, std::vector<float>& hi, std::vector<float>& lo) {
+  hi.resize(v.size());
+  lo.resize(v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    hi[i] = tf32_hi_host(v[i]);
+    lo[i] = v[i] - hi[i];
+  }
+}
+
 static std::vector<__nv_bfloat16> to_bf16(const double* p, size_t n) {
   std::vector<__nv_bfloat16> v(n);
   for (size_t i = 0; i < n; ++i) v[i] = __float2bfloat16_rn((float)p[i]);
@@ -141,6 +162,8 @@ gcp_status sync_check(Ctx& c, cudaStream_t st, const char* what) {
   gcp_status s = c.cuda(cudaStreamSynchronize(st), what);
   if (s) return s;
   std::string e = take_device_error(st);
+  if (!e.empty()) return c.fail(GCP_EDEVICE, "%s: %s", what, e.c_str());
+  e = take_tc_error(st);
   if (!e.empty()) return c.fail(GCP_EDEVICE, "%s: %s", what, e.c_str());
   return GCP_OK;
 }
@@ -220,7 +243,7 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
     for (int q = 0; q < g.d_out; ++q)
       if (!std::isfinite(d.b[q])) return c.fail(GCP_EINVAL, "layer %d: non-finite bias", i + 1);
     double *w64, *wt64 = nullptr, *b64;
-    float *w32, *wt32 = nullptr, *b32;
+    float *w32, *wt32 = nullptr, *b32, *w32h = nullptr, *w32l = nullptr, *wt32h = nullptr, *wt32l = nullptr;
     __nv_bfloat16 *w16, *wt16 = nullptr;
     UP(w64, double, d.W, nw);
     auto wf = to_f32(d.W, nw);
@@ -236,6 +259,13 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
       UP(wt32, float, tf.data(), nw);
       auto th = to_bf16(t.data(), nw);
       UP(wt16, __nv_bfloat16, th.data(), nw);
+      std::vector<float> hi, lo;
+      tf32_split(wf, hi, lo);
+      UP(w32h, float, hi.data(), nw);
+      UP(w32l, float, lo.data(), nw);
+      tf32_split(tf, hi, lo);
+      UP(wt32h, float, hi.data(), nw);
+      UP(wt32l, float, lo.data(), nw);
     }
     UP(b64, double, d.b, g.d_out);
     auto bf = to_f32(d.b, g.d_out);
@@ -243,6 +273,7 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
     net->W64.push_back(w64); net->WT64.push_back(wt64); net->b64.push_back(b64);
     net->W32.push_back(w32); net->WT32.push_back(wt32); net->b32.push_back(b32);
     net->W16.push_back(w16); net->WT16.push_back(wt16);
+    net->W32hi.push_back(w32h); net->W32lo.push_back(w32l); net->WT32hi.push_back(wt32h); net->WT32lo.push_back(wt32l);
   }
   UP(net->xlo64, double, x_lo, d0);
   UP(net->xhi64, double, x_hi, d0);
@@ -468,6 +499,10 @@ gcp_status duals_create(Ctx& c, int net_id, int cutset_id, const gcp_subdomains*
   b->R = (int64_t)S * net.K;
   b->M = M;
   b->fp64 = dual_prec == GCP_FP64;
+  {
+    const char* e = std::getenv("GCP_TC");
+    b->tc = !(e && std::strcmp(e, "0") == 0);
+  }
   gcp_status st = build_cutdev(c, net, cs, b->cuts);
   if (st) return st;
   b->N = b->cuts.N;
@@ -593,19 +628,72 @@ int Batch::n_partials() const {
   return p;
 }
 
+// Tensor-core GEMMs per operand type (none for the float64 chain).
+template <typename Top>
+struct TcOps {
+  static bool ok(int) { return false; }
+  static bool bwd(cudaStream_t, const Net&, int, int64_t, const Top*, const float*, float*) { return false; }
+  static bool fwd(cudaStream_t, const Net&, int, int64_t, const Top*, const float*, float*) { return false; }
+};
+template <>
+struct TcOps<float> {
+  static bool ok(int K) { return tc_available(K, false); }
+  static bool bwd(cudaStream_t st, const Net& n, int i, int64_t R, const float* a, const float* alo, float* y) {
+    const LayerGeom& g = n.geom[i - 1];
+    return gemm_tc_tf32x3(st, R, g.d_in, g.d_out, a, alo, n.WT32hi[i - 1], n.WT32lo[i - 1], y);
+  }
+  static bool fwd(cudaStream_t st, const Net& n, int i, int64_t R, const float* a, const float* alo, float* y) {
+    const LayerGeom& g = n.geom[i - 1];
+    return gemm_tc_tf32x3(st, R, g.d_out, g.d_in, a, alo, n.W32hi[i - 1], n.W32lo[i - 1], y);
+  }
+};
+template <>
+struct TcOps<__nv_bfloat16> {
+  static bool ok(int K) { return tc_available(K, true); }
+  static bool bwd(cudaStream_t st, const Net& n, int i, int64_t R, const __nv_bfloat16* a, const float*, float* y) {
+    const LayerGeom& g = n.geom[i - 1];
+    return gemm_tc_bf16(st, R, g.d_in, g.d_out, a, n.WT16[i - 1], y);
+  }
+  static bool fwd(cudaStream_t st, const Net& n, int i, int64_t R, const __nv_bfloat16* a, const float*, float* y) {
+    const LayerGeom& g = n.geom[i - 1];
+    return gemm_tc_bf16(st, R, g.d_out, g.d_in, a, n.W16[i - 1], y);
+  }
+};
+
+// Does the backward product through W^(i) (K = d_i) / the forward product
+// through W^(i) (K = d_{i-1}) run on the tensor cores?
+template <typename Top>
+static bool tc_bwd(const Batch& b, int i) {
+  const Net& n = *b.net;
+  return b.tc && n.geom[i - 1].kind == GCP_DENSE && TcOps<Top>::ok(n.dims[i]);
+}
+template <typename Top>
+static bool tc_fwd(const Batch& b, int i) {
+  const Net& n = *b.net;
+  return b.tc && i < n.L && n.geom[i - 1].kind == GCP_DENSE && TcOps<Top>::ok(n.dims[i - 1]);
+}
+
 // Linear backward step y^(i-1) = W^(i)^T nu^(i) for all rows.
 template <typename Top, typename T>
-static void lin_backward(cudaStream_t st, const Net& net, int i, int64_t R, const Top* nu, T* y) {
+static void lin_backward(cudaStream_t st, const Batch& b, int i, const Top* nu, const float* nu_lo, T* y) {
+  const Net& net = *b.net;
   const LayerGeom& g = net.geom[i - 1];
-  if (g.kind == GCP_DENSE) gemm_nt<Top, T>(st, R, g.d_in, g.d_out, nu, 0, WSel<Top>::WT(net, i), y);
-  else conv_T<Top, T>(st, R, g, WSel<Top>::W(net, i), nu, y);
+  if constexpr (!std::is_same<T, double>::value) {
+    if (tc_bwd<Top>(b, i) && TcOps<Top>::bwd(st, net, i, b.R, nu, nu_lo, y)) return;
+  }
+  if (g.kind == GCP_DENSE) gemm_nt<Top, T>(st, b.R, g.d_in, g.d_out, nu, 0, WSel<Top>::WT(net, i), y);
+  else conv_T<Top, T>(st, b.R, g, WSel<Top>::W(net, i), nu, y);
 }
 // Linear forward step nubar^(i) = W^(i) a for all rows.
 template <typename Top, typename T>
-static void lin_forward(cudaStream_t st, const Net& net, int i, int64_t R, const Top* a, T* out) {
+static void lin_forward(cudaStream_t st, const Batch& b, int i, const Top* a, const float* a_lo, T* out) {
+  const Net& net = *b.net;
   const LayerGeom& g = net.geom[i - 1];
-  if (g.kind == GCP_DENSE) gemm_nt<Top, T>(st, R, g.d_out, g.d_in, a, 0, WSel<Top>::W(net, i), out);
-  else conv_fwd<Top, T>(st, R, g, WSel<Top>::W(net, i), a, out);
+  if constexpr (!std::is_same<T, double>::value) {
+    if (tc_fwd<Top>(b, i) && TcOps<Top>::fwd(st, net, i, b.R, a, a_lo, out)) return;
+  }
+  if (g.kind == GCP_DENSE) gemm_nt<Top, T>(st, b.R, g.d_out, g.d_in, a, 0, WSel<Top>::W(net, i), out);
+  else conv_fwd<Top, T>(st, b.R, g, WSel<Top>::W(net, i), a, out);
 }
 
 // Evaluate g for all rows at the batch's duals. with_adjoint_start: also write
@@ -624,6 +712,12 @@ gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, 
   if (!part) return s;
   T* g = (T*)b.ws("g", (size_t)std::max<int64_t>(R, 1) * sizeof(T), &s);
   if (!g) return s;
+  const bool split = std::is_same<Top, float>::value && std::is_same<T, float>::value;
+  float* lo = nullptr;
+  if (split && b.tc) {
+    lo = (float*)b.ws("nu_lo", (size_t)R * b.dmax() * 4, &s);
+    if (!lo) return s;
+  }
   T* E = nullptr;
   if (with_adjoint_start && b.nnz) {
     E = (T*)b.ws("E", (size_t)b.nnz * R * sizeof(T), &s);
@@ -645,11 +739,12 @@ gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, 
     a.sp = sp;
     a.csc = csc_of<T>(b, i);
     a.nu_out = nu;
+    a.nu_lo = (lo && tc_bwd<Top>(b, i)) ? lo : nullptr;
     a.nuhat_out = nuhat;
     a.obj_part = part + (int64_t)poff * R;
     relax_eval<T, Top>(st, a);
     poff += (net.dims[i] + kChunk - 1) / kChunk;
-    lin_backward<Top, T>(st, net, i, R, nu, y);
+    lin_backward<Top, T>(st, b, i, nu, a.nu_lo, y);
   }
   ConcArgs<T, Top> ca{};
   ca.R = R; ca.K = b.K; ca.d0 = net.dims[0]; ca.N = b.N;
@@ -659,6 +754,7 @@ gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, 
   ca.seed = seed;
   ca.csc = csc_of<T>(b, 0);
   ca.a0_out = with_adjoint_start ? nu : nullptr;
+  ca.a0_lo = (with_adjoint_start && lo && tc_fwd<Top>(b, 1)) ? lo : nullptr;
   ca.E = E;
   ca.obj_part = part + (int64_t)poff * R;
   concretize<T, Top>(st, ca);
@@ -681,6 +777,12 @@ gcp_status run_adjoint(Ctx& c, Batch& b, cudaStream_t st, const StepArgs<T>& ste
   if (!abuf || !y) return s;
   T* E = b.nnz ? (T*)b.ws("E", (size_t)b.nnz * R * sizeof(T), &s) : nullptr;
   if (b.nnz && !E) return s;
+  const bool split = std::is_same<Top, float>::value && std::is_same<T, float>::value;
+  float* lo = nullptr;
+  if (split && b.tc) {
+    lo = (float*)b.ws("nu_lo", (size_t)R * b.dmax() * 4, &s);
+    if (!lo) return s;
+  }
   T *ma = nullptr, *va = nullptr, *mb = nullptr, *vb = nullptr, *mg = nullptr, *vg = nullptr;
   int64_t nal = 0;
   for (int i = 1; i < L; ++i) nal += (int64_t)R * net.dims[i];
@@ -701,7 +803,7 @@ gcp_status run_adjoint(Ctx& c, Batch& b, cudaStream_t st, const StepArgs<T>& ste
   SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp};
   int64_t aoff = 0;
   for (int i = 1; i < L; ++i) {
-    lin_forward<Top, T>(st, net, i, R, abuf, y);
+    lin_forward<Top, T>(st, b, i, abuf, (lo && tc_fwd<Top>(b, i)) ? lo : nullptr, y);
     const T* nuhat = (const T*)b.lazy["nuhat" + std::to_string(i)];
     AdjArgs<T, Top> a{};
     a.R = R; a.K = b.K; a.d = net.dims[i]; a.layer = i; a.M = b.M; a.N = b.N;
@@ -714,6 +816,7 @@ gcp_status run_adjoint(Ctx& c, Batch& b, cudaStream_t st, const StepArgs<T>& ste
     a.sp = sp;
     a.csc = csc_of<T>(b, i);
     a.a_out = (i < L - 1) ? abuf : nullptr;
+    a.a_lo = (lo && i < L - 1 && tc_fwd<Top>(b, i + 1)) ? lo : nullptr;
     a.E = E;
     a.g_alpha = gal ? gal + aoff : nullptr;
     a.g_beta = gbe;

@@ -25,6 +25,7 @@ struct Net {
   std::vector<double*> W64, WT64, b64;
   std::vector<float*> W32, WT32, b32;
   std::vector<__nv_bfloat16*> W16, WT16;
+  std::vector<float*> W32hi, W32lo, WT32hi, WT32lo;  // tf32 split of the dense weights
   double *xlo64 = nullptr, *xhi64 = nullptr;
   float *xlo32 = nullptr, *xhi32 = nullptr;
   double *C64 = nullptr, *negC64 = nullptr, *bL64 = nullptr;
@@ -73,6 +74,7 @@ struct Batch {
   int S = 0, K = 0, M = 0, N = 0;
   int64_t R = 0, nnz = 0, nsp = 0;
   bool fp64 = false;
+  bool tc = true;                    // use the tcgen05 GEMMs where shapes allow
   CutDev cuts;
   int32_t* sp_ptr = nullptr;
   int16_t* sp_layer = nullptr;

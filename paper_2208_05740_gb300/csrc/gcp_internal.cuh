@@ -75,7 +75,8 @@ struct RelaxArgs {
   const T* gamma;       // [R, N]
   SplitsDev sp;
   CutCSC<T> csc;
-  Top* nu_out;          // [R, d]
+  Top* nu_out;          // [R, d]   (tf32-rounded high part when nu_lo is set)
+  float* nu_lo;         // [R, d]   low part nu - nu_out for the 3-pass tf32 GEMM, or nullptr
   T* nuhat_out;         // [R, d]
   T* obj_part;          // [ceil(d/kChunk), R]
 };
@@ -97,6 +98,7 @@ struct AdjArgs {
   SplitsDev sp;
   CutCSC<T> csc;
   Top* a_out;           // [R, d] dg/dnuhat (nullptr for the last hidden layer)
+  float* a_lo;          // low part for the 3-pass tf32 GEMM, or nullptr
   T* E;                 // [R, nnz]
   T* g_alpha;           // [R, d]  (mode 0)
   T* g_beta;            // [R, M]  (mode 0)
@@ -116,6 +118,7 @@ struct ConcArgs {
   const T* seed;
   CutCSC<T> csc;        // layer 0 entries (kind X only)
   Top* a0_out;          // [R, d0] = -seed * x*  (start of the reverse pass)
+  float* a0_lo;         // low part for the 3-pass tf32 GEMM, or nullptr
   T* E;
   T* obj_part;          // [ceil(d0/kChunk), R]
 };
@@ -199,6 +202,13 @@ template <typename Tin, typename Tacc>
 void conv_T(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const Tin* in, Tacc* out);
 void conv_T_abs(cudaStream_t st, int64_t R, const LayerGeom& g, const double* W, const double* in, double* out,
                 float* outabs);
+
+// tcgen05 GEMMs (k_tc.cu); false = shape or driver not supported, use SIMT
+bool tc_available(int K, bool bf16);
+bool gemm_tc_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C);
+bool gemm_tc_tf32x3(cudaStream_t st, int64_t M, int N, int K, const float* A, const float* Alo, const float* B,
+                    const float* Blo, float* C);
+std::string take_tc_error(cudaStream_t st);
 
 template <typename T, typename Top>
 void relax_eval(cudaStream_t st, const RelaxArgs<T, Top>& a);

@@ -8,6 +8,7 @@
 // are reduced across the warp in a fixed shuffle order and written per neuron
 // chunk, then summed in a fixed order (deterministic results).
 #include <cstdio>
+#include <type_traits>
 
 #include "gcp_internal.cuh"
 
@@ -58,6 +59,28 @@ template <typename Top, typename T>
 __device__ __forceinline__ Top cvt_out(T v) { return static_cast<Top>(v); }
 template <>
 __device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
+
+// x = hi + lo with hi = x rounded to tf32 (nearest, ties away) and lo exact.
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t h;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  return __uint_as_float(h);
+}
+
+// Store an operand of the next GEMM, split into tf32 high and low parts when
+// the 3-pass tf32 GEMM consumes it.
+template <typename Top, typename T>
+__device__ __forceinline__ void put_operand(Top* hi, float* lo, int64_t i, T v) {
+  if constexpr (std::is_same<Top, float>::value) {
+    if (lo) {
+      const float h = tf32_hi(v);
+      hi[i] = h;
+      lo[i] = v - h;
+      return;
+    }
+  }
+  hi[i] = cvt_out<Top>(v);
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -154,7 +177,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_eval(RelaxArgs<T,
       nu = pi - tau - t;
     }
     term -= nu * a.bias[j];
-    a.nu_out[r * a.d + j] = cvt_out<Top>(nu);
+    put_operand<Top>(a.nu_out, a.nu_lo, r * a.d + j, nu);
     a.nuhat_out[r * a.d + j] = nh;
   }
   term = warp_sum(term);
@@ -219,7 +242,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_adj(AdjArgs<T, To
   const T dg_dnh = nb * dnu_dnh + dh_dnh;
   const T dg_ds = nb * dnu_ds + dh_ds;
   const T dg_dt = -nb;
-  if (a.a_out) a.a_out[ij] = cvt_out<Top>(dg_dnh);
+  if (a.a_out) put_operand<Top>(a.a_out, a.a_lo, ij, dg_dnh);
   int e0, e1;
   csc_range(a.csc, j, e0, e1);
   for (int e = e0; e < e1; ++e) {
@@ -265,7 +288,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_concretize(ConcArgs<T, 
     const T xl = a.x_lo[j], xh = a.x_hi[j];
     term = tmin(c0 * xl, c0 * xh);
     const T xs = c0 > T(0) ? xl : (c0 < T(0) ? xh : T(0.5) * (xl + xh));
-    if (a.a0_out) a.a0_out[r * a.d0 + j] = cvt_out<Top>(-w * xs);
+    if (a.a0_out) put_operand<Top>(a.a0_out, a.a0_lo, r * a.d0 + j, -w * xs);
     if (a.E)
       for (int e = e0; e < e1; ++e) {
         const int row = a.csc.eid[e];
@@ -555,6 +578,7 @@ void relax_eval(cudaStream_t st, const RelaxArgs<T, Top>& a) {
         reg_check(a.alpha, Rd * tb, "alpha") & reg_check(a.beta, (double)a.M * a.R * tb, "beta") &
         reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") & chk_splits(a.sp, a.R, a.K) &
         chk_csc(a.csc, a.d) & reg_check(a.nu_out, Rd * sizeof(Top), "nu out") &
+        reg_check(a.nu_lo, a.nu_lo ? Rd * 4.0 : 0.0, "nu lo") &
         reg_check(a.nuhat_out, Rd * tb, "nuhat out") & reg_check(a.obj_part, chunks(a.d) * a.R * tb, "obj part")))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
@@ -576,6 +600,7 @@ void relax_adjoint(cudaStream_t st, const AdjArgs<T, Top>& a) {
         reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") &
         reg_check(a.nuhat, Rd * tb, "nuhat") & chk_splits(a.sp, a.R, a.K) & chk_csc(a.csc, a.d) &
         reg_check(a.a_out, a.a_out ? Rd * sizeof(Top) : 0.0, "a out") &
+        reg_check(a.a_lo, (a.a_out && a.a_lo) ? Rd * 4.0 : 0.0, "a lo") &
         reg_check(a.E, a.csc.n_entries ? (double)a.csc.n_total * a.R * tb : 0.0, "E") &
         reg_check(a.g_alpha, m0 ? Rd * tb : 0.0, "g_alpha") &
         reg_check(a.g_beta, m0 ? (double)a.M * a.R * tb : 0.0, "g_beta") &
@@ -599,6 +624,7 @@ void concretize(cudaStream_t st, const ConcArgs<T, Top>& a) {
         reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") &
         reg_check(a.seed, a.seed ? a.R * tb : 0.0, "seed") & chk_csc(a.csc, a.d0) &
         reg_check(a.a0_out, a.a0_out ? Rd * sizeof(Top) : 0.0, "a0 out") &
+        reg_check(a.a0_lo, (a.a0_out && a.a0_lo) ? Rd * 4.0 : 0.0, "a0 lo") &
         reg_check(a.E, (a.E && a.csc.n_entries) ? (double)a.csc.n_total * a.R * tb : 0.0, "E") &
         reg_check(a.obj_part, chunks(a.d0) * a.R * tb, "obj part")))
     return;

@@ -26,7 +26,7 @@ GCP_PGA, GCP_ADAM = 0, 1
 EXPORTED = ["gcp_create", "gcp_destroy", "gcp_last_error", "gcp_set_stream", "gcp_mem_used", "gcp_init_net",
             "gcp_add_cuts", "gcp_duals_create", "gcp_duals_shape", "gcp_duals_export", "gcp_duals_import",
             "gcp_duals_free", "gcp_bound_batch", "gcp_grad_batch", "gcp_optimize_batch", "gcp_bound_device",
-            "gcp_grad_device", "gcp_bound_dense_noalloc", "gcp_profile_start", "gcp_profile_stop", "gcp_profile_query", "gcp_profile_report",
+            "gcp_grad_device", "gcp_bound_dense_noalloc", "gcp_selftest_gemm", "gcp_profile_start", "gcp_profile_stop", "gcp_profile_query", "gcp_profile_report",
             "gcp_serve_start", "gcp_serve_submit", "gcp_serve_poll", "gcp_serve_wait",
             "gcp_serve_stop"]
 
@@ -97,6 +97,8 @@ def lib():
             "gcp_grad_device": [P, P, I32, P, P, P, P, P, P, P, P],
             "gcp_bound_dense_noalloc": [I32, C.POINTER(I32), C.POINTER(P), C.POINTER(P), C.POINTER(P),
                                         C.POINTER(P), C.POINTER(P), P, P, P, P, I32, I64, P, P],
+            "gcp_selftest_gemm": [I32, I64, I32, I32, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                  C.POINTER(C.c_float)],
             "gcp_profile_start": [C.c_char_p],
             "gcp_profile_stop": [],
             "gcp_profile_query": [C.c_char_p, C.POINTER(I64), pd, pd, pd],
@@ -340,6 +342,19 @@ def bound_dense_noalloc(dims, WT, bias, lo, hi, alpha, x_lo, x_hi, y_last, cb, K
                                          C.c_void_p(x_lo.data_ptr()), C.c_void_p(x_hi.data_ptr()),
                                          C.c_void_p(y_last.data_ptr()), C.c_void_p(cb.data_ptr()), K, R,
                                          C.c_void_p(out.data_ptr()), C.c_void_p(stream))
+
+
+def selftest_gemm(kind: int, A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """C = A @ B.T through kind 0 (tcgen05 bf16), 1 (tcgen05 3xtf32) or 2 (SIMT fp32)."""
+    A = _c(A, np.float32)
+    B = _c(B, np.float32)
+    M, K = A.shape
+    N = B.shape[0]
+    out = np.zeros((M, N), np.float32)
+    st = lib().gcp_selftest_gemm(kind, M, N, K, _ptr(A, C.c_float), _ptr(B, C.c_float), _ptr(out, C.c_float))
+    if st != GCP_OK:
+        raise GCPError(st, "selftest gemm failed")
+    return out
 
 
 def profile_start(kernel_prefix: Optional[str] = None):
