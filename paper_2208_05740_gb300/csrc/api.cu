@@ -319,6 +319,17 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
     UP(lof, float, a.data(), di);
     UP(hif, float, b.data(), di);
     net->lo64.push_back(lo); net->hi64.push_back(hi); net->lo32.push_back(lof); net->hi32.push_back(hif);
+    std::vector<double> iv(di, 0.0);
+    std::vector<float> ivf(di, 0.f);
+    for (int j = 0; j < di; ++j) {
+      if (inter_lo[off + j] < 0 && inter_hi[off + j] > 0) iv[j] = 1.0 / (inter_hi[off + j] - inter_lo[off + j]);
+      if (a[j] < 0.f && b[j] > 0.f) ivf[j] = 1.f / (b[j] - a[j]);
+    }
+    double* ivd;
+    float* ivs;
+    UP(ivd, double, iv.data(), di);
+    UP(ivs, float, ivf.data(), di);
+    net->invul64.push_back(ivd); net->invul32.push_back(ivs);
     off += di;
   }
 #undef UP
@@ -402,7 +413,7 @@ gcp_status build_cutdev(Ctx& c, const Net& net, const CutSet* cs, CutDev& out) {
       if (cs->layer[a] != cs->layer[b]) return cs->layer[a] < cs->layer[b];
       return cs->index[a] < cs->index[b];
     });
-  std::vector<int32_t> cptr(poff[L], 0), ccut(out.nnz), ceid(out.nnz);
+  std::vector<int32_t> cptr(poff[L], 0), ccut(out.nnz), ceid(out.nnz), cnrn(out.nnz), cpos(out.nnz);
   std::vector<int8_t> ckind(out.nnz);
   std::vector<double> ccoef(out.nnz);
   std::vector<int64_t> cnt(poff[L], 0);
@@ -425,6 +436,8 @@ gcp_status build_cutdev(Ctx& c, const Net& net, const CutSet* cs, CutDev& out) {
     ckind[q] = cs->kind[e];
     ccoef[q] = cs->coef[e];
     ceid[q] = (int32_t)e;
+    cnrn[q] = cs->index[e];
+    cpos[e] = (int32_t)q;
   }
   std::vector<int32_t> cp32(out.N + 1, 0);
   for (int k = 0; k <= out.N; ++k) cp32[k] = (int32_t)(cs ? cs->ptr[k] : 0);
@@ -447,6 +460,8 @@ gcp_status build_cutdev(Ctx& c, const Net& net, const CutSet* cs, CutDev& out) {
   auto cf = to_f32(ccoef.data(), ccoef.size());
   UPC(out.csc_coef32, float, cf.data(), cf.size());
   UPC(out.csc_eid, int32_t, ceid.data(), ceid.size());
+  UPC(out.csc_nrn, int32_t, cnrn.data(), cnrn.size());
+  UPC(out.csr_pos, int32_t, cpos.data(), cpos.size());
 #undef UPC
   return GCP_OK;
 }
@@ -572,6 +587,7 @@ template <>
 struct TSel<double> {
   static const double* lo(const Net& n, int i) { return n.lo64[i - 1]; }
   static const double* hi(const Net& n, int i) { return n.hi64[i - 1]; }
+  static const double* inv(const Net& n, int i) { return n.invul64[i - 1]; }
   static const double* b(const Net& n, int i) { return n.b64[i - 1]; }
   static const double* xlo(const Net& n) { return n.xlo64; }
   static const double* xhi(const Net& n) { return n.xhi64; }
@@ -584,6 +600,7 @@ template <>
 struct TSel<float> {
   static const float* lo(const Net& n, int i) { return n.lo32[i - 1]; }
   static const float* hi(const Net& n, int i) { return n.hi32[i - 1]; }
+  static const float* inv(const Net& n, int i) { return n.invul32[i - 1]; }
   static const float* b(const Net& n, int i) { return n.b32[i - 1]; }
   static const float* xlo(const Net& n) { return n.xlo32; }
   static const float* xhi(const Net& n) { return n.xhi32; }
@@ -613,7 +630,7 @@ struct WSel<__nv_bfloat16> {
 template <typename T>
 CutCSC<T> csc_of(const Batch& b, int layer) {
   const CutDev& c = b.cuts;
-  return CutCSC<T>{c.csc_ptr + c.poff[layer], c.csc_cut, c.csc_kind, TSel<T>::coef(c), c.csc_eid,
+  return CutCSC<T>{c.csc_ptr + c.poff[layer], c.csc_cut, c.csc_kind, TSel<T>::coef(c), c.csc_eid, c.csc_nrn,
                    c.layer_nnz.empty() ? 0 : c.layer_nnz[layer], c.nnz};
 }
 
@@ -733,6 +750,7 @@ gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, 
     a.y = (i == L - 1) ? TSel<T>::YL(net) : y;
     a.y_per_spec = (i == L - 1);
     a.lo = TSel<T>::lo(net, i); a.hi = TSel<T>::hi(net, i); a.bias = TSel<T>::b(net, i);
+    a.inv_ul = TSel<T>::inv(net, i);
     a.alpha = (const T*)b.alpha[i - 1];
     a.beta = (const T*)b.beta;
     a.gamma = (const T*)b.gamma;
@@ -809,6 +827,7 @@ gcp_status run_adjoint(Ctx& c, Batch& b, cudaStream_t st, const StepArgs<T>& ste
     a.R = R; a.K = b.K; a.d = net.dims[i]; a.layer = i; a.M = b.M; a.N = b.N;
     a.nubar = y; a.seed = seed;
     a.lo = TSel<T>::lo(net, i); a.hi = TSel<T>::hi(net, i); a.bias = TSel<T>::b(net, i);
+    a.inv_ul = TSel<T>::inv(net, i);
     a.alpha = (T*)b.alpha[i - 1];
     a.beta = (T*)b.beta;
     a.gamma = (const T*)b.gamma;
@@ -826,7 +845,8 @@ gcp_status run_adjoint(Ctx& c, Batch& b, cudaStream_t st, const StepArgs<T>& ste
     aoff += (int64_t)R * net.dims[i];
   }
   if (b.N > 0) {
-    GatherArgs<T> ga{R, b.N, b.cuts.cut_ptr, E, TSel<T>::d(b.cuts), seed, (T*)b.gamma, gga, mg, vg, step, b.nnz};
+    GatherArgs<T> ga{R, b.N, b.cuts.cut_ptr, b.cuts.csr_pos, E, TSel<T>::d(b.cuts), seed, (T*)b.gamma, gga, mg, vg,
+                     step, b.nnz};
     gather_gamma<T>(st, ga);
   }
   return launch_status(c, "adjoint");
@@ -868,8 +888,8 @@ gcp_status run_certify(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
     if (g.kind == GCP_DENSE) gemm_nt_abs(st, R, g.d_in, g.d_out, nu, 0, net.WT64[i - 1], y, ya);
     else conv_T_abs(st, R, g, net.W64[i - 1], nu, y, ya);
   }
-  certify_concretize<Td>(st, R, b.K, b.N, net.dims[0], y, ya, gamma_n_host(red_len(net.geom[0])), net.xlo64, net.xhi64,
-                         (const Td*)b.gamma, csc_of<double>(b, 0), part + (int64_t)poff * R);
+  certify_concretize<Td>(st, R, b.K, b.N, net.dims[0], y, ya, gamma_n_host(red_len(net.geom[0])), net.xlo64,
+                         net.xhi64, (const Td*)b.gamma, csc_of<double>(b, 0), part + (int64_t)poff * R);
   poff += (net.dims[0] + kChunk - 1) / kChunk;
   certify_finalize<Td>(st, R, b.K, b.N, poff, net.C64, net.bL64, net.dims[L], b.cuts.d64, (const Td*)b.gamma, part,
                        out_dev);

@@ -35,6 +35,8 @@ struct Net {
   float* cb32 = nullptr;
   std::vector<double*> lo64, hi64;   // hidden layer i at index i-1
   std::vector<float*> lo32, hi32;    // rounded outwards
+  std::vector<double*> invul64;      // 1 / (hi - lo) where lo < 0 < hi, else 0
+  std::vector<float*> invul32;
   std::vector<void*> owned;
   ~Net();
 };
@@ -61,6 +63,8 @@ struct CutDev {
   double* csc_coef64 = nullptr;
   float* csc_coef32 = nullptr;
   int32_t* csc_eid = nullptr;
+  int32_t* csc_nrn = nullptr;
+  int32_t* csr_pos = nullptr;        // CSC position of each CSR entry
   std::vector<int64_t> poff;         // segment start of layer i in csc_ptr
   std::vector<int64_t> layer_nnz;    // entries per layer
   std::vector<void*> owned;

@@ -24,7 +24,7 @@
 namespace gcp {
 
 constexpr int kMaxSplits = 64;     // per subdomain (validated on the host)
-constexpr int kChunk = 32;         // neurons per epilogue block column
+constexpr int kChunk = 32;         // neurons per warp step of the per-neuron kernels
 
 struct LayerGeom {
   int kind, d_in, d_out;
@@ -39,6 +39,7 @@ struct CutCSC {
   const int8_t* kind;   // GCP_VAR_*
   const T* coef;
   const int32_t* eid;   // row of E written for this entry
+  const int32_t* nrn;   // neuron index of the entry within its layer
   int64_t n_entries;    // entries of this layer (host-side accounting only)
   int64_t n_total;      // entries of all layers (host-side validation only)
 };
@@ -69,6 +70,7 @@ struct RelaxArgs {
   int y_per_spec;
   const T* lo;          // root bounds [d]
   const T* hi;
+  const T* inv_ul;      // 1 / (hi - lo) of root-unstable neurons [d]
   const T* bias;        // b^(layer) [d]
   const T* alpha;       // [R, d]
   const T* beta;        // [R, M]
@@ -78,7 +80,7 @@ struct RelaxArgs {
   Top* nu_out;          // [R, d]   (tf32-rounded high part when nu_lo is set)
   float* nu_lo;         // [R, d]   low part nu - nu_out for the 3-pass tf32 GEMM, or nullptr
   T* nuhat_out;         // [R, d]
-  T* obj_part;          // [ceil(d/kChunk), R]
+  T* obj_part;          // [ceil(d/32), R]: one partial per row and neuron chunk
 };
 
 template <typename T, typename Top>
@@ -90,6 +92,7 @@ struct AdjArgs {
   const T* seed;        // per-row seed of the reverse pass, nullptr = 1
   const T* lo;
   const T* hi;
+  const T* inv_ul;      // 1 / (hi - lo) of root-unstable neurons [d]
   const T* bias;
   T* alpha;             // [R, d], updated in place when mode != 0
   T* beta;              // [R, M], updated in place when mode != 0
@@ -99,7 +102,7 @@ struct AdjArgs {
   CutCSC<T> csc;
   Top* a_out;           // [R, d] dg/dnuhat (nullptr for the last hidden layer)
   float* a_lo;          // low part for the 3-pass tf32 GEMM, or nullptr
-  T* E;                 // [R, nnz]
+  T* E;                 // [R, nnz], entries in CSC order
   T* g_alpha;           // [R, d]  (mode 0)
   T* g_beta;            // [R, M]  (mode 0)
   T* m_alpha; T* v_alpha; T* m_beta; T* v_beta;  // Adam state (mode 2)
@@ -120,7 +123,7 @@ struct ConcArgs {
   Top* a0_out;          // [R, d0] = -seed * x*  (start of the reverse pass)
   float* a0_lo;         // low part for the 3-pass tf32 GEMM, or nullptr
   T* E;
-  T* obj_part;          // [ceil(d0/kChunk), R]
+  T* obj_part;          // [ceil(d0/32), R]
 };
 
 template <typename T>
@@ -138,7 +141,8 @@ template <typename T>
 struct GatherArgs {
   int64_t R;
   int N;
-  const int32_t* cut_ptr;  // [N+1]
+  const int32_t* cut_ptr;  // [N+1] CSR by cut
+  const int32_t* pos;      // [nnz] CSC position (column of E) of each CSR entry
   const T* E;
   const T* d;
   const T* seed;
@@ -168,7 +172,7 @@ struct CertArgs {
   SplitsDev sp;
   CutCSC<double> csc;
   double* nu_out;        // [R, d]
-  double* obj_part;      // [ceil(d/kChunk), R] rounded-down partial sums
+  double* obj_part;      // [ceil(d/32), R] rounded-down partial sums
 };
 
 // ---------------------------------------------------------------- launch validation

@@ -29,17 +29,6 @@ __device__ __noinline__ void dev_error(unsigned long long code, long long idx, l
   }
 }
 
-// entry range of neuron j, checked against the entry count
-template <typename T>
-__device__ __forceinline__ void csc_range(const CutCSC<T>& c, int j, int& e0, int& e1) {
-  e0 = c.ptr[j];
-  e1 = c.ptr[j + 1];
-  if (e0 < 0 || e1 < e0 || (int64_t)e1 > c.n_total) {
-    dev_error(1, j, c.n_total);
-    e0 = e1 = 0;
-  }
-}
-
 // split entries of subdomain s, checked against the entry count and slots
 __device__ __forceinline__ void split_range(const SplitsDev& sp, int s, int M, int& q0, int& q1) {
   q0 = sp.ptr[s];
@@ -94,39 +83,184 @@ __device__ __forceinline__ double warp_sum_rd(double v) {
   return v;
 }
 
-// Warp coordinates: (row r, neuron chunk c, neuron j = 32c + lane). Returns
-// false for warps past the end (the whole warp leaves together).
-struct WarpPos {
-  int64_t r;
-  int c, j, lane;
+// Warp coordinates: a warp owns one 32-neuron chunk c of a layer (lane =
+// neuron j = 32c + lane) and one subdomain s, i.e. the K spec rows
+// r = sK .. sK+K-1. Everything that does not depend on the row (bounds,
+// split hits, the chunk's cut entries) is loaded once per warp; each row then
+// costs one round of independent loads.
+struct ChunkWarp {
+  int s, c, lane, j;
   bool on;
 };
-__device__ __forceinline__ bool warp_pos(int64_t R, int d, WarpPos& p) {
-  const int nch = (d + 31) >> 5;
-  const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  if (w >= R * nch) return false;
-  p.r = w / nch;
-  p.c = (int)(w - p.r * nch);
-  p.lane = threadIdx.x & 31;
-  p.j = p.c * 32 + p.lane;
-  p.on = p.j < d;
-  return true;
+__device__ __forceinline__ bool chunk_warp(int S, int d, ChunkWarp& w) {
+  w.s = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  w.c = blockIdx.y;
+  w.lane = threadIdx.x & 31;
+  w.j = w.c * 32 + w.lane;
+  w.on = w.j < d;
+  return w.s < S;
 }
 
-// Sparse cut sums for neuron j of row r: t = H^T gamma, g = G^T gamma, s = Q^T gamma.
+// The split (if any) of subdomain s on neuron j of `layer`: slot and sign.
+// Lane q of the warp inspects split q (and 32 + q) of the subdomain.
+__device__ __forceinline__ int lane_split(const SplitsDev& sp, int s, int M, int layer, int c, int lane, int& sign) {
+  int q0, q1;
+  split_range(sp, s, M, q0, q1);
+  int slot = -1;
+  sign = 0;
+  for (int base = 0; base < q1 - q0; base += 32) {
+    const int q = q0 + base + lane;
+    int lay = -1, idx = -1, sg = 0;
+    if (q < q1) {
+      lay = sp.layer[q];
+      idx = sp.index[q];
+      sg = sp.sign[q];
+    }
+    unsigned m = __ballot_sync(0xffffffffu, lay == layer && (idx >> 5) == c);
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      const int tj = __shfl_sync(0xffffffffu, idx, b) & 31;
+      const int tsg = __shfl_sync(0xffffffffu, sg, b);
+      if (tj == lane) { slot = base + b; sign = tsg; }
+    }
+  }
+  return slot;
+}
+
+// Cut entries of the chunk: entries of its neurons are contiguous in CSC
+// order. For one batch of up to 32 entries lane q holds entry cb + q; neuron
+// lanes collect their own entries with shuffles.
+template <typename T>
+struct ChunkCuts {
+  int e0, e1;       // this lane's neuron entries
+  int cb, ce;       // the chunk's entries (warp-uniform)
+  int cut, kind, nrn_lane;  // entry cb + lane of the first batch
+  T coef;
+};
+template <typename T>
+__device__ __forceinline__ void chunk_cuts(const CutCSC<T>& c, int N, int d, int ch, int lane, ChunkCuts<T>& cc) {
+  const int j = ch * 32 + lane;
+  const int jl = j < d ? j : d, jh = j + 1 < d ? j + 1 : d;
+  cc.e0 = __ldg(c.ptr + jl);
+  cc.e1 = __ldg(c.ptr + jh);
+  cc.cb = __shfl_sync(0xffffffffu, cc.e0, 0);
+  cc.ce = __shfl_sync(0xffffffffu, cc.e1, 31);
+  const bool bad = cc.e0 < cc.cb || cc.e1 < cc.e0 || cc.e1 > cc.ce;
+  if (__any_sync(0xffffffffu, bad) || cc.cb < 0 || cc.ce < cc.cb || (int64_t)cc.ce > c.n_total) {
+    if (lane == 0) dev_error(1, ch, c.n_total);
+    cc.e0 = cc.e1 = cc.cb = cc.ce = 0;
+  }
+  cc.cut = -1; cc.kind = -1; cc.nrn_lane = 0; cc.coef = T(0);
+  const int e = cc.cb + lane;
+  if (e < cc.ce && lane < 32) {
+    cc.cut = __ldg(c.cut + e);
+    cc.kind = __ldg(c.kind + e);
+    cc.nrn_lane = (__ldg(c.nrn + e) - ch * 32) & 31;
+    cc.coef = __ldg(c.coef + e);
+    if (cc.cut < 0 || cc.cut >= N) { dev_error(2, e, N); cc.cut = -1; cc.kind = -1; }
+  }
+}
+
+// Entry values coef * gamma[cut] of one batch for row grow, summed per
+// neuron lane into t (x), g (xhat), s (z). Batches past the first reload
+// their entries (chunks with more than 32 entries).
 template <typename T, typename Tg>
-__device__ __forceinline__ void cut_sums(const CutCSC<T>& c, const Tg* grow, int N, int j, T& t, T& g, T& s) {
+__device__ __forceinline__ void cut_sums_row(const CutCSC<T>& c, const ChunkCuts<T>& cc, const Tg* grow, int N,
+                                             int ch, int lane, T& t, T& g, T& s) {
   t = T(0); g = T(0); s = T(0);
-  int e0, e1;
-  csc_range(c, j, e0, e1);
-  for (int e = e0; e < e1; ++e) {
-    const int k = c.cut[e];
-    if (k < 0 || k >= N) { dev_error(2, e, N); continue; }
-    const T v = c.coef[e] * (T)grow[k];
-    const int kd = c.kind[e];
-    if (kd == GCP_VAR_X) t += v;
-    else if (kd == GCP_VAR_XHAT) g += v;
-    else s += v;
+  for (int b0 = cc.cb; b0 < cc.ce; b0 += 32) {
+    int kd = cc.kind, cut = cc.cut;
+    T cf = cc.coef;
+    if (b0 != cc.cb) {
+      const int e = b0 + lane;
+      kd = -1; cut = -1; cf = T(0);
+      if (e < cc.ce) {
+        cut = __ldg(c.cut + e);
+        kd = __ldg(c.kind + e);
+        cf = __ldg(c.coef + e);
+        if (cut < 0 || cut >= N) { dev_error(2, e, N); cut = -1; kd = -1; }
+      }
+    }
+    const T val = cut >= 0 ? cf * (T)grow[cut] : T(0);
+    const int lo_e = max(cc.e0, b0), cnt = max(0, min(cc.e1, b0 + 32) - lo_e);
+    const int mx = __reduce_max_sync(0xffffffffu, cnt);
+    for (int q = 0; q < mx; ++q) {
+      const int src = (lo_e + q - b0) & 31;
+      const T v = __shfl_sync(0xffffffffu, val, src);
+      const int kq = __shfl_sync(0xffffffffu, kd, src);
+      if (q < cnt) {
+        if (kq == GCP_VAR_X) t += v;
+        else if (kq == GCP_VAR_XHAT) g += v;
+        else if (kq == GCP_VAR_Z) s += v;
+      }
+    }
+  }
+}
+
+// E[r, e] = coef * (x: dt, xhat: -dnh, z: ds) of the entry's neuron, e the
+// entry's CSC position (the chunk's entries are contiguous: whole lines).
+template <typename T>
+__device__ __forceinline__ void cut_writes_row(const CutCSC<T>& c, const ChunkCuts<T>& cc, int ch, int lane, T dt,
+                                               T dnh, T ds, T* Erow) {
+  for (int b0 = cc.cb; b0 < cc.ce; b0 += 32) {
+    int kd = cc.kind, src = cc.nrn_lane;
+    T cf = cc.coef;
+    const int e = b0 + lane;
+    if (b0 != cc.cb) {
+      kd = -1; src = 0; cf = T(0);
+      if (e < cc.ce) {
+        kd = __ldg(c.kind + e);
+        src = (__ldg(c.nrn + e) - ch * 32) & 31;
+        cf = __ldg(c.coef + e);
+      }
+    }
+    const T vt = __shfl_sync(0xffffffffu, dt, src);
+    const T vh = __shfl_sync(0xffffffffu, dnh, src);
+    const T vs = __shfl_sync(0xffffffffu, ds, src);
+    if (e < cc.ce) Erow[e] = cf * (kd == GCP_VAR_X ? vt : (kd == GCP_VAR_XHAT ? -vh : vs));
+  }
+}
+
+// Certification variant: round-to-nearest sums with their round-up absolute
+// sums and term counts (for Higham's bound), per kind.
+template <typename Tg>
+__device__ __forceinline__ void cut_sums_row_cert(const CutCSC<double>& c, const ChunkCuts<double>& cc,
+                                                  const Tg* grow, int N, int lane, double (&sum)[3],
+                                                  double (&abs_)[3], int (&cnt_)[3]) {
+  for (int q = 0; q < 3; ++q) { sum[q] = 0.0; abs_[q] = 0.0; cnt_[q] = 0; }
+  for (int b0 = cc.cb; b0 < cc.ce; b0 += 32) {
+    int kd = cc.kind, cut = cc.cut;
+    double cf = cc.coef;
+    if (b0 != cc.cb) {
+      const int e = b0 + lane;
+      kd = -1; cut = -1; cf = 0.0;
+      if (e < cc.ce) {
+        cut = __ldg(c.cut + e);
+        kd = __ldg(c.kind + e);
+        cf = __ldg(c.coef + e);
+        if (cut < 0 || cut >= N) { dev_error(2, e, N); cut = -1; kd = -1; }
+      }
+    }
+    double val = 0.0, av = 0.0;
+    if (cut >= 0) {
+      const double gv = (double)grow[cut];
+      val = cf * gv;
+      av = __dmul_ru(fabs(cf), fabs(gv));
+    }
+    const int lo_e = max(cc.e0, b0), n = max(0, min(cc.e1, b0 + 32) - lo_e);
+    const int mx = __reduce_max_sync(0xffffffffu, n);
+    for (int q = 0; q < mx; ++q) {
+      const int src = (lo_e + q - b0) & 31;
+      const double v = __shfl_sync(0xffffffffu, val, src);
+      const double a = __shfl_sync(0xffffffffu, av, src);
+      const int kq = __shfl_sync(0xffffffffu, kd, src);
+      if (q < n && kq >= 0 && kq <= 2) {
+        sum[kq] += v;
+        abs_[kq] = __dadd_ru(abs_[kq], a);
+        ++cnt_[kq];
+      }
+    }
   }
 }
 
@@ -143,124 +277,143 @@ __device__ __forceinline__ T step_apply(const StepArgs<T>& st, T x, T grad, T lr
 // ------------------------------------------------------------------ eval
 template <typename T, typename Top>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_eval(RelaxArgs<T, Top> a) {
-  WarpPos p;
-  if (!warp_pos(a.R, a.d, p)) return;
-  const int64_t r = p.r;
-  const int j = p.j;
-  const int s = (int)(r / a.K), k = (int)(r - (int64_t)s * a.K);
-  T term = T(0);
-  if (p.on) {
-    T t, gg, sq;
-    cut_sums(a.csc, a.gamma + r * a.N, a.N, j, t, gg, sq);
-    T lo = a.lo[j], hi = a.hi[j];
-    int q0, q1;
-    split_range(a.sp, s, a.M, q0, q1);
-    for (int q = q0; q < q1; ++q)
-      if (a.sp.layer[q] == a.layer && a.sp.index[q] == j) {
-        const T bv = a.beta[r * a.M + (q - q0)];
-        if (a.sp.sign[q] > 0) { t -= bv; lo = tmax(lo, T(0)); }   // row -x <= 0
-        else { t += bv; hi = tmin(hi, T(0)); }                    // row  x <= 0
-      }
-    const T nh = a.y[(a.y_per_spec ? (int64_t)k : r) * a.d + j] - gg;
-    T nu;
-    if (hi <= T(0)) {            // inactive: xhat = 0, z = 0
-      nu = -t;
-    } else if (lo >= T(0)) {     // active: xhat = x, z = 1
-      nu = nh - t;
-      term = sq;
-    } else {                     // unstable: Lemma A.1 with q = -s
-      const T C = tmax(nh, T(0));
-      const T p0 = (hi * C - sq) / (hi - lo);
-      const T pi = tmin(tmax(p0, T(0)), C);
-      term = lo * pi - tmax(T(0), hi * (C - pi) + lo * pi - sq);
-      const T tau = a.alpha[r * a.d + j] * tmax(-nh, T(0));
-      nu = pi - tau - t;
-    }
-    term -= nu * a.bias[j];
-    put_operand<Top>(a.nu_out, a.nu_lo, r * a.d + j, nu);
-    a.nuhat_out[r * a.d + j] = nh;
+  ChunkWarp w;
+  if (!chunk_warp((int)(a.R / a.K), a.d, w)) return;
+  const int j = w.j;
+  T lo = T(0), hi = T(0), bj = T(0), iv = T(0);
+  if (w.on) {
+    lo = __ldg(a.lo + j);
+    hi = __ldg(a.hi + j);
+    bj = __ldg(a.bias + j);
+    iv = a.inv_ul ? __ldg(a.inv_ul + j) : (hi > lo ? T(1) / (hi - lo) : T(0));
   }
-  term = warp_sum(term);
-  if (p.lane == 0) a.obj_part[(int64_t)p.c * a.R + r] = term;
+  int sign = 0;
+  const int slot = lane_split(a.sp, w.s, a.M, a.layer, w.c, w.lane, sign);
+  if (slot >= 0) {
+    if (sign > 0) lo = tmax(lo, T(0)); else hi = tmin(hi, T(0));
+  }
+  const int cls = hi <= T(0) ? 0 : (lo >= T(0) ? 1 : 2);   // inactive / active / unstable
+  ChunkCuts<T> cc;
+  chunk_cuts(a.csc, a.N, a.d, w.c, w.lane, cc);
+  for (int k = 0; k < a.K; ++k) {
+    const int64_t r = (int64_t)w.s * a.K + k;
+    const int64_t ij = r * a.d + j;
+    T yv = T(0), al = T(0), bv = T(0);
+    if (w.on) {
+      yv = __ldg(a.y + (a.y_per_spec ? (int64_t)k : r) * a.d + j);
+      if (cls == 2) al = __ldg(a.alpha + ij);
+      if (slot >= 0) bv = __ldg(a.beta + r * a.M + slot);
+    }
+    T t, gg, sq;
+    cut_sums_row(a.csc, cc, a.gamma + r * a.N, a.N, w.c, w.lane, t, gg, sq);
+    T term = T(0);
+    if (w.on) {
+      if (slot >= 0) t += sign > 0 ? -bv : bv;   // split row -x <= 0 (x >= 0) or x <= 0
+      const T nh = yv - gg;
+      T nu;
+      if (cls == 0) {            // inactive: xhat = 0, z = 0
+        nu = -t;
+      } else if (cls == 1) {     // active: xhat = x, z = 1
+        nu = nh - t;
+        term = sq;
+      } else {                   // unstable: Lemma A.1 with q = -s
+        const T C = tmax(nh, T(0));
+        const T pi = tmin(tmax((hi * C - sq) * iv, T(0)), C);
+        term = lo * pi - tmax(T(0), hi * (C - pi) + lo * pi - sq);
+        nu = pi - al * tmax(-nh, T(0)) - t;
+      }
+      term -= nu * bj;
+      put_operand<Top>(a.nu_out, a.nu_lo, ij, nu);
+      a.nuhat_out[ij] = nh;
+    }
+    term = warp_sum(term);
+    if (w.lane == 0) a.obj_part[(int64_t)w.c * a.R + r] = term;
+  }
 }
 
 // ------------------------------------------------------------------ adjoint
 template <typename T, typename Top>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_adj(AdjArgs<T, Top> a) {
-  WarpPos p;
-  if (!warp_pos(a.R, a.d, p) || !p.on) return;
-  const int64_t r = p.r;
-  const int j = p.j;
-  const int s = (int)(r / a.K);
-  const T w = a.seed ? a.seed[r] : T(1);
-  const int64_t ij = r * a.d + j;
-  const T nb = a.nubar[ij] - w * a.bias[j];   // dg/dnu^(i)
-  T t, gg, sq;
-  cut_sums(a.csc, a.gamma + r * a.N, a.N, j, t, gg, sq);
-  T lo = a.lo[j], hi = a.hi[j];
-  int q0, q1;
-  split_range(a.sp, s, a.M, q0, q1);
-  int split_q = -1;
-  for (int q = q0; q < q1; ++q)
-    if (a.sp.layer[q] == a.layer && a.sp.index[q] == j) {
-      split_q = q;
-      if (a.sp.sign[q] > 0) lo = tmax(lo, T(0)); else hi = tmin(hi, T(0));
-    }
-  T dnu_dnh = T(0), dh_dnh = T(0), dnu_ds = T(0), dh_ds = T(0);
-  const bool unstable = !(hi <= T(0)) && !(lo >= T(0));
-  if (!unstable) {
-    if (!(hi <= T(0))) { dnu_dnh = T(1); dh_ds = w; }     // active
-    if (a.st.mode == 0) a.g_alpha[ij] = T(0);
-  } else {
-    const T nh = a.nuhat[ij];
-    const T al = a.alpha[ij];
-    if (nh > T(0)) {
-      const T ul = hi - lo;
-      const T p0 = (hi * nh - sq) / ul;
-      if (p0 > T(0) && p0 < nh) {          // pi* = p0
-        dnu_dnh = hi / ul;
-        dh_dnh = w * lo * hi / ul;
-        dnu_ds = -T(1) / ul;
-        dh_ds = -w * lo / ul;
-      } else if (p0 >= nh) {               // pi* = C, h = s when l C - s > 0
-        dnu_dnh = T(1);
-        dh_ds = (lo * nh - sq > T(0)) ? w : T(0);
+  ChunkWarp w;
+  if (!chunk_warp((int)(a.R / a.K), a.d, w)) return;
+  const int j = w.j;
+  T lo = T(0), hi = T(0), bj = T(0), iv = T(0);
+  if (w.on) {
+    lo = __ldg(a.lo + j);
+    hi = __ldg(a.hi + j);
+    bj = __ldg(a.bias + j);
+    iv = a.inv_ul ? __ldg(a.inv_ul + j) : (hi > lo ? T(1) / (hi - lo) : T(0));
+  }
+  int sign = 0;
+  const int slot = lane_split(a.sp, w.s, a.M, a.layer, w.c, w.lane, sign);
+  if (slot >= 0) {
+    if (sign > 0) lo = tmax(lo, T(0)); else hi = tmin(hi, T(0));
+  }
+  const int cls = hi <= T(0) ? 0 : (lo >= T(0) ? 1 : 2);
+  ChunkCuts<T> cc;
+  chunk_cuts(a.csc, a.N, a.d, w.c, w.lane, cc);
+  for (int k = 0; k < a.K; ++k) {
+    const int64_t r = (int64_t)w.s * a.K + k;
+    const int64_t ij = r * a.d + j;
+    const T wr = a.seed ? a.seed[r] : T(1);
+    T nbv = T(0), nh = T(0), al = T(0);
+    if (w.on) {
+      nbv = __ldg(a.nubar + ij);
+      if (cls == 2) {
+        nh = __ldg(a.nuhat + ij);
+        al = a.alpha[ij];
       }
-    } else {
-      if (nh < T(0)) dnu_dnh = al;         // nu = alpha * nuhat
-      dh_ds = (sq < T(0)) ? w : T(0);      // h = min(s, 0)
     }
-    const T g_alpha = nb * (-tmax(-nh, T(0)));
-    if (a.st.mode == 0) {
-      a.g_alpha[ij] = g_alpha;
-    } else {
-      T na = step_apply(a.st, al, g_alpha, a.st.lr_a, a.m_alpha ? a.m_alpha + ij : nullptr,
-                        a.v_alpha ? a.v_alpha + ij : nullptr);
-      a.alpha[ij] = tmin(tmax(na, T(0)), T(1));
+    T t, gg, sq;
+    cut_sums_row(a.csc, cc, a.gamma + r * a.N, a.N, w.c, w.lane, t, gg, sq);
+    const T nb = nbv - wr * bj;   // dg/dnu^(i)
+    T dnu_dnh = T(0), dh_dnh = T(0), dnu_ds = T(0), dh_ds = T(0);
+    if (w.on) {
+      if (cls != 2) {
+        if (cls == 1) { dnu_dnh = T(1); dh_ds = wr; }     // active
+        if (a.st.mode == 0) a.g_alpha[ij] = T(0);
+      } else {
+        if (nh > T(0)) {
+          const T p0 = (hi * nh - sq) * iv;
+          if (p0 > T(0) && p0 < nh) {          // pi* = p0
+            dnu_dnh = hi * iv;
+            dh_dnh = wr * lo * hi * iv;
+            dnu_ds = -iv;
+            dh_ds = -wr * lo * iv;
+          } else if (p0 >= nh) {               // pi* = C, h = s when l C - s > 0
+            dnu_dnh = T(1);
+            dh_ds = (lo * nh - sq > T(0)) ? wr : T(0);
+          }
+        } else {
+          if (nh < T(0)) dnu_dnh = al;         // nu = alpha * nuhat
+          dh_ds = (sq < T(0)) ? wr : T(0);     // h = min(s, 0)
+        }
+        const T g_alpha = nb * (-tmax(-nh, T(0)));
+        if (a.st.mode == 0) {
+          a.g_alpha[ij] = g_alpha;
+        } else {
+          T na = step_apply(a.st, al, g_alpha, a.st.lr_a, a.m_alpha ? a.m_alpha + ij : nullptr,
+                            a.v_alpha ? a.v_alpha + ij : nullptr);
+          a.alpha[ij] = tmin(tmax(na, T(0)), T(1));
+        }
+      }
     }
-  }
-  const T dg_dnh = nb * dnu_dnh + dh_dnh;
-  const T dg_ds = nb * dnu_ds + dh_ds;
-  const T dg_dt = -nb;
-  if (a.a_out) put_operand<Top>(a.a_out, a.a_lo, ij, dg_dnh);
-  int e0, e1;
-  csc_range(a.csc, j, e0, e1);
-  for (int e = e0; e < e1; ++e) {
-    const int kd = a.csc.kind[e];
-    const T v = kd == GCP_VAR_X ? dg_dt : (kd == GCP_VAR_XHAT ? -dg_dnh : dg_ds);
-    const int row = a.csc.eid[e];
-    if (row < 0 || (int64_t)row >= a.csc.n_total) { dev_error(4, e, a.csc.n_total); continue; }
-    a.E[r * a.csc.n_total + row] = a.csc.coef[e] * v;
-  }
-  if (split_q >= 0) {
-    const int64_t bi = r * a.M + (split_q - q0);
-    const T gb = (a.sp.sign[split_q] > 0 ? T(-1) : T(1)) * dg_dt;
-    if (a.st.mode == 0) {
-      a.g_beta[bi] = gb;
-    } else {
-      T nbv = step_apply(a.st, a.beta[bi], gb, a.st.lr_b, a.m_beta ? a.m_beta + bi : nullptr,
-                         a.v_beta ? a.v_beta + bi : nullptr);
-      a.beta[bi] = tmax(nbv, T(0));
+    const T dg_dnh = nb * dnu_dnh + dh_dnh;
+    const T dg_ds = nb * dnu_ds + dh_ds;
+    const T dg_dt = -nb;
+    if (a.E) cut_writes_row(a.csc, cc, w.c, w.lane, dg_dt, dg_dnh, dg_ds, a.E + r * a.csc.n_total);
+    if (!w.on) continue;
+    if (a.a_out) put_operand<Top>(a.a_out, a.a_lo, ij, dg_dnh);
+    if (slot >= 0) {
+      const int64_t bi = r * a.M + slot;
+      const T gb = (sign > 0 ? T(-1) : T(1)) * dg_dt;
+      if (a.st.mode == 0) {
+        a.g_beta[bi] = gb;
+      } else {
+        T nbv2 = step_apply(a.st, a.beta[bi], gb, a.st.lr_b, a.m_beta ? a.m_beta + bi : nullptr,
+                            a.v_beta ? a.v_beta + bi : nullptr);
+        a.beta[bi] = tmax(nbv2, T(0));
+      }
     }
   }
 }
@@ -268,36 +421,31 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_adj(AdjArgs<T, To
 // ------------------------------------------------------------------ concretization
 template <typename T, typename Top>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_concretize(ConcArgs<T, Top> a) {
-  WarpPos p;
-  if (!warp_pos(a.R, a.d0, p)) return;
-  const int64_t r = p.r;
-  const int j = p.j;
-  T term = T(0);
-  if (p.on) {
-    const T w = a.seed ? a.seed[r] : T(1);
-    const T* grow = a.gamma + r * a.N;
-    T h0 = T(0);
-    int e0, e1;
-    csc_range(a.csc, j, e0, e1);
-    for (int e = e0; e < e1; ++e) {
-      const int kc = a.csc.cut[e];
-      if (kc < 0 || kc >= a.N) { dev_error(2, e, a.N); continue; }
-      h0 += a.csc.coef[e] * grow[kc];
-    }
-    const T c0 = -a.y0[r * a.d0 + j] + h0;
-    const T xl = a.x_lo[j], xh = a.x_hi[j];
-    term = tmin(c0 * xl, c0 * xh);
-    const T xs = c0 > T(0) ? xl : (c0 < T(0) ? xh : T(0.5) * (xl + xh));
-    if (a.a0_out) put_operand<Top>(a.a0_out, a.a0_lo, r * a.d0 + j, -w * xs);
-    if (a.E)
-      for (int e = e0; e < e1; ++e) {
-        const int row = a.csc.eid[e];
-        if (row < 0 || (int64_t)row >= a.csc.n_total) { dev_error(4, e, a.csc.n_total); continue; }
-        a.E[r * a.csc.n_total + row] = a.csc.coef[e] * w * xs;
-      }
+  ChunkWarp w;
+  if (!chunk_warp((int)(a.R / a.K), a.d0, w)) return;
+  const int j = w.j;
+  T xl = T(0), xh = T(0);
+  if (w.on) {
+    xl = __ldg(a.x_lo + j);
+    xh = __ldg(a.x_hi + j);
   }
-  term = warp_sum(term);
-  if (p.lane == 0) a.obj_part[(int64_t)p.c * a.R + r] = term;
+  ChunkCuts<T> cc;
+  chunk_cuts(a.csc, a.N, a.d0, w.c, w.lane, cc);
+  for (int k = 0; k < a.K; ++k) {
+    const int64_t r = (int64_t)w.s * a.K + k;
+    const int64_t ij = r * a.d0 + j;
+    const T wr = a.seed ? a.seed[r] : T(1);
+    const T yv = w.on ? __ldg(a.y0 + ij) : T(0);
+    T h0, ug, us;
+    cut_sums_row(a.csc, cc, a.gamma + r * a.N, a.N, w.c, w.lane, h0, ug, us);   // layer 0: kind x only
+    const T c0 = -yv + h0;
+    const T xs = c0 > T(0) ? xl : (c0 < T(0) ? xh : T(0.5) * (xl + xh));
+    if (a.E) cut_writes_row(a.csc, cc, w.c, w.lane, wr * xs, T(0), T(0), a.E + r * a.csc.n_total);
+    T term = w.on ? tmin(c0 * xl, c0 * xh) : T(0);
+    if (w.on && a.a0_out) put_operand<Top>(a.a0_out, a.a0_lo, ij, -wr * xs);
+    term = warp_sum(term);
+    if (w.lane == 0) a.obj_part[(int64_t)w.c * a.R + r] = term;
+  }
 }
 
 // g[r] = c_k^T b^(L) - gamma_r^T d + sum of the partials; one warp per row.
@@ -326,7 +474,11 @@ __global__ void k_gather(GatherArgs<T> a) {
   int e0 = a.cut_ptr[n], e1 = a.cut_ptr[n + 1];
   if (e0 < 0 || e1 < e0 || (int64_t)e1 > a.nnz) { dev_error(5, n, a.nnz); e0 = e1 = 0; }
   const T* Er = a.E + r * a.nnz;
-  for (int e = e0; e < e1; ++e) grad += Er[e];
+  for (int e = e0; e < e1; ++e) {
+    const int q = __ldg(a.pos + e);
+    if (q < 0 || (int64_t)q >= a.nnz) { dev_error(5, e, a.nnz); continue; }
+    grad += Er[q];
+  }
   if (a.st.mode == 0) {
     a.g_gamma[i] = grad;
   } else {
@@ -350,45 +502,36 @@ __device__ __forceinline__ double gamma_of(int n) {
 
 template <typename Td>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_relax(CertArgs<Td> a) {
-  WarpPos p;
-  if (!warp_pos(a.R, a.d, p)) return;
-  const int64_t r = p.r;
-  const int j = p.j;
-  const int s = (int)(r / a.K), k = (int)(r - (int64_t)s * a.K);
-  double part = 0.0;
-  if (p.on) {
-    const int64_t yi = (a.y_per_spec ? (int64_t)k : r) * a.d + j;
-    const Td* grow = a.gamma + r * a.N;
+  ChunkWarp w;
+  if (!chunk_warp((int)(a.R / a.K), a.d, w)) return;
+  const int j = w.j;
+  int sign = 0;
+  const int slot = lane_split(a.sp, w.s, a.M, a.layer, w.c, w.lane, sign);
+  ChunkCuts<double> cc;
+  chunk_cuts(a.csc, a.N, a.d, w.c, w.lane, cc);
+  for (int k = 0; k < a.K; ++k) {
+    const int64_t r = (int64_t)w.s * a.K + k;
+    double sum[3], abs_[3];
+    int cnt_[3];
+    cut_sums_row_cert(a.csc, cc, a.gamma + r * a.N, a.N, w.lane, sum, abs_, cnt_);
+    double part = 0.0;
+    if (w.on) {
     // sparse sums in round-to-nearest with their Higham error bounds
-    double t = 0, gg = 0, sq = 0, ta = 0, ga = 0, sa = 0;
-    int nt = 0, ng = 0, ns = 0;
-    int e0, e1;
-    csc_range(a.csc, j, e0, e1);
-    for (int e = e0; e < e1; ++e) {
-      const int kc = a.csc.cut[e];
-      if (kc < 0 || kc >= a.N) { dev_error(2, e, a.N); continue; }
-      const double gv = (double)grow[kc];
-      const double v = a.csc.coef[e] * gv;
-      const double av = __dmul_ru(fabs(a.csc.coef[e]), fabs(gv));
-      const int kd = a.csc.kind[e];
-      if (kd == GCP_VAR_X) { t += v; ta = __dadd_ru(ta, av); ++nt; }
-      else if (kd == GCP_VAR_XHAT) { gg += v; ga = __dadd_ru(ga, av); ++ng; }
-      else { sq += v; sa = __dadd_ru(sa, av); ++ns; }
-    }
+    double t = sum[GCP_VAR_X], gg = sum[GCP_VAR_XHAT], sq = sum[GCP_VAR_Z];
+    double ta = abs_[GCP_VAR_X];
+    int nt = cnt_[GCP_VAR_X];
     double lo = a.lo[j], hi = a.hi[j];
-    int q0, q1;
-    split_range(a.sp, s, a.M, q0, q1);
-    for (int q = q0; q < q1; ++q)
-      if (a.sp.layer[q] == a.layer && a.sp.index[q] == j) {
-        const double bv = (double)a.beta[r * a.M + (q - q0)];
-        if (a.sp.sign[q] > 0) { t -= bv; lo = fmax(lo, 0.0); }
-        else { t += bv; hi = fmin(hi, 0.0); }
-        ta = __dadd_ru(ta, fabs(bv));
-        ++nt;
-      }
+    if (slot >= 0) {
+      const double bv = (double)a.beta[r * a.M + slot];
+      if (sign > 0) { t -= bv; lo = fmax(lo, 0.0); }
+      else { t += bv; hi = fmin(hi, 0.0); }
+      ta = __dadd_ru(ta, fabs(bv));
+      ++nt;
+    }
     const double et = __dmul_ru(gamma_of(nt), ta);
-    const double eg = __dmul_ru(gamma_of(ng), ga);
-    const double es = __dmul_ru(gamma_of(ns), sa);
+    const double eg = __dmul_ru(gamma_of(cnt_[GCP_VAR_XHAT]), abs_[GCP_VAR_XHAT]);
+    const double es = __dmul_ru(gamma_of(cnt_[GCP_VAR_Z]), abs_[GCP_VAR_Z]);
+    const int64_t yi = (a.y_per_spec ? (int64_t)k : r) * a.d + j;
     const double y = a.y[yi];
     const double ey = __dmul_ru(a.gamma_n, (double)a.yabs[yi]);
     const double nh = y - gg;
@@ -433,9 +576,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_relax(CertArgs<
     }
     part = __dadd_rd(part, __dmul_rd(-nu, a.bias[j]));
     a.nu_out[r * a.d + j] = nu;
+    }
+    part = warp_sum_rd(part);
+    if (w.lane == 0) a.obj_part[(int64_t)w.c * a.R + r] = part;
   }
-  part = warp_sum_rd(part);
-  if (p.lane == 0) a.obj_part[(int64_t)p.c * a.R + r] = part;
 }
 
 template <typename Td>
@@ -444,34 +588,29 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_conc(int64_t R,
                                                                        double gamma_n, const double* x_lo,
                                                                        const double* x_hi, const Td* gamma,
                                                                        CutCSC<double> csc, double* obj_part) {
-  WarpPos p;
-  if (!warp_pos(R, d0, p)) return;
-  const int64_t r = p.r;
-  const int j = p.j;
-  double part = 0.0;
-  if (p.on) {
-    const Td* grow = gamma + r * N;
-    double h = 0, ha = 0;
-    int n = 0;
-    int e0, e1;
-    csc_range(csc, j, e0, e1);
-    for (int e = e0; e < e1; ++e) {
-      const int kc = csc.cut[e];
-      if (kc < 0 || kc >= N) { dev_error(2, e, N); continue; }
-      const double gv = (double)grow[kc];
-      h += csc.coef[e] * gv;
-      ha = __dadd_ru(ha, __dmul_ru(fabs(csc.coef[e]), fabs(gv)));
-      ++n;
+  ChunkWarp w;
+  if (!chunk_warp((int)(R / K), d0, w)) return;
+  const int j = w.j;
+  ChunkCuts<double> cc;
+  chunk_cuts(csc, N, d0, w.c, w.lane, cc);
+  for (int k = 0; k < K; ++k) {
+    const int64_t r = (int64_t)w.s * K + k;
+    double sum[3], abs_[3];
+    int cnt_[3];
+    cut_sums_row_cert(csc, cc, gamma + r * N, N, w.lane, sum, abs_, cnt_);
+    double part = 0.0;
+    if (w.on) {
+      const double h = sum[GCP_VAR_X];
+      const double eh = __dmul_ru(gamma_of(cnt_[GCP_VAR_X]), abs_[GCP_VAR_X]);
+      const double y = y0[r * d0 + j];
+      const double ey = __dmul_ru(gamma_n, (double)y0abs[r * d0 + j]);
+      const double c_lo = __dadd_rd(__dsub_rd(-y, ey), __dsub_rd(h, eh));
+      const double c_hi = __dadd_ru(__dadd_ru(-y, ey), __dadd_ru(h, eh));
+      part = box_min_rd(c_lo, c_hi, x_lo[j], x_hi[j]);
     }
-    const double eh = __dmul_ru(gamma_of(n), ha);
-    const double y = y0[r * d0 + j];
-    const double ey = __dmul_ru(gamma_n, (double)y0abs[r * d0 + j]);
-    const double c_lo = __dadd_rd(__dsub_rd(-y, ey), __dsub_rd(h, eh));
-    const double c_hi = __dadd_ru(__dadd_ru(-y, ey), __dadd_ru(h, eh));
-    part = box_min_rd(c_lo, c_hi, x_lo[j], x_hi[j]);
+    part = warp_sum_rd(part);
+    if (w.lane == 0) obj_part[(int64_t)w.c * R + r] = part;
   }
-  part = warp_sum_rd(part);
-  if (p.lane == 0) obj_part[(int64_t)p.c * R + r] = part;
 }
 
 template <typename Td>
@@ -532,10 +671,10 @@ __global__ void k_default_alpha(int64_t R, int K, int d, int layer, const T* lo,
   }
 }
 
-// one warp per (row, 32-neuron chunk)
-inline unsigned warp_blocks(int64_t R, int d) {
-  const int64_t warps = R * (int64_t)((d + 31) / 32);
-  return (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
+// one warp per (subdomain, 32-neuron chunk)
+inline dim3 chunk_blocks(int64_t R, int K, int d) {
+  const int64_t S = R / K;
+  return dim3((unsigned)((S + kWarpsPerBlock - 1) / kWarpsPerBlock), (unsigned)((d + 31) / 32));
 }
 inline unsigned row_blocks(int64_t R) { return (unsigned)((R + kWarpsPerBlock - 1) / kWarpsPerBlock); }
 inline int flat_grid(int64_t n) {
@@ -548,7 +687,6 @@ inline int flat_grid(int64_t n) {
 
 template <typename T>
 const char* tsfx() { return sizeof(T) == 8 ? "f64" : "f32"; }
-inline double chunks(int d) { return (double)((d + kChunk - 1) / kChunk); }
 
 // host-side extent checks shared by the launchers
 inline bool chk_splits(const SplitsDev& sp, int64_t R, int K) {
@@ -560,7 +698,7 @@ template <typename T>
 inline bool chk_csc(const CutCSC<T>& c, int d) {
   return reg_check(c.ptr, (d + 1) * 4.0, "csc ptr") & reg_check(c.cut, c.n_total * 4.0, "csc cut") &
          reg_check(c.kind, (double)c.n_total, "csc kind") & reg_check(c.coef, c.n_total * (double)sizeof(T), "csc coef") &
-         reg_check(c.eid, c.n_total * 4.0, "csc eid");
+         reg_check(c.nrn, c.n_total * 4.0, "csc nrn");
 }
 
 // Algorithmic bytes per launch: every per-(row, neuron) array read or written
@@ -571,18 +709,19 @@ void relax_eval(cudaStream_t st, const RelaxArgs<T, Top>& a) {
   char nm[48];
   snprintf(nm, sizeof nm, "relax_eval_%s%s", tsfx<T>(), sizeof(Top) == 2 ? "_bf16" : "");
   const double bytes = (double)a.R * a.d * (3.0 * sizeof(T) + sizeof(Top)) +
-                       (double)a.R * (a.csc.n_entries + chunks(a.d)) * sizeof(T);
+                       (double)a.R * (a.csc.n_entries + (a.d + 31) / 32) * sizeof(T);
   const double Rd = (double)a.R * a.d, tb = sizeof(T);
   if (!(reg_check(a.y, (a.y_per_spec ? (double)a.K : (double)a.R) * a.d * tb, "relax y") &
         reg_check(a.lo, a.d * tb, "lo") & reg_check(a.hi, a.d * tb, "hi") & reg_check(a.bias, a.d * tb, "bias") &
+        reg_check(a.inv_ul, a.inv_ul ? a.d * tb : 0.0, "inv_ul") &
         reg_check(a.alpha, Rd * tb, "alpha") & reg_check(a.beta, (double)a.M * a.R * tb, "beta") &
         reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") & chk_splits(a.sp, a.R, a.K) &
         chk_csc(a.csc, a.d) & reg_check(a.nu_out, Rd * sizeof(Top), "nu out") &
         reg_check(a.nu_lo, a.nu_lo ? Rd * 4.0 : 0.0, "nu lo") &
-        reg_check(a.nuhat_out, Rd * tb, "nuhat out") & reg_check(a.obj_part, chunks(a.d) * a.R * tb, "obj part")))
+        reg_check(a.nuhat_out, Rd * tb, "nuhat out") & reg_check(a.obj_part, ((a.d + 31) / 32) * (double)a.R * tb, "obj part")))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
-  k_relax_eval<T, Top><<<warp_blocks(a.R, a.d), kWarpsPerBlock * 32, 0, st>>>(a);
+  k_relax_eval<T, Top><<<chunk_blocks(a.R, a.K, a.d), kWarpsPerBlock * 32, 0, st>>>(a);
   prof_end(st, tk);
 }
 template <typename T, typename Top>
@@ -596,6 +735,7 @@ void relax_adjoint(cudaStream_t st, const AdjArgs<T, Top>& a) {
   const bool m0 = a.st.mode == 0, m2 = a.st.mode == 2;
   if (!(reg_check(a.nubar, Rd * tb, "nubar") & reg_check(a.seed, a.seed ? a.R * tb : 0.0, "seed") &
         reg_check(a.lo, a.d * tb, "lo") & reg_check(a.hi, a.d * tb, "hi") & reg_check(a.bias, a.d * tb, "bias") &
+        reg_check(a.inv_ul, a.inv_ul ? a.d * tb : 0.0, "inv_ul") &
         reg_check(a.alpha, Rd * tb, "alpha") & reg_check(a.beta, (double)a.M * a.R * tb, "beta") &
         reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") &
         reg_check(a.nuhat, Rd * tb, "nuhat") & chk_splits(a.sp, a.R, a.K) & chk_csc(a.csc, a.d) &
@@ -609,7 +749,7 @@ void relax_adjoint(cudaStream_t st, const AdjArgs<T, Top>& a) {
         reg_check(a.v_beta, m2 ? (double)a.M * a.R * tb : 0.0, "v_beta")))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
-  k_relax_adj<T, Top><<<warp_blocks(a.R, a.d), kWarpsPerBlock * 32, 0, st>>>(a);
+  k_relax_adj<T, Top><<<chunk_blocks(a.R, a.K, a.d), kWarpsPerBlock * 32, 0, st>>>(a);
   prof_end(st, tk);
 }
 template <typename T, typename Top>
@@ -618,7 +758,7 @@ void concretize(cudaStream_t st, const ConcArgs<T, Top>& a) {
   char nm[48];
   snprintf(nm, sizeof nm, "concretize_%s", tsfx<T>());
   const double bytes = (double)a.R * a.d0 * (sizeof(T) + (a.a0_out ? sizeof(Top) : 0)) +
-                       (double)a.R * (a.csc.n_entries * (a.E ? 2.0 : 1.0) + chunks(a.d0)) * sizeof(T);
+                       (double)a.R * (a.csc.n_entries * (a.E ? 2.0 : 1.0) + (a.d0 + 31) / 32) * sizeof(T);
   const double Rd = (double)a.R * a.d0, tb = sizeof(T);
   if (!(reg_check(a.y0, Rd * tb, "y0") & reg_check(a.x_lo, a.d0 * tb, "x_lo") & reg_check(a.x_hi, a.d0 * tb, "x_hi") &
         reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") &
@@ -626,10 +766,10 @@ void concretize(cudaStream_t st, const ConcArgs<T, Top>& a) {
         reg_check(a.a0_out, a.a0_out ? Rd * sizeof(Top) : 0.0, "a0 out") &
         reg_check(a.a0_lo, (a.a0_out && a.a0_lo) ? Rd * 4.0 : 0.0, "a0 lo") &
         reg_check(a.E, (a.E && a.csc.n_entries) ? (double)a.csc.n_total * a.R * tb : 0.0, "E") &
-        reg_check(a.obj_part, chunks(a.d0) * a.R * tb, "obj part")))
+        reg_check(a.obj_part, ((a.d0 + 31) / 32) * (double)a.R * tb, "obj part")))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
-  k_concretize<T, Top><<<warp_blocks(a.R, a.d0), kWarpsPerBlock * 32, 0, st>>>(a);
+  k_concretize<T, Top><<<chunk_blocks(a.R, a.K, a.d0), kWarpsPerBlock * 32, 0, st>>>(a);
   prof_end(st, tk);
 }
 template <typename T>
@@ -650,7 +790,8 @@ void gather_gamma(cudaStream_t st, const GatherArgs<T>& a) {
   if (a.R <= 0 || a.N <= 0) return;
   const double tb = sizeof(T), NR = (double)a.N * a.R;
   const bool m0 = a.st.mode == 0, m2 = a.st.mode == 2;
-  if (!(reg_check(a.cut_ptr, (a.N + 1) * 4.0, "cut ptr") & reg_check(a.E, (double)a.nnz * a.R * tb, "E") &
+  if (!(reg_check(a.cut_ptr, (a.N + 1) * 4.0, "cut ptr") & reg_check(a.pos, a.nnz * 4.0, "cut pos") &
+        reg_check(a.E, (double)a.nnz * a.R * tb, "E") &
         reg_check(a.d, a.N * tb, "d") & reg_check(a.seed, a.seed ? a.R * tb : 0.0, "seed") &
         reg_check(a.gamma, NR * tb, "gamma") & reg_check(a.g_gamma, m0 ? NR * tb : 0.0, "g_gamma") &
         reg_check(a.m_gamma, m2 ? NR * tb : 0.0, "m_gamma") & reg_check(a.v_gamma, m2 ? NR * tb : 0.0, "v_gamma")))
@@ -664,17 +805,17 @@ template <typename Td>
 void certify_relax(cudaStream_t st, const CertArgs<Td>& a) {
   if (a.R <= 0 || a.d <= 0) return;
   const double bytes = (double)a.R * a.d * (8.0 + 4.0 + 8.0 + sizeof(Td)) +
-                       (double)a.R * (a.csc.n_entries * sizeof(Td) + chunks(a.d) * 8.0);
+                       (double)a.R * (a.csc.n_entries * sizeof(Td) + ((a.d + 31) / 32) * 8.0);
   const double Rd = (double)a.R * a.d, yr = (a.y_per_spec ? (double)a.K : (double)a.R) * a.d, tb = sizeof(Td);
   if (!(reg_check(a.y, yr * 8.0, "cert y") & reg_check(a.yabs, yr * 4.0, "cert yabs") &
         reg_check(a.lo, a.d * 8.0, "lo") & reg_check(a.hi, a.d * 8.0, "hi") & reg_check(a.bias, a.d * 8.0, "bias") &
         reg_check(a.alpha, Rd * tb, "alpha") & reg_check(a.beta, (double)a.M * a.R * tb, "beta") &
         reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") & chk_splits(a.sp, a.R, a.K) &
         chk_csc(a.csc, a.d) & reg_check(a.nu_out, Rd * 8.0, "cert nu") &
-        reg_check(a.obj_part, chunks(a.d) * a.R * 8.0, "cert part")))
+        reg_check(a.obj_part, ((a.d + 31) / 32) * (double)a.R * 8.0, "cert part")))
     return;
   int tk = prof_begin(st, "certify_relax_f64", 0.0, bytes);
-  k_certify_relax<Td><<<warp_blocks(a.R, a.d), kWarpsPerBlock * 32, 0, st>>>(a);
+  k_certify_relax<Td><<<chunk_blocks(a.R, a.K, a.d), kWarpsPerBlock * 32, 0, st>>>(a);
   prof_end(st, tk);
 }
 template <typename Td>
@@ -684,10 +825,10 @@ void certify_concretize(cudaStream_t st, int64_t R, int K, int N, int d0, const 
   if (R <= 0 || d0 <= 0) return;
   if (!(reg_check(y0, (double)R * d0 * 8.0, "cert y0") & reg_check(y0abs, (double)R * d0 * 4.0, "cert y0abs") &
         reg_check(x_lo, d0 * 8.0, "x_lo") & reg_check(x_hi, d0 * 8.0, "x_hi") & chk_csc(csc, d0) &
-        reg_check(obj_part, chunks(d0) * R * 8.0, "cert part")))
+        reg_check(obj_part, ((d0 + 31) / 32) * (double)R * 8.0, "cert part")))
     return;
   int tk = prof_begin(st, "certify_conc_f64", 0.0, (double)R * d0 * 12.0);
-  k_certify_conc<Td><<<warp_blocks(R, d0), kWarpsPerBlock * 32, 0, st>>>(R, K, N, d0, y0, y0abs, gamma_n, x_lo, x_hi,
+  k_certify_conc<Td><<<chunk_blocks(R, K, d0), kWarpsPerBlock * 32, 0, st>>>(R, K, N, d0, y0, y0abs, gamma_n, x_lo, x_hi,
                                                                     gamma, csc, obj_part);
   prof_end(st, tk);
 }
