@@ -161,6 +161,15 @@ GCP_API gcp_status gcp_add_cuts(gcp_ctx* ctx, int32_t net_id, int32_t n_cuts, co
  * *duals receives an opaque handle owned by the context. */
 GCP_API gcp_status gcp_duals_create(gcp_ctx* ctx, int32_t net_id, int32_t cutset_id,
                                     const gcp_subdomains* sub, int32_t dual_prec, void** duals);
+/* One batch for several queries on the same network, evaluated in the same
+ * launches (uneven batching): query q has cut set cutset_ids[q] (-1 = none)
+ * and subdomains subs[q]; rows are query-major (query 0's rows first). The
+ * batch's cuts are the queries' cut sets concatenated in query order, and
+ * the multipliers of a query's rows stay 0 on the other queries' cuts
+ * (exported as zeros), so every row's bound is the one it has alone up to
+ * summation order. Duals and errors as gcp_duals_create. */
+GCP_API gcp_status gcp_duals_create_multi(gcp_ctx* ctx, int32_t net_id, int32_t n_queries, const int32_t* cutset_ids,
+                                          const gcp_subdomains* subs, int32_t dual_prec, void** duals);
 /* Shape of a duals object: rows R, alpha columns sum_i d_i, max_splits, cuts N. */
 GCP_API gcp_status gcp_duals_shape(gcp_ctx* ctx, void* duals, int64_t* rows, int64_t* n_alpha,
                                    int32_t* max_splits, int32_t* n_cuts);
@@ -301,9 +310,13 @@ typedef struct {
 } gcp_result;
 
 /* Start the serving loop: a host scheduler thread admits submitted requests
- * while at most max_inflight run and their device memory fits the context's
- * budget, runs each admitted request's rounds on its own stream (requests
- * overlap on the device), and frees memory as requests finish. */
+ * while at most max_inflight run and their estimated device memory fits the
+ * context's budget, keeps each admitted request's duals on the device between
+ * rounds, and every round evaluates the active requests of one network (and
+ * optimiser schedule) in one merged batch with shared launches (as
+ * gcp_duals_create_multi); groups of different networks run concurrently on
+ * their own streams. Requests submitted meanwhile join at the next round;
+ * memory is freed as requests finish. Results are certified (FP64). */
 GCP_API gcp_status gcp_serve_start(gcp_ctx* ctx, int32_t max_inflight);
 /* Enqueue a request; *ticket identifies it. GCP_EBUDGET if it can never fit. */
 GCP_API gcp_status gcp_serve_submit(gcp_ctx* ctx, const gcp_request* req, uint64_t* ticket);
@@ -311,7 +324,8 @@ GCP_API gcp_status gcp_serve_submit(gcp_ctx* ctx, const gcp_request* req, uint64
 GCP_API gcp_status gcp_serve_poll(gcp_ctx* ctx, uint64_t ticket, gcp_result* res);
 /* Like poll but waits up to timeout_ms (GCP_ETIMEOUT if still pending). */
 GCP_API gcp_status gcp_serve_wait(gcp_ctx* ctx, uint64_t ticket, int32_t timeout_ms, gcp_result* res);
-/* Stop admitting, finish in-flight requests, join the scheduler thread. */
+/* Stop accepting submissions, finish every submitted request, join the
+ * scheduler thread and free the loop's streams. Unpolled results are dropped. */
 GCP_API gcp_status gcp_serve_stop(gcp_ctx* ctx);
 
 #ifdef __cplusplus

@@ -43,6 +43,7 @@ gcp_status Ctx::cuda(cudaError_t e, const char* what) {
 }
 
 void* Ctx::alloc(size_t bytes) {
+  std::lock_guard<std::mutex> lk(alloc_mu);
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~size_t(255);
   if (budget && used + bytes > budget) {
@@ -62,6 +63,7 @@ void* Ctx::alloc(size_t bytes) {
 
 void Ctx::release(void* p) {
   if (!p) return;
+  std::lock_guard<std::mutex> lk(alloc_mu);
   auto it = sizes.find(p);
   if (it != sizes.end()) {
     used -= it->second;
@@ -330,6 +332,10 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
     UP(ivd, double, iv.data(), di);
     UP(ivs, float, ivf.data(), di);
     net->invul64.push_back(ivd); net->invul32.push_back(ivs);
+    std::vector<int32_t> un;
+    for (int j = 0; j < di; ++j)
+      if (inter_lo[off + j] < 0 && inter_hi[off + j] > 0) un.push_back(j);
+    net->unstable.push_back(un);
     off += di;
   }
 #undef UP
@@ -467,44 +473,81 @@ gcp_status build_cutdev(Ctx& c, const Net& net, const CutSet* cs, CutDev& out) {
 }
 
 // ------------------------------------------------------------------ duals
-gcp_status duals_create(Ctx& c, int net_id, int cutset_id, const gcp_subdomains* sub, int dual_prec, Batch** out) {
+// One batch for one or several queries on the same network. parts[q] = (cut
+// set or nullptr, subdomains). Rows are query-major. With several parts the
+// cut set is the union of the parts' sets (query q's cuts at offset o_q) and
+// every subdomain may only move the multipliers of its own query's cuts; the
+// others stay exactly 0 and contribute exact zeros, so a row's duals do not
+// depend on what it is batched with.
+gcp_status duals_create_parts(Ctx& c, int net_id, const std::vector<std::pair<const CutSet*, const gcp_subdomains*>>& parts,
+                              int dual_prec, Batch** out) {
   auto it = c.nets.find(net_id);
   if (it == c.nets.end()) return c.fail(GCP_ENOTFOUND, "unknown net %d", net_id);
-  if (!sub || !out || sub->n_sub < 0) return c.fail(GCP_EINVAL, "gcp_duals_create: bad arguments");
+  if (!out || parts.empty()) return c.fail(GCP_EINVAL, "gcp_duals_create: bad arguments");
   if (dual_prec != GCP_FP64 && dual_prec != GCP_FP32) return c.fail(GCP_EINVAL, "dual_prec must be FP64 or FP32");
   Net& net = *it->second;
-  const CutSet* cs = nullptr;
-  if (cutset_id >= 0) {
-    auto ci = c.cutsets.find(cutset_id);
-    if (ci == c.cutsets.end()) return c.fail(GCP_ENOTFOUND, "unknown cut set %d", cutset_id);
-    if (ci->second->net_id != net_id) return c.fail(GCP_EINVAL, "cut set of another net");
-    cs = ci->second.get();
-  }
-  const int S = sub->n_sub;
-  if (S > 0 && !sub->split_ptr) return c.fail(GCP_EINVAL, "null split_ptr");
-  std::vector<int32_t> sptr(S + 1, 0);
+  std::vector<int32_t> sptr(1, 0), cut_lo, cut_hi;
+  std::vector<int16_t> slay;
+  std::vector<int32_t> sidx;
+  std::vector<int8_t> ssgn;
+  CutSet uni;
+  uni.net_id = net_id;
+  uni.ptr.push_back(0);
   int M = 0;
-  if (S > 0) {
-    if (sub->split_ptr[0] != 0) return c.fail(GCP_EINVAL, "split_ptr[0] must be 0");
+  for (const auto& part : parts) {
+    const CutSet* cs = part.first;
+    const gcp_subdomains* sub = part.second;
+    if (!sub || sub->n_sub < 0) return c.fail(GCP_EINVAL, "gcp_duals_create: bad subdomains");
+    if (cs && cs->net_id != net_id) return c.fail(GCP_EINVAL, "cut set of another net");
+    const int S = sub->n_sub;
+    if (S > 0 && !sub->split_ptr) return c.fail(GCP_EINVAL, "null split_ptr");
+    if (S > 0 && sub->split_ptr[0] != 0) return c.fail(GCP_EINVAL, "split_ptr[0] must be 0");
     for (int s = 0; s < S; ++s) {
       const int n = sub->split_ptr[s + 1] - sub->split_ptr[s];
       if (n < 0 || n > kMaxSplits) return c.fail(GCP_EINVAL, "subdomain %d: 0..%d splits allowed", s, kMaxSplits);
       M = std::max(M, n);
     }
-    std::copy(sub->split_ptr, sub->split_ptr + S + 1, sptr.begin());
-  }
-  const int64_t nsp = sptr[S];
-  if (nsp > 0 && (!sub->split_layer || !sub->split_index || !sub->split_sign)) return c.fail(GCP_EINVAL, "null split arrays");
-  for (int s = 0; s < S; ++s)
-    for (int q = sptr[s]; q < sptr[s + 1]; ++q) {
-      const int li = sub->split_layer[q];
-      if (li < 1 || li >= net.L) return c.fail(GCP_EINVAL, "split %d: layer %d not hidden", q, li);
-      if (sub->split_index[q] < 0 || sub->split_index[q] >= net.dims[li]) return c.fail(GCP_EINVAL, "split %d: index out of range", q);
-      if (sub->split_sign[q] != 1 && sub->split_sign[q] != -1) return c.fail(GCP_EINVAL, "split %d: sign must be +-1", q);
-      for (int q2 = sptr[s]; q2 < q; ++q2)
-        if (sub->split_layer[q2] == li && sub->split_index[q2] == sub->split_index[q])
-          return c.fail(GCP_EINVAL, "subdomain %d splits a neuron twice", s);
+    const int64_t nsp = S > 0 ? sub->split_ptr[S] : 0;
+    if (nsp > 0 && (!sub->split_layer || !sub->split_index || !sub->split_sign))
+      return c.fail(GCP_EINVAL, "null split arrays");
+    for (int s = 0; s < S; ++s)
+      for (int q = sub->split_ptr[s]; q < sub->split_ptr[s + 1]; ++q) {
+        const int li = sub->split_layer[q];
+        if (li < 1 || li >= net.L) return c.fail(GCP_EINVAL, "split %d: layer %d not hidden", q, li);
+        if (sub->split_index[q] < 0 || sub->split_index[q] >= net.dims[li])
+          return c.fail(GCP_EINVAL, "split %d: index out of range", q);
+        if (sub->split_sign[q] != 1 && sub->split_sign[q] != -1) return c.fail(GCP_EINVAL, "split %d: sign must be +-1", q);
+        for (int q2 = sub->split_ptr[s]; q2 < q; ++q2)
+          if (sub->split_layer[q2] == li && sub->split_index[q2] == sub->split_index[q])
+            return c.fail(GCP_EINVAL, "subdomain %d splits a neuron twice", s);
+      }
+    const int o = (int)uni.d.size(), nq = cs ? (int)cs->d.size() : 0;
+    for (int s = 0; s < S; ++s) {
+      sptr.push_back(sptr.back() + sub->split_ptr[s + 1] - sub->split_ptr[s]);
+      cut_lo.push_back(o);
+      cut_hi.push_back(o + nq);
     }
+    if (nsp > 0) {
+      slay.insert(slay.end(), sub->split_layer, sub->split_layer + nsp);
+      sidx.insert(sidx.end(), sub->split_index, sub->split_index + nsp);
+      ssgn.insert(ssgn.end(), sub->split_sign, sub->split_sign + nsp);
+    }
+    if (cs) {
+      const int64_t base = uni.ptr.back();
+      for (int k = 0; k < nq; ++k) uni.ptr.push_back(base + cs->ptr[k + 1]);
+      uni.layer.insert(uni.layer.end(), cs->layer.begin(), cs->layer.end());
+      uni.kind.insert(uni.kind.end(), cs->kind.begin(), cs->kind.end());
+      uni.index.insert(uni.index.end(), cs->index.begin(), cs->index.end());
+      uni.coef.insert(uni.coef.end(), cs->coef.begin(), cs->coef.end());
+      uni.d.insert(uni.d.end(), cs->d.begin(), cs->d.end());
+    }
+  }
+  if (uni.d.size() > 65535) return c.fail(GCP_EINVAL, "at most 65535 cuts per batch");
+  const int S = (int)sptr.size() - 1;
+  const int64_t nsp = sptr[S];
+  gcp_subdomains all{S, sptr.data(), slay.data(), sidx.data(), ssgn.data()};
+  const gcp_subdomains* sub = &all;
+  const CutSet* cs = uni.d.empty() ? nullptr : &uni;
   auto b = std::make_unique<Batch>();
   b->ctx = &c;
   b->net = &net;
@@ -523,6 +566,7 @@ gcp_status duals_create(Ctx& c, int net_id, int cutset_id, const gcp_subdomains*
   b->N = b->cuts.N;
   b->nnz = b->cuts.nnz;
   b->nsp = nsp;
+  b->parts = (int)parts.size();
 #define UPB(dst, T, host, n)                   \
   do {                                         \
     dst = upload<T>(c, host, n, &st);          \
@@ -533,6 +577,10 @@ gcp_status duals_create(Ctx& c, int net_id, int cutset_id, const gcp_subdomains*
   UPB(b->sp_layer, int16_t, sub->split_layer, nsp);
   UPB(b->sp_index, int32_t, sub->split_index, nsp);
   UPB(b->sp_sign, int8_t, sub->split_sign, nsp);
+  if (parts.size() > 1) {
+    UPB(b->sub_cut_lo, int32_t, cut_lo.data(), S);
+    UPB(b->sub_cut_hi, int32_t, cut_hi.data(), S);
+  }
   const size_t es = b->fp64 ? 8 : 4;
   for (int i = 1; i < net.L; ++i) {
     void* p = c.alloc((size_t)b->R * net.dims[i] * es);
@@ -552,6 +600,16 @@ gcp_status duals_create(Ctx& c, int net_id, int cutset_id, const gcp_subdomains*
   *out = b.get();
   c.batches[b.get()] = std::move(b);
   return GCP_OK;
+}
+
+gcp_status duals_create(Ctx& c, int net_id, int cutset_id, const gcp_subdomains* sub, int dual_prec, Batch** out) {
+  const CutSet* cs = nullptr;
+  if (cutset_id >= 0) {
+    auto ci = c.cutsets.find(cutset_id);
+    if (ci == c.cutsets.end()) return c.fail(GCP_ENOTFOUND, "unknown cut set %d", cutset_id);
+    cs = ci->second.get();
+  }
+  return duals_create_parts(c, net_id, {{cs, sub}}, dual_prec, out);
 }
 
 gcp_status reset_duals(Ctx& c, Batch& b, bool a, bool be, bool g) {
@@ -846,7 +904,7 @@ gcp_status run_adjoint(Ctx& c, Batch& b, cudaStream_t st, const StepArgs<T>& ste
   }
   if (b.N > 0) {
     GatherArgs<T> ga{R, b.N, b.cuts.cut_ptr, b.cuts.csr_pos, E, TSel<T>::d(b.cuts), seed, (T*)b.gamma, gga, mg, vg,
-                     step, b.nnz};
+                     step, b.nnz, b.K, b.sub_cut_lo, b.sub_cut_hi};
     gather_gamma<T>(st, ga);
   }
   return launch_status(c, "adjoint");
@@ -909,6 +967,8 @@ static StepArgs<T> make_step(const gcp_opt_params& p, int it) {
   s.eps = (T)1e-8;
   s.c1 = (T)(1.0 - std::pow(0.9, it + 1));
   s.c2 = (T)(1.0 - std::pow(0.999, it + 1));
+  s.ic1 = (T)(1.0 / (1.0 - std::pow(0.9, it + 1)));
+  s.ic2 = (T)(1.0 / (1.0 - std::pow(0.999, it + 1)));
   return s;
 }
 
@@ -1397,6 +1457,30 @@ gcp_status gcp_duals_create(gcp_ctx* h, int32_t net_id, int32_t cutset_id, const
   gcp_status s = gcp::duals_create(*c, net_id, cutset_id, sub, dual_prec, &b);
   if (s == GCP_OK) {
     s = gcp::sync_check(*c, c->stream, "duals_create");
+    if (s == GCP_OK) *duals = b;
+  }
+  return s;
+}
+
+gcp_status gcp_duals_create_multi(gcp_ctx* h, int32_t net_id, int32_t n_queries, const int32_t* cutset_ids,
+                                  const gcp_subdomains* subs, int32_t dual_prec, void** duals) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  CTX_GUARD(c);
+  if (n_queries < 1 || !cutset_ids || !subs || !duals) return c->fail(GCP_EINVAL, "gcp_duals_create_multi: bad arguments");
+  std::vector<std::pair<const gcp::CutSet*, const gcp_subdomains*>> parts;
+  for (int q = 0; q < n_queries; ++q) {
+    const gcp::CutSet* cs = nullptr;
+    if (cutset_ids[q] >= 0) {
+      auto ci = c->cutsets.find(cutset_ids[q]);
+      if (ci == c->cutsets.end()) return c->fail(GCP_ENOTFOUND, "unknown cut set %d", cutset_ids[q]);
+      cs = ci->second.get();
+    }
+    parts.push_back({cs, &subs[q]});
+  }
+  gcp::Batch* b = nullptr;
+  gcp_status s = gcp::duals_create_parts(*c, net_id, parts, dual_prec, &b);
+  if (s == GCP_OK) {
+    s = gcp::sync_check(*c, c->stream, "duals_create_multi");
     if (s == GCP_OK) *duals = b;
   }
   return s;

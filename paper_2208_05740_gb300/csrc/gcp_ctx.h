@@ -36,6 +36,7 @@ struct Net {
   std::vector<double*> lo64, hi64;   // hidden layer i at index i-1
   std::vector<float*> lo32, hi32;    // rounded outwards
   std::vector<double*> invul64;      // 1 / (hi - lo) where lo < 0 < hi, else 0
+  std::vector<std::vector<int32_t>> unstable;  // root-unstable neurons of hidden layer i at index i-1 (host)
   std::vector<float*> invul32;
   std::vector<void*> owned;
   ~Net();
@@ -77,6 +78,9 @@ struct Batch {
   int net_id = 0;
   int S = 0, K = 0, M = 0, N = 0;
   int64_t R = 0, nnz = 0, nsp = 0;
+  int parts = 1;                     // queries sharing this batch
+  int32_t* sub_cut_lo = nullptr;     // [S] first cut of the subdomain's query (several parts only)
+  int32_t* sub_cut_hi = nullptr;     // [S] end of the query's cuts
   bool fp64 = false;
   bool tc = true;                    // use the tcgen05 GEMMs where shapes allow
   CutDev cuts;
@@ -104,6 +108,7 @@ struct Ctx {
   bool over_budget = false;
   cudaStream_t own_stream = nullptr, stream = nullptr;
   std::recursive_mutex mu;
+  std::mutex alloc_mu;               // allocations may come from serving worker threads
   std::string err;
   int next_id = 1;
   std::map<int, std::unique_ptr<Net>> nets;
@@ -120,6 +125,10 @@ struct Ctx {
 
 // shared by api.cu and serve.cu
 gcp_status duals_create(Ctx& c, int net_id, int cutset_id, const gcp_subdomains* sub, int dual_prec, Batch** out);
+gcp_status duals_create_parts(Ctx& c, int net_id,
+                              const std::vector<std::pair<const CutSet*, const gcp_subdomains*>>& parts,
+                              int dual_prec, Batch** out);
+gcp_status sync_check(Ctx& c, cudaStream_t st, const char* what);
 gcp_status reset_duals(Ctx& c, Batch& b, bool a, bool be, bool g);
 gcp_status optimize_on(Ctx& c, Batch& b, const gcp_opt_params& p, cudaStream_t st, double* cert_dev);
 gcp_status eval_dispatch(Ctx& c, Batch& b, cudaStream_t st, int prec, bool adj_start, const void* seed);

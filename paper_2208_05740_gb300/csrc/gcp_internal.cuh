@@ -59,6 +59,7 @@ struct StepArgs {
   int mode;
   T lr_a, lr_b, lr_g;
   T b1, b2, eps, c1, c2;  // Adam moments and bias corrections 1-b1^t, 1-b2^t
+  T ic1, ic2;             // 1/c1, 1/c2
 };
 
 template <typename T, typename Top>
@@ -151,6 +152,9 @@ struct GatherArgs {
   T* m_gamma; T* v_gamma;
   StepArgs<T> st;
   int64_t nnz;          // cut entries (host-side accounting only)
+  int K;                // spec rows per subdomain
+  const int32_t* cut_lo;  // [S] cuts the row's query owns: [cut_lo, cut_hi), or nullptr = all
+  const int32_t* cut_hi;
 };
 
 // Certification pass (float64, outward rounding). Td: dual storage type.

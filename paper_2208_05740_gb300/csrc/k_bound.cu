@@ -264,6 +264,8 @@ __device__ __forceinline__ void cut_sums_row_cert(const CutCSC<double>& c, const
   }
 }
 
+// One ascent step on x. Adam (Kingma & Ba): bias-corrected moments; the
+// float chain uses the fast reciprocal divide (a step size, not a bound).
 template <typename T>
 __device__ __forceinline__ T step_apply(const StepArgs<T>& st, T x, T grad, T lr, T* m, T* v) {
   if (st.mode == 1) return x + lr * grad;
@@ -271,7 +273,11 @@ __device__ __forceinline__ T step_apply(const StepArgs<T>& st, T x, T grad, T lr
   T vv = st.b2 * (*v) + (T(1) - st.b2) * grad * grad;
   *m = mm;
   *v = vv;
-  return x + lr * (mm / st.c1) / (sqrt(vv / st.c2) + st.eps);
+  if constexpr (std::is_same<T, float>::value) {
+    return x + lr * __fdividef(mm * st.ic1, __fsqrt_rn(vv * st.ic2) + st.eps);
+  } else {
+    return x + lr * (mm / st.c1) / (sqrt(vv / st.c2) + st.eps);
+  }
 }
 
 // ------------------------------------------------------------------ eval
@@ -469,6 +475,14 @@ __global__ void k_gather(GatherArgs<T> a) {
   if (i >= a.R * a.N) return;
   const int64_t r = i / a.N;
   const int n = (int)(i - r * a.N);
+  if (a.cut_lo) {
+    // a cut of another query batched alongside: its multiplier stays 0
+    const int64_t s = r / a.K;
+    if (n < a.cut_lo[s] || n >= a.cut_hi[s]) {
+      if (a.st.mode == 0) a.g_gamma[i] = T(0);
+      return;
+    }
+  }
   const T w = a.seed ? a.seed[r] : T(1);
   T grad = -w * a.d[n];
   int e0 = a.cut_ptr[n], e1 = a.cut_ptr[n + 1];
@@ -794,7 +808,9 @@ void gather_gamma(cudaStream_t st, const GatherArgs<T>& a) {
         reg_check(a.E, (double)a.nnz * a.R * tb, "E") &
         reg_check(a.d, a.N * tb, "d") & reg_check(a.seed, a.seed ? a.R * tb : 0.0, "seed") &
         reg_check(a.gamma, NR * tb, "gamma") & reg_check(a.g_gamma, m0 ? NR * tb : 0.0, "g_gamma") &
-        reg_check(a.m_gamma, m2 ? NR * tb : 0.0, "m_gamma") & reg_check(a.v_gamma, m2 ? NR * tb : 0.0, "v_gamma")))
+        reg_check(a.m_gamma, m2 ? NR * tb : 0.0, "m_gamma") & reg_check(a.v_gamma, m2 ? NR * tb : 0.0, "v_gamma") &
+        reg_check(a.cut_lo, a.cut_lo ? (double)(a.R / a.K) * 4.0 : 0.0, "cut lo") &
+        reg_check(a.cut_hi, a.cut_hi ? (double)(a.R / a.K) * 4.0 : 0.0, "cut hi")))
     return;
   int tk = prof_begin(st, sizeof(T) == 8 ? "gather_gamma_f64" : "gather_gamma_f32", 0.0,
                       (double)a.R * (a.nnz + 2.0 * a.N) * sizeof(T));

@@ -24,7 +24,7 @@ GCP_FP64, GCP_FP32, GCP_BF16 = 0, 1, 2
 GCP_PGA, GCP_ADAM = 0, 1
 
 EXPORTED = ["gcp_create", "gcp_destroy", "gcp_last_error", "gcp_set_stream", "gcp_mem_used", "gcp_init_net",
-            "gcp_add_cuts", "gcp_duals_create", "gcp_duals_shape", "gcp_duals_export", "gcp_duals_import",
+            "gcp_add_cuts", "gcp_duals_create", "gcp_duals_create_multi", "gcp_duals_shape", "gcp_duals_export", "gcp_duals_import",
             "gcp_duals_free", "gcp_bound_batch", "gcp_grad_batch", "gcp_optimize_batch", "gcp_bound_device",
             "gcp_grad_device", "gcp_bound_dense_noalloc", "gcp_selftest_gemm", "gcp_profile_start", "gcp_profile_stop", "gcp_profile_query", "gcp_profile_report",
             "gcp_serve_start", "gcp_serve_submit", "gcp_serve_poll", "gcp_serve_wait",
@@ -86,6 +86,7 @@ def lib():
             "gcp_add_cuts": [P, I32, I32, C.POINTER(I64), C.POINTER(C.c_int16), C.POINTER(C.c_int8),
                              C.POINTER(I32), pd, pd, C.POINTER(I32), C.POINTER(I32)],
             "gcp_duals_create": [P, I32, I32, C.POINTER(Subdomains), I32, C.POINTER(P)],
+            "gcp_duals_create_multi": [P, I32, I32, C.POINTER(I32), C.POINTER(Subdomains), I32, C.POINTER(P)],
             "gcp_duals_shape": [P, P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I32), C.POINTER(I32)],
             "gcp_duals_export": [P, P, pd, pd, pd],
             "gcp_duals_import": [P, P, pd, pd, pd],
@@ -239,6 +240,20 @@ class Context:
         h = C.c_void_p()
         self._check(lib().gcp_duals_create(self.h, net_id, cutset_id, C.byref(sd), dual_prec, C.byref(h)))
         return Duals(self, h, net_id, cutset_id, dual_prec)
+
+    def duals_create_multi(self, net_id: int, cutset_ids, subs, dual_prec: int = GCP_FP32) -> Duals:
+        """Several queries on one network in one batch (rows query-major)."""
+        keep = []
+        arr = (Subdomains * len(subs))()
+        for q, sub in enumerate(subs):
+            a = [_c(sub.ptr, np.int32), _c(sub.layer, np.int16), _c(sub.index, np.int32), _c(sub.sign, np.int8)]
+            keep.append(a)
+            arr[q] = Subdomains(sub.n, _ptr(a[0], C.c_int32), _ptr(a[1], C.c_int16), _ptr(a[2], C.c_int32),
+                                _ptr(a[3], C.c_int8))
+        ids = (C.c_int32 * len(subs))(*cutset_ids)
+        h = C.c_void_p()
+        self._check(lib().gcp_duals_create_multi(self.h, net_id, len(subs), ids, arr, dual_prec, C.byref(h)))
+        return Duals(self, h, net_id, -1, dual_prec)
 
     def duals_export(self, D: Duals):
         a = np.zeros((D.rows, D.n_alpha))
