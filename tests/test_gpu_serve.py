@@ -143,7 +143,7 @@ def test_requests_arriving_during_a_round_join_later():
         na, csa = ctx.load_instance(a)
         ns, css = ctx.load_instance(s)
         ctx.serve_start(4)
-        t_long = _submit(ctx, na, csa, a.sub, 6, 1, iters=20)
+        t_long = _submit(ctx, na, csa, a.sub, 12, 1, iters=40)
         time.sleep(0.05)
         t_short = _submit(ctx, ns, css, s.sub, 1, 2, iters=5)
         r_short, _ = ctx.serve_wait(t_short, s.n_rows + 8)
