@@ -124,6 +124,11 @@ def kernel_peak(name, peaks, src):
         return "alu", 152 * 2 * 2 * mhz * 1e6 / 1e12, "TFLOP/s", f"DFMA peak from unit counts and {mhz:.0f} MHz"
     if name.startswith(("gemm_tc_bf16", "conv_tc_bf16")):
         return "tensor", float(peaks["bf16_tflops_sustained"]), "TFLOP/s", f"bf16 sustained ({src})"
+    if name.startswith(("gemm_tc_tf32", "conv_tc_tf32")):
+        # tf32 tensor rate = measured bf16 rate x nominal tf32/bf16 ratio (1.1/2.25);
+        # the three-pass kernel's achieved flops count the product once
+        tf = float(peaks["bf16_tflops_sustained"]) * 1.1 / 2.25
+        return "tensor", tf / 3.0, "TFLOP/s", f"tf32 tensor (bf16 sustained x 1.1/2.25, {src}) / 3 passes"
     return "hbm", float(peaks["hbm_gbs"]), "GB/s", f"copy bandwidth ({src})"
 
 
