@@ -400,7 +400,7 @@ gcp_status add_cuts(Ctx& c, int net_id, int n_cuts, const int64_t* row_ptr, cons
   return GCP_OK;
 }
 
-// Device copy of a cut set: CSR by cut for the gather, CSC by (layer, neuron).
+// Device copy of a cut set: CSR by cut for the gather, CSC by (layer, neuron, kind).
 gcp_status build_cutdev(Ctx& c, const Net& net, const CutSet* cs, CutDev& out) {
   out.ctx = &c;
   const int L = net.L;
@@ -417,7 +417,8 @@ gcp_status build_cutdev(Ctx& c, const Net& net, const CutSet* cs, CutDev& out) {
   if (out.nnz)
     std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
       if (cs->layer[a] != cs->layer[b]) return cs->layer[a] < cs->layer[b];
-      return cs->index[a] < cs->index[b];
+      if (cs->index[a] != cs->index[b]) return cs->index[a] < cs->index[b];
+      return cs->kind[a] < cs->kind[b];   // runs of equal (neuron, kind): one segment each
     });
   std::vector<int32_t> cptr(poff[L], 0), ccut(out.nnz), ceid(out.nnz), cnrn(out.nnz), cpos(out.nnz);
   std::vector<int8_t> ckind(out.nnz);
@@ -514,7 +515,8 @@ gcp_status duals_create_parts(Ctx& c, int net_id, const std::vector<std::pair<co
       for (int q = sub->split_ptr[s]; q < sub->split_ptr[s + 1]; ++q) {
         const int li = sub->split_layer[q];
         if (li < 1 || li >= net.L) return c.fail(GCP_EINVAL, "split %d: layer %d not hidden", q, li);
-        if (sub->split_index[q] < 0 || sub->split_index[q] >= net.dims[li])
+        if (sub->split_index[q] < 0 || sub->split_index[q] >= net.dims[li] || sub->split_index[q] >= (1 << 23) ||
+            li >= 128)
           return c.fail(GCP_EINVAL, "split %d: index out of range", q);
         if (sub->split_sign[q] != 1 && sub->split_sign[q] != -1) return c.fail(GCP_EINVAL, "split %d: sign must be +-1", q);
         for (int q2 = sub->split_ptr[s]; q2 < q; ++q2)
@@ -577,6 +579,14 @@ gcp_status duals_create_parts(Ctx& c, int net_id, const std::vector<std::pair<co
   UPB(b->sp_layer, int16_t, sub->split_layer, nsp);
   UPB(b->sp_index, int32_t, sub->split_index, nsp);
   UPB(b->sp_sign, int8_t, sub->split_sign, nsp);
+  {
+    const int Mt = std::max(M, 1);
+    std::vector<int32_t> tab((size_t)S * Mt, -1);
+    for (int s = 0; s < S; ++s)
+      for (int q = sptr[s]; q < sptr[s + 1]; ++q)
+        tab[(size_t)s * Mt + (q - sptr[s])] = split_code_of(sub->split_layer[q], sub->split_index[q], sub->split_sign[q]);
+    UPB(b->sp_tab, int32_t, tab.data(), tab.size());
+  }
   if (parts.size() > 1) {
     UPB(b->sub_cut_lo, int32_t, cut_lo.data(), S);
     UPB(b->sub_cut_hi, int32_t, cut_hi.data(), S);
@@ -616,7 +626,7 @@ gcp_status reset_duals(Ctx& c, Batch& b, bool a, bool be, bool g) {
   cudaStream_t st = c.stream;
   const Net& net = *b.net;
   const size_t es = b.fp64 ? 8 : 4;
-  SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp};
+  SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp, b.sp_tab};
   if (a)
     for (int i = 1; i < net.L; ++i) {
       if (b.fp64)
@@ -773,8 +783,10 @@ static void lin_forward(cudaStream_t st, const Batch& b, int i, const Top* a, co
 
 // Evaluate g for all rows at the batch's duals. with_adjoint_start: also write
 // a0 = -seed*x* into the operand buffer and the input-layer cut entries into E.
+// finalize = false leaves g itself out (ascent steps need only the gradient).
 template <typename T, typename Top>
-gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, const T* seed) {
+gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, const T* seed,
+                    bool finalize = true) {
   const Net& net = *b.net;
   const int L = net.L;
   const int64_t R = b.R;
@@ -798,7 +810,7 @@ gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, 
     E = (T*)b.ws("E", (size_t)b.nnz * R * sizeof(T), &s);
     if (!E) return s;
   }
-  SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp};
+  SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp, b.sp_tab};
   int poff = 0;
   for (int i = L - 1; i >= 1; --i) {
     T* nuhat = (T*)b.ws("nuhat" + std::to_string(i), (size_t)R * net.dims[i] * sizeof(T), &s);
@@ -835,8 +847,10 @@ gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, 
   ca.obj_part = part + (int64_t)poff * R;
   concretize<T, Top>(st, ca);
   poff += (net.dims[0] + kChunk - 1) / kChunk;
-  FinalArgs<T> fa{R, b.K, b.N, poff, TSel<T>::cb(net), TSel<T>::d(b.cuts), (const T*)b.gamma, part, g};
-  finalize_bound<T>(st, fa);
+  if (finalize) {
+    FinalArgs<T> fa{R, b.K, b.N, poff, TSel<T>::cb(net), TSel<T>::d(b.cuts), (const T*)b.gamma, part, g};
+    finalize_bound<T>(st, fa);
+  }
   return launch_status(c, "eval");
 }
 
@@ -876,7 +890,11 @@ gcp_status run_adjoint(Ctx& c, Batch& b, cudaStream_t st, const StepArgs<T>& ste
       cudaMemsetAsync(mg, 0, gb, st); cudaMemsetAsync(vg, 0, gb, st);
     }
   }
-  SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp};
+  SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp, b.sp_tab};
+  if (!gbe && b.M > 0) {   // ascent step: dg/dbeta goes through a workspace to the beta step
+    gbe = (T*)b.ws("g_beta_step", (size_t)b.M * R * sizeof(T), &s);
+    if (!gbe) return s;
+  }
   int64_t aoff = 0;
   for (int i = 1; i < L; ++i) {
     lin_forward<Top, T>(st, b, i, abuf, (lo && tc_fwd<Top>(b, i)) ? lo : nullptr, y);
@@ -887,7 +905,6 @@ gcp_status run_adjoint(Ctx& c, Batch& b, cudaStream_t st, const StepArgs<T>& ste
     a.lo = TSel<T>::lo(net, i); a.hi = TSel<T>::hi(net, i); a.bias = TSel<T>::b(net, i);
     a.inv_ul = TSel<T>::inv(net, i);
     a.alpha = (T*)b.alpha[i - 1];
-    a.beta = (T*)b.beta;
     a.gamma = (const T*)b.gamma;
     a.nuhat = nuhat;
     a.sp = sp;
@@ -897,14 +914,15 @@ gcp_status run_adjoint(Ctx& c, Batch& b, cudaStream_t st, const StepArgs<T>& ste
     a.E = E;
     a.g_alpha = gal ? gal + aoff : nullptr;
     a.g_beta = gbe;
-    if (ma) { a.m_alpha = ma + aoff; a.v_alpha = va + aoff; a.m_beta = mb; a.v_beta = vb; }
+    if (ma) { a.m_alpha = ma + aoff; a.v_alpha = va + aoff; }
     a.st = step;
     relax_adjoint<T, Top>(st, a);
     aoff += (int64_t)R * net.dims[i];
   }
-  if (b.N > 0) {
+  if (b.N > 0 || (b.M > 0 && step.mode != 0)) {
     GatherArgs<T> ga{R, b.N, b.cuts.cut_ptr, b.cuts.csr_pos, E, TSel<T>::d(b.cuts), seed, (T*)b.gamma, gga, mg, vg,
-                     step, b.nnz, b.K, b.sub_cut_lo, b.sub_cut_hi};
+                     step, b.nnz, b.K, b.sub_cut_lo, b.sub_cut_hi,
+                     b.M, b.sp_tab, (T*)b.beta, gbe, mb, vb};
     gather_gamma<T>(st, ga);
   }
   return launch_status(c, "adjoint");
@@ -922,7 +940,7 @@ gcp_status run_certify(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
   float* ya = (float*)b.ws("c_yabs", (size_t)R * b.dmax() * 4, &s);
   double* part = (double*)b.ws("c_part", (size_t)b.n_partials() * R * 8, &s);
   if (!nu || !y || !ya || !part) return s;
-  SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp};
+  SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp, b.sp_tab};
   // y^(L-1) = W^(L)^T (-c_k), one row per spec row
   const LayerGeom& gl = net.geom[L - 1];
   gemm_nt_abs(st, b.K, gl.d_in, gl.d_out, net.negC64, 0, net.WT64[L - 1], y, ya);
@@ -975,7 +993,7 @@ static StepArgs<T> make_step(const gcp_opt_params& p, int it) {
 template <typename T, typename Top>
 gcp_status optimize_steps(Ctx& c, Batch& b, cudaStream_t st, const gcp_opt_params& p) {
   for (int it = 0; it < p.iters; ++it) {
-    gcp_status s = run_eval<T, Top>(c, b, st, true, nullptr);
+    gcp_status s = run_eval<T, Top>(c, b, st, true, nullptr, false);
     if (s) return s;
     s = run_adjoint<T, Top>(c, b, st, make_step<T>(p, it), nullptr, nullptr, nullptr, nullptr);
     if (s) return s;

@@ -88,6 +88,7 @@ struct Batch {
   int16_t* sp_layer = nullptr;
   int32_t* sp_index = nullptr;
   int8_t* sp_sign = nullptr;
+  int32_t* sp_tab = nullptr;         // [S, max(M,1)] split codes by slot
   std::vector<void*> alpha;          // hidden layer i at index i-1, [R, d_i]
   void* beta = nullptr;              // [R, M]
   void* gamma = nullptr;             // [R, N]

@@ -6,7 +6,7 @@
 //   alpha^(i), nuhat^(i)           [R, d_i]  row-major, T
 //   beta                           [R, M]    (split slot m of the row's subdomain)
 //   gamma                          [R, N]
-//   E (cut-entry values)           [R, nnz]
+//   E (cut-entry values)           [R, nnz]  entries in CSC (layer, neuron, kind) order
 //   objective partials             [P, R]
 // A warp of the per-neuron kernels handles 32 consecutive neurons of one row,
 // so dense arrays move whole lines and the sparse cut gathers of a warp stay
@@ -38,7 +38,7 @@ struct CutCSC {
   const int32_t* cut;   // cut id per entry
   const int8_t* kind;   // GCP_VAR_*
   const T* coef;
-  const int32_t* eid;   // row of E written for this entry
+  const int32_t* eid;   // CSR position of the entry
   const int32_t* nrn;   // neuron index of the entry within its layer
   int64_t n_entries;    // entries of this layer (host-side accounting only)
   int64_t n_total;      // entries of all layers (host-side validation only)
@@ -50,7 +50,12 @@ struct SplitsDev {
   const int32_t* index;
   const int8_t* sign;
   int64_t n;            // total split entries (host-side validation only)
+  const int32_t* tab;   // [S, M] split codes by slot, -1 = none (see split_code)
 };
+// Split code of one slot: layer << 24 | (sign > 0) << 23 | neuron index.
+inline int32_t split_code_of(int layer, int index, int sign) {
+  return (int32_t)(((uint32_t)layer << 24) | ((sign > 0 ? 1u : 0u) << 23) | (uint32_t)index);
+}
 
 // Optimiser step applied inside the adjoint epilogues / cut gather.
 // mode 0: write gradients (no update); 1: projected gradient ascent; 2: Adam.
@@ -96,7 +101,6 @@ struct AdjArgs {
   const T* inv_ul;      // 1 / (hi - lo) of root-unstable neurons [d]
   const T* bias;
   T* alpha;             // [R, d], updated in place when mode != 0
-  T* beta;              // [R, M], updated in place when mode != 0
   const T* gamma;       // [R, N]
   const T* nuhat;       // [R, d]
   SplitsDev sp;
@@ -105,8 +109,8 @@ struct AdjArgs {
   float* a_lo;          // low part for the 3-pass tf32 GEMM, or nullptr
   T* E;                 // [R, nnz], entries in CSC order
   T* g_alpha;           // [R, d]  (mode 0)
-  T* g_beta;            // [R, M]  (mode 0)
-  T* m_alpha; T* v_alpha; T* m_beta; T* v_beta;  // Adam state (mode 2)
+  T* g_beta;            // [R, M]  dg/dbeta of the layer's splits (all modes; the gather steps beta)
+  T* m_alpha; T* v_alpha;  // Adam state (mode 2)
   StepArgs<T> st;
 };
 
@@ -144,7 +148,7 @@ struct GatherArgs {
   int N;
   const int32_t* cut_ptr;  // [N+1] CSR by cut
   const int32_t* pos;      // [nnz] CSC position (column of E) of each CSR entry
-  const T* E;
+  const T* E;              // [R, nnz], entries in CSC order
   const T* d;
   const T* seed;
   T* gamma;             // [R, N] updated when mode != 0
@@ -155,6 +159,12 @@ struct GatherArgs {
   int K;                // spec rows per subdomain
   const int32_t* cut_lo;  // [S] cuts the row's query owns: [cut_lo, cut_hi), or nullptr = all
   const int32_t* cut_hi;
+  // beta step (modes 1 and 2): dg/dbeta from the adjoint, slots holding a split
+  int M;
+  const int32_t* sp_tab;  // [S, M] split codes, -1 = empty slot
+  T* beta;                // [R, M]
+  const T* g_beta;        // [R, M]
+  T* m_beta; T* v_beta;
 };
 
 // Certification pass (float64, outward rounding). Td: dual storage type.

@@ -10,6 +10,9 @@
 #include <cstdio>
 #include <type_traits>
 
+#include <cstdlib>
+#include <algorithm>
+
 #include "gcp_internal.cuh"
 
 namespace gcp {
@@ -28,6 +31,19 @@ __device__ __noinline__ void dev_error(unsigned long long code, long long idx, l
     g_dev_err[2] = (unsigned long long)lim;
   }
 }
+
+// First failed index check of a thread, reported once when the kernel ends
+// (keeps function calls out of the load sequences of the hot kernels).
+struct DevErr {
+  unsigned code = 0;
+  long long idx = 0, lim = 0;
+  __device__ __forceinline__ void set(unsigned c, long long i, long long l) {
+    if (!code) { code = c; idx = i; lim = l; }
+  }
+  __device__ __forceinline__ void flush() const {
+    if (code) dev_error(code, idx, lim);
+  }
+};
 
 // split entries of subdomain s, checked against the entry count and slots
 __device__ __forceinline__ void split_range(const SplitsDev& sp, int s, int M, int& q0, int& q1) {
@@ -162,66 +178,6 @@ __device__ __forceinline__ void chunk_cuts(const CutCSC<T>& c, int N, int d, int
   }
 }
 
-// Entry values coef * gamma[cut] of one batch for row grow, summed per
-// neuron lane into t (x), g (xhat), s (z). Batches past the first reload
-// their entries (chunks with more than 32 entries).
-template <typename T, typename Tg>
-__device__ __forceinline__ void cut_sums_row(const CutCSC<T>& c, const ChunkCuts<T>& cc, const Tg* grow, int N,
-                                             int ch, int lane, T& t, T& g, T& s) {
-  t = T(0); g = T(0); s = T(0);
-  for (int b0 = cc.cb; b0 < cc.ce; b0 += 32) {
-    int kd = cc.kind, cut = cc.cut;
-    T cf = cc.coef;
-    if (b0 != cc.cb) {
-      const int e = b0 + lane;
-      kd = -1; cut = -1; cf = T(0);
-      if (e < cc.ce) {
-        cut = __ldg(c.cut + e);
-        kd = __ldg(c.kind + e);
-        cf = __ldg(c.coef + e);
-        if (cut < 0 || cut >= N) { dev_error(2, e, N); cut = -1; kd = -1; }
-      }
-    }
-    const T val = cut >= 0 ? cf * (T)grow[cut] : T(0);
-    const int lo_e = max(cc.e0, b0), cnt = max(0, min(cc.e1, b0 + 32) - lo_e);
-    const int mx = __reduce_max_sync(0xffffffffu, cnt);
-    for (int q = 0; q < mx; ++q) {
-      const int src = (lo_e + q - b0) & 31;
-      const T v = __shfl_sync(0xffffffffu, val, src);
-      const int kq = __shfl_sync(0xffffffffu, kd, src);
-      if (q < cnt) {
-        if (kq == GCP_VAR_X) t += v;
-        else if (kq == GCP_VAR_XHAT) g += v;
-        else if (kq == GCP_VAR_Z) s += v;
-      }
-    }
-  }
-}
-
-// E[r, e] = coef * (x: dt, xhat: -dnh, z: ds) of the entry's neuron, e the
-// entry's CSC position (the chunk's entries are contiguous: whole lines).
-template <typename T>
-__device__ __forceinline__ void cut_writes_row(const CutCSC<T>& c, const ChunkCuts<T>& cc, int ch, int lane, T dt,
-                                               T dnh, T ds, T* Erow) {
-  for (int b0 = cc.cb; b0 < cc.ce; b0 += 32) {
-    int kd = cc.kind, src = cc.nrn_lane;
-    T cf = cc.coef;
-    const int e = b0 + lane;
-    if (b0 != cc.cb) {
-      kd = -1; src = 0; cf = T(0);
-      if (e < cc.ce) {
-        kd = __ldg(c.kind + e);
-        src = (__ldg(c.nrn + e) - ch * 32) & 31;
-        cf = __ldg(c.coef + e);
-      }
-    }
-    const T vt = __shfl_sync(0xffffffffu, dt, src);
-    const T vh = __shfl_sync(0xffffffffu, dnh, src);
-    const T vs = __shfl_sync(0xffffffffu, ds, src);
-    if (e < cc.ce) Erow[e] = cf * (kd == GCP_VAR_X ? vt : (kd == GCP_VAR_XHAT ? -vh : vs));
-  }
-}
-
 // Certification variant: round-to-nearest sums with their round-up absolute
 // sums and term counts (for Higham's bound), per kind.
 template <typename Tg>
@@ -264,215 +220,703 @@ __device__ __forceinline__ void cut_sums_row_cert(const CutCSC<double>& c, const
   }
 }
 
-// One ascent step on x. Adam (Kingma & Ba): bias-corrected moments; the
+// One ascent step on x. Adam (Kingma & Ba): bias-corrected moments m, v are
+// read and updated in place (values, loaded by the caller ahead of time); the
 // float chain uses the fast reciprocal divide (a step size, not a bound).
 template <typename T>
-__device__ __forceinline__ T step_apply(const StepArgs<T>& st, T x, T grad, T lr, T* m, T* v) {
+__device__ __forceinline__ T step_apply(const StepArgs<T>& st, T x, T grad, T lr, T& m, T& v) {
   if (st.mode == 1) return x + lr * grad;
-  T mm = st.b1 * (*m) + (T(1) - st.b1) * grad;
-  T vv = st.b2 * (*v) + (T(1) - st.b2) * grad * grad;
-  *m = mm;
-  *v = vv;
+  m = st.b1 * m + (T(1) - st.b1) * grad;
+  v = st.b2 * v + (T(1) - st.b2) * grad * grad;
   if constexpr (std::is_same<T, float>::value) {
-    return x + lr * __fdividef(mm * st.ic1, __fsqrt_rn(vv * st.ic2) + st.eps);
+    return x + lr * __fdividef(m * st.ic1, __fsqrt_rn(v * st.ic2) + st.eps);
   } else {
-    return x + lr * (mm / st.c1) / (sqrt(vv / st.c2) + st.eps);
+    return x + lr * (m / st.c1) / (sqrt(v / st.c2) + st.eps);
   }
 }
 
-// ------------------------------------------------------------------ eval
-template <typename T, typename Top>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_eval(RelaxArgs<T, Top> a) {
-  ChunkWarp w;
-  if (!chunk_warp((int)(a.R / a.K), a.d, w)) return;
-  const int j = w.j;
-  T lo = T(0), hi = T(0), bj = T(0), iv = T(0);
-  if (w.on) {
-    lo = __ldg(a.lo + j);
-    hi = __ldg(a.hi + j);
-    bj = __ldg(a.bias + j);
-    iv = a.inv_ul ? __ldg(a.inv_ul + j) : (hi > lo ? T(1) / (hi - lo) : T(0));
+// ------------------------------------------------------------------ span kernels
+// The per-neuron kernels of the chain (relaxation, adjoint, concretization)
+// give each warp a span of 32*V consecutive neurons of one layer and one
+// subdomain, i.e. its K spec rows: lane l holds neurons base + lV .. base +
+// lV + V - 1, read and written as 16-byte vectors when V = 4 (float chains on
+// layers whose width is a multiple of 4). Row-independent data (bounds, split
+// hits, the span's cut entries) is set up once per warp.
+template <int V>
+struct SpanWarp {
+  int s, c, lane, base, j0;
+  bool on;              // the lane's V neurons exist (d is a multiple of V)
+};
+template <int V>
+__device__ __forceinline__ bool span_warp(int S, int d, SpanWarp<V>& w) {
+  w.s = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  w.c = blockIdx.y;
+  w.lane = threadIdx.x & 31;
+  w.base = w.c * 32 * V;
+  w.j0 = w.base + w.lane * V;
+  w.on = w.j0 < d;
+  return w.s < S;
+}
+
+template <int V, typename T>
+__device__ __forceinline__ void ldv(const T* p, T (&o)[V]) {      // read-only during the kernel
+  if constexpr (V == 4 && sizeof(T) == 4) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) o[v] = __ldg(p + v);
   }
-  int sign = 0;
-  const int slot = lane_split(a.sp, w.s, a.M, a.layer, w.c, w.lane, sign);
-  if (slot >= 0) {
-    if (sign > 0) lo = tmax(lo, T(0)); else hi = tmin(hi, T(0));
+}
+template <int V, typename T>
+__device__ __forceinline__ void ldv_rw(const T* p, T (&o)[V]) {   // also written by the kernel
+  if constexpr (V == 4 && sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) o[v] = p[v];
   }
-  const int cls = hi <= T(0) ? 0 : (lo >= T(0) ? 1 : 2);   // inactive / active / unstable
-  ChunkCuts<T> cc;
-  chunk_cuts(a.csc, a.N, a.d, w.c, w.lane, cc);
-  for (int k = 0; k < a.K; ++k) {
-    const int64_t r = (int64_t)w.s * a.K + k;
-    const int64_t ij = r * a.d + j;
-    T yv = T(0), al = T(0), bv = T(0);
-    if (w.on) {
-      yv = __ldg(a.y + (a.y_per_spec ? (int64_t)k : r) * a.d + j);
-      if (cls == 2) al = __ldg(a.alpha + ij);
-      if (slot >= 0) bv = __ldg(a.beta + r * a.M + slot);
+}
+template <int V, typename T>
+__device__ __forceinline__ void stv(T* p, const T (&o)[V]) {
+  if constexpr (V == 4 && sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) p[v] = o[v];
+  }
+}
+
+// Operand of the next GEMM for V neurons: tf32 high/low parts for the 3-pass
+// tf32 GEMM, bf16 for the bf16 GEMM, or the value itself.
+template <int V, typename Top, typename T>
+__device__ __forceinline__ void put_operand_v(Top* hi, float* lo, int64_t i, const T (&x)[V]) {
+  if constexpr (std::is_same<Top, float>::value && std::is_same<T, float>::value) {
+    if (lo) {
+      float h[V], l[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        h[v] = tf32_hi(x[v]);
+        l[v] = x[v] - h[v];
+      }
+      stv<V>(hi + i, h);
+      stv<V>(lo + i, l);
+    } else {
+      stv<V>(hi + i, x);
     }
-    T t, gg, sq;
-    cut_sums_row(a.csc, cc, a.gamma + r * a.N, a.N, w.c, w.lane, t, gg, sq);
+  } else if constexpr (std::is_same<Top, __nv_bfloat16>::value && V == 4) {
+    const __nv_bfloat162 p0 = __floats2bfloat162_rn(x[0], x[1]), p1 = __floats2bfloat162_rn(x[2], x[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<const uint32_t*>(&p0);
+    u.y = *reinterpret_cast<const uint32_t*>(&p1);
+    *reinterpret_cast<uint2*>(hi + i) = u;
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) hi[i + v] = cvt_out<Top>(x[v]);
+  }
+}
+
+// Bounds, class and split of the lane's V neurons.
+template <typename T, int V>
+struct SpanNeurons {
+  T lo[V], hi[V], bj[V], iv[V];
+  int cls[V];           // 0 inactive, 1 active, 2 unstable
+  int slot[V], sign[V]; // split slot of the row's subdomain on the neuron (-1 none)
+  bool unstable;        // any of the V neurons unstable
+  bool split;           // any of the V neurons split
+};
+template <typename T, int V>
+__device__ __forceinline__ void span_neurons(const SpanWarp<V>& w, const T* lo_, const T* hi_, const T* bias,
+                                             const T* inv_ul, const SplitsDev& sp, int M, int layer,
+                                             SpanNeurons<T, V>& n) {
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    n.lo[v] = n.hi[v] = n.bj[v] = n.iv[v] = T(0);
+    n.slot[v] = -1;
+    n.sign[v] = 0;
+  }
+  if (w.on) {
+    ldv<V>(lo_ + w.j0, n.lo);
+    ldv<V>(hi_ + w.j0, n.hi);
+    ldv<V>(bias + w.j0, n.bj);
+    if (inv_ul) {
+      ldv<V>(inv_ul + w.j0, n.iv);
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) n.iv[v] = n.hi[v] > n.lo[v] ? T(1) / (n.hi[v] - n.lo[v]) : T(0);
+    }
+  }
+  // splits of the subdomain: lane q inspects slot q (and 32 + q) of its row
+  // of the split table
+  for (int b0 = 0; b0 < M; b0 += 32) {
+    const int q = b0 + w.lane;
+    const int code = q < M ? __ldg(sp.tab + (int64_t)w.s * M + q) : -1;
+    const int lay = code >= 0 ? (code >> 24) : -1, idx = code & 0x7fffff, sg = (code >> 23) & 1 ? 1 : -1;
+    unsigned m = __ballot_sync(0xffffffffu, lay == layer && idx >= w.base && idx < w.base + 32 * V);
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      const int tj = __shfl_sync(0xffffffffu, idx, b) - w.base;
+      const int tsg = __shfl_sync(0xffffffffu, sg, b);
+      if (tj / V == w.lane) {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          if (tj % V == v) { n.slot[v] = b0 + b; n.sign[v] = tsg; }
+      }
+    }
+  }
+  n.unstable = false;
+  n.split = false;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    if (n.slot[v] >= 0) {
+      n.split = true;
+      if (n.sign[v] > 0) n.lo[v] = tmax(n.lo[v], T(0)); else n.hi[v] = tmin(n.hi[v], T(0));
+    }
+    n.cls[v] = n.hi[v] <= T(0) ? 0 : (n.lo[v] >= T(0) ? 1 : 2);
+    n.unstable |= w.on && n.cls[v] == 2;
+  }
+}
+
+// Cut entries of a span: contiguous in CSC order, sorted by (neuron, kind).
+// A batch is 32 consecutive entries, entry b0 + lane on lane `lane`; entries
+// of one (kind, neuron) form a run of lanes, and the run's first lane adds
+// the run's values (in lane order) to the per-warp shared accumulator of that
+// (kind, neuron). The first kSpanBatches batches stay in registers.
+constexpr int kSpanBatches = 3;
+template <typename T>
+struct SpanEntry {
+  int cut;      // cut id, -1 for no entry
+  int dest;     // kind * 32V + neuron - base
+  int run;      // length of the run this lane starts, 0 inside a run
+  int maxrun;   // longest run of the batch (warp-uniform)
+  T coef;
+};
+template <typename T, int V>
+__device__ __forceinline__ void span_entry(const CutCSC<T>& c, int N, int base, int b0, int ce, int lane,
+                                           SpanEntry<T>& en, DevErr& er) {
+  const int e = b0 + lane;
+  en.cut = -1;
+  en.coef = T(0);
+  en.dest = -1 - lane;   // lanes without an entry form runs of their own
+  if (e < ce) {
+    const int cut = __ldg(c.cut + e);
+    const int kind = __ldg(c.kind + e);
+    const int nl = __ldg(c.nrn + e) - base;
+    if (cut < 0 || cut >= N || kind < 0 || kind > 2 || nl < 0 || nl >= 32 * V) {
+      er.set(2, e, N);
+    } else {
+      en.cut = cut;
+      en.coef = __ldg(c.coef + e);
+      en.dest = kind * 32 * V + nl;
+    }
+  }
+  const int prev = __shfl_up_sync(0xffffffffu, en.dest, 1);
+  const bool cont = lane > 0 && prev == en.dest;
+  const unsigned cm = __ballot_sync(0xffffffffu, cont);
+  // run length: this lane plus the continuation lanes right after it
+  int len = 1;
+  if (lane < 31) {
+    const unsigned after = cm >> (lane + 1), all = 0xffffffffu >> (lane + 1);
+    len += after == all ? 31 - lane : __ffs(~after) - 1;
+  }
+  en.run = cont ? 0 : len;
+  en.maxrun = __reduce_max_sync(0xffffffffu, en.run);
+}
+template <typename T>
+struct SpanCuts {
+  int cb, ce;                       // the span's entries (warp-uniform)
+  SpanEntry<T> b[kSpanBatches];
+};
+template <typename T, int V>
+__device__ __forceinline__ void span_cuts(const CutCSC<T>& c, int N, int d, const SpanWarp<V>& w, SpanCuts<T>& sc,
+                                          DevErr& er) {
+  const int jb = min(w.base, d), je = min(w.base + 32 * V, d);
+  sc.cb = __ldg(c.ptr + jb);
+  sc.ce = __ldg(c.ptr + je);
+  if (sc.cb < 0 || sc.ce < sc.cb || (int64_t)sc.ce > c.n_total) {
+    er.set(1, w.c, c.n_total);
+    sc.cb = sc.ce = 0;
+  }
+#pragma unroll
+  for (int q = 0; q < kSpanBatches; ++q) span_entry<T, V>(c, N, w.base, sc.cb + 32 * q, sc.ce, w.lane, sc.b[q], er);
+}
+
+// acc[kind * 32V + neuron] += gamma-weighted entries of one batch; gv is
+// gamma[row, cut] of the lane's entry.
+template <typename T>
+__device__ __forceinline__ void span_batch_sum(const SpanEntry<T>& en, T gv, T* acc) {
+  T v = en.cut >= 0 ? en.coef * gv : T(0);
+  for (int q = 1; q < en.maxrun; ++q) {
+    const T u = __shfl_down_sync(0xffffffffu, v, q);
+    if (q < en.run) v += u;
+  }
+  if (en.run > 0 && en.cut >= 0) acc[en.dest] += v;
+  __syncwarp();
+}
+
+// Per-neuron cut sums of one row: t (x entries), g (xhat), s (z) of the
+// lane's V neurons. gam[32q + lane] holds gamma[row, cut] of the lane's entry
+// in cached batch q (staged ahead); later batches read the row grow. acc is
+// the warp's zeroed accumulator (3 * 32V), zeroed again on return.
+template <typename T, int V>
+__device__ __forceinline__ void span_cut_sums(const CutCSC<T>& c, const SpanCuts<T>& sc, int N,
+                                              const SpanWarp<V>& w, const T* gam, const T* grow, T* acc, T (&t)[V],
+                                              T (&g)[V], T (&s)[V], DevErr& er) {
+#pragma unroll
+  for (int v = 0; v < V; ++v) t[v] = g[v] = s[v] = T(0);
+  if (sc.cb == sc.ce) return;
+#pragma unroll
+  for (int q = 0; q < kSpanBatches; ++q)
+    if (sc.cb + 32 * q < sc.ce) span_batch_sum(sc.b[q], gam[32 * q + w.lane], acc);
+  for (int b0 = sc.cb + 32 * kSpanBatches; b0 < sc.ce; b0 += 32) {
+    SpanEntry<T> en;
+    span_entry<T, V>(c, N, w.base, b0, sc.ce, w.lane, en, er);
+    span_batch_sum(en, en.cut >= 0 ? (T)grow[en.cut] : T(0), acc);
+  }
+  T* a0 = acc + w.lane * V;
+  ldv_rw<V>(a0, t);
+  ldv_rw<V>(a0 + 32 * V, g);
+  ldv_rw<V>(a0 + 64 * V, s);
+  T z[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) z[v] = T(0);
+  stv<V>(a0, z);
+  stv<V>(a0 + 32 * V, z);
+  stv<V>(a0 + 64 * V, z);
+  __syncwarp();
+}
+
+// E[r, e] = coef_e * value of the entry's (kind, neuron): x -> vx, xhat -> vh,
+// z -> vz, e the entry's CSC position (a span's entries are contiguous, so a
+// batch is one coalesced store). ev is the warp's staging buffer (3 * 32V).
+template <typename T, int V>
+__device__ __forceinline__ void span_cut_writes(const CutCSC<T>& c, const SpanCuts<T>& sc, int N,
+                                                const SpanWarp<V>& w, const T (&vx)[V], const T (&vh)[V],
+                                                const T (&vz)[V], T* ev, T* Erow, DevErr& er) {
+  if (sc.cb == sc.ce) return;
+  T* a0 = ev + w.lane * V;
+  stv<V>(a0, vx);
+  stv<V>(a0 + 32 * V, vh);
+  stv<V>(a0 + 64 * V, vz);
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < kSpanBatches; ++q) {
+    const SpanEntry<T>& en = sc.b[q];
+    if (en.cut >= 0) Erow[sc.cb + 32 * q + w.lane] = en.coef * ev[en.dest];
+  }
+  for (int b0 = sc.cb + 32 * kSpanBatches; b0 < sc.ce; b0 += 32) {
+    SpanEntry<T> en;
+    span_entry<T, V>(c, N, w.base, b0, sc.ce, w.lane, en, er);
+    if (en.cut >= 0) Erow[b0 + w.lane] = en.coef * ev[en.dest];
+  }
+  __syncwarp();
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void span_zero(T* buf, int lane) {
+  T z[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) z[v] = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) stv<V>(buf + k * 32 * V + lane * V, z);
+  __syncwarp();
+}
+
+// Objective partial of the row: the span covers the 32-neuron partial slots
+// V*c .. V*c + V - 1 of its layer; the first gets the sum, the others 0.
+template <typename T, int V>
+__device__ __forceinline__ void span_partial(T* obj_part, int64_t R, int64_t r, int c, int d, int lane, T term) {
+  term = warp_sum(term);
+  const int slot = c * V + lane;
+  if (lane < V && slot < (d + 31) / 32) obj_part[(int64_t)slot * R + r] = lane == 0 ? term : T(0);
+}
+
+// ------------------------------------------------------------------ staging
+// The per-neuron kernels stream their rows through a kStages-deep pipeline of
+// asynchronous copies (cp.async) into the warp's shared memory: the dense
+// per-row operands of the lane's V neurons and the row's scattered values
+// (gamma of the cached cut batches, beta of the split slots). Each lane copies
+// and later reads only its own slots, so a lane waits only for its own copies.
+constexpr int kStages = 3;
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool pred) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = pred ? BYTES : 0;   // 0: no read, the slot is zero-filled
+  if constexpr (BYTES == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(BYTES), "r"(n)
+                 : "memory");
+  }
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Shared-memory layout of one warp (in elements of T): fixed buffers, then
+// kStages stages of ND dense rows of 32V, kSpanBatches x 32 gamma values and
+// NB x 32 beta values.
+template <int V, int ND, int NB, int NFIX>
+struct StageLayout {
+  static constexpr int SPAN = 32 * V;
+  static constexpr int STAGE = ND * SPAN + kSpanBatches * 32 + NB * 32;
+  static constexpr int WARP = NFIX * SPAN + kStages * STAGE;
+};
+
+// ------------------------------------------------------------------ eval
+template <typename T, typename Top, int V>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_eval(RelaxArgs<T, Top> a) {
+  using Lay = StageLayout<V, 2, V, 3>;   // dense: y, alpha; fixed: acc
+  constexpr int SPAN = Lay::SPAN, NS = kStages;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* wb = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * Lay::WARP;
+  T* acc = wb;
+  SpanWarp<V> w;
+  if (!span_warp<V>((int)(a.R / a.K), a.d, w)) return;
+  const int KR = (a.K + (int)gridDim.z - 1) / (int)gridDim.z;   // rows of this warp: [kb, ke)
+  const int kb = (int)blockIdx.z * KR, ke = min(a.K, kb + KR);
+  const T* dummy = a.y;
+  auto stage = [&](int st) { return wb + 3 * SPAN + st * Lay::STAGE; };
+  auto dense = [&](int k, int st) {
+    T* sb = stage(st) + w.lane * V;
+    const bool ok = k < ke && w.on;
+    const int64_t r = (int64_t)w.s * a.K + k;
+    cp_async<V * sizeof(T)>(sb, ok ? a.y + (a.y_per_spec ? (int64_t)k : r) * a.d + w.j0 : dummy, ok);
+    cp_async<V * sizeof(T)>(sb + SPAN, ok ? a.alpha + r * a.d + w.j0 : dummy, ok);
+  };
+  SpanNeurons<T, V> n;
+  DevErr er;
+  SpanCuts<T> sc;
+  auto scattered = [&](int k, int st) {
+    T* sb = stage(st) + 2 * SPAN;
+    const int64_t r = (int64_t)w.s * a.K + k;
+#pragma unroll
+    for (int q = 0; q < kSpanBatches; ++q) {
+      const bool ok = k < ke && sc.b[q].cut >= 0;
+      cp_async<sizeof(T)>(sb + 32 * q + w.lane, ok ? a.gamma + r * a.N + sc.b[q].cut : dummy, ok);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const bool ok = k < ke && w.on && n.slot[v] >= 0;
+      cp_async<sizeof(T)>(sb + kSpanBatches * 32 + 32 * v + w.lane, ok ? a.beta + r * a.M + n.slot[v] : dummy, ok);
+    }
+  };
+#pragma unroll
+  for (int st = 0; st < NS; ++st) dense(kb + st, st);
+  span_zero<T, V>(acc, w.lane);
+  span_neurons<T, V>(w, a.lo, a.hi, a.bias, a.inv_ul, a.sp, a.M, a.layer, n);
+  span_cuts<T, V>(a.csc, a.N, a.d, w, sc, er);
+#pragma unroll
+  for (int st = 0; st < NS; ++st) scattered(kb + st, st);
+  cp_commit();
+  for (int k = kb; k < ke; ++k) {
+    const int st = (k - kb) % NS;
+    // the prologue is one group (rows kb .. kb+NS-1); row k >= kb+NS is the
+    // group committed NS-1 groups ago
+    if (k == kb) cp_wait<0>();
+    else cp_wait<NS - 1>();
+    const T* sb = stage(st);
+    const int64_t r = (int64_t)w.s * a.K + k;
+    const int64_t ij = r * a.d + w.j0;
+    T t[V], gg[V], sq[V];
+    span_cut_sums<T, V>(a.csc, sc, a.N, w, sb + 2 * SPAN, a.gamma + r * a.N, acc, t, gg, sq, er);
     T term = T(0);
     if (w.on) {
-      if (slot >= 0) t += sign > 0 ? -bv : bv;   // split row -x <= 0 (x >= 0) or x <= 0
-      const T nh = yv - gg;
-      T nu;
-      if (cls == 0) {            // inactive: xhat = 0, z = 0
-        nu = -t;
-      } else if (cls == 1) {     // active: xhat = x, z = 1
-        nu = nh - t;
-        term = sq;
-      } else {                   // unstable: Lemma A.1 with q = -s
-        const T C = tmax(nh, T(0));
-        const T pi = tmin(tmax((hi * C - sq) * iv, T(0)), C);
-        term = lo * pi - tmax(T(0), hi * (C - pi) + lo * pi - sq);
-        nu = pi - al * tmax(-nh, T(0)) - t;
+      T yv[V], al[V], nu[V], nh[V];
+      ldv_rw<V>(sb + w.lane * V, yv);
+      ldv_rw<V>(sb + SPAN + w.lane * V, al);
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        if (n.slot[v] >= 0) {        // split row -x <= 0 (x >= 0) or x <= 0
+          const T b = sb[2 * SPAN + kSpanBatches * 32 + 32 * v + w.lane];
+          t[v] += n.sign[v] > 0 ? -b : b;
+        }
+        nh[v] = yv[v] - gg[v];
+        // unstable: Lemma A.1 with q = -s
+        const T C = tmax(nh[v], T(0));
+        const T pi = tmin(tmax((n.hi[v] * C - sq[v]) * n.iv[v], T(0)), C);
+        const T hu = n.lo[v] * pi - tmax(T(0), n.hi[v] * (C - pi) + n.lo[v] * pi - sq[v]);
+        const T nuu = pi - al[v] * tmax(-nh[v], T(0)) - t[v];
+        const int cl = n.cls[v];
+        nu[v] = cl == 2 ? nuu : (cl == 1 ? nh[v] - t[v] : -t[v]);   // active: xhat = x, z = 1
+        term += (cl == 2 ? hu : (cl == 1 ? sq[v] : T(0))) - nu[v] * n.bj[v];
       }
-      term -= nu * bj;
-      put_operand<Top>(a.nu_out, a.nu_lo, ij, nu);
-      a.nuhat_out[ij] = nh;
+      put_operand_v<V, Top>(a.nu_out, a.nu_lo, ij, nu);
+      stv<V>(a.nuhat_out + ij, nh);
     }
-    term = warp_sum(term);
-    if (w.lane == 0) a.obj_part[(int64_t)w.c * a.R + r] = term;
+    span_partial<T, V>(a.obj_part, a.R, r, w.c, a.d, w.lane, term);
+    dense(k + NS, st);
+    scattered(k + NS, st);
+    cp_commit();
   }
+  cp_wait<0>();
+  er.flush();
 }
 
 // ------------------------------------------------------------------ adjoint
-template <typename T, typename Top>
+// Writes dg/dbeta of every split slot whose neuron is in this layer into
+// g_beta (the gradient output, or the input of the beta step in the gather).
+template <typename T, typename Top, int V>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_adj(AdjArgs<T, Top> a) {
-  ChunkWarp w;
-  if (!chunk_warp((int)(a.R / a.K), a.d, w)) return;
-  const int j = w.j;
-  T lo = T(0), hi = T(0), bj = T(0), iv = T(0);
-  if (w.on) {
-    lo = __ldg(a.lo + j);
-    hi = __ldg(a.hi + j);
-    bj = __ldg(a.bias + j);
-    iv = a.inv_ul ? __ldg(a.inv_ul + j) : (hi > lo ? T(1) / (hi - lo) : T(0));
-  }
-  int sign = 0;
-  const int slot = lane_split(a.sp, w.s, a.M, a.layer, w.c, w.lane, sign);
-  if (slot >= 0) {
-    if (sign > 0) lo = tmax(lo, T(0)); else hi = tmin(hi, T(0));
-  }
-  const int cls = hi <= T(0) ? 0 : (lo >= T(0) ? 1 : 2);
-  ChunkCuts<T> cc;
-  chunk_cuts(a.csc, a.N, a.d, w.c, w.lane, cc);
-  for (int k = 0; k < a.K; ++k) {
+  using Lay = StageLayout<V, 5, 0, 6>;   // dense: nubar, nuhat, alpha, m, v; fixed: acc, ev
+  constexpr int SPAN = Lay::SPAN, NS = kStages;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* wb = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * Lay::WARP;
+  T* acc = wb;
+  T* ev = wb + 3 * SPAN;
+  SpanWarp<V> w;
+  if (!span_warp<V>((int)(a.R / a.K), a.d, w)) return;
+  const int KR = (a.K + (int)gridDim.z - 1) / (int)gridDim.z;   // rows of this warp: [kb, ke)
+  const int kb = (int)blockIdx.z * KR, ke = min(a.K, kb + KR);
+  const int mode = a.st.mode;
+  const T* dummy = a.nubar;
+  auto stage = [&](int st) { return wb + 6 * SPAN + st * Lay::STAGE; };
+  auto dense = [&](int k, int st) {
+    T* sb = stage(st) + w.lane * V;
+    const bool ok = k < ke && w.on;
+    const bool okm = ok && mode == 2;
+    const int64_t ij = ((int64_t)w.s * a.K + k) * a.d + w.j0;
+    cp_async<V * sizeof(T)>(sb, ok ? a.nubar + ij : dummy, ok);
+    cp_async<V * sizeof(T)>(sb + SPAN, ok ? a.nuhat + ij : dummy, ok);
+    cp_async<V * sizeof(T)>(sb + 2 * SPAN, ok ? a.alpha + ij : dummy, ok);
+    cp_async<V * sizeof(T)>(sb + 3 * SPAN, okm ? a.m_alpha + ij : dummy, okm);
+    cp_async<V * sizeof(T)>(sb + 4 * SPAN, okm ? a.v_alpha + ij : dummy, okm);
+  };
+  SpanNeurons<T, V> n;
+  DevErr er;
+  SpanCuts<T> sc;
+  auto scattered = [&](int k, int st) {
+    T* sb = stage(st) + 5 * SPAN;
     const int64_t r = (int64_t)w.s * a.K + k;
-    const int64_t ij = r * a.d + j;
-    const T wr = a.seed ? a.seed[r] : T(1);
-    T nbv = T(0), nh = T(0), al = T(0);
-    if (w.on) {
-      nbv = __ldg(a.nubar + ij);
-      if (cls == 2) {
-        nh = __ldg(a.nuhat + ij);
-        al = a.alpha[ij];
-      }
+#pragma unroll
+    for (int q = 0; q < kSpanBatches; ++q) {
+      const bool ok = k < ke && sc.b[q].cut >= 0;
+      cp_async<sizeof(T)>(sb + 32 * q + w.lane, ok ? a.gamma + r * a.N + sc.b[q].cut : dummy, ok);
     }
-    T t, gg, sq;
-    cut_sums_row(a.csc, cc, a.gamma + r * a.N, a.N, w.c, w.lane, t, gg, sq);
-    const T nb = nbv - wr * bj;   // dg/dnu^(i)
-    T dnu_dnh = T(0), dh_dnh = T(0), dnu_ds = T(0), dh_ds = T(0);
+  };
+#pragma unroll
+  for (int st = 0; st < NS; ++st) dense(kb + st, st);
+  span_zero<T, V>(acc, w.lane);
+  span_neurons<T, V>(w, a.lo, a.hi, a.bias, a.inv_ul, a.sp, a.M, a.layer, n);
+  span_cuts<T, V>(a.csc, a.N, a.d, w, sc, er);
+#pragma unroll
+  for (int st = 0; st < NS; ++st) scattered(kb + st, st);
+  cp_commit();
+  for (int k = kb; k < ke; ++k) {
+    const int st = (k - kb) % NS;
+    // the prologue is one group (rows kb .. kb+NS-1); row k >= kb+NS is the
+    // group committed NS-1 groups ago
+    if (k == kb) cp_wait<0>();
+    else cp_wait<NS - 1>();
+    const T* sb = stage(st);
+    const int64_t r = (int64_t)w.s * a.K + k;
+    const int64_t ij = r * a.d + w.j0;
+    const T wr = a.seed ? __ldg(a.seed + r) : T(1);
+    T t[V], gg[V], sq[V];
+    span_cut_sums<T, V>(a.csc, sc, a.N, w, sb + 5 * SPAN, a.gamma + r * a.N, acc, t, gg, sq, er);
+    T nbv[V], nh[V], al[V], ma[V], va[V];
+    ldv_rw<V>(sb + w.lane * V, nbv);
+    ldv_rw<V>(sb + SPAN + w.lane * V, nh);
+    ldv_rw<V>(sb + 2 * SPAN + w.lane * V, al);
+    ldv_rw<V>(sb + 3 * SPAN + w.lane * V, ma);
+    ldv_rw<V>(sb + 4 * SPAN + w.lane * V, va);
+    T dt[V], dnh[V], dnhn[V], ds[V], ga[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const T nb = nbv[v] - wr * n.bj[v];   // dg/dnu^(i)
+      const T h = nh[v], hi = n.hi[v], lo = n.lo[v], iv = n.iv[v];
+      // local derivatives of nu and of the objective term h by case
+      T dnu_dnh = T(0), dh_dnh = T(0), dnu_ds = T(0), dh_ds = T(0);
+      if (n.cls[v] == 1) {                       // active
+        dnu_dnh = T(1);
+        dh_ds = wr;
+      } else if (n.cls[v] == 2) {
+        const T p0 = (hi * h - sq[v]) * iv;
+        const bool pos = h > T(0);
+        const bool mid = pos && p0 > T(0) && p0 < h;          // pi* = p0
+        const bool top = pos && !(p0 < h);                    // pi* = C; h = s when l C - s > 0
+        dnu_dnh = mid ? hi * iv : (top ? T(1) : (h < T(0) ? al[v] : T(0)));
+        dh_dnh = mid ? wr * lo * hi * iv : T(0);
+        dnu_ds = mid ? -iv : T(0);
+        dh_ds = mid ? -wr * lo * iv
+                    : (top ? (lo * h - sq[v] > T(0) ? wr : T(0)) : (pos ? T(0) : (sq[v] < T(0) ? wr : T(0))));
+      }
+      ga[v] = n.cls[v] == 2 ? nb * (-tmax(-h, T(0))) : T(0);
+      dnh[v] = nb * dnu_dnh + dh_dnh;
+      dnhn[v] = -dnh[v];
+      ds[v] = nb * dnu_ds + dh_ds;
+      dt[v] = -nb;
+    }
     if (w.on) {
-      if (cls != 2) {
-        if (cls == 1) { dnu_dnh = T(1); dh_ds = wr; }     // active
-        if (a.st.mode == 0) a.g_alpha[ij] = T(0);
-      } else {
-        if (nh > T(0)) {
-          const T p0 = (hi * nh - sq) * iv;
-          if (p0 > T(0) && p0 < nh) {          // pi* = p0
-            dnu_dnh = hi * iv;
-            dh_dnh = wr * lo * hi * iv;
-            dnu_ds = -iv;
-            dh_ds = -wr * lo * iv;
-          } else if (p0 >= nh) {               // pi* = C, h = s when l C - s > 0
-            dnu_dnh = T(1);
-            dh_ds = (lo * nh - sq > T(0)) ? wr : T(0);
+      if (mode == 0) {
+        stv<V>(a.g_alpha + ij, ga);
+      } else if (n.unstable) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          if (n.cls[v] == 2) {
+            const T na = step_apply(a.st, al[v], ga[v], a.st.lr_a, ma[v], va[v]);
+            al[v] = tmin(tmax(na, T(0)), T(1));
           }
-        } else {
-          if (nh < T(0)) dnu_dnh = al;         // nu = alpha * nuhat
-          dh_ds = (sq < T(0)) ? wr : T(0);     // h = min(s, 0)
         }
-        const T g_alpha = nb * (-tmax(-nh, T(0)));
-        if (a.st.mode == 0) {
-          a.g_alpha[ij] = g_alpha;
-        } else {
-          T na = step_apply(a.st, al, g_alpha, a.st.lr_a, a.m_alpha ? a.m_alpha + ij : nullptr,
-                            a.v_alpha ? a.v_alpha + ij : nullptr);
-          a.alpha[ij] = tmin(tmax(na, T(0)), T(1));
+        stv<V>(a.alpha + ij, al);
+        if (mode == 2) {
+          stv<V>(a.m_alpha + ij, ma);
+          stv<V>(a.v_alpha + ij, va);
         }
       }
-    }
-    const T dg_dnh = nb * dnu_dnh + dh_dnh;
-    const T dg_ds = nb * dnu_ds + dh_ds;
-    const T dg_dt = -nb;
-    if (a.E) cut_writes_row(a.csc, cc, w.c, w.lane, dg_dt, dg_dnh, dg_ds, a.E + r * a.csc.n_total);
-    if (!w.on) continue;
-    if (a.a_out) put_operand<Top>(a.a_out, a.a_lo, ij, dg_dnh);
-    if (slot >= 0) {
-      const int64_t bi = r * a.M + slot;
-      const T gb = (sign > 0 ? T(-1) : T(1)) * dg_dt;
-      if (a.st.mode == 0) {
-        a.g_beta[bi] = gb;
-      } else {
-        T nbv2 = step_apply(a.st, a.beta[bi], gb, a.st.lr_b, a.m_beta ? a.m_beta + bi : nullptr,
-                            a.v_beta ? a.v_beta + bi : nullptr);
-        a.beta[bi] = tmax(nbv2, T(0));
+      if (a.a_out) put_operand_v<V, Top>(a.a_out, a.a_lo, ij, dnh);
+      if (n.split) {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          if (n.slot[v] >= 0) a.g_beta[r * a.M + n.slot[v]] = (n.sign[v] > 0 ? T(-1) : T(1)) * dt[v];
       }
     }
+    if (a.E) span_cut_writes<T, V>(a.csc, sc, a.N, w, dt, dnhn, ds, ev, a.E + r * a.csc.n_total, er);
+    dense(k + NS, st);
+    scattered(k + NS, st);
+    cp_commit();
   }
+  cp_wait<0>();
+  er.flush();
 }
 
 // ------------------------------------------------------------------ concretization
-template <typename T, typename Top>
+template <typename T, typename Top, int V>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_concretize(ConcArgs<T, Top> a) {
-  ChunkWarp w;
-  if (!chunk_warp((int)(a.R / a.K), a.d0, w)) return;
-  const int j = w.j;
-  T xl = T(0), xh = T(0);
-  if (w.on) {
-    xl = __ldg(a.x_lo + j);
-    xh = __ldg(a.x_hi + j);
-  }
-  ChunkCuts<T> cc;
-  chunk_cuts(a.csc, a.N, a.d0, w.c, w.lane, cc);
-  for (int k = 0; k < a.K; ++k) {
+  using Lay = StageLayout<V, 1, 0, 6>;   // dense: y0; fixed: acc, ev
+  constexpr int SPAN = Lay::SPAN, NS = kStages;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* wb = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * Lay::WARP;
+  T* acc = wb;
+  T* ev = wb + 3 * SPAN;
+  SpanWarp<V> w;
+  if (!span_warp<V>((int)(a.R / a.K), a.d0, w)) return;
+  const int KR = (a.K + (int)gridDim.z - 1) / (int)gridDim.z;   // rows of this warp: [kb, ke)
+  const int kb = (int)blockIdx.z * KR, ke = min(a.K, kb + KR);
+  const T* dummy = a.y0;
+  auto stage = [&](int st) { return wb + 6 * SPAN + st * Lay::STAGE; };
+  auto dense = [&](int k, int st) {
+    const bool ok = k < ke && w.on;
+    const int64_t ij = ((int64_t)w.s * a.K + k) * a.d0 + w.j0;
+    cp_async<V * sizeof(T)>(stage(st) + w.lane * V, ok ? a.y0 + ij : dummy, ok);
+  };
+  DevErr er;
+  SpanCuts<T> sc;
+  auto scattered = [&](int k, int st) {
+    T* sb = stage(st) + SPAN;
     const int64_t r = (int64_t)w.s * a.K + k;
-    const int64_t ij = r * a.d0 + j;
-    const T wr = a.seed ? a.seed[r] : T(1);
-    const T yv = w.on ? __ldg(a.y0 + ij) : T(0);
-    T h0, ug, us;
-    cut_sums_row(a.csc, cc, a.gamma + r * a.N, a.N, w.c, w.lane, h0, ug, us);   // layer 0: kind x only
-    const T c0 = -yv + h0;
-    const T xs = c0 > T(0) ? xl : (c0 < T(0) ? xh : T(0.5) * (xl + xh));
-    if (a.E) cut_writes_row(a.csc, cc, w.c, w.lane, wr * xs, T(0), T(0), a.E + r * a.csc.n_total);
-    T term = w.on ? tmin(c0 * xl, c0 * xh) : T(0);
-    if (w.on && a.a0_out) put_operand<Top>(a.a0_out, a.a0_lo, ij, -wr * xs);
-    term = warp_sum(term);
-    if (w.lane == 0) a.obj_part[(int64_t)w.c * a.R + r] = term;
+#pragma unroll
+    for (int q = 0; q < kSpanBatches; ++q) {
+      const bool ok = k < ke && sc.b[q].cut >= 0;
+      cp_async<sizeof(T)>(sb + 32 * q + w.lane, ok ? a.gamma + r * a.N + sc.b[q].cut : dummy, ok);
+    }
+  };
+#pragma unroll
+  for (int st = 0; st < NS; ++st) dense(kb + st, st);
+  span_zero<T, V>(acc, w.lane);
+  T xl[V], xh[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) xl[v] = xh[v] = T(0);
+  if (w.on) {
+    ldv<V>(a.x_lo + w.j0, xl);
+    ldv<V>(a.x_hi + w.j0, xh);
   }
+  span_cuts<T, V>(a.csc, a.N, a.d0, w, sc, er);
+#pragma unroll
+  for (int st = 0; st < NS; ++st) scattered(kb + st, st);
+  cp_commit();
+  for (int k = kb; k < ke; ++k) {
+    const int st = (k - kb) % NS;
+    // the prologue is one group (rows kb .. kb+NS-1); row k >= kb+NS is the
+    // group committed NS-1 groups ago
+    if (k == kb) cp_wait<0>();
+    else cp_wait<NS - 1>();
+    const T* sb = stage(st);
+    const int64_t r = (int64_t)w.s * a.K + k;
+    const int64_t ij = r * a.d0 + w.j0;
+    const T wr = a.seed ? __ldg(a.seed + r) : T(1);
+    T h0[V], ug[V], us[V];
+    span_cut_sums<T, V>(a.csc, sc, a.N, w, sb + SPAN, a.gamma + r * a.N, acc, h0, ug, us, er);   // layer 0: kind x
+    T yv[V];
+    ldv_rw<V>(sb + w.lane * V, yv);
+    T term = T(0), xs[V], a0[V], zero[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const T c0 = -yv[v] + h0[v];
+      const T x = c0 > T(0) ? xl[v] : (c0 < T(0) ? xh[v] : T(0.5) * (xl[v] + xh[v]));
+      xs[v] = wr * x;
+      a0[v] = -wr * x;
+      zero[v] = T(0);
+      if (w.on) term += tmin(c0 * xl[v], c0 * xh[v]);
+    }
+    if (a.E) span_cut_writes<T, V>(a.csc, sc, a.N, w, xs, zero, zero, ev, a.E + r * a.csc.n_total, er);
+    if (w.on && a.a0_out) put_operand_v<V, Top>(a.a0_out, a.a0_lo, ij, a0);
+    span_partial<T, V>(a.obj_part, a.R, r, w.c, a.d0, w.lane, term);
+    dense(k + NS, st);
+    scattered(k + NS, st);
+    cp_commit();
+  }
+  cp_wait<0>();
+  er.flush();
 }
 
-// g[r] = c_k^T b^(L) - gamma_r^T d + sum of the partials; one warp per row.
+// dynamic shared memory of one block of the span kernels
+template <typename T, int V, int ND, int NB, int NFIX>
+constexpr size_t span_smem() {
+  return (size_t)kWarpsPerBlock * StageLayout<V, ND, NB, NFIX>::WARP * sizeof(T);
+}
+
+// g[r] = c_k^T b^(L) - gamma_r^T d + sum of the partials. A warp takes 32
+// consecutive rows: lane i sums the partials of row r0 + i in slot order
+// (reads coalesced over rows), and the warp forms each row's gamma_r^T d.
 template <typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_finalize(FinalArgs<T> a) {
-  const int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  if (r >= a.R) return;
+  const int64_t r0 = ((int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * 32;
+  if (r0 >= a.R) return;
   const int lane = threadIdx.x & 31;
+  const int nr = (int)(a.R - r0 < 32 ? a.R - r0 : 32);
+  T gd = T(0);
+  if (a.N > 0) {
+    for (int i = 0; i < nr; ++i) {
+      T p = T(0);
+      for (int n = lane; n < a.N; n += 32) p += a.gamma[(r0 + i) * a.N + n] * a.d[n];
+      p = warp_sum(p);
+      if (lane == i) gd = p;
+    }
+  }
+  if (lane >= nr) return;
+  const int64_t r = r0 + lane;
   T g = T(0);
-  for (int n = lane; n < a.N; n += 32) g -= a.gamma[r * a.N + n] * a.d[n];
-  for (int q = lane; q < a.P; q += 32) g += a.obj_part[(int64_t)q * a.R + r];
-  g = warp_sum(g);
-  if (lane == 0) a.g[r] = g + a.cb[(int)(r % a.K)];
+  for (int q = 0; q < a.P; ++q) g += a.obj_part[(int64_t)q * a.R + r];
+  a.g[r] = g - gd + a.cb[(int)(r % a.K)];
 }
 
 // dg/dgamma_k = -d_k + sum of the cut's entry values (violation of cut k at the
-// primal point implied by the duals), then the projected step on gamma.
+// primal point implied by the duals), then the projected step on gamma. One
+// thread per (row, cut); the cut's entry positions in the row of E, then
+// their values, are read kGatherUnroll at a time.
+constexpr int kGatherUnroll = 8;
 template <typename T>
 __global__ void k_gather(GatherArgs<T> a) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.R * a.N) return;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.R * a.N) {
+    // threads past the cuts: the projected step on beta from dg/dbeta
+    // written by the adjoint (slots holding a split only)
+    i -= a.R * a.N;
+    if (i >= a.R * a.M) return;
+    const int64_t r = i / a.M;
+    const int q = (int)(i - r * a.M);
+    if (__ldg(a.sp_tab + (r / a.K) * a.M + q) < 0) return;
+    T m = T(0), v = T(0);
+    if (a.st.mode == 2) { m = a.m_beta[i]; v = a.v_beta[i]; }
+    const T x = step_apply(a.st, a.beta[i], a.g_beta[i], a.st.lr_b, m, v);
+    a.beta[i] = tmax(x, T(0));
+    if (a.st.mode == 2) { a.m_beta[i] = m; a.v_beta[i] = v; }
+    return;
+  }
   const int64_t r = i / a.N;
   const int n = (int)(i - r * a.N);
   if (a.cut_lo) {
@@ -483,22 +927,33 @@ __global__ void k_gather(GatherArgs<T> a) {
       return;
     }
   }
+  T x = T(0), m = T(0), v = T(0);
+  if (a.st.mode != 0) x = a.gamma[i];
+  if (a.st.mode == 2) { m = a.m_gamma[i]; v = a.v_gamma[i]; }
   const T w = a.seed ? a.seed[r] : T(1);
-  T grad = -w * a.d[n];
-  int e0 = a.cut_ptr[n], e1 = a.cut_ptr[n + 1];
+  int e0 = __ldg(a.cut_ptr + n), e1 = __ldg(a.cut_ptr + n + 1);
   if (e0 < 0 || e1 < e0 || (int64_t)e1 > a.nnz) { dev_error(5, n, a.nnz); e0 = e1 = 0; }
   const T* Er = a.E + r * a.nnz;
-  for (int e = e0; e < e1; ++e) {
-    const int q = __ldg(a.pos + e);
-    if (q < 0 || (int64_t)q >= a.nnz) { dev_error(5, e, a.nnz); continue; }
-    grad += Er[q];
+  T grad = -w * __ldg(a.d + n);
+  for (int e = e0; e < e1; e += kGatherUnroll) {
+    int q_[kGatherUnroll];
+#pragma unroll
+    for (int q = 0; q < kGatherUnroll; ++q) {
+      q_[q] = e + q < e1 ? __ldg(a.pos + e + q) : -1;
+      if (q_[q] >= 0 && (int64_t)q_[q] >= a.nnz) { dev_error(5, e + q, a.nnz); q_[q] = -1; }
+    }
+    T ev[kGatherUnroll];
+#pragma unroll
+    for (int q = 0; q < kGatherUnroll; ++q) ev[q] = q_[q] >= 0 ? Er[q_[q]] : T(0);
+#pragma unroll
+    for (int q = 0; q < kGatherUnroll; ++q) grad += ev[q];
   }
   if (a.st.mode == 0) {
     a.g_gamma[i] = grad;
   } else {
-    T x = step_apply(a.st, a.gamma[i], grad, a.st.lr_g, a.m_gamma ? a.m_gamma + i : nullptr,
-                     a.v_gamma ? a.v_gamma + i : nullptr);
+    x = step_apply(a.st, x, grad, a.st.lr_g, m, v);
     a.gamma[i] = tmax(x, T(0));
+    if (a.st.mode == 2) { a.m_gamma[i] = m; a.v_gamma[i] = v; }
   }
 }
 
@@ -702,11 +1157,36 @@ inline int flat_grid(int64_t n) {
 template <typename T>
 const char* tsfx() { return sizeof(T) == 8 ? "f64" : "f32"; }
 
+// Neurons per lane of the span kernels: 4 (16-byte vectors) for float chains
+// on layers whose width is a multiple of 4, else 1.
+template <typename T>
+inline bool span_v4(int d) { return sizeof(T) == 4 && d % 4 == 0; }
+inline int row_split(int) { return 1; }   // one warp takes all K rows of its subdomain
+inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+// Launch a span kernel with its dynamic shared memory (the opt-in above 48 KB
+// is set once per kernel).
+template <typename Kern, typename Args>
+void launch_span(Kern kern, size_t smem, dim3 grid, cudaStream_t st, const Args& a) {
+  static bool attr = false;   // one static per kernel instantiation
+  if (!attr) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  kern<<<grid, kWarpsPerBlock * 32, smem, st>>>(a);
+}
+inline dim3 span_blocks(int64_t R, int K, int d, int V) {
+  const int64_t S = R / K;
+  return dim3((unsigned)((S + kWarpsPerBlock - 1) / kWarpsPerBlock), (unsigned)((d + 32 * V - 1) / (32 * V)),
+              (unsigned)row_split(K));
+}
+
 // host-side extent checks shared by the launchers
-inline bool chk_splits(const SplitsDev& sp, int64_t R, int K) {
+inline bool chk_splits(const SplitsDev& sp, int64_t R, int K, int M = 0) {
   const double S = K > 0 ? (double)(R / K) : 0.0;
   return reg_check(sp.ptr, (S + 1) * 4.0, "split ptr") & reg_check(sp.layer, sp.n * 2.0, "split layer") &
-         reg_check(sp.index, sp.n * 4.0, "split index") & reg_check(sp.sign, (double)sp.n, "split sign");
+         reg_check(sp.index, sp.n * 4.0, "split index") & reg_check(sp.sign, (double)sp.n, "split sign") &
+         reg_check(sp.tab, M > 0 ? S * M * 4.0 : 0.0, "split table");
 }
 template <typename T>
 inline bool chk_csc(const CutCSC<T>& c, int d) {
@@ -729,13 +1209,21 @@ void relax_eval(cudaStream_t st, const RelaxArgs<T, Top>& a) {
         reg_check(a.lo, a.d * tb, "lo") & reg_check(a.hi, a.d * tb, "hi") & reg_check(a.bias, a.d * tb, "bias") &
         reg_check(a.inv_ul, a.inv_ul ? a.d * tb : 0.0, "inv_ul") &
         reg_check(a.alpha, Rd * tb, "alpha") & reg_check(a.beta, (double)a.M * a.R * tb, "beta") &
-        reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") & chk_splits(a.sp, a.R, a.K) &
+        reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") & chk_splits(a.sp, a.R, a.K, a.M) &
         chk_csc(a.csc, a.d) & reg_check(a.nu_out, Rd * sizeof(Top), "nu out") &
         reg_check(a.nu_lo, a.nu_lo ? Rd * 4.0 : 0.0, "nu lo") &
         reg_check(a.nuhat_out, Rd * tb, "nuhat out") & reg_check(a.obj_part, ((a.d + 31) / 32) * (double)a.R * tb, "obj part")))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
-  k_relax_eval<T, Top><<<chunk_blocks(a.R, a.K, a.d), kWarpsPerBlock * 32, 0, st>>>(a);
+  if constexpr (sizeof(T) == 4) {
+    if (span_v4<T>(a.d) && al16(a.y) && al16(a.alpha) && al16(a.lo) && al16(a.hi) && al16(a.bias) &&
+        al16(a.inv_ul) && al16(a.nu_out) && al16(a.nu_lo) && al16(a.nuhat_out)) {
+      launch_span(k_relax_eval<T, Top, 4>, span_smem<T, 4, 2, 4, 3>(), span_blocks(a.R, a.K, a.d, 4), st, a);
+      prof_end(st, tk);
+      return;
+    }
+  }
+  launch_span(k_relax_eval<T, Top, 1>, span_smem<T, 1, 2, 1, 3>(), span_blocks(a.R, a.K, a.d, 1), st, a);
   prof_end(st, tk);
 }
 template <typename T, typename Top>
@@ -743,27 +1231,39 @@ void relax_adjoint(cudaStream_t st, const AdjArgs<T, Top>& a) {
   if (a.R <= 0 || a.d <= 0) return;
   char nm[48];
   snprintf(nm, sizeof nm, "relax_adj_%s%s", tsfx<T>(), sizeof(Top) == 2 ? "_bf16" : "");
-  const double bytes = (double)a.R * a.d * (4.0 * sizeof(T) + (a.a_out ? sizeof(Top) : 0)) +
+  // per (row, neuron): nubar and nuhat read; alpha read and either its
+  // gradient written (mode 0) or alpha written back (PGA) together with both
+  // Adam moments read and written; a written for the next GEMM. Per cut entry
+  // and row: gamma read, E written.
+  const double per_elem = a.st.mode == 0 ? 4.0 : (a.st.mode == 1 ? 4.0 : 8.0);
+  const double bytes = (double)a.R * a.d * (per_elem * sizeof(T) + (a.a_out ? sizeof(Top) : 0)) +
                        (double)a.R * a.csc.n_entries * 2.0 * sizeof(T);
   const double Rd = (double)a.R * a.d, tb = sizeof(T);
   const bool m0 = a.st.mode == 0, m2 = a.st.mode == 2;
   if (!(reg_check(a.nubar, Rd * tb, "nubar") & reg_check(a.seed, a.seed ? a.R * tb : 0.0, "seed") &
         reg_check(a.lo, a.d * tb, "lo") & reg_check(a.hi, a.d * tb, "hi") & reg_check(a.bias, a.d * tb, "bias") &
         reg_check(a.inv_ul, a.inv_ul ? a.d * tb : 0.0, "inv_ul") &
-        reg_check(a.alpha, Rd * tb, "alpha") & reg_check(a.beta, (double)a.M * a.R * tb, "beta") &
+        reg_check(a.alpha, Rd * tb, "alpha") &
         reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") &
-        reg_check(a.nuhat, Rd * tb, "nuhat") & chk_splits(a.sp, a.R, a.K) & chk_csc(a.csc, a.d) &
+        reg_check(a.nuhat, Rd * tb, "nuhat") & chk_splits(a.sp, a.R, a.K, a.M) & chk_csc(a.csc, a.d) &
         reg_check(a.a_out, a.a_out ? Rd * sizeof(Top) : 0.0, "a out") &
         reg_check(a.a_lo, (a.a_out && a.a_lo) ? Rd * 4.0 : 0.0, "a lo") &
         reg_check(a.E, a.csc.n_entries ? (double)a.csc.n_total * a.R * tb : 0.0, "E") &
         reg_check(a.g_alpha, m0 ? Rd * tb : 0.0, "g_alpha") &
-        reg_check(a.g_beta, m0 ? (double)a.M * a.R * tb : 0.0, "g_beta") &
-        reg_check(a.m_alpha, m2 ? Rd * tb : 0.0, "m_alpha") & reg_check(a.v_alpha, m2 ? Rd * tb : 0.0, "v_alpha") &
-        reg_check(a.m_beta, m2 ? (double)a.M * a.R * tb : 0.0, "m_beta") &
-        reg_check(a.v_beta, m2 ? (double)a.M * a.R * tb : 0.0, "v_beta")))
+        reg_check(a.g_beta, a.M > 0 ? (double)a.M * a.R * tb : 0.0, "g_beta") &
+        reg_check(a.m_alpha, m2 ? Rd * tb : 0.0, "m_alpha") & reg_check(a.v_alpha, m2 ? Rd * tb : 0.0, "v_alpha")))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
-  k_relax_adj<T, Top><<<chunk_blocks(a.R, a.K, a.d), kWarpsPerBlock * 32, 0, st>>>(a);
+  if constexpr (sizeof(T) == 4) {
+    if (span_v4<T>(a.d) && al16(a.nubar) && al16(a.nuhat) && al16(a.alpha) && al16(a.m_alpha) &&
+        al16(a.v_alpha) && al16(a.g_alpha) && al16(a.lo) && al16(a.hi) && al16(a.bias) && al16(a.inv_ul) &&
+        al16(a.a_out) && al16(a.a_lo)) {
+      launch_span(k_relax_adj<T, Top, 4>, span_smem<T, 4, 5, 0, 6>(), span_blocks(a.R, a.K, a.d, 4), st, a);
+      prof_end(st, tk);
+      return;
+    }
+  }
+  launch_span(k_relax_adj<T, Top, 1>, span_smem<T, 1, 5, 0, 6>(), span_blocks(a.R, a.K, a.d, 1), st, a);
   prof_end(st, tk);
 }
 template <typename T, typename Top>
@@ -783,7 +1283,14 @@ void concretize(cudaStream_t st, const ConcArgs<T, Top>& a) {
         reg_check(a.obj_part, ((a.d0 + 31) / 32) * (double)a.R * tb, "obj part")))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
-  k_concretize<T, Top><<<chunk_blocks(a.R, a.K, a.d0), kWarpsPerBlock * 32, 0, st>>>(a);
+  if constexpr (sizeof(T) == 4) {
+    if (span_v4<T>(a.d0) && al16(a.y0) && al16(a.x_lo) && al16(a.x_hi) && al16(a.a0_out) && al16(a.a0_lo)) {
+      launch_span(k_concretize<T, Top, 4>, span_smem<T, 4, 1, 0, 6>(), span_blocks(a.R, a.K, a.d0, 4), st, a);
+      prof_end(st, tk);
+      return;
+    }
+  }
+  launch_span(k_concretize<T, Top, 1>, span_smem<T, 1, 1, 0, 6>(), span_blocks(a.R, a.K, a.d0, 1), st, a);
   prof_end(st, tk);
 }
 template <typename T>
@@ -796,25 +1303,32 @@ void finalize_bound(cudaStream_t st, const FinalArgs<T>& a) {
     return;
   int tk = prof_begin(st, sizeof(T) == 8 ? "finalize_f64" : "finalize_f32", 0.0,
                       (double)a.R * (a.N + a.P + 1) * sizeof(T));
-  k_finalize<T><<<row_blocks(a.R), kWarpsPerBlock * 32, 0, st>>>(a);
+  k_finalize<T><<<row_blocks((a.R + 31) / 32), kWarpsPerBlock * 32, 0, st>>>(a);
   prof_end(st, tk);
 }
 template <typename T>
 void gather_gamma(cudaStream_t st, const GatherArgs<T>& a) {
-  if (a.R <= 0 || a.N <= 0) return;
-  const double tb = sizeof(T), NR = (double)a.N * a.R;
+  const int64_t nb = a.st.mode != 0 ? a.R * a.M : 0;   // beta steps (modes 1 and 2)
+  if (a.R <= 0 || (a.N <= 0 && nb == 0)) return;
+  const double tb = sizeof(T), NR = (double)a.N * a.R, MR = (double)nb;
   const bool m0 = a.st.mode == 0, m2 = a.st.mode == 2;
-  if (!(reg_check(a.cut_ptr, (a.N + 1) * 4.0, "cut ptr") & reg_check(a.pos, a.nnz * 4.0, "cut pos") &
+  if (!(reg_check(a.cut_ptr, a.N > 0 ? (a.N + 1) * 4.0 : 0.0, "cut ptr") & reg_check(a.pos, a.nnz * 4.0, "cut pos") &
         reg_check(a.E, (double)a.nnz * a.R * tb, "E") &
         reg_check(a.d, a.N * tb, "d") & reg_check(a.seed, a.seed ? a.R * tb : 0.0, "seed") &
         reg_check(a.gamma, NR * tb, "gamma") & reg_check(a.g_gamma, m0 ? NR * tb : 0.0, "g_gamma") &
         reg_check(a.m_gamma, m2 ? NR * tb : 0.0, "m_gamma") & reg_check(a.v_gamma, m2 ? NR * tb : 0.0, "v_gamma") &
         reg_check(a.cut_lo, a.cut_lo ? (double)(a.R / a.K) * 4.0 : 0.0, "cut lo") &
-        reg_check(a.cut_hi, a.cut_hi ? (double)(a.R / a.K) * 4.0 : 0.0, "cut hi")))
+        reg_check(a.cut_hi, a.cut_hi ? (double)(a.R / a.K) * 4.0 : 0.0, "cut hi") &
+        reg_check(a.sp_tab, MR * 4.0 / a.K, "split table") & reg_check(a.beta, MR * tb, "beta") &
+        reg_check(a.g_beta, MR * tb, "g_beta") & reg_check(a.m_beta, m2 ? MR * tb : 0.0, "m_beta") &
+        reg_check(a.v_beta, m2 ? MR * tb : 0.0, "v_beta")))
     return;
+  // E read; gamma read and written (and both Adam moments read and written);
+  // the same for beta
   int tk = prof_begin(st, sizeof(T) == 8 ? "gather_gamma_f64" : "gather_gamma_f32", 0.0,
-                      (double)a.R * (a.nnz + 2.0 * a.N) * sizeof(T));
-  k_gather<T><<<(unsigned)((a.R * a.N + 255) / 256), 256, 0, st>>>(a);
+                      ((double)a.R * a.nnz + (m2 ? 6.0 : 2.0) * (NR + MR)) * sizeof(T));
+  const int64_t n = a.R * a.N + nb;
+  k_gather<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
   prof_end(st, tk);
 }
 template <typename Td>
@@ -826,7 +1340,7 @@ void certify_relax(cudaStream_t st, const CertArgs<Td>& a) {
   if (!(reg_check(a.y, yr * 8.0, "cert y") & reg_check(a.yabs, yr * 4.0, "cert yabs") &
         reg_check(a.lo, a.d * 8.0, "lo") & reg_check(a.hi, a.d * 8.0, "hi") & reg_check(a.bias, a.d * 8.0, "bias") &
         reg_check(a.alpha, Rd * tb, "alpha") & reg_check(a.beta, (double)a.M * a.R * tb, "beta") &
-        reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") & chk_splits(a.sp, a.R, a.K) &
+        reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") & chk_splits(a.sp, a.R, a.K, a.M) &
         chk_csc(a.csc, a.d) & reg_check(a.nu_out, Rd * 8.0, "cert nu") &
         reg_check(a.obj_part, ((a.d + 31) / 32) * (double)a.R * 8.0, "cert part")))
     return;
