@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--n-sub", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-all", action="store_true", help="print every kernel's share (untimed step)")
+    ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving stream (0: skip)")
+    ap.add_argument("--no-bf16-form", action="store_true", help="skip the BF16-chain form of the workload")
     return ap.parse_args()
 
 
@@ -204,6 +206,84 @@ def run_reference(a):
     print(json.dumps(line))
 
 
+# --------------------------------------------------------------------------- serving stream
+SERVE_SEED = 2208057405
+
+
+def serving_bench(dev, n_requests, rate=200.0, rounds=10, iters=20, max_inflight=16):
+    """Serving stream: Poisson arrivals (mean `rate` requests/s) mixing the
+    MLP 8-16-16-3, MLP 784-256x6-10 and CNN networks; each request holds
+    1-2048 subdomains (log-uniform) and one of five cut sets of 0-2000 cuts,
+    admitted under a 100 GB device-memory budget, optimised for `rounds`
+    branch-and-bound rounds of `iters` Adam steps in the BF16 chain and
+    certified in FP64 every round."""
+    import numpy as np
+    from paper_2208_05740_gb300 import gcp, synth
+    rng = np.random.default_rng(SERVE_SEED)
+    nets = [
+        (synth.mlp_small(n_sub=1, n_cuts=0), (0, 2), dict(min_vars=2, max_vars=4, hidden_only=True)),
+        (synth.mlp_256x6(n_sub=1, n_cuts=0), (1, 8),
+         dict(min_vars=2, max_vars=8, span_layers=True, need_z=True, p_input=0.99)),
+        (synth.cnn_cifar(n_sub=1, n_cuts=0), (1, 12),
+         dict(min_vars=2, max_vars=16, span_layers=True, need_z=True, p_input=0.99)),
+    ]
+    cut_counts = (0, 500, 1000, 1500, 2000)
+    ctx = gcp.Context(dev, hbm_budget_bytes=100 << 30)
+    loaded = []
+    for inst, srange, cargs in nets:
+        net_id = ctx.init_net(inst.net.layers, inst.x_lo, inst.x_hi, inst.spec, inst.inter_lo, inst.inter_hi)
+        sets = []
+        for n in cut_counts:
+            if n == 0:
+                sets.append(-1)
+                continue
+            c = synth.make_cuts(rng, inst.net, inst.inter_lo, inst.inter_hi, inst.x_lo, inst.x_hi, n, **cargs)
+            sets.append(ctx.add_cuts(net_id, c.ptr, c.layer, c.kind, c.index, c.coef, c.d)[0])
+        loaded.append((inst, net_id, sets, srange))
+    reqs = []
+    t = 0.0
+    for q in range(n_requests):
+        t += float(rng.exponential(1.0 / rate))
+        inst, net_id, sets, srange = loaded[int(rng.integers(0, len(loaded)))]
+        n_sub = int(round(float(np.exp(rng.uniform(0.0, np.log(2048.0))))))
+        sub = synth.make_subdomains(rng, inst.inter_lo, inst.inter_hi, n_sub, *srange)
+        reqs.append((t, inst, net_id, sets[int(rng.integers(0, len(sets)))], sub))
+    params = gcp.opt_params(iters, gcp.GCP_ADAM, gcp.GCP_BF16, 1, 0.1, 0.02, 0.02, 0.98)
+    ctx.serve_start(max_inflight)
+    tickets = []
+    t0 = time.perf_counter()
+    for q, (ta, inst, net_id, cs, sub) in enumerate(reqs):
+        dt = ta - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(ctx.serve_submit(net_id, cs, sub, params, rounds, SERVE_SEED + q))
+    lat, rows_total, subs_total, errs, rel = [], 0, 0, [], []
+    for (ta, inst, net_id, cs, sub), tk in zip(reqs, tickets):
+        res, out = ctx.serve_wait(tk, sub.n * inst.spec.shape[0] + 8)
+        if res.status != 0:
+            raise RuntimeError(f"serving request failed with status {res.status}")
+        lat.append(res.latency_ms)
+        rows_total += res.rows
+        subs_total += sub.n
+        errs.append(res.max_err_vs_fp64)
+        rel.append(res.max_err_vs_fp64 / max(1.0, float(np.min(np.abs(out))) if len(out) else 1.0))
+    wall = time.perf_counter() - t0
+    ctx.serve_stop()
+    ctx.close()
+    lat = np.array(lat)
+    return {
+        "workload": "serving stream: MLP 8-16-16-3 / MLP 784-256x6-10 / CNN 3x32x32-c32-c64-fc512-fc10 mix",
+        "requests": n_requests, "arrival_rate_per_s": rate, "rounds": rounds, "iters_per_round": iters,
+        "subdomains_per_request": "1-2048 log-uniform", "cuts_per_request": list(cut_counts),
+        "chain": "bf16", "certify": "fp64_outward_rounded", "hbm_budget_gb": 100, "max_inflight": max_inflight,
+        "certified_subdomain_bounds_per_s": subs_total * rounds / wall,
+        "requests_per_s": n_requests / wall, "wall_s": wall,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(lat.max())},
+        "max_err_vs_fp64": float(np.max(errs)),
+    }
+
+
 # --------------------------------------------------------------------------- GPU arm
 def main():
     a = parse()
@@ -325,6 +405,35 @@ def main():
                      "share_of_step": rep[dominant][2] / total_ms},
         "clocks": clocks,
     }
+    if not a.no_bf16_form:
+        # the same workload with the BF16 chain (tensor-core bf16 GEMMs, FP32
+        # accumulation) and the same FP64 certification: throughput and the
+        # certified bound quality beside the FP32 chain's
+        pb = gcp.opt_params(a.iters, gcp.GCP_ADAM, gcp.GCP_BF16 if prec == gcp.GCP_FP32 else gcp.GCP_FP32, 1,
+                            0.1, 0.02, 0.02, 0.98)
+        for _ in range(2):
+            ctx.duals_import(D)
+            ctx.optimize_batch(D, pb)
+        tb = []
+        for _ in range(max(3, a.steps // 2)):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.duals_import(D)
+            _, cert_b, err_b = ctx.optimize_batch(D, pb)
+            e1.record(stream)
+            e1.synchronize()
+            tb.append(e0.elapsed_time(e1))
+        other = "bf16" if prec == gcp.GCP_FP32 else "fp32"
+        line["forms"] = {
+            line["dtype"]: {"value": value, "mean_certified": float(np.mean(cert)), "ms_per_step": float(np.mean(times))},
+            other: {"value": a.n_sub * 1000.0 / float(np.mean(tb)), "mean_certified": float(np.mean(cert_b)),
+                    "ms_per_step": float(np.mean(tb)), "max_err_vs_fp64": float(np.max(err_b)),
+                    "rows_certified_at_least_as_high": float(np.mean(cert_b >= cert - 1e-6 * np.maximum(1, np.abs(cert))))},
+        }
+    if a.serve_requests > 0 and world == 1:
+        line["serving"] = serving_bench(dev, a.serve_requests)
     if world == 1 and not a.no_cpu_baseline:
         v, desc = oracle_sample(inst, 4, a.iters)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
