@@ -269,6 +269,42 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
       UP(wt32h, float, hi.data(), nw);
       UP(wt32l, float, lo.data(), nw);
     }
+    __nv_bfloat16 *cf16 = nullptr, *ct16 = nullptr;
+    int cfk = 0, cfn = 0, ctk = 0, ctn = 0;
+    if (g.kind != GCP_DENSE) {
+      // columns by the convolution plan of each direction (phases, taps,
+      // source channel padded to 8), rows = output channels padded to 16
+      auto pack = [&](bool transposed, int& kp, int& np_) {
+        ConvPlan cp;
+        std::vector<double> p;
+        if (!conv_plan(g, transposed ? 1 : 0, cp)) { kp = np_ = 0; return to_bf16(p.data(), 0); }
+        kp = cp.Kp;
+        np_ = cp.Np;
+        p.assign((size_t)np_ * kp, 0.0);
+        const int step = transposed ? g.stride : 1;
+        for (int q = 0; q < cp.nph; ++q) {
+          const ConvPhase& f = cp.f[q];
+          for (int a = 0; a < f.nkh; ++a)
+            for (int b = 0; b < f.nkw; ++b) {
+              const int kh = f.rh + step * a, kw = f.rw + step * b;
+              const size_t col0 = (size_t)f.kb0 * 64 + (size_t)(a * f.nkw + b) * cp.Csp;
+              for (int o = 0; o < g.c_out; ++o)
+                for (int ci = 0; ci < g.c_in; ++ci) {
+                  const double w = d.W[(((size_t)o * g.c_in + ci) * g.k + kh) * g.k + kw];
+                  const int n = transposed ? ci : o, c = transposed ? o : ci;
+                  p[(size_t)n * kp + col0 + c] = w;
+                }
+            }
+        }
+        return to_bf16(p.data(), p.size());
+      };
+      auto pf = pack(false, cfk, cfn);
+      if (!pf.empty()) UP(cf16, __nv_bfloat16, pf.data(), pf.size());
+      auto pt = pack(true, ctk, ctn);
+      if (!pt.empty()) UP(ct16, __nv_bfloat16, pt.data(), pt.size());
+    }
+    net->CF16.push_back(cf16); net->CT16.push_back(ct16);
+    net->cf_kp.push_back(cfk); net->cf_np.push_back(cfn); net->ct_kp.push_back(ctk); net->ct_np.push_back(ctn);
     UP(b64, double, d.b, g.d_out);
     auto bf = to_f32(d.b, g.d_out);
     UP(b32, float, bf.data(), g.d_out);
@@ -766,6 +802,11 @@ static void lin_backward(cudaStream_t st, const Batch& b, int i, const Top* nu, 
   if constexpr (!std::is_same<T, double>::value) {
     if (tc_bwd<Top>(b, i) && TcOps<Top>::bwd(st, net, i, b.R, nu, nu_lo, y)) return;
   }
+  if constexpr (std::is_same<Top, __nv_bfloat16>::value) {
+    if (g.kind != GCP_DENSE && b.tc &&
+        conv_tc_bf16(st, b.R, g, 1, net.CT16[i - 1], net.ct_kp[i - 1], net.ct_np[i - 1], nu, y))
+      return;
+  }
   if (g.kind == GCP_DENSE) gemm_nt<Top, T>(st, b.R, g.d_in, g.d_out, nu, 0, WSel<Top>::WT(net, i), y);
   else conv_T<Top, T>(st, b.R, g, WSel<Top>::W(net, i), nu, y);
 }
@@ -776,6 +817,11 @@ static void lin_forward(cudaStream_t st, const Batch& b, int i, const Top* a, co
   const LayerGeom& g = net.geom[i - 1];
   if constexpr (!std::is_same<T, double>::value) {
     if (tc_fwd<Top>(b, i) && TcOps<Top>::fwd(st, net, i, b.R, a, a_lo, out)) return;
+  }
+  if constexpr (std::is_same<Top, __nv_bfloat16>::value) {
+    if (g.kind != GCP_DENSE && b.tc &&
+        conv_tc_bf16(st, b.R, g, 0, net.CF16[i - 1], net.cf_kp[i - 1], net.cf_np[i - 1], a, out))
+      return;
   }
   if (g.kind == GCP_DENSE) gemm_nt<Top, T>(st, b.R, g.d_out, g.d_in, a, 0, WSel<Top>::W(net, i), out);
   else conv_fwd<Top, T>(st, b.R, g, WSel<Top>::W(net, i), a, out);

@@ -26,6 +26,10 @@ struct Net {
   std::vector<float*> W32, WT32, b32;
   std::vector<__nv_bfloat16*> W16, WT16;
   std::vector<float*> W32hi, W32lo, WT32hi, WT32lo;  // tf32 split of the dense weights
+  // convolution weights packed for the tensor-core implicit GEMM (bf16):
+  // forward [cf_np, cf_kp] and transposed [ct_np, ct_kp]; nullptr for dense layers
+  std::vector<__nv_bfloat16*> CF16, CT16;
+  std::vector<int> cf_kp, cf_np, ct_kp, ct_np;
   double *xlo64 = nullptr, *xhi64 = nullptr;
   float *xlo32 = nullptr, *xhi32 = nullptr;
   double *C64 = nullptr, *negC64 = nullptr, *bL64 = nullptr;

@@ -227,6 +227,64 @@ bool gemm_tc_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16*
 bool gemm_tc_tf32x3(cudaStream_t st, int64_t M, int N, int K, const float* A, const float* Alo, const float* B,
                     const float* Blo, float* C);
 std::string take_tc_error(cudaStream_t st);
+// Phase plan of the tensor-core convolution. dir 0 (out = conv(src)) is one
+// phase: every output pixel, all k*k taps. dir 1 (out = conv^T(src), stride
+// s) splits the output pixels into s*s phases (ph, pw): pixels ih = ph + s*i,
+// iw = pw + s*j, reached only by the taps kh = rh + s*a, kw = rw + s*b with
+// rh = (ph + pad) mod s, rw = (pw + pad) mod s, from source pixel
+// ((ih + pad - kh) / s, (iw + pad - kw) / s). Phase f's weight columns are
+// k-blocks kb0 .. kb0 + nkb - 1 of the packed weight: k = (kb0 * 64) +
+// (a * nkw + b) * Csp + c, c the source channel (Csp = channels padded to 8).
+constexpr int kMaxConvPhases = 16;
+struct ConvPhase {
+  int ph, pw, Hf, Wf;        // the phase's output pixels form an Hf x Wf grid
+  int rh, rw, nkh, nkw;      // its taps
+  int kb0, nkb;              // its weight k-blocks
+};
+struct ConvPlan {
+  int dir, Cs, Hs, Ws, Csp;  // source map
+  int Co, Ho, Wo;            // output map
+  int k, stride, pad;
+  int nph, Kp, Np;           // phases, packed weight [Np, Kp]
+  ConvPhase f[kMaxConvPhases];
+};
+__host__ __device__ inline bool conv_plan(const LayerGeom& g, int dir, ConvPlan& c) {
+  c.dir = dir;
+  c.k = g.k; c.stride = g.stride; c.pad = g.pad;
+  if (dir == 0) {
+    c.Cs = g.c_in; c.Hs = g.h_in; c.Ws = g.w_in; c.Co = g.c_out; c.Ho = g.h_out; c.Wo = g.w_out;
+  } else {
+    c.Cs = g.c_out; c.Hs = g.h_out; c.Ws = g.w_out; c.Co = g.c_in; c.Ho = g.h_in; c.Wo = g.w_in;
+  }
+  c.Csp = (c.Cs + 7) / 8 * 8;
+  c.Np = (c.Co + 15) / 16 * 16;
+  const int s = dir == 0 ? 1 : g.stride;
+  if (g.k < 1 || g.stride < 1 || s * s > kMaxConvPhases) return false;
+  c.nph = s * s;
+  int kb = 0;
+  for (int q = 0; q < c.nph; ++q) {
+    ConvPhase& f = c.f[q];
+    f.ph = q / s; f.pw = q % s;
+    f.Hf = f.ph < c.Ho ? (c.Ho - f.ph + s - 1) / s : 0;
+    f.Wf = f.pw < c.Wo ? (c.Wo - f.pw + s - 1) / s : 0;
+    f.rh = (f.ph + g.pad) % s; f.rw = (f.pw + g.pad) % s;
+    f.nkh = f.rh < g.k ? (g.k - f.rh + s - 1) / s : 0;
+    f.nkw = f.rw < g.k ? (g.k - f.rw + s - 1) / s : 0;
+    if (f.nkh * f.nkw == 0 && f.Hf * f.Wf > 0) return false;   // pixels no tap reaches
+    f.kb0 = kb;
+    f.nkb = (f.nkh * f.nkw * c.Csp + 63) / 64;
+    kb += f.nkb;
+  }
+  c.Kp = kb * 64;
+  return true;
+}
+
+// Convolution on the tensor cores (implicit GEMM, bf16 operands, fp32 out):
+// dir 0 out = conv(src) [R, d_out], dir 1 out = conv^T(src) [R, d_in]. Wp is
+// the weight packed for that direction's plan, [Np, Kp]. false = shape not
+// supported (use the SIMT convolution).
+bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const __nv_bfloat16* Wp, int Kp, int Np,
+                  const __nv_bfloat16* src, float* out);
 
 template <typename T, typename Top>
 void relax_eval(cudaStream_t st, const RelaxArgs<T, Top>& a);

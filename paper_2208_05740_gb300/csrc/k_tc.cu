@@ -20,6 +20,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -256,6 +257,249 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
+// ------------------------------------------------------------------ implicit-GEMM convolution
+// out = conv(src) (dir 0, the reverse-mode step through a convolution) or
+// conv^T(src) (dir 1, the backward step y = W^T nu) for all rows as one GEMM
+// on the tensor cores, bf16 operands and fp32 accumulation. The GEMM rows are
+// the output pixels of all rows, phase by phase (ConvPlan): within phase f,
+// row m = mbase_f + r * Hf * Wf + (i * Wf + j); the columns are output
+// channels; the K index runs over the phase's taps and the source channels.
+// A transposed convolution of stride s thus multiplies only the taps that
+// reach each pixel (on average k*k / s^2 of them) instead of all k*k.
+//
+// A persistent CTA of 256 threads loops over 128-row tiles (a tile never
+// crosses a phase). Per tile it stages the source-map rows its taps can reach
+// in shared memory, channel innermost, then builds each 128 x 64 A block from
+// them (two threads per row, four 16-byte chunks each) directly in the
+// 128-byte-swizzled K-major layout the MMA descriptor names, double-buffered
+// so building block j+1 overlaps the MMAs of block j. The packed weights
+// [Np, Kp] stay in shared memory for the whole kernel; the accumulator
+// (128 x Np fp32) lives in TMEM.
+struct ConvTcArgs {
+  ConvPlan c;
+  int64_t R;
+  int stg_rows;            // source-map rows the staging buffer holds
+  int tmem_cols;
+  const __nv_bfloat16* src;  // [R, Cs*Hs*Ws], channel-major (c, h, w)
+  const __nv_bfloat16* Wp;   // [Np, Kp]
+  float* out;                // [R, Co*Ho*Wo], channel-major
+};
+
+constexpr int kConvThreads = 256;
+
+struct ConvSmem {
+  int b_off, stg_off, bar_off, total;
+};
+__host__ __device__ inline ConvSmem conv_smem_layout(int Kp, int Np, int stg_rows, int Ws, int Csp) {
+  ConvSmem L;
+  L.b_off = 2 * kTileA;                                    // after the two A stages
+  L.stg_off = L.b_off + (Kp / 64) * Np * kRowBytes;        // weights: Kp/64 tiles of Np rows
+  L.bar_off = (L.stg_off + stg_rows * Ws * Csp * 2 + 15) & ~15;
+  L.total = L.bar_off + 64 + 1024;                         // barriers, TMEM slot, alignment slack
+  return L;
+}
+
+// Tile geometry: phase, first GEMM row of the phase, rows r0 .. r0 + nrt - 1
+// of the batch, and the source-map rows sh0 .. sh0 + nsh - 1 the tile reads
+// (per batch row; the whole map when the tile spans several batch rows).
+struct ConvTile {
+  int f, nrt, sh0, nsh;
+  int64_t m0, mend, r0;      // GEMM rows [m0, mend) of phase f (phase-local), first batch row
+};
+__host__ __device__ inline ConvTile conv_tile(const ConvPlan& c, int64_t R, int64_t t) {
+  ConvTile T{};
+  int64_t tb = 0;
+  for (int q = 0; q < c.nph; ++q) {
+    const int64_t Pf = (int64_t)c.f[q].Hf * c.f[q].Wf, nt = (R * Pf + 127) / 128;
+    if (t < tb + nt || q == c.nph - 1) {
+      T.f = q;
+      T.m0 = (t - tb) * 128;
+      T.mend = T.m0 + 128 < R * Pf ? T.m0 + 128 : R * Pf;
+      const ConvPhase& f = c.f[q];
+      T.r0 = T.m0 / Pf;
+      const int64_t rl = (T.mend - 1) / Pf;
+      T.nrt = (int)(rl - T.r0 + 1);
+      T.sh0 = 0;
+      T.nsh = c.Hs;
+      if (T.nrt == 1) {
+        const int i_lo = (int)((T.m0 - T.r0 * Pf) / f.Wf), i_hi = (int)((T.mend - 1 - T.r0 * Pf) / f.Wf);
+        const int s = c.dir == 0 ? 1 : c.stride;
+        const int o_lo = f.ph + s * i_lo, o_hi = f.ph + s * i_hi;   // output rows
+        int lo, hi;
+        if (c.dir == 0) {
+          lo = o_lo * c.stride - c.pad;
+          hi = o_hi * c.stride + c.k - 1 - c.pad;
+        } else {
+          lo = (o_lo + c.pad - (f.rh + s * (f.nkh - 1))) / s;   // exact: same residue
+          hi = (o_hi + c.pad - f.rh) / s;
+          if (o_lo + c.pad - (f.rh + s * (f.nkh - 1)) < 0) lo = 0;
+        }
+        lo = lo < 0 ? 0 : lo;
+        hi = hi > c.Hs - 1 ? c.Hs - 1 : hi;
+        T.sh0 = lo;
+        T.nsh = hi >= lo ? hi - lo + 1 : 0;
+      }
+      return T;
+    }
+    tb += nt;
+  }
+  return T;
+}
+__host__ __device__ inline int64_t conv_tiles(const ConvPlan& c, int64_t R) {
+  int64_t n = 0;
+  for (int q = 0; q < c.nph; ++q) n += (R * c.f[q].Hf * c.f[q].Wf + 127) / 128;
+  return n;
+}
+
+__global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_constant__ ConvTcArgs a) {
+  const ConvPlan& c = a.c;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const ConvSmem lay = conv_smem_layout(c.Kp, c.Np, a.stg_rows, c.Ws, c.Csp);
+  uint8_t* As = smem;
+  uint8_t* Bs = smem + lay.b_off;
+  __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(smem + lay.stg_off);
+  uint64_t* mma_done = reinterpret_cast<uint64_t*>(smem + lay.bar_off);   // [2]
+  uint64_t* done = mma_done + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    mbar_init(&mma_done[0], 1);
+    mbar_init(&mma_done[1], 1);
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // weights into shared memory, tile kb = K columns [64 kb, 64 kb + 64), swizzled rows
+  {
+    const int chunks = c.Kp / 8;   // 16-byte chunks per weight row
+    for (int idx = tid; idx < c.Np * chunks; idx += kConvThreads) {
+      const int n = idx / chunks, ch = idx - n * chunks;
+      const int kb = ch >> 3, j = ch & 7;
+      const uint4 v = *reinterpret_cast<const uint4*>(a.Wp + (int64_t)n * c.Kp + ch * 8);
+      *reinterpret_cast<uint4*>(Bs + kb * c.Np * kRowBytes + n * kRowBytes + ((j ^ (n & 7)) << 4)) = v;
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  const int HW = c.Hs * c.Ws, src_dim = c.Cs * HW, out_dim = c.Co * c.Ho * c.Wo;
+  const int64_t tiles = conv_tiles(c, a.R);
+  const uint32_t id = idesc(1u, BM, c.Np);
+  const int s_out = c.dir == 0 ? 1 : c.stride;     // output-pixel step within a phase
+  const int s_tap = c.dir == 0 ? 1 : c.stride;     // tap step within a phase
+  const int row = tid & (BM - 1), half = tid >> 7;  // GEMM row of the tile; chunks 4*half .. 4*half+3
+  uint32_t g = 0, it = 0;
+  bool ok = true;
+  for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++it) {
+    const ConvTile T = conv_tile(c, a.R, tile);
+    const ConvPhase& f = c.f[T.f];
+    const int Pf = f.Hf * f.Wf;
+    // stage the reachable source rows, channel innermost: one work item = 8
+    // channels of one pixel
+    const int npix = T.nsh * c.Ws, cgroups = c.Csp / 8;
+    for (int64_t item = tid; item < (int64_t)T.nrt * npix * cgroups; item += kConvThreads) {
+      const int cg = (int)(item % cgroups);
+      const int64_t t2 = item / cgroups;
+      const int pw = (int)(t2 % npix), rr = (int)(t2 / npix);
+      const __nv_bfloat16* sp = a.src + (T.r0 + rr) * src_dim + (int64_t)T.sh0 * c.Ws + pw + (int64_t)cg * 8 * HW;
+      uint32_t w[4];
+#pragma unroll
+      for (int cc = 0; cc < 8; cc += 2) {
+        const uint32_t lo = cg * 8 + cc < c.Cs ? __bfloat16_as_ushort(sp[(int64_t)cc * HW]) : 0u;
+        const uint32_t hi = cg * 8 + cc + 1 < c.Cs ? __bfloat16_as_ushort(sp[(int64_t)(cc + 1) * HW]) : 0u;
+        w[cc / 2] = lo | (hi << 16);
+      }
+      *reinterpret_cast<uint4*>(stg + ((int64_t)rr * npix + pw) * c.Csp + cg * 8) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    __syncthreads();
+    // this thread's GEMM row: batch row r, output pixel (oh, ow)
+    const int64_t m = T.m0 + row;
+    const bool mv = m < T.mend;
+    const int64_t r = mv ? m / Pf : 0;
+    const int pos = mv ? (int)(m - r * Pf) : 0;
+    const int oh = f.ph + s_out * (pos / f.Wf), ow = f.pw + s_out * (pos % f.Wf), rl = (int)(r - T.r0);
+    const int ntap = f.nkh * f.nkw;
+    for (int kb = 0; kb < f.nkb; ++kb, ++g) {
+      const int sg = g & 1;
+      bool w_ok = true;
+      if (g >= 2) w_ok = mbar_wait(&mma_done[sg], ((g >> 1) - 1) & 1);
+      if (!__syncthreads_and(w_ok)) { ok = false; break; }
+      uint8_t* At = As + sg * kTileA;
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int j = half * 4 + jj;
+        const int kk = kb * 64 + j * 8;
+        const int tt = kk / c.Csp, c0 = kk - tt * c.Csp;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (mv && tt < ntap) {
+          const int kh = f.rh + s_tap * (tt / f.nkw), kw = f.rw + s_tap * (tt % f.nkw);
+          int sh, sw;
+          if (c.dir == 0) {
+            sh = oh * c.stride + kh - c.pad;
+            sw = ow * c.stride + kw - c.pad;
+          } else {   // exact divisions: the phase fixes the residues
+            const int th = oh + c.pad - kh, tw = ow + c.pad - kw;
+            sh = th >= 0 ? th / c.stride : -1;
+            sw = tw >= 0 ? tw / c.stride : -1;
+          }
+          if (sh >= T.sh0 && sh < T.sh0 + T.nsh && sh < c.Hs && sw >= 0 && sw < c.Ws)
+            v = *reinterpret_cast<const uint4*>(stg + ((int64_t)(rl * T.nsh + sh - T.sh0) * c.Ws + sw) * c.Csp + c0);
+        }
+        *reinterpret_cast<uint4*>(At + row * kRowBytes + ((j ^ (row & 7)) << 4)) = v;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ab = smem_u32(At), bb = smem_u32(Bs + (f.kb0 + kb) * c.Np * kRowBytes);
+#pragma unroll
+        for (int k4 = 0; k4 < kRowBytes / 32; ++k4)
+          umma<0>(tmem, sdesc(ab + k4 * 32), sdesc(bb + k4 * 32), id, (kb | k4) != 0);
+        umma_commit(&mma_done[sg]);
+        if (kb == f.nkb - 1) umma_commit(done);
+      }
+    }
+    if (!ok) break;
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31; warps w and w+4 split the columns
+    const bool d_ok = __syncthreads_and(mbar_wait(done, it & 1));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!d_ok) { ok = false; break; }
+    const int erow = (warp & 3) * 32 + lane;
+    const int64_t em = T.m0 + erow;
+    const int64_t er = em / Pf;
+    const int epos = (int)(em - er * Pf);
+    const int eoh = f.ph + s_out * (epos / f.Wf), eow = f.pw + s_out * (epos % f.Wf);
+    for (int col = (warp >> 2) * 32; col < c.Np; col += 64) {
+      uint32_t v[32];
+      tmem_ld32(tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + col, v);
+      if (em < T.mend) {
+        float* dst = a.out + er * out_dim + (int64_t)eoh * c.Wo + eow;
+        const int64_t cstride = (int64_t)c.Ho * c.Wo;
+#pragma unroll
+        for (int t = 0; t < 32; ++t)
+          if (col + t < c.Co) dst[(col + t) * cstride] = __uint_as_float(v[t]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+  }
+}
+
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
@@ -339,6 +583,70 @@ bool gemm_tc_tf32x3(cudaStream_t st, int64_t M, int N, int K, const float* A, co
   const bool ok = launch_tc<1>(st, M, N, K, A, Alo, B, Blo, C);
   prof_end(st, tk);
   return ok;
+}
+
+bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const __nv_bfloat16* Wp, int Kp, int Np,
+                  const __nv_bfloat16* src, float* out) {
+  if (R <= 0) return true;
+  ConvTcArgs a{};
+  ConvPlan& c = a.c;
+  if (!Wp || !conv_plan(g, dir, c) || c.Kp != Kp || c.Np != Np || Np > 256) return false;
+  a.R = R;
+  // staging rows: the largest window over the tiles (tile starts repeat with
+  // period P_f within a phase, so the first P_f tiles of each phase cover all)
+  int64_t tb = 0;
+  int rows = 0;
+  for (int q = 0; q < c.nph; ++q) {
+    const int64_t Pf = (int64_t)c.f[q].Hf * c.f[q].Wf, nt = (R * Pf + 127) / 128;
+    for (int64_t t = 0; t < std::min<int64_t>(nt, Pf + 1); ++t) {
+      const ConvTile T = conv_tile(c, R, tb + t);
+      rows = std::max(rows, T.nrt == 1 ? T.nsh : T.nrt * c.Hs);
+    }
+    tb += nt;
+  }
+  a.stg_rows = std::max(rows, 1);
+  int tc = 32;
+  while (tc < Np) tc <<= 1;
+  a.tmem_cols = tc;
+  const ConvSmem L = conv_smem_layout(Kp, Np, a.stg_rows, c.Ws, c.Csp);
+  if (L.total > 227 * 1024) return false;
+  static std::mutex mu;
+  static int attr_bytes = 0;
+  static int n_sm = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (L.total > attr_bytes) {
+      if (cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) != cudaSuccess)
+        return false;
+      attr_bytes = L.total;
+    }
+    if (!n_sm) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+      if (n_sm <= 0) n_sm = 1;
+    }
+  }
+  a.src = src;
+  a.Wp = Wp;
+  a.out = out;
+  const int src_dim = c.Cs * c.Hs * c.Ws, out_dim = c.Co * c.Ho * c.Wo;
+  if (!(reg_check(src, (double)R * src_dim * 2, "conv src") & reg_check(Wp, (double)Np * Kp * 2, "conv W") &
+        reg_check(out, (double)R * out_dim * 4, "conv out")))
+    return true;  // reported by the caller's launch status
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc, kConvThreads, L.total);
+  per_sm = std::max(1, std::min(per_sm, 512 / tc));   // TMEM columns of the resident CTAs
+  const int64_t tiles = conv_tiles(c, R);
+  const int grid = (int)std::min<int64_t>(tiles, (int64_t)n_sm * per_sm);
+  // algorithmic work: the convolution's multiply-adds (2 flops each); bytes:
+  // source read and output written once
+  const double macs = (double)R * g.c_out * g.h_out * g.w_out * g.c_in * g.k * g.k;
+  int tk = prof_begin(st, dir == 0 ? "conv_tc_bf16_fwd" : "conv_tc_bf16_T", 2.0 * macs,
+                      (double)R * src_dim * 2 + (double)R * out_dim * 4);
+  k_conv_tc<<<grid, kConvThreads, L.total, st>>>(a);
+  prof_end(st, tk);
+  return true;
 }
 
 std::string take_tc_error(cudaStream_t st) {
