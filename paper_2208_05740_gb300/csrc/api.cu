@@ -303,6 +303,18 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
       auto pt = pack(true, ctk, ctn);
       if (!pt.empty()) UP(ct16, __nv_bfloat16, pt.data(), pt.size());
     }
+    float* wabs = nullptr;
+    if (g.kind != GCP_DENSE) {
+      std::vector<float> wa(nw);
+      for (size_t q = 0; q < nw; ++q) {
+        const double v = std::fabs(d.W[q]);
+        float f = (float)v;
+        if ((double)f < v) f = std::nextafter(f, INFINITY);   // rounded up
+        wa[q] = f;
+      }
+      UP(wabs, float, wa.data(), nw);
+    }
+    net->Wabs32.push_back(wabs);
     net->CF16.push_back(cf16); net->CT16.push_back(ct16);
     net->cf_kp.push_back(cfk); net->cf_np.push_back(cfn); net->ct_kp.push_back(ctk); net->ct_np.push_back(ctn);
     UP(b64, double, d.b, g.d_out);
@@ -986,6 +998,13 @@ gcp_status run_certify(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
   float* ya = (float*)b.ws("c_yabs", (size_t)R * b.dmax() * 4, &s);
   double* part = (double*)b.ws("c_part", (size_t)b.n_partials() * R * 8, &s);
   if (!nu || !y || !ya || !part) return s;
+  bool any_conv = false;
+  for (int i = 0; i < L; ++i) any_conv |= net.geom[i].kind != GCP_DENSE;
+  float* nuabs = nullptr;
+  if (any_conv) {
+    nuabs = (float*)b.ws("c_nuabs", (size_t)R * b.dmax() * 4, &s);
+    if (!nuabs) return s;
+  }
   SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp, b.sp_tab};
   // y^(L-1) = W^(L)^T (-c_k), one row per spec row
   const LayerGeom& gl = net.geom[L - 1];
@@ -1003,12 +1022,13 @@ gcp_status run_certify(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
     a.sp = sp;
     a.csc = csc_of<double>(b, i);
     a.nu_out = nu;
+    const LayerGeom& g = net.geom[i - 1];
+    a.nuabs_out = g.kind == GCP_DENSE ? nullptr : nuabs;
     a.obj_part = part + (int64_t)poff * R;
     certify_relax<Td>(st, a);
     poff += (net.dims[i] + kChunk - 1) / kChunk;
-    const LayerGeom& g = net.geom[i - 1];
     if (g.kind == GCP_DENSE) gemm_nt_abs(st, R, g.d_in, g.d_out, nu, 0, net.WT64[i - 1], y, ya);
-    else conv_T_abs(st, R, g, net.W64[i - 1], nu, y, ya);
+    else conv_T_abs(st, R, g, net.W64[i - 1], net.Wabs32[i - 1], nu, nuabs, y, ya);
   }
   certify_concretize<Td>(st, R, b.K, b.N, net.dims[0], y, ya, gamma_n_host(red_len(net.geom[0])), net.xlo64,
                          net.xhi64, (const Td*)b.gamma, csc_of<double>(b, 0), part + (int64_t)poff * R);

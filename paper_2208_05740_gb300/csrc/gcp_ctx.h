@@ -29,6 +29,7 @@ struct Net {
   // convolution weights packed for the tensor-core implicit GEMM (bf16):
   // forward [cf_np, cf_kp] and transposed [ct_np, ct_kp]; nullptr for dense layers
   std::vector<__nv_bfloat16*> CF16, CT16;
+  std::vector<float*> Wabs32;        // |W| in float rounded up (convolution layers; certification)
   std::vector<int> cf_kp, cf_np, ct_kp, ct_np;
   double *xlo64 = nullptr, *xhi64 = nullptr;
   float *xlo32 = nullptr, *xhi32 = nullptr;

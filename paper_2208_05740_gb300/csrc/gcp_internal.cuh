@@ -186,6 +186,7 @@ struct CertArgs {
   SplitsDev sp;
   CutCSC<double> csc;
   double* nu_out;        // [R, d]
+  float* nuabs_out;      // [R, d] |nu| in float rounded up, or nullptr
   double* obj_part;      // [ceil(d/32), R] rounded-down partial sums
 };
 
@@ -218,8 +219,10 @@ template <typename Tin, typename Tacc>
 void conv_fwd(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const Tin* in, Tacc* out);
 template <typename Tin, typename Tacc>
 void conv_T(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const Tin* in, Tacc* out);
-void conv_T_abs(cudaStream_t st, int64_t R, const LayerGeom& g, const double* W, const double* in, double* out,
-                float* outabs);
+// certification: y = W^T nu in float64 and sum |W||nu| in float rounded up,
+// from |W| and |nu| given in float rounded up
+void conv_T_abs(cudaStream_t st, int64_t R, const LayerGeom& g, const double* W, const float* Wabs, const double* in,
+                const float* inabs, double* out, float* outabs);
 
 // tcgen05 GEMMs (k_tc.cu); false = shape or driver not supported, use SIMT
 bool tc_available(int K, bool bf16);

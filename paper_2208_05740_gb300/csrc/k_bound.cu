@@ -1045,6 +1045,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_relax(CertArgs<
     }
     part = __dadd_rd(part, __dmul_rd(-nu, a.bias[j]));
     a.nu_out[r * a.d + j] = nu;
+    if (a.nuabs_out) a.nuabs_out[r * a.d + j] = __double2float_ru(fabs(nu));
     }
     part = warp_sum_rd(part);
     if (w.lane == 0) a.obj_part[(int64_t)w.c * a.R + r] = part;
@@ -1342,6 +1343,7 @@ void certify_relax(cudaStream_t st, const CertArgs<Td>& a) {
         reg_check(a.alpha, Rd * tb, "alpha") & reg_check(a.beta, (double)a.M * a.R * tb, "beta") &
         reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") & chk_splits(a.sp, a.R, a.K, a.M) &
         chk_csc(a.csc, a.d) & reg_check(a.nu_out, Rd * 8.0, "cert nu") &
+        reg_check(a.nuabs_out, a.nuabs_out ? Rd * 4.0 : 0.0, "cert |nu|") &
         reg_check(a.obj_part, ((a.d + 31) / 32) * (double)a.R * 8.0, "cert part")))
     return;
   int tk = prof_begin(st, "certify_relax_f64", 0.0, bytes);

@@ -129,42 +129,59 @@ __global__ void k_conv_fwd(int64_t R, LayerGeom g, const Tin* __restrict__ W, co
   }
 }
 
-// out[r,c,ih,iw] = sum over (o,kh,kw) with ih = oh*s+kh-p, iw = ow*s+kw-p of W[o,c,kh,kw] in[r,o,oh,ow]
+// out[r,c,ih,iw] = sum over the taps (kh,kw) that reach (ih,iw) and over the
+// channels o of W[o,c,kh,kw] in[r,o,(ih+p-kh)/s,(iw+p-kw)/s]. Threads run in
+// the order row, channel, then output pixels phase by phase: pixels with the
+// same ih mod s and iw mod s are reached by the same taps, so the threads of a
+// warp run the same taps. ABS: also sum |W||in| in float rounding up, from
+// |W| and |in| given in float rounded up.
 template <typename Tin, typename Tacc, bool ABS>
 __global__ void k_conv_T(int64_t R, LayerGeom g, const Tin* __restrict__ W, const Tin* __restrict__ in,
-                         Tacc* __restrict__ out, float* __restrict__ outabs) {
-  int64_t n = R * (int64_t)g.d_in;
+                         Tacc* __restrict__ out, const float* __restrict__ Wabs, const float* __restrict__ inabs,
+                         float* __restrict__ outabs) {
+  const int s = g.stride, HW = g.h_in * g.w_in, HWo = g.h_out * g.w_out, ckk = g.c_in * g.k * g.k;
+  const int64_t n = R * (int64_t)g.d_in;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t r = idx / g.d_in;
-    int rem = (int)(idx - r * g.d_in);
-    int c = rem / (g.h_in * g.w_in);
-    int p2 = rem - c * g.h_in * g.w_in;
-    int ih = p2 / g.w_in, iw = p2 - ih * g.w_in;
+    const int64_t r = idx / g.d_in;
+    const int rem = (int)(idx - r * g.d_in);
+    const int c = rem / HW;
+    int q = rem - c * HW;   // position in phase order
+    int ph = 0, pw = 0, Wf = 1;
+    for (int f = 0; f < s * s; ++f) {
+      ph = f / s;
+      pw = f - ph * s;
+      const int Hf = ph < g.h_in ? (g.h_in - ph + s - 1) / s : 0;
+      Wf = pw < g.w_in ? (g.w_in - pw + s - 1) / s : 0;
+      if (q < Hf * Wf) break;
+      q -= Hf * Wf;
+    }
+    const int ih = ph + s * (q / Wf), iw = pw + s * (q % Wf);
+    const int rh = (ph + g.pad) % s, rw = (pw + g.pad) % s;
     const Tin* ir = in + r * g.d_out;
+    const float* ia = ABS ? inabs + r * g.d_out : nullptr;
     Tacc acc = Tacc(0);
     float aacc = 0.f;
-    for (int kh = 0; kh < g.k; ++kh) {
-      int th = ih + g.pad - kh;
-      if (th < 0 || th % g.stride) continue;
-      int oh = th / g.stride;
+    for (int kh = rh; kh < g.k; kh += s) {
+      const int th = ih + g.pad - kh;
+      if (th < 0) break;   // larger kh only lower th
+      const int oh = th / s;
       if (oh >= g.h_out) continue;
-      for (int kw = 0; kw < g.k; ++kw) {
-        int tw = iw + g.pad - kw;
-        if (tw < 0 || tw % g.stride) continue;
-        int ow = tw / g.stride;
+      for (int kw = rw; kw < g.k; kw += s) {
+        const int tw = iw + g.pad - kw;
+        if (tw < 0) break;
+        const int ow = tw / s;
         if (ow >= g.w_out) continue;
+        const int wo = (c * g.k + kh) * g.k + kw, xo = oh * g.w_out + ow;
         for (int o = 0; o < g.c_out; ++o) {
-          Tacc wv = load_as<Tacc>(W + ((o * g.c_in + c) * g.k + kh) * g.k + kw);
-          Tacc xv = load_as<Tacc>(ir + (o * g.h_out + oh) * g.w_out + ow);
-          acc = fma(wv, xv, acc);
-          if constexpr (ABS)
-            aacc = __fmaf_ru(__double2float_ru(fabs((double)wv)), __double2float_ru(fabs((double)xv)), aacc);
+          acc = fma(load_as<Tacc>(W + o * ckk + wo), load_as<Tacc>(ir + o * HWo + xo), acc);
+          if constexpr (ABS) aacc = __fmaf_ru(Wabs[o * ckk + wo], ia[o * HWo + xo], aacc);
         }
       }
     }
-    out[idx] = acc;
-    if constexpr (ABS) outabs[idx] = aacc;
+    const int64_t oi = r * g.d_in + c * HW + ih * g.w_in + iw;
+    out[oi] = acc;
+    if constexpr (ABS) outabs[oi] = aacc;
   }
 }
 
@@ -253,20 +270,21 @@ void conv_T(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const 
   char nm[32];
   snprintf(nm, sizeof nm, "conv_T_%s", tname<Tin>());
   int tk = prof_begin(st, nm, 2.0 * R * conv_macs(g), (double)R * (g.d_out * sizeof(Tin) + g.d_in * sizeof(Tacc)));
-  k_conv_T<Tin, Tacc, false><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, nullptr);
+  k_conv_T<Tin, Tacc, false><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, nullptr, nullptr, nullptr);
   prof_end(st, tk);
 }
 
-void conv_T_abs(cudaStream_t st, int64_t R, const LayerGeom& g, const double* W, const double* in, double* out,
-                float* outabs) {
+void conv_T_abs(cudaStream_t st, int64_t R, const LayerGeom& g, const double* W, const float* Wabs, const double* in,
+                const float* inabs, double* out, float* outabs) {
   int64_t n = R * (int64_t)g.d_in;
   if (n <= 0) return;
   const double nw = (double)g.c_out * g.c_in * g.k * g.k;
-  if (!(reg_check(W, nw * 8.0, "convT W") & reg_check(in, (double)R * g.d_out * 8.0, "convT in") &
+  if (!(reg_check(W, nw * 8.0, "convT W") & reg_check(Wabs, nw * 4.0, "convT |W|") &
+        reg_check(in, (double)R * g.d_out * 8.0, "convT in") & reg_check(inabs, (double)R * g.d_out * 4.0, "convT |in|") &
         reg_check(out, (double)R * g.d_in * 8.0, "convT out") & reg_check(outabs, (double)R * g.d_in * 4.0, "convT abs")))
     return;
-  int tk = prof_begin(st, "conv_T_f64_certify", 2.0 * R * conv_macs(g), (double)R * (g.d_out * 8.0 + g.d_in * 12.0));
-  k_conv_T<double, double, true><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, outabs);
+  int tk = prof_begin(st, "conv_T_f64_certify", 2.0 * R * conv_macs(g), (double)R * (g.d_out * 12.0 + g.d_in * 12.0));
+  k_conv_T<double, double, true><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, Wabs, inabs, outabs);
   prof_end(st, tk);
 }
 
