@@ -8,6 +8,10 @@ the FP64 outward-rounded certification pass. One step = that whole hot path
 for the batch; one unit = one subdomain with all its spec rows optimised and
 certified. Inputs are seeded synthetic data of the paper's shapes.
 
+--workload cnn: CNN 3x32x32 -> conv32 3x3 s2 -> conv64 3x3 s2 -> FC512 ->
+FC10, 4096 subdomains (1-12 splits) x 9 spec rows, 1000 cuts over 2-16
+variables, 50 Adam iterations in the BF16 chain, FP64 certification.
+
 value  : device-timed (CUDA events on the library's stream), inputs resident.
 e2e    : the same through the public C ABI from host buffers: every step
          creates the batch from host split arrays (uploads splits and cuts),
@@ -39,19 +43,46 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gcp", "reference"], default="gcp")
-    ap.add_argument("--prec", choices=["fp32", "bf16"], default="fp32")
-    ap.add_argument("--iters", type=int, default=100)
-    ap.add_argument("--n-sub", type=int, default=1024)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="mlp",
+                    help="mlp: MLP 784-256x6-10 (the headline); cnn: the CIFAR-shaped CNN")
+    ap.add_argument("--prec", choices=["fp32", "bf16"], default=None, help="chain precision (workload default)")
+    ap.add_argument("--iters", type=int, default=None, help="ascent iterations (workload default)")
+    ap.add_argument("--n-sub", type=int, default=None, help="subdomains per GPU (workload default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-all", action="store_true", help="print every kernel's share (untimed step)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving stream (0: skip)")
     ap.add_argument("--no-bf16-form", action="store_true", help="skip the BF16-chain form of the workload")
-    return ap.parse_args()
+    a = ap.parse_args()
+    w = WORKLOADS[a.workload]
+    a.prec = a.prec or w["prec"]
+    a.iters = a.iters if a.iters is not None else w["iters"]
+    a.n_sub = a.n_sub if a.n_sub is not None else w["n_sub"]
+    return a
+
+
+def _build_mlp(n_sub):
+    from paper_2208_05740_gb300 import synth
+    return synth.mlp_256x6(n_sub=n_sub)
+
+
+def _build_cnn(n_sub):
+    from paper_2208_05740_gb300 import synth
+    return synth.cnn_cifar(n_sub=n_sub)
+
+
+# The two workloads: name, instance builder, defaults, oracle sample size.
+WORKLOADS = {
+    "mlp": dict(name="mlp_784_256x6_10", cuts=200, splits="1-8", prec="fp32", iters=100, n_sub=1024, sample=4,
+                build=_build_mlp),
+    "cnn": dict(name="cnn_3x32x32_c32_c64_fc512_fc10", cuts=1000, splits="1-12", prec="bf16", iters=50, n_sub=4096,
+                sample=2, build=_build_cnn),
+}
 
 
 def workload_config(a, n_gpus):
-    return {"workload": "mlp_784_256x6_10", "n_subdomains_per_gpu": a.n_sub, "spec_rows": 9, "rows_per_gpu": a.n_sub * 9,
-            "cuts": 200, "splits_per_subdomain": "1-8", "iters": a.iters, "optimizer": "adam",
+    w = WORKLOADS[a.workload]
+    return {"workload": w["name"], "n_subdomains_per_gpu": a.n_sub, "spec_rows": 9, "rows_per_gpu": a.n_sub * 9,
+            "cuts": w["cuts"], "splits_per_subdomain": w["splits"], "iters": a.iters, "optimizer": "adam",
             "lr": [0.1, 0.02, 0.02], "lr_decay": 0.98, "chain": a.prec, "certify": "fp64_outward_rounded",
             "intermediate_bounds": "interval (IBP)", "l2": "flushed between steps (256 MiB write)",
             "parallelism": f"replicas{n_gpus}" if n_gpus > 1 else "single_gpu"}
@@ -177,7 +208,7 @@ def oracle_sample(inst, n_sub, iters, seconds_cap=25.0):
     O.optimize(P, D, k, 0.1, 0.02, 0.02, optimizer="adam", lr_decay=0.98)
     t_it = max(time.perf_counter() - t0 - t_eval, 1e-9) / k
     per_batch = t_it * iters + 2 * t_eval
-    return n_sub / per_batch, f"{n_sub} subdomains x 9 rows, {k} timed Adam steps + 1 evaluation, " \
+    return n_sub / per_batch, f"{inst.name}: {n_sub} subdomains x 9 rows, {k} timed Adam steps + 1 evaluation, " \
                               f"extrapolated to {iters} steps + 2 evaluations"
 
 
@@ -187,8 +218,8 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    inst = synth.mlp_256x6()
-    n_sub = 4
+    inst = WORKLOADS[a.workload]["build"](64)
+    n_sub = WORKLOADS[a.workload]["sample"]
     cfg = workload_config(a, a.gpus)
     for _ in range(a.warmup):
         oracle_sample(inst, n_sub, a.iters, seconds_cap=2.0)
@@ -304,7 +335,7 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
     prec = gcp.GCP_FP32 if a.prec == "fp32" else gcp.GCP_BF16
-    inst = synth.mlp_256x6(n_sub=a.n_sub)
+    inst = WORKLOADS[a.workload]["build"](a.n_sub)
     ctx = gcp.Context(dev)
     ctx.set_stream(stream.cuda_stream)
     net_id, cs = ctx.load_instance(inst)
@@ -400,7 +431,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches_all),
         "roofline": {"kernel": dominant, "bound": bound_kind, "achieved": achieved, "peak": peak, "unit": unit,
-                     "frac": achieved / peak, "traffic": traffic_for(dominant, "mlp_784_256x6_10"),
+                     "frac": achieved / peak, "traffic": traffic_for(dominant, WORKLOADS[a.workload]["name"]),
                      "peak_source": note, "launches": int(n_dom), "ms_per_launch": per_launch_ms,
                      "share_of_step": rep[dominant][2] / total_ms},
         "clocks": clocks,
@@ -435,7 +466,7 @@ def main():
     if a.serve_requests > 0 and world == 1:
         line["serving"] = serving_bench(dev, a.serve_requests)
     if world == 1 and not a.no_cpu_baseline:
-        v, desc = oracle_sample(inst, 4, a.iters)
+        v, desc = oracle_sample(inst, WORKLOADS[a.workload]["sample"], a.iters)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
     print(json.dumps(line))
     ctx.close()
