@@ -287,14 +287,16 @@ struct ConvTcArgs {
 
 constexpr int kConvThreads = 256;
 
+constexpr int kConvStages = 3;   // A blocks in flight
 struct ConvSmem {
-  int b_off, stg_off, bar_off, total;
+  int b_off, stg_off, tab_off, bar_off, total;
 };
 __host__ __device__ inline ConvSmem conv_smem_layout(int Kp, int Np, int stg_rows, int Ws, int Csp) {
   ConvSmem L;
-  L.b_off = 2 * kTileA;                                    // after the two A stages
+  L.b_off = kConvStages * kTileA;                          // after the A stages
   L.stg_off = L.b_off + (Kp / 64) * Np * kRowBytes;        // weights: Kp/64 tiles of Np rows
-  L.bar_off = (L.stg_off + stg_rows * Ws * Csp * 2 + 15) & ~15;
+  L.tab_off = (L.stg_off + stg_rows * Ws * Csp * 2 + 15) & ~15;
+  L.bar_off = L.tab_off + (Kp / 8) * 4;                    // chunk table: one word per 8 K columns
   L.total = L.bar_off + 64 + 1024;                         // barriers, TMEM slot, alignment slack
   return L;
 }
@@ -359,14 +361,14 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   uint8_t* As = smem;
   uint8_t* Bs = smem + lay.b_off;
   __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(smem + lay.stg_off);
-  uint64_t* mma_done = reinterpret_cast<uint64_t*>(smem + lay.bar_off);   // [2]
-  uint64_t* done = mma_done + 2;
+  uint32_t* tab = reinterpret_cast<uint32_t*>(smem + lay.tab_off);
+  uint64_t* mma_done = reinterpret_cast<uint64_t*>(smem + lay.bar_off);   // [kConvStages]
+  uint64_t* done = mma_done + kConvStages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    mbar_init(&mma_done[0], 1);
-    mbar_init(&mma_done[1], 1);
+    for (int q = 0; q < kConvStages; ++q) mbar_init(&mma_done[q], 1);
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -386,6 +388,17 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       *reinterpret_cast<uint4*>(Bs + kb * c.Np * kRowBytes + n * kRowBytes + ((j ^ (n & 7)) << 4)) = v;
     }
   }
+  // chunk table: for the 8 K columns of chunk x (a phase's k-block kb, chunk
+  // j): tap (a, b) of the phase and source channel c0, or 0 = no tap
+  for (int q = 0; q < c.nph; ++q) {
+    const ConvPhase& f = c.f[q];
+    for (int x = tid; x < f.nkb * 8; x += kConvThreads) {
+      const int kk = x * 8, tt = kk / c.Csp, c0 = kk - tt * c.Csp;
+      uint32_t e = 0;
+      if (tt < f.nkh * f.nkw) e = 1u | (uint32_t)(tt / f.nkw) << 1 | (uint32_t)(tt % f.nkw) << 9 | (uint32_t)c0 << 17;
+      tab[f.kb0 * 8 + x] = e;
+    }
+  }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -396,7 +409,6 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   const int64_t tiles = conv_tiles(c, a.R);
   const uint32_t id = idesc(1u, BM, c.Np);
   const int s_out = c.dir == 0 ? 1 : c.stride;     // output-pixel step within a phase
-  const int s_tap = c.dir == 0 ? 1 : c.stride;     // tap step within a phase
   const int row = tid & (BM - 1), half = tid >> 7;  // GEMM row of the tile; chunks 4*half .. 4*half+3
   uint32_t g = 0, it = 0;
   bool ok = true;
@@ -422,38 +434,32 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       *reinterpret_cast<uint4*>(stg + ((int64_t)rr * npix + pw) * c.Csp + cg * 8) = make_uint4(w[0], w[1], w[2], w[3]);
     }
     __syncthreads();
-    // this thread's GEMM row: batch row r, output pixel (oh, ow)
+    // this thread's GEMM row: batch row r, output pixel (oh, ow); its source
+    // pixel for tap (a, b) is (bh + sg_tap * a, bw + sg_tap * b)
     const int64_t m = T.m0 + row;
     const bool mv = m < T.mend;
     const int64_t r = mv ? m / Pf : 0;
     const int pos = mv ? (int)(m - r * Pf) : 0;
     const int oh = f.ph + s_out * (pos / f.Wf), ow = f.pw + s_out * (pos % f.Wf), rl = (int)(r - T.r0);
-    const int ntap = f.nkh * f.nkw;
+    const int bh = c.dir == 0 ? oh * c.stride - c.pad : (oh + c.pad - f.rh) / c.stride;
+    const int bw = c.dir == 0 ? ow * c.stride - c.pad : (ow + c.pad - f.rw) / c.stride;
+    const int sg_tap = c.dir == 0 ? 1 : -1;
+    const __nv_bfloat16* srow = stg + (int64_t)rl * T.nsh * c.Ws * c.Csp;
     for (int kb = 0; kb < f.nkb; ++kb, ++g) {
-      const int sg = g & 1;
+      const int sg = g % kConvStages;
       bool w_ok = true;
-      if (g >= 2) w_ok = mbar_wait(&mma_done[sg], ((g >> 1) - 1) & 1);
+      if (g >= kConvStages) w_ok = mbar_wait(&mma_done[sg], ((g / kConvStages) - 1) & 1);
       if (!__syncthreads_and(w_ok)) { ok = false; break; }
       uint8_t* At = As + sg * kTileA;
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) {
         const int j = half * 4 + jj;
-        const int kk = kb * 64 + j * 8;
-        const int tt = kk / c.Csp, c0 = kk - tt * c.Csp;
+        const uint32_t e = tab[(f.kb0 + kb) * 8 + j];
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (mv && tt < ntap) {
-          const int kh = f.rh + s_tap * (tt / f.nkw), kw = f.rw + s_tap * (tt % f.nkw);
-          int sh, sw;
-          if (c.dir == 0) {
-            sh = oh * c.stride + kh - c.pad;
-            sw = ow * c.stride + kw - c.pad;
-          } else {   // exact divisions: the phase fixes the residues
-            const int th = oh + c.pad - kh, tw = ow + c.pad - kw;
-            sh = th >= 0 ? th / c.stride : -1;
-            sw = tw >= 0 ? tw / c.stride : -1;
-          }
+        if (mv && (e & 1u)) {
+          const int sh = bh + sg_tap * (int)((e >> 1) & 0xFFu), sw = bw + sg_tap * (int)((e >> 9) & 0xFFu);
           if (sh >= T.sh0 && sh < T.sh0 + T.nsh && sh < c.Hs && sw >= 0 && sw < c.Ws)
-            v = *reinterpret_cast<const uint4*>(stg + ((int64_t)(rl * T.nsh + sh - T.sh0) * c.Ws + sw) * c.Csp + c0);
+            v = *reinterpret_cast<const uint4*>(srow + ((int64_t)(sh - T.sh0) * c.Ws + sw) * c.Csp + (e >> 17));
         }
         *reinterpret_cast<uint4*>(At + row * kRowBytes + ((j ^ (row & 7)) << 4)) = v;
       }
