@@ -190,6 +190,31 @@ struct CertArgs {
   double* obj_part;      // [ceil(d/32), R] rounded-down partial sums
 };
 
+// ---------------------------------------------------------------- programmatic dependent launch
+// The per-iteration kernels are launched with programmatic stream
+// serialization: a kernel may begin (its static setup: bounds, split tables,
+// cut metadata, barriers, TMEM) while the previous kernel on the stream
+// drains, and executes griddep_wait() before it reads anything an earlier
+// kernel wrote or writes global memory. griddep_launch() at kernel start lets
+// the next kernel begin launching.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<A&&>(args)...);
+}
+
 // ---------------------------------------------------------------- launch validation
 // Every device allocation of the library is registered; before each launch the
 // launcher checks, on the host, that each pointer argument lies inside a live

@@ -574,6 +574,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_eval(RelaxArgs<T,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* wb = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * Lay::WARP;
   T* acc = wb;
+  griddep_launch();
   SpanWarp<V> w;
   if (!span_warp<V>((int)(a.R / a.K), a.d, w)) return;
   const int KR = (a.K + (int)gridDim.z - 1) / (int)gridDim.z;   // rows of this warp: [kb, ke)
@@ -604,13 +605,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_eval(RelaxArgs<T,
       cp_async<sizeof(T)>(sb + kSpanBatches * 32 + 32 * v + w.lane, ok ? a.beta + r * a.M + n.slot[v] : dummy, ok);
     }
   };
-#pragma unroll
-  for (int st = 0; st < NS; ++st) dense(kb + st, st);
   span_zero<T, V>(acc, w.lane);
   span_neurons<T, V>(w, a.lo, a.hi, a.bias, a.inv_ul, a.sp, a.M, a.layer, n);
   span_cuts<T, V>(a.csc, a.N, a.d, w, sc, er);
+  // everything above reads static data only; the rows come from earlier kernels
+  griddep_wait();
 #pragma unroll
-  for (int st = 0; st < NS; ++st) scattered(kb + st, st);
+  for (int st = 0; st < NS; ++st) {
+    dense(kb + st, st);
+    scattered(kb + st, st);
+  }
   cp_commit();
   for (int k = kb; k < ke; ++k) {
     const int st = (k - kb) % NS;
@@ -667,6 +671,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_adj(AdjArgs<T, To
   T* wb = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * Lay::WARP;
   T* acc = wb;
   T* ev = wb + 3 * SPAN;
+  griddep_launch();
   SpanWarp<V> w;
   if (!span_warp<V>((int)(a.R / a.K), a.d, w)) return;
   const int KR = (a.K + (int)gridDim.z - 1) / (int)gridDim.z;   // rows of this warp: [kb, ke)
@@ -697,13 +702,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_adj(AdjArgs<T, To
       cp_async<sizeof(T)>(sb + 32 * q + w.lane, ok ? a.gamma + r * a.N + sc.b[q].cut : dummy, ok);
     }
   };
-#pragma unroll
-  for (int st = 0; st < NS; ++st) dense(kb + st, st);
   span_zero<T, V>(acc, w.lane);
   span_neurons<T, V>(w, a.lo, a.hi, a.bias, a.inv_ul, a.sp, a.M, a.layer, n);
   span_cuts<T, V>(a.csc, a.N, a.d, w, sc, er);
+  // everything above reads static data only; the rows come from earlier kernels
+  griddep_wait();
 #pragma unroll
-  for (int st = 0; st < NS; ++st) scattered(kb + st, st);
+  for (int st = 0; st < NS; ++st) {
+    dense(kb + st, st);
+    scattered(kb + st, st);
+  }
   cp_commit();
   for (int k = kb; k < ke; ++k) {
     const int st = (k - kb) % NS;
@@ -792,6 +800,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_concretize(ConcArgs<T, 
   T* wb = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * Lay::WARP;
   T* acc = wb;
   T* ev = wb + 3 * SPAN;
+  griddep_launch();
   SpanWarp<V> w;
   if (!span_warp<V>((int)(a.R / a.K), a.d0, w)) return;
   const int KR = (a.K + (int)gridDim.z - 1) / (int)gridDim.z;   // rows of this warp: [kb, ke)
@@ -814,8 +823,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_concretize(ConcArgs<T, 
       cp_async<sizeof(T)>(sb + 32 * q + w.lane, ok ? a.gamma + r * a.N + sc.b[q].cut : dummy, ok);
     }
   };
-#pragma unroll
-  for (int st = 0; st < NS; ++st) dense(kb + st, st);
   span_zero<T, V>(acc, w.lane);
   T xl[V], xh[V];
 #pragma unroll
@@ -825,8 +832,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_concretize(ConcArgs<T, 
     ldv<V>(a.x_hi + w.j0, xh);
   }
   span_cuts<T, V>(a.csc, a.N, a.d0, w, sc, er);
+  // everything above reads static data only; the rows come from earlier kernels
+  griddep_wait();
 #pragma unroll
-  for (int st = 0; st < NS; ++st) scattered(kb + st, st);
+  for (int st = 0; st < NS; ++st) {
+    dense(kb + st, st);
+    scattered(kb + st, st);
+  }
   cp_commit();
   for (int k = kb; k < ke; ++k) {
     const int st = (k - kb) % NS;
@@ -901,6 +913,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_finalize(FinalArgs<T> a
 constexpr int kGatherUnroll = 8;
 template <typename T>
 __global__ void k_gather(GatherArgs<T> a) {
+  griddep_launch();
+  griddep_wait();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.R * a.N) {
     // threads past the cuts: the projected step on beta from dg/dbeta
@@ -1174,7 +1188,7 @@ void launch_span(Kern kern, size_t smem, dim3 grid, cudaStream_t st, const Args&
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  kern<<<grid, kWarpsPerBlock * 32, smem, st>>>(a);
+  launch_pdl(kern, grid, dim3(kWarpsPerBlock * 32), smem, st, a);
 }
 inline dim3 span_blocks(int64_t R, int K, int d, int V) {
   const int64_t S = R / K;
@@ -1329,7 +1343,7 @@ void gather_gamma(cudaStream_t st, const GatherArgs<T>& a) {
   int tk = prof_begin(st, sizeof(T) == 8 ? "gather_gamma_f64" : "gather_gamma_f32", 0.0,
                       ((double)a.R * a.nnz + (m2 ? 6.0 : 2.0) * (NR + MR)) * sizeof(T));
   const int64_t n = a.R * a.N + nb;
-  k_gather<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
+  launch_pdl(k_gather<T>, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, a);
   prof_end(st, tk);
 }
 template <typename Td>

@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(128, 1)
   uint64_t* done = empty + Cfg::kStages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
 
+  griddep_launch();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int KT = (K + Cfg::kKElems - 1) / Cfg::kKElems;
@@ -180,6 +181,7 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  griddep_wait();   // A (and C's previous readers) belong to earlier kernels
 
   if (warp == 0 && lane == 0) {
     // producer: TMA loads of stage kt into slot kt % S
@@ -224,29 +226,37 @@ __global__ void __launch_bounds__(128, 1)
   }
   __syncwarp();
 
-  // epilogue: thread = row of the tile, 32 columns per TMEM load
+  // epilogue: warp w reads TMEM lanes 32w .. 32w+31 (thread = row, 32 columns
+  // per load) into a row-major tile in the now idle stage memory, then writes
+  // its 32 rows to global memory as whole 512-byte row segments
   const bool ready = mbar_wait(done, 0);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ready) {
-    const int row = m0 + warp * 32 + lane;
+    constexpr int kLd = BN + 4;   // padded row stride (floats): conflict-free float4 stores
+    float* ct = reinterpret_cast<float*>(smem) + warp * 32 * kLd;
 #pragma unroll 1
     for (int c = 0; c < BN; c += 32) {
       uint32_t r[32];
       tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c, r);
-      if (row < M) {
-        float* dst = C + static_cast<int64_t>(row) * N + n0 + c;
-        const int ncol = min(32, N - (n0 + c));
-        if (ncol == 32 && (N & 3) == 0) {
 #pragma unroll
-          for (int q = 0; q < 32; q += 4)
-            *reinterpret_cast<float4*>(dst + q) =
-                make_float4(__uint_as_float(r[q]), __uint_as_float(r[q + 1]), __uint_as_float(r[q + 2]),
-                            __uint_as_float(r[q + 3]));
-        } else {
-#pragma unroll
-          for (int q = 0; q < 32; ++q)
-            if (q < ncol) dst[q] = __uint_as_float(r[q]);
-        }
+      for (int q = 0; q < 32; q += 4)
+        *reinterpret_cast<float4*>(ct + lane * kLd + c + q) =
+            make_float4(__uint_as_float(r[q]), __uint_as_float(r[q + 1]), __uint_as_float(r[q + 2]),
+                        __uint_as_float(r[q + 3]));
+    }
+    __syncwarp();
+    const int ncol = min(BN, N - n0);
+    const bool vec = ncol == BN && (N & 3) == 0;
+#pragma unroll 1
+    for (int i = 0; i < 32; ++i) {
+      const int row = m0 + warp * 32 + i;
+      if (row >= M) break;
+      float* dst = C + static_cast<int64_t>(row) * N + n0;
+      const float* srcr = ct + i * kLd;
+      if (vec) {
+        *reinterpret_cast<float4*>(dst + lane * 4) = *reinterpret_cast<const float4*>(srcr + lane * 4);
+      } else {
+        for (int q = lane; q < ncol; q += 32) dst[q] = srcr[q];
       }
     }
   }
@@ -366,6 +376,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   uint64_t* done = mma_done + kConvStages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
 
+  griddep_launch();
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int q = 0; q < kConvStages; ++q) mbar_init(&mma_done[q], 1);
@@ -404,6 +415,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  griddep_wait();   // the source maps belong to earlier kernels
 
   const int HW = c.Hs * c.Ws, src_dim = c.Cs * HW, out_dim = c.Co * c.Ho * c.Wo;
   const int64_t tiles = conv_tiles(c, a.R);
@@ -553,7 +565,7 @@ bool launch_tc(cudaStream_t st, int64_t M, int N, int K, const void* A, const vo
     tblo = tb;
   }
   dim3 grid((N + BN - 1) / BN, static_cast<unsigned>((M + BM - 1) / BM));
-  k_gemm_tc<KIND><<<grid, 128, Cfg::kSmem, st>>>(ta, talo, tb, tblo, static_cast<int>(M), N, K, C);
+  launch_pdl(k_gemm_tc<KIND>, grid, dim3(128), Cfg::kSmem, st, ta, talo, tb, tblo, static_cast<int>(M), N, K, C);
   return true;
 }
 
@@ -650,7 +662,7 @@ bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const
   const double macs = (double)R * g.c_out * g.h_out * g.w_out * g.c_in * g.k * g.k;
   int tk = prof_begin(st, dir == 0 ? "conv_tc_bf16_fwd" : "conv_tc_bf16_T", 2.0 * macs,
                       (double)R * src_dim * 2 + (double)R * out_dim * 4);
-  k_conv_tc<<<grid, kConvThreads, L.total, st>>>(a);
+  launch_pdl(k_conv_tc, dim3(grid), dim3(kConvThreads), L.total, st, a);
   prof_end(st, tk);
   return true;
 }
