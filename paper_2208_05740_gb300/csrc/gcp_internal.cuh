@@ -268,6 +268,7 @@ struct ConvPhase {
   int ph, pw, Hf, Wf;        // the phase's output pixels form an Hf x Wf grid
   int rh, rw, nkh, nkw;      // its taps
   int kb0, nkb;              // its weight k-blocks
+  int tile0, ntiles;         // its 128-row GEMM tiles (set for a given batch by the launcher)
 };
 struct ConvPlan {
   int dir, Cs, Hs, Ws, Csp;  // source map

@@ -295,9 +295,13 @@ struct ConvTcArgs {
   float* out;                // [R, Co*Ho*Wo], channel-major
 };
 
-constexpr int kConvThreads = 256;
-
-constexpr int kConvStages = 3;   // A blocks in flight
+// Roles of the 416 threads: warps 0-3 the epilogue (warp w reads TMEM lanes
+// 32w .. 32w+31), warps 4-11 the producers (staging and A blocks), warp 12
+// the MMA issuer (one lane).
+constexpr int kConvEpiWarps = 4, kConvProdWarps = 8;
+constexpr int kConvProdThreads = kConvProdWarps * 32;
+constexpr int kConvThreads = (kConvEpiWarps + kConvProdWarps + 1) * 32;
+constexpr int kConvStages = 4;   // A blocks in flight
 struct ConvSmem {
   int b_off, stg_off, tab_off, bar_off, total;
 };
@@ -306,60 +310,77 @@ __host__ __device__ inline ConvSmem conv_smem_layout(int Kp, int Np, int stg_row
   L.b_off = kConvStages * kTileA;                          // after the A stages
   L.stg_off = L.b_off + (Kp / 64) * Np * kRowBytes;        // weights: Kp/64 tiles of Np rows
   L.tab_off = (L.stg_off + stg_rows * Ws * Csp * 2 + 15) & ~15;
-  L.bar_off = L.tab_off + (Kp / 8) * 4;                    // chunk table: one word per 8 K columns
-  L.total = L.bar_off + 64 + 1024;                         // barriers, TMEM slot, alignment slack
+  L.bar_off = (L.tab_off + (Kp / 8) * 4 + 7) & ~7;         // chunk table: one word per 8 K columns
+  // barriers: full/empty per A stage, full/empty per accumulator, abort flag, TMEM slot
+  L.total = L.bar_off + (2 * kConvStages + 4) * 8 + 16 + 1024;
   return L;
 }
 
-// Tile geometry: phase, first GEMM row of the phase, rows r0 .. r0 + nrt - 1
-// of the batch, and the source-map rows sh0 .. sh0 + nsh - 1 the tile reads
-// (per batch row; the whole map when the tile spans several batch rows).
+// Named barrier 1 over the producer warps with an OR of v over them: every
+// producer gets the same answer, so they leave their loop together.
+__device__ __forceinline__ bool prod_sync_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kConvProdThreads)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Tile geometry: phase, GEMM rows [m0, mend) of the phase (phase-local), batch
+// rows r0 .. r0 + nrt - 1, and the source-map rows sh0 .. sh0 + nsh - 1 the
+// tile reads (per batch row; the whole map when the tile spans several batch
+// rows). 32-bit arithmetic: the launcher requires R * Ho * Wo < 2^31.
 struct ConvTile {
   int f, nrt, sh0, nsh;
-  int64_t m0, mend, r0;      // GEMM rows [m0, mend) of phase f (phase-local), first batch row
+  int m0, mend, r0;
 };
-__host__ __device__ inline ConvTile conv_tile(const ConvPlan& c, int64_t R, int64_t t) {
+__host__ __device__ inline ConvTile conv_tile(const ConvPlan& c, int R, int t) {
   ConvTile T{};
-  int64_t tb = 0;
-  for (int q = 0; q < c.nph; ++q) {
-    const int64_t Pf = (int64_t)c.f[q].Hf * c.f[q].Wf, nt = (R * Pf + 127) / 128;
-    if (t < tb + nt || q == c.nph - 1) {
-      T.f = q;
-      T.m0 = (t - tb) * 128;
-      T.mend = T.m0 + 128 < R * Pf ? T.m0 + 128 : R * Pf;
-      const ConvPhase& f = c.f[q];
-      T.r0 = T.m0 / Pf;
-      const int64_t rl = (T.mend - 1) / Pf;
-      T.nrt = (int)(rl - T.r0 + 1);
-      T.sh0 = 0;
-      T.nsh = c.Hs;
-      if (T.nrt == 1) {
-        const int i_lo = (int)((T.m0 - T.r0 * Pf) / f.Wf), i_hi = (int)((T.mend - 1 - T.r0 * Pf) / f.Wf);
-        const int s = c.dir == 0 ? 1 : c.stride;
-        const int o_lo = f.ph + s * i_lo, o_hi = f.ph + s * i_hi;   // output rows
-        int lo, hi;
-        if (c.dir == 0) {
-          lo = o_lo * c.stride - c.pad;
-          hi = o_hi * c.stride + c.k - 1 - c.pad;
-        } else {
-          lo = (o_lo + c.pad - (f.rh + s * (f.nkh - 1))) / s;   // exact: same residue
-          hi = (o_hi + c.pad - f.rh) / s;
-          if (o_lo + c.pad - (f.rh + s * (f.nkh - 1)) < 0) lo = 0;
-        }
-        lo = lo < 0 ? 0 : lo;
-        hi = hi > c.Hs - 1 ? c.Hs - 1 : hi;
-        T.sh0 = lo;
-        T.nsh = hi >= lo ? hi - lo + 1 : 0;
-      }
-      return T;
+  int q = 0;
+  while (q + 1 < c.nph && t >= c.f[q + 1].tile0) ++q;
+  const ConvPhase& f = c.f[q];
+  const int Pf = f.Hf * f.Wf;
+  T.f = q;
+  T.m0 = (t - f.tile0) * 128;
+  T.mend = T.m0 + 128 < R * Pf ? T.m0 + 128 : R * Pf;
+  T.r0 = T.m0 / Pf;
+  T.nrt = (T.mend - 1) / Pf - T.r0 + 1;
+  T.sh0 = 0;
+  T.nsh = c.Hs;
+  if (T.nrt == 1) {
+    const int i_lo = (T.m0 - T.r0 * Pf) / f.Wf, i_hi = (T.mend - 1 - T.r0 * Pf) / f.Wf;
+    const int s = c.dir == 0 ? 1 : c.stride;
+    const int o_lo = f.ph + s * i_lo, o_hi = f.ph + s * i_hi;   // output rows
+    int lo, hi;
+    if (c.dir == 0) {
+      lo = o_lo * c.stride - c.pad;
+      hi = o_hi * c.stride + c.k - 1 - c.pad;
+    } else {
+      const int x = o_lo + c.pad - (f.rh + s * (f.nkh - 1));   // a multiple of s when >= 0
+      lo = x > 0 ? x / s : 0;
+      hi = (o_hi + c.pad - f.rh) / s;
     }
-    tb += nt;
+    lo = lo < 0 ? 0 : lo;
+    hi = hi > c.Hs - 1 ? c.Hs - 1 : hi;
+    T.sh0 = lo;
+    T.nsh = hi >= lo ? hi - lo + 1 : 0;
   }
   return T;
 }
-__host__ __device__ inline int64_t conv_tiles(const ConvPlan& c, int64_t R) {
-  int64_t n = 0;
-  for (int q = 0; q < c.nph; ++q) n += (R * c.f[q].Hf * c.f[q].Wf + 127) / 128;
+// Tile ranges of the phases for a batch of R rows; returns the tile count.
+inline int conv_set_tiles(ConvPlan& c, int R) {
+  int n = 0;
+  for (int q = 0; q < c.nph; ++q) {
+    c.f[q].tile0 = n;
+    c.f[q].ntiles = (R * c.f[q].Hf * c.f[q].Wf + 127) / 128;
+    n += c.f[q].ntiles;
+  }
   return n;
 }
 
@@ -372,20 +393,30 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   uint8_t* Bs = smem + lay.b_off;
   __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(smem + lay.stg_off);
   uint32_t* tab = reinterpret_cast<uint32_t*>(smem + lay.tab_off);
-  uint64_t* mma_done = reinterpret_cast<uint64_t*>(smem + lay.bar_off);   // [kConvStages]
-  uint64_t* done = mma_done + kConvStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* a_full = reinterpret_cast<uint64_t*>(smem + lay.bar_off);   // [kConvStages]
+  uint64_t* a_empty = a_full + kConvStages;                              // [kConvStages]
+  uint64_t* acc_full = a_empty + kConvStages;                            // [2]
+  uint64_t* acc_empty = acc_full + 2;                                    // [2]
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(acc_empty + 2);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2) + 2;
 
   griddep_launch();
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int q = 0; q < kConvStages; ++q) mbar_init(&mma_done[q], 1);
-    mbar_init(done, 1);
+    for (int q = 0; q < kConvStages; ++q) {
+      mbar_init(&a_full[q], kConvProdThreads);
+      mbar_init(&a_empty[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&acc_full[q], 1);
+      mbar_init(&acc_empty[q], kConvEpiWarps * 32);
+    }
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(a.tmem_cols)
+                 "r"(2 * a.tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -418,103 +449,136 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   griddep_wait();   // the source maps belong to earlier kernels
 
   const int HW = c.Hs * c.Ws, src_dim = c.Cs * HW, out_dim = c.Co * c.Ho * c.Wo;
-  const int64_t tiles = conv_tiles(c, a.R);
-  const uint32_t id = idesc(1u, BM, c.Np);
+  const int R = (int)a.R;
+  const int tiles = c.f[c.nph - 1].tile0 + c.f[c.nph - 1].ntiles;
   const int s_out = c.dir == 0 ? 1 : c.stride;     // output-pixel step within a phase
-  const int row = tid & (BM - 1), half = tid >> 7;  // GEMM row of the tile; chunks 4*half .. 4*half+3
-  uint32_t g = 0, it = 0;
-  bool ok = true;
-  for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++it) {
-    const ConvTile T = conv_tile(c, a.R, tile);
-    const ConvPhase& f = c.f[T.f];
-    const int Pf = f.Hf * f.Wf;
-    // stage the reachable source rows, channel innermost: one work item = 8
-    // channels of one pixel
-    const int npix = T.nsh * c.Ws, cgroups = c.Csp / 8;
-    for (int64_t item = tid; item < (int64_t)T.nrt * npix * cgroups; item += kConvThreads) {
-      const int cg = (int)(item % cgroups);
-      const int64_t t2 = item / cgroups;
-      const int pw = (int)(t2 % npix), rr = (int)(t2 / npix);
-      const __nv_bfloat16* sp = a.src + (T.r0 + rr) * src_dim + (int64_t)T.sh0 * c.Ws + pw + (int64_t)cg * 8 * HW;
-      uint32_t w[4];
+
+  if (warp >= kConvEpiWarps && warp < kConvEpiWarps + kConvProdWarps) {
+    // ---------------- producers: stage the reachable source rows, build A blocks
+    const int ptid = tid - kConvEpiWarps * 32;
+    const int row = ptid & (BM - 1), half = ptid >> 7;   // GEMM row; chunks 4*half .. 4*half+3
+    uint32_t g = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+      // all producers finished the previous tile (the staging is free again)
+      if (prod_sync_or(*abort_flag != 0)) break;
+      const ConvTile T = conv_tile(c, R, tile);
+      const ConvPhase& f = c.f[T.f];
+      const int Pf = f.Hf * f.Wf;
+      const int npix = T.nsh * c.Ws, cgroups = c.Csp / 8;
+      for (int item = ptid; item < T.nrt * npix * cgroups; item += kConvProdThreads) {
+        const int t2 = item / cgroups, cg = item - t2 * cgroups;
+        const int rr = t2 / npix, pw = t2 - rr * npix;
+        const __nv_bfloat16* sp =
+            a.src + (int64_t)(T.r0 + rr) * src_dim + (T.sh0 * c.Ws + pw + cg * 8 * HW);
+        uint32_t w[4];
 #pragma unroll
-      for (int cc = 0; cc < 8; cc += 2) {
-        const uint32_t lo = cg * 8 + cc < c.Cs ? __bfloat16_as_ushort(sp[(int64_t)cc * HW]) : 0u;
-        const uint32_t hi = cg * 8 + cc + 1 < c.Cs ? __bfloat16_as_ushort(sp[(int64_t)(cc + 1) * HW]) : 0u;
-        w[cc / 2] = lo | (hi << 16);
-      }
-      *reinterpret_cast<uint4*>(stg + ((int64_t)rr * npix + pw) * c.Csp + cg * 8) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-    __syncthreads();
-    // this thread's GEMM row: batch row r, output pixel (oh, ow); its source
-    // pixel for tap (a, b) is (bh + sg_tap * a, bw + sg_tap * b)
-    const int64_t m = T.m0 + row;
-    const bool mv = m < T.mend;
-    const int64_t r = mv ? m / Pf : 0;
-    const int pos = mv ? (int)(m - r * Pf) : 0;
-    const int oh = f.ph + s_out * (pos / f.Wf), ow = f.pw + s_out * (pos % f.Wf), rl = (int)(r - T.r0);
-    const int bh = c.dir == 0 ? oh * c.stride - c.pad : (oh + c.pad - f.rh) / c.stride;
-    const int bw = c.dir == 0 ? ow * c.stride - c.pad : (ow + c.pad - f.rw) / c.stride;
-    const int sg_tap = c.dir == 0 ? 1 : -1;
-    const __nv_bfloat16* srow = stg + (int64_t)rl * T.nsh * c.Ws * c.Csp;
-    for (int kb = 0; kb < f.nkb; ++kb, ++g) {
-      const int sg = g % kConvStages;
-      bool w_ok = true;
-      if (g >= kConvStages) w_ok = mbar_wait(&mma_done[sg], ((g / kConvStages) - 1) & 1);
-      if (!__syncthreads_and(w_ok)) { ok = false; break; }
-      uint8_t* At = As + sg * kTileA;
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        const int j = half * 4 + jj;
-        const uint32_t e = tab[(f.kb0 + kb) * 8 + j];
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (mv && (e & 1u)) {
-          const int sh = bh + sg_tap * (int)((e >> 1) & 0xFFu), sw = bw + sg_tap * (int)((e >> 9) & 0xFFu);
-          if (sh >= T.sh0 && sh < T.sh0 + T.nsh && sh < c.Hs && sw >= 0 && sw < c.Ws)
-            v = *reinterpret_cast<const uint4*>(srow + ((int64_t)(sh - T.sh0) * c.Ws + sw) * c.Csp + (e >> 17));
+        for (int cc = 0; cc < 8; cc += 2) {
+          const uint32_t lo = cg * 8 + cc < c.Cs ? __bfloat16_as_ushort(sp[(int64_t)cc * HW]) : 0u;
+          const uint32_t hi = cg * 8 + cc + 1 < c.Cs ? __bfloat16_as_ushort(sp[(int64_t)(cc + 1) * HW]) : 0u;
+          w[cc / 2] = lo | (hi << 16);
         }
-        *reinterpret_cast<uint4*>(At + row * kRowBytes + ((j ^ (row & 7)) << 4)) = v;
+        *reinterpret_cast<uint4*>(stg + (rr * npix + pw) * c.Csp + cg * 8) = make_uint4(w[0], w[1], w[2], w[3]);
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
+      if (prod_sync_or(*abort_flag != 0)) break;   // staging complete
+      // this thread's GEMM row: batch row r, output pixel (oh, ow); its source
+      // pixel for tap (a, b) is (bh + sg_tap * a, bw + sg_tap * b)
+      const int m = T.m0 + row;
+      const bool mv = m < T.mend;
+      const int r = mv ? m / Pf : 0;
+      const int pos = mv ? m - r * Pf : 0;
+      const int pi = pos / f.Wf;
+      const int oh = f.ph + s_out * pi, ow = f.pw + s_out * (pos - pi * f.Wf), rl = r - T.r0;
+      const int bh = c.dir == 0 ? oh * c.stride - c.pad : (oh + c.pad - f.rh) / c.stride;
+      const int bw = c.dir == 0 ? ow * c.stride - c.pad : (ow + c.pad - f.rw) / c.stride;
+      const int sg_tap = c.dir == 0 ? 1 : -1;
+      const __nv_bfloat16* srow = stg + rl * T.nsh * c.Ws * c.Csp;
+      for (int kb = 0; kb < f.nkb; ++kb, ++g) {
+        const int sg = g % kConvStages;
+        if (*abort_flag) break;   // no barrier inside this loop: leaving alone is safe
+        if (g >= kConvStages && !mbar_wait(&a_empty[sg], ((g / kConvStages) - 1) & 1)) { *abort_flag = 1; break; }
+        uint8_t* At = As + sg * kTileA;
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int j = half * 4 + jj;
+          const uint32_t e = tab[(f.kb0 + kb) * 8 + j];
+          uint4 v = make_uint4(0u, 0u, 0u, 0u);
+          if (mv && (e & 1u)) {
+            const int sh = bh + sg_tap * (int)((e >> 1) & 0xFFu), sw = bw + sg_tap * (int)((e >> 9) & 0xFFu);
+            if (sh >= T.sh0 && sh < T.sh0 + T.nsh && sh < c.Hs && sw >= 0 && sw < c.Ws)
+              v = *reinterpret_cast<const uint4*>(srow + ((sh - T.sh0) * c.Ws + sw) * c.Csp + (e >> 17));
+          }
+          *reinterpret_cast<uint4*>(At + row * kRowBytes + ((j ^ (row & 7)) << 4)) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&a_full[sg]);
+      }
+    }
+  } else if (warp == kConvEpiWarps + kConvProdWarps) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t id = idesc(1u, BM, c.Np);
+      uint32_t g = 0, it = 0;
+      for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+        if (*abort_flag) break;
+        const ConvTile T = conv_tile(c, R, tile);
+        const ConvPhase& f = c.f[T.f];
+        const uint32_t b = it & 1, acc = tmem + b * a.tmem_cols;
+        if (it >= 2 && !mbar_wait(&acc_empty[b], ((it >> 1) - 1) & 1)) { *abort_flag = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ab = smem_u32(At), bb = smem_u32(Bs + (f.kb0 + kb) * c.Np * kRowBytes);
+        bool ok = true;
+        for (int kb = 0; kb < f.nkb; ++kb, ++g) {
+          const int sg = g % kConvStages;
+          if (!mbar_wait(&a_full[sg], (g / kConvStages) & 1)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t ab = smem_u32(As + sg * kTileA), bb = smem_u32(Bs + (f.kb0 + kb) * c.Np * kRowBytes);
 #pragma unroll
-        for (int k4 = 0; k4 < kRowBytes / 32; ++k4)
-          umma<0>(tmem, sdesc(ab + k4 * 32), sdesc(bb + k4 * 32), id, (kb | k4) != 0);
-        umma_commit(&mma_done[sg]);
-        if (kb == f.nkb - 1) umma_commit(done);
+          for (int k4 = 0; k4 < kRowBytes / 32; ++k4)
+            umma<0>(acc, sdesc(ab + k4 * 32), sdesc(bb + k4 * 32), id, (kb | k4) != 0);
+          umma_commit(&a_empty[sg]);   // the stage is free once these MMAs have read it
+        }
+        if (!ok) { *abort_flag = 1; break; }
+        umma_commit(&acc_full[b]);     // the tile's accumulator is complete
       }
     }
-    if (!ok) break;
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31; warps w and w+4 split the columns
-    const bool d_ok = __syncthreads_and(mbar_wait(done, it & 1));
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!d_ok) { ok = false; break; }
-    const int erow = (warp & 3) * 32 + lane;
-    const int64_t em = T.m0 + erow;
-    const int64_t er = em / Pf;
-    const int epos = (int)(em - er * Pf);
-    const int eoh = f.ph + s_out * (epos / f.Wf), eow = f.pw + s_out * (epos % f.Wf);
-    for (int col = (warp >> 2) * 32; col < c.Np; col += 64) {
-      uint32_t v[32];
-      tmem_ld32(tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + col, v);
-      if (em < T.mend) {
-        float* dst = a.out + er * out_dim + (int64_t)eoh * c.Wo + eow;
-        const int64_t cstride = (int64_t)c.Ho * c.Wo;
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: TMEM -> global, channel-major output
+    uint32_t it = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+      // decisions are warp-uniform: the TMEM loads below are warp-collective
+      if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
+      const ConvTile T = conv_tile(c, R, tile);
+      const ConvPhase& f = c.f[T.f];
+      const int Pf = f.Hf * f.Wf;
+      const uint32_t b = it & 1;
+      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[b], (it >> 1) & 1))) { *abort_flag = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int erow = warp * 32 + lane;
+      const int em = T.m0 + erow;
+      const int er = em / Pf;
+      const int epos = em - er * Pf;
+      const int epi = epos / f.Wf;
+      const int eoh = f.ph + s_out * epi, eow = f.pw + s_out * (epos - epi * f.Wf);
+      float* dst = a.out + (int64_t)er * out_dim + (eoh * c.Wo + eow);
+      const int64_t cstride = (int64_t)c.Ho * c.Wo;
+      for (int col = 0; col < c.Np; col += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem + b * a.tmem_cols + (static_cast<uint32_t>(warp * 32) << 16) + col, v);
+        if (em < T.mend) {
 #pragma unroll
-        for (int t = 0; t < 32; ++t)
-          if (col + t < c.Co) dst[(col + t) * cstride] = __uint_as_float(v[t]);
+          for (int t = 0; t < 32; ++t)
+            if (col + t < c.Co) dst[(col + t) * cstride] = __uint_as_float(v[t]);
+        }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&acc_empty[b]);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * a.tmem_cols)
+                 : "memory");
   }
 }
 
@@ -609,18 +673,18 @@ bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const
   ConvTcArgs a{};
   ConvPlan& c = a.c;
   if (!Wp || !conv_plan(g, dir, c) || c.Kp != Kp || c.Np != Np || Np > 256) return false;
+  if (R * (int64_t)c.Ho * c.Wo >= (int64_t)INT32_MAX - 128) return false;   // 32-bit tile arithmetic
   a.R = R;
+  const int tiles = conv_set_tiles(c, (int)R);
   // staging rows: the largest window over the tiles (tile starts repeat with
   // period P_f within a phase, so the first P_f tiles of each phase cover all)
-  int64_t tb = 0;
   int rows = 0;
   for (int q = 0; q < c.nph; ++q) {
-    const int64_t Pf = (int64_t)c.f[q].Hf * c.f[q].Wf, nt = (R * Pf + 127) / 128;
-    for (int64_t t = 0; t < std::min<int64_t>(nt, Pf + 1); ++t) {
-      const ConvTile T = conv_tile(c, R, tb + t);
+    const int Pf = c.f[q].Hf * c.f[q].Wf;
+    for (int t = 0; t < std::min(c.f[q].ntiles, Pf + 1); ++t) {
+      const ConvTile T = conv_tile(c, (int)R, c.f[q].tile0 + t);
       rows = std::max(rows, T.nrt == 1 ? T.nsh : T.nrt * c.Hs);
     }
-    tb += nt;
   }
   a.stg_rows = std::max(rows, 1);
   int tc = 32;
@@ -654,9 +718,9 @@ bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const
     return true;  // reported by the caller's launch status
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc, kConvThreads, L.total);
-  per_sm = std::max(1, std::min(per_sm, 512 / tc));   // TMEM columns of the resident CTAs
-  const int64_t tiles = conv_tiles(c, R);
-  const int grid = (int)std::min<int64_t>(tiles, (int64_t)n_sm * per_sm);
+  if (2 * tc > 512) return false;
+  per_sm = std::max(1, std::min(per_sm, 512 / (2 * tc)));   // TMEM columns of the resident CTAs (two accumulators)
+  const int grid = std::min(tiles, n_sm * per_sm);
   // algorithmic work: the convolution's multiply-adds (2 flops each); bytes:
   // source read and output written once
   const double macs = (double)R * g.c_out * g.h_out * g.w_out * g.c_in * g.k * g.k;
