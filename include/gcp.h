@@ -212,8 +212,9 @@ GCP_API gcp_status gcp_optimize_batch(gcp_ctx* ctx, void* duals, const gcp_opt_p
  * FP32/BF16 bound [R] to out (device). gcp_grad_device runs the adjoint with
  * the per-row seed grad_out [R] (device) and writes vector-Jacobian products
  * into g_alpha/g_beta/g_gamma (device, export layouts). Work is enqueued on
- * `stream` (cudaStream_t as void*; NULL = the context stream) and the call
- * returns without synchronising. */
+ * `stream` (cudaStream_t as void*; NULL = the context stream, which does not
+ * synchronise with the legacy default stream -- pass cudaStreamLegacy to
+ * order the work with it) and the call returns without synchronising. */
 GCP_API gcp_status gcp_bound_device(gcp_ctx* ctx, void* duals, int32_t prec, const float* alpha,
                                     const float* beta, const float* gamma, float* out, void* stream);
 GCP_API gcp_status gcp_grad_device(gcp_ctx* ctx, void* duals, int32_t prec, const float* alpha,

@@ -222,14 +222,17 @@ __device__ __forceinline__ void cut_sums_row_cert(const CutCSC<double>& c, const
 
 // One ascent step on x. Adam (Kingma & Ba): bias-corrected moments m, v are
 // read and updated in place (values, loaded by the caller ahead of time); the
-// float chain uses the fast reciprocal divide (a step size, not a bound).
+// float chain uses the approximate square root and reciprocal divide (a step
+// size, not a bound).
 template <typename T>
 __device__ __forceinline__ T step_apply(const StepArgs<T>& st, T x, T grad, T lr, T& m, T& v) {
   if (st.mode == 1) return x + lr * grad;
   m = st.b1 * m + (T(1) - st.b1) * grad;
   v = st.b2 * v + (T(1) - st.b2) * grad * grad;
   if constexpr (std::is_same<T, float>::value) {
-    return x + lr * __fdividef(m * st.ic1, __fsqrt_rn(v * st.ic2) + st.eps);
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v * st.ic2));   // a step size, not a bound
+    return x + lr * __fdividef(m * st.ic1, r + st.eps);
   } else {
     return x + lr * (m / st.c1) / (sqrt(v / st.c2) + st.eps);
   }
@@ -918,7 +921,10 @@ __global__ void k_gather(GatherArgs<T> a) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.R * a.N) {
     // threads past the cuts: the projected step on beta from dg/dbeta
-    // written by the adjoint (slots holding a split only)
+    // written by the adjoint (slots holding a split only). The launch covers
+    // these threads only when it steps (modes 1 and 2); in mode 0 they are
+    // the tail of the last block and must leave beta alone.
+    if (a.st.mode == 0) return;
     i -= a.R * a.N;
     if (i >= a.R * a.M) return;
     const int64_t r = i / a.M;

@@ -405,6 +405,16 @@ def _dptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def torch_stream_handle(stream=None) -> int:
+    """cudaStream_t of a torch stream for the device entry points. torch's
+    legacy default stream has handle 0, which the library reads as "the
+    context's own stream"; it is passed as cudaStreamLegacy (1) instead so the
+    work stays ordered with torch's."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream or 1
+
+
 def make_bound_function():
     """torch.autograd.Function around gcp_bound_device / gcp_grad_device."""
     import torch
@@ -414,7 +424,7 @@ def make_bound_function():
         def forward(fctx, alpha, beta, gamma, ctx: Context, D: Duals, prec: int):
             alpha, beta, gamma = alpha.contiguous(), beta.contiguous(), gamma.contiguous()
             out = torch.empty(D.rows, dtype=torch.float32, device=alpha.device)
-            ctx.bound_device(D, prec, alpha, beta, gamma, out, torch.cuda.current_stream().cuda_stream)
+            ctx.bound_device(D, prec, alpha, beta, gamma, out, torch_stream_handle())
             fctx.save_for_backward(alpha, beta, gamma)
             fctx.gcp = (ctx, D, prec)
             return out
@@ -425,7 +435,7 @@ def make_bound_function():
             ctx, D, prec = fctx.gcp
             ga, gb, gg = torch.empty_like(alpha), torch.zeros_like(beta), torch.empty_like(gamma)
             ctx.grad_device(D, prec, alpha, beta, gamma, grad_out.contiguous().float(), ga, gb, gg,
-                            torch.cuda.current_stream().cuda_stream)
+                            torch_stream_handle())
             return ga, gb, gg, None, None, None
 
     return GCPBound
