@@ -74,6 +74,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
+// The same with a suspend-time hint: each try may suspend the thread in
+// hardware for up to a microsecond until the phase completes, instead of
+// spinning and taking issue slots from the warps doing the work.
+__device__ __forceinline__ bool mbar_wait_idle(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (uint32_t i = 0;; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
+        : "memory");
+    if (ok) return true;
+    if ((i & 15u) == 15u && clock64() - t0 > kWaitCycles) {
+      atomicOr(&g_tc_err, 1u);
+      return false;
+    }
+  }
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
@@ -188,7 +208,7 @@ __global__ void __launch_bounds__(128, 1)
     for (int kt = 0; kt < KT; ++kt) {
       const int s = kt % Cfg::kStages;
       const uint32_t ph = (kt / Cfg::kStages) & 1;
-      if (!mbar_wait(&empty[s], ph ^ 1)) break;
+      if (!mbar_wait_idle(&empty[s], ph ^ 1)) break;
       uint8_t* st = smem + s * Cfg::kStageBytes;
       mbar_expect_tx(&full[s], Cfg::kStageBytes);
       const int x = kt * Cfg::kKElems;
@@ -206,7 +226,7 @@ __global__ void __launch_bounds__(128, 1)
     for (int kt = 0; kt < KT && ok; ++kt) {
       const int s = kt % Cfg::kStages;
       const uint32_t ph = (kt / Cfg::kStages) & 1;
-      if (!mbar_wait(&full[s], ph)) { ok = false; break; }
+      if (!mbar_wait_idle(&full[s], ph)) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a = smem_u32(smem + s * Cfg::kStageBytes);
       const uint32_t b = a + kTileA;
@@ -229,7 +249,7 @@ __global__ void __launch_bounds__(128, 1)
   // epilogue: warp w reads TMEM lanes 32w .. 32w+31 (thread = row, 32 columns
   // per load) into a row-major tile in the now idle stage memory, then writes
   // its 32 rows to global memory as whole 512-byte row segments
-  const bool ready = mbar_wait(done, 0);
+  const bool ready = mbar_wait_idle(done, 0);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ready) {
     constexpr int kLd = BN + 4;   // padded row stride (floats): conflict-free float4 stores
@@ -464,20 +484,33 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       const ConvTile T = conv_tile(c, R, tile);
       const ConvPhase& f = c.f[T.f];
       const int Pf = f.Hf * f.Wf;
-      const int npix = T.nsh * c.Ws, cgroups = c.Csp / 8;
-      for (int item = ptid; item < T.nrt * npix * cgroups; item += kConvProdThreads) {
-        const int t2 = item / cgroups, cg = item - t2 * cgroups;
-        const int rr = t2 / npix, pw = t2 - rr * npix;
+      // one work item = 8 channels of one pixel; consecutive threads take
+      // consecutive pixels of the same channel group, so each load reads a
+      // contiguous run of a channel's row. The (pixel, group, row) position
+      // advances by additions from one item to the next.
+      const int npix = T.nsh * c.Ws, cgroups = c.Csp / 8, nitems = T.nrt * npix * cgroups;
+      int pw = 0, cg = 0, rr = 0;
+      if (nitems > 0) {
+        pw = ptid % npix;
+        cg = (ptid / npix) % cgroups;
+        rr = ptid / (npix * cgroups);
+      }
+      for (int item = ptid; item < nitems; item += kConvProdThreads) {
         const __nv_bfloat16* sp =
             a.src + (int64_t)(T.r0 + rr) * src_dim + (T.sh0 * c.Ws + pw + cg * 8 * HW);
         uint32_t w[4];
 #pragma unroll
         for (int cc = 0; cc < 8; cc += 2) {
-          const uint32_t lo = cg * 8 + cc < c.Cs ? __bfloat16_as_ushort(sp[(int64_t)cc * HW]) : 0u;
-          const uint32_t hi = cg * 8 + cc + 1 < c.Cs ? __bfloat16_as_ushort(sp[(int64_t)(cc + 1) * HW]) : 0u;
+          const uint32_t lo = cg * 8 + cc < c.Cs ? __bfloat16_as_ushort(sp[cc * HW]) : 0u;
+          const uint32_t hi = cg * 8 + cc + 1 < c.Cs ? __bfloat16_as_ushort(sp[(cc + 1) * HW]) : 0u;
           w[cc / 2] = lo | (hi << 16);
         }
         *reinterpret_cast<uint4*>(stg + (rr * npix + pw) * c.Csp + cg * 8) = make_uint4(w[0], w[1], w[2], w[3]);
+        pw += kConvProdThreads;
+        while (pw >= npix) {
+          pw -= npix;
+          if (++cg == cgroups) { cg = 0; ++rr; }
+        }
       }
       if (prod_sync_or(*abort_flag != 0)) break;   // staging complete
       // this thread's GEMM row: batch row r, output pixel (oh, ow); its source
@@ -495,7 +528,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       for (int kb = 0; kb < f.nkb; ++kb, ++g) {
         const int sg = g % kConvStages;
         if (*abort_flag) break;   // no barrier inside this loop: leaving alone is safe
-        if (g >= kConvStages && !mbar_wait(&a_empty[sg], ((g / kConvStages) - 1) & 1)) { *abort_flag = 1; break; }
+        if (g >= kConvStages && !mbar_wait_idle(&a_empty[sg], ((g / kConvStages) - 1) & 1)) { *abort_flag = 1; break; }
         uint8_t* At = As + sg * kTileA;
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
@@ -523,12 +556,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
         const ConvTile T = conv_tile(c, R, tile);
         const ConvPhase& f = c.f[T.f];
         const uint32_t b = it & 1, acc = tmem + b * a.tmem_cols;
-        if (it >= 2 && !mbar_wait(&acc_empty[b], ((it >> 1) - 1) & 1)) { *abort_flag = 1; break; }
+        if (it >= 2 && !mbar_wait_idle(&acc_empty[b], ((it >> 1) - 1) & 1)) { *abort_flag = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         bool ok = true;
         for (int kb = 0; kb < f.nkb; ++kb, ++g) {
           const int sg = g % kConvStages;
-          if (!mbar_wait(&a_full[sg], (g / kConvStages) & 1)) { ok = false; break; }
+          if (!mbar_wait_idle(&a_full[sg], (g / kConvStages) & 1)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t ab = smem_u32(As + sg * kTileA), bb = smem_u32(Bs + (f.kb0 + kb) * c.Np * kRowBytes);
 #pragma unroll
@@ -551,7 +584,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       const ConvPhase& f = c.f[T.f];
       const int Pf = f.Hf * f.Wf;
       const uint32_t b = it & 1;
-      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[b], (it >> 1) & 1))) { *abort_flag = 1; break; }
+      if (!__all_sync(0xffffffffu, mbar_wait_idle(&acc_full[b], (it >> 1) & 1))) { *abort_flag = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int erow = warp * 32 + lane;
       const int em = T.m0 + erow;
