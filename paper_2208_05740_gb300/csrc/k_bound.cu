@@ -998,6 +998,19 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_relax(CertArgs<
   const int slot = lane_split(a.sp, w.s, a.M, a.layer, w.c, w.lane, sign);
   ChunkCuts<double> cc;
   chunk_cuts(a.csc, a.N, a.d, w.c, w.lane, cc);
+  // row-independent: the neuron's bounds after its split, 1/(u - l) (pi only
+  // has to lie in [0, C] for the certificate to hold), and Higham's factors
+  // for the sparse sums (the entry counts per kind do not depend on the row)
+  double lo0 = 0.0, hi0 = 0.0;
+  if (w.on) {
+    lo0 = a.lo[j];
+    hi0 = a.hi[j];
+    if (slot >= 0) {
+      if (sign > 0) lo0 = fmax(lo0, 0.0); else hi0 = fmin(hi0, 0.0);
+    }
+  }
+  const double inv_ul = hi0 > lo0 ? 1.0 / (hi0 - lo0) : 0.0;
+  double gt = 0.0, gg_n = 0.0, gs_n = 0.0;
   for (int k = 0; k < a.K; ++k) {
     const int64_t r = (int64_t)w.s * a.K + k;
     double sum[3], abs_[3];
@@ -1008,18 +1021,20 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_relax(CertArgs<
     // sparse sums in round-to-nearest with their Higham error bounds
     double t = sum[GCP_VAR_X], gg = sum[GCP_VAR_XHAT], sq = sum[GCP_VAR_Z];
     double ta = abs_[GCP_VAR_X];
-    int nt = cnt_[GCP_VAR_X];
-    double lo = a.lo[j], hi = a.hi[j];
+    const double lo = lo0, hi = hi0;
     if (slot >= 0) {
       const double bv = (double)a.beta[r * a.M + slot];
-      if (sign > 0) { t -= bv; lo = fmax(lo, 0.0); }
-      else { t += bv; hi = fmin(hi, 0.0); }
+      if (sign > 0) t -= bv; else t += bv;
       ta = __dadd_ru(ta, fabs(bv));
-      ++nt;
     }
-    const double et = __dmul_ru(gamma_of(nt), ta);
-    const double eg = __dmul_ru(gamma_of(cnt_[GCP_VAR_XHAT]), abs_[GCP_VAR_XHAT]);
-    const double es = __dmul_ru(gamma_of(cnt_[GCP_VAR_Z]), abs_[GCP_VAR_Z]);
+    if (k == 0) {
+      gt = gamma_of(cnt_[GCP_VAR_X] + (slot >= 0 ? 1 : 0));
+      gg_n = gamma_of(cnt_[GCP_VAR_XHAT]);
+      gs_n = gamma_of(cnt_[GCP_VAR_Z]);
+    }
+    const double et = __dmul_ru(gt, ta);
+    const double eg = __dmul_ru(gg_n, abs_[GCP_VAR_XHAT]);
+    const double es = __dmul_ru(gs_n, abs_[GCP_VAR_Z]);
     const int64_t yi = (a.y_per_spec ? (int64_t)k : r) * a.d + j;
     const double y = a.y[yi];
     const double ey = __dmul_ru(a.gamma_n, (double)a.yabs[yi]);
@@ -1043,7 +1058,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_relax(CertArgs<
     } else {
       // unstable: explicit duals pi, gamma_r = C - pi, tau, mu = M - tau (all >= 0)
       const double C = fmax(nh, 0.0), Mm = fmax(-nh, 0.0);
-      const double p0 = (hi * C - sq) / (hi - lo);
+      const double p0 = (hi * C - sq) * inv_ul;
       const double pi = fmin(fmax(p0, 0.0), C);
       const double gr = C - pi;
       const double al = fmin(fmax((double)a.alpha[r * a.d + j], 0.0), 1.0);
@@ -1083,6 +1098,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_conc(int64_t R,
   const int j = w.j;
   ChunkCuts<double> cc;
   chunk_cuts(csc, N, d0, w.c, w.lane, cc);
+  double gh = 0.0;   // Higham's factor of the input neuron's cut sum (the same for every row)
   for (int k = 0; k < K; ++k) {
     const int64_t r = (int64_t)w.s * K + k;
     double sum[3], abs_[3];
@@ -1091,7 +1107,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_conc(int64_t R,
     double part = 0.0;
     if (w.on) {
       const double h = sum[GCP_VAR_X];
-      const double eh = __dmul_ru(gamma_of(cnt_[GCP_VAR_X]), abs_[GCP_VAR_X]);
+      if (k == 0) gh = gamma_of(cnt_[GCP_VAR_X]);
+      const double eh = __dmul_ru(gh, abs_[GCP_VAR_X]);
       const double y = y0[r * d0 + j];
       const double ey = __dmul_ru(gamma_n, (double)y0abs[r * d0 + j]);
       const double c_lo = __dadd_rd(__dsub_rd(-y, ey), __dsub_rd(h, eh));
