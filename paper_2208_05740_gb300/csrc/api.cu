@@ -773,11 +773,11 @@ struct TcOps<float> {
   static bool ok(int K) { return tc_available(K, false); }
   static bool bwd(cudaStream_t st, const Net& n, int i, int64_t R, const float* a, const float* alo, float* y) {
     const LayerGeom& g = n.geom[i - 1];
-    return gemm_tc_tf32x3(st, R, g.d_in, g.d_out, a, alo, n.WT32hi[i - 1], n.WT32lo[i - 1], y);
+    return gemm_tc_tf32x3(st, R, g.d_in, g.d_out, a, n.WT32hi[i - 1], n.WT32lo[i - 1], y);
   }
   static bool fwd(cudaStream_t st, const Net& n, int i, int64_t R, const float* a, const float* alo, float* y) {
     const LayerGeom& g = n.geom[i - 1];
-    return gemm_tc_tf32x3(st, R, g.d_out, g.d_in, a, alo, n.W32hi[i - 1], n.W32lo[i - 1], y);
+    return gemm_tc_tf32x3(st, R, g.d_out, g.d_in, a, n.W32hi[i - 1], n.W32lo[i - 1], y);
   }
 };
 template <>
@@ -857,12 +857,7 @@ gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, 
   if (!part) return s;
   T* g = (T*)b.ws("g", (size_t)std::max<int64_t>(R, 1) * sizeof(T), &s);
   if (!g) return s;
-  const bool split = std::is_same<Top, float>::value && std::is_same<T, float>::value;
-  float* lo = nullptr;
-  if (split && b.tc) {
-    lo = (float*)b.ws("nu_lo", (size_t)R * b.dmax() * 4, &s);
-    if (!lo) return s;
-  }
+  float* lo = nullptr;   // no tf32 low plane: the tensor-core GEMM splits fp32 operands itself
   T* E = nullptr;
   if (with_adjoint_start && b.nnz) {
     E = (T*)b.ws("E", (size_t)b.nnz * R * sizeof(T), &s);
@@ -925,12 +920,7 @@ gcp_status run_adjoint(Ctx& c, Batch& b, cudaStream_t st, const StepArgs<T>& ste
   if (!abuf || !y) return s;
   T* E = b.nnz ? (T*)b.ws("E", (size_t)b.nnz * R * sizeof(T), &s) : nullptr;
   if (b.nnz && !E) return s;
-  const bool split = std::is_same<Top, float>::value && std::is_same<T, float>::value;
-  float* lo = nullptr;
-  if (split && b.tc) {
-    lo = (float*)b.ws("nu_lo", (size_t)R * b.dmax() * 4, &s);
-    if (!lo) return s;
-  }
+  float* lo = nullptr;   // no tf32 low plane: the tensor-core GEMM splits fp32 operands itself
   T *ma = nullptr, *va = nullptr, *mb = nullptr, *vb = nullptr, *mg = nullptr, *vg = nullptr;
   int64_t nal = 0;
   for (int i = 1; i < L; ++i) nal += (int64_t)R * net.dims[i];

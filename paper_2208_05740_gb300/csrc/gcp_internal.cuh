@@ -252,8 +252,9 @@ void conv_T_abs(cudaStream_t st, int64_t R, const LayerGeom& g, const double* W,
 // tcgen05 GEMMs (k_tc.cu); false = shape or driver not supported, use SIMT
 bool tc_available(int K, bool bf16);
 bool gemm_tc_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C);
-bool gemm_tc_tf32x3(cudaStream_t st, int64_t M, int N, int K, const float* A, const float* Alo, const float* B,
-                    const float* Blo, float* C);
+// A plain fp32 (split into tf32 parts in the kernel); B given as tf32 high and low parts
+bool gemm_tc_tf32x3(cudaStream_t st, int64_t M, int N, int K, const float* A, const float* B, const float* Blo,
+                    float* C);
 std::string take_tc_error(cudaStream_t st);
 // Phase plan of the tensor-core convolution. dir 0 (out = conv(src)) is one
 // phase: every output pixel, all k*k taps. dir 1 (out = conv^T(src), stride

@@ -8,7 +8,9 @@
 //  * FP32 chain: kind::tf32 in three passes (A_hi B_hi + A_hi B_lo + A_lo B_hi
 //    with x = x_hi + x_lo, x_hi = x rounded to tf32), which carries about 21
 //    mantissa bits through the product: the split-operand scheme of Henry,
-//    Tang and Heinecke for bfloat16, applied to tf32.
+//    Tang and Heinecke for bfloat16, applied to tf32. The weights are split
+//    once at network load; A arrives as plain fp32 and warps 2-3 split each
+//    staged tile in shared memory.
 //
 // One CTA computes a 128 x 128 tile; its fp32 accumulator lives in TMEM
 // (128 lanes x 128 columns). Warp 0 (one lane) streams A/B tiles into shared
@@ -165,17 +167,27 @@ struct TcCfg {
   static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 };
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// threads: warp 0 producer lane, warp 1 MMA lane, warps 0-3 epilogue, and for
+// the FP32 chain warps 2-5 the tf32 split of A
 template <int KIND>
-__global__ void __launch_bounds__(128, 1)
-    k_gemm_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tAlo,
-              const __grid_constant__ CUtensorMap tB, const __grid_constant__ CUtensorMap tBlo, int M, int N, int K,
-              float* __restrict__ C) {
+constexpr int tc_threads() { return KIND == 1 ? 192 : 128; }
+constexpr int kSplitThreads = 128;
+
+template <int KIND>
+__global__ void __launch_bounds__(tc_threads<KIND>(), 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
+              const __grid_constant__ CUtensorMap tBlo, int M, int N, int K, float* __restrict__ C) {
   using Cfg = TcCfg<KIND>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::kStages * Cfg::kStageBytes);
   uint64_t* empty = full + Cfg::kStages;
-  uint64_t* done = empty + Cfg::kStages;
+  uint64_t* xfull = empty + Cfg::kStages;   // tf32 split of the stage's A tile done (KIND 1)
+  uint64_t* done = xfull + Cfg::kStages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
 
   griddep_launch();
@@ -187,6 +199,7 @@ __global__ void __launch_bounds__(128, 1)
     for (int s = 0; s < Cfg::kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      mbar_init(&xfull[s], kSplitThreads);
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -210,14 +223,38 @@ __global__ void __launch_bounds__(128, 1)
       const uint32_t ph = (kt / Cfg::kStages) & 1;
       if (!mbar_wait_idle(&empty[s], ph ^ 1)) break;
       uint8_t* st = smem + s * Cfg::kStageBytes;
-      mbar_expect_tx(&full[s], Cfg::kStageBytes);
+      // KIND 1 loads A once (raw fp32): warps 2-3 split it into the A and A_lo slots
+      mbar_expect_tx(&full[s], KIND == 1 ? Cfg::kStageBytes - kTileA : Cfg::kStageBytes);
       const int x = kt * Cfg::kKElems;
       tma_load_2d(st, &tA, &full[s], x, m0);
       tma_load_2d(st + kTileA, &tB, &full[s], x, n0);
-      if constexpr (KIND == 1) {
-        tma_load_2d(st + kTileA + kTileB, &tAlo, &full[s], x, m0);
-        tma_load_2d(st + 2 * kTileA + kTileB, &tBlo, &full[s], x, n0);
+      if constexpr (KIND == 1) tma_load_2d(st + 2 * kTileA + kTileB, &tBlo, &full[s], x, n0);
+    }
+  } else if (KIND == 1 && warp >= 2) {
+    // tf32 split of A in shared memory: x = hi + lo, hi = x rounded to tf32
+    // (nearest, ties away), lo exact; hi overwrites x in place, lo goes to the
+    // A_lo slot at the same offset (the two tiles share one layout)
+    const int t = threadIdx.x - 64;   // 0 .. kSplitThreads-1
+    for (int kt = 0; kt < KT; ++kt) {
+      const int s = kt % Cfg::kStages;
+      const uint32_t ph = (kt / Cfg::kStages) & 1;
+      if (!mbar_wait_idle(&full[s], ph)) break;
+      float4* hi = reinterpret_cast<float4*>(smem + s * Cfg::kStageBytes);
+      float4* lo = reinterpret_cast<float4*>(smem + s * Cfg::kStageBytes + kTileA + kTileB);
+#pragma unroll 4
+      for (int q = t; q < kTileA / 16; q += kSplitThreads) {
+        const float4 v = hi[q];
+        float4 h, l;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(reinterpret_cast<uint32_t&>(h.x)) : "f"(v.x));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(reinterpret_cast<uint32_t&>(h.y)) : "f"(v.y));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(reinterpret_cast<uint32_t&>(h.z)) : "f"(v.z));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(reinterpret_cast<uint32_t&>(h.w)) : "f"(v.w));
+        l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
+        hi[q] = h;
+        lo[q] = l;
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&xfull[s]);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: 4 K-steps of 32 bytes per stage, 1 or 3 passes each
@@ -226,7 +263,7 @@ __global__ void __launch_bounds__(128, 1)
     for (int kt = 0; kt < KT && ok; ++kt) {
       const int s = kt % Cfg::kStages;
       const uint32_t ph = (kt / Cfg::kStages) & 1;
-      if (!mbar_wait_idle(&full[s], ph)) { ok = false; break; }
+      if (!mbar_wait_idle(KIND == 1 ? &xfull[s] : &full[s], ph)) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a = smem_u32(smem + s * Cfg::kStageBytes);
       const uint32_t b = a + kTileA;
@@ -249,7 +286,7 @@ __global__ void __launch_bounds__(128, 1)
   // epilogue: warp w reads TMEM lanes 32w .. 32w+31 (thread = row, 32 columns
   // per load) into a row-major tile in the now idle stage memory, then writes
   // its 32 rows to global memory as whole 512-byte row segments
-  const bool ready = mbar_wait_idle(done, 0);
+  const bool ready = warp < 4 && mbar_wait_idle(done, 0);   // warps 4-5 (split only) skip the epilogue
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ready) {
     constexpr int kLd = BN + 4;   // padded row stride (floats): conflict-free float4 stores
@@ -348,9 +385,6 @@ __device__ __forceinline__ bool prod_sync_or(bool v) {
   return r != 0;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 
 // Tile geometry: phase, GEMM rows [m0, mend) of the phase (phase-local), batch
 // rows r0 .. r0 + nrt - 1, and the source-map rows sh0 .. sh0 + nsh - 1 the
@@ -645,24 +679,23 @@ bool make_map(CUtensorMap* m, const void* base, bool bf16, int64_t rows, int64_t
 }
 
 template <int KIND>
-bool launch_tc(cudaStream_t st, int64_t M, int N, int K, const void* A, const void* Alo, const void* B,
-               const void* Blo, float* C) {
+bool launch_tc(cudaStream_t st, int64_t M, int N, int K, const void* A, const void* B, const void* Blo, float* C) {
   using Cfg = TcCfg<KIND>;
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
     cudaFuncSetAttribute(k_gemm_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
   });
   const bool bf = KIND == 0;
-  CUtensorMap ta{}, talo{}, tb{}, tblo{};
+  CUtensorMap ta{}, tb{}, tblo{};
   if (!make_map(&ta, A, bf, M, K, BM) || !make_map(&tb, B, bf, N, K, BN)) return false;
   if (KIND == 1) {
-    if (!make_map(&talo, Alo, bf, M, K, BM) || !make_map(&tblo, Blo, bf, N, K, BN)) return false;
+    if (!make_map(&tblo, Blo, bf, N, K, BN)) return false;
   } else {
-    talo = ta;
     tblo = tb;
   }
   dim3 grid((N + BN - 1) / BN, static_cast<unsigned>((M + BM - 1) / BM));
-  launch_pdl(k_gemm_tc<KIND>, grid, dim3(128), Cfg::kSmem, st, ta, talo, tb, tblo, static_cast<int>(M), N, K, C);
+  launch_pdl(k_gemm_tc<KIND>, grid, dim3(tc_threads<KIND>()), Cfg::kSmem, st, ta, tb, tblo, static_cast<int>(M), N, K,
+             C);
   return true;
 }
 
@@ -681,21 +714,20 @@ bool gemm_tc_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16*
         reg_check(C, (double)M * N * 4, "tc C")))
     return true;  // reported by the caller's launch status
   int tk = prof_begin(st, "gemm_tc_bf16", 2.0 * M * N * K, ((double)M * K + (double)N * K) * 2 + (double)M * N * 4);
-  const bool ok = launch_tc<0>(st, M, N, K, A, nullptr, B, nullptr, C);
+  const bool ok = launch_tc<0>(st, M, N, K, A, B, nullptr, C);
   prof_end(st, tk);
   return ok;
 }
 
-bool gemm_tc_tf32x3(cudaStream_t st, int64_t M, int N, int K, const float* A, const float* Alo, const float* B,
-                    const float* Blo, float* C) {
+bool gemm_tc_tf32x3(cudaStream_t st, int64_t M, int N, int K, const float* A, const float* B, const float* Blo,
+                    float* C) {
   if (M <= 0 || N <= 0) return true;
   if (!tc_available(K, false) || M > (int64_t)INT32_MAX) return false;
-  if (!(reg_check(A, (double)M * K * 4, "tc A") & reg_check(Alo, (double)M * K * 4, "tc A lo") &
-        reg_check(B, (double)N * K * 4, "tc B") & reg_check(Blo, (double)N * K * 4, "tc B lo") &
-        reg_check(C, (double)M * N * 4, "tc C")))
+  if (!(reg_check(A, (double)M * K * 4, "tc A") & reg_check(B, (double)N * K * 4, "tc B") &
+        reg_check(Blo, (double)N * K * 4, "tc B lo") & reg_check(C, (double)M * N * 4, "tc C")))
     return true;
-  int tk = prof_begin(st, "gemm_tc_tf32x3", 2.0 * M * N * K, ((double)M * K + (double)N * K) * 8 + (double)M * N * 4);
-  const bool ok = launch_tc<1>(st, M, N, K, A, Alo, B, Blo, C);
+  int tk = prof_begin(st, "gemm_tc_tf32x3", 2.0 * M * N * K, (double)M * K * 4 + (double)N * K * 8 + (double)M * N * 4);
+  const bool ok = launch_tc<1>(st, M, N, K, A, B, Blo, C);
   prof_end(st, tk);
   return ok;
 }

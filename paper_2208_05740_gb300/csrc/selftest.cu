@@ -52,17 +52,15 @@ extern "C" gcp_status gcp_selftest_gemm(int32_t kind, int64_t M, int32_t N, int3
     cudaMemcpy(db, hb.data(), nb * 2, cudaMemcpyHostToDevice);
     ran = gemm_tc_bf16(nullptr, M, N, K, da, db, dC);
   } else if (kind == 1) {
-    std::vector<float> ah(na), al(na), bh(nb), bl(nb);
-    for (size_t i = 0; i < na; ++i) { ah[i] = tf32_hi_host(A[i]); al[i] = A[i] - ah[i]; }
+    // A goes in as plain fp32 (the kernel splits it); B as tf32 high and low parts
+    std::vector<float> bh(nb), bl(nb);
     for (size_t i = 0; i < nb; ++i) { bh[i] = tf32_hi_host(B[i]); bl[i] = B[i] - bh[i]; }
-    float *dah = (float*)dalloc(na * 4), *dal = (float*)dalloc(na * 4), *dbh = (float*)dalloc(nb * 4),
-          *dbl = (float*)dalloc(nb * 4);
-    if (!dah || !dal || !dbh || !dbl) { cleanup(); return GCP_ENOMEM; }
-    cudaMemcpy(dah, ah.data(), na * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(dal, al.data(), na * 4, cudaMemcpyHostToDevice);
+    float *da = (float*)dalloc(na * 4), *dbh = (float*)dalloc(nb * 4), *dbl = (float*)dalloc(nb * 4);
+    if (!da || !dbh || !dbl) { cleanup(); return GCP_ENOMEM; }
+    cudaMemcpy(da, A, na * 4, cudaMemcpyHostToDevice);
     cudaMemcpy(dbh, bh.data(), nb * 4, cudaMemcpyHostToDevice);
     cudaMemcpy(dbl, bl.data(), nb * 4, cudaMemcpyHostToDevice);
-    ran = gemm_tc_tf32x3(nullptr, M, N, K, dah, dal, dbh, dbl, dC);
+    ran = gemm_tc_tf32x3(nullptr, M, N, K, da, dbh, dbl, dC);
   } else {
     float *da = (float*)dalloc(na * 4), *db = (float*)dalloc(nb * 4);
     if (!da || !db) { cleanup(); return GCP_ENOMEM; }
