@@ -42,18 +42,66 @@ gcp_status Ctx::cuda(cudaError_t e, const char* what) {
   return fail(GCP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+namespace {
+thread_local bool t_pool = false;
+
+// 256-byte steps up to 64 KiB, then four classes per power of two (at most
+// 25% above the request), so that batches of nearby sizes share blocks.
+size_t size_class(size_t b) {
+  b = (b + 255) & ~size_t(255);
+  if (b <= (size_t(64) << 10)) return b;
+  int k = 63;
+  while (!((b >> k) & 1)) --k;
+  const size_t step = size_t(1) << (k - 2);
+  return (b + step - 1) & ~(step - 1);
+}
+
+// pooled bytes kept at most (a quarter of the budget; 8 GiB without one)
+uint64_t pool_cap(const Ctx& c) { return c.budget ? c.budget / 4 : uint64_t(8) << 30; }
+
+// cudaFree pooled blocks, largest classes first, until at most `keep` bytes remain
+void trim_to(Ctx& c, uint64_t keep) {
+  while (c.cached > keep && !c.pool.empty()) {
+    auto it = std::prev(c.pool.end());
+    if (it->second.empty()) {
+      c.pool.erase(it);
+      continue;
+    }
+    cudaFree(it->second.back());
+    it->second.pop_back();
+    c.cached -= it->first;
+  }
+}
+}  // namespace
+
+AllocPool::AllocPool() : prev(t_pool) { t_pool = true; }
+AllocPool::~AllocPool() { t_pool = prev; }
+
 void* Ctx::alloc(size_t bytes) {
   std::lock_guard<std::mutex> lk(alloc_mu);
   if (bytes == 0) bytes = 16;
-  bytes = (bytes + 255) & ~size_t(255);
-  if (budget && used + bytes > budget) {
-    over_budget = true;
-    return nullptr;
-  }
+  bytes = t_pool ? size_class(bytes) : (bytes + 255) & ~size_t(255);
   void* p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
+  auto it = t_pool ? pool.find(bytes) : pool.end();
+  if (it != pool.end() && !it->second.empty()) {
+    p = it->second.back();
+    it->second.pop_back();
+    cached -= bytes;
+  } else {
+    if (budget && used + bytes > budget) {
+      over_budget = true;
+      return nullptr;
+    }
+    if (budget && used + cached + bytes > budget) trim_to(*this, budget - used - bytes);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      if (!cached) return nullptr;
+      trim_to(*this, 0);
+      if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+    }
   }
   sizes[p] = bytes;
   used += bytes;
@@ -71,6 +119,31 @@ void Ctx::release(void* p) {
   }
   reg_free(p);
   cudaFree(p);
+}
+
+void Ctx::recycle(void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(alloc_mu);
+  auto it = sizes.find(p);
+  if (it == sizes.end()) return;
+  const size_t bytes = it->second;
+  used -= bytes;
+  sizes.erase(it);
+  reg_free(p);
+  const uint64_t cap = pool_cap(*this);
+  if (cached + bytes > cap) trim_to(*this, cap > bytes ? cap - bytes : 0);
+  if (cached + bytes > cap) {
+    cudaFree(p);
+    return;
+  }
+  pool[bytes].push_back(p);
+  cached += bytes;
+}
+
+void Ctx::trim() {
+  std::lock_guard<std::mutex> lk(alloc_mu);
+  trim_to(*this, 0);
+  pool.clear();
 }
 
 template <typename T>
@@ -127,9 +200,16 @@ Net::~Net() {
   for (void* p : owned) ctx->release(p);
 }
 CutDev::~CutDev() {
-  for (void* p : owned) ctx->release(p);
+  for (void* p : owned) pooled ? ctx->recycle(p) : ctx->release(p);
 }
 Batch::~Batch() {
+  if (pool_stream) {
+    cudaStreamSynchronize(pool_stream);
+    cuts.pooled = true;
+    for (void* p : owned) ctx->recycle(p);
+    for (auto& kv : lazy) ctx->recycle(kv.second);
+    return;
+  }
   for (void* p : owned) ctx->release(p);
   for (auto& kv : lazy) ctx->release(kv.second);
 }
@@ -138,7 +218,12 @@ void* Batch::ws(const std::string& name, size_t bytes, gcp_status* st) {
   auto it = lazy.find(name);
   if (it != lazy.end()) {
     if (lazy_bytes[name] >= bytes) return it->second;
-    ctx->release(it->second);
+    if (pool_stream) {
+      cudaStreamSynchronize(pool_stream);
+      ctx->recycle(it->second);
+    } else {
+      ctx->release(it->second);
+    }
     lazy.erase(it);
   }
   void* p = ctx->alloc(bytes);
@@ -1476,6 +1561,7 @@ gcp_status gcp_destroy(gcp_ctx* h) {
     c->batches.clear();
     c->cutsets.clear();
     c->nets.clear();
+    c->trim();
     cudaStreamDestroy(c->own_stream);
   }
   delete c;

@@ -74,6 +74,7 @@ struct CutDev {
   std::vector<int64_t> poff;         // segment start of layer i in csc_ptr
   std::vector<int64_t> layer_nnz;    // entries per layer
   std::vector<void*> owned;
+  bool pooled = false;               // blocks go back to the context's pool (serving batches)
   ~CutDev();
 };
 
@@ -100,6 +101,9 @@ struct Batch {
   std::vector<void*> owned;
   std::map<std::string, void*> lazy; // workspace by name
   std::map<std::string, size_t> lazy_bytes;
+  // serving batches: the one stream that uses this batch's memory; its blocks
+  // go back to the context's pool once that stream has drained
+  cudaStream_t pool_stream = nullptr;
   void* ws(const std::string& name, size_t bytes, gcp_status* st);
   int64_t dmax() const;
   int n_partials() const;
@@ -121,12 +125,30 @@ struct Ctx {
   std::map<int, std::unique_ptr<CutSet>> cutsets;
   std::map<Batch*, std::unique_ptr<Batch>> batches;
   std::unordered_map<void*, size_t> sizes;
+  // Freed blocks kept for reuse by size class. Only the serving loop's merged
+  // batches use it: they are created and destroyed every round, and a
+  // cudaFree waits for the whole device, stalling the other networks'
+  // streams. A block enters the pool only after the stream that used it has
+  // drained, so a reuse from any stream is safe. `used` counts live blocks,
+  // `cached` the pooled ones; both count against the budget.
+  std::map<size_t, std::vector<void*>> pool;
+  uint64_t cached = 0;
   Serve* serve = nullptr;
 
   gcp_status fail(gcp_status st, const char* fmt, ...);
   gcp_status cuda(cudaError_t e, const char* what);
   void* alloc(size_t bytes);
-  void release(void* p);
+  void release(void* p);             // cudaFree (waits for the device)
+  void recycle(void* p);             // into the pool: no device work may use p any more
+  void trim();                       // cudaFree every pooled block
+};
+
+// Allocations made while an AllocPool guard is alive on the calling thread
+// are rounded up to a size class and may reuse pooled blocks.
+struct AllocPool {
+  AllocPool();
+  ~AllocPool();
+  bool prev;
 };
 
 // shared by api.cu and serve.cu

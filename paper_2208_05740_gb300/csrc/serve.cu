@@ -140,6 +140,7 @@ void branch(const Net& net, Request& q) {
 // optimise + certify on the network's stream, results and duals back.
 void run_group(Serve& sv, int net_id, cudaStream_t st, std::vector<Request*> group) {
   Ctx& c = *sv.ctx;
+  AllocPool pooled;   // the merged batch's blocks come from and go back to the pool
   const Net* netp = nullptr;
   Batch* b = nullptr;
   gcp_status status = GCP_OK;
@@ -159,6 +160,7 @@ void run_group(Serve& sv, int net_id, cudaStream_t st, std::vector<Request*> gro
     netp = c.nets.at(net_id).get();
     status = duals_create_parts(c, net_id, parts, GCP_FP32, &b);
     if (status == GCP_OK) status = c.cuda(cudaStreamSynchronize(c.stream), "serve batch");
+    if (b) b->pool_stream = st;
   }
   cudaSetDevice(c.device);
   const Net& net = *netp;
@@ -350,6 +352,7 @@ void serve_shutdown(Ctx& c) {
   for (auto& q : sv->active) free_resident(c, *q);
   delete sv;
   c.serve = nullptr;
+  c.trim();
 }
 
 }  // namespace gcp
