@@ -184,6 +184,7 @@ template <typename Tg>
 __device__ __forceinline__ void cut_sums_row_cert(const CutCSC<double>& c, const ChunkCuts<double>& cc,
                                                   const Tg* grow, int N, int lane, double (&sum)[3],
                                                   double (&abs_)[3], int (&cnt_)[3]) {
+#pragma unroll
   for (int q = 0; q < 3; ++q) { sum[q] = 0.0; abs_[q] = 0.0; cnt_[q] = 0; }
   for (int b0 = cc.cb; b0 < cc.ce; b0 += 32) {
     int kd = cc.kind, cut = cc.cut;
@@ -211,10 +212,13 @@ __device__ __forceinline__ void cut_sums_row_cert(const CutCSC<double>& c, const
       const double v = __shfl_sync(0xffffffffu, val, src);
       const double a = __shfl_sync(0xffffffffu, av, src);
       const int kq = __shfl_sync(0xffffffffu, kd, src);
-      if (q < n && kq >= 0 && kq <= 2) {
-        sum[kq] += v;
-        abs_[kq] = __dadd_ru(abs_[kq], a);
-        ++cnt_[kq];
+      // selects per kind, not an indexed update: the sums stay in registers
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const bool hit = q < n && kq == t;
+        sum[t] = hit ? sum[t] + v : sum[t];
+        abs_[t] = hit ? __dadd_ru(abs_[t], a) : abs_[t];
+        cnt_[t] += hit ? 1 : 0;
       }
     }
   }
@@ -362,10 +366,12 @@ __device__ __forceinline__ void span_neurons(const SpanWarp<V>& w, const T* lo_,
       m &= m - 1;
       const int tj = __shfl_sync(0xffffffffu, idx, b) - w.base;
       const int tsg = __shfl_sync(0xffffffffu, sg, b);
-      if (tj / V == w.lane) {
+      // selects, not an indexed store: the neuron arrays stay in registers
+      const int tv = tj - w.lane * V;
 #pragma unroll
-        for (int v = 0; v < V; ++v)
-          if (tj % V == v) { n.slot[v] = b0 + b; n.sign[v] = tsg; }
+      for (int v = 0; v < V; ++v) {
+        n.slot[v] = tv == v ? b0 + b : n.slot[v];
+        n.sign[v] = tv == v ? tsg : n.sign[v];
       }
     }
   }

@@ -9,8 +9,11 @@
 //    with x = x_hi + x_lo, x_hi = x rounded to tf32), which carries about 21
 //    mantissa bits through the product: the split-operand scheme of Henry,
 //    Tang and Heinecke for bfloat16, applied to tf32. The weights are split
-//    once at network load; A arrives as plain fp32 and warps 2-3 split each
-//    staged tile in shared memory.
+//    once at network load; A arrives as plain fp32, and warps 2-5 (thread =
+//    tile row) split each staged A tile and store A_hi and A_lo into tensor
+//    memory, where the MMAs read A from. Shared memory then only carries the
+//    TMA traffic and the B operands: three passes reading A and B from shared
+//    memory would move about 1.7x the bytes the tensor pipe needs per cycle.
 //
 // One CTA computes a 128 x 128 tile; its fp32 accumulator lives in TMEM
 // (128 lanes x 128 columns). Warp 0 (one lane) streams A/B tiles into shared
@@ -122,6 +125,16 @@ __host__ __device__ constexpr uint32_t idesc(uint32_t ab_format, int M, int N) {
          (static_cast<uint32_t>(M >> 4) << 24);
 }
 
+// kind::tf32 with A in tensor memory (lane = row of A, one column per K element)
+__device__ __forceinline__ void umma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t id,
+                                             uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::
+          "r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(id), "r"(accumulate)
+      : "memory");
+}
+
 template <int KIND>
 __device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id, uint32_t accumulate) {
   if constexpr (KIND == 0) {
@@ -156,16 +169,30 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
+// Stage layout: the A tile, then the B tile (KIND 1: and B_lo). KIND 1 keeps
+// A_hi | A_lo of each stage in TMEM columns kAccCols + s * 64 (32 each).
 template <int KIND>
 struct TcCfg {
-  static constexpr int kPasses = KIND == 0 ? 1 : 3;
-  static constexpr int kTiles = KIND == 0 ? 2 : 4;  // A, B (+ A_lo, B_lo)
-  static constexpr int kStageBytes = KIND == 0 ? kTileA + kTileB : 2 * kTileA + 2 * kTileB;
-  static constexpr int kStages = KIND == 0 ? 4 : 3;
+  static constexpr int kStageBytes = KIND == 0 ? kTileA + kTileB : kTileA + 2 * kTileB;
+  static constexpr int kStages = 4;
   static constexpr int kKElems = KIND == 0 ? 64 : 32;  // K elements per 128-byte row
   static constexpr uint32_t kFormat = KIND == 0 ? 1u : 2u;  // bf16 / tf32
+  static constexpr int kAccCols = BN;
+  static constexpr int kTmemCols = KIND == 0 ? BN : 512;   // a power of two >= 128 + 4 * 64
   static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 };
+static_assert(TcCfg<1>::kAccCols + TcCfg<1>::kStages * 64 <= TcCfg<1>::kTmemCols, "TMEM columns");
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -206,7 +233,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(BN)
+                 "r"(Cfg::kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -223,37 +250,45 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
       const uint32_t ph = (kt / Cfg::kStages) & 1;
       if (!mbar_wait_idle(&empty[s], ph ^ 1)) break;
       uint8_t* st = smem + s * Cfg::kStageBytes;
-      // KIND 1 loads A once (raw fp32): warps 2-3 split it into the A and A_lo slots
-      mbar_expect_tx(&full[s], KIND == 1 ? Cfg::kStageBytes - kTileA : Cfg::kStageBytes);
+      mbar_expect_tx(&full[s], Cfg::kStageBytes);
       const int x = kt * Cfg::kKElems;
       tma_load_2d(st, &tA, &full[s], x, m0);
       tma_load_2d(st + kTileA, &tB, &full[s], x, n0);
-      if constexpr (KIND == 1) tma_load_2d(st + 2 * kTileA + kTileB, &tBlo, &full[s], x, n0);
+      if constexpr (KIND == 1) tma_load_2d(st + kTileA + kTileB, &tBlo, &full[s], x, n0);
     }
   } else if (KIND == 1 && warp >= 2) {
-    // tf32 split of A in shared memory: x = hi + lo, hi = x rounded to tf32
-    // (nearest, ties away), lo exact; hi overwrites x in place, lo goes to the
-    // A_lo slot at the same offset (the two tiles share one layout)
-    const int t = threadIdx.x - 64;   // 0 .. kSplitThreads-1
+    // tf32 split of A into TMEM: x = hi + lo, hi = x rounded to tf32 (nearest,
+    // ties away), lo exact. Thread = tile row; a warp may only reach the TMEM
+    // lanes of its quadrant (warp % 4), so warps 2, 3, 4, 5 take rows 64-95,
+    // 96-127, 0-31, 32-63. The staged row is 32 floats in 16-byte chunks,
+    // chunk c at position c ^ (row % 8) (128-byte swizzle of a 1024-byte
+    // aligned tile). full[s] completing implies the MMAs of the stage's
+    // previous use have finished (the producer waited for them before the
+    // TMA), so its TMEM columns are free.
+    const int row = ((warp & 3) << 5) + lane;
+    const uint32_t trow = tmem + (static_cast<uint32_t>((warp & 3) << 5) << 16) + Cfg::kAccCols;
     for (int kt = 0; kt < KT; ++kt) {
       const int s = kt % Cfg::kStages;
       const uint32_t ph = (kt / Cfg::kStages) & 1;
       if (!mbar_wait_idle(&full[s], ph)) break;
-      float4* hi = reinterpret_cast<float4*>(smem + s * Cfg::kStageBytes);
-      float4* lo = reinterpret_cast<float4*>(smem + s * Cfg::kStageBytes + kTileA + kTileB);
-#pragma unroll 4
-      for (int q = t; q < kTileA / 16; q += kSplitThreads) {
-        const float4 v = hi[q];
-        float4 h, l;
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(reinterpret_cast<uint32_t&>(h.x)) : "f"(v.x));
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(reinterpret_cast<uint32_t&>(h.y)) : "f"(v.y));
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(reinterpret_cast<uint32_t&>(h.z)) : "f"(v.z));
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(reinterpret_cast<uint32_t&>(h.w)) : "f"(v.w));
-        l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
-        hi[q] = h;
-        lo[q] = l;
+      const uint8_t* arow = smem + s * Cfg::kStageBytes + row * kRowBytes;
+      uint32_t h[32], l[32];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float4 v = *reinterpret_cast<const float4*>(arow + ((c ^ (row & 7)) << 4));
+        const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          uint32_t hb;
+          asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(x[e]));
+          h[4 * c + e] = hb;
+          l[4 * c + e] = __float_as_uint(x[e] - __uint_as_float(hb));
+        }
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tmem_st32(trow + s * 64, h);
+      tmem_st32(trow + s * 64 + 32, l);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&xfull[s]);
     }
   } else if (warp == 1 && lane == 0) {
@@ -269,12 +304,16 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
       const uint32_t b = a + kTileA;
 #pragma unroll
       for (int kk = 0; kk < kRowBytes / 32; ++kk) {
-        const uint64_t da = sdesc(a + kk * 32), db = sdesc(b + kk * 32);
-        umma<KIND>(tmem, da, db, id, (kt | kk) != 0);
+        const uint64_t db = sdesc(b + kk * 32);
         if constexpr (KIND == 1) {
-          const uint64_t da_lo = sdesc(a + kTileA + kTileB + kk * 32), db_lo = sdesc(b + kTileA + kTileB + kk * 32);
-          umma<KIND>(tmem, da, db_lo, id, 1);
-          umma<KIND>(tmem, da_lo, db, id, 1);
+          // A_hi, A_lo: 8 TMEM columns per K-step of 8 tf32 elements
+          const uint32_t ta = tmem + Cfg::kAccCols + s * 64 + kk * 8;
+          const uint64_t db_lo = sdesc(b + kTileB + kk * 32);
+          umma_tf32_ta(tmem, ta, db, id, (kt | kk) != 0);
+          umma_tf32_ta(tmem, ta, db_lo, id, 1);
+          umma_tf32_ta(tmem, ta + 32, db, id, 1);
+        } else {
+          umma<KIND>(tmem, sdesc(a + kk * 32), db, id, (kt | kk) != 0);
         }
       }
       umma_commit(&empty[s]);  // slot free once these MMAs have read it
@@ -320,7 +359,8 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::kTmemCols)
+                 : "memory");
   }
 }
 
