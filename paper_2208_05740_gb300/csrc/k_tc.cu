@@ -107,6 +107,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// Bulk tensor store of a staged box (bulk-group completion).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_u32(src)), "r"(x), "r"(y)
+               : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes in 8-row atoms of 1024 bytes (stride 1024 between atoms).
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -193,6 +201,7 @@ struct TcCfg {
   static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 };
 static_assert(TcCfg<1>::kAccCols + TcCfg<1>::kStages * 64 <= TcCfg<1>::kTmemCols, "TMEM columns");
+static_assert(4 * 32 * BN * 4 <= TcCfg<0>::kStages * TcCfg<0>::kStageBytes, "epilogue staging fits the stages");
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -207,7 +216,8 @@ constexpr int kSplitThreads = 128;
 template <int KIND>
 __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
-              const __grid_constant__ CUtensorMap tBlo, int M, int N, int K, float* __restrict__ C) {
+              const __grid_constant__ CUtensorMap tBlo, const __grid_constant__ CUtensorMap tC, int c_tma, int M,
+              int N, int K, float* __restrict__ C) {
   using Cfg = TcCfg<KIND>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -230,6 +240,13 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x == 32) {
+    // the tensor maps are kernel parameters: fetch them while earlier kernels finish
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tB)) : "memory");
+    if (KIND == 1) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tBlo)) : "memory");
+    if (c_tma) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tC)) : "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -322,12 +339,38 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
   }
   __syncwarp();
 
-  // epilogue: warp w reads TMEM lanes 32w .. 32w+31 (thread = row, 32 columns
-  // per load) into a row-major tile in the now idle stage memory, then writes
-  // its 32 rows to global memory as whole 512-byte row segments
+  // epilogue: warp w reads TMEM lanes 32w .. 32w+31 (thread = row, 32
+  // columns per load) into the now idle stage memory. With a tensor map for C
+  // (row stride a multiple of 16 bytes) the warp stages its 32 x 128 block as
+  // four 32 x 32 boxes in the 128-byte swizzled layout (16-byte chunk q of row
+  // i at position q ^ (i % 8): conflict-free stores) and one lane hands them
+  // to bulk tensor stores, which clip the rows and columns beyond M and N.
+  // Otherwise it stages a padded row-major tile and writes whole rows.
   const bool ready = warp < 4 && mbar_wait_idle(done, 0);   // warps 4-5 (split only) skip the epilogue
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ready) {
+  if (ready && c_tma) {
+    uint8_t* stg = smem + warp * (32 * BN * 4);
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c, r);
+      uint8_t* row = stg + (c >> 5) * 4096 + lane * 128;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        *reinterpret_cast<uint4*>(row + ((q ^ (lane & 7)) << 4)) =
+            make_uint4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) {
+      const int y = m0 + warp * 32;
+      for (int c = 0; c < BN / 32; ++c)
+        if (y < M && n0 + 32 * c < N) tma_store_2d(&tC, stg + c * 4096, n0 + 32 * c, y);
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // staging read before the CTA ends
+    }
+    __syncwarp();
+  } else if (ready) {
     constexpr int kLd = BN + 4;   // padded row stride (floats): conflict-free float4 stores
     float* ct = reinterpret_cast<float*>(smem) + warp * 32 * kLd;
 #pragma unroll 1
@@ -342,18 +385,13 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
     }
     __syncwarp();
     const int ncol = min(BN, N - n0);
-    const bool vec = ncol == BN && (N & 3) == 0;
 #pragma unroll 1
     for (int i = 0; i < 32; ++i) {
       const int row = m0 + warp * 32 + i;
       if (row >= M) break;
       float* dst = C + static_cast<int64_t>(row) * N + n0;
       const float* srcr = ct + i * kLd;
-      if (vec) {
-        *reinterpret_cast<float4*>(dst + lane * 4) = *reinterpret_cast<const float4*>(srcr + lane * 4);
-      } else {
-        for (int q = lane; q < ncol; q += 32) dst[q] = srcr[q];
-      }
+      for (int q = lane; q < ncol; q += 32) dst[q] = srcr[q];
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -726,16 +764,18 @@ bool launch_tc(cudaStream_t st, int64_t M, int N, int K, const void* A, const vo
     cudaFuncSetAttribute(k_gemm_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
   });
   const bool bf = KIND == 0;
-  CUtensorMap ta{}, tb{}, tblo{};
+  CUtensorMap ta{}, tb{}, tblo{}, tc{};
   if (!make_map(&ta, A, bf, M, K, BM) || !make_map(&tb, B, bf, N, K, BN)) return false;
   if (KIND == 1) {
     if (!make_map(&tblo, Blo, bf, N, K, BN)) return false;
   } else {
     tblo = tb;
   }
+  // C through bulk tensor stores: 16-byte aligned base and row stride
+  const int c_tma = (reinterpret_cast<uintptr_t>(C) & 15) == 0 && (N & 3) == 0 && make_map(&tc, C, false, M, N, 32);
   dim3 grid((N + BN - 1) / BN, static_cast<unsigned>((M + BM - 1) / BM));
-  launch_pdl(k_gemm_tc<KIND>, grid, dim3(tc_threads<KIND>()), Cfg::kSmem, st, ta, tb, tblo, static_cast<int>(M), N, K,
-             C);
+  launch_pdl(k_gemm_tc<KIND>, grid, dim3(tc_threads<KIND>()), Cfg::kSmem, st, ta, tb, tblo, tc, c_tma,
+             static_cast<int>(M), N, K, C);
   return true;
 }
 
