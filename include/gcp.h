@@ -265,6 +265,17 @@ GCP_API gcp_status gcp_bound_dense_noalloc(int32_t n_layers, const int32_t* dims
 GCP_API gcp_status gcp_selftest_gemm(int32_t kind, int64_t M, int32_t N, int32_t K, const float* A, const float* B,
                                      float* C);
 
+/* Not a step of the paper's method: the float64 product of the certification
+ * pass, C[M, N] = A[M, K] * B[N, K]^T (row-major double host arrays), on the
+ * tensor cores by exact bf16 slices, as the certification runs it for dense
+ * layers. Cabs[M, N] (float) and *cerr give its rigorous error bound:
+ * |C - exact| <= *cerr * Cabs elementwise. A row holding a non-finite value
+ * gives NaN in C and +inf in Cabs. GCP_EINVAL when K has no slice plan
+ * (K % 8 != 0, or K above about 18,000) or the tensor cores are unavailable.
+ * For tests. */
+GCP_API gcp_status gcp_selftest_gemm_f64(int64_t M, int32_t N, int32_t K, const double* A, const double* B, double* C,
+                                         float* Cabs, double* cerr);
+
 /* --------------------------------------------------------------- profiling */
 
 /* Launch accounting (process-wide, all contexts). Not a step of the paper's

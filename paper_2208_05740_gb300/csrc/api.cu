@@ -400,6 +400,21 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
       UP(wabs, float, wa.data(), nw);
     }
     net->Wabs32.push_back(wabs);
+    // the certification's float64 product y = W^T nu on the tensor cores: the
+    // rows of W^T cut into exact bf16 slices once, here
+    SliceB sl;
+    if (g.kind == GCP_DENSE && slice_params(g.d_out, sl.b, sl.s, sl.cerr) && tc_available(g.d_out, true)) {
+      const size_t np = (size_t)g.d_in * sl.s * g.d_out;
+      UP(sl.planes, __nv_bfloat16, nullptr, np);
+      UP(sl.exps, int32_t, nullptr, (size_t)g.d_in);
+      slice_rows(c.stream, g.d_in, g.d_out, wt64, sl.b, sl.s, true, sl.planes, sl.exps);
+      if (!reg_take_error().empty()) return c.fail(GCP_EDEVICE, "layer %d: weight slices", i + 1);
+      st = c.cuda(cudaStreamSynchronize(c.stream), "weight slices");
+      if (st) return st;
+    } else {
+      sl = SliceB{};
+    }
+    net->WTsl.push_back(sl);
     net->CF16.push_back(cf16); net->CT16.push_back(ct16);
     net->cf_kp.push_back(cfk); net->cf_np.push_back(cfn); net->ct_kp.push_back(ctk); net->ct_np.push_back(ctn);
     UP(b64, double, d.b, g.d_out);
@@ -1080,16 +1095,36 @@ gcp_status run_certify(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
     nuabs = (float*)b.ws("c_nuabs", (size_t)R * b.dmax() * 4, &s);
     if (!nuabs) return s;
   }
+  // slices of nu for the dense products on the tensor cores
+  __nv_bfloat16* nu_sl = nullptr;
+  int32_t* nu_ex = nullptr;
+  float* sl_sums = nullptr;
+  size_t sl_elems = 0, sum_elems = 0;
+  for (int i = 1; i < L; ++i) {
+    const SliceB& sl = net.WTsl[i - 1];
+    if (!b.tc || !sl.planes) continue;
+    sl_elems = std::max(sl_elems, (size_t)sl.s * net.dims[i]);
+    sum_elems = std::max(sum_elems, (size_t)sl.s * net.dims[i - 1]);
+  }
+  if (sl_elems) {
+    nu_sl = (__nv_bfloat16*)b.ws("c_nu_slices", (size_t)R * sl_elems * 2, &s);
+    nu_ex = (int32_t*)b.ws("c_nu_exps", (size_t)R * 4, &s);
+    sl_sums = (float*)b.ws("c_slice_sums", (size_t)R * sum_elems * 4, &s);
+    if (!nu_sl || !nu_ex || !sl_sums) return s;
+  }
   SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp, b.sp_tab};
   // y^(L-1) = W^(L)^T (-c_k), one row per spec row
   const LayerGeom& gl = net.geom[L - 1];
   gemm_nt_abs(st, b.K, gl.d_in, gl.d_out, net.negC64, 0, net.WT64[L - 1], y, ya);
+  // |computed y - exact y| <= yerr * ya elementwise: Higham's gamma_K for the
+  // float64 dot products, the slice bound for the tensor-core product
+  double yerr = gamma_n_host(red_len(gl));
   int poff = 0;
   for (int i = L - 1; i >= 1; --i) {
     CertArgs<Td> a{};
     a.R = R; a.K = b.K; a.d = net.dims[i]; a.layer = i; a.M = b.M; a.N = b.N;
     a.y = y; a.yabs = ya; a.y_per_spec = (i == L - 1);
-    a.gamma_n = gamma_n_host(red_len(net.geom[i]));
+    a.gamma_n = yerr;
     a.lo = net.lo64[i - 1]; a.hi = net.hi64[i - 1]; a.bias = net.b64[i - 1];
     a.alpha = (const Td*)b.alpha[i - 1];
     a.beta = (const Td*)b.beta;
@@ -1102,10 +1137,19 @@ gcp_status run_certify(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
     a.obj_part = part + (int64_t)poff * R;
     certify_relax<Td>(st, a);
     poff += (net.dims[i] + kChunk - 1) / kChunk;
-    if (g.kind == GCP_DENSE) gemm_nt_abs(st, R, g.d_in, g.d_out, nu, 0, net.WT64[i - 1], y, ya);
-    else conv_T_abs(st, R, g, net.W64[i - 1], net.Wabs32[i - 1], nu, nuabs, y, ya);
+    const SliceB& sl = net.WTsl[i - 1];
+    if (g.kind == GCP_DENSE && b.tc && sl.planes &&
+        gemm_f64_slices(st, R, g.d_in, g.d_out, nu, sl, nu_sl, nu_ex, sl_sums, y, ya)) {
+      yerr = sl.cerr;
+    } else if (g.kind == GCP_DENSE) {
+      gemm_nt_abs(st, R, g.d_in, g.d_out, nu, 0, net.WT64[i - 1], y, ya);
+      yerr = gamma_n_host(red_len(g));
+    } else {
+      conv_T_abs(st, R, g, net.W64[i - 1], net.Wabs32[i - 1], nu, nuabs, y, ya);
+      yerr = gamma_n_host(red_len(g));
+    }
   }
-  certify_concretize<Td>(st, R, b.K, b.N, net.dims[0], y, ya, gamma_n_host(red_len(net.geom[0])), net.xlo64,
+  certify_concretize<Td>(st, R, b.K, b.N, net.dims[0], y, ya, yerr, net.xlo64,
                          net.xhi64, (const Td*)b.gamma, csc_of<double>(b, 0), part + (int64_t)poff * R);
   poff += (net.dims[0] + kChunk - 1) / kChunk;
   certify_finalize<Td>(st, R, b.K, b.N, poff, net.C64, net.bL64, net.dims[L], b.cuts.d64, (const Td*)b.gamma, part,

@@ -30,6 +30,7 @@ struct Net {
   // forward [cf_np, cf_kp] and transposed [ct_np, ct_kp]; nullptr for dense layers
   std::vector<__nv_bfloat16*> CF16, CT16;
   std::vector<float*> Wabs32;        // |W| in float rounded up (convolution layers; certification)
+  std::vector<SliceB> WTsl;          // exact bf16 slices of W^T (dense layers; float64 certification)
   std::vector<int> cf_kp, cf_np, ct_kp, ct_np;
   double *xlo64 = nullptr, *xhi64 = nullptr;
   float *xlo32 = nullptr, *xhi32 = nullptr;

@@ -256,6 +256,36 @@ bool gemm_tc_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16*
 bool gemm_tc_tf32x3(cudaStream_t st, int64_t M, int N, int K, const float* A, const float* B, const float* Blo,
                     float* C);
 std::string take_tc_error(cudaStream_t st);
+
+// Float64 product on the tensor cores by exact slices (the error-free
+// transformation of Ozaki, Ogita, Oishi and Rump for matrix products). Each
+// row of a float64 operand is scaled by 2^-e (e its largest magnitude's
+// exponent) and cut into s slices of b bits, small integers stored exactly in
+// bf16; the slice products are bf16 tensor-core GEMMs whose fp32 sums are
+// exact integers (s * K * (2^b - 1)^2 < 2^22), and the slice pairs with
+// i + j = t share one GEMM over K' = (t - 1) K (the slices of A in order along
+// K, those of B in reverse order). The float64 result adds the terms
+// 2^(e_r + f_c - b t) T_t from the smallest up; |result - exact| <=
+// cerr * 2^(e_r + f_c) * K, written (rounded up) as the error scale beside
+// the product.
+struct SliceB {
+  __nv_bfloat16* planes = nullptr;   // [N, s * K]: slice s .. 1 of each row
+  int32_t* exps = nullptr;           // [N] row exponents (kSliceBadExp: not finite)
+  int b = 0, s = 0;
+  double cerr = 0.0;
+};
+constexpr int32_t kSliceBadExp = 1 << 30;
+bool slice_params(int K, int& b, int& s, double& cerr);
+// slices of the rows of A [M, K] (row stride K): planes [M, s * K], slice
+// order 1 .. s, or s .. 1 with `reverse`
+bool slice_rows(cudaStream_t st, int64_t M, int K, const double* A, int b, int s, bool reverse,
+                __nv_bfloat16* planes, int32_t* exps);
+// y [M, N] = A [M, K] * B^T in float64 with its error scale yabs; ap / ae / T
+// are workspace: the slices of A ([M, s * K] bf16, [M] int32) and the s
+// exact slice sums ([s, M, N] fp32)
+bool gemm_f64_slices(cudaStream_t st, int64_t M, int N, int K, const double* A, const SliceB& B,
+                     __nv_bfloat16* ap, int32_t* ae, float* T, double* y, float* yabs);
+
 // Phase plan of the tensor-core convolution. dir 0 (out = conv(src)) is one
 // phase: every output pixel, all k*k taps. dir 1 (out = conv^T(src), stride
 // s) splits the output pixels into s*s phases (ph, pw): pixels ih = ph + s*i,

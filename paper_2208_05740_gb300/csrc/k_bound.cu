@@ -24,6 +24,9 @@ __device__ unsigned long long g_dev_err[3];
 namespace {
 
 constexpr int kWarpsPerBlock = 8;
+// Span kernels: small blocks (two warps) spread the subdomains' warps evenly
+// over the SMs; a block of eight left some SMs with half the warps of others.
+constexpr int kSpanWarps = 2;
 
 __device__ __noinline__ void dev_error(unsigned long long code, long long idx, long long lim) {
   if (atomicCAS(&g_dev_err[0], 0ull, code) == 0ull) {
@@ -256,7 +259,7 @@ struct SpanWarp {
 };
 template <int V>
 __device__ __forceinline__ bool span_warp(int S, int d, SpanWarp<V>& w) {
-  w.s = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  w.s = blockIdx.x * kSpanWarps + (threadIdx.x >> 5);
   w.c = blockIdx.y;
   w.lane = threadIdx.x & 31;
   w.base = w.c * 32 * V;
@@ -577,7 +580,7 @@ struct StageLayout {
 
 // ------------------------------------------------------------------ eval
 template <typename T, typename Top, int V>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_eval(RelaxArgs<T, Top> a) {
+__global__ void __launch_bounds__(kSpanWarps * 32) k_relax_eval(RelaxArgs<T, Top> a) {
   using Lay = StageLayout<V, 2, V, 3>;   // dense: y, alpha; fixed: acc
   constexpr int SPAN = Lay::SPAN, NS = kStages;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -625,45 +628,50 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_eval(RelaxArgs<T,
     scattered(kb + st, st);
   }
   cp_commit();
-  for (int k = kb; k < ke; ++k) {
-    const int st = (k - kb) % NS;
-    // the prologue is one group (rows kb .. kb+NS-1); row k >= kb+NS is the
-    // group committed NS-1 groups ago
-    if (k == kb) cp_wait<0>();
-    else cp_wait<NS - 1>();
-    const T* sb = stage(st);
-    const int64_t r = (int64_t)w.s * a.K + k;
-    const int64_t ij = r * a.d + w.j0;
-    T t[V], gg[V], sq[V];
-    span_cut_sums<T, V>(a.csc, sc, a.N, w, sb + 2 * SPAN, a.gamma + r * a.N, acc, t, gg, sq, er);
-    T term = T(0);
-    if (w.on) {
-      T yv[V], al[V], nu[V], nh[V];
-      ldv_rw<V>(sb + w.lane * V, yv);
-      ldv_rw<V>(sb + SPAN + w.lane * V, al);
+  // rows in groups of NS: the stage of each row is a compile-time index
+  for (int k0 = kb; k0 < ke; k0 += NS) {
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        if (n.slot[v] >= 0) {        // split row -x <= 0 (x >= 0) or x <= 0
-          const T b = sb[2 * SPAN + kSpanBatches * 32 + 32 * v + w.lane];
-          t[v] += n.sign[v] > 0 ? -b : b;
+    for (int st = 0; st < NS; ++st) {
+      const int k = k0 + st;
+      if (k >= ke) break;
+      // the prologue is one group (rows kb .. kb+NS-1); row k >= kb+NS is the
+      // group committed NS-1 groups ago
+      if (k == kb) cp_wait<0>();
+      else cp_wait<NS - 1>();
+      const T* sb = stage(st);
+      const int64_t r = (int64_t)w.s * a.K + k;
+      const int64_t ij = r * a.d + w.j0;
+      T t[V], gg[V], sq[V];
+      span_cut_sums<T, V>(a.csc, sc, a.N, w, sb + 2 * SPAN, a.gamma + r * a.N, acc, t, gg, sq, er);
+      T term = T(0);
+      if (w.on) {
+        T yv[V], al[V], nu[V], nh[V];
+        ldv_rw<V>(sb + w.lane * V, yv);
+        ldv_rw<V>(sb + SPAN + w.lane * V, al);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          if (n.slot[v] >= 0) {        // split row -x <= 0 (x >= 0) or x <= 0
+            const T b = sb[2 * SPAN + kSpanBatches * 32 + 32 * v + w.lane];
+            t[v] += n.sign[v] > 0 ? -b : b;
+          }
+          nh[v] = yv[v] - gg[v];
+          // unstable: Lemma A.1 with q = -s
+          const T C = tmax(nh[v], T(0));
+          const T pi = tmin(tmax((n.hi[v] * C - sq[v]) * n.iv[v], T(0)), C);
+          const T hu = n.lo[v] * pi - tmax(T(0), n.hi[v] * (C - pi) + n.lo[v] * pi - sq[v]);
+          const T nuu = pi - al[v] * tmax(-nh[v], T(0)) - t[v];
+          const int cl = n.cls[v];
+          nu[v] = cl == 2 ? nuu : (cl == 1 ? nh[v] - t[v] : -t[v]);   // active: xhat = x, z = 1
+          term += (cl == 2 ? hu : (cl == 1 ? sq[v] : T(0))) - nu[v] * n.bj[v];
         }
-        nh[v] = yv[v] - gg[v];
-        // unstable: Lemma A.1 with q = -s
-        const T C = tmax(nh[v], T(0));
-        const T pi = tmin(tmax((n.hi[v] * C - sq[v]) * n.iv[v], T(0)), C);
-        const T hu = n.lo[v] * pi - tmax(T(0), n.hi[v] * (C - pi) + n.lo[v] * pi - sq[v]);
-        const T nuu = pi - al[v] * tmax(-nh[v], T(0)) - t[v];
-        const int cl = n.cls[v];
-        nu[v] = cl == 2 ? nuu : (cl == 1 ? nh[v] - t[v] : -t[v]);   // active: xhat = x, z = 1
-        term += (cl == 2 ? hu : (cl == 1 ? sq[v] : T(0))) - nu[v] * n.bj[v];
+        put_operand_v<V, Top>(a.nu_out, a.nu_lo, ij, nu);
+        stv<V>(a.nuhat_out + ij, nh);
       }
-      put_operand_v<V, Top>(a.nu_out, a.nu_lo, ij, nu);
-      stv<V>(a.nuhat_out + ij, nh);
+      span_partial<T, V>(a.obj_part, a.R, r, w.c, a.d, w.lane, term);
+      dense(k + NS, st);
+      scattered(k + NS, st);
+      cp_commit();
     }
-    span_partial<T, V>(a.obj_part, a.R, r, w.c, a.d, w.lane, term);
-    dense(k + NS, st);
-    scattered(k + NS, st);
-    cp_commit();
   }
   cp_wait<0>();
   er.flush();
@@ -673,7 +681,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_eval(RelaxArgs<T,
 // Writes dg/dbeta of every split slot whose neuron is in this layer into
 // g_beta (the gradient output, or the input of the beta step in the gather).
 template <typename T, typename Top, int V>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_adj(AdjArgs<T, Top> a) {
+__global__ void __launch_bounds__(kSpanWarps * 32) k_relax_adj(AdjArgs<T, Top> a) {
   using Lay = StageLayout<V, 5, 0, 6>;   // dense: nubar, nuhat, alpha, m, v; fixed: acc, ev
   constexpr int SPAN = Lay::SPAN, NS = kStages;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -722,79 +730,84 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_adj(AdjArgs<T, To
     scattered(kb + st, st);
   }
   cp_commit();
-  for (int k = kb; k < ke; ++k) {
-    const int st = (k - kb) % NS;
-    // the prologue is one group (rows kb .. kb+NS-1); row k >= kb+NS is the
-    // group committed NS-1 groups ago
-    if (k == kb) cp_wait<0>();
-    else cp_wait<NS - 1>();
-    const T* sb = stage(st);
-    const int64_t r = (int64_t)w.s * a.K + k;
-    const int64_t ij = r * a.d + w.j0;
-    const T wr = a.seed ? __ldg(a.seed + r) : T(1);
-    T t[V], gg[V], sq[V];
-    span_cut_sums<T, V>(a.csc, sc, a.N, w, sb + 5 * SPAN, a.gamma + r * a.N, acc, t, gg, sq, er);
-    T nbv[V], nh[V], al[V], ma[V], va[V];
-    ldv_rw<V>(sb + w.lane * V, nbv);
-    ldv_rw<V>(sb + SPAN + w.lane * V, nh);
-    ldv_rw<V>(sb + 2 * SPAN + w.lane * V, al);
-    ldv_rw<V>(sb + 3 * SPAN + w.lane * V, ma);
-    ldv_rw<V>(sb + 4 * SPAN + w.lane * V, va);
-    T dt[V], dnh[V], dnhn[V], ds[V], ga[V];
+  // rows in groups of NS: the stage of each row is a compile-time index
+  for (int k0 = kb; k0 < ke; k0 += NS) {
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const T nb = nbv[v] - wr * n.bj[v];   // dg/dnu^(i)
-      const T h = nh[v], hi = n.hi[v], lo = n.lo[v], iv = n.iv[v];
-      // local derivatives of nu and of the objective term h by case
-      T dnu_dnh = T(0), dh_dnh = T(0), dnu_ds = T(0), dh_ds = T(0);
-      if (n.cls[v] == 1) {                       // active
-        dnu_dnh = T(1);
-        dh_ds = wr;
-      } else if (n.cls[v] == 2) {
-        const T p0 = (hi * h - sq[v]) * iv;
-        const bool pos = h > T(0);
-        const bool mid = pos && p0 > T(0) && p0 < h;          // pi* = p0
-        const bool top = pos && !(p0 < h);                    // pi* = C; h = s when l C - s > 0
-        dnu_dnh = mid ? hi * iv : (top ? T(1) : (h < T(0) ? al[v] : T(0)));
-        dh_dnh = mid ? wr * lo * hi * iv : T(0);
-        dnu_ds = mid ? -iv : T(0);
-        dh_ds = mid ? -wr * lo * iv
-                    : (top ? (lo * h - sq[v] > T(0) ? wr : T(0)) : (pos ? T(0) : (sq[v] < T(0) ? wr : T(0))));
+    for (int st = 0; st < NS; ++st) {
+      const int k = k0 + st;
+      if (k >= ke) break;
+      // the prologue is one group (rows kb .. kb+NS-1); row k >= kb+NS is the
+      // group committed NS-1 groups ago
+      if (k == kb) cp_wait<0>();
+      else cp_wait<NS - 1>();
+      const T* sb = stage(st);
+      const int64_t r = (int64_t)w.s * a.K + k;
+      const int64_t ij = r * a.d + w.j0;
+      const T wr = a.seed ? __ldg(a.seed + r) : T(1);
+      T t[V], gg[V], sq[V];
+      span_cut_sums<T, V>(a.csc, sc, a.N, w, sb + 5 * SPAN, a.gamma + r * a.N, acc, t, gg, sq, er);
+      T nbv[V], nh[V], al[V], ma[V], va[V];
+      ldv_rw<V>(sb + w.lane * V, nbv);
+      ldv_rw<V>(sb + SPAN + w.lane * V, nh);
+      ldv_rw<V>(sb + 2 * SPAN + w.lane * V, al);
+      ldv_rw<V>(sb + 3 * SPAN + w.lane * V, ma);
+      ldv_rw<V>(sb + 4 * SPAN + w.lane * V, va);
+      T dt[V], dnh[V], dnhn[V], ds[V], ga[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const T nb = nbv[v] - wr * n.bj[v];   // dg/dnu^(i)
+        const T h = nh[v], hi = n.hi[v], lo = n.lo[v], iv = n.iv[v];
+        // local derivatives of nu and of the objective term h by case
+        T dnu_dnh = T(0), dh_dnh = T(0), dnu_ds = T(0), dh_ds = T(0);
+        if (n.cls[v] == 1) {                       // active
+          dnu_dnh = T(1);
+          dh_ds = wr;
+        } else if (n.cls[v] == 2) {
+          const T p0 = (hi * h - sq[v]) * iv;
+          const bool pos = h > T(0);
+          const bool mid = pos && p0 > T(0) && p0 < h;          // pi* = p0
+          const bool top = pos && !(p0 < h);                    // pi* = C; h = s when l C - s > 0
+          dnu_dnh = mid ? hi * iv : (top ? T(1) : (h < T(0) ? al[v] : T(0)));
+          dh_dnh = mid ? wr * lo * hi * iv : T(0);
+          dnu_ds = mid ? -iv : T(0);
+          dh_ds = mid ? -wr * lo * iv
+                      : (top ? (lo * h - sq[v] > T(0) ? wr : T(0)) : (pos ? T(0) : (sq[v] < T(0) ? wr : T(0))));
+        }
+        ga[v] = n.cls[v] == 2 ? nb * (-tmax(-h, T(0))) : T(0);
+        dnh[v] = nb * dnu_dnh + dh_dnh;
+        dnhn[v] = -dnh[v];
+        ds[v] = nb * dnu_ds + dh_ds;
+        dt[v] = -nb;
       }
-      ga[v] = n.cls[v] == 2 ? nb * (-tmax(-h, T(0))) : T(0);
-      dnh[v] = nb * dnu_dnh + dh_dnh;
-      dnhn[v] = -dnh[v];
-      ds[v] = nb * dnu_ds + dh_ds;
-      dt[v] = -nb;
-    }
-    if (w.on) {
-      if (mode == 0) {
-        stv<V>(a.g_alpha + ij, ga);
-      } else if (n.unstable) {
+      if (w.on) {
+        if (mode == 0) {
+          stv<V>(a.g_alpha + ij, ga);
+        } else if (n.unstable) {
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-          if (n.cls[v] == 2) {
-            const T na = step_apply(a.st, al[v], ga[v], a.st.lr_a, ma[v], va[v]);
-            al[v] = tmin(tmax(na, T(0)), T(1));
+          for (int v = 0; v < V; ++v) {
+            if (n.cls[v] == 2) {
+              const T na = step_apply(a.st, al[v], ga[v], a.st.lr_a, ma[v], va[v]);
+              al[v] = tmin(tmax(na, T(0)), T(1));
+            }
+          }
+          stv<V>(a.alpha + ij, al);
+          if (mode == 2) {
+            stv<V>(a.m_alpha + ij, ma);
+            stv<V>(a.v_alpha + ij, va);
           }
         }
-        stv<V>(a.alpha + ij, al);
-        if (mode == 2) {
-          stv<V>(a.m_alpha + ij, ma);
-          stv<V>(a.v_alpha + ij, va);
+        if (a.a_out) put_operand_v<V, Top>(a.a_out, a.a_lo, ij, dnh);
+        if (n.split) {
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+            if (n.slot[v] >= 0) a.g_beta[r * a.M + n.slot[v]] = (n.sign[v] > 0 ? T(-1) : T(1)) * dt[v];
         }
       }
-      if (a.a_out) put_operand_v<V, Top>(a.a_out, a.a_lo, ij, dnh);
-      if (n.split) {
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-          if (n.slot[v] >= 0) a.g_beta[r * a.M + n.slot[v]] = (n.sign[v] > 0 ? T(-1) : T(1)) * dt[v];
-      }
+      if (a.E) span_cut_writes<T, V>(a.csc, sc, a.N, w, dt, dnhn, ds, ev, a.E + r * a.csc.n_total, er);
+      dense(k + NS, st);
+      scattered(k + NS, st);
+      cp_commit();
     }
-    if (a.E) span_cut_writes<T, V>(a.csc, sc, a.N, w, dt, dnhn, ds, ev, a.E + r * a.csc.n_total, er);
-    dense(k + NS, st);
-    scattered(k + NS, st);
-    cp_commit();
   }
   cp_wait<0>();
   er.flush();
@@ -802,7 +815,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_relax_adj(AdjArgs<T, To
 
 // ------------------------------------------------------------------ concretization
 template <typename T, typename Top, int V>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_concretize(ConcArgs<T, Top> a) {
+__global__ void __launch_bounds__(kSpanWarps * 32) k_concretize(ConcArgs<T, Top> a) {
   using Lay = StageLayout<V, 1, 0, 6>;   // dense: y0; fixed: acc, ev
   constexpr int SPAN = Lay::SPAN, NS = kStages;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -849,36 +862,41 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_concretize(ConcArgs<T, 
     scattered(kb + st, st);
   }
   cp_commit();
-  for (int k = kb; k < ke; ++k) {
-    const int st = (k - kb) % NS;
-    // the prologue is one group (rows kb .. kb+NS-1); row k >= kb+NS is the
-    // group committed NS-1 groups ago
-    if (k == kb) cp_wait<0>();
-    else cp_wait<NS - 1>();
-    const T* sb = stage(st);
-    const int64_t r = (int64_t)w.s * a.K + k;
-    const int64_t ij = r * a.d0 + w.j0;
-    const T wr = a.seed ? __ldg(a.seed + r) : T(1);
-    T h0[V], ug[V], us[V];
-    span_cut_sums<T, V>(a.csc, sc, a.N, w, sb + SPAN, a.gamma + r * a.N, acc, h0, ug, us, er);   // layer 0: kind x
-    T yv[V];
-    ldv_rw<V>(sb + w.lane * V, yv);
-    T term = T(0), xs[V], a0[V], zero[V];
+  // rows in groups of NS: the stage of each row is a compile-time index
+  for (int k0 = kb; k0 < ke; k0 += NS) {
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const T c0 = -yv[v] + h0[v];
-      const T x = c0 > T(0) ? xl[v] : (c0 < T(0) ? xh[v] : T(0.5) * (xl[v] + xh[v]));
-      xs[v] = wr * x;
-      a0[v] = -wr * x;
-      zero[v] = T(0);
-      if (w.on) term += tmin(c0 * xl[v], c0 * xh[v]);
+    for (int st = 0; st < NS; ++st) {
+      const int k = k0 + st;
+      if (k >= ke) break;
+      // the prologue is one group (rows kb .. kb+NS-1); row k >= kb+NS is the
+      // group committed NS-1 groups ago
+      if (k == kb) cp_wait<0>();
+      else cp_wait<NS - 1>();
+      const T* sb = stage(st);
+      const int64_t r = (int64_t)w.s * a.K + k;
+      const int64_t ij = r * a.d0 + w.j0;
+      const T wr = a.seed ? __ldg(a.seed + r) : T(1);
+      T h0[V], ug[V], us[V];
+      span_cut_sums<T, V>(a.csc, sc, a.N, w, sb + SPAN, a.gamma + r * a.N, acc, h0, ug, us, er);   // layer 0: kind x
+      T yv[V];
+      ldv_rw<V>(sb + w.lane * V, yv);
+      T term = T(0), xs[V], a0[V], zero[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const T c0 = -yv[v] + h0[v];
+        const T x = c0 > T(0) ? xl[v] : (c0 < T(0) ? xh[v] : T(0.5) * (xl[v] + xh[v]));
+        xs[v] = wr * x;
+        a0[v] = -wr * x;
+        zero[v] = T(0);
+        if (w.on) term += tmin(c0 * xl[v], c0 * xh[v]);
+      }
+      if (a.E) span_cut_writes<T, V>(a.csc, sc, a.N, w, xs, zero, zero, ev, a.E + r * a.csc.n_total, er);
+      if (w.on && a.a0_out) put_operand_v<V, Top>(a.a0_out, a.a0_lo, ij, a0);
+      span_partial<T, V>(a.obj_part, a.R, r, w.c, a.d0, w.lane, term);
+      dense(k + NS, st);
+      scattered(k + NS, st);
+      cp_commit();
     }
-    if (a.E) span_cut_writes<T, V>(a.csc, sc, a.N, w, xs, zero, zero, ev, a.E + r * a.csc.n_total, er);
-    if (w.on && a.a0_out) put_operand_v<V, Top>(a.a0_out, a.a0_lo, ij, a0);
-    span_partial<T, V>(a.obj_part, a.R, r, w.c, a.d0, w.lane, term);
-    dense(k + NS, st);
-    scattered(k + NS, st);
-    cp_commit();
   }
   cp_wait<0>();
   er.flush();
@@ -887,7 +905,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_concretize(ConcArgs<T, 
 // dynamic shared memory of one block of the span kernels
 template <typename T, int V, int ND, int NB, int NFIX>
 constexpr size_t span_smem() {
-  return (size_t)kWarpsPerBlock * StageLayout<V, ND, NB, NFIX>::WARP * sizeof(T);
+  return (size_t)kSpanWarps * StageLayout<V, ND, NB, NFIX>::WARP * sizeof(T);
 }
 
 // g[r] = c_k^T b^(L) - gamma_r^T d + sum of the partials. A warp takes 32
@@ -1217,11 +1235,11 @@ void launch_span(Kern kern, size_t smem, dim3 grid, cudaStream_t st, const Args&
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  launch_pdl(kern, grid, dim3(kWarpsPerBlock * 32), smem, st, a);
+  launch_pdl(kern, grid, dim3(kSpanWarps * 32), smem, st, a);
 }
 inline dim3 span_blocks(int64_t R, int K, int d, int V) {
   const int64_t S = R / K;
-  return dim3((unsigned)((S + kWarpsPerBlock - 1) / kWarpsPerBlock), (unsigned)((d + 32 * V - 1) / (32 * V)),
+  return dim3((unsigned)((S + kSpanWarps - 1) / kSpanWarps), (unsigned)((d + 32 * V - 1) / (32 * V)),
               (unsigned)row_split(K));
 }
 

@@ -26,6 +26,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -743,11 +744,12 @@ bool encoder() {
   return g_encode != nullptr;
 }
 
-// 2-D map of a row-major [rows, cols] matrix, box of box_rows x 128 bytes.
-bool make_map(CUtensorMap* m, const void* base, bool bf16, int64_t rows, int64_t cols, int box_rows) {
+// 2-D map of a row-major [rows, cols] matrix (row stride ld elements, 0: cols),
+// box of box_rows x 128 bytes.
+bool make_map(CUtensorMap* m, const void* base, bool bf16, int64_t rows, int64_t cols, int box_rows, int64_t ld = 0) {
   const int es = bf16 ? 2 : 4;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
-  cuuint64_t strides[1] = {static_cast<cuuint64_t>(cols) * es};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld ? ld : cols) * es};
   cuuint32_t box[2] = {static_cast<cuuint32_t>(kRowBytes / es), static_cast<cuuint32_t>(box_rows)};
   cuuint32_t estr[2] = {1, 1};
   return g_encode(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
@@ -757,7 +759,8 @@ bool make_map(CUtensorMap* m, const void* base, bool bf16, int64_t rows, int64_t
 }
 
 template <int KIND>
-bool launch_tc(cudaStream_t st, int64_t M, int N, int K, const void* A, const void* B, const void* Blo, float* C) {
+bool launch_tc(cudaStream_t st, int64_t M, int N, int K, const void* A, const void* B, const void* Blo, float* C,
+               int64_t lda = 0, int64_t ldb = 0) {
   using Cfg = TcCfg<KIND>;
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
@@ -765,9 +768,9 @@ bool launch_tc(cudaStream_t st, int64_t M, int N, int K, const void* A, const vo
   });
   const bool bf = KIND == 0;
   CUtensorMap ta{}, tb{}, tblo{}, tc{};
-  if (!make_map(&ta, A, bf, M, K, BM) || !make_map(&tb, B, bf, N, K, BN)) return false;
+  if (!make_map(&ta, A, bf, M, K, BM, lda) || !make_map(&tb, B, bf, N, K, BN, ldb)) return false;
   if (KIND == 1) {
-    if (!make_map(&tblo, Blo, bf, N, K, BN)) return false;
+    if (!make_map(&tblo, Blo, bf, N, K, BN, ldb)) return false;
   } else {
     tblo = tb;
   }
@@ -810,6 +813,191 @@ bool gemm_tc_tf32x3(cudaStream_t st, int64_t M, int N, int K, const float* A, co
   const bool ok = launch_tc<1>(st, M, N, K, A, B, Blo, C);
   prof_end(st, tk);
   return ok;
+}
+
+// ------------------------------------------------------------------ float64 by exact slices
+namespace {
+// Row exponent e with max |A[r, :]| < 2^e, from the bit pattern of the
+// largest magnitude m (normal: m = 1.f 2^(E-1023) < 2^(E-1022)); 0 for m = 0.
+__device__ __forceinline__ int exp_above(double m) {
+  const long long bits = __double_as_longlong(m);
+  const int E = static_cast<int>((bits >> 52) & 0x7ff);
+  if (E != 0) return E - 1022;
+  if (m == 0.0) return 0;
+  const unsigned long long f = static_cast<unsigned long long>(bits) & ((1ull << 52) - 1);
+  return -1074 + (64 - __clzll(static_cast<long long>(f)));   // subnormal: f 2^-1074 < 2^(bit length - 1074)
+}
+
+// One warp per row. x = A[r, k] 2^-e lies in (-1, 1); its first b * s bits
+// after the binary point, X = trunc(|x| 2^(bs)), come from the mantissa by an
+// integer shift, and slice i (1 = most significant) is bits
+// b (s - i) .. b (s - i + 1) - 1 of X with the sign of x: the same integers as
+// s rounds of x *= 2^b, a = trunc(x), x -= a. |a| < 2^b, exact in bf16. A
+// row holding a non-finite value gets the exponent kSliceBadExp and zeros.
+__global__ void k_slice_rows(int64_t M, int K, const double* __restrict__ A, int b, int s, int reverse,
+                             __nv_bfloat16* __restrict__ planes, int32_t* __restrict__ exps) {
+  const int64_t row = static_cast<int64_t>(blockIdx.x) * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= M) return;
+  const double* a = A + row * K;
+  double mx = 0.0;
+  bool bad = false;
+  for (int k = lane; k < K; k += 32) {
+    const double v = a[k];
+    bad |= !isfinite(v);
+    mx = fmax(mx, fabs(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  bad = __any_sync(0xffffffffu, bad);
+  const int e = bad ? 0 : exp_above(mx);
+  if (lane == 0) exps[row] = bad ? kSliceBadExp : e;
+  const int bs = b * s;   // <= 56
+  const unsigned long long digit = (1ull << b) - 1;
+  __nv_bfloat16* out = planes + row * static_cast<int64_t>(s) * K;
+  for (int k = lane; k < K; k += 32) {
+    const long long bits = bad ? 0 : __double_as_longlong(a[k]);
+    const int E = static_cast<int>((bits >> 52) & 0x7ff);
+    const unsigned long long m = (static_cast<unsigned long long>(bits) & ((1ull << 52) - 1)) | (E ? (1ull << 52) : 0);
+    // |x| 2^bs = m 2^(max(E,1) - 1075 - e + bs)
+    const int sh = (E ? E : 1) - 1075 - e + bs;
+    const unsigned long long X = sh >= 0 ? (sh < 64 ? m << sh : 0) : (-sh < 64 ? m >> -sh : 0);
+    const float sg = bits < 0 ? -1.f : 1.f;
+    for (int i = 1; i <= s; ++i) {
+      const float d = static_cast<float>((X >> (b * (s - i))) & digit);
+      out[static_cast<int64_t>(reverse ? s - i : i - 1) * K + k] = __float2bfloat16_rn(sg * d);
+    }
+  }
+}
+
+// y[r, c] = sum over t = 2 .. s+1 of T_t[r, c] 2^(e_r + f_c - b t) (T_t the
+// exact integer sums of the slice GEMMs, plane t - 2 of T), formed exactly as
+// the 128-bit integer sum_t T_t 2^(b (s + 1 - t)) and rounded once to the
+// nearest float64 (integer operations only: float64 arithmetic is scarce on
+// this part); yabs[r, c] = 2^(e_r + f_c) K rounded up to float. Block = 8 rows
+// of y, threads along c.
+__device__ __forceinline__ double scale_pow2(double d, int k) {   // d * 2^k, d normal
+  const int E = static_cast<int>((__double_as_longlong(d) >> 52) & 0x7ff);
+  if (E + k >= 1 && E + k <= 2046)
+    return __longlong_as_double(__double_as_longlong(d) + (static_cast<long long>(k) << 52));
+  return ldexp(d, k);
+}
+__device__ __forceinline__ double i128_to_double_scaled(__int128 v, int k) {   // round(v) * 2^k
+  if (v == 0) return 0.0;
+  const bool neg = v < 0;
+  const unsigned __int128 u = neg ? static_cast<unsigned __int128>(-v) : static_cast<unsigned __int128>(v);
+  const unsigned long long hi = static_cast<unsigned long long>(u >> 64), lo = static_cast<unsigned long long>(u);
+  const int nbits = hi ? 128 - __clzll(static_cast<long long>(hi)) : 64 - __clzll(static_cast<long long>(lo));
+  int sh = nbits - 53;
+  unsigned long long mant;
+  if (sh > 0) {
+    mant = static_cast<unsigned long long>(u >> sh);
+    const unsigned __int128 rem = u & ((static_cast<unsigned __int128>(1) << sh) - 1);
+    const unsigned __int128 half = static_cast<unsigned __int128>(1) << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1))) ++mant;   // to nearest, ties to even
+    if (mant >> 53) {
+      mant >>= 1;
+      ++sh;
+    }
+  } else {
+    mant = lo << -sh;
+  }
+  // value = mant 2^(sh + k), 2^52 <= mant < 2^53
+  const int ef = 52 + sh + k + 1023;
+  if (ef >= 1 && ef <= 2046)
+    return __longlong_as_double((neg ? (1ll << 63) : 0ll) | (static_cast<long long>(ef) << 52) |
+                                static_cast<long long>(mant & ((1ull << 52) - 1)));
+  const double m = ldexp(static_cast<double>(mant), sh + k);   // outside the normal range (exact mant)
+  return neg ? -m : m;
+}
+__global__ void k_slice_combine(int64_t M, int N, int b, int s, double kred, const float* __restrict__ T,
+                                const int32_t* __restrict__ er, const int32_t* __restrict__ fc,
+                                double* __restrict__ y, float* __restrict__ yabs) {
+  const int64_t plane = M * N;
+  const int64_t r1 = min(M, static_cast<int64_t>(blockIdx.x + 1) * 8);
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * 8; r < r1; ++r) {
+    const int e = er[r];
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+      const int64_t i = r * N + c;
+      const int f = __ldg(fc + c);
+      if (e >= kSliceBadExp || f >= kSliceBadExp) {
+        y[i] = __longlong_as_double(0x7ff8000000000000ll);
+        yabs[i] = __int_as_float(0x7f800000);
+        continue;
+      }
+      __int128 acc = 0;
+      for (int t = 2; t <= s + 1; ++t)
+        acc += static_cast<__int128>(__float2int_rz(__ldg(T + (t - 2) * plane + i))) *
+               (static_cast<__int128>(1) << (b * (s + 1 - t)));
+      y[i] = i128_to_double_scaled(acc, e + f - b * (s + 1));
+      yabs[i] = __double2float_ru(scale_pow2(kred, e + f));
+    }
+  }
+}
+}  // namespace
+
+bool slice_params(int K, int& b, int& s, double& cerr) {
+  // at least 50 bits of each operand, and every partial sum of a slice GEMM
+  // an integer below 2^22 (exact in the fp32 accumulator with room to spare)
+  if (K <= 0 || K % 8 != 0) return false;
+  for (b = 8; b >= 2; --b) {
+    s = (50 + b - 1) / b;
+    const double m = static_cast<double>((1 << b) - 1);
+    if (static_cast<double>(s) * K * m * m < 4194304.0) break;
+  }
+  if (b < 2) return false;
+  // truncation of both operands (2 + slop), the pairs i + j > s + 1 left out
+  // ((s - 1) / (1 - 2^-b)), both relative to 2^-bs; the rounding of the sum
+  // of the s terms to float64 (one rounding of the exact sum; bounded here as
+  // gamma_(s-1) times the terms' magnitudes, <= 1 / (1 - 2^-b)^2); everything
+  // in units of 2^(e_r + f_c) K
+  const double u = std::ldexp(1.0, -53), r = 1.0 - std::ldexp(1.0, -b);
+  const double gam = (s - 1) * u / (1.0 - (s - 1) * u);
+  cerr = (std::ldexp(2.01 + (s - 1) / r, -b * s) + gam / (r * r)) * (1.0 + std::ldexp(1.0, -20));
+  return true;
+}
+
+bool slice_rows(cudaStream_t st, int64_t M, int K, const double* A, int b, int s, bool reverse,
+                __nv_bfloat16* planes, int32_t* exps) {
+  if (M <= 0) return true;
+  if (!(reg_check(A, (double)M * K * 8, "slice A") & reg_check(planes, (double)M * s * K * 2, "slice planes") &
+        reg_check(exps, (double)M * 4, "slice exps")))
+    return true;   // reported by the caller's launch status
+  int tk = prof_begin(st, "slice_f64", 0.0, (double)M * K * (8.0 + 2.0 * s));
+  k_slice_rows<<<static_cast<unsigned>((M + 7) / 8), 256, 0, st>>>(M, K, A, b, s, reverse ? 1 : 0, planes, exps);
+  prof_end(st, tk);
+  return true;
+}
+
+bool gemm_f64_slices(cudaStream_t st, int64_t M, int N, int K, const double* A, const SliceB& B,
+                     __nv_bfloat16* ap, int32_t* ae, float* T, double* y, float* yabs) {
+  if (M <= 0 || N <= 0) return true;
+  const int s = B.s;
+  if (!B.planes || s < 1 || !tc_available(K, true) || M > (int64_t)INT32_MAX) return false;
+  if (!(reg_check(B.planes, (double)N * s * K * 2, "slice B") & reg_check(B.exps, (double)N * 4, "slice B exps") &
+        reg_check(T, (double)s * M * N * 4, "slice sums") & reg_check(y, (double)M * N * 8, "slice y") &
+        reg_check(yabs, (double)M * N * 4, "slice yabs")))
+    return true;   // reported by the caller's launch status
+  slice_rows(st, M, K, A, B.b, s, false, ap, ae);
+  // T_t for t = 2 .. s+1: A's slices 1 .. t-1 (a prefix of each row) against
+  // B's t-1 .. 1 (a suffix of B's reversed rows), K' = (t - 1) K. Each launch
+  // is counted with the share (t - 1) / (s (s + 1) / 2) of the product's
+  // algorithmic flops 2 M N K, and the slices it reads and the sums it writes.
+  const double pairs = 0.5 * s * (s + 1);
+  const int64_t plane = M * (int64_t)N;
+  bool ok = true;
+  for (int t = 2; t <= s + 1 && ok; ++t) {
+    int tk = prof_begin(st, "gemm_tc_f64_slices", 2.0 * M * N * K * (t - 1) / pairs,
+                        ((double)M + N) * K * 2.0 * (t - 1) + (double)plane * 4.0);
+    ok = launch_tc<0>(st, M, N, (t - 1) * K, ap, B.planes + static_cast<int64_t>(s - t + 1) * K, nullptr,
+                      T + (t - 2) * plane, static_cast<int64_t>(s) * K, static_cast<int64_t>(s) * K);
+    prof_end(st, tk);
+  }
+  if (!ok) return false;
+  int tk = prof_begin(st, "slice_combine_f64", 0.0, (double)plane * (4.0 * s + 12.0));
+  k_slice_combine<<<static_cast<unsigned>((M + 7) / 8), 256, 0, st>>>(M, N, B.b, s, static_cast<double>(K), T, ae,
+                                                                        B.exps, y, yabs);
+  prof_end(st, tk);
+  return true;
 }
 
 bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const __nv_bfloat16* Wp, int Kp, int Np,

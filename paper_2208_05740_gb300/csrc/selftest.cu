@@ -77,3 +77,46 @@ extern "C" gcp_status gcp_selftest_gemm(int32_t kind, int64_t M, int32_t N, int3
   cleanup();
   return st;
 }
+
+extern "C" gcp_status gcp_selftest_gemm_f64(int64_t M, int32_t N, int32_t K, const double* A, const double* B,
+                                            double* C, float* Cabs, double* cerr) {
+  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || !Cabs || !cerr) return GCP_EINVAL;
+  SliceB sl;
+  if (!slice_params(K, sl.b, sl.s, sl.cerr) || !tc_available(K, true)) return GCP_EINVAL;
+  const size_t na = (size_t)M * K, nb = (size_t)N * K, nc = (size_t)M * N;
+  std::vector<void*> bufs;
+  auto dalloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    reg_alloc(p, bytes);
+    bufs.push_back(p);
+    return p;
+  };
+  auto cleanup = [&]() {
+    for (void* p : bufs) {
+      reg_free(p);
+      cudaFree(p);
+    }
+  };
+  double *da = (double*)dalloc(na * 8), *db = (double*)dalloc(nb * 8), *dc = (double*)dalloc(nc * 8);
+  float* dca = (float*)dalloc(nc * 4);
+  sl.planes = (__nv_bfloat16*)dalloc(nb * sl.s * 2);
+  sl.exps = (int32_t*)dalloc((size_t)N * 4);
+  auto* ap = (__nv_bfloat16*)dalloc(na * sl.s * 2);
+  auto* ae = (int32_t*)dalloc((size_t)M * 4);
+  auto* sums = (float*)dalloc(nc * sl.s * 4);
+  if (!da || !db || !dc || !dca || !sl.planes || !sl.exps || !ap || !ae || !sums) { cleanup(); return GCP_ENOMEM; }
+  cudaMemcpy(da, A, na * 8, cudaMemcpyHostToDevice);
+  cudaMemcpy(db, B, nb * 8, cudaMemcpyHostToDevice);
+  gcp_status st = GCP_OK;
+  slice_rows(nullptr, N, K, db, sl.b, sl.s, true, sl.planes, sl.exps);
+  if (!gemm_f64_slices(nullptr, M, N, K, da, sl, ap, ae, sums, dc, dca)) st = GCP_EINVAL;
+  if (!reg_take_error().empty()) st = GCP_EDEVICE;
+  if (st == GCP_OK && cudaDeviceSynchronize() != cudaSuccess) st = GCP_ECUDA;
+  if (st == GCP_OK && !take_tc_error(nullptr).empty()) st = GCP_EDEVICE;
+  if (st == GCP_OK && cudaMemcpy(C, dc, nc * 8, cudaMemcpyDeviceToHost) != cudaSuccess) st = GCP_ECUDA;
+  if (st == GCP_OK && cudaMemcpy(Cabs, dca, nc * 4, cudaMemcpyDeviceToHost) != cudaSuccess) st = GCP_ECUDA;
+  if (st == GCP_OK) *cerr = sl.cerr;
+  cleanup();
+  return st;
+}

@@ -85,7 +85,11 @@ size_t estimate_bytes(const Net& net, int64_t R, int N, int64_t nnz, int Mcap) {
     dmax = std::max<int64_t>(dmax, net.dims[i]);
     P += (net.dims[i] + kChunk - 1) / kChunk;
   }
-  const double per_row = 4.0 * (5 * sum_d + 5 * dmax + nnz + 3 * N + 3 * Mcap) + 8.0 * (2 * dmax + P) + 4.0 * (dmax + P);
+  // certification by exact slices: bf16 slices of nu and the fp32 slice sums
+  int smax = 0;
+  for (const SliceB& sl : net.WTsl) smax = std::max(smax, sl.s);
+  const double per_row = 4.0 * (5 * sum_d + 5 * dmax + nnz + 3 * N + 3 * Mcap) + 8.0 * (2 * dmax + P) +
+                         4.0 * (dmax + P) + 6.0 * smax * dmax;
   const double resident = 4.0 * (sum_d + Mcap + N);
   return (size_t)(R * (per_row + resident)) + (size_t(16) << 20);
 }

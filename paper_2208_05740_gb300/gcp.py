@@ -26,7 +26,7 @@ GCP_PGA, GCP_ADAM = 0, 1
 EXPORTED = ["gcp_create", "gcp_destroy", "gcp_last_error", "gcp_set_stream", "gcp_mem_used", "gcp_init_net",
             "gcp_add_cuts", "gcp_duals_create", "gcp_duals_create_multi", "gcp_duals_shape", "gcp_duals_export", "gcp_duals_import",
             "gcp_duals_free", "gcp_bound_batch", "gcp_grad_batch", "gcp_optimize_batch", "gcp_bound_device",
-            "gcp_grad_device", "gcp_bound_dense_noalloc", "gcp_selftest_gemm", "gcp_profile_start", "gcp_profile_stop", "gcp_profile_query", "gcp_profile_report",
+            "gcp_grad_device", "gcp_bound_dense_noalloc", "gcp_selftest_gemm", "gcp_selftest_gemm_f64", "gcp_profile_start", "gcp_profile_stop", "gcp_profile_query", "gcp_profile_report",
             "gcp_serve_start", "gcp_serve_submit", "gcp_serve_poll", "gcp_serve_wait",
             "gcp_serve_stop"]
 
@@ -100,6 +100,7 @@ def lib():
                                         C.POINTER(P), C.POINTER(P), P, P, P, P, I32, I64, P, P],
             "gcp_selftest_gemm": [I32, I64, I32, I32, C.POINTER(C.c_float), C.POINTER(C.c_float),
                                   C.POINTER(C.c_float)],
+            "gcp_selftest_gemm_f64": [I64, I32, I32, pd, pd, pd, C.POINTER(C.c_float), pd],
             "gcp_profile_start": [C.c_char_p],
             "gcp_profile_stop": [],
             "gcp_profile_query": [C.c_char_p, C.POINTER(I64), pd, pd, pd],
@@ -370,6 +371,23 @@ def selftest_gemm(kind: int, A: np.ndarray, B: np.ndarray) -> np.ndarray:
     if st != GCP_OK:
         raise GCPError(st, "selftest gemm failed")
     return out
+
+
+def selftest_gemm_f64(A: np.ndarray, B: np.ndarray):
+    """(C, Cabs, cerr): C = A @ B.T in float64 on the tensor cores by exact
+    slices, with |C - exact| <= cerr * Cabs."""
+    A = _c(A, np.float64)
+    B = _c(B, np.float64)
+    M, K = A.shape
+    N = B.shape[0]
+    out = np.zeros((M, N), np.float64)
+    cabs = np.zeros((M, N), np.float32)
+    cerr = C.c_double()
+    st = lib().gcp_selftest_gemm_f64(M, N, K, _ptr(A, C.c_double), _ptr(B, C.c_double), _ptr(out, C.c_double),
+                                     _ptr(cabs, C.c_float), C.byref(cerr))
+    if st != GCP_OK:
+        raise GCPError(st, "selftest float64 gemm failed")
+    return out, cabs, cerr.value
 
 
 def profile_start(kernel_prefix: Optional[str] = None):

@@ -332,3 +332,89 @@ def test_full_size_mlp_sampled_rows(ctx):
     assert_rel(cert[rows], ref, 1e-9, "sampled certified")
     assert np.all(np.isfinite(bound)) and np.all(np.isfinite(cert))
     assert np.all(cert <= bound + 1e-5 * np.maximum(1, np.abs(bound)))
+
+
+def test_full_size_cnn_sampled_rows(ctx):
+    """CNN 3x32x32-c32-c64-fc512-fc10 at its full batch: 4096 subdomains x 9
+    rows, 1000 cuts, BF16 ascent steps (tensor-core convolutions), then FP64
+    certification; 4 sampled subdomains checked row by row against the oracle
+    at the reached duals."""
+    inst = synth.cnn_cifar()
+    net_id, cs = ctx.load_instance(inst)
+    D = ctx.duals_create(net_id, cs, inst.sub, gcp.GCP_FP32)
+    bound, cert, _ = ctx.optimize_batch(D, gcp.opt_params(5, gcp.GCP_ADAM, gcp.GCP_BF16, 1, 0.1, 0.02, 0.02, 0.98))
+    A, B, G = ctx.duals_export(D)
+    idx = [0, 1, 2047, 4095]
+    rows = rows_of(inst, idx)
+    sub_inst = select(inst, idx)
+    P = O.build_problem(sub_inst)
+    ref = O.evaluate(P, oracle_duals(sub_inst, A[rows], B[rows][:, :P.max_splits], G[rows]))
+    assert_rel(bound[rows], ref, 1e-3, "sampled bf16")
+    assert_rel(cert[rows], ref, 1e-9, "sampled certified")
+    assert np.all(np.isfinite(bound)) and np.all(np.isfinite(cert))
+    ctx.duals_free(D)
+
+
+def test_full_size_three_queries_sampled_rows(ctx):
+    """MLP 784-1024x4-10, three queries of 64, 700 and 2048 subdomains with 0,
+    500 and 3000 cuts in one batch (shared launches), FP32 ascent steps and
+    FP64 certification; sampled subdomains of each query checked against the
+    oracle at the reached duals."""
+    qs = synth.mlp_1024x4_queries()
+    q0 = qs[0]
+    net_id = ctx.init_net(q0.net.layers, q0.x_lo, q0.x_hi, q0.spec, q0.inter_lo, q0.inter_hi)
+    cs_ids = []
+    for q in qs:
+        c = q.cuts
+        cs_ids.append(ctx.add_cuts(net_id, c.ptr, c.layer, c.kind, c.index, c.coef, c.d)[0] if c.n else -1)
+    M = ctx.duals_create_multi(net_id, cs_ids, [q.sub for q in qs], gcp.GCP_FP32)
+    assert M.rows == 9 * (64 + 700 + 2048) and M.n_cuts == 3500
+    bound, cert, _ = ctx.optimize_batch(M, gcp.opt_params(5, gcp.GCP_ADAM, gcp.GCP_FP32, 1, 0.1, 0.02, 0.02, 0.98))
+    A, B, G = ctx.duals_export(M)
+    r0, c0 = 0, 0
+    for q, idx in zip(qs, ([0, 63], [0, 350, 699], [0, 1024, 2047])):
+        n = q.sub.n * 9
+        Aq, Bq, Gq = A[r0:r0 + n], B[r0:r0 + n], G[r0:r0 + n, c0:c0 + q.cuts.n]
+        mask = np.ones(M.n_cuts, bool)
+        mask[c0:c0 + q.cuts.n] = False
+        assert np.all(G[r0:r0 + n][:, mask] == 0)          # other queries' cuts stay at zero
+        rows = rows_of(q, idx)
+        sub_q = select(q, idx)
+        P = O.build_problem(sub_q)
+        ref = O.evaluate(P, oracle_duals(sub_q, Aq[rows], Bq[rows][:, :P.max_splits], Gq[rows]))
+        assert_rel(bound[r0 + rows], ref, 1e-5, f"query of {q.sub.n}: sampled fp32")
+        assert_rel(cert[r0 + rows], ref, 1e-9, f"query of {q.sub.n}: sampled certified")
+        r0 += n
+        c0 += q.cuts.n
+    assert np.all(np.isfinite(bound)) and np.all(np.isfinite(cert))
+    ctx.duals_free(M)
+
+
+def test_certify_by_slices_matches_simt_float64(ctx):
+    """The certification's dense products on the tensor cores (exact bf16
+    slices) against the SIMT float64 products (GCP_TC=0): the two certified
+    bounds differ only by their rounding-error terms, and both lie within
+    1e-9 of the oracle at the same duals."""
+    import os
+    inst = synth.mlp_256x6(n_sub=40, n_cuts=60)
+    P = O.build_problem(inst)
+    net_id, cs = ctx.load_instance(inst)
+    A, B, G = _rand_duals(inst, 23, 0.2)
+    certs = []
+    for tc in ("1", "0"):
+        old = os.environ.get("GCP_TC")
+        os.environ["GCP_TC"] = tc
+        try:
+            D = ctx.duals_create(net_id, cs, inst.sub, gcp.GCP_FP32)
+        finally:
+            if old is None:
+                os.environ.pop("GCP_TC", None)
+            else:
+                os.environ["GCP_TC"] = old
+        ctx.duals_import(D, A, B, G)
+        _, cert = ctx.bound_batch(D, gcp.GCP_FP32, certify=True)
+        certs.append(cert)
+        Ae, Be, Ge = ctx.duals_export(D)
+        assert_rel(cert, O.evaluate(P, oracle_duals(inst, Ae, Be, Ge)), 1e-9, f"certified (GCP_TC={tc})")
+        ctx.duals_free(D)
+    assert_rel(certs[0], certs[1], 1e-11, "slices vs SIMT float64")
