@@ -426,6 +426,8 @@ struct ConvTcArgs {
   int64_t R;
   int stg_rows;            // source-map rows the staging buffer holds
   int tmem_cols;
+  int group;               // tiles per work unit: 1, or 2 = phases (ph, 0) and (ph, 1) together
+  int units;
   const __nv_bfloat16* src;  // [R, Cs*Hs*Ws], channel-major (c, h, w)
   const __nv_bfloat16* Wp;   // [Np, Kp]
   float* out;                // [R, Co*Ho*Wo], channel-major
@@ -473,6 +475,17 @@ struct ConvTile {
   int f, nrt, sh0, nsh;
   int m0, mend, r0;
 };
+// Work unit u: one tile, or (group 2, a stride-2 transposed convolution)
+// tile q of phases (ph, 0) and (ph, 1), which cover the same batch rows and
+// phase-local pixels and read the same source rows. Their outputs interleave
+// along w (columns 2j and 2j + 1), so the unit stages its source rows once and
+// writes each output row segment whole: adjacent float pairs, full sectors.
+__host__ __device__ inline int unit_tile(const ConvTcArgs& a, int u, int g) {
+  if (a.group == 1) return u;
+  const int p = u < a.c.f[0].ntiles ? 0 : 1;
+  return a.c.f[2 * p + g].tile0 + (p ? u - a.c.f[0].ntiles : u);
+}
+
 __host__ __device__ inline ConvTile conv_tile(const ConvPlan& c, int R, int t) {
   ConvTile T{};
   int q = 0;
@@ -549,7 +562,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(2 * a.tmem_cols)
+                 "r"(2 * a.group * a.tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -583,7 +596,6 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
 
   const int HW = c.Hs * c.Ws, src_dim = c.Cs * HW, out_dim = c.Co * c.Ho * c.Wo;
   const int R = (int)a.R;
-  const int tiles = c.f[c.nph - 1].tile0 + c.f[c.nph - 1].ntiles;
   const int s_out = c.dir == 0 ? 1 : c.stride;     // output-pixel step within a phase
 
   if (warp >= kConvEpiWarps && warp < kConvEpiWarps + kConvProdWarps) {
@@ -591,12 +603,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
     const int ptid = tid - kConvEpiWarps * 32;
     const int row = ptid & (BM - 1), half = ptid >> 7;   // GEMM row; chunks 4*half .. 4*half+3
     uint32_t g = 0;
-    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-      // all producers finished the previous tile (the staging is free again)
+    for (int u = blockIdx.x; u < a.units; u += gridDim.x) {
+      // all producers finished the previous unit (the staging is free again)
       if (prod_sync_or(*abort_flag != 0)) break;
-      const ConvTile T = conv_tile(c, R, tile);
-      const ConvPhase& f = c.f[T.f];
-      const int Pf = f.Hf * f.Wf;
+      const ConvTile T = conv_tile(c, R, unit_tile(a, u, 0));
       // one work item = 8 channels of one pixel; consecutive threads take
       // consecutive pixels of the same channel group, so each load reads a
       // contiguous run of a channel's row. The (pixel, group, row) position
@@ -626,6 +636,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
         }
       }
       if (prod_sync_or(*abort_flag != 0)) break;   // staging complete
+      bool quit = false;
+      for (int gs = 0; gs < a.group && !quit; ++gs) {
+      // the unit's tiles share rows, pixels and staged source rows
+      const ConvPhase& f = c.f[gs ? conv_tile(c, R, unit_tile(a, u, gs)).f : T.f];
+      const int Pf = f.Hf * f.Wf;
       // this thread's GEMM row: batch row r, output pixel (oh, ow); its source
       // pixel for tap (a, b) is (bh + sg_tap * a, bw + sg_tap * b)
       const int m = T.m0 + row;
@@ -640,8 +655,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       const __nv_bfloat16* srow = stg + rl * T.nsh * c.Ws * c.Csp;
       for (int kb = 0; kb < f.nkb; ++kb, ++g) {
         const int sg = g % kConvStages;
-        if (*abort_flag) break;   // no barrier inside this loop: leaving alone is safe
-        if (g >= kConvStages && !mbar_wait_idle(&a_empty[sg], ((g / kConvStages) - 1) & 1)) { *abort_flag = 1; break; }
+        if (*abort_flag) { quit = true; break; }   // no barrier inside this loop: leaving alone is safe
+        if (g >= kConvStages && !mbar_wait_idle(&a_empty[sg], ((g / kConvStages) - 1) & 1)) {
+          *abort_flag = 1;
+          quit = true;
+          break;
+        }
         uint8_t* At = As + sg * kTileA;
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
@@ -658,42 +677,45 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&a_full[sg]);
       }
+      }
     }
   } else if (warp == kConvEpiWarps + kConvProdWarps) {
     // ---------------- MMA issuer
     if (lane == 0) {
       const uint32_t id = idesc(1u, BM, c.Np);
       uint32_t g = 0, it = 0;
-      for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+      for (int u = blockIdx.x; u < a.units; u += gridDim.x, ++it) {
         if (*abort_flag) break;
-        const ConvTile T = conv_tile(c, R, tile);
-        const ConvPhase& f = c.f[T.f];
-        const uint32_t b = it & 1, acc = tmem + b * a.tmem_cols;
+        const uint32_t b = it & 1;
         if (it >= 2 && !mbar_wait_idle(&acc_empty[b], ((it >> 1) - 1) & 1)) { *abort_flag = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         bool ok = true;
-        for (int kb = 0; kb < f.nkb; ++kb, ++g) {
-          const int sg = g % kConvStages;
-          if (!mbar_wait_idle(&a_full[sg], (g / kConvStages) & 1)) { ok = false; break; }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t ab = smem_u32(As + sg * kTileA), bb = smem_u32(Bs + (f.kb0 + kb) * c.Np * kRowBytes);
+        for (int gs = 0; gs < a.group && ok; ++gs) {
+          const ConvPhase& f = c.f[conv_tile(c, R, unit_tile(a, u, gs)).f];
+          const uint32_t acc = tmem + (b * a.group + gs) * a.tmem_cols;
+          for (int kb = 0; kb < f.nkb; ++kb, ++g) {
+            const int sg = g % kConvStages;
+            if (!mbar_wait_idle(&a_full[sg], (g / kConvStages) & 1)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ab = smem_u32(As + sg * kTileA), bb = smem_u32(Bs + (f.kb0 + kb) * c.Np * kRowBytes);
 #pragma unroll
-          for (int k4 = 0; k4 < kRowBytes / 32; ++k4)
-            umma<0>(acc, sdesc(ab + k4 * 32), sdesc(bb + k4 * 32), id, (kb | k4) != 0);
-          umma_commit(&a_empty[sg]);   // the stage is free once these MMAs have read it
+            for (int k4 = 0; k4 < kRowBytes / 32; ++k4)
+              umma<0>(acc, sdesc(ab + k4 * 32), sdesc(bb + k4 * 32), id, (kb | k4) != 0);
+            umma_commit(&a_empty[sg]);   // the stage is free once these MMAs have read it
+          }
         }
         if (!ok) { *abort_flag = 1; break; }
-        umma_commit(&acc_full[b]);     // the tile's accumulator is complete
+        umma_commit(&acc_full[b]);     // the unit's accumulators are complete
       }
     }
     __syncwarp();
   } else {
     // ---------------- epilogue: TMEM -> global, channel-major output
     uint32_t it = 0;
-    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+    for (int u = blockIdx.x; u < a.units; u += gridDim.x, ++it) {
       // decisions are warp-uniform: the TMEM loads below are warp-collective
       if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
-      const ConvTile T = conv_tile(c, R, tile);
+      const ConvTile T = conv_tile(c, R, unit_tile(a, u, 0));
       const ConvPhase& f = c.f[T.f];
       const int Pf = f.Hf * f.Wf;
       const uint32_t b = it & 1;
@@ -707,13 +729,31 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       const int eoh = f.ph + s_out * epi, eow = f.pw + s_out * (epos - epi * f.Wf);
       float* dst = a.out + (int64_t)er * out_dim + (eoh * c.Wo + eow);
       const int64_t cstride = (int64_t)c.Ho * c.Wo;
-      for (int col = 0; col < c.Np; col += 32) {
-        uint32_t v[32];
-        tmem_ld32(tmem + b * a.tmem_cols + (static_cast<uint32_t>(warp * 32) << 16) + col, v);
-        if (em < T.mend) {
+      const uint32_t tl = tmem + b * a.group * a.tmem_cols + (static_cast<uint32_t>(warp * 32) << 16);
+      if (a.group == 1) {
+        for (int col = 0; col < c.Np; col += 32) {
+          uint32_t v[32];
+          tmem_ld32(tl + col, v);
+          if (em < T.mend) {
 #pragma unroll
-          for (int t = 0; t < 32; ++t)
-            if (col + t < c.Co) dst[(col + t) * cstride] = __uint_as_float(v[t]);
+            for (int t = 0; t < 32; ++t)
+              if (col + t < c.Co) dst[(col + t) * cstride] = __uint_as_float(v[t]);
+          }
+        }
+      } else {
+        // phase (ph, 0) at column eow = 2j, phase (ph, 1) at 2j + 1: one
+        // 8-byte store per channel (Wo and the row offsets are even)
+        for (int col = 0; col < c.Np; col += 32) {
+          uint32_t v0[32], v1[32];
+          tmem_ld32(tl + col, v0);
+          tmem_ld32(tl + a.tmem_cols + col, v1);
+          if (em < T.mend) {
+#pragma unroll
+            for (int t = 0; t < 32; ++t)
+              if (col + t < c.Co)
+                *reinterpret_cast<float2*>(dst + (col + t) * cstride) =
+                    make_float2(__uint_as_float(v0[t]), __uint_as_float(v1[t]));
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -723,7 +763,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * a.tmem_cols)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * a.group * a.tmem_cols)
                  : "memory");
   }
 }
@@ -1023,6 +1063,19 @@ bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const
   int tc = 32;
   while (tc < Np) tc <<= 1;
   a.tmem_cols = tc;
+  // pair the phases (ph, 0), (ph, 1) of a stride-2 transposed convolution
+  a.group = 1;
+  if (dir == 1 && c.stride == 2 && c.nph == 4 && c.Wo % 2 == 0 && 4 * tc <= 512 &&
+      (reinterpret_cast<uintptr_t>(out) & 7) == 0) {
+    bool pairs = true;
+    for (int p = 0; p < 2; ++p) {
+      const ConvPhase &f0 = c.f[2 * p], &f1 = c.f[2 * p + 1];
+      pairs = pairs && f0.ph == f1.ph && f0.pw == 0 && f1.pw == 1 && f0.Hf == f1.Hf && f0.Wf == f1.Wf &&
+              f0.ntiles == f1.ntiles;
+    }
+    if (pairs) a.group = 2;
+  }
+  a.units = a.group == 2 ? c.f[0].ntiles + c.f[2].ntiles : tiles;
   const ConvSmem L = conv_smem_layout(Kp, Np, a.stg_rows, c.Ws, c.Csp);
   if (L.total > 227 * 1024) return false;
   static std::mutex mu;
@@ -1051,9 +1104,10 @@ bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const
     return true;  // reported by the caller's launch status
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc, kConvThreads, L.total);
-  if (2 * tc > 512) return false;
-  per_sm = std::max(1, std::min(per_sm, 512 / (2 * tc)));   // TMEM columns of the resident CTAs (two accumulators)
-  const int grid = std::min(tiles, n_sm * per_sm);
+  if (2 * a.group * tc > 512) return false;
+  // TMEM columns of the resident CTAs (two buffers of `group` accumulators each)
+  per_sm = std::max(1, std::min(per_sm, 512 / (2 * a.group * tc)));
+  const int grid = std::min(a.units, n_sm * per_sm);
   // algorithmic work: the convolution's multiply-adds (2 flops each); bytes:
   // source read and output written once
   const double macs = (double)R * g.c_out * g.h_out * g.w_out * g.c_in * g.k * g.k;
