@@ -428,6 +428,7 @@ struct ConvTcArgs {
   int tmem_cols;
   int group;               // tiles per work unit: 1, or 2 = phases (ph, 0) and (ph, 1) together
   int units;
+  int stg_bufs;            // staging buffers: 2 = the next unit's source rows load during this unit's A blocks
   const __nv_bfloat16* src;  // [R, Cs*Hs*Ws], channel-major (c, h, w)
   const __nv_bfloat16* Wp;   // [Np, Kp]
   float* out;                // [R, Co*Ho*Wo], channel-major
@@ -443,11 +444,11 @@ constexpr int kConvStages = 4;   // A blocks in flight
 struct ConvSmem {
   int b_off, stg_off, tab_off, bar_off, total;
 };
-__host__ __device__ inline ConvSmem conv_smem_layout(int Kp, int Np, int stg_rows, int Ws, int Csp) {
+__host__ __device__ inline ConvSmem conv_smem_layout(int Kp, int Np, int stg_rows, int Ws, int Csp, int bufs) {
   ConvSmem L;
   L.b_off = kConvStages * kTileA;                          // after the A stages
   L.stg_off = L.b_off + (Kp / 64) * Np * kRowBytes;        // weights: Kp/64 tiles of Np rows
-  L.tab_off = (L.stg_off + stg_rows * Ws * Csp * 2 + 15) & ~15;
+  L.tab_off = (L.stg_off + bufs * stg_rows * Ws * Csp * 2 + 15) & ~15;
   L.bar_off = (L.tab_off + (Kp / 8) * 4 + 7) & ~7;         // chunk table: one word per 8 K columns
   // barriers: full/empty per A stage, full/empty per accumulator, abort flag, TMEM slot
   L.total = L.bar_off + (2 * kConvStages + 4) * 8 + 16 + 1024;
@@ -530,11 +531,87 @@ inline int conv_set_tiles(ConvPlan& c, int R) {
   return n;
 }
 
+// Staging of a unit's source rows in shared memory, channel innermost: one
+// item = 8 channels of one pixel; consecutive producer threads take
+// consecutive pixels of the same channel group, so each load reads a
+// contiguous run of a channel's row. A thread's first kStageAhead items are
+// loaded into registers one unit ahead (stage_load, issued before the current
+// unit's A blocks are built) and written out at the start of their unit
+// (stage_store), which also loads and writes any further items directly.
+constexpr int kStageAhead = 4;
+struct StageAhead {
+  uint32_t v[kStageAhead][8];
+  int dst[kStageAhead];   // element offset in the staging buffer, -1 = none
+};
+struct StageGeom {
+  int npix, cgroups, nitems;
+};
+__device__ __forceinline__ StageGeom stage_geom(const ConvPlan& c, const ConvTile& T) {
+  StageGeom G;
+  G.npix = T.nsh * c.Ws;
+  G.cgroups = c.Csp / 8;
+  G.nitems = T.nrt * G.npix * G.cgroups;
+  return G;
+}
+// the item's position: pixel pw of the staged rows, channel group cg, batch row rr
+__device__ __forceinline__ void stage_pos(const StageGeom& G, int item, int& pw, int& cg, int& rr) {
+  pw = item % G.npix;
+  cg = (item / G.npix) % G.cgroups;
+  rr = item / (G.npix * G.cgroups);
+}
+__device__ __forceinline__ void stage_item_load(const ConvTcArgs& a, const ConvTile& T, int pw, int cg, int rr,
+                                                uint32_t (&v)[8]) {
+  const ConvPlan& c = a.c;
+  const int HW = c.Hs * c.Ws;
+  const __nv_bfloat16* sp = a.src + (int64_t)(T.r0 + rr) * (c.Cs * HW) + (T.sh0 * c.Ws + pw + cg * 8 * HW);
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) v[cc] = cg * 8 + cc < c.Cs ? (uint32_t)__bfloat16_as_ushort(sp[cc * HW]) : 0u;
+}
+__device__ __forceinline__ void stage_item_store(__nv_bfloat16* dst, const uint32_t (&v)[8]) {
+  *reinterpret_cast<uint4*>(dst) =
+      make_uint4(v[0] | (v[1] << 16), v[2] | (v[3] << 16), v[4] | (v[5] << 16), v[6] | (v[7] << 16));
+}
+__device__ __forceinline__ void stage_load(const ConvTcArgs& a, const ConvTile& T, int ptid, StageAhead& sa) {
+  const StageGeom G = stage_geom(a.c, T);
+#pragma unroll
+  for (int q = 0; q < kStageAhead; ++q) {
+    const int item = ptid + q * kConvProdThreads;
+    sa.dst[q] = -1;
+    if (item < G.nitems) {
+      int pw, cg, rr;
+      stage_pos(G, item, pw, cg, rr);
+      stage_item_load(a, T, pw, cg, rr, sa.v[q]);
+      sa.dst[q] = (rr * G.npix + pw) * a.c.Csp + cg * 8;
+    }
+  }
+}
+__device__ __forceinline__ void stage_store(const ConvTcArgs& a, const ConvTile& T, int ptid, const StageAhead& sa,
+                                            __nv_bfloat16* stg) {
+#pragma unroll
+  for (int q = 0; q < kStageAhead; ++q)
+    if (sa.dst[q] >= 0) stage_item_store(stg + sa.dst[q], sa.v[q]);
+  const StageGeom G = stage_geom(a.c, T);
+  int item = ptid + kStageAhead * kConvProdThreads;
+  if (item >= G.nitems) return;
+  int pw, cg, rr;
+  stage_pos(G, item, pw, cg, rr);
+  for (; item < G.nitems; item += kConvProdThreads) {
+    uint32_t v[8];
+    stage_item_load(a, T, pw, cg, rr, v);
+    stage_item_store(stg + (rr * G.npix + pw) * a.c.Csp + cg * 8, v);
+    pw += kConvProdThreads;   // the next item's position by additions
+    while (pw >= G.npix) {
+      pw -= G.npix;
+      if (++cg == G.cgroups) { cg = 0; ++rr; }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_constant__ ConvTcArgs a) {
   const ConvPlan& c = a.c;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const ConvSmem lay = conv_smem_layout(c.Kp, c.Np, a.stg_rows, c.Ws, c.Csp);
+  const ConvSmem lay = conv_smem_layout(c.Kp, c.Np, a.stg_rows, c.Ws, c.Csp, a.stg_bufs);
   uint8_t* As = smem;
   uint8_t* Bs = smem + lay.b_off;
   __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(smem + lay.stg_off);
@@ -603,39 +680,30 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
     const int ptid = tid - kConvEpiWarps * 32;
     const int row = ptid & (BM - 1), half = ptid >> 7;   // GEMM row; chunks 4*half .. 4*half+3
     uint32_t g = 0;
+    const int stg_elems = a.stg_rows * c.Ws * c.Csp;
+    StageAhead sa;
+    ConvTile Tn{};
+    if (blockIdx.x < (unsigned)a.units) {
+      Tn = conv_tile(c, R, unit_tile(a, blockIdx.x, 0));
+      stage_load(a, Tn, ptid, sa);
+    }
+    int cur = 0;
     for (int u = blockIdx.x; u < a.units; u += gridDim.x) {
-      // all producers finished the previous unit (the staging is free again)
-      if (prod_sync_or(*abort_flag != 0)) break;
-      const ConvTile T = conv_tile(c, R, unit_tile(a, u, 0));
-      // one work item = 8 channels of one pixel; consecutive threads take
-      // consecutive pixels of the same channel group, so each load reads a
-      // contiguous run of a channel's row. The (pixel, group, row) position
-      // advances by additions from one item to the next.
-      const int npix = T.nsh * c.Ws, cgroups = c.Csp / 8, nitems = T.nrt * npix * cgroups;
-      int pw = 0, cg = 0, rr = 0;
-      if (nitems > 0) {
-        pw = ptid % npix;
-        cg = (ptid / npix) % cgroups;
-        rr = ptid / (npix * cgroups);
-      }
-      for (int item = ptid; item < nitems; item += kConvProdThreads) {
-        const __nv_bfloat16* sp =
-            a.src + (int64_t)(T.r0 + rr) * src_dim + (T.sh0 * c.Ws + pw + cg * 8 * HW);
-        uint32_t w[4];
-#pragma unroll
-        for (int cc = 0; cc < 8; cc += 2) {
-          const uint32_t lo = cg * 8 + cc < c.Cs ? __bfloat16_as_ushort(sp[cc * HW]) : 0u;
-          const uint32_t hi = cg * 8 + cc + 1 < c.Cs ? __bfloat16_as_ushort(sp[(cc + 1) * HW]) : 0u;
-          w[cc / 2] = lo | (hi << 16);
-        }
-        *reinterpret_cast<uint4*>(stg + (rr * npix + pw) * c.Csp + cg * 8) = make_uint4(w[0], w[1], w[2], w[3]);
-        pw += kConvProdThreads;
-        while (pw >= npix) {
-          pw -= npix;
-          if (++cg == cgroups) { cg = 0; ++rr; }
-        }
-      }
+      // one staging buffer: wait until all producers finished the previous
+      // unit's A blocks. Two: the buffer was last read two units ago, before
+      // every producer passed the previous unit's staging barrier.
+      if (a.stg_bufs == 1 && prod_sync_or(*abort_flag != 0)) break;
+      const ConvTile T = Tn;
+      __nv_bfloat16* sbuf = stg + cur * stg_elems;
+      stage_store(a, T, ptid, sa, sbuf);
       if (prod_sync_or(*abort_flag != 0)) break;   // staging complete
+      // the next unit's loads fly while this unit's A blocks are built
+      const int un = u + (int)gridDim.x;
+      if (un < a.units) {
+        Tn = conv_tile(c, R, unit_tile(a, un, 0));
+        stage_load(a, Tn, ptid, sa);
+      }
+      if (a.stg_bufs == 2) cur ^= 1;
       bool quit = false;
       for (int gs = 0; gs < a.group && !quit; ++gs) {
       // the unit's tiles share rows, pixels and staged source rows
@@ -652,7 +720,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       const int bh = c.dir == 0 ? oh * c.stride - c.pad : (oh + c.pad - f.rh) / c.stride;
       const int bw = c.dir == 0 ? ow * c.stride - c.pad : (ow + c.pad - f.rw) / c.stride;
       const int sg_tap = c.dir == 0 ? 1 : -1;
-      const __nv_bfloat16* srow = stg + rl * T.nsh * c.Ws * c.Csp;
+      const __nv_bfloat16* srow = sbuf + rl * T.nsh * c.Ws * c.Csp;
       for (int kb = 0; kb < f.nkb; ++kb, ++g) {
         const int sg = g % kConvStages;
         if (*abort_flag) { quit = true; break; }   // no barrier inside this loop: leaving alone is safe
@@ -1076,7 +1144,12 @@ bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const
     if (pairs) a.group = 2;
   }
   a.units = a.group == 2 ? c.f[0].ntiles + c.f[2].ntiles : tiles;
-  const ConvSmem L = conv_smem_layout(Kp, Np, a.stg_rows, c.Ws, c.Csp);
+  a.stg_bufs = 2;
+  ConvSmem L = conv_smem_layout(Kp, Np, a.stg_rows, c.Ws, c.Csp, 2);
+  if (L.total > 227 * 1024) {
+    a.stg_bufs = 1;
+    L = conv_smem_layout(Kp, Np, a.stg_rows, c.Ws, c.Csp, 1);
+  }
   if (L.total > 227 * 1024) return false;
   static std::mutex mu;
   static int attr_bytes = 0;
