@@ -982,7 +982,7 @@ gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, 
     a.nu_out = nu;
     a.nu_lo = (lo && tc_bwd<Top>(b, i)) ? lo : nullptr;
     a.nuhat_out = nuhat;
-    a.obj_part = part + (int64_t)poff * R;
+    a.obj_part = finalize ? part + (int64_t)poff * R : nullptr;   // ascent steps need no objective
     relax_eval<T, Top>(st, a);
     poff += (net.dims[i] + kChunk - 1) / kChunk;
     lin_backward<Top, T>(st, b, i, nu, a.nu_lo, y);
@@ -997,7 +997,7 @@ gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, 
   ca.a0_out = with_adjoint_start ? nu : nullptr;
   ca.a0_lo = (with_adjoint_start && lo && tc_fwd<Top>(b, 1)) ? lo : nullptr;
   ca.E = E;
-  ca.obj_part = part + (int64_t)poff * R;
+  ca.obj_part = finalize ? part + (int64_t)poff * R : nullptr;
   concretize<T, Top>(st, ca);
   poff += (net.dims[0] + kChunk - 1) / kChunk;
   if (finalize) {

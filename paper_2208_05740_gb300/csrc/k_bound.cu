@@ -603,23 +603,29 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_eval(RelaxArgs<T, Top
   SpanNeurons<T, V> n;
   DevErr er;
   SpanCuts<T> sc;
+  bool wsplit = false;   // some lane of the warp has a split neuron (warp-uniform)
   auto scattered = [&](int k, int st) {
     T* sb = stage(st) + 2 * SPAN;
     const int64_t r = (int64_t)w.s * a.K + k;
 #pragma unroll
     for (int q = 0; q < kSpanBatches; ++q) {
-      const bool ok = k < ke && sc.b[q].cut >= 0;
+      const bool ok = k < ke && sc.b[q].cut >= 0 && sc.cb + 32 * q < sc.ce;
       cp_async<sizeof(T)>(sb + 32 * q + w.lane, ok ? a.gamma + r * a.N + sc.b[q].cut : dummy, ok);
     }
+    if (wsplit) {
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const bool ok = k < ke && w.on && n.slot[v] >= 0;
-      cp_async<sizeof(T)>(sb + kSpanBatches * 32 + 32 * v + w.lane, ok ? a.beta + r * a.M + n.slot[v] : dummy, ok);
+      for (int v = 0; v < V; ++v) {
+        const bool ok = k < ke && w.on && n.slot[v] >= 0;
+        cp_async<sizeof(T)>(sb + kSpanBatches * 32 + 32 * v + w.lane, ok ? a.beta + r * a.M + n.slot[v] : dummy,
+                            ok);
+      }
     }
   };
   span_zero<T, V>(acc, w.lane);
   span_neurons<T, V>(w, a.lo, a.hi, a.bias, a.inv_ul, a.sp, a.M, a.layer, n);
+  wsplit = __any_sync(0xffffffffu, w.on && n.split);
   span_cuts<T, V>(a.csc, a.N, a.d, w, sc, er);
+  const bool obj = a.obj_part != nullptr;   // ascent steps leave the objective out
   // everything above reads static data only; the rows come from earlier kernels
   griddep_wait();
 #pragma unroll
@@ -662,12 +668,12 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_eval(RelaxArgs<T, Top
           const T nuu = pi - al[v] * tmax(-nh[v], T(0)) - t[v];
           const int cl = n.cls[v];
           nu[v] = cl == 2 ? nuu : (cl == 1 ? nh[v] - t[v] : -t[v]);   // active: xhat = x, z = 1
-          term += (cl == 2 ? hu : (cl == 1 ? sq[v] : T(0))) - nu[v] * n.bj[v];
+          if (obj) term += (cl == 2 ? hu : (cl == 1 ? sq[v] : T(0))) - nu[v] * n.bj[v];
         }
         put_operand_v<V, Top>(a.nu_out, a.nu_lo, ij, nu);
         stv<V>(a.nuhat_out + ij, nh);
       }
-      span_partial<T, V>(a.obj_part, a.R, r, w.c, a.d, w.lane, term);
+      if (obj) span_partial<T, V>(a.obj_part, a.R, r, w.c, a.d, w.lane, term);
       dense(k + NS, st);
       scattered(k + NS, st);
       cp_commit();
@@ -715,7 +721,7 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_adj(AdjArgs<T, Top> a
     const int64_t r = (int64_t)w.s * a.K + k;
 #pragma unroll
     for (int q = 0; q < kSpanBatches; ++q) {
-      const bool ok = k < ke && sc.b[q].cut >= 0;
+      const bool ok = k < ke && sc.b[q].cut >= 0 && sc.cb + 32 * q < sc.ce;
       cp_async<sizeof(T)>(sb + 32 * q + w.lane, ok ? a.gamma + r * a.N + sc.b[q].cut : dummy, ok);
     }
   };
@@ -841,7 +847,7 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_concretize(ConcArgs<T, Top>
     const int64_t r = (int64_t)w.s * a.K + k;
 #pragma unroll
     for (int q = 0; q < kSpanBatches; ++q) {
-      const bool ok = k < ke && sc.b[q].cut >= 0;
+      const bool ok = k < ke && sc.b[q].cut >= 0 && sc.cb + 32 * q < sc.ce;
       cp_async<sizeof(T)>(sb + 32 * q + w.lane, ok ? a.gamma + r * a.N + sc.b[q].cut : dummy, ok);
     }
   };
@@ -892,7 +898,7 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_concretize(ConcArgs<T, Top>
       }
       if (a.E) span_cut_writes<T, V>(a.csc, sc, a.N, w, xs, zero, zero, ev, a.E + r * a.csc.n_total, er);
       if (w.on && a.a0_out) put_operand_v<V, Top>(a.a0_out, a.a0_lo, ij, a0);
-      span_partial<T, V>(a.obj_part, a.R, r, w.c, a.d0, w.lane, term);
+      if (a.obj_part) span_partial<T, V>(a.obj_part, a.R, r, w.c, a.d0, w.lane, term);
       dense(k + NS, st);
       scattered(k + NS, st);
       cp_commit();
@@ -1274,7 +1280,8 @@ void relax_eval(cudaStream_t st, const RelaxArgs<T, Top>& a) {
         reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") & chk_splits(a.sp, a.R, a.K, a.M) &
         chk_csc(a.csc, a.d) & reg_check(a.nu_out, Rd * sizeof(Top), "nu out") &
         reg_check(a.nu_lo, a.nu_lo ? Rd * 4.0 : 0.0, "nu lo") &
-        reg_check(a.nuhat_out, Rd * tb, "nuhat out") & reg_check(a.obj_part, ((a.d + 31) / 32) * (double)a.R * tb, "obj part")))
+        reg_check(a.nuhat_out, Rd * tb, "nuhat out") &
+        (!a.obj_part || reg_check(a.obj_part, ((a.d + 31) / 32) * (double)a.R * tb, "obj part"))))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
   if constexpr (sizeof(T) == 4) {
@@ -1342,7 +1349,7 @@ void concretize(cudaStream_t st, const ConcArgs<T, Top>& a) {
         reg_check(a.a0_out, a.a0_out ? Rd * sizeof(Top) : 0.0, "a0 out") &
         reg_check(a.a0_lo, (a.a0_out && a.a0_lo) ? Rd * 4.0 : 0.0, "a0 lo") &
         reg_check(a.E, (a.E && a.csc.n_entries) ? (double)a.csc.n_total * a.R * tb : 0.0, "E") &
-        reg_check(a.obj_part, ((a.d0 + 31) / 32) * (double)a.R * tb, "obj part")))
+        (!a.obj_part || reg_check(a.obj_part, ((a.d0 + 31) / 32) * (double)a.R * tb, "obj part"))))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
   if constexpr (sizeof(T) == 4) {
