@@ -537,20 +537,32 @@ inline int conv_set_tiles(ConvPlan& c, int R) {
 // contiguous run of a channel's row. A thread's first kStageAhead items are
 // loaded into registers one unit ahead (stage_load, issued before the current
 // unit's A blocks are built) and written out at the start of their unit
-// (stage_store), which also loads and writes any further items directly.
+// (stage_store), which also loads and writes any further items directly. The
+// loads read a valid channel unconditionally (the last one for the padding
+// channels) and the padding is zeroed at the store, so nothing consumes a
+// loaded value before the store: the loads stay in flight. Chunk cg of pixel
+// p sits at chunk position cg ^ (p & smask) of the pixel (smask = channel
+// groups - 1 when that is a power of two), so that the 16-byte accesses of
+// consecutive pixels, here and in the A-block build, fall in distinct banks.
 constexpr int kStageAhead = 4;
 struct StageAhead {
   uint32_t v[kStageAhead][8];
   int dst[kStageAhead];   // element offset in the staging buffer, -1 = none
+  int nv[kStageAhead];    // real channels of the item (the rest is padding)
 };
 struct StageGeom {
-  int npix, cgroups, nitems;
+  int npix, cgroups, nitems, smask;
 };
+__device__ __forceinline__ int stage_smask(const ConvPlan& c) {
+  const int cg = c.Csp / 8;
+  return (cg & (cg - 1)) == 0 ? cg - 1 : 0;
+}
 __device__ __forceinline__ StageGeom stage_geom(const ConvPlan& c, const ConvTile& T) {
   StageGeom G;
   G.npix = T.nsh * c.Ws;
   G.cgroups = c.Csp / 8;
   G.nitems = T.nrt * G.npix * G.cgroups;
+  G.smask = stage_smask(c);
   return G;
 }
 // the item's position: pixel pw of the staged rows, channel group cg, batch row rr
@@ -559,29 +571,41 @@ __device__ __forceinline__ void stage_pos(const StageGeom& G, int item, int& pw,
   cg = (item / G.npix) % G.cgroups;
   rr = item / (G.npix * G.cgroups);
 }
+__device__ __forceinline__ int stage_off(const ConvPlan& c, const StageGeom& G, int pw, int cg, int rr) {
+  return (rr * G.npix + pw) * c.Csp + ((cg ^ (pw & G.smask)) << 3);
+}
 __device__ __forceinline__ void stage_item_load(const ConvTcArgs& a, const ConvTile& T, int pw, int cg, int rr,
                                                 uint32_t (&v)[8]) {
   const ConvPlan& c = a.c;
   const int HW = c.Hs * c.Ws;
-  const __nv_bfloat16* sp = a.src + (int64_t)(T.r0 + rr) * (c.Cs * HW) + (T.sh0 * c.Ws + pw + cg * 8 * HW);
+  const __nv_bfloat16* sp = a.src + (int64_t)(T.r0 + rr) * (c.Cs * HW) + (T.sh0 * c.Ws + pw);
 #pragma unroll
-  for (int cc = 0; cc < 8; ++cc) v[cc] = cg * 8 + cc < c.Cs ? (uint32_t)__bfloat16_as_ushort(sp[cc * HW]) : 0u;
+  for (int cc = 0; cc < 8; ++cc) v[cc] = __bfloat16_as_ushort(sp[min(cg * 8 + cc, c.Cs - 1) * HW]);
 }
-__device__ __forceinline__ void stage_item_store(__nv_bfloat16* dst, const uint32_t (&v)[8]) {
+__device__ __forceinline__ void stage_item_store(__nv_bfloat16* dst, const uint32_t (&v)[8], int nv) {
+  uint32_t w[8];
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) w[cc] = cc < nv ? v[cc] : 0u;
   *reinterpret_cast<uint4*>(dst) =
-      make_uint4(v[0] | (v[1] << 16), v[2] | (v[3] << 16), v[4] | (v[5] << 16), v[6] | (v[7] << 16));
+      make_uint4(w[0] | (w[1] << 16), w[2] | (w[3] << 16), w[4] | (w[5] << 16), w[6] | (w[7] << 16));
 }
 __device__ __forceinline__ void stage_load(const ConvTcArgs& a, const ConvTile& T, int ptid, StageAhead& sa) {
   const StageGeom G = stage_geom(a.c, T);
+  int pw = 0, cg = 0, rr = 0;
+  if (ptid < G.nitems) stage_pos(G, ptid, pw, cg, rr);   // later items by additions
 #pragma unroll
   for (int q = 0; q < kStageAhead; ++q) {
     const int item = ptid + q * kConvProdThreads;
     sa.dst[q] = -1;
     if (item < G.nitems) {
-      int pw, cg, rr;
-      stage_pos(G, item, pw, cg, rr);
       stage_item_load(a, T, pw, cg, rr, sa.v[q]);
-      sa.dst[q] = (rr * G.npix + pw) * a.c.Csp + cg * 8;
+      sa.dst[q] = stage_off(a.c, G, pw, cg, rr);
+      sa.nv[q] = a.c.Cs - cg * 8;
+      pw += kConvProdThreads;
+      while (pw >= G.npix) {
+        pw -= G.npix;
+        if (++cg == G.cgroups) { cg = 0; ++rr; }
+      }
     }
   }
 }
@@ -589,7 +613,7 @@ __device__ __forceinline__ void stage_store(const ConvTcArgs& a, const ConvTile&
                                             __nv_bfloat16* stg) {
 #pragma unroll
   for (int q = 0; q < kStageAhead; ++q)
-    if (sa.dst[q] >= 0) stage_item_store(stg + sa.dst[q], sa.v[q]);
+    if (sa.dst[q] >= 0) stage_item_store(stg + sa.dst[q], sa.v[q], sa.nv[q]);
   const StageGeom G = stage_geom(a.c, T);
   int item = ptid + kStageAhead * kConvProdThreads;
   if (item >= G.nitems) return;
@@ -598,7 +622,7 @@ __device__ __forceinline__ void stage_store(const ConvTcArgs& a, const ConvTile&
   for (; item < G.nitems; item += kConvProdThreads) {
     uint32_t v[8];
     stage_item_load(a, T, pw, cg, rr, v);
-    stage_item_store(stg + (rr * G.npix + pw) * a.c.Csp + cg * 8, v);
+    stage_item_store(stg + stage_off(a.c, G, pw, cg, rr), v, a.c.Cs - cg * 8);
     pw += kConvProdThreads;   // the next item's position by additions
     while (pw >= G.npix) {
       pw -= G.npix;
@@ -679,6 +703,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
     // ---------------- producers: stage the reachable source rows, build A blocks
     const int ptid = tid - kConvEpiWarps * 32;
     const int row = ptid & (BM - 1), half = ptid >> 7;   // GEMM row; chunks 4*half .. 4*half+3
+    const int smask = stage_smask(c);   // staging chunk swizzle
     uint32_t g = 0;
     const int stg_elems = a.stg_rows * c.Ws * c.Csp;
     StageAhead sa;
@@ -737,8 +762,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
           uint4 v = make_uint4(0u, 0u, 0u, 0u);
           if (mv && (e & 1u)) {
             const int sh = bh + sg_tap * (int)((e >> 1) & 0xFFu), sw = bw + sg_tap * (int)((e >> 9) & 0xFFu);
-            if (sh >= T.sh0 && sh < T.sh0 + T.nsh && sh < c.Hs && sw >= 0 && sw < c.Ws)
-              v = *reinterpret_cast<const uint4*>(srow + ((sh - T.sh0) * c.Ws + sw) * c.Csp + (e >> 17));
+            if (sh >= T.sh0 && sh < T.sh0 + T.nsh && sh < c.Hs && sw >= 0 && sw < c.Ws) {
+              const int pix = (sh - T.sh0) * c.Ws + sw;
+              v = *reinterpret_cast<const uint4*>(srow + pix * c.Csp + (((e >> 20) ^ (pix & smask)) << 3));
+            }
           }
           *reinterpret_cast<uint4*>(At + row * kRowBytes + ((j ^ (row & 7)) << 4)) = v;
         }
