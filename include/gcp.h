@@ -206,6 +206,28 @@ GCP_API gcp_status gcp_grad_batch(gcp_ctx* ctx, void* duals, int32_t prec, doubl
 GCP_API gcp_status gcp_optimize_batch(gcp_ctx* ctx, void* duals, const gcp_opt_params* p,
                                       double* out_bound, double* out_certified, double* out_err_vs_fp64);
 
+/* Root intermediate bounds l, u of every hidden pre-activation (the sound
+ * bounds Sec. 2 assumes, used by gcp_init_net), computed by this library's own
+ * bound propagation, layer by layer. Hidden layer 1: the interval image of the
+ * box under W^(1) x + b^(1), every product and sum rounded outwards on the host.
+ * Hidden layer i > 1: the network truncated after the linear map of layer i,
+ * with the spec rows +e_j and -e_j over its pre-activations, is bounded with
+ * the already computed bounds of the layers below (at most 512 neurons per
+ * batch): l_j = g(+e_j), u_j = -g(-e_j), each the FP64 outward-rounded
+ * certified value, so the bounds are sound in any chain precision.
+ * p == NULL: one evaluation at the default slopes (CROWN bounds). Otherwise
+ * p->iters ascent steps on the slopes of every such row in the chain p->prec
+ * (GCP_FP32 or GCP_BF16) with p's optimiser and rates (alpha-CROWN bounds);
+ * p->certify is ignored (always on). layers / x_lo / x_hi as gcp_init_net
+ * (n_layers >= 2; the last layer is not bounded). inter_lo / inter_hi: host,
+ * caller-owned, sum of d_1 .. d_{L-1} doubles each (hidden layers in order);
+ * untouched on error. Errors: GCP_EINVAL (shapes, null arguments, non-finite
+ * bounds), and those of gcp_init_net / gcp_bound_batch / gcp_optimize_batch.
+ * Temporary networks and duals are freed before returning. */
+GCP_API gcp_status gcp_intermediate_bounds(gcp_ctx* ctx, const gcp_layer_desc* layers, int32_t n_layers,
+                                           const double* x_lo, const double* x_hi, const gcp_opt_params* p,
+                                           double* inter_lo, double* inter_hi);
+
 /* Device-pointer entry points behind the PyTorch autograd wrapper.
  * alpha/beta/gamma are float32 device arrays in the export layouts; they
  * replace the duals object's values (copied in). gcp_bound_device writes the

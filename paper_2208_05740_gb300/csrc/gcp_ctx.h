@@ -153,6 +153,11 @@ struct AllocPool {
 };
 
 // shared by api.cu and serve.cu
+gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const double* x_lo, const double* x_hi,
+                    const double* spec_c, int n_spec, const double* inter_lo, const double* inter_hi, int* out_id);
+gcp_status bound_batch(Ctx& c, Batch& b, int prec, int certify, double* out_bound, double* out_cert);
+gcp_status optimize_batch(Ctx& c, Batch& b, const gcp_opt_params* p, double* out_bound, double* out_cert,
+                          double* out_err);
 gcp_status duals_create(Ctx& c, int net_id, int cutset_id, const gcp_subdomains* sub, int dual_prec, Batch** out);
 gcp_status duals_create_parts(Ctx& c, int net_id,
                               const std::vector<std::pair<const CutSet*, const gcp_subdomains*>>& parts,

@@ -24,6 +24,7 @@ GCP_FP64, GCP_FP32, GCP_BF16 = 0, 1, 2
 GCP_PGA, GCP_ADAM = 0, 1
 
 EXPORTED = ["gcp_create", "gcp_destroy", "gcp_last_error", "gcp_set_stream", "gcp_mem_used", "gcp_init_net",
+            "gcp_intermediate_bounds",
             "gcp_add_cuts", "gcp_duals_create", "gcp_duals_create_multi", "gcp_duals_shape", "gcp_duals_export", "gcp_duals_import",
             "gcp_duals_free", "gcp_bound_batch", "gcp_grad_batch", "gcp_optimize_batch", "gcp_bound_device",
             "gcp_grad_device", "gcp_bound_dense_noalloc", "gcp_selftest_gemm", "gcp_selftest_gemm_f64", "gcp_profile_start", "gcp_profile_stop", "gcp_profile_query", "gcp_profile_report",
@@ -94,6 +95,7 @@ def lib():
             "gcp_bound_batch": [P, P, I32, I32, pd, pd],
             "gcp_grad_batch": [P, P, I32, pd, pd, pd, pd],
             "gcp_optimize_batch": [P, P, C.POINTER(OptParams), pd, pd, pd],
+            "gcp_intermediate_bounds": [P, C.POINTER(LayerDesc), I32, pd, pd, C.POINTER(OptParams), pd, pd],
             "gcp_bound_device": [P, P, I32, P, P, P, P, P],
             "gcp_grad_device": [P, P, I32, P, P, P, P, P, P, P, P],
             "gcp_bound_dense_noalloc": [I32, C.POINTER(I32), C.POINTER(P), C.POINTER(P), C.POINTER(P),
@@ -189,9 +191,8 @@ class Context:
         return v.value
 
     # ------------------------------------------------------------ inputs
-    def init_net(self, layers, x_lo, x_hi, spec_c, inter_lo, inter_hi) -> int:
-        """layers: objects with kind, W, b, in_shape, out_shape, stride, pad."""
-        keep = []
+    @staticmethod
+    def _layer_descs(layers, keep):
         descs = (LayerDesc * len(layers))()
         for i, ly in enumerate(layers):
             W = _c(ly.W, np.float64)
@@ -207,6 +208,12 @@ class Context:
                 d.k, d.stride, d.pad = W.shape[2], ly.stride, ly.pad
             d.W = _ptr(W, C.c_double)
             d.b = _ptr(b, C.c_double)
+        return descs
+
+    def init_net(self, layers, x_lo, x_hi, spec_c, inter_lo, inter_hi) -> int:
+        """layers: objects with kind, W, b, in_shape, out_shape, stride, pad."""
+        keep = []
+        descs = self._layer_descs(layers, keep)
         xl, xh, sc = _c(x_lo, np.float64), _c(x_hi, np.float64), _c(spec_c, np.float64)
         lo = _c(np.concatenate([np.asarray(a, np.float64) for a in inter_lo]) if len(inter_lo) else np.zeros(0), np.float64)
         hi = _c(np.concatenate([np.asarray(a, np.float64) for a in inter_hi]) if len(inter_hi) else np.zeros(0), np.float64)
@@ -215,6 +222,26 @@ class Context:
                                        _ptr(sc, C.c_double), sc.shape[0], _ptr(lo, C.c_double), _ptr(hi, C.c_double),
                                        C.byref(nid)))
         return nid.value
+
+    def intermediate_bounds(self, layers, x_lo, x_hi, params: Optional[OptParams] = None):
+        """Root bounds (lo, hi) of every hidden layer (list of arrays), by the
+        library's own certified bound propagation: CROWN at the default
+        slopes (params None) or alpha-CROWN with params.iters ascent steps."""
+        keep = []
+        descs = self._layer_descs(layers, keep)
+        xl, xh = _c(x_lo, np.float64), _c(x_hi, np.float64)
+        dims = [int(np.prod(ly.out_shape)) for ly in layers[:-1]]
+        lo, hi = np.zeros(sum(dims)), np.zeros(sum(dims))
+        pp = C.byref(params) if params is not None else None
+        self._check(lib().gcp_intermediate_bounds(self.h, descs, len(layers), _ptr(xl, C.c_double),
+                                                  _ptr(xh, C.c_double), pp, _ptr(lo, C.c_double),
+                                                  _ptr(hi, C.c_double)))
+        out_lo, out_hi, o = [], [], 0
+        for d in dims:
+            out_lo.append(lo[o:o + d].copy())
+            out_hi.append(hi[o:o + d].copy())
+            o += d
+        return out_lo, out_hi
 
     def add_cuts(self, net_id: int, ptr, layer, kind, index, coef, d, cutset_id: int = -1):
         ptr = _c(ptr, np.int64)
