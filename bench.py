@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--iters", type=int, default=None, help="ascent iterations (workload default)")
     ap.add_argument("--n-sub", type=int, default=None, help="subdomains per GPU (workload default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-inter-bounds", action="store_true",
+                    help="skip the GPU intermediate-bounds measurement (CROWN / alpha-CROWN root bounds)")
     ap.add_argument("--profile-all", action="store_true", help="print every kernel's share (untimed step)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving stream (0: skip)")
     ap.add_argument("--no-bf16-form", action="store_true", help="skip the BF16-chain form of the workload")
@@ -315,6 +317,41 @@ def serving_bench(dev, n_requests, rate=200.0, rounds=10, iters=20, max_inflight
     }
 
 
+def inter_bounds_bench(ctx, inst, params, cert_ibp):
+    """Root intermediate bounds by the library's own certified propagation:
+    wall time of CROWN (default slopes) and alpha-CROWN (20 Adam steps per
+    neuron row) bounds for the workload's network, the fraction of unstable
+    hidden neurons under each, and the workload's certified bounds (same
+    subdomains, cuts and schedule) with the CROWN root bounds in place of the
+    interval bounds the synthetic instance carries."""
+    import numpy as np
+    import torch
+    from paper_2208_05740_gb300 import gcp, synth
+
+    def unstable(lo, hi):
+        n = sum(len(x) for x in lo)
+        return float(sum(int(np.sum((l < 0) & (h > 0))) for l, h in zip(lo, hi)) / n)
+
+    out = {"note": "wall time on the host clock around the whole layer-by-layer procedure (one GPU)"}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lo, hi = ctx.intermediate_bounds(inst.net.layers, inst.x_lo, inst.x_hi)
+    out["crown_s"] = time.perf_counter() - t0
+    pa = gcp.opt_params(20, gcp.GCP_ADAM, gcp.GCP_FP32, 1, 0.1, 0.02, 0.02, 0.98)
+    t0 = time.perf_counter()
+    alo, ahi = ctx.intermediate_bounds(inst.net.layers, inst.x_lo, inst.x_hi, pa)
+    out["alpha_crown_20it_s"] = time.perf_counter() - t0
+    out["unstable_fraction"] = {"interval": unstable(inst.inter_lo, inst.inter_hi), "crown": unstable(lo, hi),
+                                "alpha_crown": unstable(alo, ahi)}
+    tr = synth.Instance(inst.name, inst.net, inst.x_lo, inst.x_hi, inst.spec, lo, hi, inst.sub, inst.cuts)
+    net_id, cs = ctx.load_instance(tr)
+    D = ctx.duals_create(net_id, cs, tr.sub, gcp.GCP_FP32)
+    _, cert, _ = ctx.optimize_batch(D, params)
+    ctx.duals_free(D)
+    out["mean_certified"] = {"interval_root_bounds": float(np.mean(cert_ibp)), "crown_root_bounds": float(np.mean(cert))}
+    return out
+
+
 # --------------------------------------------------------------------------- GPU arm
 def main():
     a = parse()
@@ -477,6 +514,8 @@ def main():
                     "ms_per_step": float(np.mean(tb)), "max_err_vs_fp64": float(np.max(err_b)),
                     "rows_certified_at_least_as_high": float(np.mean(cert_b >= cert - 1e-6 * np.maximum(1, np.abs(cert))))},
         }
+    if world == 1 and not a.no_inter_bounds:
+        line["intermediate_bounds"] = inter_bounds_bench(ctx, inst, params, cert)
     if a.serve_requests > 0 and world == 1:
         line["serving"] = serving_bench(dev, a.serve_requests)
     if world == 1 and not a.no_cpu_baseline:

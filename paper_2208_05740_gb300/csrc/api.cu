@@ -441,6 +441,7 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
   for (int k = 0; k < n_spec; ++k) {
     for (int q = 0; q < dL; ++q) {
       const double cv = spec_c[(size_t)k * dL + q];
+      if (cv == 0.0) continue;   // sparse specs (unit rows) skip the zero columns
       cb[k] += cv * last.b[q];
       for (int j = 0; j < dl1; ++j) yl[(size_t)k * dl1 + j] -= cv * last.W[(size_t)q * dl1 + j];
     }
