@@ -228,6 +228,39 @@ GCP_API gcp_status gcp_intermediate_bounds(gcp_ctx* ctx, const gcp_layer_desc* l
                                            const double* x_lo, const double* x_hi, const gcp_opt_params* p,
                                            double* inter_lo, double* inter_hi);
 
+/* Branch and bound over ReLU splits (Sec. 3.2, App. B) with this library's
+ * bounding: proves that every spec row of the network is positive over the
+ * input box. Starting from the root (no splits), each round bounds up to
+ * `batch` pending subdomains in one batch (p->iters ascent steps, then the FP64
+ * certification; p->certify is forced on); when more are pending, the easiest
+ * ones (largest lower bound) go first, the order of Sec. 3.2. A subdomain whose
+ * certified bounds are all positive is verified; any other is split on its not
+ * yet split root-unstable neuron with the largest relaxation intercept
+ * -l u / (u - l) into the x >= 0 and x <= 0 children, which start from the
+ * parent's duals. Cuts (cutset_id >= 0) hold in every subdomain (they are valid
+ * at the root). Stops when nothing is pending (verified = 1), after
+ * max_rounds rounds, when more than max_domains subdomains are pending, after
+ * timeout_s seconds, or when a subdomain with every root-unstable neuron split
+ * still has a non-positive bound (verified = 0 in all these cases: not proven).
+ * min_bound: the smallest certified bound over the bounded leaves and the
+ * pending subdomains' priorities. The result is written only on GCP_OK. */
+typedef struct {
+  int32_t batch;         /* subdomains bounded per round, at most */
+  int32_t max_rounds;
+  int64_t max_domains;
+  double timeout_s;      /* <= 0: none */
+  gcp_opt_params p;
+} gcp_bab_params;
+typedef struct {
+  int32_t verified;
+  int32_t rounds;
+  int64_t domains_bounded, domains_verified, domains_left;
+  double min_bound;
+  double time_ms;
+} gcp_bab_result;
+GCP_API gcp_status gcp_bab_verify(gcp_ctx* ctx, int32_t net_id, int32_t cutset_id, const gcp_bab_params* bp,
+                                  gcp_bab_result* res);
+
 /* Device-pointer entry points behind the PyTorch autograd wrapper.
  * alpha/beta/gamma are float32 device arrays in the export layouts; they
  * replace the duals object's values (copied in). gcp_bound_device writes the

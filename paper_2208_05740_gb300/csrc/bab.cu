@@ -1,0 +1,200 @@
+// Branch and bound over ReLU splits with the library's bounding (Sec. 3.2).
+//
+// A property (every spec row c_k of the network positive over the input box)
+// is verified by splitting the input region's ReLU phases: a subdomain whose
+// certified bounds are all positive is done; any other is split on one more
+// unstable neuron into its x >= 0 and x <= 0 children (App. B), which start
+// from the parent's duals. Each round bounds up to `batch` pending subdomains
+// in one batch (ascent steps, then the FP64 certification); when more are
+// pending, the easiest ones, with the largest lower bounds, go first (the
+// order the paper uses so that cuts arriving later meet the hard domains).
+// The branching neuron of a subdomain is its not yet split root-unstable
+// neuron with the largest relaxation intercept -l u / (u - l).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "gcp_ctx.h"
+
+namespace gcp {
+namespace {
+
+struct Domain {
+  std::vector<int16_t> lay;
+  std::vector<int32_t> idx;
+  std::vector<int8_t> sgn;
+  double margin = -INFINITY;    // priority: the parent's smallest certified bound
+  std::vector<float> alpha;     // [K, na] parent's duals (empty: defaults)
+  std::vector<float> beta;      // [K, splits of the parent]
+  std::vector<float> gamma;     // [K, N]
+};
+
+}  // namespace
+
+gcp_status duals_export(Ctx& c, Batch& b, double* alpha, double* beta, double* gamma);
+gcp_status duals_import(Ctx& c, Batch& b, const double* alpha, const double* beta, const double* gamma);
+
+gcp_status bab_verify(Ctx& c, int net_id, int cutset_id, const gcp_bab_params& bp, gcp_bab_result& res) {
+  const auto t0 = std::chrono::steady_clock::now();
+  auto it = c.nets.find(net_id);
+  if (it == c.nets.end()) return c.fail(GCP_ENOTFOUND, "unknown network %d", net_id);
+  if (bp.batch < 1 || bp.max_rounds < 1 || bp.max_domains < 1 || bp.p.iters < 0)
+    return c.fail(GCP_EINVAL, "gcp_bab_verify: batch, max_rounds, max_domains >= 1 and iters >= 0");
+  const Net& net = *it->second;
+  const int K = net.K;
+  int64_t na = 0;
+  for (int i = 1; i < net.L; ++i) na += net.dims[i];
+  // root-unstable neurons by decreasing intercept -l u / (u - l)
+  struct Cand {
+    double score;
+    int16_t layer;
+    int32_t index;
+  };
+  std::vector<Cand> cand;
+  {
+    std::vector<double> lo, hi;
+    for (int i = 1; i < net.L; ++i) {
+      const int di = net.dims[i];
+      lo.resize(di);
+      hi.resize(di);
+      cudaMemcpy(lo.data(), net.lo64[i - 1], di * 8, cudaMemcpyDeviceToHost);
+      cudaMemcpy(hi.data(), net.hi64[i - 1], di * 8, cudaMemcpyDeviceToHost);
+      for (int j = 0; j < di; ++j)
+        if (lo[j] < 0 && hi[j] > 0) cand.push_back({-lo[j] * hi[j] / (hi[j] - lo[j]), (int16_t)i, j});
+    }
+    std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) { return a.score > b.score; });
+  }
+  gcp_opt_params p = bp.p;
+  p.certify = 1;
+  std::vector<Domain> pending(1);
+  res = gcp_bab_result{};
+  res.min_bound = INFINITY;
+  bool undecided = false;   // a subdomain with every candidate split and a non-positive bound
+  while (!pending.empty()) {
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (res.rounds >= bp.max_rounds || (int64_t)pending.size() > bp.max_domains ||
+        (bp.timeout_s > 0 && el > bp.timeout_s))
+      break;
+    // the easiest domains first
+    const size_t n = std::min<size_t>(pending.size(), (size_t)bp.batch);
+    std::stable_sort(pending.begin(), pending.end(),
+                     [](const Domain& a, const Domain& b) { return a.margin > b.margin; });
+    std::vector<Domain> cur(std::make_move_iterator(pending.begin()), std::make_move_iterator(pending.begin() + n));
+    pending.erase(pending.begin(), pending.begin() + n);
+    std::vector<int32_t> ptr{0};
+    std::vector<int16_t> lay;
+    std::vector<int32_t> idx;
+    std::vector<int8_t> sgn;
+    for (const Domain& d : cur) {
+      lay.insert(lay.end(), d.lay.begin(), d.lay.end());
+      idx.insert(idx.end(), d.idx.begin(), d.idx.end());
+      sgn.insert(sgn.end(), d.sgn.begin(), d.sgn.end());
+      ptr.push_back((int32_t)lay.size());
+    }
+    lay.push_back(0);   // keep the arrays non-empty
+    idx.push_back(0);
+    sgn.push_back(0);
+    const gcp_subdomains sub{(int32_t)n, ptr.data(), lay.data(), idx.data(), sgn.data()};
+    Batch* b = nullptr;
+    gcp_status s = duals_create(c, net_id, cutset_id, &sub, GCP_FP32, &b);
+    if (s) return s;
+    const int64_t R = b->R;
+    const int M = b->M, N = b->N;
+    std::vector<double> A((size_t)R * na), Bt((size_t)R * std::max(M, 1)), G((size_t)R * std::max(N, 1));
+    // warm start: the parents' duals (new split slots and defaults elsewhere)
+    bool warm = false;
+    for (const Domain& d : cur) warm |= !d.alpha.empty();
+    if (warm) {
+      s = duals_export(c, *b, A.data(), Bt.data(), G.data());
+      for (size_t q = 0; q < n && s == GCP_OK; ++q) {
+        const Domain& d = cur[q];
+        if (d.alpha.empty()) continue;
+        const int np = (int)d.beta.size() / K;
+        for (int k = 0; k < K; ++k) {
+          const int64_t r = (int64_t)q * K + k;
+          for (int64_t j = 0; j < na; ++j) A[r * na + j] = d.alpha[(size_t)k * na + j];
+          for (int m = 0; m < np && m < M; ++m) Bt[r * M + m] = d.beta[(size_t)k * np + m];
+          for (int m = np; m < M; ++m) Bt[r * M + m] = 0.0;
+          for (int e = 0; e < N; ++e) G[r * N + e] = d.gamma[(size_t)k * N + e];
+        }
+      }
+      if (s == GCP_OK) s = duals_import(c, *b, A.data(), M > 0 ? Bt.data() : nullptr, N > 0 ? G.data() : nullptr);
+    }
+    std::vector<double> cert((size_t)R);
+    if (s == GCP_OK) s = optimize_batch(c, *b, &p, nullptr, cert.data(), nullptr);
+    if (s == GCP_OK) s = duals_export(c, *b, A.data(), Bt.data(), G.data());
+    cudaStreamSynchronize(c.stream);
+    c.batches.erase(b);
+    if (s) return s;
+    res.rounds += 1;
+    res.domains_bounded += (int64_t)n;
+    for (size_t q = 0; q < n; ++q) {
+      Domain& d = cur[q];
+      double m = INFINITY;
+      for (int k = 0; k < K; ++k) m = std::min(m, cert[q * K + k]);
+      if (m > 0) {   // a verified leaf
+        res.domains_verified += 1;
+        res.min_bound = std::min(res.min_bound, m);
+        continue;
+      }
+      // branch: the first candidate not split in this domain
+      const Cand* pick = nullptr;
+      for (const Cand& cd : cand) {
+        bool dup = false;
+        for (size_t e = 0; e < d.lay.size() && !dup; ++e) dup = d.lay[e] == cd.layer && d.idx[e] == cd.index;
+        if (!dup) {
+          pick = &cd;
+          break;
+        }
+      }
+      if (!pick) {   // every root-unstable neuron is split: nothing left to refine
+        undecided = true;
+        res.min_bound = std::min(res.min_bound, m);
+        continue;
+      }
+      const int np = (int)d.lay.size();
+      std::vector<float> al((size_t)K * na), be((size_t)K * np), ga((size_t)K * N);
+      for (int k = 0; k < K; ++k) {
+        const int64_t r = (int64_t)q * K + k;
+        for (int64_t j = 0; j < na; ++j) al[(size_t)k * na + j] = (float)A[r * na + j];
+        for (int e = 0; e < np; ++e) be[(size_t)k * np + e] = (float)Bt[r * M + e];
+        for (int e = 0; e < N; ++e) ga[(size_t)k * N + e] = (float)G[r * N + e];
+      }
+      for (int side = 0; side < 2; ++side) {
+        Domain ch;
+        ch.lay = d.lay;
+        ch.idx = d.idx;
+        ch.sgn = d.sgn;
+        ch.lay.push_back(pick->layer);
+        ch.idx.push_back(pick->index);
+        ch.sgn.push_back(side == 0 ? 1 : -1);
+        ch.margin = m;
+        ch.alpha = al;
+        ch.beta = be;
+        ch.gamma = ga;
+        pending.push_back(std::move(ch));
+      }
+    }
+    if (undecided) break;
+  }
+  for (const Domain& d : pending) res.min_bound = std::min(res.min_bound, d.margin);
+  res.domains_left = (int64_t)pending.size();
+  res.verified = (!undecided && pending.empty()) ? 1 : 0;
+  res.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return GCP_OK;
+}
+
+}  // namespace gcp
+
+extern "C" gcp_status gcp_bab_verify(gcp_ctx* h, int32_t net_id, int32_t cutset_id, const gcp_bab_params* bp,
+                                     gcp_bab_result* res) {
+  gcp::Ctx* c = reinterpret_cast<gcp::Ctx*>(h);
+  if (!c || !bp || !res) return GCP_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  gcp_bab_result r{};
+  const gcp_status s = gcp::bab_verify(*c, net_id, cutset_id, *bp, r);
+  if (s == GCP_OK) *res = r;
+  return s;
+}

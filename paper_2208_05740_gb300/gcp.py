@@ -24,7 +24,7 @@ GCP_FP64, GCP_FP32, GCP_BF16 = 0, 1, 2
 GCP_PGA, GCP_ADAM = 0, 1
 
 EXPORTED = ["gcp_create", "gcp_destroy", "gcp_last_error", "gcp_set_stream", "gcp_mem_used", "gcp_init_net",
-            "gcp_intermediate_bounds",
+            "gcp_intermediate_bounds", "gcp_bab_verify",
             "gcp_add_cuts", "gcp_duals_create", "gcp_duals_create_multi", "gcp_duals_shape", "gcp_duals_export", "gcp_duals_import",
             "gcp_duals_free", "gcp_bound_batch", "gcp_grad_batch", "gcp_optimize_batch", "gcp_bound_device",
             "gcp_grad_device", "gcp_bound_dense_noalloc", "gcp_selftest_gemm", "gcp_selftest_gemm_f64", "gcp_profile_start", "gcp_profile_stop", "gcp_profile_query", "gcp_profile_report",
@@ -54,6 +54,17 @@ class OptParams(C.Structure):
     _fields_ = [("iters", C.c_int32), ("optimizer", C.c_int32), ("prec", C.c_int32), ("certify", C.c_int32),
                 ("lr_alpha", C.c_double), ("lr_beta", C.c_double), ("lr_gamma", C.c_double),
                 ("lr_decay", C.c_double)]
+
+
+class BabParams(C.Structure):
+    _fields_ = [("batch", C.c_int32), ("max_rounds", C.c_int32), ("max_domains", C.c_int64),
+                ("timeout_s", C.c_double), ("p", OptParams)]
+
+
+class BabResult(C.Structure):
+    _fields_ = [("verified", C.c_int32), ("rounds", C.c_int32), ("domains_bounded", C.c_int64),
+                ("domains_verified", C.c_int64), ("domains_left", C.c_int64), ("min_bound", C.c_double),
+                ("time_ms", C.c_double)]
 
 
 class Request(C.Structure):
@@ -96,6 +107,7 @@ def lib():
             "gcp_grad_batch": [P, P, I32, pd, pd, pd, pd],
             "gcp_optimize_batch": [P, P, C.POINTER(OptParams), pd, pd, pd],
             "gcp_intermediate_bounds": [P, C.POINTER(LayerDesc), I32, pd, pd, C.POINTER(OptParams), pd, pd],
+            "gcp_bab_verify": [P, I32, I32, C.POINTER(BabParams), C.POINTER(BabResult)],
             "gcp_bound_device": [P, P, I32, P, P, P, P, P],
             "gcp_grad_device": [P, P, I32, P, P, P, P, P, P, P, P],
             "gcp_bound_dense_noalloc": [I32, C.POINTER(I32), C.POINTER(P), C.POINTER(P), C.POINTER(P),
@@ -242,6 +254,14 @@ class Context:
             out_hi.append(hi[o:o + d].copy())
             o += d
         return out_lo, out_hi
+
+    def bab_verify(self, net_id: int, cutset_id: int, params: OptParams, batch: int = 256, max_rounds: int = 100,
+                   max_domains: int = 1 << 16, timeout_s: float = 0.0) -> dict:
+        """Branch and bound over ReLU splits: is every spec row positive over the box?"""
+        bp = BabParams(batch, max_rounds, max_domains, timeout_s, params)
+        r = BabResult()
+        self._check(lib().gcp_bab_verify(self.h, net_id, cutset_id, C.byref(bp), C.byref(r)))
+        return {f: getattr(r, f) for f, _ in BabResult._fields_}
 
     def add_cuts(self, net_id: int, ptr, layer, kind, index, coef, d, cutset_id: int = -1):
         ptr = _c(ptr, np.int64)
