@@ -349,6 +349,17 @@ def inter_bounds_bench(ctx, inst, params, cert_ibp):
     _, cert, _ = ctx.optimize_batch(D, params)
     ctx.duals_free(D)
     out["mean_certified"] = {"interval_root_bounds": float(np.mean(cert_ibp)), "crown_root_bounds": float(np.mean(cert))}
+    # branch and bound from the root on these bounds: a few rounds of full batches
+    pb = gcp.opt_params(20, gcp.GCP_ADAM, gcp.GCP_FP32, 1, 0.1, 0.02, 0.02, 0.98)
+    # children keep their parents' duals on the host: smaller batches for wide networks
+    na = sum(inst.net.dims[1:-1]) * inst.spec.shape[0]
+    batch = 1024 if na <= 50_000 else 64
+    torch.cuda.synchronize()
+    r = ctx.bab_verify(net_id, cs, pb, batch=batch, max_rounds=12)
+    out["bab"] = {"batch": batch, "iters_per_round": 20, "rounds": r["rounds"], "domains_bounded": r["domains_bounded"],
+                  "domains_verified": r["domains_verified"], "domains_left": r["domains_left"],
+                  "verified": r["verified"], "min_bound": r["min_bound"], "time_s": r["time_ms"] / 1e3,
+                  "domains_per_s": r["domains_bounded"] / max(r["time_ms"] / 1e3, 1e-9)}
     return out
 
 
