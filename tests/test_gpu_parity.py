@@ -418,3 +418,23 @@ def test_certify_by_slices_matches_simt_float64(ctx):
         assert_rel(cert, O.evaluate(P, oracle_duals(inst, Ae, Be, Ge)), 1e-9, f"certified (GCP_TC={tc})")
         ctx.duals_free(D)
     assert_rel(certs[0], certs[1], 1e-11, "slices vs SIMT float64")
+
+
+def test_degenerate_box_gives_the_exact_output(ctx):
+    """A zero-width input box (x_lo = x_hi = x0): the interval bounds are exact,
+    no neuron is unstable, and the certified bound of every spec row equals
+    c^T f(x0) (within the FP64 certification's rounding), in every chain."""
+    inst = synth.mlp_256x6(n_sub=3, n_cuts=0)
+    x0 = (inst.x_lo + inst.x_hi) / 2
+    lo, hi = synth.interval_bounds(inst.net, x0, x0)
+    sub = synth.Subdomains(np.arange(4, dtype=np.int32) * 0, np.zeros(0, np.int16), np.zeros(0, np.int32),
+                           np.zeros(0, np.int8))
+    net_id = ctx.init_net(inst.net.layers, x0, x0, inst.spec, lo, hi)
+    exact = inst.spec @ synth.forward_all(inst.net, x0[None, :])[-1][0]
+    for prec in (gcp.GCP_FP32, gcp.GCP_BF16):
+        D = ctx.duals_create(net_id, -1, sub, gcp.GCP_FP32)
+        g, cert = ctx.bound_batch(D, prec, certify=True)
+        assert_rel(cert, np.tile(exact, 3), 1e-9, "certified at a point")
+        ex = np.tile(exact, 3)
+        assert np.all(cert <= ex + 1e-12 * np.maximum(1, np.abs(ex)))   # sound: never above
+        ctx.duals_free(D)
