@@ -704,6 +704,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
     const int ptid = tid - kConvEpiWarps * 32;
     const int row = ptid & (BM - 1), half = ptid >> 7;   // GEMM row; chunks 4*half .. 4*half+3
     const int smask = stage_smask(c);   // staging chunk swizzle
+    const bool csp32 = (c.Csp & 31) == 0;    // a thread's four chunks of a block share one tap
     uint32_t g = 0;
     const int stg_elems = a.stg_rows * c.Ws * c.Csp;
     StageAhead sa;
@@ -755,19 +756,43 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
           break;
         }
         uint8_t* At = As + sg * kTileA;
+        if (csp32) {
+          // four chunks of one tap (the tap's channels are a multiple of 32):
+          // one table entry, one bounds check, one staged pixel
+          const uint32_t e = tab[(f.kb0 + kb) * 8 + half * 4];
+          uint4 v[4];
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int j = half * 4 + jj;
-          const uint32_t e = tab[(f.kb0 + kb) * 8 + j];
-          uint4 v = make_uint4(0u, 0u, 0u, 0u);
+          for (int jj = 0; jj < 4; ++jj) v[jj] = make_uint4(0u, 0u, 0u, 0u);
           if (mv && (e & 1u)) {
             const int sh = bh + sg_tap * (int)((e >> 1) & 0xFFu), sw = bw + sg_tap * (int)((e >> 9) & 0xFFu);
             if (sh >= T.sh0 && sh < T.sh0 + T.nsh && sh < c.Hs && sw >= 0 && sw < c.Ws) {
               const int pix = (sh - T.sh0) * c.Ws + sw;
-              v = *reinterpret_cast<const uint4*>(srow + pix * c.Csp + (((e >> 20) ^ (pix & smask)) << 3));
+              const __nv_bfloat16* sp = srow + pix * c.Csp;
+              const int q0 = (int)(e >> 20), xm = pix & smask;
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) v[jj] = *reinterpret_cast<const uint4*>(sp + (((q0 + jj) ^ xm) << 3));
             }
           }
-          *reinterpret_cast<uint4*>(At + row * kRowBytes + ((j ^ (row & 7)) << 4)) = v;
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int j = half * 4 + jj;
+            *reinterpret_cast<uint4*>(At + row * kRowBytes + ((j ^ (row & 7)) << 4)) = v[jj];
+          }
+        } else {
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int j = half * 4 + jj;
+            const uint32_t e = tab[(f.kb0 + kb) * 8 + j];
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (mv && (e & 1u)) {
+              const int sh = bh + sg_tap * (int)((e >> 1) & 0xFFu), sw = bw + sg_tap * (int)((e >> 9) & 0xFFu);
+              if (sh >= T.sh0 && sh < T.sh0 + T.nsh && sh < c.Hs && sw >= 0 && sw < c.Ws) {
+                const int pix = (sh - T.sh0) * c.Ws + sw;
+                v = *reinterpret_cast<const uint4*>(srow + pix * c.Csp + (((e >> 20) ^ (pix & smask)) << 3));
+              }
+            }
+            *reinterpret_cast<uint4*>(At + row * kRowBytes + ((j ^ (row & 7)) << 4)) = v;
+          }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&a_full[sg]);
