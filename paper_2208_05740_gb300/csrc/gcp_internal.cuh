@@ -295,17 +295,41 @@ bool gemm_f64_slices(cudaStream_t st, int64_t M, int N, int K, const double* A, 
 // k-blocks kb0 .. kb0 + nkb - 1 of the packed weight: k = (kb0 * 64) +
 // (a * nkw + b) * Csp + c, c the source channel (Csp = channels padded to 8).
 constexpr int kMaxConvPhases = 16;
+// Division by an invariant divisor d >= 1 for 0 <= n < 2^31: q = (t + n) >> s
+// with t = high word of n * m, s = ceil(log2 d), m = floor(2^32 (2^s - d) / d)
+// + 1 -- the round-up multiplier method of Granlund and Montgomery (1994)
+// with its 33-bit multiplier 2^32 + m; t + n stays below 2^32 for n < 2^31.
+struct FastDiv {
+  uint32_t m = 1;
+  int s = 0;
+  FastDiv() = default;
+  __host__ explicit FastDiv(uint32_t d) {
+    while ((1ull << s) < d) ++s;
+    m = static_cast<uint32_t>(((1ull << 32) * ((1ull << s) - d)) / d + 1);
+  }
+  __host__ __device__ int div(int n) const {
+#ifdef __CUDA_ARCH__
+    const uint32_t t = __umulhi(static_cast<uint32_t>(n), m);
+#else
+    const uint32_t t = static_cast<uint32_t>((static_cast<uint64_t>(static_cast<uint32_t>(n)) * m) >> 32);
+#endif
+    return static_cast<int>((t + static_cast<uint32_t>(n)) >> s);
+  }
+};
+
 struct ConvPhase {
   int ph, pw, Hf, Wf;        // the phase's output pixels form an Hf x Wf grid
   int rh, rw, nkh, nkw;      // its taps
   int kb0, nkb;              // its weight k-blocks
   int tile0, ntiles;         // its 128-row GEMM tiles (set for a given batch by the launcher)
+  FastDiv dPf, dWf;          // division by Hf * Wf and by Wf (set by the launcher)
 };
 struct ConvPlan {
   int dir, Cs, Hs, Ws, Csp;  // source map
   int Co, Ho, Wo;            // output map
   int k, stride, pad;
   int nph, Kp, Np;           // phases, packed weight [Np, Kp]
+  FastDiv dS;                // division by the stride (set by the launcher)
   ConvPhase f[kMaxConvPhases];
 };
 __host__ __device__ inline bool conv_plan(const LayerGeom& g, int dir, ConvPlan& c) {

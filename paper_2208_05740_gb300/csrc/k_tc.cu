@@ -496,12 +496,12 @@ __host__ __device__ inline ConvTile conv_tile(const ConvPlan& c, int R, int t) {
   T.f = q;
   T.m0 = (t - f.tile0) * 128;
   T.mend = T.m0 + 128 < R * Pf ? T.m0 + 128 : R * Pf;
-  T.r0 = T.m0 / Pf;
-  T.nrt = (T.mend - 1) / Pf - T.r0 + 1;
+  T.r0 = f.dPf.div(T.m0);
+  T.nrt = f.dPf.div(T.mend - 1) - T.r0 + 1;
   T.sh0 = 0;
   T.nsh = c.Hs;
   if (T.nrt == 1) {
-    const int i_lo = (T.m0 - T.r0 * Pf) / f.Wf, i_hi = (T.mend - 1 - T.r0 * Pf) / f.Wf;
+    const int i_lo = f.dWf.div(T.m0 - T.r0 * Pf), i_hi = f.dWf.div(T.mend - 1 - T.r0 * Pf);
     const int s = c.dir == 0 ? 1 : c.stride;
     const int o_lo = f.ph + s * i_lo, o_hi = f.ph + s * i_hi;   // output rows
     int lo, hi;
@@ -510,8 +510,8 @@ __host__ __device__ inline ConvTile conv_tile(const ConvPlan& c, int R, int t) {
       hi = o_hi * c.stride + c.k - 1 - c.pad;
     } else {
       const int x = o_lo + c.pad - (f.rh + s * (f.nkh - 1));   // a multiple of s when >= 0
-      lo = x > 0 ? x / s : 0;
-      hi = (o_hi + c.pad - f.rh) / s;
+      lo = x > 0 ? c.dS.div(x) : 0;
+      hi = c.dS.div(o_hi + c.pad - f.rh);
     }
     lo = lo < 0 ? 0 : lo;
     hi = hi > c.Hs - 1 ? c.Hs - 1 : hi;
@@ -523,7 +523,10 @@ __host__ __device__ inline ConvTile conv_tile(const ConvPlan& c, int R, int t) {
 // Tile ranges of the phases for a batch of R rows; returns the tile count.
 inline int conv_set_tiles(ConvPlan& c, int R) {
   int n = 0;
+  c.dS = FastDiv(static_cast<uint32_t>(c.stride));
   for (int q = 0; q < c.nph; ++q) {
+    c.f[q].dPf = FastDiv(static_cast<uint32_t>(std::max(1, c.f[q].Hf * c.f[q].Wf)));
+    c.f[q].dWf = FastDiv(static_cast<uint32_t>(std::max(1, c.f[q].Wf)));
     c.f[q].tile0 = n;
     c.f[q].ntiles = (R * c.f[q].Hf * c.f[q].Wf + 127) / 128;
     n += c.f[q].ntiles;
@@ -739,12 +742,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       // pixel for tap (a, b) is (bh + sg_tap * a, bw + sg_tap * b)
       const int m = T.m0 + row;
       const bool mv = m < T.mend;
-      const int r = mv ? m / Pf : 0;
+      const int r = mv ? f.dPf.div(m) : 0;
       const int pos = mv ? m - r * Pf : 0;
-      const int pi = pos / f.Wf;
+      const int pi = f.dWf.div(pos);
       const int oh = f.ph + s_out * pi, ow = f.pw + s_out * (pos - pi * f.Wf), rl = r - T.r0;
-      const int bh = c.dir == 0 ? oh * c.stride - c.pad : (oh + c.pad - f.rh) / c.stride;
-      const int bw = c.dir == 0 ? ow * c.stride - c.pad : (ow + c.pad - f.rw) / c.stride;
+      const int bh = c.dir == 0 ? oh * c.stride - c.pad : c.dS.div(oh + c.pad - f.rh);
+      const int bw = c.dir == 0 ? ow * c.stride - c.pad : c.dS.div(ow + c.pad - f.rw);
       const int sg_tap = c.dir == 0 ? 1 : -1;
       const __nv_bfloat16* srow = sbuf + rl * T.nsh * c.Ws * c.Csp;
       for (int kb = 0; kb < f.nkb; ++kb, ++g) {
@@ -843,9 +846,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int erow = warp * 32 + lane;
       const int em = T.m0 + erow;
-      const int er = em / Pf;
+      const int er = f.dPf.div(em);
       const int epos = em - er * Pf;
-      const int epi = epos / f.Wf;
+      const int epi = f.dWf.div(epos);
       const int eoh = f.ph + s_out * epi, eow = f.pw + s_out * (epos - epi * f.Wf);
       float* dst = a.out + (int64_t)er * out_dim + (eoh * c.Wo + eow);
       const int64_t cstride = (int64_t)c.Ho * c.Wo;
