@@ -17,7 +17,12 @@ It is a plain, slow restatement, in float64 and in the paper's notation, of
     optimisable duals (the paper optimises them by gradient ascent, Sec. 3.1
     after Theorem 3.1; App. C.1 names Adam with 20 iterations);
   * the LP of Eq. 16 and its MIP counterpart (Eq. 2-10 plus cuts), solved by
-    SciPy/HiGHS, used only to pin the bound from outside.
+    SciPy/HiGHS, used only to pin the bound from outside;
+  * residual (skip) connections, x^(k) = W^(k) xhat^(k-1) + b^(k) + xhat^(m)
+    with m < k: the paper states the method for general computational graphs
+    (Sec. 2 defines the feed-forward case for clarity, App. C.2 verifies
+    residual networks); the skip term is one more linear map, the identity,
+    whose multiplier nu^(k) is added to the coefficient of xhat^(m).
 
 Readings of the paper (each is listed with its reason in the design notes):
   R1 concretisation is the minimum of the linear input term over the box,
@@ -43,6 +48,10 @@ Readings of the paper (each is listed with its reason in the design notes):
      clip(p, 0, C) passes d/dp only strictly inside (0, C) and d/dC for
      p >= C; at nuhat = 0 exactly every local derivative is 0.
  R10 default initial duals: alpha = 1 if u >= -l else 0, beta = gamma = 0.
+ R11 a skip connection enters the Lagrangian like the layer's weight matrix:
+     the equality x^(k) - W^(k) xhat^(k-1) - b^(k) - xhat^(m) = 0 with
+     multiplier nu^(k) adds nu^(k) to y^(m), the coefficient of xhat^(m)
+     (xhat^(0) = x, so m = 0 adds it to the input term before concretisation).
 
 Layouts (float64 numpy): rows r = s * K + k for subdomain s and spec row k;
 alpha is a list over hidden layers of [R, d_i]; beta is [R, max_splits]
@@ -124,6 +133,8 @@ class Problem:
     G: list
     Q: list
     d: np.ndarray
+    # per layer (index i-1 for layer i): 0, or s >= 1 when layer i adds xhat^(s-1)
+    skip: List[int] = dataclasses.field(default_factory=list)
 
     @property
     def K(self) -> int:
@@ -148,6 +159,9 @@ def build_problem(inst) -> Problem:
     L = net.L
     dims = [net.layers[0].d_in] + [ly.d_out for ly in net.layers]
     Wm, b = [], []
+    skip = [int(getattr(ly, "skip", 0)) for ly in net.layers]
+    for i, s_ in enumerate(skip):
+        assert 0 <= s_ <= i + 1 and (s_ == 0 or dims[s_ - 1] == dims[i + 1]), "skip source must precede the layer"
     for ly in net.layers:
         if ly.kind == DENSE:
             Wm.append(np.asarray(ly.W, np.float64))
@@ -184,7 +198,7 @@ def build_problem(inst) -> Problem:
                    np.asarray(inst.spec, np.float64), [np.asarray(a, np.float64) for a in inst.inter_lo],
                    [np.asarray(a, np.float64) for a in inst.inter_hi], sub_lo, sub_hi,
                    np.asarray(sub.ptr), np.asarray(sub.layer), np.asarray(sub.index), np.asarray(sub.sign),
-                   sub.max_splits if S else 0, H, G, Q, np.asarray(cuts.d, np.float64))
+                   sub.max_splits if S else 0, H, G, Q, np.asarray(cuts.d, np.float64), skip)
 
 
 # ----------------------------------------------------------------------------
@@ -283,10 +297,16 @@ def evaluate(P: Problem, D: Duals, trace: bool = False):
     # nu^(L) = -c (spec folded as the last layer, Sec. 2); its bias term.
     nu = -P.spec[rk]                                  # [R, d_L]
     obj = -(nu @ P.b[P.L - 1]) - gam @ P.d
+    # R11: multipliers of skip terms waiting for the layer they skip to
+    carry = {}
+    if P.skip and P.skip[P.L - 1]:
+        carry[P.skip[P.L - 1] - 1] = nu.copy()
     T = Trace([None] * (P.L - 1), [None] * (P.L - 1), [None] * (P.L - 1), [None] * (P.L - 1),
               [None] * (P.L - 1), [None] * (P.L - 1), None, None)
     for i in range(P.L - 1, 0, -1):
         y = _rmul(nu, P.Wm[i])                        # nu^(i+1)^T W^(i+1)
+        if i in carry:
+            y = y + carry.pop(i)                      # + nu^(k) of the layer k that adds xhat^(i)
         t = np.asarray((P.H[i].T @ gam.T).T) if P.N else np.zeros((R, P.dims[i]))
         gg = np.asarray((P.G[i].T @ gam.T).T) if P.N else np.zeros((R, P.dims[i]))
         s = np.asarray((P.Q[i].T @ gam.T).T) if P.N else np.zeros((R, P.dims[i]))
@@ -309,7 +329,12 @@ def evaluate(P: Problem, D: Duals, trace: bool = False):
             T.nu[i - 1], T.nu_hat[i - 1], T.t[i - 1], T.s[i - 1] = nu_i, nu_hat, t, s
             T.lo[i - 1], T.hi[i - 1] = lo, hi
         nu = nu_i
+        if P.skip and P.skip[i - 1]:
+            m = P.skip[i - 1] - 1
+            carry[m] = carry[m] + nu_i if m in carry else nu_i.copy()
     y0 = _rmul(nu, P.Wm[0])
+    if 0 in carry:
+        y0 = y0 + carry.pop(0)
     c0 = -y0 + (np.asarray((P.H[0].T @ gam.T).T) if P.N else 0.0)
     obj = obj + np.sum(np.minimum(c0 * P.x_lo[None, :], c0 * P.x_hi[None, :]), axis=1)
     if trace:
@@ -322,7 +347,8 @@ def gradient(P: Problem, D: Duals):
     """g and dg/d(alpha, beta, gamma) by reverse mode through Theorem 3.1.
 
     The adjoint of y^(i-1) = W^(i)^T nu^(i) is a forward pass: with
-    a = dg/dy^(i-1), nubar^(i) = W^(i) a - b^(i) = dg/dnu^(i). Starting value
+    a = dg/dy^(i-1), nubar^(i) = W^(i) a - b^(i) = dg/dnu^(i) (plus dg/dy^(m)
+    when layer i adds xhat^(m), R11). Starting value
     a = -x*, the box corner minimising c0^T x (R1, R9: the centre where
     c0 = 0). dg/dgamma_k is then the violation H x + G xhat + Q z - d of cut k
     at the primal point implied by the duals (x = -nubar, xhat = -dg/dnuhat,
@@ -333,12 +359,16 @@ def gradient(P: Problem, D: Duals):
     xc = 0.5 * (P.x_lo + P.x_hi)
     xstar = np.where(T.c0 > 0, P.x_lo[None, :], np.where(T.c0 < 0, P.x_hi[None, :], xc[None, :]))
     a = -xstar
+    sources = {s_ - 1 for s_ in P.skip[:P.L - 1] if s_}
+    a_saved = {0: a} if 0 in sources else {}
     g_gamma = -np.repeat(P.d[None, :], R, 0) + (np.asarray((P.H[0] @ xstar.T).T) if P.N else 0.0)
     g_beta = np.zeros_like(D.beta)
     g_alpha = [np.zeros_like(x) for x in D.alpha]
     for i in range(1, P.L):
         Wi = P.Wm[i - 1]
         nubar = (np.asarray(Wi @ a.T).T if sp.issparse(Wi) else a @ Wi.T) - P.b[i - 1][None, :]
+        if P.skip and P.skip[i - 1]:
+            nubar = nubar + a_saved[P.skip[i - 1] - 1]
         nu_hat, s, lo, hi = T.nu_hat[i - 1], T.s[i - 1], T.lo[i - 1], T.hi[i - 1]
         al = D.alpha[i - 1]
         inactive = hi <= 0
@@ -373,6 +403,8 @@ def gradient(P: Problem, D: Duals):
         if len(rr):
             np.add.at(g_beta, (rr, mm), hh * dg_dt[rr, jj])
         a = dg_dnh
+        if i in sources:
+            a_saved[i] = a
     return g, Duals(g_alpha, g_beta, g_gamma)
 
 
@@ -432,11 +464,13 @@ def optimize(P: Problem, D: Duals, iters: int, lr_alpha: float, lr_beta: float, 
 def _lp_model(P: Problem, s: int, k: int, cut_d: Optional[np.ndarray] = None, with_cuts: bool = True):
     """Variables, constraints and objective of Eq. 16 for subdomain s, spec row k.
 
-    Variables: x0, then per hidden layer i: x^(i), xhat^(i), z^(i). Stable
+    Variables: x0, then per hidden layer i: x^(i), xhat^(i), z^(i). A skip
+    connection adds -xhat^(m) to its layer's equality rows (R11). Stable
     neurons keep their equalities (Eq. 9-10) and fixed z (R5); unstable ones
     get Eq. 4-7 and 0 <= z <= 1. Split rows are extra constraints
     (-x <= 0 for x >= 0, x <= 0 for x <= 0). The objective is
-    c^T (W^(L) xhat^(L-1) + b^(L)).
+    c^T (W^(L) xhat^(L-1) + b^(L)), plus c^T xhat^(m) when the last layer
+    adds xhat^(m).
     """
     dims = P.dims
     off = [0]
@@ -484,12 +518,16 @@ def _lp_model(P: Problem, s: int, k: int, cut_d: Optional[np.ndarray] = None, wi
         Wi = P.Wm[i - 1]
         Wd = Wi.toarray() if sp.issparse(Wi) else Wi
         prev = (lambda j: vx(0, j)) if i == 1 else (lambda j, i=i: vxh(i - 1, j))
+        m = P.skip[i - 1] - 1 if P.skip and P.skip[i - 1] else -1
+        src = None if m < 0 else ((lambda j: vx(0, j)) if m == 0 else (lambda j, m=m: vxh(m, j)))
         lo = P.sub_lo[i - 1][s]
         hi = P.sub_hi[i - 1][s]
         for j in range(dims[i]):
             row = [(vx(i, j), 1.0)]
             nz = np.nonzero(Wd[j])[0]
             row += [(prev(q), -Wd[j, q]) for q in nz]
+            if src is not None:
+                row.append((src(j), -1.0))
             eq(row, P.b[i - 1][j])
             if hi[j] <= 0:                       # inactive: xhat = 0, z = 0
                 lb[vxh(i, j)] = ub[vxh(i, j)] = 0.0
@@ -522,13 +560,17 @@ def _lp_model(P: Problem, s: int, k: int, cut_d: Optional[np.ndarray] = None, wi
                 le(row, float(dvec[kk]))
             elif dvec[kk] < 0:
                 le([(0, 0.0)], float(dvec[kk]))
-    # objective c^T (W^(L) xhat^(L-1) + b^(L))
+    # objective c^T (W^(L) xhat^(L-1) + b^(L) [+ xhat^(m)])
     cvec = np.zeros(nvar)
     WL = P.Wm[P.L - 1]
     WLd = WL.toarray() if sp.issparse(WL) else WL
     coef = P.spec[k] @ WLd
     for j in range(dims[P.L - 1]):
         cvec[vxh(P.L - 1, j) if P.L > 1 else vx(0, j)] += coef[j]
+    if P.skip and P.skip[P.L - 1]:
+        m = P.skip[P.L - 1] - 1
+        for j in range(dims[m]):
+            cvec[vxh(m, j) if m > 0 else vx(0, j)] += P.spec[k][j]
     const = float(P.spec[k] @ P.b[P.L - 1])
     Aeq = sp.csr_matrix((Aeq_v, (Aeq_r, Aeq_c)), shape=(neq[0], nvar)) if neq[0] else None
     Aub = sp.csr_matrix((Aub_v, (Aub_r, Aub_c)), shape=(nub[0], nvar)) if nub[0] else None

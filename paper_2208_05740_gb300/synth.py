@@ -52,6 +52,7 @@ class Layer:
     out_shape: tuple
     stride: int = 1
     pad: int = 0
+    skip: int = 0      # 0: none; s >= 1: the layer adds xhat^(s-1) (s = 1: the input x) to W x + b
 
     @property
     def d_in(self) -> int:
@@ -170,11 +171,13 @@ def layer_apply(ly: Layer, x: np.ndarray, W: Optional[np.ndarray] = None) -> np.
 def forward_all(net: Network, x: np.ndarray):
     """Return pre-activations [x^(1..L)] for a batch of inputs x [B, d0]."""
     pre = []
-    h = x
+    post = [x]            # xhat^(0) = x, xhat^(i) = ReLU(x^(i))
     for i, ly in enumerate(net.layers):
-        z = layer_apply(ly, h) + ly.b[None, :]
+        z = layer_apply(ly, post[-1]) + ly.b[None, :]
+        if ly.skip:
+            z = z + post[ly.skip - 1]
         pre.append(z)
-        h = np.maximum(z, 0.0)
+        post.append(np.maximum(z, 0.0))
     return pre
 
 
@@ -231,15 +234,21 @@ def interval_bounds(net: Network, x_lo: np.ndarray, x_hi: np.ndarray):
     """Interval (IBP) pre-activation bounds for hidden layers 1..L-1."""
     c = 0.5 * (x_lo + x_hi)
     r = 0.5 * (x_hi - x_lo)
+    cs, rs = [c], [r]     # centre and radius of xhat^(0..)
     lo_list, hi_list = [], []
     for i, ly in enumerate(net.layers[:-1]):
         cc = layer_apply(ly, c[None, :])[0] + ly.b
         rr = layer_apply(ly, r[None, :], np.abs(ly.W))[0]
+        if ly.skip:
+            cc = cc + cs[ly.skip - 1]
+            rr = rr + rs[ly.skip - 1]
         lo, hi = cc - rr, cc + rr
         lo_list.append(lo)
         hi_list.append(hi)
         c = 0.5 * (np.maximum(lo, 0) + np.maximum(hi, 0))
         r = 0.5 * (np.maximum(hi, 0) - np.maximum(lo, 0))
+        cs.append(c)
+        rs.append(r)
     return lo_list, hi_list
 
 
@@ -379,6 +388,25 @@ def cnn_cifar(seed: int = SEED_BASE + 3, n_sub: int = 4096, n_cuts: int = 1000) 
     x0 = rng.random(3 * 32 * 32)
     return _finish("cnn_3x32x32_c32_c64_fc512_fc10", rng, net, x0, 2.0 / 255.0, 9, n_sub, (1, 12),
                    dict(n_cuts=n_cuts, min_vars=2, max_vars=16, span_layers=True, need_z=True, p_input=0.99))
+
+
+def mlp_residual(seed: int = SEED_BASE + 6, width: int = 16, d0: int = 8, blocks: int = 2, d_out: int = 3,
+                 eps: float = 0.1, n_spec: int = 2, n_sub: int = 4, n_cuts: int = 8, max_splits: int = 2) -> Instance:
+    """Residual MLP: d0 -> width, then `blocks` blocks of two layers whose
+    second layer adds the block input (xhat two layers back) to its
+    pre-activation, then width -> d_out. Weights N(0, 1/fan_in), biases
+    N(0, 0.1); the skip-carrying layers are scaled by 1/2 (residual nets keep
+    the block's branch small)."""
+    rng = np.random.default_rng(seed)
+    dims = [d0] + [width] * (2 * blocks + 1) + [d_out]
+    net = make_mlp(rng, dims)
+    for q in range(blocks):
+        i = 3 + 2 * q                  # 1-based index of the block's second layer
+        ly = net.layers[i - 1]
+        net.layers[i - 1] = dataclasses.replace(ly, W=0.5 * ly.W, skip=i - 1)   # adds xhat^(i-2)
+    x0 = rng.random(d0)
+    return _finish(f"mlp_residual_{d0}_{width}x{2 * blocks + 1}_{d_out}", rng, net, x0, eps, n_spec, n_sub,
+                   (0, max_splits), dict(n_cuts=n_cuts, min_vars=2, max_vars=4, hidden_only=True))
 
 
 def mlp_1024x4_queries(seed: int = SEED_BASE + 4, sizes=(64, 700, 2048), cut_counts=(0, 500, 3000)):
