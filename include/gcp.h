@@ -70,13 +70,22 @@ enum { GCP_PGA = 0, GCP_ADAM = 1 };
  * conv2d: W is [c_out, c_in, k, k] (OIHW), cross-correlation with the given
  *         stride and zero padding; activations are CHW-flattened, so
  *         d_in = c_in*h_in*w_in and d_out = c_out*h_out*w_out.
- * b has d_out entries (per output element, CHW order for conv2d). */
+ * b has d_out entries (per output element, CHW order for conv2d).
+ * skip: 0 for a plain layer; s >= 1 adds the post-activation xhat^(s-1) of an
+ *       earlier layer (s = 1: the input x; s = i: the layer's own input) to
+ *       the layer's output, x^(i) = W^(i) xhat^(i-1) + b^(i) + xhat^(s-1): the
+ *       identity shortcut of a residual block (the residual CIFAR models of
+ *       Sec. 4 / App. C.1). Needs d_{s-1} = d_out; each xhat feeds at most one
+ *       skip. The skip's multiplier nu^(i) joins the coefficient of
+ *       xhat^(s-1) in the backward pass (Theorem 3.1 with the identity as one
+ *       more linear map). Zero-initialise the struct to leave it off. */
 typedef struct {
   int32_t kind;
   int32_t d_in, d_out;
   int32_t c_in, h_in, w_in, c_out, h_out, w_out, k, stride, pad;
   const double* W;
   const double* b;
+  int32_t skip;
 } gcp_layer_desc;
 
 /* Branch-and-bound subdomains as neuron split sets (App. B), CSR by

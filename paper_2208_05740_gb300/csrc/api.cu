@@ -269,7 +269,8 @@ static int64_t red_len(const LayerGeom& g) {
 
 // ------------------------------------------------------------------ net
 gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const double* x_lo, const double* x_hi,
-                    const double* spec_c, int n_spec, const double* inter_lo, const double* inter_hi, int* out_id) {
+                    const double* spec_c, int n_spec, const double* inter_lo, const double* inter_hi, int* out_id,
+                    int last_skip_off) {
   if (!layers || n_layers < 1 || !x_lo || !x_hi || !spec_c || n_spec < 1 || !out_id)
     return c.fail(GCP_EINVAL, "gcp_init_net: null argument or empty network/spec");
   auto net = std::make_unique<Net>();
@@ -303,6 +304,25 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
   for (int i = 0; i < n_layers; ++i) net->dims.push_back(layers[i].d_out);
   const int L = n_layers;
   const int d0 = net->dims[0], dL = net->dims[L];
+  // skip connections: x^(i) += xhat^(s-1), one consumer per source
+  net->skip.assign(L, 0);
+  net->consumer.assign(L, 0);
+  net->skip_off = last_skip_off;
+  if (last_skip_off < 0 || (last_skip_off > 0 && layers[L - 1].skip == 0))
+    return c.fail(GCP_EINVAL, "skip offset without a skip on the last layer");
+  for (int i = 1; i <= L; ++i) {
+    const int s = layers[i - 1].skip;
+    if (s == 0) continue;
+    const int off = i == L ? last_skip_off : 0;
+    if (s < 0 || s > i) return c.fail(GCP_EINVAL, "layer %d: skip %d must name an earlier xhat (1..%d)", i, s, i);
+    const int m = s - 1;
+    if (i < L ? net->dims[m] != net->dims[i] : (int64_t)off + net->dims[i] > net->dims[m])
+      return c.fail(GCP_EINVAL, "layer %d: skip from xhat^(%d) of width %d does not fit width %d", i, m,
+                    net->dims[m], net->dims[i]);
+    if (net->consumer[m]) return c.fail(GCP_EINVAL, "xhat^(%d) feeds two skips (layers %d and %d)", m, net->consumer[m], i);
+    net->skip[i - 1] = s;
+    net->consumer[m] = i;
+  }
   int64_t nh = 0;
   for (int i = 1; i < L; ++i) nh += net->dims[i];
   if (nh > 0 && (!inter_lo || !inter_hi)) return c.fail(GCP_EINVAL, "intermediate bounds required");
@@ -434,6 +454,10 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
   std::vector<double> negc((size_t)n_spec * dL);
   for (size_t q = 0; q < negc.size(); ++q) negc[q] = -spec_c[q];
   UP(net->negC64, double, negc.data(), negc.size());
+  {
+    auto nf = to_f32(negc.data(), negc.size());
+    UP(net->negC32, float, nf.data(), nf.size());
+  }
   // y^(L-1) = W^(L)^T nu^(L) = -W^(L)^T c_k and c_k^T b^(L), per spec row
   const gcp_layer_desc& last = layers[L - 1];
   const int dl1 = net->dims[L - 1];
@@ -444,6 +468,8 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
       if (cv == 0.0) continue;   // sparse specs (unit rows) skip the zero columns
       cb[k] += cv * last.b[q];
       for (int j = 0; j < dl1; ++j) yl[(size_t)k * dl1 + j] -= cv * last.W[(size_t)q * dl1 + j];
+      // a skip from the last layer's own input: + the multiplier -c_k itself
+      if (net->skip[L - 1] == L) yl[(size_t)k * dl1 + net->skip_off + q] -= cv;
     }
   }
   UP(net->YL64, double, yl.data(), yl.size());
@@ -940,6 +966,42 @@ static void lin_forward(cudaStream_t st, const Batch& b, int i, const Top* a, co
   else conv_fwd<Top, T>(st, b.R, g, WSel<Top>::W(net, i), a, out);
 }
 
+// Skip connections in the backward pass (Theorem 3.1 with the identity as one
+// more linear map): once y^(i-1) = W^(i)^T nu^(i) is formed, nu^(i) of a skip
+// from xhat^(i-1) joins it; nu^(i) of a skip from further back is parked until
+// its y^(m) exists; y^(i-1) then takes what was parked for it, or -c_k when
+// the last layer adds xhat^(i-1) (from L-1 it is already folded into YL).
+template <typename Top, typename T>
+static gcp_status skip_backward(Ctx& c, Batch& b, cudaStream_t st, int i, const Top* nu, T* y, const T* negC) {
+  const Net& net = *b.net;
+  const int L = net.L;
+  gcp_status s = GCP_OK;
+  const int si = net.skip[i - 1];
+  if (si == i) {
+    skip_add<Top, T>(st, b.R, net.dims[i], net.dims[i], 0, nu, 0, y);
+  } else if (si) {
+    Top* park = (Top*)b.ws("skip" + std::to_string(si - 1), (size_t)b.R * net.dims[si - 1] * sizeof(Top), &s);
+    if (!park) return s;
+    cudaMemcpyAsync(park, nu, (size_t)b.R * net.dims[i] * sizeof(Top), cudaMemcpyDeviceToDevice, st);
+  }
+  const int k = net.consumer[i - 1];
+  if (k == L && i - 1 < L - 1) {
+    skip_add<T, T>(st, b.R, net.dims[L], net.dims[i - 1], net.skip_off, negC, b.K, y);
+  } else if (k > i && k < L) {
+    const Top* park = (const Top*)b.ws("skip" + std::to_string(i - 1), (size_t)b.R * net.dims[i - 1] * sizeof(Top), &s);
+    if (!park) return s;
+    skip_add<Top, T>(st, b.R, net.dims[i - 1], net.dims[i - 1], 0, park, 0, y);
+  }
+  return GCP_OK;
+}
+
+template <typename T>
+static const T* neg_spec(const Net& n);
+template <>
+const double* neg_spec<double>(const Net& n) { return n.negC64; }
+template <>
+const float* neg_spec<float>(const Net& n) { return n.negC32; }
+
 // Evaluate g for all rows at the batch's duals. with_adjoint_start: also write
 // a0 = -seed*x* into the operand buffer and the input-layer cut entries into E.
 // finalize = false leaves g itself out (ascent steps need only the gradient).
@@ -987,6 +1049,8 @@ gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, 
     relax_eval<T, Top>(st, a);
     poff += (net.dims[i] + kChunk - 1) / kChunk;
     lin_backward<Top, T>(st, b, i, nu, a.nu_lo, y);
+    s = skip_backward<Top, T>(c, b, st, i, nu, y, neg_spec<T>(net));
+    if (s) return s;
   }
   ConcArgs<T, Top> ca{};
   ca.R = R; ca.K = b.K; ca.d0 = net.dims[0]; ca.N = b.N;
@@ -1044,9 +1108,29 @@ gcp_status run_adjoint(Ctx& c, Batch& b, cudaStream_t st, const StepArgs<T>& ste
     gbe = (T*)b.ws("g_beta_step", (size_t)b.M * R * sizeof(T), &s);
     if (!gbe) return s;
   }
+  // skips in the reverse pass: dg/dnu^(k) gains dg/dy^(m), the adjoint a^(m)
+  // of the xhat^(m) that layer k adds; a^(m) is parked when a later layer needs it
+  auto park_a = [&](int m) -> gcp_status {
+    const int k = net.consumer[m];
+    if (k <= m + 1 || k >= L) return GCP_OK;
+    Top* park = (Top*)b.ws("skip" + std::to_string(m), (size_t)R * net.dims[m] * sizeof(Top), &s);
+    if (!park) return s;
+    cudaMemcpyAsync(park, abuf, (size_t)R * net.dims[m] * sizeof(Top), cudaMemcpyDeviceToDevice, st);
+    return GCP_OK;
+  };
+  s = park_a(0);
+  if (s) return s;
   int64_t aoff = 0;
   for (int i = 1; i < L; ++i) {
     lin_forward<Top, T>(st, b, i, abuf, (lo && tc_fwd<Top>(b, i)) ? lo : nullptr, y);
+    if (const int si = net.skip[i - 1]) {
+      const Top* src = abuf;
+      if (si < i) {
+        src = (const Top*)b.ws("skip" + std::to_string(si - 1), (size_t)R * net.dims[si - 1] * sizeof(Top), &s);
+        if (!src) return s;
+      }
+      skip_add<Top, T>(st, R, net.dims[i], net.dims[i], 0, src, 0, y);
+    }
     const T* nuhat = (const T*)b.lazy["nuhat" + std::to_string(i)];
     AdjArgs<T, Top> a{};
     a.R = R; a.K = b.K; a.d = net.dims[i]; a.layer = i; a.M = b.M; a.N = b.N;
@@ -1067,6 +1151,10 @@ gcp_status run_adjoint(Ctx& c, Batch& b, cudaStream_t st, const StepArgs<T>& ste
     a.st = step;
     relax_adjoint<T, Top>(st, a);
     aoff += (int64_t)R * net.dims[i];
+    if (i < L - 1) {
+      s = park_a(i);
+      if (s) return s;
+    }
   }
   if (b.N > 0 || (b.M > 0 && step.mode != 0)) {
     GatherArgs<T> ga{R, b.N, b.cuts.cut_ptr, b.cuts.csr_pos, E, TSel<T>::d(b.cuts), seed, (T*)b.gamma, gga, mg, vg,
@@ -1120,6 +1208,13 @@ gcp_status run_certify(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
   // |computed y - exact y| <= yerr * ya elementwise: Higham's gamma_K for the
   // float64 dot products, the slice bound for the tensor-core product
   double yerr = gamma_n_host(red_len(gl));
+  // a skip adds an exact float64 term t to y: |fl(y + t) - (y_exact + t)| <=
+  // yerr ya + u (|y| + |t|) <= (yerr + 2u) (ya + |t|), and ya grows by |t|
+  auto skip_err = [](double e) { return std::nextafter(e + std::ldexp(1.0, -52), INFINITY); };
+  if (net.skip[L - 1] == L) {
+    skip_add_cert(st, b.K, net.dims[L], net.dims[L - 1], net.skip_off, net.negC64, 0, y, ya);
+    yerr = skip_err(yerr);
+  }
   int poff = 0;
   for (int i = L - 1; i >= 1; --i) {
     CertArgs<Td> a{};
@@ -1148,6 +1243,26 @@ gcp_status run_certify(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
     } else {
       conv_T_abs(st, R, g, net.W64[i - 1], net.Wabs32[i - 1], nu, nuabs, y, ya);
       yerr = gamma_n_host(red_len(g));
+    }
+    // skips, as in the chain's backward pass, with the error bound widened
+    const int si = net.skip[i - 1];
+    if (si == i) {
+      skip_add_cert(st, R, net.dims[i], net.dims[i], 0, nu, 0, y, ya);
+      yerr = skip_err(yerr);
+    } else if (si) {
+      double* park = (double*)b.ws("c_skip" + std::to_string(si - 1), (size_t)R * net.dims[si - 1] * 8, &s);
+      if (!park) return s;
+      cudaMemcpyAsync(park, nu, (size_t)R * net.dims[i] * 8, cudaMemcpyDeviceToDevice, st);
+    }
+    const int k = net.consumer[i - 1];
+    if (k == L && i - 1 < L - 1) {
+      skip_add_cert(st, R, net.dims[L], net.dims[i - 1], net.skip_off, net.negC64, b.K, y, ya);
+      yerr = skip_err(yerr);
+    } else if (k > i && k < L) {
+      const double* park = (const double*)b.ws("c_skip" + std::to_string(i - 1), (size_t)R * net.dims[i - 1] * 8, &s);
+      if (!park) return s;
+      skip_add_cert(st, R, net.dims[i - 1], net.dims[i - 1], 0, park, 0, y, ya);
+      yerr = skip_err(yerr);
     }
   }
   certify_concretize<Td>(st, R, b.K, b.N, net.dims[0], y, ya, yerr, net.xlo64,

@@ -10,7 +10,9 @@
 // certified FP64 values give lo_j = g(+e_j) and hi_j = -g(-e_j). At the
 // default slopes this is CROWN; with ascent steps on the slopes of each such
 // row it is alpha-CROWN. Every value is a certified (outward-rounded) bound,
-// so the result is sound whatever precision the chain runs in.
+// so the result is sound whatever precision the chain runs in. A residual
+// layer keeps its skip in the truncated network: the last layer's skip then
+// adds the rows' own slice of xhat^(m).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -62,6 +64,8 @@ gcp_status intermediate_bounds(Ctx& c, const gcp_layer_desc* layers, int L, cons
     if (!layers[i].W || !layers[i].b || layers[i].d_in <= 0 || layers[i].d_out <= 0 ||
         (i > 0 && layers[i].d_in != layers[i - 1].d_out))
       return c.fail(GCP_EINVAL, "gcp_intermediate_bounds: layer %d: bad shape or null weights", i + 1);
+  if (layers[0].skip != 0 && (layers[0].skip != 1 || layers[0].d_in != layers[0].d_out))
+    return c.fail(GCP_EINVAL, "gcp_intermediate_bounds: layer 1 can only add the input (skip 1, d_in = d_out)");
   if (p && (p->iters < 0 || p->prec < GCP_FP32 || p->prec > GCP_BF16))
     return c.fail(GCP_EINVAL, "gcp_intermediate_bounds: iters >= 0 and prec FP32 or BF16");
   int64_t total = 0;
@@ -83,6 +87,10 @@ gcp_status intermediate_bounds(Ctx& c, const gcp_layer_desc* layers, int L, cons
           const double a = w * x_lo[k], e = w * x_hi[k];
           lo = round_down(lo + round_down(std::min(a, e)));
           hi = round_up(hi + round_up(std::max(a, e)));
+        }
+        if (d.skip == 1) {   // x^(1) = W x + b + x
+          lo = round_down(lo + x_lo[j0 + q]);
+          hi = round_up(hi + x_hi[j0 + q]);
         }
         if (!std::isfinite(lo) || !std::isfinite(hi)) return c.fail(GCP_EINVAL, "layer 1 bounds not finite");
         blo[j0 + q] = lo;
@@ -108,6 +116,7 @@ gcp_status intermediate_bounds(Ctx& c, const gcp_layer_desc* layers, int L, cons
       last.d_out = nj;
       last.W = W.data();
       last.b = b.data();
+      last.skip = d.skip;
       net.push_back(last);
       std::vector<double> spec((size_t)2 * nj * nj, 0.0);
       for (int q = 0; q < nj; ++q) {
@@ -115,7 +124,8 @@ gcp_status intermediate_bounds(Ctx& c, const gcp_layer_desc* layers, int L, cons
         spec[(size_t)(nj + q) * nj + q] = -1.0;
       }
       int nid = -1;
-      gcp_status s = init_net(c, net.data(), i, x_lo, x_hi, spec.data(), 2 * nj, blo.data(), bhi.data(), &nid);
+      gcp_status s = init_net(c, net.data(), i, x_lo, x_hi, spec.data(), 2 * nj, blo.data(), bhi.data(), &nid,
+                              d.skip ? j0 : 0);
       if (s) return s;
       Batch* bt = nullptr;
       s = duals_create(c, nid, -1, &sub, GCP_FP32, &bt);

@@ -39,6 +39,11 @@ struct Net {
   float* YL32 = nullptr;
   double* cb64 = nullptr;            // [K] = c_k^T b^(L)
   float* cb32 = nullptr;
+  float* negC32 = nullptr;           // [K, d_L] = -c_k in float (a skip into the last layer)
+  // skip connections: skip[i-1] = s >= 1 when layer i adds xhat^(s-1);
+  // consumer[m] = the layer that adds xhat^(m), or 0
+  std::vector<int> skip, consumer;
+  int skip_off = 0;                  // the last layer's skip adds xhat^(m)[skip_off ..]
   std::vector<double*> lo64, hi64;   // hidden layer i at index i-1
   std::vector<float*> lo32, hi32;    // rounded outwards
   std::vector<double*> invul64;      // 1 / (hi - lo) where lo < 0 < hi, else 0
@@ -152,9 +157,12 @@ struct AllocPool {
   bool prev;
 };
 
-// shared by api.cu and serve.cu
+// shared by api.cu and serve.cu. last_skip_off: the last layer's skip adds
+// xhat^(m)[off .. off + d_L) instead of all of xhat^(m) (bounds of a block of
+// rows of a residual layer; 0 through the public entry point)
 gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const double* x_lo, const double* x_hi,
-                    const double* spec_c, int n_spec, const double* inter_lo, const double* inter_hi, int* out_id);
+                    const double* spec_c, int n_spec, const double* inter_lo, const double* inter_hi, int* out_id,
+                    int last_skip_off = 0);
 gcp_status bound_batch(Ctx& c, Batch& b, int prec, int certify, double* out_bound, double* out_cert);
 gcp_status optimize_batch(Ctx& c, Batch& b, const gcp_opt_params* p, double* out_bound, double* out_cert,
                           double* out_err);

@@ -249,6 +249,16 @@ void conv_T(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const 
 void conv_T_abs(cudaStream_t st, int64_t R, const LayerGeom& g, const double* W, const float* Wabs, const double* in,
                 const float* inabs, double* out, float* outabs);
 
+// Skip connections: y[r, off + j] += src[r', j] for r < R, j < d, where
+// r' = r % src_mod (src_mod > 0: one source row per spec row) or r; y rows
+// have stride ld, source rows stride d.
+template <typename Ts, typename Td>
+void skip_add(cudaStream_t st, int64_t R, int d, int ld, int off, const Ts* src, int src_mod, Td* y);
+// the same in the certification: float64 sum in round-to-nearest and the
+// magnitude bound yabs += |src| in float rounded up
+void skip_add_cert(cudaStream_t st, int64_t R, int d, int ld, int off, const double* src, int src_mod, double* y,
+                   float* yabs);
+
 // tcgen05 GEMMs (k_tc.cu); false = shape or driver not supported, use SIMT
 bool tc_available(int K, bool bf16);
 bool gemm_tc_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C);

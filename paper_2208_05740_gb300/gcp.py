@@ -42,7 +42,7 @@ class LayerDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("d_in", C.c_int32), ("d_out", C.c_int32), ("c_in", C.c_int32),
                 ("h_in", C.c_int32), ("w_in", C.c_int32), ("c_out", C.c_int32), ("h_out", C.c_int32),
                 ("w_out", C.c_int32), ("k", C.c_int32), ("stride", C.c_int32), ("pad", C.c_int32),
-                ("W", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double))]
+                ("W", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double)), ("skip", C.c_int32)]
 
 
 class Subdomains(C.Structure):
@@ -220,10 +220,12 @@ class Context:
                 d.k, d.stride, d.pad = W.shape[2], ly.stride, ly.pad
             d.W = _ptr(W, C.c_double)
             d.b = _ptr(b, C.c_double)
+            d.skip = int(getattr(ly, "skip", 0))
         return descs
 
     def init_net(self, layers, x_lo, x_hi, spec_c, inter_lo, inter_hi) -> int:
-        """layers: objects with kind, W, b, in_shape, out_shape, stride, pad."""
+        """layers: objects with kind, W, b, in_shape, out_shape, stride, pad
+        and optionally skip (0, or s >= 1: the layer adds xhat^(s-1))."""
         keep = []
         descs = self._layer_descs(layers, keep)
         xl, xh, sc = _c(x_lo, np.float64), _c(x_hi, np.float64), _c(spec_c, np.float64)

@@ -409,6 +409,40 @@ def mlp_residual(seed: int = SEED_BASE + 6, width: int = 16, d0: int = 8, blocks
                    (0, max_splits), dict(n_cuts=n_cuts, min_vars=2, max_vars=4, hidden_only=True))
 
 
+def make_resnet(rng, hw: int = 32, ch=(16, 32), fc: int = 100, d_out: int = 10) -> Network:
+    """Residual CNN of two identity-shortcut blocks (the shape of the residual
+    CIFAR models, App. C.1, with identity shortcuts only):
+    3 x hw x hw -> conv ch0 3x3 s2 p1 -> block(ch0) -> conv ch1 3x3 s2 p1 ->
+    block(ch1) -> FC fc -> FC d_out, where block(c) is conv c 3x3 s1 p1 then
+    conv c 3x3 s1 p1 whose output adds the block input. The second conv of a
+    block is scaled by 1/2."""
+    layers = []
+    shape = (3, hw, hw)
+    for c in ch:
+        down = make_conv(rng, shape, c, 3, 2, 1)
+        a = make_conv(rng, down.out_shape, c, 3, 1, 1)
+        b = make_conv(rng, a.out_shape, c, 3, 1, 1)
+        layers += [down, a, dataclasses.replace(b, W=0.5 * b.W, skip=len(layers) + 2)]  # adds xhat of `down`
+        shape = b.out_shape
+    d = int(np.prod(shape))
+    W1 = rng.normal(0.0, math.sqrt(1.0 / d), size=(fc, d))
+    b1 = rng.normal(0.0, math.sqrt(0.1), size=fc)
+    W2 = rng.normal(0.0, math.sqrt(1.0 / fc), size=(d_out, fc))
+    b2 = rng.normal(0.0, math.sqrt(0.1), size=d_out)
+    return Network(layers + [Layer(DENSE, W1, b1, (d,), (fc,)), Layer(DENSE, W2, b2, (fc,), (d_out,))])
+
+
+def cnn_resnet(seed: int = SEED_BASE + 7, hw: int = 32, ch=(16, 32), fc: int = 100, eps: float = 2.0 / 255.0,
+               n_spec: int = 9, n_sub: int = 2048, n_cuts: int = 500, max_splits: int = 12) -> Instance:
+    """Residual CNN (make_resnet), eps 2/255, 9 spec rows, 1-12 splits, cuts of 2-16 variables."""
+    rng = np.random.default_rng(seed)
+    net = make_resnet(rng, hw, ch, fc)
+    x0 = rng.random(3 * hw * hw)
+    return _finish(f"resnet_3x{hw}x{hw}_c{ch[0]}_c{ch[1]}_fc{fc}_fc10", rng, net, x0, eps, n_spec, n_sub,
+                   (1, max_splits), dict(n_cuts=n_cuts, min_vars=2, max_vars=16, span_layers=True, need_z=True,
+                                         p_input=0.99))
+
+
 def mlp_1024x4_queries(seed: int = SEED_BASE + 4, sizes=(64, 700, 2048), cut_counts=(0, 500, 3000)):
     """Three queries on one MLP 784-1024x4-10 with different batch and cut counts."""
     rng = np.random.default_rng(seed)

@@ -57,3 +57,33 @@ def test_instances_have_the_documented_shapes():
     has_z = [np.any(c.kind[c.ptr[k]:c.ptr[k + 1]] == 2) for k in range(c.n)]
     span = [len(set(c.layer[c.ptr[k]:c.ptr[k + 1]].tolist())) >= 2 for k in range(c.n)]
     assert np.mean(has_in) > 0.9 and all(has_z) and np.mean(span) > 0.95
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """Every struct of the header has the binding's size and field offsets
+    (a small C program compiled against the header prints them)."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [("gcp_layer_desc", gcp.LayerDesc), ("gcp_subdomains", gcp.Subdomains), ("gcp_opt_params", gcp.OptParams),
+             ("gcp_bab_params", gcp.BabParams), ("gcp_bab_result", gcp.BabResult), ("gcp_request", gcp.Request),
+             ("gcp_result", gcp.Result)]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "gcp.h"', "int main(void) {"]
+    for cname, py in pairs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict((" ".join(l.split()[:2]), int(l.split()[2]))
+               for l in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines())
+    for cname, py in pairs:
+        assert got[f"{cname} size"] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[f"{cname} {f}"] == getattr(py, f).offset, (cname, f)
