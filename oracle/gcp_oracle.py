@@ -18,11 +18,11 @@ It is a plain, slow restatement, in float64 and in the paper's notation, of
     after Theorem 3.1; App. C.1 names Adam with 20 iterations);
   * the LP of Eq. 16 and its MIP counterpart (Eq. 2-10 plus cuts), solved by
     SciPy/HiGHS, used only to pin the bound from outside;
-  * residual (skip) connections, x^(k) = W^(k) xhat^(k-1) + b^(k) + xhat^(m)
-    with m < k: the paper states the method for general computational graphs
-    (Sec. 2 defines the feed-forward case for clarity, App. C.2 verifies
-    residual networks); the skip term is one more linear map, the identity,
-    whose multiplier nu^(k) is added to the coefficient of xhat^(m).
+  * residual (skip) connections, x^(k) = W^(k) xhat^(k-1) + b^(k) + S xhat^(m)
+    with m < k and S the identity or a projection shortcut (a 1x1 convolution
+    where a block changes channels or size): the residual CIFAR models of
+    Sec. 4 / App. C.1 (ResBlock(a, b)); the skip term is one more linear map,
+    whose multiplier nu^(k) adds S^T nu^(k) to the coefficient of xhat^(m).
 
 Readings of the paper (each is listed with its reason in the design notes):
   R1 concretisation is the minimum of the linear input term over the box,
@@ -49,9 +49,10 @@ Readings of the paper (each is listed with its reason in the design notes):
      p >= C; at nuhat = 0 exactly every local derivative is 0.
  R10 default initial duals: alpha = 1 if u >= -l else 0, beta = gamma = 0.
  R11 a skip connection enters the Lagrangian like the layer's weight matrix:
-     the equality x^(k) - W^(k) xhat^(k-1) - b^(k) - xhat^(m) = 0 with
-     multiplier nu^(k) adds nu^(k) to y^(m), the coefficient of xhat^(m)
-     (xhat^(0) = x, so m = 0 adds it to the input term before concretisation).
+     the equality x^(k) - W^(k) xhat^(k-1) - b^(k) - S xhat^(m) - b_S = 0 with
+     multiplier nu^(k) adds S^T nu^(k) to y^(m), the coefficient of xhat^(m)
+     (xhat^(0) = x, so m = 0 adds it to the input term before concretisation);
+     the shortcut's bias b_S joins b^(k).
 
 Layouts (float64 numpy): rows r = s * K + k for subdomain s and spec row k;
 alpha is a list over hidden layers of [R, d_i]; beta is [R, max_splits]
@@ -135,6 +136,8 @@ class Problem:
     d: np.ndarray
     # per layer (index i-1 for layer i): 0, or s >= 1 when layer i adds xhat^(s-1)
     skip: List[int] = dataclasses.field(default_factory=list)
+    # per layer: the shortcut S [d_i, d_{s-1}] (dense or csr), None for the identity
+    skip_map: list = dataclasses.field(default_factory=list)
 
     @property
     def K(self) -> int:
@@ -160,14 +163,26 @@ def build_problem(inst) -> Problem:
     dims = [net.layers[0].d_in] + [ly.d_out for ly in net.layers]
     Wm, b = [], []
     skip = [int(getattr(ly, "skip", 0)) for ly in net.layers]
-    for i, s_ in enumerate(skip):
-        assert 0 <= s_ <= i + 1 and (s_ == 0 or dims[s_ - 1] == dims[i + 1]), "skip source must precede the layer"
+    skip_map = []
+    for i, (s_, ly) in enumerate(zip(skip, net.layers)):
+        sc = getattr(ly, "shortcut", None) if s_ else None
+        assert 0 <= s_ <= i + 1, "skip source must precede the layer"
+        if sc is None:
+            assert s_ == 0 or dims[s_ - 1] == dims[i + 1], "an identity skip needs equal widths"
+            skip_map.append(None)
+        else:
+            assert sc.d_in == dims[s_ - 1] and sc.d_out == dims[i + 1], "shortcut shape"
+            skip_map.append(np.asarray(sc.W, np.float64) if sc.kind == DENSE else
+                            conv_matrix(np.asarray(sc.W, np.float64), sc.in_shape, sc.out_shape, sc.stride, sc.pad))
     for ly in net.layers:
         if ly.kind == DENSE:
             Wm.append(np.asarray(ly.W, np.float64))
         else:
             Wm.append(conv_matrix(np.asarray(ly.W, np.float64), ly.in_shape, ly.out_shape, ly.stride, ly.pad))
         b.append(np.asarray(ly.b, np.float64))
+        sc = getattr(ly, "shortcut", None) if getattr(ly, "skip", 0) else None
+        if sc is not None:
+            b[-1] = b[-1] + np.asarray(sc.b, np.float64)
     sub = inst.sub
     S = sub.n
     sub_lo = [np.repeat(np.asarray(lo, np.float64)[None, :], S, 0) for lo in inst.inter_lo]
@@ -198,7 +213,7 @@ def build_problem(inst) -> Problem:
                    np.asarray(inst.spec, np.float64), [np.asarray(a, np.float64) for a in inst.inter_lo],
                    [np.asarray(a, np.float64) for a in inst.inter_hi], sub_lo, sub_hi,
                    np.asarray(sub.ptr), np.asarray(sub.layer), np.asarray(sub.index), np.asarray(sub.sign),
-                   sub.max_splits if S else 0, H, G, Q, np.asarray(cuts.d, np.float64), skip)
+                   sub.max_splits if S else 0, H, G, Q, np.asarray(cuts.d, np.float64), skip, skip_map)
 
 
 # ----------------------------------------------------------------------------
@@ -213,6 +228,20 @@ class Duals:
 
     def copy(self) -> "Duals":
         return Duals([a.copy() for a in self.alpha], self.beta.copy(), self.gamma.copy())
+
+
+def _through_skip(P: Problem, layer: int, nu: np.ndarray) -> np.ndarray:
+    """S^T nu of the skip of `layer` (nu itself for the identity), as rows [R, d_m]."""
+    S = P.skip_map[layer - 1] if P.skip_map else None
+    return nu.copy() if S is None else _rmul(nu, S)
+
+
+def _skip_forward(P: Problem, layer: int, a: np.ndarray) -> np.ndarray:
+    """S a of the skip of `layer` as rows [R, d_layer] (a itself for the identity)."""
+    S = P.skip_map[layer - 1] if P.skip_map else None
+    if S is None:
+        return a
+    return np.asarray(S @ a.T).T if sp.issparse(S) else a @ S.T
 
 
 def row_sub(P: Problem) -> np.ndarray:
@@ -300,7 +329,7 @@ def evaluate(P: Problem, D: Duals, trace: bool = False):
     # R11: multipliers of skip terms waiting for the layer they skip to
     carry = {}
     if P.skip and P.skip[P.L - 1]:
-        carry[P.skip[P.L - 1] - 1] = nu.copy()
+        carry[P.skip[P.L - 1] - 1] = _through_skip(P, P.L, nu)
     T = Trace([None] * (P.L - 1), [None] * (P.L - 1), [None] * (P.L - 1), [None] * (P.L - 1),
               [None] * (P.L - 1), [None] * (P.L - 1), None, None)
     for i in range(P.L - 1, 0, -1):
@@ -331,7 +360,8 @@ def evaluate(P: Problem, D: Duals, trace: bool = False):
         nu = nu_i
         if P.skip and P.skip[i - 1]:
             m = P.skip[i - 1] - 1
-            carry[m] = carry[m] + nu_i if m in carry else nu_i.copy()
+            v = _through_skip(P, i, nu_i)
+            carry[m] = carry[m] + v if m in carry else v
     y0 = _rmul(nu, P.Wm[0])
     if 0 in carry:
         y0 = y0 + carry.pop(0)
@@ -368,7 +398,7 @@ def gradient(P: Problem, D: Duals):
         Wi = P.Wm[i - 1]
         nubar = (np.asarray(Wi @ a.T).T if sp.issparse(Wi) else a @ Wi.T) - P.b[i - 1][None, :]
         if P.skip and P.skip[i - 1]:
-            nubar = nubar + a_saved[P.skip[i - 1] - 1]
+            nubar = nubar + _skip_forward(P, i, a_saved[P.skip[i - 1] - 1])
         nu_hat, s, lo, hi = T.nu_hat[i - 1], T.s[i - 1], T.lo[i - 1], T.hi[i - 1]
         al = D.alpha[i - 1]
         inactive = hi <= 0
@@ -465,12 +495,12 @@ def _lp_model(P: Problem, s: int, k: int, cut_d: Optional[np.ndarray] = None, wi
     """Variables, constraints and objective of Eq. 16 for subdomain s, spec row k.
 
     Variables: x0, then per hidden layer i: x^(i), xhat^(i), z^(i). A skip
-    connection adds -xhat^(m) to its layer's equality rows (R11). Stable
+    connection adds -S xhat^(m) to its layer's equality rows (R11). Stable
     neurons keep their equalities (Eq. 9-10) and fixed z (R5); unstable ones
     get Eq. 4-7 and 0 <= z <= 1. Split rows are extra constraints
     (-x <= 0 for x >= 0, x <= 0 for x <= 0). The objective is
-    c^T (W^(L) xhat^(L-1) + b^(L)), plus c^T xhat^(m) when the last layer
-    adds xhat^(m).
+    c^T (W^(L) xhat^(L-1) + b^(L)), plus c^T S xhat^(m) when the last layer
+    adds S xhat^(m).
     """
     dims = P.dims
     off = [0]
@@ -520,14 +550,18 @@ def _lp_model(P: Problem, s: int, k: int, cut_d: Optional[np.ndarray] = None, wi
         prev = (lambda j: vx(0, j)) if i == 1 else (lambda j, i=i: vxh(i - 1, j))
         m = P.skip[i - 1] - 1 if P.skip and P.skip[i - 1] else -1
         src = None if m < 0 else ((lambda j: vx(0, j)) if m == 0 else (lambda j, m=m: vxh(m, j)))
+        Sk = P.skip_map[i - 1] if src is not None and P.skip_map else None
+        Sd = None if Sk is None else (Sk.toarray() if sp.issparse(Sk) else Sk)
         lo = P.sub_lo[i - 1][s]
         hi = P.sub_hi[i - 1][s]
         for j in range(dims[i]):
             row = [(vx(i, j), 1.0)]
             nz = np.nonzero(Wd[j])[0]
             row += [(prev(q), -Wd[j, q]) for q in nz]
-            if src is not None:
+            if src is not None and Sd is None:
                 row.append((src(j), -1.0))
+            elif src is not None:
+                row += [(src(q), -Sd[j, q]) for q in np.nonzero(Sd[j])[0]]
             eq(row, P.b[i - 1][j])
             if hi[j] <= 0:                       # inactive: xhat = 0, z = 0
                 lb[vxh(i, j)] = ub[vxh(i, j)] = 0.0
@@ -569,8 +603,9 @@ def _lp_model(P: Problem, s: int, k: int, cut_d: Optional[np.ndarray] = None, wi
         cvec[vxh(P.L - 1, j) if P.L > 1 else vx(0, j)] += coef[j]
     if P.skip and P.skip[P.L - 1]:
         m = P.skip[P.L - 1] - 1
+        sc = _through_skip(P, P.L, P.spec[k][None, :])[0]       # c^T S
         for j in range(dims[m]):
-            cvec[vxh(m, j) if m > 0 else vx(0, j)] += P.spec[k][j]
+            cvec[vxh(m, j) if m > 0 else vx(0, j)] += sc[j]
     const = float(P.spec[k] @ P.b[P.L - 1])
     Aeq = sp.csr_matrix((Aeq_v, (Aeq_r, Aeq_c)), shape=(neq[0], nvar)) if neq[0] else None
     Aub = sp.csr_matrix((Aub_v, (Aub_r, Aub_c)), shape=(nub[0], nvar)) if nub[0] else None

@@ -53,6 +53,9 @@ class Layer:
     stride: int = 1
     pad: int = 0
     skip: int = 0      # 0: none; s >= 1: the layer adds xhat^(s-1) (s = 1: the input x) to W x + b
+    # the map applied to xhat^(s-1) before it is added (a projection shortcut,
+    # S xhat^(s-1) + b_S); None: the identity
+    shortcut: Optional["Layer"] = None
 
     @property
     def d_in(self) -> int:
@@ -175,7 +178,8 @@ def forward_all(net: Network, x: np.ndarray):
     for i, ly in enumerate(net.layers):
         z = layer_apply(ly, post[-1]) + ly.b[None, :]
         if ly.skip:
-            z = z + post[ly.skip - 1]
+            src = post[ly.skip - 1]
+            z = z + (src if ly.shortcut is None else layer_apply(ly.shortcut, src) + ly.shortcut.b[None, :])
         pre.append(z)
         post.append(np.maximum(z, 0.0))
     return pre
@@ -239,9 +243,13 @@ def interval_bounds(net: Network, x_lo: np.ndarray, x_hi: np.ndarray):
     for i, ly in enumerate(net.layers[:-1]):
         cc = layer_apply(ly, c[None, :])[0] + ly.b
         rr = layer_apply(ly, r[None, :], np.abs(ly.W))[0]
-        if ly.skip:
+        if ly.skip and ly.shortcut is None:
             cc = cc + cs[ly.skip - 1]
             rr = rr + rs[ly.skip - 1]
+        elif ly.skip:
+            sc = ly.shortcut
+            cc = cc + layer_apply(sc, cs[ly.skip - 1][None, :])[0] + sc.b
+            rr = rr + layer_apply(sc, rs[ly.skip - 1][None, :], np.abs(sc.W))[0]
         lo, hi = cc - rr, cc + rr
         lo_list.append(lo)
         hi_list.append(hi)
@@ -409,21 +417,28 @@ def mlp_residual(seed: int = SEED_BASE + 6, width: int = 16, d0: int = 8, blocks
                    (0, max_splits), dict(n_cuts=n_cuts, min_vars=2, max_vars=4, hidden_only=True))
 
 
-def make_resnet(rng, hw: int = 32, ch=(16, 32), fc: int = 100, d_out: int = 10) -> Network:
-    """Residual CNN of two identity-shortcut blocks (the shape of the residual
-    CIFAR models, App. C.1, with identity shortcuts only):
-    3 x hw x hw -> conv ch0 3x3 s2 p1 -> block(ch0) -> conv ch1 3x3 s2 p1 ->
-    block(ch1) -> FC fc -> FC d_out, where block(c) is conv c 3x3 s1 p1 then
-    conv c 3x3 s1 p1 whose output adds the block input. The second conv of a
-    block is scaled by 1/2."""
-    layers = []
-    shape = (3, hw, hw)
-    for c in ch:
-        down = make_conv(rng, shape, c, 3, 2, 1)
-        a = make_conv(rng, down.out_shape, c, 3, 1, 1)
-        b = make_conv(rng, a.out_shape, c, 3, 1, 1)
-        layers += [down, a, dataclasses.replace(b, W=0.5 * b.W, skip=len(layers) + 2)]  # adds xhat of `down`
-        shape = b.out_shape
+def make_resnet(rng, hw: int = 32, stem: int = 8, blocks=((16, 2), (16, 1)), fc: int = 100,
+                d_out: int = 10) -> Network:
+    """Residual CNN shaped like the residual CIFAR models (App. C.1):
+    3 x hw x hw -> conv stem 3x3 s2 p1 -> residual blocks -> FC fc -> FC d_out.
+    A block (c, stride) is conv c 3x3 s(stride) p1, then conv c 3x3 s1 p1
+    whose output adds the block input: through the identity when channels and
+    size are unchanged, else through a 1x1 convolution with the block's stride
+    (ResBlock(a, b)). The second conv of a block is scaled by 1/2. The
+    defaults give the resnet2b shape (FC 1024 -> 100); stem 16 with blocks
+    ((32, 2), (32, 2)) gives the resnet4b shape (FC 512 -> 100)."""
+    layers = [make_conv(rng, (3, hw, hw), stem, 3, 2, 1)]
+    shape = layers[0].out_shape
+    for c, stride in blocks:
+        n = len(layers)                       # the block adds xhat^(n), its input
+        first = make_conv(rng, shape, c, 3, stride, 1)
+        second = make_conv(rng, first.out_shape, c, 3, 1, 1)
+        sc = None
+        if c != shape[0] or stride != 1:
+            sc = make_conv(rng, shape, c, 1, stride, 0)
+            sc = dataclasses.replace(sc, b=np.zeros(sc.d_out))      # one bias per output (the second conv's)
+        layers += [first, dataclasses.replace(second, W=0.5 * second.W, skip=n + 1, shortcut=sc)]
+        shape = second.out_shape
     d = int(np.prod(shape))
     W1 = rng.normal(0.0, math.sqrt(1.0 / d), size=(fc, d))
     b1 = rng.normal(0.0, math.sqrt(0.1), size=fc)
@@ -432,13 +447,16 @@ def make_resnet(rng, hw: int = 32, ch=(16, 32), fc: int = 100, d_out: int = 10) 
     return Network(layers + [Layer(DENSE, W1, b1, (d,), (fc,)), Layer(DENSE, W2, b2, (fc,), (d_out,))])
 
 
-def cnn_resnet(seed: int = SEED_BASE + 7, hw: int = 32, ch=(16, 32), fc: int = 100, eps: float = 2.0 / 255.0,
-               n_spec: int = 9, n_sub: int = 2048, n_cuts: int = 500, max_splits: int = 12) -> Instance:
-    """Residual CNN (make_resnet), eps 2/255, 9 spec rows, 1-12 splits, cuts of 2-16 variables."""
+def cnn_resnet(seed: int = SEED_BASE + 7, hw: int = 32, stem: int = 8, blocks=((16, 2), (16, 1)), fc: int = 100,
+               eps: float = 2.0 / 255.0, n_spec: int = 9, n_sub: int = 2048, n_cuts: int = 500,
+               max_splits: int = 12) -> Instance:
+    """Residual CNN (make_resnet; resnet2b shape by default), eps 2/255, 9 spec rows, 1-12 splits, cuts of
+    2-16 variables."""
     rng = np.random.default_rng(seed)
-    net = make_resnet(rng, hw, ch, fc)
+    net = make_resnet(rng, hw, stem, blocks, fc)
     x0 = rng.random(3 * hw * hw)
-    return _finish(f"resnet_3x{hw}x{hw}_c{ch[0]}_c{ch[1]}_fc{fc}_fc10", rng, net, x0, eps, n_spec, n_sub,
+    tag = "_".join(f"b{c}s{st}" for c, st in blocks)
+    return _finish(f"resnet_3x{hw}x{hw}_c{stem}_{tag}_fc{fc}_fc10", rng, net, x0, eps, n_spec, n_sub,
                    (1, max_splits), dict(n_cuts=n_cuts, min_vars=2, max_vars=16, span_layers=True, need_z=True,
                                          p_input=0.99))
 

@@ -1,15 +1,17 @@
 """Pins of the oracle's skip connections (residual networks, R11).
 
-A skip x^(k) = W^(k) xhat^(k-1) + b^(k) + xhat^(m) changes no arithmetic of
-Theorem 3.1 other than adding nu^(k) to the coefficient of xhat^(m). The
-pins below hold the oracle to facts written without that code path:
+A skip x^(k) = W^(k) xhat^(k-1) + b^(k) + S xhat^(m) (S the identity or a
+projection shortcut) changes no arithmetic of Theorem 3.1 other than adding
+S^T nu^(k) to the coefficient of xhat^(m). The pins below hold the oracle to
+facts written without that code path:
 
 * the same function as a plain feed-forward network: xhat^(m) >= 0 rides
   through the layers in between on extra neurons with identity rows and zero
   bias, whose pre-activation bounds [max(l,0), max(u,0)] make them stable
   (active, or inactive where xhat^(m) = 0), so Theorem 3.1 treats them
   exactly and the bound, its gradient and the LP optimum of Eq. 16 are the
-  plain network's; a skip from the layer's own input is W^(k) + I;
+  plain network's (S on the carried columns of layer k); a skip from the
+  layer's own input is W^(k) + S;
 * weak duality against the LP and MIP of the residual network;
 * soundness on sampled inputs pushed through the network's forward pass;
 * central differences of the bound.
@@ -25,7 +27,7 @@ from paper_2208_05740_gb300 import synth
 
 def _dense(ly):
     if ly.kind == synth.DENSE:
-        return np.asarray(ly.W, np.float64)
+        return np.array(ly.W, np.float64)        # a copy: the plain network is edited in place
     return O.conv_matrix(np.asarray(ly.W, np.float64), ly.in_shape, ly.out_shape, ly.stride, ly.pad).toarray()
 
 
@@ -46,8 +48,13 @@ def plain_equivalent(inst):
         if not s:
             continue
         m = s - 1
+        sc = net.layers[k - 1].shortcut
+        d_m = widths[m - 1] if m >= 1 else net.layers[0].d_in
+        S = np.eye(widths[k - 1], d_m) if sc is None else _dense(sc)
+        if sc is not None:
+            bs[k - 1] = bs[k - 1] + np.asarray(sc.b, np.float64)
         if m == k - 1:
-            Ws[k - 1] = Ws[k - 1] + np.eye(Ws[k - 1].shape[0], Ws[k - 1].shape[1])
+            Ws[k - 1][:, :S.shape[1]] += S
             continue
         assert m >= 1, "a skip from the input is only exact as W + I"
         d = widths[m - 1]
@@ -66,7 +73,7 @@ def plain_equivalent(inst):
             lo[t - 1] = np.concatenate([lo[t - 1], np.maximum(inst.inter_lo[m - 1], 0.0)])
             hi[t - 1] = np.concatenate([hi[t - 1], np.maximum(inst.inter_hi[m - 1], 0.0)])
             src_off = row_off
-        Ws[k - 1][:, src_off:src_off + d] += np.eye(Ws[k - 1].shape[0], d)
+        Ws[k - 1][:, src_off:src_off + d] += S
     layers = [synth.Layer(synth.DENSE, W, b, (W.shape[1],), (W.shape[0],)) for W, b in zip(Ws, bs)]
     plain = dataclasses.replace(inst, net=synth.Network(layers), inter_lo=lo, inter_hi=hi)
     return plain, widths
@@ -95,6 +102,10 @@ def _with_skip(inst, k, s, scale=1.0):
     return dataclasses.replace(inst, net=net, inter_lo=lo, inter_hi=hi)
 
 
+def _proj(rng, d_out, d_in):
+    return synth.Layer(synth.DENSE, rng.normal(0, 0.3, (d_out, d_in)), rng.normal(0, 0.1, d_out), (d_in,), (d_out,))
+
+
 def _cases():
     yield "blocks", synth.mlp_residual(n_sub=4, n_cuts=8)
     yield "wide_blocks", synth.mlp_residual(seed=synth.SEED_BASE + 61, width=12, d0=6, blocks=3, n_sub=3,
@@ -107,6 +118,17 @@ def _cases():
     net.layers[3] = dataclasses.replace(net.layers[3], W=0.5 * net.layers[3].W, skip=2)   # x^(4) += xhat^(1)
     yield "three_back", synth._finish("three_back", rng, net, rng.random(8), 0.1, 2, 3, (0, 2),
                                       dict(n_cuts=8, min_vars=2, max_vars=4, hidden_only=True))
+    # dense projection shortcuts between layers of different widths
+    rng = np.random.default_rng(synth.SEED_BASE + 65)
+    net = synth.make_mlp(rng, [8, 16, 12, 10, 3])
+    net.layers[0] = dataclasses.replace(net.layers[0], skip=1, shortcut=_proj(rng, 16, 8))    # x^(1) += S x
+    net.layers[1] = dataclasses.replace(net.layers[1], skip=2, shortcut=_proj(rng, 12, 16))   # x^(2) += S xhat^(1)
+    net.layers[2] = dataclasses.replace(net.layers[2], skip=2, shortcut=_proj(rng, 10, 16))   # x^(3) += S xhat^(1)
+    yield "projections", synth._finish("proj", rng, net, rng.random(8), 0.1, 2, 3, (0, 2),
+                                       dict(n_cuts=8, min_vars=2, max_vars=4, hidden_only=True))
+    # a residual CNN with a 1x1 stride-2 convolution shortcut (the resnet2b block structure, small)
+    yield "resnet_small", synth.cnn_resnet(hw=8, stem=4, blocks=((8, 2), (8, 1)), fc=16, n_spec=2, n_sub=2,
+                                           n_cuts=6, max_splits=2)
 
 
 @pytest.mark.parametrize("name,inst", list(_cases()))
@@ -126,12 +148,18 @@ def test_residual_bound_equals_its_plain_network(name, inst):
         np.testing.assert_allclose(G.gamma, H.gamma, rtol=1e-10, atol=1e-10)
 
 
-def test_skip_from_the_input_and_into_the_spec_layer():
-    """m = 0 on layer 1 (x^(1) = (W + I) x + b) and a skip on the last layer."""
+@pytest.mark.parametrize("projection", [False, True])
+def test_skip_from_the_input_and_into_the_spec_layer(projection):
+    """m = 0 on layer 1 (x^(1) = (W + S) x + b) and a skip on the last layer."""
     rng = np.random.default_rng(synth.SEED_BASE + 63)
-    net = synth.make_mlp(rng, [6, 6, 8, 8, 8])
-    net.layers[0] = dataclasses.replace(net.layers[0], skip=1)
-    net.layers[3] = dataclasses.replace(net.layers[3], skip=3)       # adds xhat^(2) to the output layer
+    if projection:
+        net = synth.make_mlp(rng, [6, 8, 8, 8, 5])
+        net.layers[0] = dataclasses.replace(net.layers[0], skip=1, shortcut=_proj(rng, 8, 6))
+        net.layers[3] = dataclasses.replace(net.layers[3], skip=3, shortcut=_proj(rng, 5, 8))
+    else:
+        net = synth.make_mlp(rng, [6, 6, 8, 8, 8])
+        net.layers[0] = dataclasses.replace(net.layers[0], skip=1)
+        net.layers[3] = dataclasses.replace(net.layers[3], skip=3)       # adds xhat^(2) to the output layer
     x0 = rng.random(6)
     inst = synth._finish("skip_io", rng, net, x0, 0.1, 2, 3, (0, 2),
                          dict(n_cuts=6, min_vars=2, max_vars=3, hidden_only=True))
@@ -150,9 +178,16 @@ def test_skip_from_the_input_and_into_the_spec_layer():
             assert abs(a - b) <= 1e-7 * max(1.0, abs(a))
 
 
-@pytest.mark.parametrize("seed", [0, 1])
-def test_residual_weak_duality_and_lp_of_the_plain_network(seed):
-    inst = synth.mlp_residual(seed=synth.SEED_BASE + 70 + seed, n_sub=3, n_cuts=6)
+def _duality_cases():
+    yield "blocks0", synth.mlp_residual(seed=synth.SEED_BASE + 70, n_sub=3, n_cuts=6)
+    yield "blocks1", synth.mlp_residual(seed=synth.SEED_BASE + 71, n_sub=3, n_cuts=6)
+    cases = dict(_cases())
+    yield "projections", cases["projections"]
+    yield "resnet_small", cases["resnet_small"]
+
+
+@pytest.mark.parametrize("name,inst", list(_duality_cases()))
+def test_residual_weak_duality_and_lp_of_the_plain_network(name, inst):
     P = O.build_problem(inst)
     Q = O.build_problem(plain_equivalent(inst)[0])
     g, _ = O.optimize(P, O.default_duals(P), 20, 0.1, 0.1, 0.1)
