@@ -73,19 +73,26 @@ enum { GCP_PGA = 0, GCP_ADAM = 1 };
  * b has d_out entries (per output element, CHW order for conv2d).
  * skip: 0 for a plain layer; s >= 1 adds the post-activation xhat^(s-1) of an
  *       earlier layer (s = 1: the input x; s = i: the layer's own input) to
- *       the layer's output, x^(i) = W^(i) xhat^(i-1) + b^(i) + xhat^(s-1): the
- *       identity shortcut of a residual block (the residual CIFAR models of
- *       Sec. 4 / App. C.1). Needs d_{s-1} = d_out; each xhat feeds at most one
- *       skip. The skip's multiplier nu^(i) joins the coefficient of
- *       xhat^(s-1) in the backward pass (Theorem 3.1 with the identity as one
- *       more linear map). Zero-initialise the struct to leave it off. */
-typedef struct {
+ *       the layer's output, x^(i) = W^(i) xhat^(i-1) + b^(i) + S xhat^(s-1):
+ *       the shortcut of a residual block (ResBlock of the residual CIFAR
+ *       models, Sec. 4 / App. C.1). Each xhat feeds at most one skip. The
+ *       skip's multiplier nu^(i) adds S^T nu^(i) to the coefficient of
+ *       xhat^(s-1) in the backward pass (Theorem 3.1 with S as one more
+ *       linear map).
+ * shortcut: NULL for the identity (S = I, needs d_{s-1} = d_out), else the
+ *       projection S as a layer of its own (dense, or conv2d such as a 1x1
+ *       stride-2 convolution; dense on the last layer) with d_in = d_{s-1},
+ *       d_out = this layer's d_out, b = NULL (b^(i) carries the sum's bias),
+ *       skip 0 and no shortcut. Read during gcp_init_net only.
+ * Zero-initialise the struct to leave skip and shortcut off. */
+typedef struct gcp_layer_desc {
   int32_t kind;
   int32_t d_in, d_out;
   int32_t c_in, h_in, w_in, c_out, h_out, w_out, k, stride, pad;
   const double* W;
   const double* b;
   int32_t skip;
+  const struct gcp_layer_desc* shortcut;
 } gcp_layer_desc;
 
 /* Branch-and-bound subdomains as neuron split sets (App. B), CSR by

@@ -277,52 +277,78 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
   net->ctx = &c;
   net->L = n_layers;
   net->K = n_spec;
-  for (int i = 0; i < n_layers; ++i) {
-    const gcp_layer_desc& d = layers[i];
-    LayerGeom g{};
+  auto parse = [&](const gcp_layer_desc& d, const char* what, int i, LayerGeom& g) -> gcp_status {
+    g = LayerGeom{};
     g.kind = d.kind;
     g.d_in = d.d_in;
     g.d_out = d.d_out;
     if (d.kind == GCP_DENSE) {
-      if (d.d_in <= 0 || d.d_out <= 0) return c.fail(GCP_EINVAL, "layer %d: bad dense shape", i + 1);
+      if (d.d_in <= 0 || d.d_out <= 0) return c.fail(GCP_EINVAL, "%s %d: bad dense shape", what, i);
     } else if (d.kind == GCP_CONV2D) {
       g.c_in = d.c_in; g.h_in = d.h_in; g.w_in = d.w_in; g.c_out = d.c_out; g.h_out = d.h_out;
       g.w_out = d.w_out; g.k = d.k; g.stride = d.stride; g.pad = d.pad;
       if (d.c_in <= 0 || d.h_in <= 0 || d.w_in <= 0 || d.c_out <= 0 || d.k <= 0 || d.stride <= 0 || d.pad < 0 ||
           d.h_out != (d.h_in + 2 * d.pad - d.k) / d.stride + 1 || d.w_out != (d.w_in + 2 * d.pad - d.k) / d.stride + 1 ||
           d.d_in != d.c_in * d.h_in * d.w_in || d.d_out != d.c_out * d.h_out * d.w_out || d.h_out <= 0 || d.w_out <= 0)
-        return c.fail(GCP_EINVAL, "layer %d: inconsistent conv2d geometry", i + 1);
-      if (i == n_layers - 1) return c.fail(GCP_EINVAL, "the last (spec) layer must be dense");
+        return c.fail(GCP_EINVAL, "%s %d: inconsistent conv2d geometry", what, i);
     } else {
-      return c.fail(GCP_EINVAL, "layer %d: unknown kind %d", i + 1, d.kind);
+      return c.fail(GCP_EINVAL, "%s %d: unknown kind %d", what, i, d.kind);
     }
+    if (!d.W) return c.fail(GCP_EINVAL, "%s %d: null W", what, i);
+    return GCP_OK;
+  };
+  for (int i = 0; i < n_layers; ++i) {
+    const gcp_layer_desc& d = layers[i];
+    LayerGeom g;
+    if (gcp_status e = parse(d, "layer", i + 1, g)) return e;
+    if (d.kind == GCP_CONV2D && i == n_layers - 1) return c.fail(GCP_EINVAL, "the last (spec) layer must be dense");
     if (i > 0 && d.d_in != layers[i - 1].d_out) return c.fail(GCP_EINVAL, "layer %d: d_in mismatch", i + 1);
-    if (!d.W || !d.b) return c.fail(GCP_EINVAL, "layer %d: null W or b", i + 1);
+    if (!d.b) return c.fail(GCP_EINVAL, "layer %d: null b", i + 1);
     net->geom.push_back(g);
   }
   net->dims.push_back(layers[0].d_in);
   for (int i = 0; i < n_layers; ++i) net->dims.push_back(layers[i].d_out);
   const int L = n_layers;
   const int d0 = net->dims[0], dL = net->dims[L];
-  // skip connections: x^(i) += xhat^(s-1), one consumer per source
+  // skip connections: x^(i) += S xhat^(s-1), one consumer per source; the
+  // projections S become maps L+1, L+2, ... after the layers
   net->skip.assign(L, 0);
   net->consumer.assign(L, 0);
+  net->sc_map.assign(L, 0);
   net->skip_off = last_skip_off;
-  if (last_skip_off < 0 || (last_skip_off > 0 && layers[L - 1].skip == 0))
-    return c.fail(GCP_EINVAL, "skip offset without a skip on the last layer");
+  std::vector<const gcp_layer_desc*> maps;
+  for (int i = 0; i < L; ++i) maps.push_back(&layers[i]);
+  if (last_skip_off < 0 || (last_skip_off > 0 && (layers[L - 1].skip == 0 || layers[L - 1].shortcut)))
+    return c.fail(GCP_EINVAL, "skip offset without an identity skip on the last layer");
   for (int i = 1; i <= L; ++i) {
-    const int s = layers[i - 1].skip;
-    if (s == 0) continue;
+    const gcp_layer_desc& d = layers[i - 1];
+    const int s = d.skip;
+    if (s == 0) {
+      if (d.shortcut) return c.fail(GCP_EINVAL, "layer %d: shortcut without a skip", i);
+      continue;
+    }
     const int off = i == L ? last_skip_off : 0;
     if (s < 0 || s > i) return c.fail(GCP_EINVAL, "layer %d: skip %d must name an earlier xhat (1..%d)", i, s, i);
     const int m = s - 1;
-    if (i < L ? net->dims[m] != net->dims[i] : (int64_t)off + net->dims[i] > net->dims[m])
+    if (const gcp_layer_desc* sd = d.shortcut) {
+      LayerGeom g;
+      if (gcp_status e = parse(*sd, "shortcut of layer", i, g)) return e;
+      if (sd->d_in != net->dims[m] || sd->d_out != net->dims[i] || sd->b || sd->skip || sd->shortcut ||
+          (i == L && sd->kind != GCP_DENSE))
+        return c.fail(GCP_EINVAL, "layer %d: the shortcut maps xhat^(%d) (%d) to %d outputs, with b = NULL, no skip "
+                      "of its own, dense on the last layer", i, m, net->dims[m], net->dims[i]);
+      net->geom.push_back(g);
+      maps.push_back(sd);
+      net->sc_map[i - 1] = (int)maps.size();
+    } else if (i < L ? net->dims[m] != net->dims[i] : (int64_t)off + net->dims[i] > net->dims[m]) {
       return c.fail(GCP_EINVAL, "layer %d: skip from xhat^(%d) of width %d does not fit width %d", i, m,
                     net->dims[m], net->dims[i]);
+    }
     if (net->consumer[m]) return c.fail(GCP_EINVAL, "xhat^(%d) feeds two skips (layers %d and %d)", m, net->consumer[m], i);
     net->skip[i - 1] = s;
     net->consumer[m] = i;
   }
+  const int n_maps = (int)maps.size();
   int64_t nh = 0;
   for (int i = 1; i < L; ++i) nh += net->dims[i];
   if (nh > 0 && (!inter_lo || !inter_hi)) return c.fail(GCP_EINVAL, "intermediate bounds required");
@@ -341,14 +367,16 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
     if (!dst) return st;                       \
     net->owned.push_back((void*)dst);          \
   } while (0)
-  for (int i = 0; i < L; ++i) {
-    const gcp_layer_desc& d = layers[i];
+  const std::vector<double> no_bias((size_t)*std::max_element(net->dims.begin(), net->dims.end()), 0.0);
+  for (int i = 0; i < n_maps; ++i) {
+    const gcp_layer_desc& d = *maps[i];
     const LayerGeom& g = net->geom[i];
+    const double* bias = d.b ? d.b : no_bias.data();    // projections carry no bias
     size_t nw = g.kind == GCP_DENSE ? (size_t)g.d_out * g.d_in : (size_t)g.c_out * g.c_in * g.k * g.k;
     for (size_t q = 0; q < nw; ++q)
-      if (!std::isfinite(d.W[q])) return c.fail(GCP_EINVAL, "layer %d: non-finite weight", i + 1);
+      if (!std::isfinite(d.W[q])) return c.fail(GCP_EINVAL, "map %d: non-finite weight", i + 1);
     for (int q = 0; q < g.d_out; ++q)
-      if (!std::isfinite(d.b[q])) return c.fail(GCP_EINVAL, "layer %d: non-finite bias", i + 1);
+      if (!std::isfinite(bias[q])) return c.fail(GCP_EINVAL, "layer %d: non-finite bias", i + 1);
     double *w64, *wt64 = nullptr, *b64;
     float *w32, *wt32 = nullptr, *b32, *w32h = nullptr, *w32l = nullptr, *wt32h = nullptr, *wt32l = nullptr;
     __nv_bfloat16 *w16, *wt16 = nullptr;
@@ -437,8 +465,8 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
     net->WTsl.push_back(sl);
     net->CF16.push_back(cf16); net->CT16.push_back(ct16);
     net->cf_kp.push_back(cfk); net->cf_np.push_back(cfn); net->ct_kp.push_back(ctk); net->ct_np.push_back(ctn);
-    UP(b64, double, d.b, g.d_out);
-    auto bf = to_f32(d.b, g.d_out);
+    UP(b64, double, bias, g.d_out);
+    auto bf = to_f32(bias, g.d_out);
     UP(b32, float, bf.data(), g.d_out);
     net->W64.push_back(w64); net->WT64.push_back(wt64); net->b64.push_back(b64);
     net->W32.push_back(w32); net->WT32.push_back(wt32); net->b32.push_back(b32);
@@ -454,10 +482,6 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
   std::vector<double> negc((size_t)n_spec * dL);
   for (size_t q = 0; q < negc.size(); ++q) negc[q] = -spec_c[q];
   UP(net->negC64, double, negc.data(), negc.size());
-  {
-    auto nf = to_f32(negc.data(), negc.size());
-    UP(net->negC32, float, nf.data(), nf.size());
-  }
   // y^(L-1) = W^(L)^T nu^(L) = -W^(L)^T c_k and c_k^T b^(L), per spec row
   const gcp_layer_desc& last = layers[L - 1];
   const int dl1 = net->dims[L - 1];
@@ -468,8 +492,30 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
       if (cv == 0.0) continue;   // sparse specs (unit rows) skip the zero columns
       cb[k] += cv * last.b[q];
       for (int j = 0; j < dl1; ++j) yl[(size_t)k * dl1 + j] -= cv * last.W[(size_t)q * dl1 + j];
-      // a skip from the last layer's own input: + the multiplier -c_k itself
-      if (net->skip[L - 1] == L) yl[(size_t)k * dl1 + net->skip_off + q] -= cv;
+    }
+  }
+  // a skip on the last layer adds S^T nu^(L) = -S^T c_k (S = I: -c_k at the
+  // skip's offset) to y^(m); from the last hidden layer it folds into y^(L-1)
+  if (const int sL = net->skip[L - 1]) {
+    const int m = sL - 1, dm = net->dims[m];
+    std::vector<double> sk((size_t)n_spec * dm, 0.0);
+    for (int k = 0; k < n_spec; ++k)
+      for (int q = 0; q < dL; ++q) {
+        const double cv = spec_c[(size_t)k * dL + q];
+        if (cv == 0.0) continue;
+        if (!last.shortcut) {
+          sk[(size_t)k * dm + net->skip_off + q] -= cv;
+        } else {
+          const double* Srow = last.shortcut->W + (size_t)q * dm;
+          for (int j = 0; j < dm; ++j) sk[(size_t)k * dm + j] -= cv * Srow[j];
+        }
+      }
+    if (m == L - 1) {
+      for (size_t q = 0; q < yl.size(); ++q) yl[q] += sk[q];
+    } else {
+      UP(net->SK64, double, sk.data(), sk.size());
+      auto skf = to_f32(sk.data(), sk.size());
+      UP(net->SK32, float, skf.data(), skf.size());
     }
   }
   UP(net->YL64, double, yl.data(), yl.size());
@@ -922,15 +968,16 @@ struct TcOps<__nv_bfloat16> {
 
 // Does the backward product through W^(i) (K = d_i) / the forward product
 // through W^(i) (K = d_{i-1}) run on the tensor cores?
+// (i: a layer, or the map index of a projection shortcut)
 template <typename Top>
 static bool tc_bwd(const Batch& b, int i) {
-  const Net& n = *b.net;
-  return b.tc && n.geom[i - 1].kind == GCP_DENSE && TcOps<Top>::ok(n.dims[i]);
+  const LayerGeom& g = b.net->geom[i - 1];
+  return b.tc && g.kind == GCP_DENSE && TcOps<Top>::ok(g.d_out);
 }
 template <typename Top>
 static bool tc_fwd(const Batch& b, int i) {
-  const Net& n = *b.net;
-  return b.tc && i < n.L && n.geom[i - 1].kind == GCP_DENSE && TcOps<Top>::ok(n.dims[i - 1]);
+  const LayerGeom& g = b.net->geom[i - 1];
+  return b.tc && i != b.net->L && g.kind == GCP_DENSE && TcOps<Top>::ok(g.d_in);
 }
 
 // Linear backward step y^(i-1) = W^(i)^T nu^(i) for all rows.
@@ -966,41 +1013,57 @@ static void lin_forward(cudaStream_t st, const Batch& b, int i, const Top* a, co
   else conv_fwd<Top, T>(st, b.R, g, WSel<Top>::W(net, i), a, out);
 }
 
-// Skip connections in the backward pass (Theorem 3.1 with the identity as one
-// more linear map): once y^(i-1) = W^(i)^T nu^(i) is formed, nu^(i) of a skip
-// from xhat^(i-1) joins it; nu^(i) of a skip from further back is parked until
-// its y^(m) exists; y^(i-1) then takes what was parked for it, or -c_k when
-// the last layer adds xhat^(i-1) (from L-1 it is already folded into YL).
+// Skip connections in the backward pass (Theorem 3.1 with the shortcut S as
+// one more linear map): once y^(i-1) = W^(i)^T nu^(i) is formed, S^T nu^(i) of
+// a skip from xhat^(i-1) joins it; that of a skip from further back is parked
+// until its y^(m) exists (nu^(i) itself for the identity, S^T nu^(i) in the
+// chain's accumulation type for a projection); y^(i-1) then takes what was
+// parked for it, or -S^T c_k when the last layer adds xhat^(i-1) (from L-1
+// that is already folded into YL).
 template <typename Top, typename T>
-static gcp_status skip_backward(Ctx& c, Batch& b, cudaStream_t st, int i, const Top* nu, T* y, const T* negC) {
+static gcp_status skip_backward(Ctx& c, Batch& b, cudaStream_t st, int i, const Top* nu, T* y, const T* SK) {
   const Net& net = *b.net;
   const int L = net.L;
+  const int64_t R = b.R;
   gcp_status s = GCP_OK;
-  const int si = net.skip[i - 1];
-  if (si == i) {
-    skip_add<Top, T>(st, b.R, net.dims[i], net.dims[i], 0, nu, 0, y);
-  } else if (si) {
-    Top* park = (Top*)b.ws("skip" + std::to_string(si - 1), (size_t)b.R * net.dims[si - 1] * sizeof(Top), &s);
-    if (!park) return s;
-    cudaMemcpyAsync(park, nu, (size_t)b.R * net.dims[i] * sizeof(Top), cudaMemcpyDeviceToDevice, st);
+  const int si = net.skip[i - 1], sc = net.sc_map[i - 1];
+  if (si) {
+    const int m = si - 1, dm = net.dims[m];
+    if (sc) {
+      T* dst = si == i ? (T*)b.ws("skip_tmp", (size_t)R * b.dmax() * sizeof(T), &s)
+                       : (T*)b.ws("skipT" + std::to_string(m), (size_t)R * dm * sizeof(T), &s);
+      if (!dst) return s;
+      lin_backward<Top, T>(st, b, sc, nu, nullptr, dst);
+      if (si == i) skip_add<T, T>(st, R, dm, dm, 0, dst, 0, y);
+    } else if (si == i) {
+      skip_add<Top, T>(st, R, dm, dm, 0, nu, 0, y);
+    } else {
+      Top* park = (Top*)b.ws("skip" + std::to_string(m), (size_t)R * dm * sizeof(Top), &s);
+      if (!park) return s;
+      cudaMemcpyAsync(park, nu, (size_t)R * dm * sizeof(Top), cudaMemcpyDeviceToDevice, st);
+    }
   }
-  const int k = net.consumer[i - 1];
+  const int k = net.consumer[i - 1], dm = net.dims[i - 1];
   if (k == L && i - 1 < L - 1) {
-    skip_add<T, T>(st, b.R, net.dims[L], net.dims[i - 1], net.skip_off, negC, b.K, y);
-  } else if (k > i && k < L) {
-    const Top* park = (const Top*)b.ws("skip" + std::to_string(i - 1), (size_t)b.R * net.dims[i - 1] * sizeof(Top), &s);
+    skip_add<T, T>(st, R, dm, dm, 0, SK, b.K, y);
+  } else if (k > i && k < L && net.sc_map[k - 1]) {
+    const T* park = (const T*)b.ws("skipT" + std::to_string(i - 1), (size_t)R * dm * sizeof(T), &s);
     if (!park) return s;
-    skip_add<Top, T>(st, b.R, net.dims[i - 1], net.dims[i - 1], 0, park, 0, y);
+    skip_add<T, T>(st, R, dm, dm, 0, park, 0, y);
+  } else if (k > i && k < L) {
+    const Top* park = (const Top*)b.ws("skip" + std::to_string(i - 1), (size_t)R * dm * sizeof(Top), &s);
+    if (!park) return s;
+    skip_add<Top, T>(st, R, dm, dm, 0, park, 0, y);
   }
   return GCP_OK;
 }
 
 template <typename T>
-static const T* neg_spec(const Net& n);
+static const T* spec_skip(const Net& n);
 template <>
-const double* neg_spec<double>(const Net& n) { return n.negC64; }
+const double* spec_skip<double>(const Net& n) { return n.SK64; }
 template <>
-const float* neg_spec<float>(const Net& n) { return n.negC32; }
+const float* spec_skip<float>(const Net& n) { return n.SK32; }
 
 // Evaluate g for all rows at the batch's duals. with_adjoint_start: also write
 // a0 = -seed*x* into the operand buffer and the input-layer cut entries into E.
@@ -1049,7 +1112,7 @@ gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, 
     relax_eval<T, Top>(st, a);
     poff += (net.dims[i] + kChunk - 1) / kChunk;
     lin_backward<Top, T>(st, b, i, nu, a.nu_lo, y);
-    s = skip_backward<Top, T>(c, b, st, i, nu, y, neg_spec<T>(net));
+    s = skip_backward<Top, T>(c, b, st, i, nu, y, spec_skip<T>(net));
     if (s) return s;
   }
   ConcArgs<T, Top> ca{};
@@ -1129,7 +1192,14 @@ gcp_status run_adjoint(Ctx& c, Batch& b, cudaStream_t st, const StepArgs<T>& ste
         src = (const Top*)b.ws("skip" + std::to_string(si - 1), (size_t)R * net.dims[si - 1] * sizeof(Top), &s);
         if (!src) return s;
       }
-      skip_add<Top, T>(st, R, net.dims[i], net.dims[i], 0, src, 0, y);
+      if (const int sc = net.sc_map[i - 1]) {   // + S a^(m) through the shortcut's own product
+        T* tmp = (T*)b.ws("skip_tmp", (size_t)R * b.dmax() * sizeof(T), &s);
+        if (!tmp) return s;
+        lin_forward<Top, T>(st, b, sc, src, nullptr, tmp);
+        skip_add<T, T>(st, R, net.dims[i], net.dims[i], 0, tmp, 0, y);
+      } else {
+        skip_add<Top, T>(st, R, net.dims[i], net.dims[i], 0, src, 0, y);
+      }
     }
     const T* nuhat = (const T*)b.lazy["nuhat" + std::to_string(i)];
     AdjArgs<T, Top> a{};
@@ -1170,6 +1240,7 @@ template <typename Td>
 gcp_status run_certify(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
   const Net& net = *b.net;
   const int L = net.L;
+  const int n_maps = (int)net.geom.size();   // the layers, then the projection shortcuts
   const int64_t R = b.R;
   gcp_status s = GCP_OK;
   double* nu = (double*)b.ws("c_nu", (size_t)R * b.dmax() * 8, &s);
@@ -1178,7 +1249,7 @@ gcp_status run_certify(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
   double* part = (double*)b.ws("c_part", (size_t)b.n_partials() * R * 8, &s);
   if (!nu || !y || !ya || !part) return s;
   bool any_conv = false;
-  for (int i = 0; i < L; ++i) any_conv |= net.geom[i].kind != GCP_DENSE;
+  for (int i = 0; i < n_maps; ++i) any_conv |= net.geom[i].kind != GCP_DENSE;
   float* nuabs = nullptr;
   if (any_conv) {
     nuabs = (float*)b.ws("c_nuabs", (size_t)R * b.dmax() * 4, &s);
@@ -1189,11 +1260,11 @@ gcp_status run_certify(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
   int32_t* nu_ex = nullptr;
   float* sl_sums = nullptr;
   size_t sl_elems = 0, sum_elems = 0;
-  for (int i = 1; i < L; ++i) {
-    const SliceB& sl = net.WTsl[i - 1];
-    if (!b.tc || !sl.planes) continue;
-    sl_elems = std::max(sl_elems, (size_t)sl.s * net.dims[i]);
-    sum_elems = std::max(sum_elems, (size_t)sl.s * net.dims[i - 1]);
+  for (int mi = 1; mi <= n_maps; ++mi) {
+    const SliceB& sl = net.WTsl[mi - 1];
+    if (mi == L || !b.tc || !sl.planes) continue;
+    sl_elems = std::max(sl_elems, (size_t)sl.s * net.geom[mi - 1].d_out);
+    sum_elems = std::max(sum_elems, (size_t)sl.s * net.geom[mi - 1].d_in);
   }
   if (sl_elems) {
     nu_sl = (__nv_bfloat16*)b.ws("c_nu_slices", (size_t)R * sl_elems * 2, &s);
@@ -1201,22 +1272,55 @@ gcp_status run_certify(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
     sl_sums = (float*)b.ws("c_slice_sums", (size_t)R * sum_elems * 4, &s);
     if (!nu_sl || !nu_ex || !sl_sums) return s;
   }
+  // yo = M^T nu for all rows through map mi (a layer or a shortcut) with
+  // yao >= |M|^T |nu|; returns e with |yo - exact| <= e * yao: Higham's
+  // gamma_K for the float64 dot products, the slice bound on the tensor cores
+  auto product = [&](int mi, double* yo, float* yao) -> double {
+    const LayerGeom& g = net.geom[mi - 1];
+    const SliceB& sl = net.WTsl[mi - 1];
+    if (g.kind == GCP_DENSE && b.tc && sl.planes &&
+        gemm_f64_slices(st, R, g.d_in, g.d_out, nu, sl, nu_sl, nu_ex, sl_sums, yo, yao))
+      return sl.cerr;
+    if (g.kind == GCP_DENSE) gemm_nt_abs(st, R, g.d_in, g.d_out, nu, 0, net.WT64[mi - 1], yo, yao);
+    else conv_T_abs(st, R, g, net.W64[mi - 1], net.Wabs32[mi - 1], nu, nuabs, yo, yao);
+    return gamma_n_host(red_len(g));
+  };
+  // adding a term t with |t - exact| <= e_t * ta to y: |fl(y + t) - exact| <=
+  // yerr ya + e_t ta + u (|y| + |t|) <= (max(yerr, e_t) + 2u) (ya + ta), and
+  // ya grows by ta (|t| for an exact t)
+  auto skip_err = [](double e, double e_t) {
+    return std::nextafter(std::max(e, e_t) + std::ldexp(1.0, -52), INFINITY);
+  };
+  std::map<int, double> parked_err;       // error factor of the term parked for y^(m)
   SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp, b.sp_tab};
   // y^(L-1) = W^(L)^T (-c_k), one row per spec row
   const LayerGeom& gl = net.geom[L - 1];
+  const int dL = net.dims[L];
   gemm_nt_abs(st, b.K, gl.d_in, gl.d_out, net.negC64, 0, net.WT64[L - 1], y, ya);
-  // |computed y - exact y| <= yerr * ya elementwise: Higham's gamma_K for the
-  // float64 dot products, the slice bound for the tensor-core product
   double yerr = gamma_n_host(red_len(gl));
-  // a skip adds an exact float64 term t to y: |fl(y + t) - (y_exact + t)| <=
-  // yerr ya + u (|y| + |t|) <= (yerr + 2u) (ya + |t|), and ya grows by |t|
-  auto skip_err = [](double e) { return std::nextafter(e + std::ldexp(1.0, -52), INFINITY); };
-  if (net.skip[L - 1] == L) {
-    skip_add_cert(st, b.K, net.dims[L], net.dims[L - 1], net.skip_off, net.negC64, 0, y, ya);
-    yerr = skip_err(yerr);
+  // a skip on the last layer: -c_k (identity, exact) or -S^T c_k (certified product)
+  double* sk = nullptr;
+  float* ska = nullptr;
+  if (const int sL = net.skip[L - 1]) {
+    const int m = sL - 1, dm = net.dims[m];
+    if (const int sc = net.sc_map[L - 1]) {
+      sk = (double*)b.ws("c_spec_skip", (size_t)b.K * dm * 8, &s);
+      ska = (float*)b.ws("c_spec_skip_abs", (size_t)b.K * dm * 4, &s);
+      if (!sk || !ska) return s;
+      gemm_nt_abs(st, b.K, dm, dL, net.negC64, 0, net.WT64[sc - 1], sk, ska);
+      parked_err[m] = gamma_n_host(dL);
+      if (m == L - 1) {
+        skip_add_cert(st, b.K, dm, dm, 0, sk, ska, 0, y, ya);
+        yerr = skip_err(yerr, parked_err[m]);
+      }
+    } else if (m == L - 1) {
+      skip_add_cert(st, b.K, dL, dm, net.skip_off, net.negC64, nullptr, 0, y, ya);
+      yerr = skip_err(yerr, 0.0);
+    }
   }
   int poff = 0;
   for (int i = L - 1; i >= 1; --i) {
+    const int si = net.skip[i - 1], sc = net.sc_map[i - 1];
     CertArgs<Td> a{};
     a.R = R; a.K = b.K; a.d = net.dims[i]; a.layer = i; a.M = b.M; a.N = b.N;
     a.y = y; a.yabs = ya; a.y_per_spec = (i == L - 1);
@@ -1229,40 +1333,49 @@ gcp_status run_certify(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
     a.csc = csc_of<double>(b, i);
     a.nu_out = nu;
     const LayerGeom& g = net.geom[i - 1];
-    a.nuabs_out = g.kind == GCP_DENSE ? nullptr : nuabs;
+    const bool conv_here = g.kind != GCP_DENSE || (sc && net.geom[sc - 1].kind != GCP_DENSE);
+    a.nuabs_out = conv_here ? nuabs : nullptr;
     a.obj_part = part + (int64_t)poff * R;
     certify_relax<Td>(st, a);
     poff += (net.dims[i] + kChunk - 1) / kChunk;
-    const SliceB& sl = net.WTsl[i - 1];
-    if (g.kind == GCP_DENSE && b.tc && sl.planes &&
-        gemm_f64_slices(st, R, g.d_in, g.d_out, nu, sl, nu_sl, nu_ex, sl_sums, y, ya)) {
-      yerr = sl.cerr;
-    } else if (g.kind == GCP_DENSE) {
-      gemm_nt_abs(st, R, g.d_in, g.d_out, nu, 0, net.WT64[i - 1], y, ya);
-      yerr = gamma_n_host(red_len(g));
-    } else {
-      conv_T_abs(st, R, g, net.W64[i - 1], net.Wabs32[i - 1], nu, nuabs, y, ya);
-      yerr = gamma_n_host(red_len(g));
-    }
+    yerr = product(i, y, ya);
     // skips, as in the chain's backward pass, with the error bound widened
-    const int si = net.skip[i - 1];
-    if (si == i) {
-      skip_add_cert(st, R, net.dims[i], net.dims[i], 0, nu, 0, y, ya);
-      yerr = skip_err(yerr);
-    } else if (si) {
-      double* park = (double*)b.ws("c_skip" + std::to_string(si - 1), (size_t)R * net.dims[si - 1] * 8, &s);
-      if (!park) return s;
-      cudaMemcpyAsync(park, nu, (size_t)R * net.dims[i] * 8, cudaMemcpyDeviceToDevice, st);
+    if (si) {
+      const int m = si - 1, dm = net.dims[m];
+      if (sc) {
+        const std::string nm = si == i ? std::string("c_skip_tmp") : "c_skip" + std::to_string(m);
+        double* ys = (double*)b.ws(nm, (size_t)R * b.dmax() * 8, &s);
+        float* yas = (float*)b.ws(nm + "_abs", (size_t)R * b.dmax() * 4, &s);
+        if (!ys || !yas) return s;
+        const double e = product(sc, ys, yas);
+        if (si == i) {
+          skip_add_cert(st, R, dm, dm, 0, ys, yas, 0, y, ya);
+          yerr = skip_err(yerr, e);
+        } else {
+          parked_err[m] = e;
+        }
+      } else if (si == i) {
+        skip_add_cert(st, R, dm, dm, 0, nu, nullptr, 0, y, ya);
+        yerr = skip_err(yerr, 0.0);
+      } else {
+        double* park = (double*)b.ws("c_skip" + std::to_string(m), (size_t)R * b.dmax() * 8, &s);
+        if (!park) return s;
+        cudaMemcpyAsync(park, nu, (size_t)R * dm * 8, cudaMemcpyDeviceToDevice, st);
+        parked_err[m] = 0.0;
+      }
     }
-    const int k = net.consumer[i - 1];
+    const int k = net.consumer[i - 1], dm = net.dims[i - 1];
     if (k == L && i - 1 < L - 1) {
-      skip_add_cert(st, R, net.dims[L], net.dims[i - 1], net.skip_off, net.negC64, b.K, y, ya);
-      yerr = skip_err(yerr);
+      if (sk) skip_add_cert(st, R, dm, dm, 0, sk, ska, b.K, y, ya);
+      else skip_add_cert(st, R, dL, dm, net.skip_off, net.negC64, nullptr, b.K, y, ya);
+      yerr = skip_err(yerr, sk ? parked_err[i - 1] : 0.0);
     } else if (k > i && k < L) {
-      const double* park = (const double*)b.ws("c_skip" + std::to_string(i - 1), (size_t)R * net.dims[i - 1] * 8, &s);
-      if (!park) return s;
-      skip_add_cert(st, R, net.dims[i - 1], net.dims[i - 1], 0, park, 0, y, ya);
-      yerr = skip_err(yerr);
+      const std::string nm = "c_skip" + std::to_string(i - 1);
+      const double* ys = (const double*)b.ws(nm, (size_t)R * b.dmax() * 8, &s);
+      const float* yas = net.sc_map[k - 1] ? (const float*)b.ws(nm + "_abs", (size_t)R * b.dmax() * 4, &s) : nullptr;
+      if (!ys || (net.sc_map[k - 1] && !yas)) return s;
+      skip_add_cert(st, R, dm, dm, 0, ys, yas, 0, y, ya);
+      yerr = skip_err(yerr, parked_err[i - 1]);
     }
   }
   certify_concretize<Td>(st, R, b.K, b.N, net.dims[0], y, ya, yerr, net.xlo64,

@@ -12,7 +12,8 @@
 // row it is alpha-CROWN. Every value is a certified (outward-rounded) bound,
 // so the result is sound whatever precision the chain runs in. A residual
 // layer keeps its skip in the truncated network: the last layer's skip then
-// adds the rows' own slice of xhat^(m).
+// adds the rows' own slice of xhat^(m) (identity) or the same rows of its
+// projection S.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -28,13 +29,13 @@ double round_down(double x) { return std::nextafter(x, -INFINITY); }
 double round_up(double x) { return std::nextafter(x, INFINITY); }
 
 // rows j0 .. j0+nj-1 of a layer's linear map as a dense [nj, d_in] matrix
-// (a convolution's rows materialised) and their biases
+// (a convolution's rows materialised) and their biases (0 without b)
 void dense_rows(const gcp_layer_desc& d, int j0, int nj, std::vector<double>& W, std::vector<double>& b) {
   W.assign((size_t)nj * d.d_in, 0.0);
   b.resize(nj);
   for (int q = 0; q < nj; ++q) {
     const int j = j0 + q;
-    b[q] = d.b[j];
+    b[q] = d.b ? d.b[j] : 0.0;
     double* row = W.data() + (size_t)q * d.d_in;
     if (d.kind == GCP_DENSE) {
       std::copy(d.W + (size_t)j * d.d_in, d.W + (size_t)(j + 1) * d.d_in, row);
@@ -64,8 +65,14 @@ gcp_status intermediate_bounds(Ctx& c, const gcp_layer_desc* layers, int L, cons
     if (!layers[i].W || !layers[i].b || layers[i].d_in <= 0 || layers[i].d_out <= 0 ||
         (i > 0 && layers[i].d_in != layers[i - 1].d_out))
       return c.fail(GCP_EINVAL, "gcp_intermediate_bounds: layer %d: bad shape or null weights", i + 1);
-  if (layers[0].skip != 0 && (layers[0].skip != 1 || layers[0].d_in != layers[0].d_out))
-    return c.fail(GCP_EINVAL, "gcp_intermediate_bounds: layer 1 can only add the input (skip 1, d_in = d_out)");
+  {
+    const gcp_layer_desc& d = layers[0];
+    const gcp_layer_desc* sc = d.shortcut;
+    if (d.skip != 0 && (d.skip != 1 || (sc ? (sc->d_in != d.d_in || sc->d_out != d.d_out || !sc->W)
+                                           : d.d_in != d.d_out)))
+      return c.fail(GCP_EINVAL, "gcp_intermediate_bounds: layer 1 can only add the input (skip 1) through the "
+                    "identity (d_in = d_out) or a shortcut of its shape");
+  }
   if (p && (p->iters < 0 || p->prec < GCP_FP32 || p->prec > GCP_BF16))
     return c.fail(GCP_EINVAL, "gcp_intermediate_bounds: iters >= 0 and prec FP32 or BF16");
   int64_t total = 0;
@@ -75,20 +82,26 @@ gcp_status intermediate_bounds(Ctx& c, const gcp_layer_desc* layers, int L, cons
   // hidden layer 1: interval image of the box, each product and sum rounded outwards
   {
     const gcp_layer_desc& d = layers[0];
+    std::vector<double> S, bs;
     for (int j0 = 0; j0 < d.d_out; j0 += kBoundRows) {
       const int nj = std::min(kBoundRows, d.d_out - j0);
       dense_rows(d, j0, nj, W, b);
+      if (d.skip == 1 && d.shortcut) dense_rows(*d.shortcut, j0, nj, S, bs);
       for (int q = 0; q < nj; ++q) {
         double lo = b[q], hi = b[q];
-        const double* row = W.data() + (size_t)q * d.d_in;
-        for (int k = 0; k < d.d_in; ++k) {
-          const double w = row[k];
-          if (w == 0.0) continue;
-          const double a = w * x_lo[k], e = w * x_hi[k];
-          lo = round_down(lo + round_down(std::min(a, e)));
-          hi = round_up(hi + round_up(std::max(a, e)));
-        }
-        if (d.skip == 1) {   // x^(1) = W x + b + x
+        auto add_row = [&](const double* row) {
+          for (int k = 0; k < d.d_in; ++k) {
+            const double w = row[k];
+            if (w == 0.0) continue;
+            const double a = w * x_lo[k], e = w * x_hi[k];
+            lo = round_down(lo + round_down(std::min(a, e)));
+            hi = round_up(hi + round_up(std::max(a, e)));
+          }
+        };
+        add_row(W.data() + (size_t)q * d.d_in);
+        if (d.skip == 1 && d.shortcut) {         // x^(1) = W x + b + S x
+          add_row(S.data() + (size_t)q * d.d_in);
+        } else if (d.skip == 1) {                // x^(1) = W x + b + x
           lo = round_down(lo + x_lo[j0 + q]);
           hi = round_up(hi + x_hi[j0 + q]);
         }
@@ -104,11 +117,20 @@ gcp_status intermediate_bounds(Ctx& c, const gcp_layer_desc* layers, int L, cons
   std::vector<int16_t> lay{0};
   std::vector<int8_t> sgn{0};
   const gcp_subdomains sub{1, ptr.data(), lay.data(), idx.data(), sgn.data()};
+  std::vector<double> S, bs;
   for (int i = 2; i < L; ++i) {
     const gcp_layer_desc& d = layers[i - 1];
     for (int j0 = 0; j0 < d.d_out; j0 += kBoundRows) {
       const int nj = std::min(kBoundRows, d.d_out - j0);
       dense_rows(d, j0, nj, W, b);
+      gcp_layer_desc sc{};                  // the same rows of a projection shortcut
+      if (d.skip && d.shortcut) {
+        dense_rows(*d.shortcut, j0, nj, S, bs);
+        sc.kind = GCP_DENSE;
+        sc.d_in = d.shortcut->d_in;
+        sc.d_out = nj;
+        sc.W = S.data();
+      }
       std::vector<gcp_layer_desc> net(layers, layers + (i - 1));
       gcp_layer_desc last{};
       last.kind = GCP_DENSE;
@@ -117,6 +139,7 @@ gcp_status intermediate_bounds(Ctx& c, const gcp_layer_desc* layers, int L, cons
       last.W = W.data();
       last.b = b.data();
       last.skip = d.skip;
+      last.shortcut = (d.skip && d.shortcut) ? &sc : nullptr;
       net.push_back(last);
       std::vector<double> spec((size_t)2 * nj * nj, 0.0);
       for (int q = 0; q < nj; ++q) {
@@ -125,7 +148,7 @@ gcp_status intermediate_bounds(Ctx& c, const gcp_layer_desc* layers, int L, cons
       }
       int nid = -1;
       gcp_status s = init_net(c, net.data(), i, x_lo, x_hi, spec.data(), 2 * nj, blo.data(), bhi.data(), &nid,
-                              d.skip ? j0 : 0);
+                              (d.skip && !d.shortcut) ? j0 : 0);
       if (s) return s;
       Batch* bt = nullptr;
       s = duals_create(c, nid, -1, &sub, GCP_FP32, &bt);

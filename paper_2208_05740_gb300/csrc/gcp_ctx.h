@@ -39,11 +39,16 @@ struct Net {
   float* YL32 = nullptr;
   double* cb64 = nullptr;            // [K] = c_k^T b^(L)
   float* cb32 = nullptr;
-  float* negC32 = nullptr;           // [K, d_L] = -c_k in float (a skip into the last layer)
-  // skip connections: skip[i-1] = s >= 1 when layer i adds xhat^(s-1);
-  // consumer[m] = the layer that adds xhat^(m), or 0
-  std::vector<int> skip, consumer;
-  int skip_off = 0;                  // the last layer's skip adds xhat^(m)[skip_off ..]
+  // skip connections: skip[i-1] = s >= 1 when layer i adds S xhat^(s-1);
+  // consumer[m] = the layer that adds xhat^(m), or 0; sc_map[i-1] = the map
+  // index (L+1, L+2, ... in geom and the weight vectors) of layer i's
+  // projection S, 0 for the identity
+  std::vector<int> skip, consumer, sc_map;
+  int skip_off = 0;                  // the last layer's identity skip adds xhat^(m)[skip_off ..]
+  // [K, d_m] = -S^T c_k of a skip on the last layer from xhat^(m), m < L-1
+  // (from m = L-1 it is folded into YL)
+  double* SK64 = nullptr;
+  float* SK32 = nullptr;
   std::vector<double*> lo64, hi64;   // hidden layer i at index i-1
   std::vector<float*> lo32, hi32;    // rounded outwards
   std::vector<double*> invul64;      // 1 / (hi - lo) where lo < 0 < hi, else 0

@@ -255,9 +255,10 @@ void conv_T_abs(cudaStream_t st, int64_t R, const LayerGeom& g, const double* W,
 template <typename Ts, typename Td>
 void skip_add(cudaStream_t st, int64_t R, int d, int ld, int off, const Ts* src, int src_mod, Td* y);
 // the same in the certification: float64 sum in round-to-nearest and the
-// magnitude bound yabs += |src| in float rounded up
-void skip_add_cert(cudaStream_t st, int64_t R, int d, int ld, int off, const double* src, int src_mod, double* y,
-                   float* yabs);
+// magnitude bound yabs += src_abs (or |src| where src_abs is null) in float
+// rounded up
+void skip_add_cert(cudaStream_t st, int64_t R, int d, int ld, int off, const double* src, const float* src_abs,
+                   int src_mod, double* y, float* yabs);
 
 // tcgen05 GEMMs (k_tc.cu); false = shape or driver not supported, use SIMT
 bool tc_available(int K, bool bf16);

@@ -294,7 +294,8 @@ namespace {
 // Elementwise over R x d, grid-stride; rows of y start at r * ld + off.
 template <typename Ts, typename Td, bool CERT>
 __global__ void __launch_bounds__(256) k_skip_add(int64_t R, int d, int ld, int off, const Ts* __restrict__ src,
-                                                  int src_mod, Td* __restrict__ y, float* __restrict__ yabs) {
+                                                  const float* __restrict__ src_abs, int src_mod, Td* __restrict__ y,
+                                                  float* __restrict__ yabs) {
   const int64_t n = R * d;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / d;
@@ -303,7 +304,8 @@ __global__ void __launch_bounds__(256) k_skip_add(int64_t R, int d, int ld, int 
     const Td v = (Td)src[rs * d + j];
     const int64_t yi = r * ld + off + j;
     y[yi] += v;
-    if constexpr (CERT) yabs[yi] = __fadd_ru(yabs[yi], __double2float_ru(fabs((double)v)));
+    if constexpr (CERT)
+      yabs[yi] = __fadd_ru(yabs[yi], src_abs ? src_abs[rs * d + j] : __double2float_ru(fabs((double)v)));
   }
 }
 
@@ -318,21 +320,22 @@ void skip_add(cudaStream_t st, int64_t R, int d, int ld, int off, const Ts* src,
   if (!(reg_check(src, srows * d * sizeof(Ts), "skip src") & reg_check(y, (double)R * ld * sizeof(Td), "skip y")))
     return;
   int tk = prof_begin(st, "skip_add", (double)R * d, (double)R * d * (sizeof(Ts) + 2 * sizeof(Td)));
-  k_skip_add<Ts, Td, false><<<grid_for(R * d, 256), 256, 0, st>>>(R, d, ld, off, src, src_mod, y, nullptr);
+  k_skip_add<Ts, Td, false><<<grid_for(R * d, 256), 256, 0, st>>>(R, d, ld, off, src, nullptr, src_mod, y, nullptr);
   prof_end(st, tk);
 }
 
-void skip_add_cert(cudaStream_t st, int64_t R, int d, int ld, int off, const double* src, int src_mod, double* y,
-                   float* yabs) {
+void skip_add_cert(cudaStream_t st, int64_t R, int d, int ld, int off, const double* src, const float* src_abs,
+                   int src_mod, double* y, float* yabs) {
   if (R <= 0 || d <= 0) return;
   const double srows = src_mod ? (double)src_mod : (double)R;
   if (off < 0 || off + d > ld)
     return (void)reg_check(nullptr, 1.0, "skip add: row window outside the destination");
-  if (!(reg_check(src, srows * d * 8.0, "skip src") & reg_check(y, (double)R * ld * 8.0, "skip y") &
-        reg_check(yabs, (double)R * ld * 4.0, "skip yabs")))
+  if (!(reg_check(src, srows * d * 8.0, "skip src") & reg_check(src_abs, src_abs ? srows * d * 4.0 : 0.0, "skip src abs") &
+        reg_check(y, (double)R * ld * 8.0, "skip y") & reg_check(yabs, (double)R * ld * 4.0, "skip yabs")))
     return;
   int tk = prof_begin(st, "skip_add_certify", (double)R * d, (double)R * d * 24.0);
-  k_skip_add<double, double, true><<<grid_for(R * d, 256), 256, 0, st>>>(R, d, ld, off, src, src_mod, y, yabs);
+  k_skip_add<double, double, true><<<grid_for(R * d, 256), 256, 0, st>>>(R, d, ld, off, src, src_abs, src_mod, y,
+                                                                            yabs);
   prof_end(st, tk);
 }
 

@@ -88,13 +88,16 @@ size_t estimate_bytes(const Net& net, int64_t R, int N, int64_t nnz, int Mcap) {
   // certification by exact slices: bf16 slices of nu and the fp32 slice sums
   int smax = 0;
   for (const SliceB& sl : net.WTsl) smax = std::max(smax, sl.s);
-  // skips from further back than the layer's input park nu / a (fp32) and the
-  // certification's nu (fp64) of their source's width
+  // skips from further back than the layer's input park nu, S^T nu, a (fp32)
+  // and the certification's term and its magnitude bound, of their source's
+  // width; projections add one product buffer of each kind
   int64_t parked = 0;
+  bool proj = false;
   for (int m = 0; m < net.L; ++m)
     if (net.consumer[m] > m + 1 && net.consumer[m] < net.L) parked += net.dims[m];
+  for (int i = 0; i < net.L; ++i) proj |= net.sc_map[i] != 0;
   const double per_row = 4.0 * (5 * sum_d + 5 * dmax + nnz + 3 * N + 3 * Mcap) + 8.0 * (2 * dmax + P) +
-                         4.0 * (dmax + P) + 6.0 * smax * dmax + 12.0 * parked;
+                         4.0 * (dmax + P) + 6.0 * smax * dmax + 24.0 * parked + (proj ? 28.0 * dmax : 0.0);
   const double resident = 4.0 * (sum_d + Mcap + N);
   return (size_t)(R * (per_row + resident)) + (size_t(16) << 20);
 }

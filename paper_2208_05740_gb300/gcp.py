@@ -39,10 +39,14 @@ class GCPError(RuntimeError):
 
 
 class LayerDesc(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("d_in", C.c_int32), ("d_out", C.c_int32), ("c_in", C.c_int32),
-                ("h_in", C.c_int32), ("w_in", C.c_int32), ("c_out", C.c_int32), ("h_out", C.c_int32),
-                ("w_out", C.c_int32), ("k", C.c_int32), ("stride", C.c_int32), ("pad", C.c_int32),
-                ("W", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double)), ("skip", C.c_int32)]
+    pass
+
+
+LayerDesc._fields_ = [("kind", C.c_int32), ("d_in", C.c_int32), ("d_out", C.c_int32), ("c_in", C.c_int32),
+                      ("h_in", C.c_int32), ("w_in", C.c_int32), ("c_out", C.c_int32), ("h_out", C.c_int32),
+                      ("w_out", C.c_int32), ("k", C.c_int32), ("stride", C.c_int32), ("pad", C.c_int32),
+                      ("W", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double)), ("skip", C.c_int32),
+                      ("shortcut", C.POINTER(LayerDesc))]
 
 
 class Subdomains(C.Structure):
@@ -205,12 +209,9 @@ class Context:
     # ------------------------------------------------------------ inputs
     @staticmethod
     def _layer_descs(layers, keep):
-        descs = (LayerDesc * len(layers))()
-        for i, ly in enumerate(layers):
+        def fill(d, ly, with_bias=True):
             W = _c(ly.W, np.float64)
-            b = _c(ly.b, np.float64)
-            keep += [W, b]
-            d = descs[i]
+            keep.append(W)
             d.kind = ly.kind
             d.d_in = int(np.prod(ly.in_shape))
             d.d_out = int(np.prod(ly.out_shape))
@@ -219,13 +220,30 @@ class Context:
                 d.c_out, d.h_out, d.w_out = ly.out_shape
                 d.k, d.stride, d.pad = W.shape[2], ly.stride, ly.pad
             d.W = _ptr(W, C.c_double)
-            d.b = _ptr(b, C.c_double)
+            if with_bias:
+                b = _c(ly.b, np.float64)
+                keep.append(b)
+                d.b = _ptr(b, C.c_double)
+
+        descs = (LayerDesc * len(layers))()
+        for i, ly in enumerate(layers):
+            d = descs[i]
+            fill(d, ly)
             d.skip = int(getattr(ly, "skip", 0))
+            sc = getattr(ly, "shortcut", None) if d.skip else None
+            if sc is not None:
+                if np.any(np.asarray(sc.b) != 0):
+                    raise ValueError("a shortcut's bias belongs in the layer's own bias b")
+                sd = LayerDesc()
+                fill(sd, sc, with_bias=False)
+                keep.append(sd)
+                d.shortcut = C.pointer(sd)
         return descs
 
     def init_net(self, layers, x_lo, x_hi, spec_c, inter_lo, inter_hi) -> int:
         """layers: objects with kind, W, b, in_shape, out_shape, stride, pad
-        and optionally skip (0, or s >= 1: the layer adds xhat^(s-1))."""
+        and optionally skip (0, or s >= 1: the layer adds xhat^(s-1)) and
+        shortcut (None, or a layer object S applied to xhat^(s-1), zero bias)."""
         keep = []
         descs = self._layer_descs(layers, keep)
         xl, xh, sc = _c(x_lo, np.float64), _c(x_hi, np.float64), _c(spec_c, np.float64)

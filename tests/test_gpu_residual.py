@@ -34,13 +34,20 @@ def _load(ctx, inst, seed, scale=0.05, fp64=False):
     return D, ctx.duals_export(D)
 
 
-def _net_with_skips(seed, dims, skips, name, n_sub=24, n_cuts=40, eps=0.02):
-    """MLP of the given widths; skips maps a 1-based layer to its skip s."""
+def _net_with_skips(seed, dims, skips, name, n_sub=24, n_cuts=40, eps=0.02, projections=()):
+    """MLP of the given widths; skips maps a 1-based layer to its skip s; the
+    layers in projections add their source through a dense shortcut
+    N(0, 1/(4 d_m)) instead of the identity."""
     rng = np.random.default_rng(seed)
     net = synth.make_mlp(rng, list(dims))
     for k, s in skips.items():
         ly = net.layers[k - 1]
-        net.layers[k - 1] = dataclasses.replace(ly, W=0.5 * ly.W, skip=s)
+        sc = None
+        if k in projections:
+            dm = dims[s - 1]
+            sc = synth.Layer(synth.DENSE, rng.normal(0, 0.5 / np.sqrt(dm), (ly.d_out, dm)), np.zeros(ly.d_out),
+                             (dm,), (ly.d_out,))
+        net.layers[k - 1] = dataclasses.replace(ly, W=0.5 * ly.W, skip=s, shortcut=sc)
     return synth._finish(name, rng, net, rng.random(dims[0]), eps, 4, n_sub, (0, 4),
                          dict(n_cuts=n_cuts, min_vars=2, max_vars=6, span_layers=True, need_z=True, p_input=0.5))
 
@@ -57,6 +64,11 @@ def _cases():
     yield "own_input_of_last", _net_with_skips(synth.SEED_BASE + 82, [128, 256, 256, 256], {2: 2, 3: 3}, "skips_self",
                                                eps=0.1)
     yield "three_back", _net_with_skips(synth.SEED_BASE + 83, [300, 256, 256, 256, 256, 10], {4: 2}, "skips_far")
+    # dense projections: from the layer's own input, from the input two layers back, into the spec layer
+    yield "projections", _net_with_skips(synth.SEED_BASE + 84, [200, 256, 192, 256, 10], {2: 2, 3: 1, 4: 3},
+                                         "proj", projections=(2, 3, 4))
+    yield "projection_into_last", _net_with_skips(synth.SEED_BASE + 85, [128, 256, 128, 10], {3: 3}, "proj_last",
+                                                  projections=(3,))
 
 
 CASES = list(_cases())
@@ -81,7 +93,10 @@ def test_residual_fp32_bf16_and_certified_at_same_duals(ctx, name, inst):
     ctx.duals_free(D)
 
 
-@pytest.mark.parametrize("name,inst", CASES[:2], ids=[c[0] for c in CASES[:2]])
+FP64_CASES = [c for c in CASES if c[0] in ("blocks", "input_and_spec_layer", "projections")]
+
+
+@pytest.mark.parametrize("name,inst", FP64_CASES, ids=[c[0] for c in FP64_CASES])
 def test_residual_fp64_chain_bound_and_gradient(ctx, name, inst):
     P = O.build_problem(inst)
     D, (A, B, G) = _load(ctx, inst, 6, fp64=True)
@@ -113,9 +128,18 @@ def test_residual_optimisation_improves_and_certifies(ctx):
 
 
 # ----------------------------------------------------------------------------- residual CNN
-@pytest.fixture(scope="module")
-def resnet_case(ctx):
-    inst = synth.cnn_resnet(hw=16, ch=(8, 16), fc=64, n_sub=3, n_cuts=60)
+RESNETS = {
+    # resnet2b's block structure at 16 x 16: a 1x1 stride-2 convolution shortcut, then an identity block
+    "resnet2b_16": dict(hw=16, stem=8, blocks=((16, 2), (16, 1)), fc=64),
+    # resnet4b's: both blocks downsample through projections
+    "resnet4b_16": dict(hw=16, stem=8, blocks=((16, 2), (16, 2)), fc=64),
+}
+
+
+@pytest.fixture(scope="module", params=list(RESNETS))
+def resnet_case(ctx, request):
+    inst = synth.cnn_resnet(n_sub=3, n_cuts=60, **RESNETS[request.param])
+    assert any(ly.shortcut is not None for ly in inst.net.layers)
     P = O.build_problem(inst)
     D, duals = _load(ctx, inst, 9)
     return inst, P, D, duals
@@ -156,9 +180,10 @@ def _oracle_rows(inst, lo, hi, i, idx):
     return g[:len(idx)], -g[len(idx):]
 
 
-@pytest.mark.parametrize("make", [lambda: CASES[1][1], lambda: synth.cnn_resnet(hw=16, ch=(8, 16), fc=64, n_sub=1,
-                                                                                 n_cuts=0)],
-                         ids=["mlp_input_and_spec_skips", "resnet"])
+@pytest.mark.parametrize("make", [lambda: CASES[1][1], lambda: dict(CASES)["projections"],
+                                  lambda: synth.cnn_resnet(n_sub=1, n_cuts=0, **RESNETS["resnet2b_16"]),
+                                  lambda: synth.cnn_resnet(n_sub=1, n_cuts=0, **RESNETS["resnet4b_16"])],
+                         ids=["mlp_input_and_spec_skips", "mlp_projections", "resnet2b_16", "resnet4b_16"])
 def test_root_bounds_of_residual_networks(ctx, make):
     inst = make()
     lo, hi = ctx.intermediate_bounds(inst.net.layers, inst.x_lo, inst.x_hi)
@@ -186,7 +211,15 @@ def test_bad_skips_are_rejected(ctx):
     shared[3] = dataclasses.replace(layers[3], skip=2)               # xhat^(1) already feeds layer 3
     later = layers[:]
     later[1] = dataclasses.replace(layers[1], skip=3)                # not an earlier layer
-    for net in (bad_width, shared, later):
+    wrong_proj = layers[:]
+    wrong_proj[2] = dataclasses.replace(layers[2], shortcut=synth.Layer(synth.DENSE, np.ones((256, 100)), np.zeros(256),
+                                                                        (100,), (256,)))   # xhat^(1) has 256 entries
+    for net in (bad_width, shared, later, wrong_proj):
         with pytest.raises(gcp.GCPError) as e:
             ctx.init_net(net, inst.x_lo, inst.x_hi, inst.spec, inst.inter_lo, inst.inter_hi)
         assert e.value.status == -1          # GCP_EINVAL
+    biased = layers[:]
+    biased[2] = dataclasses.replace(layers[2], shortcut=synth.Layer(synth.DENSE, np.eye(256), np.ones(256),
+                                                                    (256,), (256,)))
+    with pytest.raises(ValueError):
+        ctx.init_net(biased, inst.x_lo, inst.x_hi, inst.spec, inst.inter_lo, inst.inter_hi)
