@@ -67,8 +67,10 @@ def _cases():
     # dense projections: from the layer's own input, from the input two layers back, into the spec layer
     yield "projections", _net_with_skips(synth.SEED_BASE + 84, [200, 256, 192, 256, 10], {2: 2, 3: 1, 4: 3},
                                          "proj", projections=(2, 3, 4))
+    # eps 0.05 for the same reason as above: at 0.02 two rows of the BF16 chain sit at 1.2e-3 (as in the CPU
+    # emulation of its roundings)
     yield "projection_into_last", _net_with_skips(synth.SEED_BASE + 85, [128, 256, 128, 10], {3: 3}, "proj_last",
-                                                  projections=(3,))
+                                                  projections=(3,), eps=0.05)
 
 
 CASES = list(_cases())
