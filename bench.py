@@ -12,6 +12,12 @@ certified. Inputs are seeded synthetic data of the paper's shapes.
 FC10, 4096 subdomains (1-12 splits) x 9 spec rows, 1000 cuts over 2-16
 variables, 50 Adam iterations in the BF16 chain, FP64 certification.
 
+--workload resnet: residual CNN of the resnet2b shape, 3x32x32 -> conv8 3x3
+s2 -> ResBlock(8,16) (conv s2, conv, 1x1 s2 shortcut) -> ResBlock(16,16)
+(identity shortcut) -> FC100 -> FC10, 2048 subdomains (the residual models'
+batch size) x 9 spec rows, 500 cuts over 2-16 variables, 20 Adam iterations
+in the BF16 chain, FP64 certification.
+
 value  : device-timed (CUDA events on the library's stream), inputs resident.
 e2e    : the same through the public C ABI from host buffers: every step
          creates the batch from host split arrays (uploads splits and cuts),
@@ -44,7 +50,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gcp", "reference"], default="gcp")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="mlp",
-                    help="mlp: MLP 784-256x6-10 (the headline); cnn: the CIFAR-shaped CNN")
+                    help="mlp: MLP 784-256x6-10 (the headline); cnn: the CIFAR-shaped CNN; resnet: resnet2b shape")
     ap.add_argument("--prec", choices=["fp32", "bf16"], default=None, help="chain precision (workload default)")
     ap.add_argument("--iters", type=int, default=None, help="ascent iterations (workload default)")
     ap.add_argument("--n-sub", type=int, default=None, help="subdomains per GPU (workload default)")
@@ -72,12 +78,19 @@ def _build_cnn(n_sub):
     return synth.cnn_cifar(n_sub=n_sub)
 
 
-# The two workloads: name, instance builder, defaults, oracle sample size.
+def _build_resnet(n_sub):
+    from paper_2208_05740_gb300 import synth
+    return synth.cnn_resnet(n_sub=n_sub)
+
+
+# The workloads: name, instance builder, defaults, oracle sample size.
 WORKLOADS = {
     "mlp": dict(name="mlp_784_256x6_10", cuts=200, splits="1-8", prec="fp32", iters=100, n_sub=1024, sample=4,
                 build=_build_mlp),
     "cnn": dict(name="cnn_3x32x32_c32_c64_fc512_fc10", cuts=1000, splits="1-12", prec="bf16", iters=50, n_sub=4096,
                 sample=2, build=_build_cnn),
+    "resnet": dict(name="resnet_3x32x32_c8_b16s2_b16s1_fc100_fc10", cuts=500, splits="1-12", prec="bf16", iters=20,
+                   n_sub=2048, sample=2, build=_build_resnet),
 }
 
 

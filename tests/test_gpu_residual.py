@@ -95,6 +95,21 @@ def test_residual_fp32_bf16_and_certified_at_same_duals(ctx, name, inst):
     ctx.duals_free(D)
 
 
+@pytest.mark.parametrize("name,dims,skips,proj,seed", [
+    ("own_input_of_last", [128, 256, 256, 256], {2: 2, 3: 3}, (), synth.SEED_BASE + 82),
+    ("projection_into_last", [128, 256, 128, 10], {3: 3}, (3,), synth.SEED_BASE + 85)])
+def test_small_eps_nets_fp32_and_certified(ctx, name, dims, skips, proj, seed):
+    """The two nets whose BF16 case runs at a larger eps, at eps 0.02 (bounds near zero) in the FP32 chain."""
+    inst = _net_with_skips(seed, dims, skips, name, projections=proj)
+    P = O.build_problem(inst)
+    D, (A, B, G) = _load(ctx, inst, 5)
+    ref = O.evaluate(P, oracle_duals(inst, A, B, G))
+    g, cert = ctx.bound_batch(D, gcp.GCP_FP32, certify=True)
+    assert_rel(g, ref, 1e-5, f"{name} fp32 bound")
+    assert_rel(cert, ref, 1e-9, f"{name} certified")
+    ctx.duals_free(D)
+
+
 FP64_CASES = [c for c in CASES if c[0] in ("blocks", "input_and_spec_layer", "projections")]
 
 
