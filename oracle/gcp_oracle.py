@@ -13,6 +13,12 @@ It is a plain, slow restatement, in float64 and in the paper's notation, of
     closed form of Lemma A.1 (App. A) for unstable neurons;
   * beta-CROWN's neuron splits as special cut rows (Sec. 3.1, "Connection to
     CROWN-like bound propagation methods");
+  * the bound with the ReLU duals pi (and gamma_r = C - pi) of every unstable
+    neuron optimised directly instead of set by Lemma A.1's closed form: the
+    closed form maximises each neuron's own term but ignores pi's effect on
+    nu and hence on the layers below, so optimising pi too is what reaches
+    the LP optimum (the remark closing App. A); pi = theta * [nuhat]_+ with
+    theta in [0, 1];
   * reverse-mode differentiation of that bound with respect to the
     optimisable duals (the paper optimises them by gradient ascent, Sec. 3.1
     after Theorem 3.1; App. C.1 names Adam with 20 iterations);
@@ -53,6 +59,11 @@ Readings of the paper (each is listed with its reason in the design notes):
      multiplier nu^(k) adds S^T nu^(k) to y^(m), the coefficient of xhat^(m)
      (xhat^(0) = x, so m = 0 adds it to the input term before concretisation);
      the shortcut's bias b_S joins b^(k).
+ R12 optimised pi (App. A's closing remark) is parametrised as
+     pi = theta * C, C = [nuhat]_+, theta in [0, 1] per row and neuron, so it
+     stays feasible (0 <= pi <= C) whatever the other duals do; its start is
+     Lemma A.1's pi* (theta = pi* / C, u / (u - l) where C = 0) and its step
+     uses alpha's learning rate.
 
 Layouts (float64 numpy): rows r = s * K + k for subdomain s and spec row k;
 alpha is a list over hidden layers of [R, d_i]; beta is [R, max_splits]
@@ -225,9 +236,13 @@ class Duals:
     alpha: List[np.ndarray]   # per hidden layer [R, d_i]
     beta: np.ndarray          # [R, max_splits]
     gamma: np.ndarray         # [R, N]
+    # per hidden layer [R, d_i]: pi = theta * [nuhat]_+ on unstable neurons
+    # (R12); None: Lemma A.1's closed-form pi
+    theta: Optional[List[np.ndarray]] = None
 
     def copy(self) -> "Duals":
-        return Duals([a.copy() for a in self.alpha], self.beta.copy(), self.gamma.copy())
+        return Duals([a.copy() for a in self.alpha], self.beta.copy(), self.gamma.copy(),
+                     None if self.theta is None else [t.copy() for t in self.theta])
 
 
 def _through_skip(P: Problem, layer: int, nu: np.ndarray) -> np.ndarray:
@@ -351,6 +366,10 @@ def evaluate(P: Problem, D: Duals, trace: bool = False):
         den_l = np.where(unstable, lo, -1.0)
         den_u = np.where(unstable, hi, 1.0)
         pi, tau, h = unstable_closed_form(nu_hat, s, den_l, den_u, D.alpha[i - 1])
+        if D.theta is not None:     # R12: pi = theta * C, h at that pi (Lemma A.1's objective)
+            C = np.maximum(nu_hat, 0.0)
+            pi = np.clip(D.theta[i - 1], 0.0, 1.0) * C
+            h = den_l * pi - np.maximum(0.0, den_u * (C - pi) + den_l * pi - s)
         nu_i = np.where(active, nu_hat - t, np.where(inactive, -t, pi - tau - t))
         obj = obj + np.sum(np.where(unstable, h, 0.0), axis=1) + np.sum(np.where(active, s, 0.0), axis=1)
         obj = obj - nu_i @ P.b[i - 1]
@@ -394,6 +413,7 @@ def gradient(P: Problem, D: Duals):
     g_gamma = -np.repeat(P.d[None, :], R, 0) + (np.asarray((P.H[0] @ xstar.T).T) if P.N else 0.0)
     g_beta = np.zeros_like(D.beta)
     g_alpha = [np.zeros_like(x) for x in D.alpha]
+    g_theta = None if D.theta is None else [np.zeros_like(x) for x in D.theta]
     for i in range(1, P.L):
         Wi = P.Wm[i - 1]
         nubar = (np.asarray(Wi @ a.T).T if sp.issparse(Wi) else a @ Wi.T) - P.b[i - 1][None, :]
@@ -418,6 +438,16 @@ def gradient(P: Problem, D: Duals):
         # h = min(s, 0) when C = 0; h = s when pi* = C with l C - s > 0
         dh_ds = np.where(pos, np.where(inside, -lo / ul, np.where(upper & (lo * C - s > 0), 1.0, 0.0)),
                          np.where(s < 0, 1.0, 0.0))
+        if D.theta is not None:
+            # R12: pi = th C, q = u (C - pi) + l pi - s, h = l pi - max(q, 0), nu = pi - tau - t
+            th = np.clip(D.theta[i - 1], 0.0, 1.0)
+            q = hi * (C - th * C) + lo * th * C - s
+            act = q > 0
+            dnu_dnh = np.where(pos, th, np.where(nu_hat < 0, al, 0.0))
+            dh_dnh = np.where(pos, lo * th - np.where(act, hi * (1.0 - th) + lo * th, 0.0), 0.0)
+            dnu_ds = np.zeros_like(nu_hat)
+            dh_ds = np.where(act, 1.0, 0.0)
+            g_theta[i - 1] = np.where(unstable, C * (nubar + lo + np.where(act, hi - lo, 0.0)), 0.0)
         dnu_dnh = np.where(unstable, dnu_dnh, np.where(active, 1.0, 0.0))
         dh_dnh = np.where(unstable, dh_dnh, 0.0)
         dnu_ds = np.where(unstable, dnu_ds, 0.0)
@@ -435,12 +465,28 @@ def gradient(P: Problem, D: Duals):
         a = dg_dnh
         if i in sources:
             a_saved[i] = a
-    return g, Duals(g_alpha, g_beta, g_gamma)
+    return g, Duals(g_alpha, g_beta, g_gamma, g_theta)
+
+
+def theta_closed_form(P: Problem, D: Duals) -> List[np.ndarray]:
+    """theta with theta * C = Lemma A.1's pi* at the duals D (R12's start);
+    u / (u - l) where C = 0 and on stable neurons (where it is unused)."""
+    _, T = evaluate(P, D, trace=True)
+    out = []
+    for i in range(1, P.L):
+        nu_hat, s, lo, hi = T.nu_hat[i - 1], T.s[i - 1], T.lo[i - 1], T.hi[i - 1]
+        unstable = (hi > 0) & (lo < 0)
+        den_l = np.where(unstable, lo, -1.0)
+        den_u = np.where(unstable, hi, 1.0)
+        pi, _, _ = unstable_closed_form(nu_hat, s, den_l, den_u, D.alpha[i - 1])
+        C = np.maximum(nu_hat, 0.0)
+        out.append(np.where(C > 0, pi / np.where(C > 0, C, 1.0), den_u / (den_u - den_l)))
+    return out
 
 
 def project(P: Problem, D: Duals) -> None:
     """0 <= alpha <= 1, beta >= 0, gamma >= 0 (Theorem 3.1's domain)."""
-    for a in D.alpha:
+    for a in D.alpha + (D.theta or []):
         np.clip(a, 0.0, 1.0, out=a)
     np.maximum(D.beta, 0.0, out=D.beta)
     np.maximum(D.gamma, 0.0, out=D.gamma)
@@ -454,18 +500,20 @@ def optimize(P: Problem, D: Duals, iters: int, lr_alpha: float, lr_beta: float, 
     'pga': x <- proj(x + lr_t * grad). 'adam': Adam (Kingma & Ba) ascent with
     moments 0.9 / 0.999 and eps 1e-8 (the paper names Adam but not its
     moments, App. C.1). lr_t = lr * lr_decay**t at iteration t = 0, 1, ...
+    With D.theta set, theta (R12) is optimised too, at alpha's rate.
     Returns the bound at the final duals (one more evaluation) and the duals.
     """
     D = D.copy()
     if optimizer == "adam":
-        m = Duals([np.zeros_like(a) for a in D.alpha], np.zeros_like(D.beta), np.zeros_like(D.gamma))
+        m = Duals([np.zeros_like(a) for a in D.alpha], np.zeros_like(D.beta), np.zeros_like(D.gamma),
+                  None if D.theta is None else [np.zeros_like(t) for t in D.theta])
         v = m.copy()
     for it in range(iters):
         _, G = gradient(P, D)
         f = lr_decay ** it
         lrs = (lr_alpha * f, lr_beta * f, lr_gamma * f)
         if optimizer == "pga":
-            for a, ga in zip(D.alpha, G.alpha):
+            for a, ga in zip(D.alpha + (D.theta or []), G.alpha + (G.theta or [])):
                 a += lrs[0] * ga
             D.beta += lrs[1] * G.beta
             D.gamma += lrs[2] * G.gamma
@@ -479,7 +527,8 @@ def optimize(P: Problem, D: Duals, iters: int, lr_alpha: float, lr_beta: float, 
                 vx *= adam_b2
                 vx += (1 - adam_b2) * gx * gx
                 x += lr * (mx / c1) / (np.sqrt(vx / c2) + adam_eps)
-            for a, ga, ma, va in zip(D.alpha, G.alpha, m.alpha, v.alpha):
+            for a, ga, ma, va in zip(D.alpha + (D.theta or []), G.alpha + (G.theta or []),
+                                     m.alpha + (m.theta or []), v.alpha + (v.theta or [])):
                 step(a, ga, ma, va, lrs[0])
             step(D.beta, G.beta, m.beta, v.beta, lrs[1])
             step(D.gamma, G.gamma, m.gamma, v.gamma, lrs[2])
