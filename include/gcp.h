@@ -114,10 +114,18 @@ typedef struct {
  * Learning rate at step t is lr * lr_decay^t. prec: chain arithmetic
  * (GCP_FP64 needs duals created with GCP_FP64; GCP_FP32 / GCP_BF16 need
  * GCP_FP32 duals). certify != 0: also run the FP64 outward-rounded
- * certification pass at the final duals. */
+ * certification pass at the final duals.
+ * opt_pi != 0: also optimise the ReLU duals pi (and gamma_r = C - pi) of every
+ * unstable neuron directly, as App. A's closing remark suggests, instead of
+ * Lemma A.1's closed form: pi = theta * [nuhat]_+ with theta in [0, 1] per row
+ * and neuron, started at the closed form and stepped at lr_alpha. The duals
+ * object then keeps theta (gcp_duals_theta) and every later bound,
+ * gradient and certification of it uses theta until gcp_duals_import or an
+ * optimisation with opt_pi = 0. Zero-initialise to leave it off. */
 typedef struct {
   int32_t iters, optimizer, prec, certify;
   double lr_alpha, lr_beta, lr_gamma, lr_decay;
+  int32_t opt_pi;
 } gcp_opt_params;
 
 /* ------------------------------------------------------------------ context */
@@ -196,6 +204,11 @@ GCP_API gcp_status gcp_duals_export(gcp_ctx* ctx, void* duals, double* alpha, do
 GCP_API gcp_status gcp_duals_import(gcp_ctx* ctx, void* duals, const double* alpha, const double* beta,
                                    const double* gamma);
 GCP_API gcp_status gcp_duals_free(gcp_ctx* ctx, void* duals);
+/* The directly optimised ReLU duals theta (opt_pi, pi = theta * [nuhat]_+),
+ * row-major [R, n_alpha] in alpha's layout. theta_out != NULL copies them out
+ * (GCP_ENOTFOUND while the duals object uses the closed form); theta_in !=
+ * NULL sets them (used as given) and switches the object to theta. */
+GCP_API gcp_status gcp_duals_theta(gcp_ctx* ctx, void* duals, const double* theta_in, double* theta_out);
 
 /* ------------------------------------------------------------------ bounds */
 

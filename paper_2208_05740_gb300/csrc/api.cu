@@ -1065,12 +1065,25 @@ const double* spec_skip<double>(const Net& n) { return n.SK64; }
 template <>
 const float* spec_skip<float>(const Net& n) { return n.SK32; }
 
+// The directly optimised ReLU duals theta (pi = theta [nuhat]_+) of the batch,
+// layer i's block at R * (d_1 + .. + d_{i-1}); nullptr while the batch uses
+// Lemma A.1's closed form.
+template <typename T>
+static T* theta_of(Batch& b, int i) {
+  if (!b.theta_on) return nullptr;
+  auto it = b.lazy.find("theta");
+  if (it == b.lazy.end()) return nullptr;
+  int64_t off = 0;
+  for (int q = 1; q < i; ++q) off += b.R * b.net->dims[q];
+  return (T*)it->second + off;
+}
+
 // Evaluate g for all rows at the batch's duals. with_adjoint_start: also write
 // a0 = -seed*x* into the operand buffer and the input-layer cut entries into E.
 // finalize = false leaves g itself out (ascent steps need only the gradient).
 template <typename T, typename Top>
 gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, const T* seed,
-                    bool finalize = true) {
+                    bool finalize = true, bool theta_init = false) {
   const Net& net = *b.net;
   const int L = net.L;
   const int64_t R = b.R;
@@ -1109,6 +1122,8 @@ gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, 
     a.nu_lo = (lo && tc_bwd<Top>(b, i)) ? lo : nullptr;
     a.nuhat_out = nuhat;
     a.obj_part = finalize ? part + (int64_t)poff * R : nullptr;   // ascent steps need no objective
+    a.theta = theta_of<T>(b, i);
+    a.theta_init = theta_init;
     relax_eval<T, Top>(st, a);
     poff += (net.dims[i] + kChunk - 1) / kChunk;
     lin_backward<Top, T>(st, b, i, nu, a.nu_lo, y);
@@ -1219,6 +1234,13 @@ gcp_status run_adjoint(Ctx& c, Batch& b, cudaStream_t st, const StepArgs<T>& ste
     a.g_beta = gbe;
     if (ma) { a.m_alpha = ma + aoff; a.v_alpha = va + aoff; }
     a.st = step;
+    if ((a.theta = theta_of<T>(b, i))) {
+      a.g_theta = nullptr;
+      if (step.mode == 2) {
+        a.m_theta = (T*)b.lazy["m_theta"] + aoff;
+        a.v_theta = (T*)b.lazy["v_theta"] + aoff;
+      }
+    }
     relax_adjoint<T, Top>(st, a);
     aoff += (int64_t)R * net.dims[i];
     if (i < L - 1) {
@@ -1336,6 +1358,7 @@ gcp_status run_certify(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
     const bool conv_here = g.kind != GCP_DENSE || (sc && net.geom[sc - 1].kind != GCP_DENSE);
     a.nuabs_out = conv_here ? nuabs : nullptr;
     a.obj_part = part + (int64_t)poff * R;
+    a.theta = theta_of<Td>(b, i);
     certify_relax<Td>(st, a);
     poff += (net.dims[i] + kChunk - 1) / kChunk;
     yerr = product(i, y, ya);
@@ -1407,7 +1430,8 @@ static StepArgs<T> make_step(const gcp_opt_params& p, int it) {
 template <typename T, typename Top>
 gcp_status optimize_steps(Ctx& c, Batch& b, cudaStream_t st, const gcp_opt_params& p) {
   for (int it = 0; it < p.iters; ++it) {
-    gcp_status s = run_eval<T, Top>(c, b, st, true, nullptr, false);
+    // with opt_pi, the first evaluation sets theta from the closed form
+    gcp_status s = run_eval<T, Top>(c, b, st, true, nullptr, false, p.opt_pi && it == 0);
     if (s) return s;
     s = run_adjoint<T, Top>(c, b, st, make_step<T>(p, it), nullptr, nullptr, nullptr, nullptr);
     if (s) return s;
@@ -1439,10 +1463,11 @@ static gcp_status fetch_bound(Ctx& c, Batch& b, cudaStream_t st, double* out) {
   return GCP_OK;
 }
 
-gcp_status eval_dispatch(Ctx& c, Batch& b, cudaStream_t st, int prec, bool adj_start, const void* seed) {
-  if (prec == GCP_FP64) return run_eval<double, double>(c, b, st, adj_start, (const double*)seed);
-  if (prec == GCP_FP32) return run_eval<float, float>(c, b, st, adj_start, (const float*)seed);
-  return run_eval<float, __nv_bfloat16>(c, b, st, adj_start, (const float*)seed);
+gcp_status eval_dispatch(Ctx& c, Batch& b, cudaStream_t st, int prec, bool adj_start, const void* seed,
+                         bool theta_init) {
+  if (prec == GCP_FP64) return run_eval<double, double>(c, b, st, adj_start, (const double*)seed, true, theta_init);
+  if (prec == GCP_FP32) return run_eval<float, float>(c, b, st, adj_start, (const float*)seed, true, theta_init);
+  return run_eval<float, __nv_bfloat16>(c, b, st, adj_start, (const float*)seed, true, theta_init);
 }
 
 gcp_status certify_dispatch(Ctx& c, Batch& b, cudaStream_t st, double* out_dev) {
@@ -1544,11 +1569,28 @@ gcp_status optimize_on(Ctx& c, Batch& b, const gcp_opt_params& p, cudaStream_t s
   if (p.iters < 0 || (p.optimizer != GCP_PGA && p.optimizer != GCP_ADAM) || !(p.lr_decay > 0))
     return c.fail(GCP_EINVAL, "bad optimiser parameters");
   if (b.R == 0) return GCP_OK;
+  // directly optimised pi (App. A's closing remark): theta and its Adam
+  // moments start afresh in every call, theta from the closed form
+  b.theta_on = false;
+  if (p.opt_pi) {
+    int64_t nal = 0;
+    for (int i = 1; i < b.net->L; ++i) nal += b.R * b.net->dims[i];
+    const size_t bytes = (size_t)std::max<int64_t>(nal, 1) * (b.fp64 ? 8 : 4);
+    if (!b.ws("theta", bytes, &s)) return s;
+    if (p.optimizer == GCP_ADAM) {
+      void* m = b.ws("m_theta", bytes, &s);
+      void* v = m ? b.ws("v_theta", bytes, &s) : nullptr;
+      if (!v) return s;
+      cudaMemsetAsync(m, 0, bytes, st);
+      cudaMemsetAsync(v, 0, bytes, st);
+    }
+    b.theta_on = true;
+  }
   if (p.prec == GCP_FP64) s = optimize_steps<double, double>(c, b, st, p);
   else if (p.prec == GCP_FP32) s = optimize_steps<float, float>(c, b, st, p);
   else s = optimize_steps<float, __nv_bfloat16>(c, b, st, p);
   if (s) return s;
-  s = eval_dispatch(c, b, st, p.prec, false, nullptr);
+  s = eval_dispatch(c, b, st, p.prec, false, nullptr, p.opt_pi && p.iters == 0);
   if (s) return s;
   if (p.certify && cert_dev) s = certify_dispatch(c, b, st, cert_dev);
   return s;
@@ -1594,6 +1636,57 @@ gcp_status optimize_batch(Ctx& c, Batch& b, const gcp_opt_params* p, double* out
 }
 
 // ------------------------------------------------------------------ dual import / export
+// theta (layer-major [R, d_i] blocks on the device) <-> host [R, sum d_i]
+gcp_status duals_theta(Ctx& c, Batch& b, const double* theta_in, double* theta_out) {
+  const Net& net = *b.net;
+  int64_t cols = 0;
+  for (int i = 1; i < net.L; ++i) cols += net.dims[i];
+  const size_t es = b.fp64 ? 8 : 4, bytes = (size_t)std::max<int64_t>(cols * b.R, 1) * es;
+  if (theta_in) {
+    for (int64_t q = 0; q < cols * b.R; ++q)
+      if (!std::isfinite(theta_in[q])) return c.fail(GCP_EINVAL, "theta: non-finite entry");
+    gcp_status s = GCP_OK;
+    char* d = (char*)b.ws("theta", bytes, &s);
+    if (!d) return s;
+    std::vector<char> h((size_t)cols * b.R * es);
+    int64_t off = 0, coff = 0;
+    for (int i = 1; i < net.L; ++i) {
+      const int di = net.dims[i];
+      for (int64_t r = 0; r < b.R; ++r)
+        for (int j = 0; j < di; ++j) {
+          const double v = theta_in[r * cols + coff + j];
+          const size_t k = (size_t)(off + r * di + j);
+          if (b.fp64) ((double*)h.data())[k] = v; else ((float*)h.data())[k] = (float)v;
+        }
+      off += b.R * di;
+      coff += di;
+    }
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (!e && !h.empty()) e = cudaMemcpy(d, h.data(), h.size(), cudaMemcpyHostToDevice);
+    if (e) return c.cuda(e, "import theta");
+    b.theta_on = true;
+  }
+  if (theta_out) {
+    if (!b.theta_on) return c.fail(GCP_ENOTFOUND, "the duals use the closed-form pi (no theta)");
+    std::vector<char> h((size_t)cols * b.R * es);
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (!e && !h.empty()) e = cudaMemcpy(h.data(), b.lazy["theta"], h.size(), cudaMemcpyDeviceToHost);
+    if (e) return c.cuda(e, "export theta");
+    int64_t off = 0, coff = 0;
+    for (int i = 1; i < net.L; ++i) {
+      const int di = net.dims[i];
+      for (int64_t r = 0; r < b.R; ++r)
+        for (int j = 0; j < di; ++j) {
+          const size_t k = (size_t)(off + r * di + j);
+          theta_out[r * cols + coff + j] = b.fp64 ? ((const double*)h.data())[k] : (double)((const float*)h.data())[k];
+        }
+      off += b.R * di;
+      coff += di;
+    }
+  }
+  return GCP_OK;
+}
+
 gcp_status duals_export(Ctx& c, Batch& b, double* alpha, double* beta, double* gamma) {
   const Net& net = *b.net;
   cudaError_t e = cudaStreamSynchronize(c.stream);
@@ -1636,6 +1729,7 @@ gcp_status duals_import(Ctx& c, Batch& b, const double* alpha, const double* bet
   const Net& net = *b.net;
   gcp_status s = reset_duals(c, b, !alpha, !beta, !gamma);
   if (s) return s;
+  b.theta_on = false;                 // back to the closed-form pi
   cudaError_t e = cudaStreamSynchronize(c.stream);
   if (e) return c.cuda(e, "import sync");
   const size_t es = b.fp64 ? 8 : 4;
@@ -1940,6 +2034,14 @@ gcp_status gcp_duals_export(gcp_ctx* h, void* duals, double* a, double* be, doub
   gcp::Batch* b = find_batch(c, duals);
   if (!b) return c->fail(GCP_ENOTFOUND, "unknown duals");
   return gcp::duals_export(*c, *b, a, be, g);
+}
+
+gcp_status gcp_duals_theta(gcp_ctx* h, void* duals, const double* theta_in, double* theta_out) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  CTX_GUARD(c);
+  gcp::Batch* b = find_batch(c, duals);
+  if (!b) return c->fail(GCP_ENOTFOUND, "unknown duals");
+  return gcp::duals_theta(*c, *b, theta_in, theta_out);
 }
 
 gcp_status gcp_duals_import(gcp_ctx* h, void* duals, const double* a, const double* be, const double* g) {

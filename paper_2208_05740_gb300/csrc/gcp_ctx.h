@@ -109,6 +109,9 @@ struct Batch {
   std::vector<void*> alpha;          // hidden layer i at index i-1, [R, d_i]
   void* beta = nullptr;              // [R, M]
   void* gamma = nullptr;             // [R, N]
+  // the workspace "theta" holds directly optimised ReLU duals (pi = theta
+  // [nuhat]_+) that every pass uses instead of the closed form
+  bool theta_on = false;
   std::vector<void*> owned;
   std::map<std::string, void*> lazy; // workspace by name
   std::map<std::string, size_t> lazy_bytes;
@@ -178,7 +181,8 @@ gcp_status duals_create_parts(Ctx& c, int net_id,
 gcp_status sync_check(Ctx& c, cudaStream_t st, const char* what);
 gcp_status reset_duals(Ctx& c, Batch& b, bool a, bool be, bool g);
 gcp_status optimize_on(Ctx& c, Batch& b, const gcp_opt_params& p, cudaStream_t st, double* cert_dev);
-gcp_status eval_dispatch(Ctx& c, Batch& b, cudaStream_t st, int prec, bool adj_start, const void* seed);
+gcp_status eval_dispatch(Ctx& c, Batch& b, cudaStream_t st, int prec, bool adj_start, const void* seed,
+                         bool theta_init = false);
 gcp_status certify_dispatch(Ctx& c, Batch& b, cudaStream_t st, double* out_dev);
 void serve_shutdown(Ctx& c);
 

@@ -87,6 +87,11 @@ struct RelaxArgs {
   float* nu_lo;         // [R, d]   low part nu - nu_out for the 3-pass tf32 GEMM, or nullptr
   T* nuhat_out;         // [R, d]
   T* obj_part;          // [ceil(d/32), R]: one partial per row and neuron chunk
+  // directly optimised ReLU duals pi = theta * [nuhat]_+ on unstable neurons
+  // (nullptr: Lemma A.1's closed form); theta_init: use the closed form and
+  // write the theta that reproduces it
+  T* theta;             // [R, d]
+  int theta_init;
 };
 
 template <typename T, typename Top>
@@ -112,6 +117,12 @@ struct AdjArgs {
   T* g_beta;            // [R, M]  dg/dbeta of the layer's splits (all modes; the gather steps beta)
   T* m_alpha; T* v_alpha;  // Adam state (mode 2)
   StepArgs<T> st;
+  // directly optimised pi = theta * [nuhat]_+ (nullptr: closed form); theta
+  // is stepped in place at alpha's rate when mode != 0, its gradient written
+  // to g_theta in mode 0
+  T* theta;             // [R, d]
+  T* g_theta;           // [R, d] (mode 0, may be nullptr)
+  T* m_theta; T* v_theta;  // Adam state (mode 2)
 };
 
 template <typename T, typename Top>
@@ -188,6 +199,7 @@ struct CertArgs {
   double* nu_out;        // [R, d]
   float* nuabs_out;      // [R, d] |nu| in float rounded up, or nullptr
   double* obj_part;      // [ceil(d/32), R] rounded-down partial sums
+  const Td* theta;       // [R, d] pi = theta * [nuhat]_+ on unstable neurons, or nullptr (closed form)
 };
 
 // ---------------------------------------------------------------- programmatic dependent launch

@@ -579,7 +579,10 @@ struct StageLayout {
 };
 
 // ------------------------------------------------------------------ eval
-template <typename T, typename Top, int V>
+// PI: the unstable neurons' pi is theta * [nuhat]_+ with theta a dual of its
+// own (App. A's closing remark), read from a.theta, or written there from
+// Lemma A.1's closed form when a.theta_init is set.
+template <typename T, typename Top, int V, bool PI>
 __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_eval(RelaxArgs<T, Top> a) {
   using Lay = StageLayout<V, 2, V, 3>;   // dense: y, alpha; fixed: acc
   constexpr int SPAN = Lay::SPAN, NS = kStages;
@@ -651,9 +654,12 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_eval(RelaxArgs<T, Top
       span_cut_sums<T, V>(a.csc, sc, a.N, w, sb + 2 * SPAN, a.gamma + r * a.N, acc, t, gg, sq, er);
       T term = T(0);
       if (w.on) {
-        T yv[V], al[V], nu[V], nh[V];
+        T yv[V], al[V], nu[V], nh[V], th[V];
         ldv_rw<V>(sb + w.lane * V, yv);
         ldv_rw<V>(sb + SPAN + w.lane * V, al);
+        if constexpr (PI) {
+          if (!a.theta_init) ldv_rw<V>(a.theta + ij, th);
+        }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           if (n.slot[v] >= 0) {        // split row -x <= 0 (x >= 0) or x <= 0
@@ -663,7 +669,11 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_eval(RelaxArgs<T, Top
           nh[v] = yv[v] - gg[v];
           // unstable: Lemma A.1 with q = -s
           const T C = tmax(nh[v], T(0));
-          const T pi = tmin(tmax((n.hi[v] * C - sq[v]) * n.iv[v], T(0)), C);
+          T pi = tmin(tmax((n.hi[v] * C - sq[v]) * n.iv[v], T(0)), C);
+          if constexpr (PI) {
+            if (a.theta_init) th[v] = C > T(0) ? tmin(pi / C, T(1)) : n.hi[v] * n.iv[v];
+            else pi = tmin(tmax(th[v], T(0)), T(1)) * C;
+          }
           const T hu = n.lo[v] * pi - tmax(T(0), n.hi[v] * (C - pi) + n.lo[v] * pi - sq[v]);
           const T nuu = pi - al[v] * tmax(-nh[v], T(0)) - t[v];
           const int cl = n.cls[v];
@@ -672,6 +682,9 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_eval(RelaxArgs<T, Top
         }
         put_operand_v<V, Top>(a.nu_out, a.nu_lo, ij, nu);
         stv<V>(a.nuhat_out + ij, nh);
+        if constexpr (PI) {
+          if (a.theta_init) stv<V>(a.theta + ij, th);
+        }
       }
       if (obj) span_partial<T, V>(a.obj_part, a.R, r, w.c, a.d, w.lane, term);
       dense(k + NS, st);
@@ -686,7 +699,7 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_eval(RelaxArgs<T, Top
 // ------------------------------------------------------------------ adjoint
 // Writes dg/dbeta of every split slot whose neuron is in this layer into
 // g_beta (the gradient output, or the input of the beta step in the gather).
-template <typename T, typename Top, int V>
+template <typename T, typename Top, int V, bool PI>
 __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_adj(AdjArgs<T, Top> a) {
   using Lay = StageLayout<V, 5, 0, 6>;   // dense: nubar, nuhat, alpha, m, v; fixed: acc, ev
   constexpr int SPAN = Lay::SPAN, NS = kStages;
@@ -759,6 +772,18 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_adj(AdjArgs<T, Top> a
       ldv_rw<V>(sb + 3 * SPAN + w.lane * V, ma);
       ldv_rw<V>(sb + 4 * SPAN + w.lane * V, va);
       T dt[V], dnh[V], dnhn[V], ds[V], ga[V];
+      T th[V], gt[V], mt[V], vt[V];     // pi = theta * [nuhat]_+ (PI)
+#pragma unroll
+      for (int v = 0; v < V; ++v) th[v] = gt[v] = mt[v] = vt[v] = T(0);
+      if constexpr (PI) {
+        if (w.on) {
+          ldv_rw<V>(a.theta + ij, th);
+          if (mode == 2) {
+            ldv_rw<V>(a.m_theta + ij, mt);
+            ldv_rw<V>(a.v_theta + ij, vt);
+          }
+        }
+      }
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         const T nb = nbv[v] - wr * n.bj[v];   // dg/dnu^(i)
@@ -768,6 +793,16 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_adj(AdjArgs<T, Top> a
         if (n.cls[v] == 1) {                       // active
           dnu_dnh = T(1);
           dh_ds = wr;
+        } else if (PI && n.cls[v] == 2) {
+          // pi = th C, q = u (C - pi) + l pi - s, h = l pi - max(q, 0), nu = pi - tau - t
+          const T tc = tmin(tmax(th[v], T(0)), T(1));
+          const bool pos = h > T(0);
+          const T C = pos ? h : T(0);
+          const bool act = hi * (C - tc * C) + lo * tc * C - sq[v] > T(0);
+          dnu_dnh = pos ? tc : (h < T(0) ? al[v] : T(0));
+          dh_dnh = pos ? wr * (lo * tc - (act ? hi * (T(1) - tc) + lo * tc : T(0))) : T(0);
+          dh_ds = act ? wr : T(0);
+          gt[v] = C * (nb + wr * (lo + (act ? hi - lo : T(0))));
         } else if (n.cls[v] == 2) {
           const T p0 = (hi * h - sq[v]) * iv;
           const bool pos = h > T(0);
@@ -800,6 +835,24 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_adj(AdjArgs<T, Top> a
           if (mode == 2) {
             stv<V>(a.m_alpha + ij, ma);
             stv<V>(a.v_alpha + ij, va);
+          }
+        }
+        if constexpr (PI) {
+          if (mode == 0) {
+            if (a.g_theta) stv<V>(a.g_theta + ij, gt);
+          } else if (n.unstable) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              if (n.cls[v] == 2) {
+                const T nt = step_apply(a.st, th[v], gt[v], a.st.lr_a, mt[v], vt[v]);
+                th[v] = tmin(tmax(nt, T(0)), T(1));
+              }
+            }
+            stv<V>(a.theta + ij, th);
+            if (mode == 2) {
+              stv<V>(a.m_theta + ij, mt);
+              stv<V>(a.v_theta + ij, vt);
+            }
           }
         }
         if (a.a_out) put_operand_v<V, Top>(a.a_out, a.a_lo, ij, dnh);
@@ -1089,7 +1142,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_relax(CertArgs<
       // unstable: explicit duals pi, gamma_r = C - pi, tau, mu = M - tau (all >= 0)
       const double C = fmax(nh, 0.0), Mm = fmax(-nh, 0.0);
       const double p0 = (hi * C - sq) * inv_ul;
-      const double pi = fmin(fmax(p0, 0.0), C);
+      // Lemma A.1's pi, or theta * C for directly optimised duals; either is
+      // in [0, C] (theta <= 1 and rounding is monotone), so gr >= 0
+      const double pi = a.theta ? fmin(fmax((double)a.theta[r * a.d + j], 0.0), 1.0) * C : fmin(fmax(p0, 0.0), C);
       const double gr = C - pi;
       const double al = fmin(fmax((double)a.alpha[r * a.d + j], 0.0), 1.0);
       const double tau = al * Mm;
@@ -1280,19 +1335,25 @@ void relax_eval(cudaStream_t st, const RelaxArgs<T, Top>& a) {
         reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") & chk_splits(a.sp, a.R, a.K, a.M) &
         chk_csc(a.csc, a.d) & reg_check(a.nu_out, Rd * sizeof(Top), "nu out") &
         reg_check(a.nu_lo, a.nu_lo ? Rd * 4.0 : 0.0, "nu lo") &
-        reg_check(a.nuhat_out, Rd * tb, "nuhat out") &
+        reg_check(a.nuhat_out, Rd * tb, "nuhat out") & reg_check(a.theta, a.theta ? Rd * tb : 0.0, "theta") &
         (!a.obj_part || reg_check(a.obj_part, ((a.d + 31) / 32) * (double)a.R * tb, "obj part"))))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
   if constexpr (sizeof(T) == 4) {
     if (span_v4<T>(a.d) && al16(a.y) && al16(a.alpha) && al16(a.lo) && al16(a.hi) && al16(a.bias) &&
-        al16(a.inv_ul) && al16(a.nu_out) && al16(a.nu_lo) && al16(a.nuhat_out)) {
-      launch_span(k_relax_eval<T, Top, 4>, span_smem<T, 4, 2, 4, 3>(), span_blocks(a.R, a.K, a.d, 4), st, a);
+        al16(a.inv_ul) && al16(a.nu_out) && al16(a.nu_lo) && al16(a.nuhat_out) && al16(a.theta)) {
+      if (a.theta)
+        launch_span(k_relax_eval<T, Top, 4, true>, span_smem<T, 4, 2, 4, 3>(), span_blocks(a.R, a.K, a.d, 4), st, a);
+      else
+        launch_span(k_relax_eval<T, Top, 4, false>, span_smem<T, 4, 2, 4, 3>(), span_blocks(a.R, a.K, a.d, 4), st, a);
       prof_end(st, tk);
       return;
     }
   }
-  launch_span(k_relax_eval<T, Top, 1>, span_smem<T, 1, 2, 1, 3>(), span_blocks(a.R, a.K, a.d, 1), st, a);
+  if (a.theta)
+    launch_span(k_relax_eval<T, Top, 1, true>, span_smem<T, 1, 2, 1, 3>(), span_blocks(a.R, a.K, a.d, 1), st, a);
+  else
+    launch_span(k_relax_eval<T, Top, 1, false>, span_smem<T, 1, 2, 1, 3>(), span_blocks(a.R, a.K, a.d, 1), st, a);
   prof_end(st, tk);
 }
 template <typename T, typename Top>
@@ -1320,19 +1381,29 @@ void relax_adjoint(cudaStream_t st, const AdjArgs<T, Top>& a) {
         reg_check(a.E, a.csc.n_entries ? (double)a.csc.n_total * a.R * tb : 0.0, "E") &
         reg_check(a.g_alpha, m0 ? Rd * tb : 0.0, "g_alpha") &
         reg_check(a.g_beta, a.M > 0 ? (double)a.M * a.R * tb : 0.0, "g_beta") &
-        reg_check(a.m_alpha, m2 ? Rd * tb : 0.0, "m_alpha") & reg_check(a.v_alpha, m2 ? Rd * tb : 0.0, "v_alpha")))
+        reg_check(a.m_alpha, m2 ? Rd * tb : 0.0, "m_alpha") & reg_check(a.v_alpha, m2 ? Rd * tb : 0.0, "v_alpha") &
+        reg_check(a.theta, a.theta ? Rd * tb : 0.0, "theta") &
+        reg_check(a.g_theta, (a.theta && m0 && a.g_theta) ? Rd * tb : 0.0, "g_theta") &
+        reg_check(a.m_theta, (a.theta && m2) ? Rd * tb : 0.0, "m_theta") &
+        reg_check(a.v_theta, (a.theta && m2) ? Rd * tb : 0.0, "v_theta")))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
   if constexpr (sizeof(T) == 4) {
     if (span_v4<T>(a.d) && al16(a.nubar) && al16(a.nuhat) && al16(a.alpha) && al16(a.m_alpha) &&
         al16(a.v_alpha) && al16(a.g_alpha) && al16(a.lo) && al16(a.hi) && al16(a.bias) && al16(a.inv_ul) &&
-        al16(a.a_out) && al16(a.a_lo)) {
-      launch_span(k_relax_adj<T, Top, 4>, span_smem<T, 4, 5, 0, 6>(), span_blocks(a.R, a.K, a.d, 4), st, a);
+        al16(a.a_out) && al16(a.a_lo) && al16(a.theta) && al16(a.g_theta) && al16(a.m_theta) && al16(a.v_theta)) {
+      if (a.theta)
+        launch_span(k_relax_adj<T, Top, 4, true>, span_smem<T, 4, 5, 0, 6>(), span_blocks(a.R, a.K, a.d, 4), st, a);
+      else
+        launch_span(k_relax_adj<T, Top, 4, false>, span_smem<T, 4, 5, 0, 6>(), span_blocks(a.R, a.K, a.d, 4), st, a);
       prof_end(st, tk);
       return;
     }
   }
-  launch_span(k_relax_adj<T, Top, 1>, span_smem<T, 1, 5, 0, 6>(), span_blocks(a.R, a.K, a.d, 1), st, a);
+  if (a.theta)
+    launch_span(k_relax_adj<T, Top, 1, true>, span_smem<T, 1, 5, 0, 6>(), span_blocks(a.R, a.K, a.d, 1), st, a);
+  else
+    launch_span(k_relax_adj<T, Top, 1, false>, span_smem<T, 1, 5, 0, 6>(), span_blocks(a.R, a.K, a.d, 1), st, a);
   prof_end(st, tk);
 }
 template <typename T, typename Top>
@@ -1412,6 +1483,7 @@ void certify_relax(cudaStream_t st, const CertArgs<Td>& a) {
         reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") & chk_splits(a.sp, a.R, a.K, a.M) &
         chk_csc(a.csc, a.d) & reg_check(a.nu_out, Rd * 8.0, "cert nu") &
         reg_check(a.nuabs_out, a.nuabs_out ? Rd * 4.0 : 0.0, "cert |nu|") &
+        reg_check(a.theta, a.theta ? Rd * tb : 0.0, "cert theta") &
         reg_check(a.obj_part, ((a.d + 31) / 32) * (double)a.R * 8.0, "cert part")))
     return;
   int tk = prof_begin(st, "certify_relax_f64", 0.0, bytes);

@@ -26,7 +26,7 @@ GCP_PGA, GCP_ADAM = 0, 1
 EXPORTED = ["gcp_create", "gcp_destroy", "gcp_last_error", "gcp_set_stream", "gcp_mem_used", "gcp_init_net",
             "gcp_intermediate_bounds", "gcp_bab_verify",
             "gcp_add_cuts", "gcp_duals_create", "gcp_duals_create_multi", "gcp_duals_shape", "gcp_duals_export", "gcp_duals_import",
-            "gcp_duals_free", "gcp_bound_batch", "gcp_grad_batch", "gcp_optimize_batch", "gcp_bound_device",
+            "gcp_duals_free", "gcp_duals_theta", "gcp_bound_batch", "gcp_grad_batch", "gcp_optimize_batch", "gcp_bound_device",
             "gcp_grad_device", "gcp_bound_dense_noalloc", "gcp_selftest_gemm", "gcp_selftest_gemm_f64", "gcp_profile_start", "gcp_profile_stop", "gcp_profile_query", "gcp_profile_report",
             "gcp_serve_start", "gcp_serve_submit", "gcp_serve_poll", "gcp_serve_wait",
             "gcp_serve_stop"]
@@ -57,7 +57,7 @@ class Subdomains(C.Structure):
 class OptParams(C.Structure):
     _fields_ = [("iters", C.c_int32), ("optimizer", C.c_int32), ("prec", C.c_int32), ("certify", C.c_int32),
                 ("lr_alpha", C.c_double), ("lr_beta", C.c_double), ("lr_gamma", C.c_double),
-                ("lr_decay", C.c_double)]
+                ("lr_decay", C.c_double), ("opt_pi", C.c_int32)]
 
 
 class BabParams(C.Structure):
@@ -107,6 +107,7 @@ def lib():
             "gcp_duals_export": [P, P, pd, pd, pd],
             "gcp_duals_import": [P, P, pd, pd, pd],
             "gcp_duals_free": [P, P],
+            "gcp_duals_theta": [P, P, pd, pd],
             "gcp_bound_batch": [P, P, I32, I32, pd, pd],
             "gcp_grad_batch": [P, P, I32, pd, pd, pd, pd],
             "gcp_optimize_batch": [P, P, C.POINTER(OptParams), pd, pd, pd],
@@ -150,8 +151,8 @@ def _c(a, dtype):
 
 
 def opt_params(iters, optimizer=GCP_PGA, prec=GCP_FP32, certify=1, lr_alpha=0.1, lr_beta=0.1, lr_gamma=0.1,
-               lr_decay=1.0) -> OptParams:
-    return OptParams(iters, optimizer, prec, certify, lr_alpha, lr_beta, lr_gamma, lr_decay)
+               lr_decay=1.0, opt_pi=0) -> OptParams:
+    return OptParams(iters, optimizer, prec, certify, lr_alpha, lr_beta, lr_gamma, lr_decay, opt_pi)
 
 
 class Duals:
@@ -330,6 +331,17 @@ class Context:
         self._check(lib().gcp_duals_export(self.h, D.handle, _ptr(a, C.c_double), _ptr(b, C.c_double),
                                            _ptr(g, C.c_double)))
         return a, b, g
+
+    def duals_theta(self, D: Duals, theta=None):
+        """The directly optimised ReLU duals theta [R, n_alpha] (pi = theta *
+        [nuhat]_+): sets them when theta is given, returns them otherwise."""
+        if theta is not None:
+            t = _c(theta, np.float64)
+            self._check(lib().gcp_duals_theta(self.h, D.handle, _ptr(t, C.c_double), None))
+            return None
+        out = np.zeros((D.rows, D.n_alpha))
+        self._check(lib().gcp_duals_theta(self.h, D.handle, None, _ptr(out, C.c_double)))
+        return out
 
     def duals_import(self, D: Duals, alpha=None, beta=None, gamma=None):
         a = None if alpha is None else _c(alpha, np.float64)
