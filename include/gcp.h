@@ -118,9 +118,10 @@ typedef struct {
  * opt_pi != 0: also optimise the ReLU duals pi (and gamma_r = C - pi) of every
  * unstable neuron directly, as App. A's closing remark suggests, instead of
  * Lemma A.1's closed form: pi = theta * [nuhat]_+ with theta in [0, 1] per row
- * and neuron, started at the closed form and stepped at lr_alpha. The duals
- * object then keeps theta (gcp_duals_theta) and every later bound,
- * gradient and certification of it uses theta until gcp_duals_import or an
+ * and neuron, stepped at lr_alpha; it starts at the closed form, or continues
+ * from the theta the duals object already holds (an earlier opt_pi call or
+ * gcp_duals_theta). The object keeps theta, and every later bound, gradient
+ * and certification of it uses theta until gcp_duals_import or an
  * optimisation with opt_pi = 0. Zero-initialise to leave it off. */
 typedef struct {
   int32_t iters, optimizer, prec, certify;

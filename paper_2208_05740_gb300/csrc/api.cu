@@ -1428,10 +1428,10 @@ static StepArgs<T> make_step(const gcp_opt_params& p, int it) {
 }
 
 template <typename T, typename Top>
-gcp_status optimize_steps(Ctx& c, Batch& b, cudaStream_t st, const gcp_opt_params& p) {
+gcp_status optimize_steps(Ctx& c, Batch& b, cudaStream_t st, const gcp_opt_params& p, bool theta_init) {
   for (int it = 0; it < p.iters; ++it) {
-    // with opt_pi, the first evaluation sets theta from the closed form
-    gcp_status s = run_eval<T, Top>(c, b, st, true, nullptr, false, p.opt_pi && it == 0);
+    // theta_init: the first evaluation sets theta from the closed form
+    gcp_status s = run_eval<T, Top>(c, b, st, true, nullptr, false, theta_init && it == 0);
     if (s) return s;
     s = run_adjoint<T, Top>(c, b, st, make_step<T>(p, it), nullptr, nullptr, nullptr, nullptr);
     if (s) return s;
@@ -1569,8 +1569,10 @@ gcp_status optimize_on(Ctx& c, Batch& b, const gcp_opt_params& p, cudaStream_t s
   if (p.iters < 0 || (p.optimizer != GCP_PGA && p.optimizer != GCP_ADAM) || !(p.lr_decay > 0))
     return c.fail(GCP_EINVAL, "bad optimiser parameters");
   if (b.R == 0) return GCP_OK;
-  // directly optimised pi (App. A's closing remark): theta and its Adam
-  // moments start afresh in every call, theta from the closed form
+  // directly optimised pi (App. A's closing remark): theta continues from the
+  // duals' own theta when they hold one, else it starts at the closed form;
+  // its Adam moments start afresh in every call
+  const bool theta_init = p.opt_pi && !b.theta_on;
   b.theta_on = false;
   if (p.opt_pi) {
     int64_t nal = 0;
@@ -1586,11 +1588,11 @@ gcp_status optimize_on(Ctx& c, Batch& b, const gcp_opt_params& p, cudaStream_t s
     }
     b.theta_on = true;
   }
-  if (p.prec == GCP_FP64) s = optimize_steps<double, double>(c, b, st, p);
-  else if (p.prec == GCP_FP32) s = optimize_steps<float, float>(c, b, st, p);
-  else s = optimize_steps<float, __nv_bfloat16>(c, b, st, p);
+  if (p.prec == GCP_FP64) s = optimize_steps<double, double>(c, b, st, p, theta_init);
+  else if (p.prec == GCP_FP32) s = optimize_steps<float, float>(c, b, st, p, theta_init);
+  else s = optimize_steps<float, __nv_bfloat16>(c, b, st, p, theta_init);
   if (s) return s;
-  s = eval_dispatch(c, b, st, p.prec, false, nullptr, p.opt_pi && p.iters == 0);
+  s = eval_dispatch(c, b, st, p.prec, false, nullptr, theta_init && p.iters == 0);
   if (s) return s;
   if (p.certify && cert_dev) s = certify_dispatch(c, b, st, cert_dev);
   return s;
