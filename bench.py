@@ -229,6 +229,24 @@ def oracle_sample(inst, n_sub, iters, seconds_cap=25.0):
                               f"extrapolated to {iters} steps + 2 evaluations"
 
 
+# --------------------------------------------------------------------------- ranks
+def max_over_ranks(x: float, device) -> float:
+    """The maximum of a per-rank scalar over all ranks of the job (its time is
+    the slowest rank's); the value itself without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, units_per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank * steps / seconds
+
+
 def run_reference(a):
     import numpy as np
     from paper_2208_05740_gb300 import synth
@@ -457,12 +475,8 @@ def main():
     times, (bound, cert, err), (launches_all, *_), _ = timed_steps(None)
     times_instr, _, _, (n_dom, ms_dom, fl_dom, by_dom) = timed_steps(dominant)
     clocks = sampler.stop()
-    total_s = sum(times) / 1000.0
-    if world > 1:
-        t = torch.tensor([total_s], device=f"cuda:{dev}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * a.n_sub * a.steps / total_s
+    total_s = max_over_ranks(sum(times) / 1000.0, f"cuda:{dev}")
+    value = job_value(world, a.n_sub, a.steps, total_s)
 
     # ---- end to end through the C ABI from host buffers
     sub = inst.sub
@@ -479,12 +493,8 @@ def main():
         b2, c2, r2 = ctx.optimize_batch(D2, params)
         ctx.duals_free(D2)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e_t)
-    if world > 1:
-        t = torch.tensor([e2e_s], device=f"cuda:{dev}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * a.n_sub * a.steps / e2e_s
+    e2e_s = max_over_ranks(sum(e2e_t), f"cuda:{dev}")
+    e2e_value = job_value(world, a.n_sub, a.steps, e2e_s)
 
     if rank != 0:
         return
