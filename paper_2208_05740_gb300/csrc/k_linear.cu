@@ -185,6 +185,40 @@ __global__ void k_conv_T(int64_t R, LayerGeom g, const Tin* __restrict__ W, cons
   }
 }
 
+// The transposed 1x1 convolution without padding (a residual block's
+// projection shortcut): out[r,c,ih,iw] = sum_o W[o,c] in[r,o,ih/s,iw/s] where s
+// divides ih and iw (and ih/s, iw/s lie in the source map), else 0. One thread
+// per output element in storage order, so the stores coalesce; the source row
+// (c_out x h_out x w_out) is re-read from L1/L2 by the c_in output channels.
+template <typename Tin, typename Tacc, bool ABS>
+__global__ void __launch_bounds__(256) k_conv_T_1x1(int64_t R, LayerGeom g, const Tin* __restrict__ W,
+                                                    const Tin* __restrict__ in, Tacc* __restrict__ out,
+                                                    const float* __restrict__ Wabs, const float* __restrict__ inabs,
+                                                    float* __restrict__ outabs) {
+  const int s = g.stride, HW = g.h_in * g.w_in, HWo = g.h_out * g.w_out;
+  const int64_t n = R * (int64_t)g.d_in;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / g.d_in;
+    const int rem = (int)(idx - r * g.d_in);
+    const int c = rem / HW, p = rem - c * HW;
+    const int ih = p / g.w_in, iw = p - ih * g.w_in;
+    const int oh = ih / s, ow = iw / s;
+    Tacc acc = Tacc(0);
+    float aacc = 0.f;
+    if (ih == oh * s && iw == ow * s && oh < g.h_out && ow < g.w_out) {
+      const Tin* ir = in + r * g.d_out + oh * g.w_out + ow;
+      const float* ia = ABS ? inabs + r * g.d_out + oh * g.w_out + ow : nullptr;
+      for (int o = 0; o < g.c_out; ++o) {
+        acc = fma(load_as<Tacc>(W + o * g.c_in + c), load_as<Tacc>(ir + (int64_t)o * HWo), acc);
+        if constexpr (ABS) aacc = __fmaf_ru(Wabs[o * g.c_in + c], ia[(int64_t)o * HWo], aacc);
+      }
+    }
+    out[idx] = acc;
+    if constexpr (ABS) outabs[idx] = aacc;
+  }
+}
+
 template <typename T>
 const char* tname();
 template <>
@@ -270,7 +304,10 @@ void conv_T(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const 
   char nm[32];
   snprintf(nm, sizeof nm, "conv_T_%s", tname<Tin>());
   int tk = prof_begin(st, nm, 2.0 * R * conv_macs(g), (double)R * (g.d_out * sizeof(Tin) + g.d_in * sizeof(Tacc)));
-  k_conv_T<Tin, Tacc, false><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, nullptr, nullptr, nullptr);
+  if (g.k == 1 && g.pad == 0)
+    k_conv_T_1x1<Tin, Tacc, false><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, nullptr, nullptr, nullptr);
+  else
+    k_conv_T<Tin, Tacc, false><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, nullptr, nullptr, nullptr);
   prof_end(st, tk);
 }
 
@@ -284,7 +321,10 @@ void conv_T_abs(cudaStream_t st, int64_t R, const LayerGeom& g, const double* W,
         reg_check(out, (double)R * g.d_in * 8.0, "convT out") & reg_check(outabs, (double)R * g.d_in * 4.0, "convT abs")))
     return;
   int tk = prof_begin(st, "conv_T_f64_certify", 2.0 * R * conv_macs(g), (double)R * (g.d_out * 12.0 + g.d_in * 12.0));
-  k_conv_T<double, double, true><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, Wabs, inabs, outabs);
+  if (g.k == 1 && g.pad == 0)
+    k_conv_T_1x1<double, double, true><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, Wabs, inabs, outabs);
+  else
+    k_conv_T<double, double, true><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, Wabs, inabs, outabs);
   prof_end(st, tk);
 }
 

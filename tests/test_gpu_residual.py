@@ -11,7 +11,7 @@ import pytest
 
 from oracle import gcp_oracle as O
 from paper_2208_05740_gb300 import gcp, synth
-from tests.helpers import assert_rel, join_alpha, oracle_duals
+from tests.helpers import assert_rel, join_alpha, oracle_duals, rows_of, select
 
 pytestmark = pytest.mark.gpu
 
@@ -240,3 +240,24 @@ def test_bad_skips_are_rejected(ctx):
                                                                     (256,), (256,)))
     with pytest.raises(ValueError):
         ctx.init_net(biased, inst.x_lo, inst.x_hi, inst.spec, inst.inter_lo, inst.inter_hi)
+
+
+def test_full_size_resnet_sampled_rows(ctx):
+    """The residual CNN (resnet2b shape) at the bench's size: 2048 subdomains x
+    9 rows, 500 cuts, BF16 ascent steps (tensor-core convolutions, a 1x1 stride-2
+    projection shortcut and an identity block), FP64 certification; 4 sampled
+    subdomains checked row by row against the oracle at the reached duals."""
+    inst = synth.cnn_resnet()
+    net_id, cs = ctx.load_instance(inst)
+    D = ctx.duals_create(net_id, cs, inst.sub, gcp.GCP_FP32)
+    bound, cert, _ = ctx.optimize_batch(D, gcp.opt_params(5, gcp.GCP_ADAM, gcp.GCP_BF16, 1, 0.1, 0.02, 0.02, 0.98))
+    A, B, G = ctx.duals_export(D)
+    idx = [0, 1, 1023, 2047]
+    rows = rows_of(inst, idx)
+    sub_inst = select(inst, idx)
+    P = O.build_problem(sub_inst)
+    ref = O.evaluate(P, oracle_duals(sub_inst, A[rows], B[rows][:, :P.max_splits], G[rows]))
+    assert_rel(bound[rows], ref, 1e-3, "sampled bf16")
+    assert_rel(cert[rows], ref, 1e-9, "sampled certified")
+    assert np.all(np.isfinite(bound)) and np.all(np.isfinite(cert))
+    ctx.duals_free(D)
