@@ -257,6 +257,19 @@ GCP_API gcp_status gcp_optimize_batch(gcp_ctx* ctx, void* duals, const gcp_opt_p
 GCP_API gcp_status gcp_intermediate_bounds(gcp_ctx* ctx, const gcp_layer_desc* layers, int32_t n_layers,
                                            const double* x_lo, const double* x_hi, const gcp_opt_params* p,
                                            double* inter_lo, double* inter_hi);
+/* The same with cutting planes (Eq. 15) in the propagation: hidden layer i's
+ * bounds take every cut whose variables all lie in layers 0 .. i-1 (the
+ * truncated network has them) with its multiplier gamma optimised together
+ * with the slopes. With p == NULL (gamma = 0) the result is
+ * gcp_intermediate_bounds'. The cuts must hold for every input of the box
+ * (for example cuts of the root MIP, Sec. 3.2): root bounds are bounds over
+ * the whole box. Cut arrays as in gcp_add_cuts (layer 0 = the input, kind
+ * GCP_VAR_X there). Errors as gcp_intermediate_bounds and gcp_add_cuts. */
+GCP_API gcp_status gcp_intermediate_bounds_cuts(gcp_ctx* ctx, const gcp_layer_desc* layers, int32_t n_layers,
+                                                const double* x_lo, const double* x_hi, const gcp_opt_params* p,
+                                                int32_t n_cuts, const int64_t* row_ptr, const int16_t* layer,
+                                                const int8_t* kind, const int32_t* index, const double* coef,
+                                                const double* d, double* inter_lo, double* inter_hi);
 
 /* Branch and bound over ReLU splits (Sec. 3.2, App. B) with this library's
  * bounding: proves that every spec row of the network is positive over the

@@ -25,6 +25,17 @@ namespace {
 
 constexpr int kBoundRows = 512;   // neurons of a layer bounded per batch (spec rows = 2x)
 
+// Cutting planes for the root bounds, CSR by cut as in gcp_add_cuts.
+struct CutRows {
+  int n = 0;
+  const int64_t* ptr = nullptr;
+  const int16_t* layer = nullptr;
+  const int8_t* kind = nullptr;
+  const int32_t* index = nullptr;
+  const double* coef = nullptr;
+  const double* d = nullptr;
+};
+
 double round_down(double x) { return std::nextafter(x, -INFINITY); }
 double round_up(double x) { return std::nextafter(x, INFINITY); }
 
@@ -58,7 +69,7 @@ void dense_rows(const gcp_layer_desc& d, int j0, int nj, std::vector<double>& W,
 }  // namespace
 
 gcp_status intermediate_bounds(Ctx& c, const gcp_layer_desc* layers, int L, const double* x_lo, const double* x_hi,
-                               const gcp_opt_params* p, double* out_lo, double* out_hi) {
+                               const gcp_opt_params* p, double* out_lo, double* out_hi, const CutRows* cuts = nullptr) {
   if (!layers || L < 2 || !x_lo || !x_hi || !out_lo || !out_hi)
     return c.fail(GCP_EINVAL, "gcp_intermediate_bounds: null argument or no hidden layer");
   for (int i = 0; i < L; ++i)
@@ -117,6 +128,19 @@ gcp_status intermediate_bounds(Ctx& c, const gcp_layer_desc* layers, int L, cons
   std::vector<int16_t> lay{0};
   std::vector<int8_t> sgn{0};
   const gcp_subdomains sub{1, ptr.data(), lay.data(), idx.data(), sgn.data()};
+  // each cut's deepest layer: it constrains the truncated networks of the layers below it
+  std::vector<int> cut_top;
+  if (cuts && cuts->n > 0) {
+    if (!cuts->ptr || !cuts->d || cuts->ptr[0] != 0) return c.fail(GCP_EINVAL, "cut arrays");
+    cut_top.assign(cuts->n, 0);
+    for (int k = 0; k < cuts->n; ++k) {
+      if (cuts->ptr[k + 1] < cuts->ptr[k]) return c.fail(GCP_EINVAL, "cut %d: row_ptr decreases", k);
+      for (int64_t e = cuts->ptr[k]; e < cuts->ptr[k + 1]; ++e) {
+        if (cuts->layer[e] < 0 || cuts->layer[e] >= L) return c.fail(GCP_EINVAL, "cut %d: layer out of range", k);
+        cut_top[k] = std::max<int>(cut_top[k], cuts->layer[e]);
+      }
+    }
+  }
   std::vector<double> S, bs;
   for (int i = 2; i < L; ++i) {
     const gcp_layer_desc& d = layers[i - 1];
@@ -150,8 +174,37 @@ gcp_status intermediate_bounds(Ctx& c, const gcp_layer_desc* layers, int L, cons
       gcp_status s = init_net(c, net.data(), i, x_lo, x_hi, spec.data(), 2 * nj, blo.data(), bhi.data(), &nid,
                               (d.skip && !d.shortcut) ? j0 : 0);
       if (s) return s;
+      // the cuts over layers 0 .. i-1 constrain this truncated network
+      int cs_id = -1;
+      if (!cut_top.empty()) {
+        std::vector<int64_t> ptr{0};
+        std::vector<int16_t> lay;
+        std::vector<int8_t> knd;
+        std::vector<int32_t> idx;
+        std::vector<double> cf, dd;
+        for (int k = 0; k < cuts->n; ++k) {
+          if (cut_top[k] > i - 1) continue;
+          for (int64_t e = cuts->ptr[k]; e < cuts->ptr[k + 1]; ++e) {
+            lay.push_back(cuts->layer[e]);
+            knd.push_back(cuts->kind[e]);
+            idx.push_back(cuts->index[e]);
+            cf.push_back(cuts->coef[e]);
+          }
+          ptr.push_back((int64_t)lay.size());
+          dd.push_back(cuts->d[k]);
+        }
+        if (!dd.empty()) {
+          int first = 0;
+          s = add_cuts(c, nid, (int)dd.size(), ptr.data(), lay.data(), knd.data(), idx.data(), cf.data(), dd.data(),
+                       &cs_id, &first);
+          if (s) {
+            c.nets.erase(nid);
+            return s;
+          }
+        }
+      }
       Batch* bt = nullptr;
-      s = duals_create(c, nid, -1, &sub, GCP_FP32, &bt);
+      s = duals_create(c, nid, cs_id, &sub, GCP_FP32, &bt);
       std::vector<double> cert((size_t)2 * nj);
       if (s == GCP_OK) {
         if (p) {
@@ -166,6 +219,7 @@ gcp_status intermediate_bounds(Ctx& c, const gcp_layer_desc* layers, int L, cons
         cudaStreamSynchronize(c.stream);
         c.batches.erase(bt);
       }
+      if (cs_id >= 0) c.cutsets.erase(cs_id);
       c.nets.erase(nid);
       if (s) return s;
       for (int q = 0; q < nj; ++q) {
@@ -193,4 +247,19 @@ extern "C" gcp_status gcp_intermediate_bounds(gcp_ctx* h, const gcp_layer_desc* 
   std::lock_guard<std::recursive_mutex> lk(c->mu);
   cudaSetDevice(c->device);
   return gcp::intermediate_bounds(*c, layers, n_layers, x_lo, x_hi, p, inter_lo, inter_hi);
+}
+
+extern "C" gcp_status gcp_intermediate_bounds_cuts(gcp_ctx* h, const gcp_layer_desc* layers, int32_t n_layers,
+                                                   const double* x_lo, const double* x_hi, const gcp_opt_params* p,
+                                                   int32_t n_cuts, const int64_t* row_ptr, const int16_t* layer,
+                                                   const int8_t* kind, const int32_t* index, const double* coef,
+                                                   const double* d, double* inter_lo, double* inter_hi) {
+  gcp::Ctx* c = reinterpret_cast<gcp::Ctx*>(h);
+  if (!c) return GCP_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  if (n_cuts < 0 || (n_cuts > 0 && (!row_ptr || !layer || !kind || !index || !coef || !d)))
+    return c->fail(GCP_EINVAL, "gcp_intermediate_bounds_cuts: bad cut arrays");
+  gcp::CutRows cr{n_cuts, row_ptr, layer, kind, index, coef, d};
+  return gcp::intermediate_bounds(*c, layers, n_layers, x_lo, x_hi, p, inter_lo, inter_hi, &cr);
 }

@@ -172,6 +172,8 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
                     const double* spec_c, int n_spec, const double* inter_lo, const double* inter_hi, int* out_id,
                     int last_skip_off = 0);
 gcp_status bound_batch(Ctx& c, Batch& b, int prec, int certify, double* out_bound, double* out_cert);
+gcp_status add_cuts(Ctx& c, int net_id, int n_cuts, const int64_t* row_ptr, const int16_t* layer, const int8_t* kind,
+                    const int32_t* index, const double* coef, const double* d, int* cutset_id, int* first_cut);
 gcp_status optimize_batch(Ctx& c, Batch& b, const gcp_opt_params* p, double* out_bound, double* out_cert,
                           double* out_err);
 gcp_status duals_create(Ctx& c, int net_id, int cutset_id, const gcp_subdomains* sub, int dual_prec, Batch** out);

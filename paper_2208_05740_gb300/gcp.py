@@ -24,7 +24,7 @@ GCP_FP64, GCP_FP32, GCP_BF16 = 0, 1, 2
 GCP_PGA, GCP_ADAM = 0, 1
 
 EXPORTED = ["gcp_create", "gcp_destroy", "gcp_last_error", "gcp_set_stream", "gcp_mem_used", "gcp_init_net",
-            "gcp_intermediate_bounds", "gcp_bab_verify",
+            "gcp_intermediate_bounds", "gcp_intermediate_bounds_cuts", "gcp_bab_verify",
             "gcp_add_cuts", "gcp_duals_create", "gcp_duals_create_multi", "gcp_duals_shape", "gcp_duals_export", "gcp_duals_import",
             "gcp_duals_free", "gcp_duals_theta", "gcp_bound_batch", "gcp_grad_batch", "gcp_optimize_batch", "gcp_bound_device",
             "gcp_grad_device", "gcp_bound_dense_noalloc", "gcp_selftest_gemm", "gcp_selftest_gemm_f64", "gcp_profile_start", "gcp_profile_stop", "gcp_profile_query", "gcp_profile_report",
@@ -112,6 +112,9 @@ def lib():
             "gcp_grad_batch": [P, P, I32, pd, pd, pd, pd],
             "gcp_optimize_batch": [P, P, C.POINTER(OptParams), pd, pd, pd],
             "gcp_intermediate_bounds": [P, C.POINTER(LayerDesc), I32, pd, pd, C.POINTER(OptParams), pd, pd],
+            "gcp_intermediate_bounds_cuts": [P, C.POINTER(LayerDesc), I32, pd, pd, C.POINTER(OptParams), I32,
+                                             C.POINTER(I64), C.POINTER(C.c_int16), C.POINTER(C.c_int8),
+                                             C.POINTER(I32), pd, pd, pd, pd],
             "gcp_bab_verify": [P, I32, I32, C.POINTER(BabParams), C.POINTER(BabResult)],
             "gcp_bound_device": [P, P, I32, P, P, P, P, P],
             "gcp_grad_device": [P, P, I32, P, P, P, P, P, P, P, P],
@@ -256,19 +259,30 @@ class Context:
                                        C.byref(nid)))
         return nid.value
 
-    def intermediate_bounds(self, layers, x_lo, x_hi, params: Optional[OptParams] = None):
+    def intermediate_bounds(self, layers, x_lo, x_hi, params: Optional[OptParams] = None, cuts=None):
         """Root bounds (lo, hi) of every hidden layer (list of arrays), by the
         library's own certified bound propagation: CROWN at the default
-        slopes (params None) or alpha-CROWN with params.iters ascent steps."""
+        slopes (params None) or alpha-CROWN with params.iters ascent steps.
+        cuts (ptr, layer, kind, index, coef, d, as for add_cuts; valid over the
+        whole box): each layer's bounds also use the cuts over the layers below
+        it, with their multipliers optimised (params given)."""
         keep = []
         descs = self._layer_descs(layers, keep)
         xl, xh = _c(x_lo, np.float64), _c(x_hi, np.float64)
         dims = [int(np.prod(ly.out_shape)) for ly in layers[:-1]]
         lo, hi = np.zeros(sum(dims)), np.zeros(sum(dims))
         pp = C.byref(params) if params is not None else None
-        self._check(lib().gcp_intermediate_bounds(self.h, descs, len(layers), _ptr(xl, C.c_double),
-                                                  _ptr(xh, C.c_double), pp, _ptr(lo, C.c_double),
-                                                  _ptr(hi, C.c_double)))
+        if cuts is None:
+            self._check(lib().gcp_intermediate_bounds(self.h, descs, len(layers), _ptr(xl, C.c_double),
+                                                      _ptr(xh, C.c_double), pp, _ptr(lo, C.c_double),
+                                                      _ptr(hi, C.c_double)))
+        else:
+            a = [_c(cuts.ptr, np.int64), _c(cuts.layer, np.int16), _c(cuts.kind, np.int8), _c(cuts.index, np.int32),
+                 _c(cuts.coef, np.float64), _c(cuts.d, np.float64)]
+            self._check(lib().gcp_intermediate_bounds_cuts(
+                self.h, descs, len(layers), _ptr(xl, C.c_double), _ptr(xh, C.c_double), pp, len(a[5]),
+                _ptr(a[0], C.c_int64), _ptr(a[1], C.c_int16), _ptr(a[2], C.c_int8), _ptr(a[3], C.c_int32),
+                _ptr(a[4], C.c_double), _ptr(a[5], C.c_double), _ptr(lo, C.c_double), _ptr(hi, C.c_double)))
         out_lo, out_hi, o = [], [], 0
         for d in dims:
             out_lo.append(lo[o:o + d].copy())
