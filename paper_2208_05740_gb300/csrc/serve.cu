@@ -432,6 +432,7 @@ gcp_status gcp_serve_submit(gcp_ctx* h, const gcp_request* req, uint64_t* ticket
     q->Mcap = std::max(1, M + req->rounds - 1);
     for (int i = 1; i < net.L; ++i) q->na += net.dims[i];
     q->estimate = gcp::estimate_bytes(net, q->R, N, nnz, q->Mcap);
+    if (q->p.opt_pi) q->estimate += (size_t)(12.0 * (double)q->R * (double)q->na);   // theta and its Adam moments
     if (c->budget && q->estimate > c->budget) return c->fail(GCP_EBUDGET, "request needs about %zu bytes", q->estimate);
   }
   gcp::Serve* sv = c->serve;
