@@ -303,6 +303,20 @@ typedef struct {
 } gcp_bab_result;
 GCP_API gcp_status gcp_bab_verify(gcp_ctx* ctx, int32_t net_id, int32_t cutset_id, const gcp_bab_params* bp,
                                   gcp_bab_result* res);
+/* Branch and bound label by label (Sec. 3.2: the easiest target label first,
+ * its root bound closest to zero, so that harder labels come later). Every
+ * spec row is bounded at the root (one batch, p->iters steps, certified);
+ * rows already positive are verified; each other row gets a branch and bound
+ * of its own (as gcp_bab_verify on that single row, with bp's limits per
+ * label). label_order[n_spec] receives the order in which the labels were
+ * settled (root-positive ones first), label_verified[n_spec] 1 (proved), 0
+ * (not proved) or -1 (not attempted: stop_at_failure != 0 and an earlier
+ * label failed). res sums rounds and domains over the root batch and the
+ * labels; min_bound is the smallest certified bound reached; verified = every
+ * label proved. */
+GCP_API gcp_status gcp_bab_verify_labels(gcp_ctx* ctx, int32_t net_id, int32_t cutset_id, const gcp_bab_params* bp,
+                                         int32_t stop_at_failure, int32_t* label_order, int32_t* label_verified,
+                                         gcp_bab_result* res);
 
 /* Device-pointer entry points behind the PyTorch autograd wrapper.
  * alpha/beta/gamma are float32 device arrays in the export layouts; they

@@ -10,6 +10,12 @@
 // order the paper uses so that cuts arriving later meet the hard domains).
 // The branching neuron of a subdomain is its not yet split root-unstable
 // neuron with the largest relaxation intercept -l u / (u - l).
+//
+// Label by label (the same section): every spec row (target label) is
+// bounded at the root, and the rows not yet positive get a branch and bound
+// of their own, the easiest first -- the root bound closest to zero -- so that
+// harder labels come later (when cuts from a MIP solver are stronger). Each
+// label runs on a one-row view of the network that shares its device data.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -185,7 +191,136 @@ gcp_status bab_verify(Ctx& c, int net_id, int cutset_id, const gcp_bab_params& b
   return GCP_OK;
 }
 
+namespace {
+
+// A one-spec-row view of a network: the same device weights and bounds, the
+// spec-derived arrays offset to row k; it owns nothing.
+int label_view(Ctx& c, const Net& net, int k) {
+  auto v = std::make_unique<Net>(net);
+  v->owned.clear();
+  const int dL = net.dims[net.L], dl1 = net.dims[net.L - 1];
+  v->K = 1;
+  v->C64 = net.C64 + (size_t)k * dL;
+  v->negC64 = net.negC64 + (size_t)k * dL;
+  v->YL64 = net.YL64 + (size_t)k * dl1;
+  v->YL32 = net.YL32 + (size_t)k * dl1;
+  v->cb64 = net.cb64 + k;
+  v->cb32 = net.cb32 + k;
+  if (net.skip[net.L - 1]) {
+    const int dm = net.dims[net.skip[net.L - 1] - 1];
+    if (net.SK64) v->SK64 = net.SK64 + (size_t)k * dm;
+    if (net.SK32) v->SK32 = net.SK32 + (size_t)k * dm;
+  }
+  const int id = c.next_id++;
+  c.nets[id] = std::move(v);
+  return id;
+}
+
+}  // namespace
+
+gcp_status bab_verify_labels(Ctx& c, int net_id, int cutset_id, const gcp_bab_params& bp, bool stop_at_failure,
+                             int32_t* order, int32_t* label_verified, gcp_bab_result& res) {
+  const auto t0 = std::chrono::steady_clock::now();
+  auto it = c.nets.find(net_id);
+  if (it == c.nets.end()) return c.fail(GCP_ENOTFOUND, "unknown network %d", net_id);
+  if (cutset_id >= 0 && c.cutsets.find(cutset_id) == c.cutsets.end())
+    return c.fail(GCP_ENOTFOUND, "unknown cut set %d", cutset_id);
+  const Net& net = *it->second;
+  const int K = net.K;
+  // root bounds of every label: one subdomain, no splits
+  std::vector<double> root(K);
+  {
+    std::vector<int32_t> ptr{0, 0};
+    std::vector<int16_t> lay{0};
+    std::vector<int32_t> idx{0};
+    std::vector<int8_t> sgn{0};
+    const gcp_subdomains sub{1, ptr.data(), lay.data(), idx.data(), sgn.data()};
+    Batch* b = nullptr;
+    gcp_status s = duals_create(c, net_id, cutset_id, &sub, GCP_FP32, &b);
+    gcp_opt_params p = bp.p;
+    p.certify = 1;
+    if (s == GCP_OK) s = optimize_batch(c, *b, &p, nullptr, root.data(), nullptr);
+    if (b) {
+      cudaStreamSynchronize(c.stream);
+      c.batches.erase(b);
+    }
+    if (s) return s;
+  }
+  // positive labels are done; the others by closeness of their root bound to zero
+  std::vector<int> lab(K);
+  for (int k = 0; k < K; ++k) lab[k] = k;
+  std::stable_sort(lab.begin(), lab.end(), [&](int a, int b) {
+    const bool pa = root[a] > 0, pb = root[b] > 0;
+    if (pa != pb) return pa;
+    return pa ? false : root[a] > root[b];
+  });
+  res = gcp_bab_result{};
+  res.rounds = 1;
+  res.domains_bounded = 1;
+  res.min_bound = INFINITY;
+  bool all = true, failed = false;
+  for (int q = 0; q < K; ++q) {
+    const int k = lab[q];
+    order[q] = k;
+    if (root[k] > 0) {
+      label_verified[k] = 1;
+      res.min_bound = std::min(res.min_bound, root[k]);
+      continue;
+    }
+    if (failed && stop_at_failure) {
+      label_verified[k] = -1;
+      all = false;
+      continue;
+    }
+    const int vid = label_view(c, net, k);
+    int vcs = -1;
+    if (cutset_id >= 0) {
+      auto cs = std::make_unique<CutSet>(*c.cutsets[cutset_id]);
+      cs->net_id = vid;
+      vcs = c.next_id++;
+      c.cutsets[vcs] = std::move(cs);
+    }
+    gcp_bab_result r{};
+    const gcp_status s = bab_verify(c, vid, vcs, bp, r);
+    if (vcs >= 0) c.cutsets.erase(vcs);
+    c.nets.erase(vid);
+    if (s) return s;
+    label_verified[k] = r.verified;
+    all = all && r.verified;
+    failed = failed || !r.verified;
+    res.rounds += r.rounds;
+    res.domains_bounded += r.domains_bounded;
+    res.domains_verified += r.domains_verified;
+    res.domains_left += r.domains_left;
+    res.min_bound = std::min(res.min_bound, r.min_bound);
+  }
+  res.verified = all ? 1 : 0;
+  res.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return GCP_OK;
+}
+
 }  // namespace gcp
+
+extern "C" gcp_status gcp_bab_verify_labels(gcp_ctx* h, int32_t net_id, int32_t cutset_id, const gcp_bab_params* bp,
+                                            int32_t stop_at_failure, int32_t* label_order, int32_t* label_verified,
+                                            gcp_bab_result* res) {
+  gcp::Ctx* c = reinterpret_cast<gcp::Ctx*>(h);
+  if (!c || !bp || !res || !label_order || !label_verified) return GCP_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  auto it = c->nets.find(net_id);
+  if (it == c->nets.end()) return c->fail(GCP_ENOTFOUND, "unknown network %d", net_id);
+  const int K = it->second->K;
+  std::vector<int32_t> ord(K), ver(K);
+  gcp_bab_result r{};
+  const gcp_status s = gcp::bab_verify_labels(*c, net_id, cutset_id, *bp, stop_at_failure != 0, ord.data(), ver.data(), r);
+  if (s == GCP_OK) {
+    std::copy(ord.begin(), ord.end(), label_order);
+    std::copy(ver.begin(), ver.end(), label_verified);
+    *res = r;
+  }
+  return s;
+}
 
 extern "C" gcp_status gcp_bab_verify(gcp_ctx* h, int32_t net_id, int32_t cutset_id, const gcp_bab_params* bp,
                                      gcp_bab_result* res) {

@@ -24,7 +24,7 @@ GCP_FP64, GCP_FP32, GCP_BF16 = 0, 1, 2
 GCP_PGA, GCP_ADAM = 0, 1
 
 EXPORTED = ["gcp_create", "gcp_destroy", "gcp_last_error", "gcp_set_stream", "gcp_mem_used", "gcp_init_net",
-            "gcp_intermediate_bounds", "gcp_intermediate_bounds_cuts", "gcp_bab_verify",
+            "gcp_intermediate_bounds", "gcp_intermediate_bounds_cuts", "gcp_bab_verify", "gcp_bab_verify_labels",
             "gcp_add_cuts", "gcp_duals_create", "gcp_duals_create_multi", "gcp_duals_shape", "gcp_duals_export", "gcp_duals_import",
             "gcp_duals_free", "gcp_duals_theta", "gcp_bound_batch", "gcp_grad_batch", "gcp_optimize_batch", "gcp_bound_device",
             "gcp_grad_device", "gcp_bound_dense_noalloc", "gcp_selftest_gemm", "gcp_selftest_gemm_f64", "gcp_profile_start", "gcp_profile_stop", "gcp_profile_query", "gcp_profile_report",
@@ -116,6 +116,8 @@ def lib():
                                              C.POINTER(I64), C.POINTER(C.c_int16), C.POINTER(C.c_int8),
                                              C.POINTER(I32), pd, pd, pd, pd],
             "gcp_bab_verify": [P, I32, I32, C.POINTER(BabParams), C.POINTER(BabResult)],
+            "gcp_bab_verify_labels": [P, I32, I32, C.POINTER(BabParams), I32, C.POINTER(I32), C.POINTER(I32),
+                                      C.POINTER(BabResult)],
             "gcp_bound_device": [P, P, I32, P, P, P, P, P],
             "gcp_grad_device": [P, P, I32, P, P, P, P, P, P, P, P],
             "gcp_bound_dense_noalloc": [I32, C.POINTER(I32), C.POINTER(P), C.POINTER(P), C.POINTER(P),
@@ -297,6 +299,19 @@ class Context:
         r = BabResult()
         self._check(lib().gcp_bab_verify(self.h, net_id, cutset_id, C.byref(bp), C.byref(r)))
         return {f: getattr(r, f) for f, _ in BabResult._fields_}
+
+    def bab_verify_labels(self, net_id: int, cutset_id: int, n_spec: int, params: OptParams, batch: int = 256,
+                          max_rounds: int = 100, max_domains: int = 1 << 16, timeout_s: float = 0.0,
+                          stop_at_failure: bool = False):
+        """Branch and bound label by label, the easiest first: (result dict,
+        order of the labels, per-label 1 proved / 0 not / -1 not attempted)."""
+        bp = BabParams(batch, max_rounds, max_domains, timeout_s, params)
+        r = BabResult()
+        order = np.zeros(n_spec, np.int32)
+        ver = np.zeros(n_spec, np.int32)
+        self._check(lib().gcp_bab_verify_labels(self.h, net_id, cutset_id, C.byref(bp), int(stop_at_failure),
+                                                _ptr(order, C.c_int32), _ptr(ver, C.c_int32), C.byref(r)))
+        return {f: getattr(r, f) for f, _ in BabResult._fields_}, order, ver
 
     def add_cuts(self, net_id: int, ptr, layer, kind, index, coef, d, cutset_id: int = -1):
         ptr = _c(ptr, np.int64)

@@ -88,3 +88,62 @@ def test_bab_with_cuts(ctx):
     n0, _ = _load(ctx, plain)
     r0 = ctx.bab_verify(n0, -1, gcp.opt_params(**PARAMS), batch=64, max_rounds=400)
     assert r0["verified"] == 1 and r["domains_bounded"] <= r0["domains_bounded"], (r, r0)
+
+
+def _two_labels(m0, m1):
+    """MLP 8-16-16-3 with its two spec rows e_y - e_a, e_y - e_b; the biases of
+    classes a and b shifted so that the exact minima (the oracle's MILP) are
+    m0 and m1."""
+    inst = synth.mlp_small()
+    C = inst.spec
+    root = synth.Subdomains(np.zeros(2, np.int32), np.zeros(0, np.int16), np.zeros(0, np.int32),
+                            np.zeros(0, np.int8))
+    base = dataclasses.replace(inst, sub=root, cuts=synth.Cuts.empty())
+    P = O.build_problem(base)
+    m = [O.lp_value(P, 0, k, integral=True, with_cuts=False) for k in range(2)]
+    last = inst.net.layers[-1]
+    b = last.b.copy()
+    for k, target in enumerate((m0, m1)):
+        other = int(np.argmin(C[k]))            # the -1 entry: class a (row 0) or b (row 1)
+        b[other] += m[k] - target              # raising f_a lowers f_y - f_a
+    net = synth.Network(inst.net.layers[:-1] + [dataclasses.replace(last, b=b)])
+    out = dataclasses.replace(base, net=net)
+    P2 = O.build_problem(out)
+    for k, target in enumerate((m0, m1)):
+        assert abs(O.lp_value(P2, 0, k, integral=True, with_cuts=False) - target) < 1e-6
+    return out
+
+
+def test_bab_label_by_label_easiest_first(ctx):
+    """Label 0's minimum is +0.05 (provable), label 1's -0.05 (false): the
+    labels are settled in the order of their root bounds closest to zero, the
+    first is proved and the second is not; with stop_at_failure the labels
+    after a failure are not attempted. Every label's verdict matches
+    gcp_bab_verify on that label alone."""
+    inst = _two_labels(0.05, -0.05)
+    net_id, cs = _load(ctx, inst)
+    p = gcp.opt_params(**PARAMS)
+    D = ctx.duals_create(net_id, cs, inst.sub, gcp.GCP_FP32)
+    _, root, _ = ctx.optimize_batch(D, p)
+    ctx.duals_free(D)
+    r, order, ver = ctx.bab_verify_labels(net_id, cs, 2, p, batch=64, max_rounds=400, max_domains=1 << 15)
+    pos = [k for k in range(2) if root[k] > 0]
+    neg = sorted([k for k in range(2) if root[k] <= 0], key=lambda k: -root[k])
+    assert list(order) == pos + neg
+    assert list(ver) == [1, 0] and r["verified"] == 0
+    for k in range(2):
+        one = dataclasses.replace(inst, spec=inst.spec[k:k + 1])
+        nk, ck = _load(ctx, one)
+        rk = ctx.bab_verify(nk, ck, p, batch=64, max_rounds=400, max_domains=1 << 15)
+        assert rk["verified"] == ver[k]
+    r2, order2, ver2 = ctx.bab_verify_labels(net_id, cs, 2, p, batch=64, max_rounds=400, max_domains=1 << 15,
+                                             stop_at_failure=True)
+    seen_fail = False
+    for k in order2:
+        if seen_fail:
+            assert ver2[k] == -1
+        seen_fail = seen_fail or ver2[k] == 0
+    proved = _two_labels(0.05, 0.1)
+    n2, c2 = _load(ctx, proved)
+    r3, _, ver3 = ctx.bab_verify_labels(n2, c2, 2, p, batch=64, max_rounds=400, max_domains=1 << 15)
+    assert list(ver3) == [1, 1] and r3["verified"] == 1 and r3["min_bound"] > 0
