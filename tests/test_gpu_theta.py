@@ -161,3 +161,29 @@ def test_zero_iterations_reproduce_the_closed_form(ctx):
     T = ctx.duals_theta(D)
     assert np.all((T >= 0) & (T <= 1))
     ctx.duals_free(D)
+
+
+def test_full_size_mlp_opt_pi_sampled_rows(ctx):
+    """The benchmark's MLP at its full batch (1024 subdomains x 9 rows, 200
+    cuts) with opt_pi in the FP32 chain, 20 Adam steps, FP64 certification;
+    four sampled subdomains checked row by row against the oracle at the
+    reached duals, theta included."""
+    from tests.helpers import rows_of, select
+    inst = synth.mlp_256x6()
+    net_id, cs = ctx.load_instance(inst)
+    D = ctx.duals_create(net_id, cs, inst.sub, gcp.GCP_FP32)
+    bound, cert, _ = ctx.optimize_batch(D, gcp.opt_params(20, gcp.GCP_ADAM, gcp.GCP_FP32, 1, 0.1, 0.02, 0.02, 0.98,
+                                                          opt_pi=1))
+    A, B, G = ctx.duals_export(D)
+    T = ctx.duals_theta(D)
+    idx = [0, 1, 511, 1023]
+    rows = rows_of(inst, idx)
+    sub_inst = select(inst, idx)
+    P = O.build_problem(sub_inst)
+    Dr = oracle_duals(sub_inst, A[rows], B[rows][:, :P.max_splits], G[rows])
+    Dr.theta = split_alpha(sub_inst, T[rows])
+    ref = O.evaluate(P, Dr)
+    assert_rel(bound[rows], ref, 1e-5, "sampled fp32 with theta")
+    assert_rel(cert[rows], ref, 1e-9, "sampled certified with theta")
+    assert np.all(np.isfinite(bound)) and np.all(np.isfinite(cert))
+    ctx.duals_free(D)
