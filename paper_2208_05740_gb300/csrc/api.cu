@@ -226,7 +226,13 @@ void* Batch::ws(const std::string& name, size_t bytes, gcp_status* st) {
     }
     lazy.erase(it);
   }
-  void* p = ctx->alloc(bytes);
+  void* p = nullptr;
+  if (pool_stream) {
+    AllocPool g;
+    p = ctx->alloc(bytes);
+  } else {
+    p = ctx->alloc(bytes);
+  }
   if (!p) {
     *st = ctx->over_budget ? ctx->fail(GCP_EBUDGET, "device memory budget exceeded (%s)", name.c_str())
                            : ctx->fail(GCP_ENOMEM, "cudaMalloc of %zu bytes failed (%s)", bytes, name.c_str());
@@ -1983,8 +1989,15 @@ gcp_status gcp_duals_create(gcp_ctx* h, int32_t net_id, int32_t cutset_id, const
   Ctx* c = reinterpret_cast<Ctx*>(h);
   CTX_GUARD(c);
   gcp::Batch* b = nullptr;
-  gcp_status s = gcp::duals_create(*c, net_id, cutset_id, sub, dual_prec, &b);
+  gcp_status s;
+  {
+    // blocks come from (and go back to) the context's pool: a batch created
+    // and freed every step reuses the previous one's memory
+    gcp::AllocPool g;
+    s = gcp::duals_create(*c, net_id, cutset_id, sub, dual_prec, &b);
+  }
   if (s == GCP_OK) {
+    b->pool_stream = c->stream;
     s = gcp::sync_check(*c, c->stream, "duals_create");
     if (s == GCP_OK) *duals = b;
   }
@@ -2007,8 +2020,13 @@ gcp_status gcp_duals_create_multi(gcp_ctx* h, int32_t net_id, int32_t n_queries,
     parts.push_back({cs, &subs[q]});
   }
   gcp::Batch* b = nullptr;
-  gcp_status s = gcp::duals_create_parts(*c, net_id, parts, dual_prec, &b);
+  gcp_status s;
+  {
+    gcp::AllocPool g;
+    s = gcp::duals_create_parts(*c, net_id, parts, dual_prec, &b);
+  }
   if (s == GCP_OK) {
+    b->pool_stream = c->stream;
     s = gcp::sync_check(*c, c->stream, "duals_create_multi");
     if (s == GCP_OK) *duals = b;
   }

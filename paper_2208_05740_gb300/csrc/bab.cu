@@ -103,8 +103,13 @@ gcp_status bab_verify(Ctx& c, int net_id, int cutset_id, const gcp_bab_params& b
     sgn.push_back(0);
     const gcp_subdomains sub{(int32_t)n, ptr.data(), lay.data(), idx.data(), sgn.data()};
     Batch* b = nullptr;
-    gcp_status s = duals_create(c, net_id, cutset_id, &sub, GCP_FP32, &b);
+    gcp_status s;
+    {
+      AllocPool g;   // every round's batch reuses the previous round's memory
+      s = duals_create(c, net_id, cutset_id, &sub, GCP_FP32, &b);
+    }
     if (s) return s;
+    b->pool_stream = c.stream;
     const int64_t R = b->R;
     const int M = b->M, N = b->N;
     std::vector<double> A((size_t)R * na), Bt((size_t)R * std::max(M, 1)), G((size_t)R * std::max(N, 1));
