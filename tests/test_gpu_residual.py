@@ -261,3 +261,29 @@ def test_full_size_resnet_sampled_rows(ctx):
     assert_rel(cert[rows], ref, 1e-9, "sampled certified")
     assert np.all(np.isfinite(bound)) and np.all(np.isfinite(cert))
     ctx.duals_free(D)
+
+
+def test_serving_a_residual_network_alone_and_in_a_mix():
+    """The serving loop on residual networks (the resnet2b-shaped CNN with its
+    projection shortcut and a residual MLP with opt_pi): each request's result
+    is the same alone and in a mix with another network's request."""
+    rn = synth.cnn_resnet(hw=16, stem=8, blocks=((16, 2), (16, 1)), fc=64, n_sub=6, n_cuts=40)
+    mlp = CASES[0][1]
+    p = gcp.opt_params(10, gcp.GCP_ADAM, gcp.GCP_BF16, 1, 0.1, 0.02, 0.02, 0.98)
+    q = gcp.opt_params(10, gcp.GCP_ADAM, gcp.GCP_BF16, 1, 0.1, 0.02, 0.02, 0.98, opt_pi=1)
+    with gcp.Context(0) as c:
+        nr, cr = c.load_instance(rn)
+        nm, cm = c.load_instance(mlp)
+        c.serve_start(8)
+        r1, alone_r = c.serve_wait(c.serve_submit(nr, cr, rn.sub, p, 3, 11), rn.n_rows + 64)
+        r2, alone_m = c.serve_wait(c.serve_submit(nm, cm, mlp.sub, q, 3, 12), mlp.n_rows + 64)
+        t1 = c.serve_submit(nr, cr, rn.sub, p, 3, 11)
+        t2 = c.serve_submit(nm, cm, mlp.sub, q, 3, 12)
+        s1, mixed_r = c.serve_wait(t1, rn.n_rows + 64)
+        s2, mixed_m = c.serve_wait(t2, mlp.n_rows + 64)
+        c.serve_stop()
+    for r in (r1, r2, s1, s2):
+        assert r.status == 0
+    assert_rel(mixed_r[:r1.rows], alone_r[:r1.rows], 1e-9, "resnet alone vs mixed")
+    assert_rel(mixed_m[:r2.rows], alone_m[:r2.rows], 1e-9, "residual MLP (opt_pi) alone vs mixed")
+    assert np.all(np.isfinite(alone_r[:r1.rows])) and np.all(np.isfinite(alone_m[:r2.rows]))
