@@ -1084,6 +1084,69 @@ static T* theta_of(Batch& b, int i) {
   return (T*)it->second + off;
 }
 
+// Stored or recomputed nuhat for the adjoint. Storing costs R * (d_1 + ..
+// + d_{L-1}) values; recomputing needs three buffers of the widest hidden
+// layer and re-runs the evaluation from the top down to each layer (about
+// L/2 times the evaluation's work). The adjoint recomputes when the memory
+// budget cannot hold the stored copies and recomputing saves memory, or when
+// GCP_NUHAT=recompute asks for it; not for networks with skip connections
+// (their parked terms share the evaluation's buffers).
+static bool want_recompute(const Ctx& c, const Batch& b, size_t es) {
+  const Net& net = *b.net;
+  for (int i = 0; i < net.L; ++i)
+    if (net.skip[i]) return false;
+  const char* e = std::getenv("GCP_NUHAT");
+  if (e && std::strcmp(e, "recompute") == 0) return true;
+  if (e && std::strcmp(e, "store") == 0) return false;
+  int64_t sum = 0, mx = 0;
+  for (int i = 1; i < net.L; ++i) {
+    sum += net.dims[i];
+    mx = std::max<int64_t>(mx, net.dims[i]);
+  }
+  if (!c.budget || 3 * mx >= sum) return false;
+  return c.used + (uint64_t)b.R * sum * es > c.budget;
+}
+
+static int64_t max_hidden(const Net& net) {
+  int64_t mx = 1;
+  for (int i = 1; i < net.L; ++i) mx = std::max<int64_t>(mx, net.dims[i]);
+  return mx;
+}
+
+// nuhat^(target) recomputed: the evaluation's layers from the top down to
+// `target` (no objective), on buffers of its own; the duals of these layers
+// are the ones the evaluation used (the adjoint steps them after this call).
+template <typename T, typename Top>
+static const T* recompute_nuhat(Ctx& c, Batch& b, cudaStream_t st, int target, gcp_status* s) {
+  const Net& net = *b.net;
+  const int L = net.L;
+  const int64_t R = b.R, mh = max_hidden(net);
+  Top* nu = (Top*)b.ws("rc_nu", (size_t)R * mh * sizeof(Top), s);
+  T* y = nu ? (T*)b.ws("rc_y", (size_t)R * mh * sizeof(T), s) : nullptr;
+  T* nh = y ? (T*)b.ws("rc_nuhat", (size_t)R * mh * sizeof(T), s) : nullptr;
+  if (!nh) return nullptr;
+  SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp, b.sp_tab};
+  for (int i = L - 1; i >= target; --i) {
+    RelaxArgs<T, Top> a{};
+    a.R = R; a.K = b.K; a.d = net.dims[i]; a.layer = i; a.M = b.M; a.N = b.N;
+    a.y = (i == L - 1) ? TSel<T>::YL(net) : y;
+    a.y_per_spec = (i == L - 1);
+    a.lo = TSel<T>::lo(net, i); a.hi = TSel<T>::hi(net, i); a.bias = TSel<T>::b(net, i);
+    a.inv_ul = TSel<T>::inv(net, i);
+    a.alpha = (const T*)b.alpha[i - 1];
+    a.beta = (const T*)b.beta;
+    a.gamma = (const T*)b.gamma;
+    a.sp = sp;
+    a.csc = csc_of<T>(b, i);
+    a.nu_out = nu;
+    a.nuhat_out = nh;
+    a.theta = theta_of<T>(b, i);
+    relax_eval<T, Top>(st, a);
+    if (i > target) lin_backward<Top, T>(st, b, i, nu, nullptr, y);
+  }
+  return nh;
+}
+
 // Evaluate g for all rows at the batch's duals. with_adjoint_start: also write
 // a0 = -seed*x* into the operand buffer and the input-layer cut entries into E.
 // finalize = false leaves g itself out (ascent steps need only the gradient).
@@ -1109,9 +1172,16 @@ gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, 
     if (!E) return s;
   }
   SplitsDev sp{b.sp_ptr, b.sp_layer, b.sp_index, b.sp_sign, b.nsp, b.sp_tab};
+  if (with_adjoint_start && !b.recompute_decided) {
+    b.recompute = want_recompute(c, b, sizeof(T));
+    b.recompute_decided = true;
+  }
+  // nuhat per layer only where the adjoint will read it; otherwise one scratch row block
+  const bool keep = with_adjoint_start && !b.recompute;
   int poff = 0;
   for (int i = L - 1; i >= 1; --i) {
-    T* nuhat = (T*)b.ws("nuhat" + std::to_string(i), (size_t)R * net.dims[i] * sizeof(T), &s);
+    T* nuhat = keep ? (T*)b.ws("nuhat" + std::to_string(i), (size_t)R * net.dims[i] * sizeof(T), &s)
+                    : (T*)b.ws("rc_nuhat", (size_t)R * max_hidden(net) * sizeof(T), &s);
     if (!nuhat) return s;
     RelaxArgs<T, Top> a{};
     a.R = R; a.K = b.K; a.d = net.dims[i]; a.layer = i; a.M = b.M; a.N = b.N;
@@ -1222,7 +1292,9 @@ gcp_status run_adjoint(Ctx& c, Batch& b, cudaStream_t st, const StepArgs<T>& ste
         skip_add<Top, T>(st, R, net.dims[i], net.dims[i], 0, src, 0, y);
       }
     }
-    const T* nuhat = (const T*)b.lazy["nuhat" + std::to_string(i)];
+    const T* nuhat = b.recompute ? recompute_nuhat<T, Top>(c, b, st, i, &s)
+                                 : (const T*)b.lazy["nuhat" + std::to_string(i)];
+    if (!nuhat) return s;
     AdjArgs<T, Top> a{};
     a.R = R; a.K = b.K; a.d = net.dims[i]; a.layer = i; a.M = b.M; a.N = b.N;
     a.nubar = y; a.seed = seed;

@@ -100,6 +100,9 @@ struct Batch {
   int32_t* sub_cut_hi = nullptr;     // [S] end of the query's cuts
   bool fp64 = false;
   bool tc = true;                    // use the tcgen05 GEMMs where shapes allow
+  // the adjoint recomputes each layer's nuhat from the top instead of reading
+  // it stored by the evaluation (decided at the first adjoint evaluation)
+  bool recompute = false, recompute_decided = false;
   CutDev cuts;
   int32_t* sp_ptr = nullptr;
   int16_t* sp_layer = nullptr;
