@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <memory>
 #include <vector>
 
 #include "gcp_ctx.h"
@@ -26,20 +27,36 @@
 namespace gcp {
 namespace {
 
+// One round's duals kept on the device for the children of its subdomains
+// (alpha row-major [rows, na], beta [rows, M], gamma [rows, N]); its blocks go
+// back to the context's pool once the last child has been bounded (after that
+// round's stream synchronisation).
+struct ParentStore {
+  Ctx* c = nullptr;
+  float* alpha = nullptr;
+  float* beta = nullptr;
+  float* gamma = nullptr;
+  int64_t rows = 0;
+  int M = 0;
+  ~ParentStore() {
+    if (!c) return;
+    c->recycle(alpha);
+    c->recycle(beta);
+    c->recycle(gamma);
+  }
+};
+
 struct Domain {
   std::vector<int16_t> lay;
   std::vector<int32_t> idx;
   std::vector<int8_t> sgn;
   double margin = -INFINITY;    // priority: the parent's smallest certified bound
-  std::vector<float> alpha;     // [K, na] parent's duals (empty: defaults)
-  std::vector<float> beta;      // [K, splits of the parent]
-  std::vector<float> gamma;     // [K, N]
+  std::shared_ptr<ParentStore> par;   // the parent's duals (null: defaults)
+  int64_t prow = 0;                   // the parent's first row in it
 };
 
 }  // namespace
 
-gcp_status duals_export(Ctx& c, Batch& b, double* alpha, double* beta, double* gamma);
-gcp_status duals_import(Ctx& c, Batch& b, const double* alpha, const double* beta, const double* gamma);
 
 gcp_status bab_verify(Ctx& c, int net_id, int cutset_id, const gcp_bab_params& bp, gcp_bab_result& res) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -112,29 +129,86 @@ gcp_status bab_verify(Ctx& c, int net_id, int cutset_id, const gcp_bab_params& b
     b->pool_stream = c.stream;
     const int64_t R = b->R;
     const int M = b->M, N = b->N;
-    std::vector<double> A((size_t)R * na), Bt((size_t)R * std::max(M, 1)), G((size_t)R * std::max(N, 1));
-    // warm start: the parents' duals (new split slots and defaults elsewhere)
+    const int L1 = net.L - 1;
+    // warm start: each child's rows from its parent's rows on the device (new split slots 0)
     bool warm = false;
-    for (const Domain& d : cur) warm |= !d.alpha.empty();
-    if (warm) {
-      s = duals_export(c, *b, A.data(), Bt.data(), G.data());
-      for (size_t q = 0; q < n && s == GCP_OK; ++q) {
+    for (const Domain& d : cur) warm |= (bool)d.par;
+    if (warm && L1 > 0) {
+      std::vector<WarmSrc> src((size_t)R);
+      for (size_t q = 0; q < n; ++q) {
         const Domain& d = cur[q];
-        if (d.alpha.empty()) continue;
-        const int np = (int)d.beta.size() / K;
         for (int k = 0; k < K; ++k) {
-          const int64_t r = (int64_t)q * K + k;
-          for (int64_t j = 0; j < na; ++j) A[r * na + j] = d.alpha[(size_t)k * na + j];
-          for (int m = 0; m < np && m < M; ++m) Bt[r * M + m] = d.beta[(size_t)k * np + m];
-          for (int m = np; m < M; ++m) Bt[r * M + m] = 0.0;
-          for (int e = 0; e < N; ++e) G[r * N + e] = d.gamma[(size_t)k * N + e];
+          WarmSrc& w = src[q * K + k];
+          w = WarmSrc{};
+          if (!d.par) continue;
+          const int64_t pr = d.prow + k;
+          if (pr < 0 || pr >= d.par->rows) {
+            cudaStreamSynchronize(c.stream);
+            c.batches.erase(b);
+            return c.fail(GCP_EINVAL, "branch and bound: parent row %lld outside its store", (long long)pr);
+          }
+          w.alpha = d.par->alpha + pr * na;
+          w.beta = d.par->M > 0 ? d.par->beta + pr * d.par->M : nullptr;
+          w.gamma = N > 0 ? d.par->gamma + pr * N : nullptr;
+          w.np = std::min<int>((int)d.lay.size() - 1, d.par->M);
         }
       }
-      if (s == GCP_OK) s = duals_import(c, *b, A.data(), M > 0 ? Bt.data() : nullptr, N > 0 ? G.data() : nullptr);
+      std::vector<int> dims(L1);
+      std::vector<float*> aptr(L1);
+      for (int l = 0; l < L1; ++l) {
+        dims[l] = net.dims[l + 1];
+        aptr[l] = (float*)b->alpha[l];
+      }
+      WarmSrc* src_d = (WarmSrc*)b->ws("bab_src", src.size() * sizeof(WarmSrc), &s);
+      int* dims_d = src_d ? (int*)b->ws("bab_dims", dims.size() * sizeof(int), &s) : nullptr;
+      float** aptr_d = dims_d ? (float**)b->ws("bab_aptr", aptr.size() * sizeof(float*), &s) : nullptr;
+      if (aptr_d) {
+        cudaMemcpyAsync(src_d, src.data(), src.size() * sizeof(WarmSrc), cudaMemcpyHostToDevice, c.stream);
+        cudaMemcpyAsync(dims_d, dims.data(), dims.size() * sizeof(int), cudaMemcpyHostToDevice, c.stream);
+        cudaMemcpyAsync(aptr_d, aptr.data(), aptr.size() * sizeof(float*), cudaMemcpyHostToDevice, c.stream);
+        bab_warm_start(c.stream, R, L1, dims_d, aptr_d, na, (float*)b->beta, M, (float*)b->gamma, N, src_d);
+        if (!reg_take_error().empty()) s = c.fail(GCP_EDEVICE, "branch and bound: warm start launch check");
+      }
     }
     std::vector<double> cert((size_t)R);
     if (s == GCP_OK) s = optimize_batch(c, *b, &p, nullptr, cert.data(), nullptr);
-    if (s == GCP_OK) s = duals_export(c, *b, A.data(), Bt.data(), G.data());
+    // the subdomains that branch keep this round's duals on the device for their children
+    std::shared_ptr<ParentStore> store;
+    if (s == GCP_OK) {
+      bool branching = false;
+      for (size_t q = 0; q < n && !branching; ++q)
+        for (int k = 0; k < K; ++k) branching |= !(cert[q * K + k] > 0);
+      if (branching) {
+        store = std::make_shared<ParentStore>();
+        store->c = &c;
+        store->rows = R;
+        store->M = M;
+        {
+          AllocPool g;
+          store->alpha = (float*)c.alloc((size_t)R * std::max<int64_t>(na, 1) * 4);
+          store->beta = (float*)c.alloc((size_t)R * std::max(M, 1) * 4);
+          store->gamma = (float*)c.alloc((size_t)R * std::max(N, 1) * 4);
+        }
+        if (!store->alpha || !store->beta || !store->gamma) {
+          s = c.fail(c.over_budget ? GCP_EBUDGET : GCP_ENOMEM, "branch and bound: parent store");
+        } else {
+          int64_t off = 0;
+          for (int l = 0; l < L1 && s == GCP_OK; ++l) {
+            const int d = net.dims[l + 1];
+            const cudaError_t e = cudaMemcpy2DAsync(store->alpha + off, (size_t)na * 4, b->alpha[l], (size_t)d * 4,
+                                                    (size_t)d * 4, (size_t)R, cudaMemcpyDeviceToDevice, c.stream);
+            if (e) s = c.cuda(e, "branch and bound: store alpha");
+            off += d;
+          }
+          if (s == GCP_OK && M > 0)
+            s = c.cuda(cudaMemcpyAsync(store->beta, b->beta, (size_t)R * M * 4, cudaMemcpyDeviceToDevice, c.stream),
+                       "branch and bound: store beta");
+          if (s == GCP_OK && N > 0)
+            s = c.cuda(cudaMemcpyAsync(store->gamma, b->gamma, (size_t)R * N * 4, cudaMemcpyDeviceToDevice,
+                                       c.stream), "branch and bound: store gamma");
+        }
+      }
+    }
     cudaStreamSynchronize(c.stream);
     c.batches.erase(b);
     if (s) return s;
@@ -164,14 +238,6 @@ gcp_status bab_verify(Ctx& c, int net_id, int cutset_id, const gcp_bab_params& b
         res.min_bound = std::min(res.min_bound, m);
         continue;
       }
-      const int np = (int)d.lay.size();
-      std::vector<float> al((size_t)K * na), be((size_t)K * np), ga((size_t)K * N);
-      for (int k = 0; k < K; ++k) {
-        const int64_t r = (int64_t)q * K + k;
-        for (int64_t j = 0; j < na; ++j) al[(size_t)k * na + j] = (float)A[r * na + j];
-        for (int e = 0; e < np; ++e) be[(size_t)k * np + e] = (float)Bt[r * M + e];
-        for (int e = 0; e < N; ++e) ga[(size_t)k * N + e] = (float)G[r * N + e];
-      }
       for (int side = 0; side < 2; ++side) {
         Domain ch;
         ch.lay = d.lay;
@@ -181,9 +247,8 @@ gcp_status bab_verify(Ctx& c, int net_id, int cutset_id, const gcp_bab_params& b
         ch.idx.push_back(pick->index);
         ch.sgn.push_back(side == 0 ? 1 : -1);
         ch.margin = m;
-        ch.alpha = al;
-        ch.beta = be;
-        ch.gamma = ga;
+        ch.par = store;
+        ch.prow = (int64_t)q * K;
         pending.push_back(std::move(ch));
       }
     }

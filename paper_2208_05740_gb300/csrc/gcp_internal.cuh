@@ -272,6 +272,20 @@ void skip_add(cudaStream_t st, int64_t R, int d, int ld, int off, const Ts* src,
 void skip_add_cert(cudaStream_t st, int64_t R, int d, int ld, int off, const double* src, const float* src_abs,
                    int src_mod, double* y, float* yabs);
 
+// Branch and bound warm start: row r of a new batch copies its parent's row
+// src[r] (alpha over the layer blocks alpha_dev[l] of width dims[l], beta
+// slots below np, the rest 0, gamma); rows whose src.alpha is null keep the
+// defaults.
+struct WarmSrc {
+  const float* alpha;   // [na] parent's row, layers concatenated
+  const float* beta;    // parent's beta row (np valid slots)
+  const float* gamma;   // [N]
+  int np;
+  int pad_;
+};
+void bab_warm_start(cudaStream_t st, int64_t R, int n_layers, const int* dims_dev, float* const* alpha_dev, int64_t na,
+                    float* beta, int M, float* gamma, int N, const WarmSrc* src);
+
 // tcgen05 GEMMs (k_tc.cu); false = shape or driver not supported, use SIMT
 bool tc_available(int K, bool bf16);
 bool gemm_tc_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C);

@@ -413,6 +413,40 @@ void skip_add_cert(cudaStream_t st, int64_t R, int d, int ld, int off, const dou
   prof_end(st, tk);
 }
 
+// ---------------------------------------------------------------- branch and bound warm start
+namespace {
+__global__ void __launch_bounds__(128) k_bab_warm(int64_t R, int n_layers, const int* __restrict__ dims,
+                                                  float* const* __restrict__ alpha, float* __restrict__ beta, int M,
+                                                  float* __restrict__ gamma, int N, const WarmSrc* __restrict__ src) {
+  for (int64_t r = blockIdx.x; r < R; r += gridDim.x) {
+    const WarmSrc w = src[r];
+    if (!w.alpha) continue;
+    int64_t off = 0;
+    for (int l = 0; l < n_layers; ++l) {
+      const int d = dims[l];
+      float* dst = alpha[l] + r * d;
+      for (int j = threadIdx.x; j < d; j += blockDim.x) dst[j] = w.alpha[off + j];
+      off += d;
+    }
+    for (int m = threadIdx.x; m < M; m += blockDim.x) beta[r * M + m] = m < w.np ? w.beta[m] : 0.f;
+    for (int e = threadIdx.x; e < N; e += blockDim.x) gamma[r * N + e] = w.gamma[e];
+  }
+}
+}  // namespace
+
+void bab_warm_start(cudaStream_t st, int64_t R, int n_layers, const int* dims_dev, float* const* alpha_dev, int64_t na,
+                    float* beta, int M, float* gamma, int N, const WarmSrc* src) {
+  if (R <= 0) return;
+  if (!(reg_check(dims_dev, n_layers * 4.0, "warm dims") & reg_check(alpha_dev, n_layers * 8.0, "warm alpha ptrs") &
+        reg_check(beta, (double)R * M * 4.0, "warm beta") & reg_check(gamma, (double)R * N * 4.0, "warm gamma") &
+        reg_check(src, (double)R * sizeof(WarmSrc), "warm sources")))
+    return;
+  int tk = prof_begin(st, "bab_warm_start", 0.0, (double)R * (na + M + N) * 8.0);
+  k_bab_warm<<<(unsigned)std::min<int64_t>(R, 152 * 16), 128, 0, st>>>(R, n_layers, dims_dev, alpha_dev, beta, M,
+                                                                        gamma, N, src);
+  prof_end(st, tk);
+}
+
 template void skip_add<double, double>(cudaStream_t, int64_t, int, int, int, const double*, int, double*);
 template void skip_add<float, float>(cudaStream_t, int64_t, int, int, int, const float*, int, float*);
 template void skip_add<__nv_bfloat16, float>(cudaStream_t, int64_t, int, int, int, const __nv_bfloat16*, int, float*);
