@@ -519,21 +519,27 @@ def optimize(P: Problem, D: Duals, iters: int, lr_alpha: float, lr_beta: float, 
             D.gamma += lrs[2] * G.gamma
         else:
             tt = it + 1
-            c1, c2 = 1.0 - adam_b1 ** tt, 1.0 - adam_b2 ** tt
-
-            def step(x, gx, mx, vx, lr):
-                mx *= adam_b1
-                mx += (1 - adam_b1) * gx
-                vx *= adam_b2
-                vx += (1 - adam_b2) * gx * gx
-                x += lr * (mx / c1) / (np.sqrt(vx / c2) + adam_eps)
             for a, ga, ma, va in zip(D.alpha + (D.theta or []), G.alpha + (G.theta or []),
                                      m.alpha + (m.theta or []), v.alpha + (v.theta or [])):
-                step(a, ga, ma, va, lrs[0])
-            step(D.beta, G.beta, m.beta, v.beta, lrs[1])
-            step(D.gamma, G.gamma, m.gamma, v.gamma, lrs[2])
+                adam_step(a, ga, ma, va, lrs[0], tt, adam_b1, adam_b2, adam_eps)
+            adam_step(D.beta, G.beta, m.beta, v.beta, lrs[1], tt, adam_b1, adam_b2, adam_eps)
+            adam_step(D.gamma, G.gamma, m.gamma, v.gamma, lrs[2], tt, adam_b1, adam_b2, adam_eps)
         project(P, D)
     return evaluate(P, D), D
+
+
+def adam_step(x, gx, mx, vx, lr, t, b1, b2, eps):
+    """One Adam ascent step in place (Kingma & Ba 2015, Algorithm 1), step number t >= 1.
+
+    m <- b1 m + (1-b1) g; v <- b2 v + (1-b2) g^2; x <- x + lr m-hat / (sqrt(v-hat) + eps)
+    with the bias corrections m-hat = m / (1 - b1^t), v-hat = v / (1 - b2^t).
+    """
+    mx *= b1
+    mx += (1 - b1) * gx
+    vx *= b2
+    vx += (1 - b2) * gx * gx
+    c1, c2 = 1.0 - b1 ** t, 1.0 - b2 ** t
+    x += lr * (mx / c1) / (np.sqrt(vx / c2) + eps)
 
 
 # ----------------------------------------------------------------------------
