@@ -362,40 +362,55 @@ def make_cuts(rng, net: Network, inter_lo, inter_hi, x_lo, x_hi, n_cuts: int,
 # the five workloads
 # ----------------------------------------------------------------------------
 
-def _finish(name, rng, net, x0, eps, n_spec, n_sub, split_rng, cut_args) -> Instance:
+def _finish(name, rng, net, x0, eps, n_spec, n_sub, split_rng, cut_args, root_bounds=None) -> Instance:
+    """The instance around a network: box, spec rows, root intermediate bounds,
+    subdomains (splits of root-unstable neurons) and cuts.
+
+    root_bounds: None for interval bounds, else a callable (net, x_lo, x_hi) ->
+    (lo, hi) supplied by the caller (e.g. CROWN bounds computed by the library
+    or by the oracle); the random stream is the same either way, so the same
+    seed gives the same network, box and spec whatever bounds are used.
+    """
     x_lo, x_hi = x0 - eps, x0 + eps
     C = spec_rows(net, x0, n_spec)
-    lo, hi = interval_bounds(net, x_lo, x_hi)
+    if root_bounds is None:
+        lo, hi = interval_bounds(net, x_lo, x_hi)
+    else:
+        lo, hi = root_bounds(net, x_lo, x_hi)
+        lo = [np.asarray(v, np.float64) for v in lo]
+        hi = [np.asarray(v, np.float64) for v in hi]
     sub = make_subdomains(rng, lo, hi, n_sub, *split_rng)
     cuts = make_cuts(rng, net, lo, hi, x_lo, x_hi, **cut_args)
     return Instance(name, net, x_lo, x_hi, C, lo, hi, sub, cuts)
 
 
-def mlp_small(seed: int = SEED_BASE + 1, n_sub: int = 4, n_cuts: int = 8) -> Instance:
+def mlp_small(seed: int = SEED_BASE + 1, n_sub: int = 4, n_cuts: int = 8, root_bounds=None) -> Instance:
     """MLP 8-16-16-3, eps 0.1, 2 spec rows, 0-2 splits, 8 hidden-layer cuts of 2-4 vars."""
     rng = np.random.default_rng(seed)
     net = make_mlp(rng, [8, 16, 16, 3])
     x0 = rng.random(8)
     return _finish("mlp_8_16_16_3", rng, net, x0, 0.1, 2, n_sub, (0, 2),
-                   dict(n_cuts=n_cuts, min_vars=2, max_vars=4, hidden_only=True))
+                   dict(n_cuts=n_cuts, min_vars=2, max_vars=4, hidden_only=True), root_bounds)
 
 
-def mlp_256x6(seed: int = SEED_BASE + 2, n_sub: int = 1024, n_cuts: int = 200) -> Instance:
+def mlp_256x6(seed: int = SEED_BASE + 2, n_sub: int = 1024, n_cuts: int = 200, root_bounds=None) -> Instance:
     """MLP 784-256x6-10, eps 0.015, 9 spec rows, 1-8 splits, 200 cuts of 2-8 vars."""
     rng = np.random.default_rng(seed)
     net = make_mlp(rng, [784] + [256] * 6 + [10])
     x0 = rng.random(784)
     return _finish("mlp_784_256x6_10", rng, net, x0, 0.015, 9, n_sub, (1, 8),
-                   dict(n_cuts=n_cuts, min_vars=2, max_vars=8, span_layers=True, need_z=True, p_input=0.99))
+                   dict(n_cuts=n_cuts, min_vars=2, max_vars=8, span_layers=True, need_z=True, p_input=0.99),
+                   root_bounds)
 
 
-def cnn_cifar(seed: int = SEED_BASE + 3, n_sub: int = 4096, n_cuts: int = 1000) -> Instance:
+def cnn_cifar(seed: int = SEED_BASE + 3, n_sub: int = 4096, n_cuts: int = 1000, root_bounds=None) -> Instance:
     """CNN 3x32x32 -> conv32 s2 -> conv64 s2 -> FC512 -> FC10, eps 2/255, 9 rows."""
     rng = np.random.default_rng(seed)
     net = make_cnn(rng)
     x0 = rng.random(3 * 32 * 32)
     return _finish("cnn_3x32x32_c32_c64_fc512_fc10", rng, net, x0, 2.0 / 255.0, 9, n_sub, (1, 12),
-                   dict(n_cuts=n_cuts, min_vars=2, max_vars=16, span_layers=True, need_z=True, p_input=0.99))
+                   dict(n_cuts=n_cuts, min_vars=2, max_vars=16, span_layers=True, need_z=True, p_input=0.99),
+                   root_bounds)
 
 
 def mlp_residual(seed: int = SEED_BASE + 6, width: int = 16, d0: int = 8, blocks: int = 2, d_out: int = 3,
@@ -449,7 +464,7 @@ def make_resnet(rng, hw: int = 32, stem: int = 8, blocks=((16, 2), (16, 1)), fc:
 
 def cnn_resnet(seed: int = SEED_BASE + 7, hw: int = 32, stem: int = 8, blocks=((16, 2), (16, 1)), fc: int = 100,
                eps: float = 2.0 / 255.0, n_spec: int = 9, n_sub: int = 2048, n_cuts: int = 500,
-               max_splits: int = 12) -> Instance:
+               max_splits: int = 12, root_bounds=None) -> Instance:
     """Residual CNN (make_resnet; resnet2b shape by default), eps 2/255, 9 spec rows, 1-12 splits, cuts of
     2-16 variables."""
     rng = np.random.default_rng(seed)
@@ -458,7 +473,7 @@ def cnn_resnet(seed: int = SEED_BASE + 7, hw: int = 32, stem: int = 8, blocks=((
     tag = "_".join(f"b{c}s{st}" for c, st in blocks)
     return _finish(f"resnet_3x{hw}x{hw}_c{stem}_{tag}_fc{fc}_fc10", rng, net, x0, eps, n_spec, n_sub,
                    (1, max_splits), dict(n_cuts=n_cuts, min_vars=2, max_vars=16, span_layers=True, need_z=True,
-                                         p_input=0.99))
+                                         p_input=0.99), root_bounds)
 
 
 def mlp_1024x4_queries(seed: int = SEED_BASE + 4, sizes=(64, 700, 2048), cut_counts=(0, 500, 3000)):
