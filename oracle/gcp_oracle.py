@@ -542,6 +542,53 @@ def adam_step(x, gx, mx, vx, lr, t, b1, b2, eps):
     x += lr * (mx / c1) / (np.sqrt(vx / c2) + eps)
 
 
+def crown_root_bounds(net, x_lo, x_hi, block: int = 512):
+    """Root intermediate bounds l, u of every hidden layer (Sec. 2, Eq. 1: the
+    method takes them from a bound propagation such as CROWN or IBP).
+
+    Hidden layer 1: the interval image of the box under W^(1) x + b^(1).
+    Hidden layer i > 1: the network truncated after layer i's linear map, with
+    spec rows +e_j and -e_j over its neurons, bounded by this module's
+    Theorem 3.1 at the default duals (no cuts, no splits; R10's adaptive
+    slope) over the bounds already found for the layers below:
+    l_j = g(+e_j), u_j = -g(-e_j). That is CROWN. Plain feed-forward networks
+    (no skip connections).
+    """
+    layers = net.layers
+    if any(int(getattr(ly, "skip", 0)) for ly in layers):
+        raise ValueError("crown_root_bounds: skip connections are not handled")
+    L = len(layers)
+    dims = [layers[0].d_in] + [ly.d_out for ly in layers]
+    mats = [np.asarray(ly.W, np.float64) if ly.kind == DENSE else
+            conv_matrix(np.asarray(ly.W, np.float64), ly.in_shape, ly.out_shape, ly.stride, ly.pad) for ly in layers]
+    bias = [np.asarray(ly.b, np.float64) for ly in layers]
+    x_lo = np.asarray(x_lo, np.float64)
+    x_hi = np.asarray(x_hi, np.float64)
+    c0, r0 = (x_hi + x_lo) / 2, (x_hi - x_lo) / 2
+    z = np.asarray(mats[0] @ c0).ravel() + bias[0]
+    rad = np.asarray(abs(mats[0]) @ r0).ravel()
+    lo, hi = [z - rad], [z + rad]
+    for i in range(2, L):
+        li, ui = np.empty(dims[i]), np.empty(dims[i])
+        for a in range(0, dims[i], block):
+            idx = np.arange(a, min(dims[i], a + block))
+            n = len(idx)
+            rows = mats[i - 1][idx]
+            rows = rows.toarray() if sp.issparse(rows) else rows
+            dt = dims[:i] + [n]
+            none = [sp.csr_matrix((0, d)) for d in dt[:-1]]
+            P = Problem(i, dt, mats[:i - 1] + [rows], bias[:i - 1] + [bias[i - 1][idx]], x_lo, x_hi,
+                        np.concatenate([np.eye(n), -np.eye(n)]), lo, hi,
+                        [l[None, :] for l in lo], [h[None, :] for h in hi],
+                        np.zeros(2, np.int64), np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0, np.int64),
+                        0, none, list(none), list(none), np.zeros(0), [0] * i, [None] * i)
+            g = evaluate(P, default_duals(P))
+            li[idx], ui[idx] = g[:n], -g[n:]
+        lo.append(li)
+        hi.append(ui)
+    return lo, hi
+
+
 # ----------------------------------------------------------------------------
 # LP / MIP of the same relaxation (Eq. 2-10, Eq. 16), via SciPy HiGHS
 # ----------------------------------------------------------------------------

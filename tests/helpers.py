@@ -56,46 +56,6 @@ def rows_of(inst, sub_idx):
     return np.concatenate([np.arange(s * K, (s + 1) * K) for s in sub_idx])
 
 
-def _layer_rows(ly, idx):
-    """Rows idx of a layer's linear map as dense [len(idx), d_in] (convolutions materialised)."""
-    if ly.kind == synth.DENSE:
-        return ly.W[idx]
-    return O.conv_matrix(ly.W, ly.in_shape, ly.out_shape, ly.stride, ly.pad)[idx].toarray()
-
-
-def oracle_crown_bounds(net, x_lo, x_hi, block=512):
-    """Root intermediate bounds l, u (Sec. 2) computed by the oracle alone.
-
-    Hidden layer 1: the interval image of the box under W^(1) x + b^(1).
-    Hidden layer i > 1: the network truncated after layer i's linear map,
-    with spec rows +e_j and -e_j, bounded by the oracle's Theorem 3.1 at the
-    default duals (no cuts, no splits) over the bounds already found for the
-    layers below: l_j = g(+e_j), u_j = -g(-e_j) -- CROWN with the adaptive
-    lower slope. Plain feed-forward networks only (no skip connections).
-    """
-    if any(getattr(ly, "skip", 0) for ly in net.layers):
-        raise ValueError("oracle_crown_bounds: skip connections are not handled here")
-    ly = net.layers[0]
-    W = _layer_rows(ly, np.arange(ly.d_out))
-    c0, r0 = (x_hi + x_lo) / 2, (x_hi - x_lo) / 2
-    z = W @ c0 + ly.b
-    rad = np.abs(W) @ r0
-    lo, hi = [z - rad], [z + rad]
-    empty = synth.Subdomains(np.zeros(2, np.int32), np.zeros(0, np.int16), np.zeros(0, np.int32),
-                             np.zeros(0, np.int8))
-    for i in range(2, net.L):
-        ly = net.layers[i - 1]
-        d = ly.d_out
-        li, hi_ = np.empty(d), np.empty(d)
-        for a in range(0, d, block):
-            idx = np.arange(a, min(d, a + block))
-            last = synth.Layer(synth.DENSE, _layer_rows(ly, idx), ly.b[idx], ly.in_shape, (len(idx),))
-            tr = synth.Instance("prefix", synth.Network(net.layers[:i - 1] + [last]), x_lo, x_hi,
-                                np.concatenate([np.eye(len(idx)), -np.eye(len(idx))]), lo, hi, empty,
-                                synth.Cuts.empty())
-            P = O.build_problem(tr)
-            g = O.evaluate(P, O.default_duals(P))
-            li[idx], hi_[idx] = g[:len(idx)], -g[len(idx):]
-        lo.append(li)
-        hi.append(hi_)
-    return lo, hi
+def oracle_crown_bounds(net, x_lo, x_hi):
+    """Root intermediate bounds by CROWN, computed by the oracle alone (Sec. 2)."""
+    return O.crown_root_bounds(net, x_lo, x_hi)

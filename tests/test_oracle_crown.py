@@ -1,9 +1,9 @@
-"""Pins of the test-side CROWN root bounds (tests/helpers.py:oracle_crown_bounds).
+"""Pins of the oracle's CROWN root bounds (crown_root_bounds).
 
 The method takes sound pre-activation bounds l, u as input (Sec. 2, Eq. 1);
-the measured workloads take them from CROWN, which the tests compute by
-composing the oracle's Theorem 3.1 over truncated networks. Pinned here from
-outside that composition:
+the measured workloads take them from CROWN, which the oracle computes by
+composing its Theorem 3.1 over truncated networks. Pinned here from outside
+that composition:
   * hidden layer 1 equals the exact interval image of the box (corners);
   * every bound is sound: sampled inputs' pre-activations lie inside;
   * every bound is at most as tight as the LP of the same truncated network
@@ -19,7 +19,8 @@ import pytest
 
 from oracle import gcp_oracle as O
 from paper_2208_05740_gb300 import synth
-from tests.helpers import oracle_crown_bounds
+
+crown_root_bounds = O.crown_root_bounds
 
 
 def _net(seed, dims):
@@ -31,7 +32,7 @@ def _net(seed, dims):
 
 def test_layer_one_is_the_exact_interval_image():
     net, lo, hi = _net(1, (4, 6, 5, 2))
-    L, H = oracle_crown_bounds(net, lo, hi)
+    L, H = crown_root_bounds(net, lo, hi)
     W, b = net.layers[0].W, net.layers[0].b
     corners = np.array(list(itertools.product(*zip(lo, hi))))
     z = corners @ W.T + b
@@ -42,7 +43,7 @@ def test_layer_one_is_the_exact_interval_image():
 @pytest.mark.parametrize("seed", [2, 3, 4])
 def test_bounds_are_sound_on_sampled_inputs(seed):
     net, lo, hi = _net(seed, (8, 16, 16, 16, 3))
-    L, H = oracle_crown_bounds(net, lo, hi)
+    L, H = crown_root_bounds(net, lo, hi)
     X = synth.sample_box(np.random.default_rng(seed), lo, hi, 20000)
     for i, z in enumerate(synth.forward_all(net, X)[:-1]):
         assert np.all(z >= L[i] - 1e-12) and np.all(z <= H[i] + 1e-12), f"layer {i + 1}"
@@ -51,7 +52,7 @@ def test_bounds_are_sound_on_sampled_inputs(seed):
 @pytest.mark.parametrize("seed", [5, 6])
 def test_bounds_do_not_beat_the_lp_of_the_truncated_network(seed):
     net, lo, hi = _net(seed, (6, 10, 10, 3))
-    L, H = oracle_crown_bounds(net, lo, hi)
+    L, H = crown_root_bounds(net, lo, hi)
     empty = synth.Subdomains(np.zeros(2, np.int32), np.zeros(0, np.int16), np.zeros(0, np.int32),
                              np.zeros(0, np.int8))
     ly = net.layers[1]
@@ -78,7 +79,7 @@ def test_stable_first_layer_gives_exact_box_extrema():
                          synth.Layer(synth.DENSE, W2, b2, (d1,), (d2,)),
                          synth.Layer(synth.DENSE, W3, np.zeros(2), (d2,), (2,))])
     lo, hi = -0.5 * np.ones(d0), 0.5 * np.ones(d0)
-    L, H = oracle_crown_bounds(net, lo, hi)
+    L, H = crown_root_bounds(net, lo, hi)
     assert np.all(L[0] > 0)
     corners = np.array(list(itertools.product(*zip(lo, hi))))
     z2 = (corners @ W1.T + b1) @ W2.T + b2            # linear on the box: extrema at corners
@@ -88,7 +89,7 @@ def test_stable_first_layer_gives_exact_box_extrema():
 
 def test_inside_interval_bounds():
     net, lo, hi = _net(8, (8, 16, 16, 16, 3))
-    L, H = oracle_crown_bounds(net, lo, hi)
+    L, H = crown_root_bounds(net, lo, hi)
     IL, IH = synth.interval_bounds(net, lo, hi)
     for a, b, c, d in zip(L, H, IL, IH):
         assert np.all(a >= c - 1e-12) and np.all(b <= d + 1e-12)
