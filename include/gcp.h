@@ -338,9 +338,9 @@ GCP_API gcp_status gcp_grad_device(gcp_ctx* ctx, void* duals, int32_t prec, cons
 /* The FP32 bound g(alpha) of dense ReLU networks without cuts or splits,
  * enqueued on `stream` with no device allocation at all. The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
- * device memory -- work recorded into a CUDA graph under stream capture,
- * processes that reserve the whole GPU for their own pool up front, loops
- * that cannot afford cudaMalloc's implicit synchronisation.
+ * device memory -- processes that reserve the whole GPU for their own memory
+ * pool up front, so that any further cudaMalloc fails, and loops that cannot
+ * afford the device-wide synchronisation cudaMalloc and cudaFree imply.
  *
  * Every argument is the caller's and stays the caller's: dims (host,
  * d_0..d_L); WT, bias, lo, hi, alpha (host arrays of L-1 device pointers,
@@ -419,11 +419,17 @@ typedef struct {
   uint64_t seed;
   gcp_subdomains sub;
   gcp_opt_params p;
+  /* 1: keep the last round's subdomains and duals on the host when the
+   * request finishes, for gcp_serve_final (costs one device-to-host copy of
+   * rows x (hidden neurons + splits + cuts) floats); 0: drop them. */
+  int32_t keep_final;
 } gcp_request;
 
 /* Result of a finished request. certified (caller-allocated, >= rows of the
  * last round) receives the certified bounds of the last round; min_certified
- * the minimum over them; latency_ms = completion - submission. */
+ * the minimum over them; latency_ms = completion - submission;
+ * max_err_vs_fp64 = max over rows |chain bound - certified bound|, and
+ * max_rel_err_vs_fp64 the same divided by max(1, |certified bound|). */
 typedef struct {
   gcp_status status;
   int32_t rows;
@@ -431,7 +437,27 @@ typedef struct {
   double min_certified;
   double latency_ms;
   double max_err_vs_fp64;
+  double max_rel_err_vs_fp64;
 } gcp_result;
+
+/* The final state of a request submitted with keep_final = 1: the subdomains
+ * of its last round (split CSR as in gcp_subdomains; App. B's children after
+ * rounds - 1 branchings) and the duals at which its certified bounds were
+ * computed (layouts of gcp_duals_export: alpha [rows, sum of hidden widths],
+ * beta [rows, max_splits] with slot m = the m-th split of the row's
+ * subdomain, gamma [rows, n_cuts] over the request's cut set). The ReLU duals
+ * theta of an opt_pi request are not included. */
+typedef struct {
+  int32_t n_sub, rows, n_alpha, max_splits, n_cuts;
+  int64_t n_split_entries;
+  int32_t* split_ptr;    /* [n_sub + 1] */
+  int16_t* split_layer;  /* [n_split_entries] */
+  int32_t* split_index;  /* [n_split_entries] */
+  int8_t* split_sign;    /* [n_split_entries] */
+  float* alpha;          /* [rows, n_alpha] */
+  float* beta;           /* [rows, max_splits] */
+  float* gamma;          /* [rows, n_cuts] */
+} gcp_final;
 
 /* Start the serving loop: a host scheduler thread admits submitted requests
  * while at most max_inflight run and their estimated device memory fits the
@@ -448,8 +474,17 @@ GCP_API gcp_status gcp_serve_submit(gcp_ctx* ctx, const gcp_request* req, uint64
 GCP_API gcp_status gcp_serve_poll(gcp_ctx* ctx, uint64_t ticket, gcp_result* res);
 /* Like poll but waits up to timeout_ms (GCP_ETIMEOUT if still pending). */
 GCP_API gcp_status gcp_serve_wait(gcp_ctx* ctx, uint64_t ticket, int32_t timeout_ms, gcp_result* res);
+/* The final state of a finished keep_final request whose result has been
+ * taken by gcp_serve_poll / gcp_serve_wait. The sizes in *out are always
+ * filled; when every pointer of *out is non-NULL the arrays are copied into
+ * those caller-allocated buffers and the state is forgotten (a second call
+ * gives GCP_ENOTFOUND). With any pointer NULL only the sizes are written (a
+ * size query). GCP_ENOTFOUND: unknown ticket, no keep_final, or not yet
+ * taken; GCP_EINVAL: the request failed. */
+GCP_API gcp_status gcp_serve_final(gcp_ctx* ctx, uint64_t ticket, gcp_final* out);
 /* Stop accepting submissions, finish every submitted request, join the
- * scheduler thread and free the loop's streams. Unpolled results are dropped. */
+ * scheduler thread and free the loop's streams. Unpolled results and kept
+ * final states are dropped. */
 GCP_API gcp_status gcp_serve_stop(gcp_ctx* ctx);
 
 #ifdef __cplusplus

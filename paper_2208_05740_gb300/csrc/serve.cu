@@ -54,7 +54,10 @@ struct Request {
   size_t resident_bytes = 0, estimate = 0;
   // results of the last round
   std::vector<double> certified;
-  double min_cert = 0, max_err = 0;
+  double min_cert = 0, max_err = 0, max_rel_err = 0;
+  // keep_final: the last round's duals, copied to the host when it finishes
+  bool keep_final = false;
+  std::vector<float> fin_alpha, fin_beta, fin_gamma;
   gcp_status status = GCP_PENDING;
   Clock::time_point t_submit, t_done;
 };
@@ -70,6 +73,7 @@ struct Serve {
   std::deque<std::unique_ptr<Request>> pending;
   std::vector<std::unique_ptr<Request>> active;
   std::map<uint64_t, std::unique_ptr<Request>> finished;
+  std::map<uint64_t, std::unique_ptr<Request>> kept;   // taken keep_final results, for gcp_serve_final
   std::map<int, cudaStream_t> streams;   // one per network
   size_t reserved = 0;                   // device bytes promised to admitted requests
 };
@@ -91,13 +95,16 @@ size_t estimate_bytes(const Net& net, int64_t R, int N, int64_t nnz, int Mcap) {
   // skips from further back than the layer's input park nu, S^T nu, a (fp32)
   // and the certification's term and its magnitude bound, of their source's
   // width; projections add one product buffer of each kind
+  // (the mixed-precision chain adds nu's three-term bf16 operand and its
+  // float form, 10 bytes per neuron of the widest layer)
   int64_t parked = 0;
   bool proj = false;
   for (int m = 0; m < net.L; ++m)
     if (net.consumer[m] > m + 1 && net.consumer[m] < net.L) parked += net.dims[m];
   for (int i = 0; i < net.L; ++i) proj |= net.sc_map[i] != 0;
   const double per_row = 4.0 * (5 * sum_d + 5 * dmax + nnz + 3 * N + 3 * Mcap) + 8.0 * (2 * dmax + P) +
-                         4.0 * (dmax + P) + 6.0 * smax * dmax + 24.0 * parked + (proj ? 28.0 * dmax : 0.0);
+                         4.0 * (dmax + P) + 6.0 * smax * dmax + 24.0 * parked + (proj ? 28.0 * dmax : 0.0) +
+                         10.0 * dmax;
   const double resident = 4.0 * (sum_d + Mcap + N);
   return (size_t)(R * (per_row + resident)) + (size_t(16) << 20);
 }
@@ -257,7 +264,12 @@ void run_group(Serve& sv, int net_id, cudaStream_t st, std::vector<Request*> gro
     q->certified.assign(h_cert.begin() + r0, h_cert.begin() + r0 + q->R);
     q->min_cert = q->R ? *std::min_element(q->certified.begin(), q->certified.end()) : 0.0;
     q->max_err = 0;
-    for (int64_t r = 0; r < q->R; ++r) q->max_err = std::max(q->max_err, std::fabs(h_bound[r0 + r] - h_cert[r0 + r]));
+    q->max_rel_err = 0;
+    for (int64_t r = 0; r < q->R; ++r) {
+      const double e = std::fabs(h_bound[r0 + r] - h_cert[r0 + r]);
+      q->max_err = std::max(q->max_err, e);
+      q->max_rel_err = std::max(q->max_rel_err, e / std::max(1.0, std::fabs(h_cert[r0 + r])));
+    }
     r0 += q->R;
     q->done += 1;
     if (q->done < q->rounds) branch(net, *q);
@@ -325,6 +337,20 @@ void scheduler(Serve* sv) {
       for (auto it = sv->active.begin(); it != sv->active.end();) {
         Request& q = **it;
         if (q.done >= q.rounds) {
+          if (q.keep_final && q.status == GCP_OK) {
+            // the round's stream was synchronised: the resident duals are final
+            q.fin_alpha.resize((size_t)q.R * q.na);
+            q.fin_beta.resize((size_t)q.R * q.Mcap);
+            q.fin_gamma.resize((size_t)q.R * q.N);
+            cudaError_t e = cudaSuccess;
+            if (!q.fin_alpha.empty())
+              e = cudaMemcpy(q.fin_alpha.data(), q.alpha, q.fin_alpha.size() * 4, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && !q.fin_beta.empty())
+              e = cudaMemcpy(q.fin_beta.data(), q.beta, q.fin_beta.size() * 4, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && !q.fin_gamma.empty())
+              e = cudaMemcpy(q.fin_gamma.data(), q.gamma, q.fin_gamma.size() * 4, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) q.status = GCP_ECUDA;
+          }
           free_resident(c, q);
           sv->reserved -= std::min(sv->reserved, q.estimate);
           q.t_done = Clock::now();
@@ -339,12 +365,20 @@ void scheduler(Serve* sv) {
   }
 }
 
+// A taken result is forgotten, unless its request keeps its final state for
+// gcp_serve_final.
+void take_finished(Serve& sv, std::map<uint64_t, std::unique_ptr<Request>>::iterator it) {
+  if (it->second->keep_final) sv.kept[it->first] = std::move(it->second);
+  sv.finished.erase(it);
+}
+
 gcp_status fill_result(Request& q, gcp_result* res) {
   res->status = q.status;
   res->rows = (int32_t)q.certified.size();
   if (res->certified) std::copy(q.certified.begin(), q.certified.end(), res->certified);
   res->min_certified = q.min_cert;
   res->max_err_vs_fp64 = q.max_err;
+  res->max_rel_err_vs_fp64 = q.max_rel_err;
   res->latency_ms = std::chrono::duration<double, std::milli>(q.t_done - q.t_submit).count();
   return GCP_OK;
 }
@@ -425,6 +459,7 @@ gcp_status gcp_serve_submit(gcp_ctx* h, const gcp_request* req, uint64_t* ticket
     q->rounds = req->rounds;
     q->p = req->p;
     q->rng.seed(req->seed);
+    q->keep_final = req->keep_final != 0;
     q->S = sd.n_sub;
     q->K = net.K;
     q->R = (int64_t)q->S * q->K;
@@ -461,7 +496,7 @@ gcp_status gcp_serve_poll(gcp_ctx* h, uint64_t ticket, gcp_result* res) {
     return GCP_ENOTFOUND;
   }
   gcp::fill_result(*it->second, res);
-  sv->finished.erase(it);
+  gcp::take_finished(*sv, it);
   return GCP_OK;
 }
 
@@ -480,7 +515,36 @@ gcp_status gcp_serve_wait(gcp_ctx* h, uint64_t ticket, int32_t timeout_ms, gcp_r
   }
   auto it = sv->finished.find(ticket);
   gcp::fill_result(*it->second, res);
-  sv->finished.erase(it);
+  gcp::take_finished(*sv, it);
+  return GCP_OK;
+}
+
+gcp_status gcp_serve_final(gcp_ctx* h, uint64_t ticket, gcp_final* out) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  if (!c || !out || !c->serve) return GCP_EINVAL;
+  gcp::Serve* sv = c->serve;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->kept.find(ticket);
+  if (it == sv->kept.end()) return GCP_ENOTFOUND;
+  gcp::Request& q = *it->second;
+  if (q.status != GCP_OK) return GCP_EINVAL;
+  out->n_sub = q.S;
+  out->rows = (int32_t)q.R;
+  out->n_alpha = (int32_t)q.na;
+  out->max_splits = q.Mcap;
+  out->n_cuts = q.N;
+  out->n_split_entries = (int64_t)q.layer.size();
+  if (!out->split_ptr || !out->split_layer || !out->split_index || !out->split_sign || !out->alpha ||
+      !out->beta || !out->gamma)
+    return GCP_OK;
+  std::copy(q.ptr.begin(), q.ptr.end(), out->split_ptr);
+  std::copy(q.layer.begin(), q.layer.end(), out->split_layer);
+  std::copy(q.index.begin(), q.index.end(), out->split_index);
+  std::copy(q.sign.begin(), q.sign.end(), out->split_sign);
+  std::copy(q.fin_alpha.begin(), q.fin_alpha.end(), out->alpha);
+  std::copy(q.fin_beta.begin(), q.fin_beta.end(), out->beta);
+  std::copy(q.fin_gamma.begin(), q.fin_gamma.end(), out->gamma);
+  sv->kept.erase(it);
   return GCP_OK;
 }
 

@@ -29,7 +29,7 @@ EXPORTED = ["gcp_create", "gcp_destroy", "gcp_last_error", "gcp_set_stream", "gc
             "gcp_duals_free", "gcp_duals_theta", "gcp_bound_batch", "gcp_grad_batch", "gcp_optimize_batch", "gcp_bound_device",
             "gcp_grad_device", "gcp_bound_dense_noalloc", "gcp_selftest_gemm", "gcp_selftest_gemm_f64", "gcp_profile_start", "gcp_profile_stop", "gcp_profile_query", "gcp_profile_report",
             "gcp_serve_start", "gcp_serve_submit", "gcp_serve_poll", "gcp_serve_wait",
-            "gcp_serve_stop"]
+            "gcp_serve_final", "gcp_serve_stop"]
 
 
 class GCPError(RuntimeError):
@@ -73,12 +73,21 @@ class BabResult(C.Structure):
 
 class Request(C.Structure):
     _fields_ = [("net_id", C.c_int32), ("cutset_id", C.c_int32), ("rounds", C.c_int32), ("seed", C.c_uint64),
-                ("sub", Subdomains), ("p", OptParams)]
+                ("sub", Subdomains), ("p", OptParams), ("keep_final", C.c_int32)]
 
 
 class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("rows", C.c_int32), ("certified", C.POINTER(C.c_double)),
-                ("min_certified", C.c_double), ("latency_ms", C.c_double), ("max_err_vs_fp64", C.c_double)]
+                ("min_certified", C.c_double), ("latency_ms", C.c_double), ("max_err_vs_fp64", C.c_double),
+                ("max_rel_err_vs_fp64", C.c_double)]
+
+
+class Final(C.Structure):
+    _fields_ = [("n_sub", C.c_int32), ("rows", C.c_int32), ("n_alpha", C.c_int32), ("max_splits", C.c_int32),
+                ("n_cuts", C.c_int32), ("n_split_entries", C.c_int64), ("split_ptr", C.POINTER(C.c_int32)),
+                ("split_layer", C.POINTER(C.c_int16)), ("split_index", C.POINTER(C.c_int32)),
+                ("split_sign", C.POINTER(C.c_int8)), ("alpha", C.POINTER(C.c_float)), ("beta", C.POINTER(C.c_float)),
+                ("gamma", C.POINTER(C.c_float))]
 
 
 _lib = None
@@ -420,29 +429,53 @@ class Context:
     def serve_start(self, max_inflight: int):
         self._check(lib().gcp_serve_start(self.h, max_inflight))
 
-    def serve_submit(self, net_id, cutset_id, sub, params: OptParams, rounds: int, seed: int) -> int:
+    def serve_submit(self, net_id, cutset_id, sub, params: OptParams, rounds: int, seed: int,
+                     keep_final: bool = False) -> int:
         arrs = [_c(sub.ptr, np.int32), _c(sub.layer, np.int16), _c(sub.index, np.int32), _c(sub.sign, np.int8)]
         sd = Subdomains(sub.n, _ptr(arrs[0], C.c_int32), _ptr(arrs[1], C.c_int16), _ptr(arrs[2], C.c_int32),
                         _ptr(arrs[3], C.c_int8))
-        req = Request(net_id, cutset_id, rounds, seed, sd, params)
+        req = Request(net_id, cutset_id, rounds, seed, sd, params, 1 if keep_final else 0)
         t = C.c_uint64()
         self._check(lib().gcp_serve_submit(self.h, C.byref(req), C.byref(t)))
         return t.value
 
     def serve_wait(self, ticket: int, capacity: int, timeout_ms: int = 600000):
         buf = np.zeros(max(capacity, 1))
-        res = Result(0, 0, _ptr(buf, C.c_double), 0.0, 0.0, 0.0)
+        res = Result(0, 0, _ptr(buf, C.c_double), 0.0, 0.0, 0.0, 0.0)
         st = lib().gcp_serve_wait(self.h, ticket, timeout_ms, C.byref(res))
         self._check(st)
         return res, buf[:res.rows].copy()
 
     def serve_poll(self, ticket: int, capacity: int):
         buf = np.zeros(max(capacity, 1))
-        res = Result(0, 0, _ptr(buf, C.c_double), 0.0, 0.0, 0.0)
+        res = Result(0, 0, _ptr(buf, C.c_double), 0.0, 0.0, 0.0, 0.0)
         st = self._check(lib().gcp_serve_poll(self.h, ticket, C.byref(res)))
         if st == GCP_PENDING:
             return None, None
         return res, buf[:res.rows].copy()
+
+    def serve_final(self, ticket: int):
+        """The last round's subdomains and duals of a finished keep_final request
+        (after serve_wait / serve_poll took its result): (Subdomains, alpha, beta, gamma)."""
+        f = Final()
+        self._check(lib().gcp_serve_final(self.h, ticket, C.byref(f)))
+        ptr = np.zeros(f.n_sub + 1, np.int32)
+        lay = np.zeros(max(f.n_split_entries, 1), np.int16)
+        idx = np.zeros(max(f.n_split_entries, 1), np.int32)
+        sgn = np.zeros(max(f.n_split_entries, 1), np.int8)
+        A = np.zeros((f.rows, f.n_alpha), np.float32)
+        B = np.zeros((f.rows, f.max_splits), np.float32)
+        G = np.zeros((f.rows, f.n_cuts), np.float32)
+        f.split_ptr, f.split_layer = _ptr(ptr, C.c_int32), _ptr(lay, C.c_int16)
+        f.split_index, f.split_sign = _ptr(idx, C.c_int32), _ptr(sgn, C.c_int8)
+        f.alpha = _ptr(A if A.size else np.zeros(1, np.float32), C.c_float)
+        f.beta = _ptr(B if B.size else np.zeros(1, np.float32), C.c_float)
+        f.gamma = _ptr(G if G.size else np.zeros(1, np.float32), C.c_float)
+        self._check(lib().gcp_serve_final(self.h, ticket, C.byref(f)))
+        n = int(f.n_split_entries)
+        from . import synth
+        sub = synth.Subdomains(ptr, lay[:n].copy(), idx[:n].copy(), sgn[:n].copy())
+        return sub, A.astype(np.float64), B.astype(np.float64), G.astype(np.float64)
 
     def serve_stop(self):
         self._check(lib().gcp_serve_stop(self.h))

@@ -153,3 +153,58 @@ def test_requests_arriving_during_a_round_join_later():
     # the short request was admitted while the long one was running and
     # finished without waiting for all of its rounds
     assert r_short.latency_ms < r_long.latency_ms
+
+
+def _oracle_final(inst, sub, A, B, G):
+    """The oracle's bound of a finished request at its last round's subdomains and duals."""
+    fin = dataclasses.replace(inst, sub=sub)
+    P = O.build_problem(fin)
+    return O.evaluate(P, oracle_duals(fin, A, B[:, :P.max_splits], G))
+
+
+def test_serving_results_match_the_oracle_alone_and_in_a_three_network_mix():
+    """Every finished request's certified bounds equal the oracle's evaluation
+    (1e-9) at the request's last-round subdomains (App. B children) and duals,
+    for requests of three networks served together and for one served alone;
+    the BF16 chain's error against the certified FP64 bound stays within 1e-3."""
+    a = synth.mlp_small(n_sub=6)
+    c = synth.mlp_256x6(n_sub=10, n_cuts=40)
+    n = synth.cnn_cifar(n_sub=3, n_cuts=60)
+    rounds = 3
+    with gcp.Context(0) as ctx:
+        ids = [ctx.load_instance(x) for x in (a, c, n)]
+        ctx.serve_start(8)
+        t_alone = ctx.serve_submit(ids[1][0], ids[1][1], c.sub,
+                                   gcp.opt_params(10, gcp.GCP_ADAM, gcp.GCP_BF16, 1, 0.1, 0.02, 0.02, 0.98),
+                                   rounds, 17, keep_final=True)
+        r_alone, cert_alone = ctx.serve_wait(t_alone, c.n_rows)
+        final_alone = ctx.serve_final(t_alone)
+        tickets = [ctx.serve_submit(nid, cs, x.sub,
+                                    gcp.opt_params(10, gcp.GCP_ADAM, gcp.GCP_BF16, 1, 0.1, 0.02, 0.02, 0.98),
+                                    rounds, seed, keep_final=True)
+                   for x, (nid, cs), seed in zip((a, c, n), ids, (30, 17, 31))]
+        results = [ctx.serve_wait(t, x.n_rows) for t, x in zip(tickets, (a, c, n))]
+        finals = [ctx.serve_final(t) for t in tickets]
+        with pytest.raises(gcp.GCPError):
+            ctx.serve_final(tickets[0])             # taken once
+        ctx.serve_stop()
+    checks = [(c, r_alone, cert_alone, final_alone)] + [(x, r, cert, f) for x, (r, cert), f in
+                                                         zip((a, c, n), results, finals)]
+    for inst, res, cert, (sub, A, B, G) in checks:
+        assert res.status == 0 and res.rows == inst.n_rows
+        # the last round's subdomains are children of the submitted ones
+        for s in range(inst.sub.n):
+            p0, p1 = int(inst.sub.ptr[s]), int(inst.sub.ptr[s + 1])
+            q0, q1 = int(sub.ptr[s]), int(sub.ptr[s + 1])
+            assert p1 - p0 <= q1 - q0 <= p1 - p0 + rounds - 1
+            np.testing.assert_array_equal(sub.layer[q0:q0 + p1 - p0], inst.sub.layer[p0:p1])
+            np.testing.assert_array_equal(sub.index[q0:q0 + p1 - p0], inst.sub.index[p0:p1])
+            np.testing.assert_array_equal(sub.sign[q0:q0 + p1 - p0], inst.sub.sign[p0:p1])
+        ref = _oracle_final(inst, sub, A, B, G)
+        assert_rel(cert, ref, 1e-9, f"{inst.name}: served certified bound vs oracle")
+        assert res.max_rel_err_vs_fp64 <= 1e-3, (inst.name, res.max_rel_err_vs_fp64)
+        assert abs(res.min_certified - float(np.min(cert))) == 0.0
+    # the request served alone and the same request (same seed) in the mix
+    # took the same children; both are anchored to the oracle above
+    np.testing.assert_array_equal(final_alone[0].index, finals[1][0].index)
+    assert_rel(results[1][1], cert_alone, 1e-9, "same request alone and in the mix")
