@@ -16,6 +16,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <type_traits>
 #include <numeric>
 #include <type_traits>
 #include <string>
@@ -77,8 +78,15 @@ void trim_to(Ctx& c, uint64_t keep) {
 AllocPool::AllocPool() : prev(t_pool) { t_pool = true; }
 AllocPool::~AllocPool() { t_pool = prev; }
 
+namespace {
+thread_local bool t_over_budget = false;
+}  // namespace
+
+bool Ctx::over_budget() const { return t_over_budget; }
+
 void* Ctx::alloc(size_t bytes) {
   std::lock_guard<std::mutex> lk(alloc_mu);
+  t_over_budget = false;
   if (bytes == 0) bytes = 16;
   bytes = t_pool ? size_class(bytes) : (bytes + 255) & ~size_t(255);
   void* p = nullptr;
@@ -89,7 +97,7 @@ void* Ctx::alloc(size_t bytes) {
     cached -= bytes;
   } else {
     if (budget && used + bytes > budget) {
-      over_budget = true;
+      t_over_budget = true;
       return nullptr;
     }
     if (budget && used + cached + bytes > budget) trim_to(*this, budget - used - bytes);
@@ -150,7 +158,7 @@ template <typename T>
 T* upload(Ctx& c, const T* host, size_t n, gcp_status* st) {
   T* d = static_cast<T*>(c.alloc(n * sizeof(T)));
   if (!d) {
-    *st = c.over_budget ? c.fail(GCP_EBUDGET, "device memory budget exceeded")
+    *st = c.over_budget() ? c.fail(GCP_EBUDGET, "device memory budget exceeded")
                         : c.fail(GCP_ENOMEM, "cudaMalloc of %zu bytes failed", n * sizeof(T));
     return nullptr;
   }
@@ -189,6 +197,10 @@ static void tf32_split(const std::vector<float>& v, std::vector<float>& hi, std:
     lo[i] = v[i] - hi[i];
   }
 }
+
+// bf16(w) as a double (the high term of the three-term weights; the low term
+// is w - bf16_hi(w), rounded to bf16 in turn)
+static double bf16_hi(double w) { return (double)__bfloat162float(__float2bfloat16_rn((float)w)); }
 
 static std::vector<__nv_bfloat16> to_bf16(const double* p, size_t n) {
   std::vector<__nv_bfloat16> v(n);
@@ -234,7 +246,7 @@ void* Batch::ws(const std::string& name, size_t bytes, gcp_status* st) {
     p = ctx->alloc(bytes);
   }
   if (!p) {
-    *st = ctx->over_budget ? ctx->fail(GCP_EBUDGET, "device memory budget exceeded (%s)", name.c_str())
+    *st = ctx->over_budget() ? ctx->fail(GCP_EBUDGET, "device memory budget exceeded (%s)", name.c_str())
                            : ctx->fail(GCP_ENOMEM, "cudaMalloc of %zu bytes failed (%s)", bytes, name.c_str());
     return nullptr;
   }
@@ -408,15 +420,18 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
       UP(wt32h, float, hi.data(), nw);
       UP(wt32l, float, lo.data(), nw);
     }
-    __nv_bfloat16 *cf16 = nullptr, *ct16 = nullptr;
-    int cfk = 0, cfn = 0, ctk = 0, ctn = 0;
+    __nv_bfloat16 *cf16 = nullptr, *ct16 = nullptr, *ct16x3 = nullptr, *wt16x3 = nullptr;
+    int cfk = 0, cfn = 0, ctk = 0, ctn = 0, ct3k = 0, ct3n = 0;
     if (g.kind != GCP_DENSE) {
       // columns by the convolution plan of each direction (phases, taps,
       // source channel padded to 8), rows = output channels padded to 16
-      auto pack = [&](bool transposed, int& kp, int& np_) {
+      // gg: the plan's geometry; for split_geom(g) (the three-term operand of
+      // the mixed chain) output channel t c_out + o carries W_hi of channel o
+      // for t = 0, 1 and W_lo for t = 2
+      auto pack = [&](bool transposed, int& kp, int& np_, const LayerGeom& gg) {
         ConvPlan cp;
         std::vector<double> p;
-        if (!conv_plan(g, transposed ? 1 : 0, cp)) { kp = np_ = 0; return to_bf16(p.data(), 0); }
+        if (!conv_plan(gg, transposed ? 1 : 0, cp)) { kp = np_ = 0; return to_bf16(p.data(), 0); }
         kp = cp.Kp;
         np_ = cp.Np;
         p.assign((size_t)np_ * kp, 0.0);
@@ -427,9 +442,11 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
             for (int b = 0; b < f.nkw; ++b) {
               const int kh = f.rh + step * a, kw = f.rw + step * b;
               const size_t col0 = (size_t)f.kb0 * 64 + (size_t)(a * f.nkw + b) * cp.Csp;
-              for (int o = 0; o < g.c_out; ++o)
+              for (int o = 0; o < gg.c_out; ++o)
                 for (int ci = 0; ci < g.c_in; ++ci) {
-                  const double w = d.W[(((size_t)o * g.c_in + ci) * g.k + kh) * g.k + kw];
+                  const double wf = d.W[(((size_t)(o % g.c_out) * g.c_in + ci) * g.k + kh) * g.k + kw];
+                  const int term = o / g.c_out;
+                  const double w = term == 0 ? wf : (term == 1 ? bf16_hi(wf) : wf - bf16_hi(wf));
                   const int n = transposed ? ci : o, c = transposed ? o : ci;
                   p[(size_t)n * kp + col0 + c] = w;
                 }
@@ -437,10 +454,25 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
         }
         return to_bf16(p.data(), p.size());
       };
-      auto pf = pack(false, cfk, cfn);
+      auto pf = pack(false, cfk, cfn, g);
       if (!pf.empty()) UP(cf16, __nv_bfloat16, pf.data(), pf.size());
-      auto pt = pack(true, ctk, ctn);
+      auto pt = pack(true, ctk, ctn, g);
       if (!pt.empty()) UP(ct16, __nv_bfloat16, pt.data(), pt.size());
+      const LayerGeom g3 = split_geom(g);
+      auto p3 = pack(true, ct3k, ct3n, g3);
+      if (!p3.empty() && conv_tc_fits(g3, 1, ct3k, ct3n)) UP(ct16x3, __nv_bfloat16, p3.data(), p3.size());
+    } else if (tc_available(kTerms * g.d_out, true)) {
+      // rows of [W_hi^T | W_hi^T | W_lo^T] for the three-term operand [hi | lo | hi]
+      const size_t K3 = (size_t)kTerms * g.d_out;
+      std::vector<double> t3((size_t)g.d_in * K3);
+      for (int q = 0; q < g.d_in; ++q)
+        for (int o = 0; o < g.d_out; ++o) {
+          const double w = d.W[(size_t)o * g.d_in + q];
+          t3[(size_t)q * K3 + o] = t3[(size_t)q * K3 + g.d_out + o] = bf16_hi(w);
+          t3[(size_t)q * K3 + 2 * g.d_out + o] = w - bf16_hi(w);
+        }
+      auto t3h = to_bf16(t3.data(), t3.size());
+      UP(wt16x3, __nv_bfloat16, t3h.data(), t3h.size());
     }
     float* wabs = nullptr;
     if (g.kind != GCP_DENSE) {
@@ -471,6 +503,8 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
     net->WTsl.push_back(sl);
     net->CF16.push_back(cf16); net->CT16.push_back(ct16);
     net->cf_kp.push_back(cfk); net->cf_np.push_back(cfn); net->ct_kp.push_back(ctk); net->ct_np.push_back(ctn);
+    net->WT16x3.push_back(wt16x3); net->CT16x3.push_back(ct16x3);
+    net->ct3_kp.push_back(ct3k); net->ct3_np.push_back(ct3n);
     UP(b64, double, bias, g.d_out);
     auto bf = to_f32(bias, g.d_out);
     UP(b32, float, bf.data(), g.d_out);
@@ -821,15 +855,15 @@ gcp_status duals_create_parts(Ctx& c, int net_id, const std::vector<std::pair<co
   const size_t es = b->fp64 ? 8 : 4;
   for (int i = 1; i < net.L; ++i) {
     void* p = c.alloc((size_t)b->R * net.dims[i] * es);
-    if (!p) return c.fail(c.over_budget ? GCP_EBUDGET : GCP_ENOMEM, "alpha allocation failed");
+    if (!p) return c.fail(c.over_budget() ? GCP_EBUDGET : GCP_ENOMEM, "alpha allocation failed");
     b->owned.push_back(p);
     b->alpha.push_back(p);
   }
   b->beta = c.alloc((size_t)std::max(M, 1) * b->R * es);
-  if (!b->beta) return c.fail(c.over_budget ? GCP_EBUDGET : GCP_ENOMEM, "beta allocation failed");
+  if (!b->beta) return c.fail(c.over_budget() ? GCP_EBUDGET : GCP_ENOMEM, "beta allocation failed");
   b->owned.push_back(b->beta);
   b->gamma = c.alloc((size_t)std::max(b->N, 1) * b->R * es);
-  if (!b->gamma) return c.fail(c.over_budget ? GCP_EBUDGET : GCP_ENOMEM, "gamma allocation failed");
+  if (!b->gamma) return c.fail(c.over_budget() ? GCP_EBUDGET : GCP_ENOMEM, "gamma allocation failed");
   b->owned.push_back(b->gamma);
 #undef UPB
   st = reset_duals(c, *b, true, true, true);
@@ -1002,6 +1036,55 @@ static void lin_backward(cudaStream_t st, const Batch& b, int i, const Top* nu, 
   if (g.kind == GCP_DENSE) gemm_nt<Top, T>(st, b.R, g.d_in, g.d_out, nu, 0, WSel<Top>::WT(net, i), y);
   else conv_T<Top, T>(st, b.R, g, WSel<Top>::W(net, i), nu, y);
 }
+// The mixed-precision chain (bf16 operands, float accumulation) runs the
+// backward product through W^(i) as one tensor-core product of three bf16
+// terms concatenated along K (kTerms): [nu_hi | nu_lo | nu_hi] against
+// [W_hi | W_hi | W_lo], i.e. nu_hi W_hi + nu_lo W_hi + nu_hi W_lo, whose
+// operands keep about 16 significant bits each. A single bf16 rounding of nu
+// or of W, passed down the chain, moves the bound by up to a few 1e-3 of
+// max(|g|, 1) on networks whose bounds sit near zero. Products that have no
+// tensor-core form take nu in float on the SIMT units.
+template <typename Top>
+static bool split_bwd(const Batch& b, int i) {
+  if constexpr (!std::is_same<Top, __nv_bfloat16>::value) {
+    return false;
+  } else {
+    const Net& n = *b.net;
+    return b.tc && (n.geom[i - 1].kind == GCP_DENSE ? n.WT16x3[i - 1] != nullptr : n.CT16x3[i - 1] != nullptr);
+  }
+}
+// y = W^(i)^T nu in the mixed-precision chain, from the three-term operand
+// nu2 [R, kTerms d_i] or from nu in float. false: a tensor-core launch was refused.
+template <typename Top, typename T>
+static bool lin_backward_mixed(cudaStream_t st, const Batch& b, int i, const Top* nu2, const T* full, T* y) {
+  if constexpr (std::is_same<Top, __nv_bfloat16>::value && std::is_same<T, float>::value) {
+    const Net& net = *b.net;
+    const LayerGeom& g = net.geom[i - 1];
+    if (split_bwd<Top>(b, i)) {
+      if (g.kind == GCP_DENSE)
+        return gemm_tc_bf16(st, b.R, g.d_in, kTerms * g.d_out, nu2, net.WT16x3[i - 1], y, 1.0 / kTerms);
+      return conv_tc_bf16(st, b.R, split_geom(g), 1, net.CT16x3[i - 1], net.ct3_kp[i - 1], net.ct3_np[i - 1], nu2, y,
+                          1.0 / kTerms);
+    }
+    if (g.kind == GCP_DENSE) gemm_nt<float, float>(st, b.R, g.d_in, g.d_out, full, 0, net.WT32[i - 1], y);
+    else conv_T<float, float>(st, b.R, g, net.W32[i - 1], full, y);
+    return true;
+  }
+  return false;
+}
+// Which of nu's forms layer i's relaxation writes in the mixed-precision
+// chain: the three-term operand for tensor-core products (the layer's, or its
+// projection shortcut's), float for SIMT products and identity skips.
+template <typename Top>
+static void mixed_forms(const Batch& b, int i, bool& split, bool& full) {
+  const Net& net = *b.net;
+  const int sc = net.skip[i - 1] ? net.sc_map[i - 1] : 0;
+  const bool ident = net.skip[i - 1] && !sc;
+  const bool sp_i = split_bwd<Top>(b, i), sp_sc = sc && split_bwd<Top>(b, sc);
+  split = sp_i || sp_sc;
+  full = !sp_i || ident || (sc && !sp_sc);
+}
+
 // Linear forward step nubar^(i) = W^(i) a for all rows.
 template <typename Top, typename T>
 static void lin_forward(cudaStream_t st, const Batch& b, int i, const Top* a, const float* a_lo, T* out) {
@@ -1025,9 +1108,13 @@ static void lin_forward(cudaStream_t st, const Batch& b, int i, const Top* a, co
 // until its y^(m) exists (nu^(i) itself for the identity, S^T nu^(i) in the
 // chain's accumulation type for a projection); y^(i-1) then takes what was
 // parked for it, or -S^T c_k when the last layer adds xhat^(i-1) (from L-1
-// that is already folded into YL).
+// that is already folded into YL). In the mixed-precision chain (operand type
+// narrower than T) an identity skip takes nu in T (nu_full), not the operand
+// copy: an identity passes its term unaveraged into y^(m), so an operand
+// rounding there would reach the bound at full size.
 template <typename Top, typename T>
-static gcp_status skip_backward(Ctx& c, Batch& b, cudaStream_t st, int i, const Top* nu, T* y, const T* SK) {
+static gcp_status skip_backward(Ctx& c, Batch& b, cudaStream_t st, int i, const Top* nu, const Top* nu2,
+                                const T* nu_full, T* y, const T* SK) {
   const Net& net = *b.net;
   const int L = net.L;
   const int64_t R = b.R;
@@ -1039,8 +1126,19 @@ static gcp_status skip_backward(Ctx& c, Batch& b, cudaStream_t st, int i, const 
       T* dst = si == i ? (T*)b.ws("skip_tmp", (size_t)R * b.dmax() * sizeof(T), &s)
                        : (T*)b.ws("skipT" + std::to_string(m), (size_t)R * dm * sizeof(T), &s);
       if (!dst) return s;
-      lin_backward<Top, T>(st, b, sc, nu, nullptr, dst);
+      if (!std::is_same<Top, T>::value) {
+        if (!lin_backward_mixed<Top, T>(st, b, sc, nu2, nu_full, dst))
+          return c.fail(GCP_EDEVICE, "projection of layer %d: tensor-core product refused", i);
+      } else {
+        lin_backward<Top, T>(st, b, sc, nu, nullptr, dst);
+      }
       if (si == i) skip_add<T, T>(st, R, dm, dm, 0, dst, 0, y);
+    } else if (nu_full && si == i) {
+      skip_add<T, T>(st, R, dm, dm, 0, nu_full, 0, y);
+    } else if (nu_full) {
+      T* park = (T*)b.ws("skipT" + std::to_string(m), (size_t)R * dm * sizeof(T), &s);
+      if (!park) return s;
+      cudaMemcpyAsync(park, nu_full, (size_t)R * dm * sizeof(T), cudaMemcpyDeviceToDevice, st);
     } else if (si == i) {
       skip_add<Top, T>(st, R, dm, dm, 0, nu, 0, y);
     } else {
@@ -1052,7 +1150,7 @@ static gcp_status skip_backward(Ctx& c, Batch& b, cudaStream_t st, int i, const 
   const int k = net.consumer[i - 1], dm = net.dims[i - 1];
   if (k == L && i - 1 < L - 1) {
     skip_add<T, T>(st, R, dm, dm, 0, SK, b.K, y);
-  } else if (k > i && k < L && net.sc_map[k - 1]) {
+  } else if (k > i && k < L && (net.sc_map[k - 1] || !std::is_same<Top, T>::value)) {
     const T* park = (const T*)b.ws("skipT" + std::to_string(i - 1), (size_t)R * dm * sizeof(T), &s);
     if (!park) return s;
     skip_add<T, T>(st, R, dm, dm, 0, park, 0, y);
@@ -1141,8 +1239,24 @@ static const T* recompute_nuhat(Ctx& c, Batch& b, cudaStream_t st, int target, g
     a.nu_out = nu;
     a.nuhat_out = nh;
     a.theta = theta_of<T>(b, i);
+    if (!std::is_same<Top, T>::value && i > target) {
+      bool sp = false, fu = false;
+      mixed_forms<Top>(b, i, sp, fu);
+      a.nu_out = nullptr;
+      if (sp && !(a.nu_split = (Top*)b.ws("rc_nu2", (size_t)R * kTerms * mh * sizeof(Top), s))) return nullptr;
+      if (fu && !(a.nu_full = (T*)b.ws("rc_nu_full", (size_t)R * mh * sizeof(T), s))) return nullptr;
+    }
     relax_eval<T, Top>(st, a);
-    if (i > target) lin_backward<Top, T>(st, b, i, nu, nullptr, y);
+    if (i > target) {
+      if (!std::is_same<Top, T>::value) {
+        if (!lin_backward_mixed<Top, T>(st, b, i, a.nu_split, a.nu_full, y)) {
+          *s = c.fail(GCP_EDEVICE, "layer %d: tensor-core product refused", i);
+          return nullptr;
+        }
+      } else {
+        lin_backward<Top, T>(st, b, i, nu, nullptr, y);
+      }
+    }
   }
   return nh;
 }
@@ -1200,10 +1314,22 @@ gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, 
     a.obj_part = finalize ? part + (int64_t)poff * R : nullptr;   // ascent steps need no objective
     a.theta = theta_of<T>(b, i);
     a.theta_init = theta_init;
+    if (!std::is_same<Top, T>::value) {
+      bool sp = false, fu = false;
+      mixed_forms<Top>(b, i, sp, fu);
+      a.nu_out = nullptr;
+      if (sp && !(a.nu_split = (Top*)b.ws("nu2", (size_t)R * kTerms * b.dmax() * sizeof(Top), &s))) return s;
+      if (fu && !(a.nu_full = (T*)b.ws("nu_full", (size_t)R * b.dmax() * sizeof(T), &s))) return s;
+    }
     relax_eval<T, Top>(st, a);
     poff += (net.dims[i] + kChunk - 1) / kChunk;
-    lin_backward<Top, T>(st, b, i, nu, a.nu_lo, y);
-    s = skip_backward<Top, T>(c, b, st, i, nu, y, spec_skip<T>(net));
+    if (!std::is_same<Top, T>::value) {
+      if (!lin_backward_mixed<Top, T>(st, b, i, a.nu_split, a.nu_full, y))
+        return c.fail(GCP_EDEVICE, "layer %d: tensor-core product refused", i);
+    } else {
+      lin_backward<Top, T>(st, b, i, nu, a.nu_lo, y);
+    }
+    s = skip_backward<Top, T>(c, b, st, i, nu, a.nu_split, a.nu_full, y, spec_skip<T>(net));
     if (s) return s;
   }
   ConcArgs<T, Top> ca{};
@@ -1849,7 +1975,7 @@ gcp_status duals_import(Ctx& c, Batch& b, const double* alpha, const double* bet
 // Caller-owned device arrays of the device entry points take part in the launch
 // checks for the duration of the call (registered with their documented sizes).
 struct ForeignArrays {
-  std::vector<const void*> regs;
+  std::vector<uint64_t> regs;
   gcp_status add(Ctx& c, const void* p, size_t bytes, const char* what) {
     if (!p || bytes == 0) return GCP_OK;
     cudaPointerAttributes at{};
@@ -1857,12 +1983,11 @@ struct ForeignArrays {
       cudaGetLastError();
       return c.fail(GCP_EINVAL, "%s is not a device pointer", what);
     }
-    reg_alloc(p, bytes);
-    regs.push_back(p);
+    regs.push_back(reg_foreign(p, bytes));
     return GCP_OK;
   }
   ~ForeignArrays() {
-    for (const void* p : regs) reg_free(p);
+    for (uint64_t t : regs) reg_unforeign(t);
   }
 };
 

@@ -172,41 +172,60 @@ gcp_status bab_verify(Ctx& c, int net_id, int cutset_id, const gcp_bab_params& b
     }
     std::vector<double> cert((size_t)R);
     if (s == GCP_OK) s = optimize_batch(c, *b, &p, nullptr, cert.data(), nullptr);
-    // the subdomains that branch keep this round's duals on the device for their children
+    // the subdomains that branch keep their rows of this round's duals on the
+    // device for their children (only those rows, gathered by runs of
+    // consecutive branching subdomains); if the store cannot be allocated the
+    // children start from the default duals instead
     std::shared_ptr<ParentStore> store;
+    std::vector<int64_t> store_slot(n, -1);   // first store row of subdomain q
     if (s == GCP_OK) {
-      bool branching = false;
-      for (size_t q = 0; q < n && !branching; ++q)
-        for (int k = 0; k < K; ++k) branching |= !(cert[q * K + k] > 0);
-      if (branching) {
-        store = std::make_shared<ParentStore>();
-        store->c = &c;
-        store->rows = R;
-        store->M = M;
+      int64_t nb = 0;
+      for (size_t q = 0; q < n; ++q) {
+        bool br = false;
+        for (int k = 0; k < K; ++k) br |= !(cert[q * K + k] > 0);
+        if (br) store_slot[q] = (nb++) * K;
+      }
+      if (nb > 0) {
+        const int64_t rows = nb * K;
+        auto st_ = std::make_shared<ParentStore>();
+        st_->c = &c;
+        st_->rows = rows;
+        st_->M = M;
         {
           AllocPool g;
-          store->alpha = (float*)c.alloc((size_t)R * std::max<int64_t>(na, 1) * 4);
-          store->beta = (float*)c.alloc((size_t)R * std::max(M, 1) * 4);
-          store->gamma = (float*)c.alloc((size_t)R * std::max(N, 1) * 4);
+          st_->alpha = (float*)c.alloc((size_t)rows * std::max<int64_t>(na, 1) * 4);
+          st_->beta = (float*)c.alloc((size_t)rows * std::max(M, 1) * 4);
+          st_->gamma = (float*)c.alloc((size_t)rows * std::max(N, 1) * 4);
         }
-        if (!store->alpha || !store->beta || !store->gamma) {
-          s = c.fail(c.over_budget ? GCP_EBUDGET : GCP_ENOMEM, "branch and bound: parent store");
-        } else {
-          int64_t off = 0;
-          for (int l = 0; l < L1 && s == GCP_OK; ++l) {
-            const int d = net.dims[l + 1];
-            const cudaError_t e = cudaMemcpy2DAsync(store->alpha + off, (size_t)na * 4, b->alpha[l], (size_t)d * 4,
-                                                    (size_t)d * 4, (size_t)R, cudaMemcpyDeviceToDevice, c.stream);
-            if (e) s = c.cuda(e, "branch and bound: store alpha");
-            off += d;
+        if (st_->alpha && st_->beta && st_->gamma) {
+          store = st_;
+          for (size_t q0 = 0; q0 < n && s == GCP_OK;) {
+            if (store_slot[q0] < 0) {
+              ++q0;
+              continue;
+            }
+            size_t q1 = q0 + 1;   // a run of consecutive branching subdomains
+            while (q1 < n && store_slot[q1] >= 0) ++q1;
+            const int64_t src = (int64_t)q0 * K, dst = store_slot[q0], cnt = (int64_t)(q1 - q0) * K;
+            int64_t off = 0;
+            for (int l = 0; l < L1 && s == GCP_OK; ++l) {
+              const int d = net.dims[l + 1];
+              const cudaError_t e =
+                  cudaMemcpy2DAsync(store->alpha + dst * na + off, (size_t)na * 4, (float*)b->alpha[l] + src * d,
+                                    (size_t)d * 4, (size_t)d * 4, (size_t)cnt, cudaMemcpyDeviceToDevice, c.stream);
+              if (e) s = c.cuda(e, "branch and bound: store alpha");
+              off += d;
+            }
+            if (s == GCP_OK && M > 0)
+              s = c.cuda(cudaMemcpyAsync(store->beta + dst * M, (float*)b->beta + src * M, (size_t)cnt * M * 4,
+                                         cudaMemcpyDeviceToDevice, c.stream), "branch and bound: store beta");
+            if (s == GCP_OK && N > 0)
+              s = c.cuda(cudaMemcpyAsync(store->gamma + dst * N, (float*)b->gamma + src * N, (size_t)cnt * N * 4,
+                                         cudaMemcpyDeviceToDevice, c.stream), "branch and bound: store gamma");
+            q0 = q1;
           }
-          if (s == GCP_OK && M > 0)
-            s = c.cuda(cudaMemcpyAsync(store->beta, b->beta, (size_t)R * M * 4, cudaMemcpyDeviceToDevice, c.stream),
-                       "branch and bound: store beta");
-          if (s == GCP_OK && N > 0)
-            s = c.cuda(cudaMemcpyAsync(store->gamma, b->gamma, (size_t)R * N * 4, cudaMemcpyDeviceToDevice,
-                                       c.stream), "branch and bound: store gamma");
         }
+        // else: st_ gives back what it got; store stays null (default duals)
       }
     }
     cudaStreamSynchronize(c.stream);
@@ -248,7 +267,7 @@ gcp_status bab_verify(Ctx& c, int net_id, int cutset_id, const gcp_bab_params& b
         ch.sgn.push_back(side == 0 ? 1 : -1);
         ch.margin = m;
         ch.par = store;
-        ch.prow = (int64_t)q * K;
+        ch.prow = store ? store_slot[q] : 0;
         pending.push_back(std::move(ch));
       }
     }

@@ -32,6 +32,13 @@ struct Net {
   std::vector<float*> Wabs32;        // |W| in float rounded up (convolution layers; certification)
   std::vector<SliceB> WTsl;          // exact bf16 slices of W^T (dense layers; float64 certification)
   std::vector<int> cf_kp, cf_np, ct_kp, ct_np;
+  // the mixed-precision chain's backward products with three-term bf16
+  // operands: dense layers [d_in, 3 d_out] = rows of [W_hi^T | W_hi^T | W_lo^T];
+  // convolutions packed for the transposed plan of split_geom(g) (source
+  // channels tripled, the weights of terms hi, hi, lo); nullptr where that
+  // product stays on the SIMT units (with nu in float)
+  std::vector<__nv_bfloat16*> WT16x3, CT16x3;
+  std::vector<int> ct3_kp, ct3_np;
   double *xlo64 = nullptr, *xhi64 = nullptr;
   float *xlo32 = nullptr, *xhi32 = nullptr;
   double *C64 = nullptr, *negC64 = nullptr, *bL64 = nullptr;
@@ -132,7 +139,10 @@ struct Serve;
 struct Ctx {
   int device = 0;
   uint64_t budget = 0, used = 0;
-  bool over_budget = false;
+  // whether this thread's last failed allocation was refused by the budget
+  // (rather than by cudaMalloc); per thread, as serving workers allocate
+  // concurrently
+  bool over_budget() const;
   cudaStream_t own_stream = nullptr, stream = nullptr;
   std::recursive_mutex mu;
   std::mutex alloc_mu;               // allocations may come from serving worker threads

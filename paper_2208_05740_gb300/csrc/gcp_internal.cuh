@@ -30,6 +30,18 @@ struct LayerGeom {
   int kind, d_in, d_out;
   int c_in, h_in, w_in, c_out, h_out, w_out, k, stride, pad;
 };
+// The mixed-precision chain's products run as three bf16 terms concatenated
+// along K: operand [nu_hi | nu_lo | nu_hi] against weights [W_hi | W_hi | W_lo]
+// (hi = bf16(x), lo = bf16(x - hi)), i.e. nu_hi W_hi + nu_lo W_hi + nu_hi W_lo
+// in one tensor-core product with float accumulation.
+constexpr int kTerms = 3;
+// The geometry whose transposed product takes that operand: output channels
+// (the transposed product's source channels) times kTerms.
+inline LayerGeom split_geom(LayerGeom g) {
+  g.c_out *= kTerms;
+  g.d_out *= kTerms;
+  return g;
+}
 
 // Cut entries of one layer in CSC order (per neuron), pointers already offset.
 template <typename T>
@@ -92,6 +104,14 @@ struct RelaxArgs {
   // write the theta that reproduces it
   T* theta;             // [R, d]
   int theta_init;
+  // Outputs of the mixed-precision chain (bf16 operands, T = float), each
+  // written only where set: nu in T, for the products that stay on the SIMT
+  // units and for identity skip connections (which would otherwise carry an
+  // operand rounding into y^(m) unaveraged); and nu's three-term operand, row
+  // r = [hi | lo | hi] with hi = bf16(nu) and lo = bf16(nu - hi), for the
+  // tensor-core products against [W_hi | W_hi | W_lo] (nu_out is then nullptr).
+  T* nu_full;           // [R, d]
+  Top* nu_split;        // [R, kTerms * d]
 };
 
 template <typename T, typename Top>
@@ -233,10 +253,18 @@ inline cudaError_t launch_pdl(void (*kern)(P...), dim3 grid, dim3 block, size_t 
 // allocation with room for the largest extent the kernel can touch. A launch
 // that fails the check is skipped and the problem is recorded for the API
 // call to report (GCP_EDEVICE), so a bad argument never reaches the GPU.
+// Allocations are keyed by device: a pointer passes only on the device it was
+// allocated on (the current device at the check). Caller-owned arrays that
+// take part in one call are registered beside the library's allocations by
+// token, so a caller pointer equal to (or inside) a library allocation never
+// replaces or removes the library's own entry. Problems are recorded per
+// host thread: each API call (and each serving worker) reads its own.
 void reg_alloc(const void* p, size_t bytes);
 void reg_free(const void* p);
+uint64_t reg_foreign(const void* p, size_t bytes);   // returns a token for reg_unforeign
+void reg_unforeign(uint64_t token);
 bool reg_check(const void* p, double bytes, const char* what);
-// first recorded problem since the last call (empty if none); clears it
+// first problem this thread recorded since it last asked (empty if none); clears it
 std::string reg_take_error();
 // first failed in-kernel index check since the last call (synchronises st)
 std::string take_device_error(cudaStream_t st);
@@ -288,7 +316,10 @@ void bab_warm_start(cudaStream_t st, int64_t R, int n_layers, const int* dims_de
 
 // tcgen05 GEMMs (k_tc.cu); false = shape or driver not supported, use SIMT
 bool tc_available(int K, bool bf16);
-bool gemm_tc_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C);
+// flop_scale scales the flops the profiler counts (1/3 for a product whose K
+// is tripled by the three-term operands: the product is counted once)
+bool gemm_tc_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C,
+                  double flop_scale = 1.0);
 // A plain fp32 (split into tf32 parts in the kernel); B given as tf32 high and low parts
 bool gemm_tc_tf32x3(cudaStream_t st, int64_t M, int N, int K, const float* A, const float* B, const float* Blo,
                     float* C);
@@ -403,9 +434,12 @@ __host__ __device__ inline bool conv_plan(const LayerGeom& g, int dir, ConvPlan&
 // Convolution on the tensor cores (implicit GEMM, bf16 operands, fp32 out):
 // dir 0 out = conv(src) [R, d_out], dir 1 out = conv^T(src) [R, d_in]. Wp is
 // the weight packed for that direction's plan, [Np, Kp]. false = shape not
-// supported (use the SIMT convolution).
+// supported (use the SIMT convolution). flop_scale as for gemm_tc_bf16.
 bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const __nv_bfloat16* Wp, int Kp, int Np,
-                  const __nv_bfloat16* src, float* out);
+                  const __nv_bfloat16* src, float* out, double flop_scale = 1.0);
+// Whether conv_tc_bf16 takes this plan at any row count (its staging fits
+// shared memory and its accumulators TMEM).
+bool conv_tc_fits(const LayerGeom& g, int dir, int Kp, int Np);
 
 template <typename T, typename Top>
 void relax_eval(cudaStream_t st, const RelaxArgs<T, Top>& a);

@@ -327,6 +327,42 @@ __device__ __forceinline__ void put_operand_v(Top* hi, float* lo, int64_t i, con
   }
 }
 
+// Three-term bf16 operand of the mixed-precision chain: hi = bf16(x) at p[i]
+// and p[i + 2d], lo = bf16(x - hi) at p[i + d] (hi + lo carries about 16
+// significant bits).
+template <int V, typename Top, typename T>
+__device__ __forceinline__ void put_split_v(Top* p, int64_t i, int d, const T (&x)[V]) {
+  if constexpr (std::is_same<Top, __nv_bfloat16>::value && std::is_same<T, float>::value) {
+    float lo[V];
+    __nv_bfloat16 h[V], l[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      h[v] = __float2bfloat16_rn(x[v]);
+      lo[v] = x[v] - __bfloat162float(h[v]);
+      l[v] = __float2bfloat16_rn(lo[v]);
+    }
+    if constexpr (V == 4) {
+      const __nv_bfloat162 h0 = __halves2bfloat162(h[0], h[1]), h1 = __halves2bfloat162(h[2], h[3]);
+      const __nv_bfloat162 l0 = __halves2bfloat162(l[0], l[1]), l1 = __halves2bfloat162(l[2], l[3]);
+      uint2 uh, ul;
+      uh.x = *reinterpret_cast<const uint32_t*>(&h0);
+      uh.y = *reinterpret_cast<const uint32_t*>(&h1);
+      ul.x = *reinterpret_cast<const uint32_t*>(&l0);
+      ul.y = *reinterpret_cast<const uint32_t*>(&l1);
+      *reinterpret_cast<uint2*>(p + i) = uh;
+      *reinterpret_cast<uint2*>(p + i + d) = ul;
+      *reinterpret_cast<uint2*>(p + i + 2 * d) = uh;
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        p[i + v] = h[v];
+        p[i + d + v] = l[v];
+        p[i + 2 * d + v] = h[v];
+      }
+    }
+  }
+}
+
 // Bounds, class and split of the lane's V neurons.
 template <typename T, int V>
 struct SpanNeurons {
@@ -680,7 +716,9 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_eval(RelaxArgs<T, Top
           nu[v] = cl == 2 ? nuu : (cl == 1 ? nh[v] - t[v] : -t[v]);   // active: xhat = x, z = 1
           if (obj) term += (cl == 2 ? hu : (cl == 1 ? sq[v] : T(0))) - nu[v] * n.bj[v];
         }
-        put_operand_v<V, Top>(a.nu_out, a.nu_lo, ij, nu);
+        if (a.nu_out) put_operand_v<V, Top>(a.nu_out, a.nu_lo, ij, nu);
+        if (a.nu_split) put_split_v<V, Top>(a.nu_split, r * kTerms * a.d + w.j0, a.d, nu);
+        if (a.nu_full) stv<V>(a.nu_full + ij, nu);
         stv<V>(a.nuhat_out + ij, nh);
         if constexpr (PI) {
           if (a.theta_init) stv<V>(a.theta + ij, th);
@@ -1325,7 +1363,8 @@ void relax_eval(cudaStream_t st, const RelaxArgs<T, Top>& a) {
   if (a.R <= 0 || a.d <= 0) return;
   char nm[48];
   snprintf(nm, sizeof nm, "relax_eval_%s%s", tsfx<T>(), sizeof(Top) == 2 ? "_bf16" : "");
-  const double bytes = (double)a.R * a.d * (3.0 * sizeof(T) + sizeof(Top)) +
+  const double bytes = (double)a.R * a.d * (3.0 * sizeof(T) + (a.nu_out ? sizeof(Top) : 0) +
+                                            (a.nu_split ? kTerms * sizeof(Top) : 0.0) + (a.nu_full ? sizeof(T) : 0)) +
                        (double)a.R * (a.csc.n_entries + (a.d + 31) / 32) * sizeof(T);
   const double Rd = (double)a.R * a.d, tb = sizeof(T);
   if (!(reg_check(a.y, (a.y_per_spec ? (double)a.K : (double)a.R) * a.d * tb, "relax y") &
@@ -1333,15 +1372,18 @@ void relax_eval(cudaStream_t st, const RelaxArgs<T, Top>& a) {
         reg_check(a.inv_ul, a.inv_ul ? a.d * tb : 0.0, "inv_ul") &
         reg_check(a.alpha, Rd * tb, "alpha") & reg_check(a.beta, (double)a.M * a.R * tb, "beta") &
         reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") & chk_splits(a.sp, a.R, a.K, a.M) &
-        chk_csc(a.csc, a.d) & reg_check(a.nu_out, Rd * sizeof(Top), "nu out") &
+        chk_csc(a.csc, a.d) & reg_check(a.nu_out, a.nu_out ? Rd * sizeof(Top) : 0.0, "nu out") &
+        reg_check(a.nu_split, a.nu_split ? kTerms * Rd * sizeof(Top) : 0.0, "nu split") &
         reg_check(a.nu_lo, a.nu_lo ? Rd * 4.0 : 0.0, "nu lo") &
         reg_check(a.nuhat_out, Rd * tb, "nuhat out") & reg_check(a.theta, a.theta ? Rd * tb : 0.0, "theta") &
+        reg_check(a.nu_full, a.nu_full ? Rd * tb : 0.0, "nu full") &
         (!a.obj_part || reg_check(a.obj_part, ((a.d + 31) / 32) * (double)a.R * tb, "obj part"))))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
   if constexpr (sizeof(T) == 4) {
     if (span_v4<T>(a.d) && al16(a.y) && al16(a.alpha) && al16(a.lo) && al16(a.hi) && al16(a.bias) &&
-        al16(a.inv_ul) && al16(a.nu_out) && al16(a.nu_lo) && al16(a.nuhat_out) && al16(a.theta)) {
+        al16(a.inv_ul) && al16(a.nu_out) && al16(a.nu_lo) && al16(a.nuhat_out) && al16(a.theta) &&
+        al16(a.nu_full) && (reinterpret_cast<uintptr_t>(a.nu_split) & 7) == 0) {
       if (a.theta)
         launch_span(k_relax_eval<T, Top, 4, true>, span_smem<T, 4, 2, 4, 3>(), span_blocks(a.R, a.K, a.d, 4), st, a);
       else

@@ -953,13 +953,15 @@ bool tc_available(int K, bool bf16) {
   return bf16 ? (K % 8 == 0) : (K % 4 == 0);
 }
 
-bool gemm_tc_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C) {
+bool gemm_tc_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C,
+                  double flop_scale) {
   if (M <= 0 || N <= 0) return true;
   if (!tc_available(K, true) || M > (int64_t)INT32_MAX) return false;
   if (!(reg_check(A, (double)M * K * 2, "tc A") & reg_check(B, (double)N * K * 2, "tc B") &
         reg_check(C, (double)M * N * 4, "tc C")))
     return true;  // reported by the caller's launch status
-  int tk = prof_begin(st, "gemm_tc_bf16", 2.0 * M * N * K, ((double)M * K + (double)N * K) * 2 + (double)M * N * 4);
+  int tk = prof_begin(st, "gemm_tc_bf16", flop_scale * 2.0 * M * N * K,
+                      ((double)M * K + (double)N * K) * 2 + (double)M * N * 4);
   const bool ok = launch_tc<0>(st, M, N, K, A, B, nullptr, C);
   prof_end(st, tk);
   return ok;
@@ -1163,8 +1165,28 @@ bool gemm_f64_slices(cudaStream_t st, int64_t M, int N, int K, const double* A, 
   return true;
 }
 
+bool conv_tc_fits(const LayerGeom& g, int dir, int Kp, int Np) {
+  ConvPlan c;
+  if (!conv_plan(g, dir, c) || c.Kp != Kp || c.Np != Np || Np > 256) return false;
+  // the staging window grows with the row count until a tile spans whole
+  // rows of every phase; a large row count gives the largest
+  const int R = 1 << 16;
+  conv_set_tiles(c, R);
+  int rows = 0;
+  for (int q = 0; q < c.nph; ++q) {
+    const int Pf = c.f[q].Hf * c.f[q].Wf;
+    for (int t = 0; t < std::min(c.f[q].ntiles, Pf + 1); ++t) {
+      const ConvTile T = conv_tile(c, R, c.f[q].tile0 + t);
+      rows = std::max(rows, T.nrt == 1 ? T.nsh : T.nrt * c.Hs);
+    }
+  }
+  int tc = 32;
+  while (tc < Np) tc <<= 1;
+  return conv_smem_layout(Kp, Np, std::max(rows, 1), c.Ws, c.Csp, 1).total <= 227 * 1024 && 2 * tc <= 512;
+}
+
 bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const __nv_bfloat16* Wp, int Kp, int Np,
-                  const __nv_bfloat16* src, float* out) {
+                  const __nv_bfloat16* src, float* out, double flop_scale) {
   if (R <= 0) return true;
   ConvTcArgs a{};
   ConvPlan& c = a.c;
@@ -1239,7 +1261,7 @@ bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const
   // algorithmic work: the convolution's multiply-adds (2 flops each); bytes:
   // source read and output written once
   const double macs = (double)R * g.c_out * g.h_out * g.w_out * g.c_in * g.k * g.k;
-  int tk = prof_begin(st, dir == 0 ? "conv_tc_bf16_fwd" : "conv_tc_bf16_T", 2.0 * macs,
+  int tk = prof_begin(st, dir == 0 ? "conv_tc_bf16_fwd" : "conv_tc_bf16_T", flop_scale * 2.0 * macs,
                       (double)R * src_dim * 2 + (double)R * out_dim * 4);
   launch_pdl(k_conv_tc, dim3(grid), dim3(kConvThreads), L.total, st, a);
   prof_end(st, tk);

@@ -1,13 +1,13 @@
 // Bound evaluation that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc: work recorded into a CUDA graph under
-// stream capture (an allocation there breaks the capture), serving processes
-// that reserve the whole GPU for their own memory pool up front and forbid
-// any further allocation, and latency-critical loops where cudaMalloc's
-// implicit device synchronisation is not acceptable. For them this file
-// provides gcp_bound_dense_noalloc: the FP32 bound of dense ReLU networks
-// without cuts or splits, every input and the output passed in by the caller,
-// and the scratch of the chain kept in a fixed device array of this file.
+// Some callers cannot call cudaMalloc: serving processes that reserve the
+// whole GPU for their own memory pool up front, so that any further
+// allocation fails, and latency-critical loops where the device-wide
+// synchronisation of cudaMalloc and cudaFree is not acceptable. For them this
+// file provides gcp_bound_dense_noalloc: the FP32 bound of dense ReLU
+// networks without cuts or splits, every input and the output passed in by
+// the caller, and the scratch of the chain kept in a fixed device array of
+// this file.
 #include <cstdint>
 #include <mutex>
 #include <vector>
@@ -43,7 +43,7 @@ cudaError_t scratch_of(int dev, void** out) {
 
 // Caller arrays take part in the launch checks while the call enqueues work.
 struct CallerArrays {
-  std::vector<const void*> regs;
+  std::vector<uint64_t> regs;
   bool add(const void* p, size_t bytes) {
     if (bytes == 0) return true;
     if (!p) return false;
@@ -52,12 +52,11 @@ struct CallerArrays {
       cudaGetLastError();
       return false;
     }
-    reg_alloc(p, bytes);
-    regs.push_back(p);
+    regs.push_back(reg_foreign(p, bytes));
     return true;
   }
   ~CallerArrays() {
-    for (const void* p : regs) reg_free(p);
+    for (uint64_t t : regs) reg_unforeign(t);
   }
 };
 

@@ -137,48 +137,93 @@ gcp_status gcp_profile_report(char* buf, int64_t cap) {
 // ---------------------------------------------------------------- launch validation
 namespace gcp {
 namespace {
+struct RegKey {
+  int dev;
+  uintptr_t base;
+  bool operator<(const RegKey& o) const { return dev != o.dev ? dev < o.dev : base < o.base; }
+};
+struct Foreign {
+  int dev;
+  uintptr_t base;
+  size_t bytes;
+};
 std::mutex g_reg_mu;
-std::map<uintptr_t, size_t> g_reg;
-std::string g_reg_err;
+std::map<RegKey, size_t> g_reg;                 // the library's allocations (disjoint per device)
+std::map<uint64_t, Foreign> g_foreign;          // caller arrays of calls in flight, by token
+uint64_t g_next_token = 1;
+thread_local std::string t_reg_err;             // the calling thread's first problem
+
+int current_device() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return d;
+}
+
+bool covers(uintptr_t base, size_t bytes, uintptr_t a, double need, size_t& have) {
+  if (a < base || a - base > bytes) return false;
+  have = bytes - (a - base);
+  return (double)have >= need;
+}
 }  // namespace
 
 void reg_alloc(const void* p, size_t bytes) {
+  const int dev = current_device();
   std::lock_guard<std::mutex> lk(g_reg_mu);
-  g_reg[(uintptr_t)p] = bytes;
+  g_reg[RegKey{dev, (uintptr_t)p}] = bytes;
 }
 
 void reg_free(const void* p) {
+  const int dev = current_device();
   std::lock_guard<std::mutex> lk(g_reg_mu);
-  g_reg.erase((uintptr_t)p);
+  g_reg.erase(RegKey{dev, (uintptr_t)p});
+}
+
+uint64_t reg_foreign(const void* p, size_t bytes) {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  const uint64_t t = g_next_token++;
+  g_foreign[t] = Foreign{dev, (uintptr_t)p, bytes};
+  return t;
+}
+
+void reg_unforeign(uint64_t token) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  g_foreign.erase(token);
 }
 
 bool reg_check(const void* p, double bytes, const char* what) {
   if (bytes <= 0) return true;
-  std::lock_guard<std::mutex> lk(g_reg_mu);
+  const int dev = current_device();
   const uintptr_t a = (uintptr_t)p;
-  auto it = g_reg.upper_bound(a);
   bool ok = false;
   size_t have = 0;
-  if (p && it != g_reg.begin()) {
-    --it;
-    if (a >= it->first && a - it->first <= it->second) {
-      have = it->second - (a - it->first);
-      ok = (double)have >= bytes;
+  {
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    if (p) {
+      auto it = g_reg.upper_bound(RegKey{dev, a});
+      if (it != g_reg.begin()) {
+        --it;
+        if (it->first.dev == dev) ok = covers(it->first.base, it->second, a, bytes, have);
+      }
+      for (auto f = g_foreign.begin(); !ok && f != g_foreign.end(); ++f)
+        if (f->second.dev == dev) ok = covers(f->second.base, f->second.bytes, a, bytes, have);
     }
   }
-  if (!ok && g_reg_err.empty()) {
+  if (!ok && t_reg_err.empty()) {
     char buf[256];
     snprintf(buf, sizeof buf, "launch check failed: %s at %p needs %.0f bytes, allocation has %zu", what, p, bytes,
              have);
-    g_reg_err = buf;
+    t_reg_err = buf;
   }
   return ok;
 }
 
 std::string reg_take_error() {
-  std::lock_guard<std::mutex> lk(g_reg_mu);
   std::string e;
-  e.swap(g_reg_err);
+  e.swap(t_reg_err);
   return e;
 }
 }  // namespace gcp

@@ -1,10 +1,12 @@
 """Tensor-core implicit-GEMM convolution of the BF16 chain.
 
 The BF16 chain runs both convolution directions on the tensor cores (the
-backward step y = W^T nu as a transposed convolution, the reverse-mode step
-W a as a convolution). Here it is compared with the SIMT convolution on the
-same bf16 operands (the two differ only in the fp32 summation order) and with
-the FP64 oracle at the bf16 tolerance, on the CIFAR-shaped CNN (tiles that
+backward step y = W^T nu as a transposed convolution of three-term bf16
+operands, the reverse-mode step W a as a convolution). Without the tensor
+cores the backward step runs in float on the SIMT units and the reverse-mode
+step on the same bf16 operands. Here the two are compared with the FP64
+oracle (the tensor-core chain at the bf16 tolerance, the float one at the
+fp32 tolerance) and with each other, on the CIFAR-shaped CNN (tiles that
 straddle rows, a ragged last tile) and on a CNN with odd shapes: 5 input
 channels (padded to 8 in the GEMM's K), 7x9 maps, a stride-2 padded and a
 stride-1 unpadded convolution, 12 and 20 channels; and on kernels 5 and 4 with
@@ -100,15 +102,9 @@ def test_conv_tc_matches_simt_and_oracle(ctx, case):
     ref = O.evaluate(O.build_problem(inst), oracle_duals(inst, A, B, G))
     gt, _ = ctx.bound_batch(Dt, gcp.GCP_BF16)
     gs, _ = ctx.bound_batch(Ds, gcp.GCP_BF16)
-    assert_rel(gt, gs, 1e-5, f"{case}: tensor-core vs SIMT convolution")
-    if case == "cifar":
-        assert_rel(gt, ref, 1e-3, f"{case}: bf16 chain vs oracle")
-    else:
-        # on the small odd-shape networks (bounds near 1, much cancellation)
-        # the bf16 operand rounding alone can exceed 1e-3: the tensor-core
-        # convolution must add nothing beyond it
-        scale = np.maximum(1.0, np.abs(ref))
-        assert np.all(np.abs(gt - ref) <= np.abs(gs - ref) + 1e-5 * scale), f"{case}: tensor cores add error"
+    assert_rel(gt, ref, 1e-3, f"{case}: bf16 chain (three-term tensor-core products) vs oracle")
+    assert_rel(gs, ref, 1e-5, f"{case}: bf16 chain without tensor cores (float products) vs oracle")
+    assert_rel(gt, gs, 1e-4, f"{case}: tensor-core vs SIMT convolution")
     # reverse mode: the forward convolution on the tensor cores. The reverse
     # pass rounds each layer's operand a to bf16, so a last-bit difference of
     # the fp32 sums upstream can flip one rounding (a 2^-8 relative change of
