@@ -1,16 +1,22 @@
 #!/usr/bin/env python
 """Benchmark: certified subdomain-bounds per second at a fixed iteration count.
 
-Workload (default): ReLU MLP 784-256x6-10, 1024 branch-and-bound subdomains
-(1-8 neuron splits each) x 9 spec rows, 200 sparse cuts over 2-8 variables,
-100 Adam ascent iterations on (alpha, beta, gamma) in the FP32 chain, then
-the FP64 outward-rounded certification pass. One step = that whole hot path
-for the batch; one unit = one subdomain with all its spec rows optimised and
-certified. Inputs are seeded synthetic data of the paper's shapes.
+Every workload takes its root intermediate bounds from CROWN (Sec. 2),
+computed by the library's own certified propagation before the timed region
+(the oracle legs compute them with the oracle).
 
---workload cnn: CNN 3x32x32 -> conv32 3x3 s2 -> conv64 3x3 s2 -> FC512 ->
-FC10, 4096 subdomains (1-12 splits) x 9 spec rows, 1000 cuts over 2-16
-variables, 50 Adam iterations in the BF16 chain, FP64 certification.
+Headline (default --workload mlp): ReLU MLP 784-256x6-10, 1024
+branch-and-bound subdomains (1-8 neuron splits each) x 9 spec rows, 200
+sparse cuts over 2-8 variables, 100 Adam ascent iterations on (alpha, beta,
+gamma) in the FP32 chain, then the FP64 outward-rounded certification pass.
+One step = that whole hot path for the batch; one unit = one subdomain with
+all its spec rows optimised and certified. Inputs are seeded synthetic data
+of the paper's shapes.
+
+The default run also times, under "workloads.cnn", the CNN 3x32x32 ->
+conv32 3x3 s2 -> conv64 3x3 s2 -> FC512 -> FC10, 4096 subdomains (1-12
+splits) x 9 spec rows, 1000 cuts over 2-16 variables, 50 Adam iterations in
+the BF16 chain, FP64 certification (--workload cnn makes it the headline).
 
 --workload resnet: residual CNN of the resnet2b shape, 3x32x32 -> conv8 3x3
 s2 -> ResBlock(8,16) (conv s2, conv, 1x1 s2 shortcut) -> ResBlock(16,16)
@@ -22,6 +28,11 @@ value  : device-timed (CUDA events on the library's stream), inputs resident.
 e2e    : the same through the public C ABI from host buffers: every step
          creates the batch from host split arrays (uploads splits and cuts),
          optimises, certifies, copies bounds back and frees the batch.
+forms  : the same workload in the other chain precision (and with pi
+         optimised directly), with the certified-bound quality of each form
+         against the workload's own form.
+serving: the continuous-batching stream at 200 requests/s (over capacity)
+         and at 1 request/s (below it).
 --impl reference : the FP64 CPU oracle on a bounded sample of the workload.
 Multi-GPU (torchrun): every rank runs its own batch (weak scaling, no
 collective on the data path); value = all ranks' subdomains / max time.
@@ -60,6 +71,8 @@ def parse():
     ap.add_argument("--profile-all", action="store_true", help="print every kernel's share (untimed step)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving stream (0: skip)")
     ap.add_argument("--no-bf16-form", action="store_true", help="skip the BF16-chain form of the workload")
+    ap.add_argument("--no-cnn", action="store_true",
+                    help="skip the CNN workload that the default (mlp) run also times")
     ap.add_argument("--no-opt-pi-form", action="store_true",
                     help="skip the form with the ReLU duals pi optimised directly (opt_pi)")
     a = ap.parse_args()
@@ -70,19 +83,19 @@ def parse():
     return a
 
 
-def _build_mlp(n_sub):
+def _build_mlp(n_sub, root_bounds=None):
     from paper_2208_05740_gb300 import synth
-    return synth.mlp_256x6(n_sub=n_sub)
+    return synth.mlp_256x6(n_sub=n_sub, root_bounds=root_bounds)
 
 
-def _build_cnn(n_sub):
+def _build_cnn(n_sub, root_bounds=None):
     from paper_2208_05740_gb300 import synth
-    return synth.cnn_cifar(n_sub=n_sub)
+    return synth.cnn_cifar(n_sub=n_sub, root_bounds=root_bounds)
 
 
-def _build_resnet(n_sub):
+def _build_resnet(n_sub, root_bounds=None):
     from paper_2208_05740_gb300 import synth
-    return synth.cnn_resnet(n_sub=n_sub)
+    return synth.cnn_resnet(n_sub=n_sub, root_bounds=root_bounds)
 
 
 # The workloads: name, instance builder, defaults, oracle sample size.
@@ -96,12 +109,12 @@ WORKLOADS = {
 }
 
 
-def workload_config(a, n_gpus):
-    w = WORKLOADS[a.workload]
-    return {"workload": w["name"], "n_subdomains_per_gpu": a.n_sub, "spec_rows": 9, "rows_per_gpu": a.n_sub * 9,
-            "cuts": w["cuts"], "splits_per_subdomain": w["splits"], "iters": a.iters, "optimizer": "adam",
-            "lr": [0.1, 0.02, 0.02], "lr_decay": 0.98, "chain": a.prec, "certify": "fp64_outward_rounded",
-            "intermediate_bounds": "interval (IBP)", "l2": "flushed between steps (256 MiB write)",
+def workload_config(wname, n_sub, iters, prec, n_gpus, inter="CROWN"):
+    w = WORKLOADS[wname]
+    return {"workload": w["name"], "n_subdomains_per_gpu": n_sub, "spec_rows": 9, "rows_per_gpu": n_sub * 9,
+            "cuts": w["cuts"], "splits_per_subdomain": w["splits"], "iters": iters, "optimizer": "adam",
+            "lr": [0.1, 0.02, 0.02], "lr_decay": 0.98, "chain": prec, "certify": "fp64_outward_rounded",
+            "intermediate_bounds": inter, "l2": "flushed between steps (256 MiB write)",
             "parallelism": f"replicas{n_gpus}" if n_gpus > 1 else "single_gpu"}
 
 
@@ -247,15 +260,20 @@ def job_value(world: int, units_per_rank: int, steps: int, seconds: float) -> fl
     return world * units_per_rank * steps / seconds
 
 
+def oracle_instance(wname, n_sub):
+    """The workload with CROWN root bounds computed by the oracle (CPU legs only)."""
+    from oracle import gcp_oracle as O
+    return WORKLOADS[wname]["build"](n_sub, O.crown_root_bounds)
+
+
 def run_reference(a):
     import numpy as np
-    from paper_2208_05740_gb300 import synth
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    inst = WORKLOADS[a.workload]["build"](64)
+    inst = oracle_instance(a.workload, 64)
     n_sub = WORKLOADS[a.workload]["sample"]
-    cfg = workload_config(a, a.gpus)
+    cfg = workload_config(a.workload, a.n_sub, a.iters, a.prec, a.gpus)
     for _ in range(a.warmup):
         oracle_sample(inst, n_sub, a.iters, seconds_cap=2.0)
     vals = []
@@ -332,7 +350,7 @@ def serving_bench(dev, n_requests, rate=200.0, rounds=10, iters=20, max_inflight
         rows_total += res.rows
         subs_total += sub.n
         errs.append(res.max_err_vs_fp64)
-        rel.append(res.max_err_vs_fp64 / max(1.0, float(np.min(np.abs(out))) if len(out) else 1.0))
+        rel.append(res.max_rel_err_vs_fp64)
     wall = time.perf_counter() - t0
     ctx.serve_stop()
     ctx.close()
@@ -347,19 +365,23 @@ def serving_bench(dev, n_requests, rate=200.0, rounds=10, iters=20, max_inflight
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "max": float(lat.max())},
         "max_err_vs_fp64": float(np.max(errs)),
+        "max_rel_err_vs_fp64": float(np.max(rel)),
+        "note": "latency = completion - submission; max errors are over every row of every request, chain "
+                "(BF16) bound against the certified FP64 bound; relative = divided by max(1, |certified|)",
     }
 
 
-def inter_bounds_bench(ctx, inst, params, cert_ibp):
+def inter_bounds_bench(ctx, wname, inst, params):
     """Root intermediate bounds by the library's own certified propagation:
     wall time of CROWN (default slopes) and alpha-CROWN (20 Adam steps per
     neuron row) bounds for the workload's network, the fraction of unstable
-    hidden neurons under each, and the workload's certified bounds (same
-    subdomains, cuts and schedule) with the CROWN root bounds in place of the
-    interval bounds the synthetic instance carries."""
+    hidden neurons under interval, CROWN and alpha-CROWN bounds, the
+    workload's mean certified bound under interval and CROWN root bounds
+    (same seed and schedule), and a few rounds of branch and bound from the
+    root on the CROWN bounds."""
     import numpy as np
     import torch
-    from paper_2208_05740_gb300 import gcp, synth
+    from paper_2208_05740_gb300 import gcp
 
     def unstable(lo, hi):
         n = sum(len(x) for x in lo)
@@ -374,17 +396,17 @@ def inter_bounds_bench(ctx, inst, params, cert_ibp):
     t0 = time.perf_counter()
     alo, ahi = ctx.intermediate_bounds(inst.net.layers, inst.x_lo, inst.x_hi, pa)
     out["alpha_crown_20it_s"] = time.perf_counter() - t0
-    out["unstable_fraction"] = {"interval": unstable(inst.inter_lo, inst.inter_hi), "crown": unstable(lo, hi),
+    ibp = WORKLOADS[wname]["build"](inst.sub.n)
+    out["unstable_fraction"] = {"interval": unstable(ibp.inter_lo, ibp.inter_hi), "crown": unstable(lo, hi),
                                 "alpha_crown": unstable(alo, ahi)}
-    tr = synth.Instance(inst.name, inst.net, inst.x_lo, inst.x_hi, inst.spec, lo, hi, inst.sub, inst.cuts)
-    net_id, cs = ctx.load_instance(tr)
-    D = ctx.duals_create(net_id, cs, tr.sub, gcp.GCP_FP32)
-    _, cert, _ = ctx.optimize_batch(D, params)
+    net_i, cs_i = ctx.load_instance(ibp)
+    D = ctx.duals_create(net_i, cs_i, ibp.sub, gcp.GCP_FP32)
+    _, cert_ibp, _ = ctx.optimize_batch(D, params)
     ctx.duals_free(D)
-    out["mean_certified"] = {"interval_root_bounds": float(np.mean(cert_ibp)), "crown_root_bounds": float(np.mean(cert))}
-    # branch and bound from the root on these bounds: a few rounds of full batches
+    out["mean_certified"] = {"interval_root_bounds": float(np.mean(cert_ibp))}
+    # branch and bound from the root on the CROWN bounds: a few rounds of full batches
+    net_id, cs = ctx.load_instance(inst)
     pb = gcp.opt_params(20, gcp.GCP_ADAM, gcp.GCP_FP32, 1, 0.1, 0.02, 0.02, 0.98)
-    # children keep their parents' duals on the host: smaller batches for wide networks
     na = sum(inst.net.dims[1:-1]) * inst.spec.shape[0]
     batch = 1024 if na <= 50_000 else 64
     torch.cuda.synchronize()
@@ -396,40 +418,40 @@ def inter_bounds_bench(ctx, inst, params, cert_ibp):
     return out
 
 
-# --------------------------------------------------------------------------- GPU arm
-def main():
-    a = parse()
-    if a.impl == "reference":
-        return run_reference(a)
+def quality(cert, ref, K):
+    """Certified-bound quality of a form against a reference form on the same rows."""
+    import numpy as np
+    ok = cert >= ref - 1e-3 * np.maximum(1.0, np.abs(ref))
+    return {"mean_certified": float(np.mean(cert)),
+            "rows_certified_at_least_as_high": float(np.mean(ok)),
+            "rows_certified_at_least_as_high_tol": "1e-3 * max(1, |reference form's certified bound|)",
+            "subdomains_verified": float(np.mean(np.all(cert.reshape(-1, K) > 0, axis=1)))}
+
+
+def measure_workload(ctx, stream, dev, world, wname, prec_name, iters, n_sub, steps, warmup, flush,
+                     forms=("other",), timed_profile=True):
+    """Time one workload on CROWN root bounds computed by the library before
+    the timed region: device time of `steps` steps (L2 flushed, events on the
+    library's stream), the dominant kernel's per-launch time in a second pass,
+    the end-to-end rate through the C ABI from host buffers, and the other
+    forms of the same workload. Returns (the JSON fields, instance, certified
+    bounds)."""
     import numpy as np
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    from paper_2208_05740_gb300 import build, gcp, synth
-    build.build()
-    dev = local
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.Stream(device=dev)
-    prec = gcp.GCP_FP32 if a.prec == "fp32" else gcp.GCP_BF16
-    inst = WORKLOADS[a.workload]["build"](a.n_sub)
-    ctx = gcp.Context(dev)
-    ctx.set_stream(stream.cuda_stream)
+    from paper_2208_05740_gb300 import gcp
+    prec = gcp.GCP_FP32 if prec_name == "fp32" else gcp.GCP_BF16
+    inst = WORKLOADS[wname]["build"](n_sub, lambda net, lo, hi: ctx.intermediate_bounds(net.layers, lo, hi))
     net_id, cs = ctx.load_instance(inst)
-    params = gcp.opt_params(a.iters, gcp.GCP_ADAM, prec, 1, 0.1, 0.02, 0.02, 0.98)
+    params = gcp.opt_params(iters, gcp.GCP_ADAM, prec, 1, 0.1, 0.02, 0.02, 0.98)
     D = ctx.duals_create(net_id, cs, inst.sub, gcp.GCP_FP32)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")
+    K = inst.spec.shape[0]
 
     def step():
         ctx.duals_import(D)                       # default duals: same work every step
-        return ctx.optimize_batch(D, params)      # 100 iterations + final bound + FP64 certify
+        return ctx.optimize_batch(D, params)      # the ascent + final bound + FP64 certify
 
-    for _ in range(a.warmup):
-        bound, cert, err = step()
+    for _ in range(warmup):
+        step()
     # shares of every kernel in one untimed step, to pick the dominant one
     gcp.profile_start("*")
     step()
@@ -437,17 +459,11 @@ def main():
     gcp.profile_stop()
     dominant = max(rep, key=lambda k: rep[k][2])
     total_ms = sum(v[2] for v in rep.values())
-    if a.profile_all and rank == 0:
-        for k, v in sorted(rep.items(), key=lambda kv: -kv[1][2]):
-            print(f"# {k:28s} launches {v[0]:6d} ms {v[2]:9.3f} share {100 * v[2] / total_ms:5.1f}%", file=sys.stderr)
 
     def timed_steps(selector):
-        """K steps, L2 flushed before each, device time per step from events
-        on the launching stream; `selector` picks the kernels bracketed by
-        their own events (None = launches are only counted)."""
         gcp.profile_start(selector)
         ts = []
-        for _ in range(a.steps):
+        for _ in range(steps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -466,7 +482,7 @@ def main():
     # launches stops the second from overlapping the first one's tail
     # (programmatic dependent launch), so the step time is taken with the
     # launches only counted, and the dominant kernel's per-launch time in a
-    # second pass of the same K steps with each of its launches bracketed.
+    # second pass of the same steps with each of its launches bracketed.
     sampler = ClockSampler(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -476,7 +492,7 @@ def main():
     times_instr, _, _, (n_dom, ms_dom, fl_dom, by_dom) = timed_steps(dominant)
     clocks = sampler.stop()
     total_s = max_over_ranks(sum(times) / 1000.0, f"cuda:{dev}")
-    value = job_value(world, a.n_sub, a.steps, total_s)
+    value = job_value(world, n_sub, steps, total_s)
 
     # ---- end to end through the C ABI from host buffers
     sub = inst.sub
@@ -486,18 +502,16 @@ def main():
     h2d += (c.n + 1) * 4 + c.n * 12 + sum(d + 1 for d in inst.net.dims[:-1]) * 4 + nnz * (4 + 1 + 8 + 4 + 4 + 4)
     d2h = 3 * 8 * inst.n_rows
     e2e_t = []
-    for _ in range(a.steps):
+    for _ in range(steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         D2 = ctx.duals_create(net_id, cs, sub, gcp.GCP_FP32)
-        b2, c2, r2 = ctx.optimize_batch(D2, params)
+        ctx.optimize_batch(D2, params)
         ctx.duals_free(D2)
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = max_over_ranks(sum(e2e_t), f"cuda:{dev}")
-    e2e_value = job_value(world, a.n_sub, a.steps, e2e_s)
+    e2e_value = job_value(world, n_sub, steps, e2e_s)
 
-    if rank != 0:
-        return
     peaks, src = measured_peaks()
     bound_kind, peak, unit, note = kernel_peak(dominant, peaks, src)
     per_launch_ms = ms_dom / max(n_dom, 1)
@@ -506,31 +520,32 @@ def main():
     else:
         achieved = (by_dom / max(n_dom, 1)) / (per_launch_ms / 1e3) / 1e9
     lat = np.array(times)
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
-        "ms_per_step": float(np.mean(times)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if a.prec == "fp32" else "bf16", "data": "synthetic", "config": workload_config(a, world),
+    dtype = "f32" if prec_name == "fp32" else "bf16"
+    res = {
+        "value": value, "unit": UNIT, "steps": steps, "warmup": warmup, "ms_per_step": float(np.mean(times)),
+        "dtype": dtype, "config": workload_config(wname, n_sub, iters, prec_name, world),
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "bound": {"mean_certified": float(np.mean(cert)), "max_err_vs_fp64": float(np.max(err)),
-                  "max_rel_err_vs_fp64": float(np.max(err / np.maximum(1.0, np.abs(cert))))},
+                  "max_rel_err_vs_fp64": float(np.max(err / np.maximum(1.0, np.abs(cert)))),
+                  "subdomains_verified": float(np.mean(np.all(cert.reshape(-1, K) > 0, axis=1)))},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches_all),
         "roofline": {"kernel": dominant, "bound": bound_kind, "achieved": achieved, "peak": peak, "unit": unit,
-                     "frac": achieved / peak, "traffic": traffic_for(dominant, WORKLOADS[a.workload]["name"]),
+                     "frac": achieved / peak, "traffic": traffic_for(dominant, WORKLOADS[wname]["name"]),
                      "peak_source": note, "launches": int(n_dom), "ms_per_launch": per_launch_ms,
                      "share_of_step": rep[dominant][2] / total_ms,
-                     "timed_in": "second pass of the K timed steps, each launch of this kernel bracketed by events",
+                     "timed_in": "second pass of the timed steps, each launch of this kernel bracketed by events",
                      "ms_per_step_bracketed": float(np.mean(times_instr))},
         "clocks": clocks,
     }
-    def timed_form(pf):
+
+    def timed_form(pf, n_timed):
         """The same workload under other optimiser settings: steps timed like
         the headline's (L2 flushed, events on the library's stream)."""
-        for _ in range(2):
-            ctx.duals_import(D)
-            ctx.optimize_batch(D, pf)
+        ctx.duals_import(D)
+        ctx.optimize_batch(D, pf)
         tb = []
-        for _ in range(max(3, a.steps // 2)):
+        for _ in range(n_timed):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -541,33 +556,89 @@ def main():
             e1.synchronize()
             tb.append(e0.elapsed_time(e1))
         ms = float(np.mean(tb))
-        return {"value": a.n_sub * 1000.0 / ms, "mean_certified": float(np.mean(cert_f)), "ms_per_step": ms,
-                "max_err_vs_fp64": float(np.max(err_f)),
-                "rows_certified_at_least_as_high": float(np.mean(cert_f >= cert - 1e-6 * np.maximum(1, np.abs(cert))))}
+        out = {"value": n_sub * 1000.0 / ms, "ms_per_step": ms, "max_err_vs_fp64": float(np.max(err_f)),
+               "max_rel_err_vs_fp64": float(np.max(err_f / np.maximum(1.0, np.abs(cert_f))))}
+        out.update(quality(cert_f, cert, K))
+        out["quality_against"] = dtype
+        return out
 
-    forms = {line["dtype"]: {"value": value, "mean_certified": float(np.mean(cert)), "ms_per_step": float(np.mean(times))}}
-    if not a.no_bf16_form:
-        # the same workload with the BF16 chain (tensor-core bf16 GEMMs, FP32
-        # accumulation) and the same FP64 certification: throughput and the
-        # certified bound quality beside the FP32 chain's
-        other = "bf16" if prec == gcp.GCP_FP32 else "fp32"
-        forms[other] = timed_form(gcp.opt_params(a.iters, gcp.GCP_ADAM,
-                                                 gcp.GCP_BF16 if prec == gcp.GCP_FP32 else gcp.GCP_FP32, 1,
-                                                 0.1, 0.02, 0.02, 0.98))
-    if not a.no_opt_pi_form:
-        # the headline's chain with the ReLU duals pi optimised directly
+    fm = {dtype: dict(value=value, ms_per_step=res["ms_per_step"], **quality(cert, cert, K))}
+    n_form = max(3, min(steps, 5))
+    if "other" in forms:
+        # the same workload with the other chain precision (BF16 tensor-core
+        # chain with FP32 accumulation <-> FP32 chain) and the same FP64
+        # certification: throughput and certified-bound quality side by side
+        other = gcp.GCP_BF16 if prec == gcp.GCP_FP32 else gcp.GCP_FP32
+        fm["bf16" if prec == gcp.GCP_FP32 else "f32"] = timed_form(
+            gcp.opt_params(iters, gcp.GCP_ADAM, other, 1, 0.1, 0.02, 0.02, 0.98), n_form)
+    if "opt_pi" in forms:
+        # the workload's chain with the ReLU duals pi optimised directly
         # (opt_pi, App. A's closing remark) instead of Lemma A.1's closed form
-        forms[line["dtype"] + "_opt_pi"] = timed_form(gcp.opt_params(a.iters, gcp.GCP_ADAM, prec, 1, 0.1, 0.02, 0.02,
-                                                                     0.98, opt_pi=1))
-    if len(forms) > 1:
-        line["forms"] = forms
+        fm[dtype + "_opt_pi"] = timed_form(gcp.opt_params(iters, gcp.GCP_ADAM, prec, 1, 0.1, 0.02, 0.02, 0.98,
+                                                          opt_pi=1), n_form)
+    res["forms"] = fm
+    ctx.duals_free(D)
+    return res, inst, params
+
+
+def cpu_leg(wname, iters):
+    v, desc = oracle_sample(oracle_instance(wname, 64), WORKLOADS[wname]["sample"], iters)
+    return {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": desc + "; CROWN root bounds computed by the oracle"}
+
+
+# --------------------------------------------------------------------------- GPU arm
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_2208_05740_gb300 import build, gcp
+    build.build()
+    dev = local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = gcp.Context(dev)
+    ctx.set_stream(stream.cuda_stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")
+    forms = () if a.no_bf16_form else ("other",)
+    forms += () if a.no_opt_pi_form else ("opt_pi",)
+    head, inst, params = measure_workload(ctx, stream, dev, world, a.workload, a.prec, a.iters, a.n_sub, a.steps,
+                                          a.warmup, flush, forms)
+    # the largest single-GPU configuration (CNN, 4096 subdomains x 9 rows,
+    # 1000 cuts, 50 steps, BF16 chain + FP64 certify) beside the headline
+    extra = {}
+    if a.workload == "mlp" and not a.no_cnn:
+        w = WORKLOADS["cnn"]
+        extra["cnn"], _, _ = measure_workload(ctx, stream, dev, world, "cnn", w["prec"], w["iters"], w["n_sub"],
+                                              max(3, min(a.steps, 5)), a.warmup, flush, ("other",))
+    if rank != 0:
+        ctx.close()
+        return
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": head["dtype"], "data": "synthetic", "config": head["config"]}
+    for k in ("latency_ms", "bound", "e2e", "gpu_launches", "roofline", "clocks", "forms"):
+        line[k] = head[k]
+    if extra:
+        line["workloads"] = extra
     if world == 1 and not a.no_inter_bounds:
-        line["intermediate_bounds"] = inter_bounds_bench(ctx, inst, params, cert)
+        line["intermediate_bounds"] = inter_bounds_bench(ctx, a.workload, inst, params)
     if a.serve_requests > 0 and world == 1:
         line["serving"] = serving_bench(dev, a.serve_requests)
+        # below the measured service rate: latency once admitted, not the backlog
+        line["serving"]["below_capacity"] = serving_bench(dev, max(8, a.serve_requests // 2), rate=1.0)
     if world == 1 and not a.no_cpu_baseline:
-        v, desc = oracle_sample(inst, WORKLOADS[a.workload]["sample"], a.iters)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
+        line["cpu_baseline"] = cpu_leg(a.workload, a.iters)
+        for k, v in extra.items():
+            v["cpu_baseline"] = cpu_leg(k, v["config"]["iters"])
     print(json.dumps(line))
     ctx.close()
 
