@@ -429,7 +429,7 @@ def quality(cert, ref, K):
 
 
 def measure_workload(ctx, stream, dev, world, wname, prec_name, iters, n_sub, steps, warmup, flush,
-                     forms=("other",), timed_profile=True):
+                     forms=("other",), profile_all=False):
     """Time one workload on CROWN root bounds computed by the library before
     the timed region: device time of `steps` steps (L2 flushed, events on the
     library's stream), the dominant kernel's per-launch time in a second pass,
@@ -459,6 +459,10 @@ def measure_workload(ctx, stream, dev, world, wname, prec_name, iters, n_sub, st
     gcp.profile_stop()
     dominant = max(rep, key=lambda k: rep[k][2])
     total_ms = sum(v[2] for v in rep.values())
+    if profile_all:
+        for k, v in sorted(rep.items(), key=lambda kv: -kv[1][2]):
+            print(f"# {wname} {k:28s} launches {v[0]:6d} ms {v[2]:9.3f} share {100 * v[2] / total_ms:5.1f}%",
+                  file=sys.stderr)
 
     def timed_steps(selector):
         gcp.profile_start(selector)
@@ -611,14 +615,14 @@ def main():
     forms = () if a.no_bf16_form else ("other",)
     forms += () if a.no_opt_pi_form else ("opt_pi",)
     head, inst, params = measure_workload(ctx, stream, dev, world, a.workload, a.prec, a.iters, a.n_sub, a.steps,
-                                          a.warmup, flush, forms)
+                                          a.warmup, flush, forms, a.profile_all)
     # the largest single-GPU configuration (CNN, 4096 subdomains x 9 rows,
     # 1000 cuts, 50 steps, BF16 chain + FP64 certify) beside the headline
     extra = {}
     if a.workload == "mlp" and not a.no_cnn:
         w = WORKLOADS["cnn"]
         extra["cnn"], _, _ = measure_workload(ctx, stream, dev, world, "cnn", w["prec"], w["iters"], w["n_sub"],
-                                              max(3, min(a.steps, 5)), a.warmup, flush, ("other",))
+                                              max(3, min(a.steps, 5)), a.warmup, flush, ("other",), a.profile_all)
     if rank != 0:
         ctx.close()
         return
