@@ -409,12 +409,16 @@ def inter_bounds_bench(ctx, wname, inst, params):
     pb = gcp.opt_params(20, gcp.GCP_ADAM, gcp.GCP_FP32, 1, 0.1, 0.02, 0.02, 0.98)
     na = sum(inst.net.dims[1:-1]) * inst.spec.shape[0]
     batch = 1024 if na <= 50_000 else 64
-    torch.cuda.synchronize()
-    r = ctx.bab_verify(net_id, cs, pb, batch=batch, max_rounds=12)
-    out["bab"] = {"batch": batch, "iters_per_round": 20, "rounds": r["rounds"], "domains_bounded": r["domains_bounded"],
-                  "domains_verified": r["domains_verified"], "domains_left": r["domains_left"],
-                  "verified": r["verified"], "min_bound": r["min_bound"], "time_s": r["time_ms"] / 1e3,
-                  "domains_per_s": r["domains_bounded"] / max(r["time_ms"] / 1e3, 1e-9)}
+    out["bab"] = {}
+    for rule, name in ((0, "by_duals"), (1, "static_intercept")):
+        ctx.bab_verify(net_id, cs, pb, batch=batch, max_rounds=2, branching=rule)   # warm
+        torch.cuda.synchronize()
+        r = ctx.bab_verify(net_id, cs, pb, batch=batch, max_rounds=12, branching=rule)
+        out["bab"][name] = {"batch": batch, "iters_per_round": 20, "rounds": r["rounds"],
+                            "domains_bounded": r["domains_bounded"], "domains_verified": r["domains_verified"],
+                            "domains_left": r["domains_left"], "verified": r["verified"], "min_bound": r["min_bound"],
+                            "time_s": r["time_ms"] / 1e3,
+                            "domains_per_s": r["domains_bounded"] / max(r["time_ms"] / 1e3, 1e-9)}
     return out
 
 

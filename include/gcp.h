@@ -236,6 +236,20 @@ GCP_API gcp_status gcp_grad_batch(gcp_ctx* ctx, void* duals, int32_t prec, doubl
 GCP_API gcp_status gcp_optimize_batch(gcp_ctx* ctx, void* duals, const gcp_opt_params* p,
                                       double* out_bound, double* out_certified, double* out_err_vs_fp64);
 
+/* The branching neuron of every subdomain of a batch at its current duals,
+ * for a branch-and-bound loop (Sec. 3.2, App. B: a subdomain that is not
+ * verified is split on one more unstable ReLU). One evaluation in chain `prec`
+ * (GCP_FP32 or GCP_BF16; float duals) gives nuhat; over the root-unstable
+ * neurons the subdomain has not split, the pick maximises
+ * w_j * sum over the subdomain's spec rows of [nuhat_j]_+ with
+ * w_j = -l_j u_j / (u_j - l_j): the part of the bound that the triangle
+ * relaxation's intercept costs at neuron j (without cuts Lemma A.1 gives
+ * pi* = u C / (u - l) and the term l pi* = -w_j C, C = [nuhat]_+), which a
+ * split removes -- the intercept score of BaBSR (Bunel et al., 2020). Ties go
+ * to the lower layer, then the lower index. layer[n_sub], index[n_sub]
+ * (host) receive the pick, or -1 when every score is zero. */
+GCP_API gcp_status gcp_branch_picks(gcp_ctx* ctx, void* duals, int32_t prec, int32_t* layer, int32_t* index);
+
 /* Root intermediate bounds l, u of every hidden pre-activation (the sound
  * bounds Sec. 2 assumes, used by gcp_init_net), computed by this library's own
  * bound propagation, layer by layer. Hidden layer 1: the interval image of the
@@ -277,10 +291,13 @@ GCP_API gcp_status gcp_intermediate_bounds_cuts(gcp_ctx* ctx, const gcp_layer_de
  * `batch` pending subdomains in one batch (p->iters ascent steps, then the FP64
  * certification; p->certify is forced on); when more are pending, the easiest
  * ones (largest lower bound) go first, the order of Sec. 3.2. A subdomain whose
- * certified bounds are all positive is verified; any other is split on its not
+ * certified bounds are all positive is verified; any other is split into the
+ * x >= 0 and x <= 0 children of one more neuron, which start from the
+ * parent's duals. branching = 0 picks the neuron by its duals at the end of
+ * the round (gcp_branch_picks' score, from the round's last evaluation; the
+ * static order below where every score is zero); branching = 1 takes the not
  * yet split root-unstable neuron with the largest relaxation intercept
- * -l u / (u - l) into the x >= 0 and x <= 0 children, which start from the
- * parent's duals. Cuts (cutset_id >= 0) hold in every subdomain (they are valid
+ * -l u / (u - l) (a static order). Cuts (cutset_id >= 0) hold in every subdomain (they are valid
  * at the root). Stops when nothing is pending (verified = 1), after
  * max_rounds rounds, when more than max_domains subdomains are pending, after
  * timeout_s seconds, or when a subdomain with every root-unstable neuron split
@@ -293,6 +310,7 @@ typedef struct {
   int64_t max_domains;
   double timeout_s;      /* <= 0: none */
   gcp_opt_params p;
+  int32_t branching;     /* 0: by the duals (gcp_branch_picks), 1: static root intercept */
 } gcp_bab_params;
 typedef struct {
   int32_t verified;

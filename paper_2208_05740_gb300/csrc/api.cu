@@ -1291,7 +1291,7 @@ gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, 
     b.recompute_decided = true;
   }
   // nuhat per layer only where the adjoint will read it; otherwise one scratch row block
-  const bool keep = with_adjoint_start && !b.recompute;
+  const bool keep = (with_adjoint_start || b.keep_nuhat) && !b.recompute;
   int poff = 0;
   for (int i = L - 1; i >= 1; --i) {
     T* nuhat = keep ? (T*)b.ws("nuhat" + std::to_string(i), (size_t)R * net.dims[i] * sizeof(T), &s)
@@ -1802,6 +1802,27 @@ gcp_status optimize_on(Ctx& c, Batch& b, const gcp_opt_params& p, cudaStream_t s
   return s;
 }
 
+gcp_status branch_picks_from_last_eval(Ctx& c, Batch& b, cudaStream_t st, int32_t* picks_dev) {
+  const Net& net = *b.net;
+  if (b.fp64 || b.recompute) return c.fail(GCP_EINVAL, "branching score: needs float duals with stored nuhat");
+  std::vector<ScoreLayer> ls;
+  for (int i = 1; i < net.L; ++i) {
+    auto it = b.lazy.find("nuhat" + std::to_string(i));
+    if (it == b.lazy.end()) return c.fail(GCP_EINVAL, "branching score: layer %d's nuhat was not kept", i);
+    ls.push_back(ScoreLayer{(const float*)it->second, net.lo32[i - 1], net.hi32[i - 1], net.dims[i], i});
+  }
+  if (ls.empty() || b.S == 0) return GCP_OK;
+  gcp_status s = GCP_OK;
+  ScoreLayer* ld = (ScoreLayer*)b.ws("score_layers", ls.size() * sizeof(ScoreLayer), &s);
+  if (!ld) return s;
+  cudaError_t e = cudaMemcpyAsync(ld, ls.data(), ls.size() * sizeof(ScoreLayer), cudaMemcpyHostToDevice, st);
+  if (e) return c.cuda(e, "branching score layers");
+  bab_branch_score(st, b.S, b.K, (int)ls.size(), ld, b.sp_tab, b.M, picks_dev);
+  e = cudaStreamSynchronize(st);   // ls is read by the copy above
+  if (e) return c.cuda(e, "branching score");
+  return launch_status(c, "branching score");
+}
+
 gcp_status optimize_batch(Ctx& c, Batch& b, const gcp_opt_params* p, double* out_bound, double* out_cert,
                           double* out_err) {
   if (!p) return c.fail(GCP_EINVAL, "null params");
@@ -2295,6 +2316,35 @@ gcp_status gcp_grad_batch(gcp_ctx* h, void* duals, int32_t prec, double* out_bou
   gcp::Batch* b = find_batch(c, duals);
   if (!b) return c->fail(GCP_ENOTFOUND, "unknown duals");
   return gcp::grad_batch(*c, *b, prec, out_bound, ga, gb, gg);
+}
+
+gcp_status gcp_branch_picks(gcp_ctx* h, void* duals, int32_t prec, int32_t* layer, int32_t* index) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  CTX_GUARD(c);
+  gcp::Batch* b = find_batch(c, duals);
+  if (!b) return c->fail(GCP_ENOTFOUND, "unknown duals");
+  if (!layer || !index) return c->fail(GCP_EINVAL, "gcp_branch_picks: null output");
+  if (prec != GCP_FP32 && prec != GCP_BF16) return c->fail(GCP_EINVAL, "gcp_branch_picks: FP32 or BF16 chain");
+  if (b->fp64) return c->fail(GCP_EINVAL, "gcp_branch_picks: needs GCP_FP32 duals");
+  gcp_status s0 = gcp::check_prec(*c, *b, prec);
+  if (s0) return s0;
+  if (b->S == 0) return GCP_OK;
+  gcp_status s = GCP_OK;
+  int32_t* pd = (int32_t*)b->ws("picks", (size_t)b->S * 4, &s);
+  if (!pd) return s;
+  b->keep_nuhat = true;
+  s = gcp::eval_dispatch(*c, *b, c->stream, prec, false, nullptr, false);
+  b->keep_nuhat = false;
+  if (s == GCP_OK) s = gcp::branch_picks_from_last_eval(*c, *b, c->stream, pd);
+  if (s) return s;
+  std::vector<int32_t> h_picks((size_t)b->S);
+  cudaError_t e = cudaMemcpy(h_picks.data(), pd, (size_t)b->S * 4, cudaMemcpyDeviceToHost);
+  if (e) return c->cuda(e, "gcp_branch_picks");
+  for (int q = 0; q < b->S; ++q) {
+    layer[q] = h_picks[q] < 0 ? -1 : (h_picks[q] >> 24);
+    index[q] = h_picks[q] < 0 ? -1 : (h_picks[q] & 0xffffff);
+  }
+  return GCP_OK;
 }
 
 gcp_status gcp_optimize_batch(gcp_ctx* h, void* duals, const gcp_opt_params* p, double* out_bound,

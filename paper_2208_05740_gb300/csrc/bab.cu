@@ -8,8 +8,11 @@
 // in one batch (ascent steps, then the FP64 certification); when more are
 // pending, the easiest ones, with the largest lower bounds, go first (the
 // order the paper uses so that cuts arriving later meet the hard domains).
-// The branching neuron of a subdomain is its not yet split root-unstable
-// neuron with the largest relaxation intercept -l u / (u - l).
+// The branching neuron of a subdomain is chosen from its duals at the end of
+// its round: the largest intercept cost w_j * sum_k [nuhat_j]_+ over its
+// unsplit root-unstable neurons (BaBSR's score; kernel bab_branch_score),
+// or, by request or where every score is zero, its not yet split
+// root-unstable neuron with the largest relaxation intercept -l u / (u - l).
 //
 // Label by label (the same section): every spec row (target label) is
 // bounded at the root, and the rows not yet positive get a branch and bound
@@ -171,7 +174,19 @@ gcp_status bab_verify(Ctx& c, int net_id, int cutset_id, const gcp_bab_params& b
       }
     }
     std::vector<double> cert((size_t)R);
+    // branching by the duals: the round's last evaluation keeps nuhat for the score
+    const bool by_duals = bp.branching == 0 && p.prec != GCP_FP64 && !b->fp64;
+    b->keep_nuhat = by_duals;
     if (s == GCP_OK) s = optimize_batch(c, *b, &p, nullptr, cert.data(), nullptr);
+    std::vector<int32_t> picks;
+    if (s == GCP_OK && by_duals && !b->recompute) {
+      int32_t* pd = (int32_t*)b->ws("bab_picks", n * 4, &s);
+      if (pd) s = branch_picks_from_last_eval(c, *b, c.stream, pd);
+      if (s == GCP_OK) {
+        picks.resize(n);
+        s = c.cuda(cudaMemcpy(picks.data(), pd, n * 4, cudaMemcpyDeviceToHost), "branch and bound: picks");
+      }
+    }
     // the subdomains that branch keep their rows of this round's duals on the
     // device for their children (only those rows, gathered by runs of
     // consecutive branching subdomains); if the store cannot be allocated the
@@ -242,15 +257,19 @@ gcp_status bab_verify(Ctx& c, int net_id, int cutset_id, const gcp_bab_params& b
         res.min_bound = std::min(res.min_bound, m);
         continue;
       }
-      // branch: the first candidate not split in this domain
+      // branch: the duals' pick (never a neuron already split here), else
+      // the first candidate of the static order not split in this domain
       const Cand* pick = nullptr;
-      for (const Cand& cd : cand) {
+      Cand dual_pick{};
+      if (!picks.empty() && picks[q] >= 0) {
+        dual_pick = Cand{0.0, (int16_t)(picks[q] >> 24), picks[q] & 0xffffff};
+        pick = &dual_pick;
+      }
+      for (size_t ci = 0; ci < cand.size() && !pick; ++ci) {
+        const Cand& cd = cand[ci];
         bool dup = false;
         for (size_t e = 0; e < d.lay.size() && !dup; ++e) dup = d.lay[e] == cd.layer && d.idx[e] == cd.index;
-        if (!dup) {
-          pick = &cd;
-          break;
-        }
+        if (!dup) pick = &cd;
       }
       if (!pick) {   // every root-unstable neuron is split: nothing left to refine
         undecided = true;

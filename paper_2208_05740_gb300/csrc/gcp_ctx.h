@@ -110,6 +110,9 @@ struct Batch {
   // the adjoint recomputes each layer's nuhat from the top instead of reading
   // it stored by the evaluation (decided at the first adjoint evaluation)
   bool recompute = false, recompute_decided = false;
+  // every evaluation keeps each layer's nuhat (as the adjoint's evaluations
+  // do), for the branching score of branch and bound
+  bool keep_nuhat = false;
   CutDev cuts;
   int32_t* sp_ptr = nullptr;
   int16_t* sp_layer = nullptr;
@@ -190,6 +193,10 @@ gcp_status add_cuts(Ctx& c, int net_id, int n_cuts, const int64_t* row_ptr, cons
 gcp_status optimize_batch(Ctx& c, Batch& b, const gcp_opt_params* p, double* out_bound, double* out_cert,
                           double* out_err);
 gcp_status duals_create(Ctx& c, int net_id, int cutset_id, const gcp_subdomains* sub, int dual_prec, Batch** out);
+// Branching picks (layer << 24 | index, or -1) of every subdomain from the
+// nuhat the batch's last evaluation kept (keep_nuhat, float duals): S values
+// into picks_dev, enqueued on st.
+gcp_status branch_picks_from_last_eval(Ctx& c, Batch& b, cudaStream_t st, int32_t* picks_dev);
 gcp_status duals_create_parts(Ctx& c, int net_id,
                               const std::vector<std::pair<const CutSet*, const gcp_subdomains*>>& parts,
                               int dual_prec, Batch** out);

@@ -313,6 +313,21 @@ struct WarmSrc {
 };
 void bab_warm_start(cudaStream_t st, int64_t R, int n_layers, const int* dims_dev, float* const* alpha_dev, int64_t na,
                     float* beta, int M, float* gamma, int N, const WarmSrc* src);
+// Branching neuron of every subdomain from its current duals: over the
+// root-unstable neurons the subdomain has not split, the largest
+// w_j * sum_k [nuhat_j]_+ (rows k of the subdomain) with w_j = -l_j u_j / (u_j - l_j):
+// the part of the bound that the triangle relaxation's intercept costs at
+// neuron j (Lemma A.1 without cuts: pi* = u C / (u - l), h = l pi* = -w_j C with
+// C = [nuhat]_+), which a split of j removes. Ties go to the lower layer, then
+// the lower index. picks[s] = layer << 24 | index, or -1 when every score is 0.
+struct ScoreLayer {
+  const float* nuhat;   // [R, d] of the batch's last evaluation
+  const float* lo;      // root bounds [d]
+  const float* hi;
+  int d, layer;
+};
+void bab_branch_score(cudaStream_t st, int S, int K, int n_layers, const ScoreLayer* layers_dev,
+                      const int32_t* sp_tab, int M, int32_t* picks);
 
 // tcgen05 GEMMs (k_tc.cu); false = shape or driver not supported, use SIMT
 bool tc_available(int K, bool bf16);

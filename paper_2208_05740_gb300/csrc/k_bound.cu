@@ -1322,7 +1322,16 @@ const char* tsfx() { return sizeof(T) == 8 ? "f64" : "f32"; }
 // on layers whose width is a multiple of 4, else 1.
 template <typename T>
 inline bool span_v4(int d) { return sizeof(T) == 4 && d % 4 == 0; }
-inline int row_split(int) { return 1; }   // one warp takes all K rows of its subdomain
+// A warp takes all K rows of its subdomain span, its setup (bounds, split
+// hits, cut entries) shared by the rows; a launch that would then leave the
+// GPU mostly idle (a small batch, where one warp's K rows in sequence are the
+// kernel's latency) spreads each span's rows over gridDim.z warps instead,
+// enough to bring the launch near 8 warps per SM.
+inline int row_split(int64_t S, int K, int spans) {
+  const int64_t warps = S * spans, target = 152 * 8;
+  if (warps >= target || K <= 1) return 1;
+  return (int)std::min<int64_t>(K, (target + warps - 1) / warps);
+}
 inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 // Launch a span kernel with its dynamic shared memory (the opt-in above 48 KB
@@ -1338,8 +1347,8 @@ void launch_span(Kern kern, size_t smem, dim3 grid, cudaStream_t st, const Args&
 }
 inline dim3 span_blocks(int64_t R, int K, int d, int V) {
   const int64_t S = R / K;
-  return dim3((unsigned)((S + kSpanWarps - 1) / kSpanWarps), (unsigned)((d + 32 * V - 1) / (32 * V)),
-              (unsigned)row_split(K));
+  const int spans = (d + 32 * V - 1) / (32 * V);
+  return dim3((unsigned)((S + kSpanWarps - 1) / kSpanWarps), (unsigned)spans, (unsigned)row_split(S, K, spans));
 }
 
 // host-side extent checks shared by the launchers

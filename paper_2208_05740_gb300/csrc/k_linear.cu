@@ -447,6 +447,91 @@ void bab_warm_start(cudaStream_t st, int64_t R, int n_layers, const int* dims_de
   prof_end(st, tk);
 }
 
+// ---------------------------------------------------------------- branch and bound: branching score
+namespace {
+// a beats b: larger score, then lower layer, then lower index
+__device__ __forceinline__ bool score_better(float sa, int la, int ja, float sb, int lb, int jb) {
+  if (sa != sb) return sa > sb;
+  if (la != lb) return la < lb;
+  return ja < jb;
+}
+constexpr int kScoreThreads = 256;
+__global__ void __launch_bounds__(kScoreThreads) k_bab_score(int S, int K, int n_layers,
+                                                             const ScoreLayer* __restrict__ layers,
+                                                             const int32_t* __restrict__ sp_tab, int M,
+                                                             int32_t* __restrict__ picks) {
+  __shared__ int32_t codes[kMaxSplits];
+  __shared__ float ws[kScoreThreads / 32];
+  __shared__ int wl[kScoreThreads / 32], wj[kScoreThreads / 32];
+  for (int q = blockIdx.x; q < S; q += gridDim.x) {
+    const int nm = M < kMaxSplits ? M : kMaxSplits;
+    __syncthreads();
+    for (int m = threadIdx.x; m < nm; m += blockDim.x) codes[m] = sp_tab[(int64_t)q * M + m];
+    __syncthreads();
+    float best = 0.f;
+    int bl = 1 << 30, bj = 1 << 30;
+    for (int l = 0; l < n_layers; ++l) {
+      const ScoreLayer L = layers[l];
+      for (int j = threadIdx.x; j < L.d; j += blockDim.x) {
+        const float lo = L.lo[j], hi = L.hi[j];
+        if (!(lo < 0.f && hi > 0.f)) continue;
+        bool split = false;
+        for (int m = 0; m < nm; ++m) {
+          const int c = codes[m];
+          split |= c >= 0 && (c >> 24) == L.layer && (c & 0x7fffff) == j;
+        }
+        if (split) continue;
+        float cs = 0.f;
+        for (int k = 0; k < K; ++k) cs += fmaxf(L.nuhat[((int64_t)q * K + k) * L.d + j], 0.f);
+        const float sc = (-lo * hi / (hi - lo)) * cs;
+        if (sc > 0.f && score_better(sc, L.layer, j, best, bl, bj)) {
+          best = sc;
+          bl = L.layer;
+          bj = j;
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float s2 = __shfl_down_sync(0xffffffffu, best, o);
+      const int l2 = __shfl_down_sync(0xffffffffu, bl, o), j2 = __shfl_down_sync(0xffffffffu, bj, o);
+      if (score_better(s2, l2, j2, best, bl, bj)) {
+        best = s2;
+        bl = l2;
+        bj = j2;
+      }
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+      ws[w] = best;
+      wl[w] = bl;
+      wj[w] = bj;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int v = 1; v < kScoreThreads / 32; ++v)
+        if (score_better(ws[v], wl[v], wj[v], best, bl, bj)) {
+          best = ws[v];
+          bl = wl[v];
+          bj = wj[v];
+        }
+      picks[q] = best > 0.f ? (bl << 24) | bj : -1;
+    }
+  }
+}
+}  // namespace
+
+void bab_branch_score(cudaStream_t st, int S, int K, int n_layers, const ScoreLayer* layers_dev,
+                      const int32_t* sp_tab, int M, int32_t* picks) {
+  if (S <= 0) return;
+  if (!(reg_check(layers_dev, n_layers * (double)sizeof(ScoreLayer), "score layers") &
+        reg_check(sp_tab, (double)S * (M > 0 ? M : 1) * 4.0, "split table") & reg_check(picks, S * 4.0, "picks")))
+    return;
+  int tk = prof_begin(st, "bab_branch_score", 0.0, 0.0);
+  k_bab_score<<<(unsigned)std::min(S, 152 * 8), kScoreThreads, 0, st>>>(S, K, n_layers, layers_dev, sp_tab, M,
+                                                                         picks);
+  prof_end(st, tk);
+}
+
 template void skip_add<double, double>(cudaStream_t, int64_t, int, int, int, const double*, int, double*);
 template void skip_add<float, float>(cudaStream_t, int64_t, int, int, int, const float*, int, float*);
 template void skip_add<__nv_bfloat16, float>(cudaStream_t, int64_t, int, int, int, const __nv_bfloat16*, int, float*);

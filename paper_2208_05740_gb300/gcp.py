@@ -27,6 +27,7 @@ EXPORTED = ["gcp_create", "gcp_destroy", "gcp_last_error", "gcp_set_stream", "gc
             "gcp_intermediate_bounds", "gcp_intermediate_bounds_cuts", "gcp_bab_verify", "gcp_bab_verify_labels",
             "gcp_add_cuts", "gcp_duals_create", "gcp_duals_create_multi", "gcp_duals_shape", "gcp_duals_export", "gcp_duals_import",
             "gcp_duals_free", "gcp_duals_theta", "gcp_bound_batch", "gcp_grad_batch", "gcp_optimize_batch", "gcp_bound_device",
+            "gcp_branch_picks",
             "gcp_grad_device", "gcp_bound_dense_noalloc", "gcp_selftest_gemm", "gcp_selftest_gemm_f64", "gcp_profile_start", "gcp_profile_stop", "gcp_profile_query", "gcp_profile_report",
             "gcp_serve_start", "gcp_serve_submit", "gcp_serve_poll", "gcp_serve_wait",
             "gcp_serve_final", "gcp_serve_stop"]
@@ -62,7 +63,7 @@ class OptParams(C.Structure):
 
 class BabParams(C.Structure):
     _fields_ = [("batch", C.c_int32), ("max_rounds", C.c_int32), ("max_domains", C.c_int64),
-                ("timeout_s", C.c_double), ("p", OptParams)]
+                ("timeout_s", C.c_double), ("p", OptParams), ("branching", C.c_int32)]
 
 
 class BabResult(C.Structure):
@@ -119,6 +120,7 @@ def lib():
             "gcp_duals_theta": [P, P, pd, pd],
             "gcp_bound_batch": [P, P, I32, I32, pd, pd],
             "gcp_grad_batch": [P, P, I32, pd, pd, pd, pd],
+            "gcp_branch_picks": [P, P, I32, C.POINTER(I32), C.POINTER(I32)],
             "gcp_optimize_batch": [P, P, C.POINTER(OptParams), pd, pd, pd],
             "gcp_intermediate_bounds": [P, C.POINTER(LayerDesc), I32, pd, pd, C.POINTER(OptParams), pd, pd],
             "gcp_intermediate_bounds_cuts": [P, C.POINTER(LayerDesc), I32, pd, pd, C.POINTER(OptParams), I32,
@@ -302,19 +304,20 @@ class Context:
         return out_lo, out_hi
 
     def bab_verify(self, net_id: int, cutset_id: int, params: OptParams, batch: int = 256, max_rounds: int = 100,
-                   max_domains: int = 1 << 16, timeout_s: float = 0.0) -> dict:
-        """Branch and bound over ReLU splits: is every spec row positive over the box?"""
-        bp = BabParams(batch, max_rounds, max_domains, timeout_s, params)
+                   max_domains: int = 1 << 16, timeout_s: float = 0.0, branching: int = 0) -> dict:
+        """Branch and bound over ReLU splits: is every spec row positive over the box?
+        branching 0: by the duals (gcp_branch_picks' score), 1: static root intercept."""
+        bp = BabParams(batch, max_rounds, max_domains, timeout_s, params, branching)
         r = BabResult()
         self._check(lib().gcp_bab_verify(self.h, net_id, cutset_id, C.byref(bp), C.byref(r)))
         return {f: getattr(r, f) for f, _ in BabResult._fields_}
 
     def bab_verify_labels(self, net_id: int, cutset_id: int, n_spec: int, params: OptParams, batch: int = 256,
                           max_rounds: int = 100, max_domains: int = 1 << 16, timeout_s: float = 0.0,
-                          stop_at_failure: bool = False):
+                          stop_at_failure: bool = False, branching: int = 0):
         """Branch and bound label by label, the easiest first: (result dict,
         order of the labels, per-label 1 proved / 0 not / -1 not attempted)."""
-        bp = BabParams(batch, max_rounds, max_domains, timeout_s, params)
+        bp = BabParams(batch, max_rounds, max_domains, timeout_s, params, branching)
         r = BabResult()
         order = np.zeros(n_spec, np.int32)
         ver = np.zeros(n_spec, np.int32)
@@ -407,6 +410,14 @@ class Context:
         self._check(lib().gcp_grad_batch(self.h, D.handle, prec, _ptr(out, C.c_double), _ptr(ga, C.c_double),
                                          _ptr(gb, C.c_double), _ptr(gg, C.c_double)))
         return out, ga, gb, gg
+
+    def branch_picks(self, D: Duals, prec: int, n_sub: int):
+        """The branching neuron (layer, index; -1 for none) of each of the batch's n_sub subdomains."""
+        S = n_sub
+        lay = np.zeros(max(S, 1), np.int32)
+        idx = np.zeros(max(S, 1), np.int32)
+        self._check(lib().gcp_branch_picks(self.h, D.handle, prec, _ptr(lay, C.c_int32), _ptr(idx, C.c_int32)))
+        return lay[:S], idx[:S]
 
     def optimize_batch(self, D: Duals, params: OptParams):
         out = np.zeros(D.rows)

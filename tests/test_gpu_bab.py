@@ -82,11 +82,12 @@ def test_bab_with_cuts(ctx):
     d_valid = O.valid_cut_offsets(P)   # MIP-valid offsets: the cuts hold at every feasible point
     inst = dataclasses.replace(inst, cuts=dataclasses.replace(cuts, d=d_valid))
     net_id, cs = _load(ctx, inst)
-    r = ctx.bab_verify(net_id, cs, gcp.opt_params(**PARAMS), batch=64, max_rounds=400)
+    # the static branching order: the same tree with and without the cuts
+    r = ctx.bab_verify(net_id, cs, gcp.opt_params(**PARAMS), batch=64, max_rounds=400, branching=1)
     assert r["verified"] == 1, r
     plain = _shifted(0.05)
     n0, _ = _load(ctx, plain)
-    r0 = ctx.bab_verify(n0, -1, gcp.opt_params(**PARAMS), batch=64, max_rounds=400)
+    r0 = ctx.bab_verify(n0, -1, gcp.opt_params(**PARAMS), batch=64, max_rounds=400, branching=1)
     assert r0["verified"] == 1 and r["domains_bounded"] <= r0["domains_bounded"], (r, r0)
 
 
@@ -147,3 +148,69 @@ def test_bab_label_by_label_easiest_first(ctx):
     n2, c2 = _load(ctx, proved)
     r3, _, ver3 = ctx.bab_verify_labels(n2, c2, 2, p, batch=64, max_rounds=400, max_domains=1 << 15)
     assert list(ver3) == [1, 1] and r3["verified"] == 1 and r3["min_bound"] > 0
+
+
+def _oracle_scores(inst, A, B, G):
+    """The branching score of every (subdomain, layer, neuron) from the oracle's
+    nuhat at the given duals: w_j * sum_k [nuhat_j]_+ over the subdomain's rows,
+    w_j = -l u / (u - l) on root-unstable neurons the subdomain has not split."""
+    from tests.helpers import oracle_duals
+    P = O.build_problem(inst)
+    _, T = O.evaluate(P, oracle_duals(inst, A, B[:, :P.max_splits], G), trace=True)
+    K = inst.spec.shape[0]
+    S = inst.sub.n
+    out = []
+    for s in range(S):
+        split = {(int(inst.sub.layer[e]), int(inst.sub.index[e])) for e in range(inst.sub.ptr[s], inst.sub.ptr[s + 1])}
+        sc = {}
+        for i, (lo, hi) in enumerate(zip(inst.inter_lo, inst.inter_hi), start=1):
+            nh = T.nu_hat[i - 1][s * K:(s + 1) * K]
+            w = np.where((lo < 0) & (hi > 0), -lo * hi / np.where(hi - lo > 0, hi - lo, 1.0), 0.0)
+            tot = w * np.maximum(nh, 0.0).sum(axis=0)
+            for j in np.nonzero(tot > 0)[0]:
+                if (i, int(j)) not in split:
+                    sc[(i, int(j))] = float(tot[j])
+        out.append(sc)
+    return out
+
+
+@pytest.mark.parametrize("prec", [gcp.GCP_FP32, gcp.GCP_BF16])
+def test_branch_picks_maximise_the_oracle_score(ctx, prec):
+    """gcp_branch_picks: for every subdomain the pick's score (computed by the
+    oracle) is the largest up to the chain's tolerance, is never a split
+    neuron, and is the oracle's argmax wherever the best two are apart."""
+    inst = synth.mlp_256x6(n_sub=24, n_cuts=30)
+    net_id, cs = ctx.load_instance(inst)
+    D = ctx.duals_create(net_id, cs, inst.sub, gcp.GCP_FP32)
+    ctx.optimize_batch(D, gcp.opt_params(10, gcp.GCP_ADAM, gcp.GCP_FP32, 0, 0.1, 0.02, 0.02, 0.98))
+    A, B, G = ctx.duals_export(D)
+    lay, idx = ctx.branch_picks(D, prec, inst.sub.n)
+    ctx.duals_free(D)
+    scores = _oracle_scores(inst, A, B, G)
+    tol = 1e-5 if prec == gcp.GCP_FP32 else 1e-3
+    exact = 0
+    for s, sc in enumerate(scores):
+        if not sc:
+            assert lay[s] == -1
+            continue
+        best = max(sc.values())
+        got = sc.get((int(lay[s]), int(idx[s])))
+        assert got is not None, (s, lay[s], idx[s])          # an unsplit root-unstable neuron with a score
+        assert got >= best * (1 - 10 * tol), (s, got, best)
+        top = sorted(sc.values(), reverse=True)
+        if len(top) == 1 or top[0] > top[1] * (1 + 100 * tol):
+            assert got == best
+            exact += 1
+    if prec == gcp.GCP_FP32:
+        assert exact >= len(scores) // 2
+
+
+@pytest.mark.parametrize("margin", [0.05, -0.05])
+def test_bab_branching_by_duals_and_static_order_agree_on_verdicts(ctx, margin):
+    inst = _shifted(margin)
+    net_id, cs = _load(ctx, inst)
+    rd = ctx.bab_verify(net_id, cs, gcp.opt_params(**PARAMS), batch=64, max_rounds=400, max_domains=1 << 15,
+                        branching=0)
+    rs = ctx.bab_verify(net_id, cs, gcp.opt_params(**PARAMS), batch=64, max_rounds=400, max_domains=1 << 15,
+                        branching=1)
+    assert rd["verified"] == rs["verified"] == (1 if margin > 0 else 0), (rd, rs)
