@@ -458,8 +458,12 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
       if (!pf.empty()) UP(cf16, __nv_bfloat16, pf.data(), pf.size());
       auto pt = pack(true, ctk, ctn, g);
       if (!pt.empty()) UP(ct16, __nv_bfloat16, pt.data(), pt.size());
+      // the three-term transposed product on the tensor cores; a map of fewer
+      // than 8 output channels (an input layer's c_in) fills at most 8 of a
+      // tile's 16 columns while its producers stage three times the source
+      // channels: it runs in float on the SIMT units instead
       const LayerGeom g3 = split_geom(g);
-      auto p3 = pack(true, ct3k, ct3n, g3);
+      auto p3 = g.c_in >= 8 ? pack(true, ct3k, ct3n, g3) : std::vector<__nv_bfloat16>();
       if (!p3.empty() && conv_tc_fits(g3, 1, ct3k, ct3n)) UP(ct16x3, __nv_bfloat16, p3.data(), p3.size());
     } else if (tc_available(kTerms * g.d_out, true)) {
       // rows of [W_hi^T | W_hi^T | W_lo^T] for the three-term operand [hi | lo | hi]

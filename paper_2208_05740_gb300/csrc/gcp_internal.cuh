@@ -329,7 +329,10 @@ struct ScoreLayer {
 void bab_branch_score(cudaStream_t st, int S, int K, int n_layers, const ScoreLayer* layers_dev,
                       const int32_t* sp_tab, int M, int32_t* picks);
 
-// tcgen05 GEMMs (k_tc.cu); false = shape or driver not supported, use SIMT
+// tcgen05 GEMMs (k_tc.cu); false = shape or driver not supported, use SIMT.
+// B must not be written by kernels still in flight when the GEMM launches
+// (the weights and their slices are static): its first tiles load before the
+// programmatic dependency wait.
 bool tc_available(int K, bool bf16);
 // flop_scale scales the flops the profiler counts (1/3 for a product whose K
 // is tripled by the three-term operands: the product is counted once)

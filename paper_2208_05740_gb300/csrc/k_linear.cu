@@ -100,34 +100,49 @@ __global__ void __launch_bounds__(256) k_gemm_nt(int64_t M, int N, int K, const 
   }
 }
 
-// out[r,o,oh,ow] = sum_{c,kh,kw} W[o,c,kh,kw] in[r,c,oh*s+kh-p,ow*s+kw-p]
+// out[r,o,oh,ow] = sum_{c,kh,kw} W[o,c,kh,kw] in[r,c,oh*s+kh-p,ow*s+kw-p], each
+// thread computing kConvFT output channels of one output pixel (every source
+// value it loads serves all of them).
+constexpr int kConvFT = 4;
 template <typename Tin, typename Tacc>
-__global__ void k_conv_fwd(int64_t R, LayerGeom g, const Tin* __restrict__ W, const Tin* __restrict__ in,
-                           Tacc* __restrict__ out) {
-  int64_t n = R * (int64_t)g.d_out;
+__global__ void __launch_bounds__(256) k_conv_fwd_tile(int64_t R, LayerGeom g, const Tin* __restrict__ W,
+                                                       const Tin* __restrict__ in, Tacc* __restrict__ out) {
+  const int HWo = g.h_out * g.w_out, ckk = g.c_in * g.k * g.k;
+  const int nct = (g.c_out + kConvFT - 1) / kConvFT;
+  const int64_t n = R * (int64_t)nct * HWo;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t r = idx / g.d_out;
-    int rem = (int)(idx - r * g.d_out);
-    int o = rem / (g.h_out * g.w_out);
-    int p2 = rem - o * g.h_out * g.w_out;
-    int oh = p2 / g.w_out, ow = p2 - oh * g.w_out;
+    const int64_t r = idx / ((int64_t)nct * HWo);
+    const int rem = (int)(idx - r * nct * HWo);
+    const int o0 = (rem / HWo) * kConvFT;
+    const int p2 = rem - (o0 / kConvFT) * HWo;
+    const int oh = p2 / g.w_out, ow = p2 - oh * g.w_out;
     const Tin* ir = in + r * g.d_in;
-    Tacc acc = Tacc(0);
+    Tacc acc[kConvFT];
+#pragma unroll
+    for (int t = 0; t < kConvFT; ++t) acc[t] = Tacc(0);
     for (int c = 0; c < g.c_in; ++c)
       for (int kh = 0; kh < g.k; ++kh) {
-        int ih = oh * g.stride + kh - g.pad;
+        const int ih = oh * g.stride + kh - g.pad;
         if (ih < 0 || ih >= g.h_in) continue;
         for (int kw = 0; kw < g.k; ++kw) {
-          int iw = ow * g.stride + kw - g.pad;
+          const int iw = ow * g.stride + kw - g.pad;
           if (iw < 0 || iw >= g.w_in) continue;
-          acc = fma(load_as<Tacc>(W + ((o * g.c_in + c) * g.k + kh) * g.k + kw),
-                    load_as<Tacc>(ir + (c * g.h_in + ih) * g.w_in + iw), acc);
+          const Tacc v = load_as<Tacc>(ir + (c * g.h_in + ih) * g.w_in + iw);
+#pragma unroll
+          for (int t = 0; t < kConvFT; ++t) {
+            const int o = o0 + t < g.c_out ? o0 + t : g.c_out - 1;   // a valid address; not stored
+            acc[t] = fma(load_as<Tacc>(W + (size_t)o * ckk + (c * g.k + kh) * g.k + kw), v, acc[t]);
+          }
         }
       }
-    out[idx] = acc;
+    Tacc* orow = out + r * g.d_out + p2;
+#pragma unroll
+    for (int t = 0; t < kConvFT; ++t)
+      if (o0 + t < g.c_out) orow[(int64_t)(o0 + t) * HWo] = acc[t];
   }
 }
+
 
 // out[r,c,ih,iw] = sum over the taps (kh,kw) that reach (ih,iw) and over the
 // channels o of W[o,c,kh,kw] in[r,o,(ih+p-kh)/s,(iw+p-kw)/s]. Threads run in
@@ -182,6 +197,66 @@ __global__ void k_conv_T(int64_t R, LayerGeom g, const Tin* __restrict__ W, cons
     const int64_t oi = r * g.d_in + c * HW + ih * g.w_in + iw;
     out[oi] = acc;
     if constexpr (ABS) outabs[oi] = aacc;
+  }
+}
+
+// The same product with each thread computing kConvCT output channels of one
+// output pixel: every source value it loads serves all of them, where the
+// kernel above loads it once per output channel. The sums run over the taps
+// and channels in the same order, so each output is the same number.
+constexpr int kConvCT = 4;
+template <typename Tin, typename Tacc>
+__global__ void __launch_bounds__(256) k_conv_T_tile(int64_t R, LayerGeom g, const Tin* __restrict__ W,
+                                                     const Tin* __restrict__ in, Tacc* __restrict__ out) {
+  const int s = g.stride, HW = g.h_in * g.w_in, HWo = g.h_out * g.w_out, ckk = g.c_in * g.k * g.k;
+  const int nct = (g.c_in + kConvCT - 1) / kConvCT;
+  const int64_t n = R * (int64_t)nct * HW;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / ((int64_t)nct * HW);
+    const int rem = (int)(idx - r * nct * HW);
+    const int c0 = (rem / HW) * kConvCT;
+    int q = rem - (c0 / kConvCT) * HW;   // position in phase order
+    int ph = 0, pw = 0, Wf = 1;
+    for (int f = 0; f < s * s; ++f) {
+      ph = f / s;
+      pw = f - ph * s;
+      const int Hf = ph < g.h_in ? (g.h_in - ph + s - 1) / s : 0;
+      Wf = pw < g.w_in ? (g.w_in - pw + s - 1) / s : 0;
+      if (q < Hf * Wf) break;
+      q -= Hf * Wf;
+    }
+    const int ih = ph + s * (q / Wf), iw = pw + s * (q % Wf);
+    const int rh = (ph + g.pad) % s, rw = (pw + g.pad) % s;
+    const Tin* ir = in + r * g.d_out;
+    Tacc acc[kConvCT];
+#pragma unroll
+    for (int t = 0; t < kConvCT; ++t) acc[t] = Tacc(0);
+    for (int kh = rh; kh < g.k; kh += s) {
+      const int th = ih + g.pad - kh;
+      if (th < 0) break;   // larger kh only lower th
+      const int oh = th / s;
+      if (oh >= g.h_out) continue;
+      for (int kw = rw; kw < g.k; kw += s) {
+        const int tw = iw + g.pad - kw;
+        if (tw < 0) break;
+        const int ow = tw / s;
+        if (ow >= g.w_out) continue;
+        const int xo = oh * g.w_out + ow;
+        for (int o = 0; o < g.c_out; ++o) {
+          const Tacc v = load_as<Tacc>(ir + o * HWo + xo);
+#pragma unroll
+          for (int t = 0; t < kConvCT; ++t) {
+            const int c = c0 + t < g.c_in ? c0 + t : g.c_in - 1;   // a valid address; not stored
+            acc[t] = fma(load_as<Tacc>(W + o * ckk + (c * g.k + kh) * g.k + kw), v, acc[t]);
+          }
+        }
+      }
+    }
+    Tacc* orow = out + r * g.d_in + ih * g.w_in + iw;
+#pragma unroll
+    for (int t = 0; t < kConvCT; ++t)
+      if (c0 + t < g.c_in) orow[(int64_t)(c0 + t) * HW] = acc[t];
   }
 }
 
@@ -289,7 +364,8 @@ void conv_fwd(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, cons
   char nm[32];
   snprintf(nm, sizeof nm, "conv_fwd_%s", tname<Tin>());
   int tk = prof_begin(st, nm, 2.0 * R * conv_macs(g), (double)R * (g.d_in * sizeof(Tin) + g.d_out * sizeof(Tacc)));
-  k_conv_fwd<Tin, Tacc><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out);
+  k_conv_fwd_tile<Tin, Tacc><<<grid_for(R * (int64_t)((g.c_out + kConvFT - 1) / kConvFT) * g.h_out * g.w_out, 256),
+                               256, 0, st>>>(R, g, W, in, out);
   prof_end(st, tk);
 }
 
@@ -307,7 +383,8 @@ void conv_T(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const 
   if (g.k == 1 && g.pad == 0)
     k_conv_T_1x1<Tin, Tacc, false><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, nullptr, nullptr, nullptr);
   else
-    k_conv_T<Tin, Tacc, false><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, nullptr, nullptr, nullptr);
+    k_conv_T_tile<Tin, Tacc><<<grid_for(R * (int64_t)((g.c_in + kConvCT - 1) / kConvCT) * g.h_in * g.w_in, 256), 256, 0,
+                               st>>>(R, g, W, in, out);
   prof_end(st, tk);
 }
 

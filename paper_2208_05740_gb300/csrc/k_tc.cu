@@ -259,6 +259,19 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  // B (weights, or their exact slices) is never written by kernels that may
+  // still be running: the first stages' B tiles load before the dependency
+  // wait, under the previous kernel's tail; their stage barriers then wait
+  // for A's bytes as well
+  const int npre = KT < Cfg::kStages ? KT : Cfg::kStages;
+  if (warp == 0 && lane == 0) {
+    for (int kt = 0; kt < npre; ++kt) {
+      uint8_t* st = smem + kt * Cfg::kStageBytes;
+      mbar_expect_tx(&full[kt], Cfg::kStageBytes);
+      tma_load_2d(st + kTileA, &tB, &full[kt], kt * Cfg::kKElems, n0);
+      if constexpr (KIND == 1) tma_load_2d(st + kTileA + kTileB, &tBlo, &full[kt], kt * Cfg::kKElems, n0);
+    }
+  }
   griddep_wait();   // A (and C's previous readers) belong to earlier kernels
 
   if (warp == 0 && lane == 0) {
@@ -268,11 +281,13 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
       const uint32_t ph = (kt / Cfg::kStages) & 1;
       if (!mbar_wait_idle(&empty[s], ph ^ 1)) break;
       uint8_t* st = smem + s * Cfg::kStageBytes;
-      mbar_expect_tx(&full[s], Cfg::kStageBytes);
       const int x = kt * Cfg::kKElems;
+      if (kt >= npre) {
+        mbar_expect_tx(&full[s], Cfg::kStageBytes);
+        tma_load_2d(st + kTileA, &tB, &full[s], x, n0);
+        if constexpr (KIND == 1) tma_load_2d(st + kTileA + kTileB, &tBlo, &full[s], x, n0);
+      }
       tma_load_2d(st, &tA, &full[s], x, m0);
-      tma_load_2d(st + kTileA, &tB, &full[s], x, n0);
-      if constexpr (KIND == 1) tma_load_2d(st + kTileA + kTileB, &tBlo, &full[s], x, n0);
     }
   } else if (KIND == 1 && warp >= 2) {
     // tf32 split of A into TMEM: x = hi + lo, hi = x rounded to tf32 (nearest,
