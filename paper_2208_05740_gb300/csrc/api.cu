@@ -420,18 +420,20 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
       UP(wt32h, float, hi.data(), nw);
       UP(wt32l, float, lo.data(), nw);
     }
-    __nv_bfloat16 *cf16 = nullptr, *ct16 = nullptr, *ct16x3 = nullptr, *wt16x3 = nullptr;
-    int cfk = 0, cfn = 0, ctk = 0, ctn = 0, ct3k = 0, ct3n = 0;
+    __nv_bfloat16 *cf16 = nullptr, *ct16 = nullptr, *cs16 = nullptr, *wt16x3 = nullptr;
+    int cfk = 0, cfn = 0, ctk = 0, ctn = 0, cs_k = 0, cs_n = 0;
+    ConvSecondB b2;
     if (g.kind != GCP_DENSE) {
       // columns by the convolution plan of each direction (phases, taps,
       // source channel padded to 8), rows = output channels padded to 16
-      // gg: the plan's geometry; for split_geom(g) (the three-term operand of
-      // the mixed chain) output channel t c_out + o carries W_hi of channel o
-      // for t = 0, 1 and W_lo for t = 2
-      auto pack = [&](bool transposed, int& kp, int& np_, const LayerGeom& gg) {
+      // gg: the plan's geometry; for split_geom(g) (the mixed chain's operand
+      // [nu_hi | nu_lo] as twice the channels) output channel t c_out + o
+      // carries term(weight of o, t): W_hi for both t in the first weight
+      // operand, W_lo for t = 0 and 0 for t = 1 in the second
+      auto pack_d = [&](bool transposed, int& kp, int& np_, const LayerGeom& gg, int which) {
         ConvPlan cp;
         std::vector<double> p;
-        if (!conv_plan(gg, transposed ? 1 : 0, cp)) { kp = np_ = 0; return to_bf16(p.data(), 0); }
+        if (!conv_plan(gg, transposed ? 1 : 0, cp)) { kp = np_ = 0; return p; }
         kp = cp.Kp;
         np_ = cp.Np;
         p.assign((size_t)np_ * kp, 0.0);
@@ -446,28 +448,67 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
                 for (int ci = 0; ci < g.c_in; ++ci) {
                   const double wf = d.W[(((size_t)(o % g.c_out) * g.c_in + ci) * g.k + kh) * g.k + kw];
                   const int term = o / g.c_out;
-                  const double w = term == 0 ? wf : (term == 1 ? bf16_hi(wf) : wf - bf16_hi(wf));
+                  const double w = which == 0 ? wf : (which == 1 ? bf16_hi(wf) : (term == 0 ? wf - bf16_hi(wf) : 0.0));
                   const int n = transposed ? ci : o, c = transposed ? o : ci;
                   p[(size_t)n * kp + col0 + c] = w;
                 }
             }
         }
+        return p;
+      };
+      auto pack = [&](bool transposed, int& kp, int& np_, const LayerGeom& gg) {
+        auto p = pack_d(transposed, kp, np_, gg, 0);
         return to_bf16(p.data(), p.size());
       };
       auto pf = pack(false, cfk, cfn, g);
       if (!pf.empty()) UP(cf16, __nv_bfloat16, pf.data(), pf.size());
       auto pt = pack(true, ctk, ctn, g);
       if (!pt.empty()) UP(ct16, __nv_bfloat16, pt.data(), pt.size());
-      // the three-term transposed product on the tensor cores; a map of fewer
-      // than 8 output channels (an input layer's c_in) fills at most 8 of a
-      // tile's 16 columns while its producers stage three times the source
+      // the transposed product of the mixed chain on the tensor cores: A from
+      // [nu_hi | nu_lo], weights [W_hi | W_hi] and, reusing each A block,
+      // [W_lo | 0] (its all-zero K blocks left out). A map of fewer than 8
+      // output channels (an input layer's c_in) would fill at most 8 of a
+      // tile's 16 columns while its producers stage twice the source
       // channels: it runs in float on the SIMT units instead
-      const LayerGeom g3 = split_geom(g);
-      auto p3 = g.c_in >= 8 ? pack(true, ct3k, ct3n, g3) : std::vector<__nv_bfloat16>();
-      if (!p3.empty() && conv_tc_fits(g3, 1, ct3k, ct3n)) UP(ct16x3, __nv_bfloat16, p3.data(), p3.size());
-    } else if (tc_available(kTerms * g.d_out, true)) {
+      if (g.c_in >= 8) {
+        const LayerGeom g2 = split_geom(g);
+        auto p1 = pack_d(true, cs_k, cs_n, g2, 1);
+        int k2 = 0, n2 = 0;
+        auto p2 = pack_d(true, k2, n2, g2, 2);
+        if (!p1.empty() && k2 == cs_k && n2 == cs_n && cs_k / 64 <= kConvMaxKb) {
+          const int nkb = cs_k / 64;
+          b2.map.assign(nkb, -1);
+          std::vector<int> keep;
+          for (int kb = 0; kb < nkb; ++kb) {
+            bool any = false;
+            for (int n = 0; n < cs_n && !any; ++n)
+              for (int j = 0; j < 64 && !any; ++j) any = p2[(size_t)n * cs_k + kb * 64 + j] != 0.0;
+            if (any) {
+              b2.map[kb] = (int8_t)keep.size();
+              keep.push_back(kb);
+            }
+          }
+          b2.nb2 = (int)keep.size();
+          std::vector<double> c2((size_t)cs_n * 64 * std::max(b2.nb2, 1), 0.0);
+          for (int n = 0; n < cs_n; ++n)
+            for (int t = 0; t < b2.nb2; ++t)
+              for (int j = 0; j < 64; ++j)
+                c2[(size_t)n * 64 * b2.nb2 + t * 64 + j] = p2[(size_t)n * cs_k + keep[t] * 64 + j];
+          if (conv_tc_fits(g2, 1, cs_k, cs_n, b2.nb2)) {
+            auto h1 = to_bf16(p1.data(), p1.size());
+            auto h2 = to_bf16(c2.data(), c2.size());
+            UP(cs16, __nv_bfloat16, h1.data(), h1.size());
+            __nv_bfloat16* w2 = nullptr;
+            UP(w2, __nv_bfloat16, h2.data(), h2.size());
+            b2.W = b2.nb2 > 0 ? w2 : nullptr;
+          } else {
+            b2 = ConvSecondB{};
+          }
+        }
+      }
+    } else if (tc_available(kDenseTerms * g.d_out, true)) {
       // rows of [W_hi^T | W_hi^T | W_lo^T] for the three-term operand [hi | lo | hi]
-      const size_t K3 = (size_t)kTerms * g.d_out;
+      const size_t K3 = (size_t)kDenseTerms * g.d_out;
       std::vector<double> t3((size_t)g.d_in * K3);
       for (int q = 0; q < g.d_in; ++q)
         for (int o = 0; o < g.d_out; ++o) {
@@ -507,8 +548,8 @@ gcp_status init_net(Ctx& c, const gcp_layer_desc* layers, int n_layers, const do
     net->WTsl.push_back(sl);
     net->CF16.push_back(cf16); net->CT16.push_back(ct16);
     net->cf_kp.push_back(cfk); net->cf_np.push_back(cfn); net->ct_kp.push_back(ctk); net->ct_np.push_back(ctn);
-    net->WT16x3.push_back(wt16x3); net->CT16x3.push_back(ct16x3);
-    net->ct3_kp.push_back(ct3k); net->ct3_np.push_back(ct3n);
+    net->WT16x3.push_back(wt16x3); net->CT16s.push_back(cs16);
+    net->cts_kp.push_back(cs16 ? cs_k : 0); net->cts_np.push_back(cs16 ? cs_n : 0); net->CTs_b2.push_back(b2);
     UP(b64, double, bias, g.d_out);
     auto bf = to_f32(bias, g.d_out);
     UP(b32, float, bf.data(), g.d_out);
@@ -1054,21 +1095,25 @@ static bool split_bwd(const Batch& b, int i) {
     return false;
   } else {
     const Net& n = *b.net;
-    return b.tc && (n.geom[i - 1].kind == GCP_DENSE ? n.WT16x3[i - 1] != nullptr : n.CT16x3[i - 1] != nullptr);
+    return b.tc && (n.geom[i - 1].kind == GCP_DENSE ? n.WT16x3[i - 1] != nullptr : n.CT16s[i - 1] != nullptr);
   }
 }
 // y = W^(i)^T nu in the mixed-precision chain, from the three-term operand
 // nu2 [R, kTerms d_i] or from nu in float. false: a tensor-core launch was refused.
+// The operand's term count a map's tensor-core product takes.
+static int map_terms(const Net& n, int i) { return n.geom[i - 1].kind == GCP_DENSE ? kDenseTerms : kConvTerms; }
+
 template <typename Top, typename T>
-static bool lin_backward_mixed(cudaStream_t st, const Batch& b, int i, const Top* nu2, const T* full, T* y) {
+static bool lin_backward_mixed(cudaStream_t st, const Batch& b, int i, const Top* nu2, int terms, const T* full,
+                               T* y) {
   if constexpr (std::is_same<Top, __nv_bfloat16>::value && std::is_same<T, float>::value) {
     const Net& net = *b.net;
     const LayerGeom& g = net.geom[i - 1];
-    if (split_bwd<Top>(b, i)) {
+    if (split_bwd<Top>(b, i) && nu2 && terms == map_terms(net, i)) {
       if (g.kind == GCP_DENSE)
-        return gemm_tc_bf16(st, b.R, g.d_in, kTerms * g.d_out, nu2, net.WT16x3[i - 1], y, 1.0 / kTerms);
-      return conv_tc_bf16(st, b.R, split_geom(g), 1, net.CT16x3[i - 1], net.ct3_kp[i - 1], net.ct3_np[i - 1], nu2, y,
-                          1.0 / kTerms);
+        return gemm_tc_bf16(st, b.R, g.d_in, kDenseTerms * g.d_out, nu2, net.WT16x3[i - 1], y, 1.0 / kDenseTerms);
+      return conv_tc_bf16(st, b.R, split_geom(g), 1, net.CT16s[i - 1], net.cts_kp[i - 1], net.cts_np[i - 1], nu2, y,
+                          1.0 / kConvTerms, &net.CTs_b2[i - 1]);
     }
     if (g.kind == GCP_DENSE) gemm_nt<float, float>(st, b.R, g.d_in, g.d_out, full, 0, net.WT32[i - 1], y);
     else conv_T<float, float>(st, b.R, g, net.W32[i - 1], full, y);
@@ -1080,13 +1125,17 @@ static bool lin_backward_mixed(cudaStream_t st, const Batch& b, int i, const Top
 // chain: the three-term operand for tensor-core products (the layer's, or its
 // projection shortcut's), float for SIMT products and identity skips.
 template <typename Top>
-static void mixed_forms(const Batch& b, int i, bool& split, bool& full) {
+static void mixed_forms(const Batch& b, int i, bool& split, bool& full, int& terms) {
   const Net& net = *b.net;
   const int sc = net.skip[i - 1] ? net.sc_map[i - 1] : 0;
   const bool ident = net.skip[i - 1] && !sc;
   const bool sp_i = split_bwd<Top>(b, i), sp_sc = sc && split_bwd<Top>(b, sc);
-  split = sp_i || sp_sc;
-  full = !sp_i || ident || (sc && !sp_sc);
+  // one operand layout serves the layer's product and its shortcut's; a
+  // consumer that wants the other layout takes nu in float
+  terms = sp_i ? map_terms(net, i) : (sp_sc ? map_terms(net, sc) : kDenseTerms);
+  const bool use_i = sp_i && map_terms(net, i) == terms, use_sc = sp_sc && map_terms(net, sc) == terms;
+  split = use_i || use_sc;
+  full = !use_i || ident || (sc && !use_sc);
 }
 
 // Linear forward step nubar^(i) = W^(i) a for all rows.
@@ -1118,7 +1167,7 @@ static void lin_forward(cudaStream_t st, const Batch& b, int i, const Top* a, co
 // rounding there would reach the bound at full size.
 template <typename Top, typename T>
 static gcp_status skip_backward(Ctx& c, Batch& b, cudaStream_t st, int i, const Top* nu, const Top* nu2,
-                                const T* nu_full, T* y, const T* SK) {
+                                int nu2_terms, const T* nu_full, T* y, const T* SK) {
   const Net& net = *b.net;
   const int L = net.L;
   const int64_t R = b.R;
@@ -1131,7 +1180,7 @@ static gcp_status skip_backward(Ctx& c, Batch& b, cudaStream_t st, int i, const 
                        : (T*)b.ws("skipT" + std::to_string(m), (size_t)R * dm * sizeof(T), &s);
       if (!dst) return s;
       if (!std::is_same<Top, T>::value) {
-        if (!lin_backward_mixed<Top, T>(st, b, sc, nu2, nu_full, dst))
+        if (!lin_backward_mixed<Top, T>(st, b, sc, nu2, nu2_terms, nu_full, dst))
           return c.fail(GCP_EDEVICE, "projection of layer %d: tensor-core product refused", i);
       } else {
         lin_backward<Top, T>(st, b, sc, nu, nullptr, dst);
@@ -1245,15 +1294,15 @@ static const T* recompute_nuhat(Ctx& c, Batch& b, cudaStream_t st, int target, g
     a.theta = theta_of<T>(b, i);
     if (!std::is_same<Top, T>::value && i > target) {
       bool sp = false, fu = false;
-      mixed_forms<Top>(b, i, sp, fu);
+      mixed_forms<Top>(b, i, sp, fu, a.split_terms);
       a.nu_out = nullptr;
-      if (sp && !(a.nu_split = (Top*)b.ws("rc_nu2", (size_t)R * kTerms * mh * sizeof(Top), s))) return nullptr;
+      if (sp && !(a.nu_split = (Top*)b.ws("rc_nu2", (size_t)R * kMaxTerms * mh * sizeof(Top), s))) return nullptr;
       if (fu && !(a.nu_full = (T*)b.ws("rc_nu_full", (size_t)R * mh * sizeof(T), s))) return nullptr;
     }
     relax_eval<T, Top>(st, a);
     if (i > target) {
       if (!std::is_same<Top, T>::value) {
-        if (!lin_backward_mixed<Top, T>(st, b, i, a.nu_split, a.nu_full, y)) {
+        if (!lin_backward_mixed<Top, T>(st, b, i, a.nu_split, a.split_terms, a.nu_full, y)) {
           *s = c.fail(GCP_EDEVICE, "layer %d: tensor-core product refused", i);
           return nullptr;
         }
@@ -1320,20 +1369,20 @@ gcp_status run_eval(Ctx& c, Batch& b, cudaStream_t st, bool with_adjoint_start, 
     a.theta_init = theta_init;
     if (!std::is_same<Top, T>::value) {
       bool sp = false, fu = false;
-      mixed_forms<Top>(b, i, sp, fu);
+      mixed_forms<Top>(b, i, sp, fu, a.split_terms);
       a.nu_out = nullptr;
-      if (sp && !(a.nu_split = (Top*)b.ws("nu2", (size_t)R * kTerms * b.dmax() * sizeof(Top), &s))) return s;
+      if (sp && !(a.nu_split = (Top*)b.ws("nu2", (size_t)R * kMaxTerms * b.dmax() * sizeof(Top), &s))) return s;
       if (fu && !(a.nu_full = (T*)b.ws("nu_full", (size_t)R * b.dmax() * sizeof(T), &s))) return s;
     }
     relax_eval<T, Top>(st, a);
     poff += (net.dims[i] + kChunk - 1) / kChunk;
     if (!std::is_same<Top, T>::value) {
-      if (!lin_backward_mixed<Top, T>(st, b, i, a.nu_split, a.nu_full, y))
+      if (!lin_backward_mixed<Top, T>(st, b, i, a.nu_split, a.split_terms, a.nu_full, y))
         return c.fail(GCP_EDEVICE, "layer %d: tensor-core product refused", i);
     } else {
       lin_backward<Top, T>(st, b, i, nu, a.nu_lo, y);
     }
-    s = skip_backward<Top, T>(c, b, st, i, nu, a.nu_split, a.nu_full, y, spec_skip<T>(net));
+    s = skip_backward<Top, T>(c, b, st, i, nu, a.nu_split, a.split_terms, a.nu_full, y, spec_skip<T>(net));
     if (s) return s;
   }
   ConcArgs<T, Top> ca{};

@@ -32,13 +32,15 @@ struct Net {
   std::vector<float*> Wabs32;        // |W| in float rounded up (convolution layers; certification)
   std::vector<SliceB> WTsl;          // exact bf16 slices of W^T (dense layers; float64 certification)
   std::vector<int> cf_kp, cf_np, ct_kp, ct_np;
-  // the mixed-precision chain's backward products with three-term bf16
+  // the mixed-precision chain's backward products with multi-term bf16
   // operands: dense layers [d_in, 3 d_out] = rows of [W_hi^T | W_hi^T | W_lo^T];
   // convolutions packed for the transposed plan of split_geom(g) (source
-  // channels tripled, the weights of terms hi, hi, lo); nullptr where that
-  // product stays on the SIMT units (with nu in float)
-  std::vector<__nv_bfloat16*> WT16x3, CT16x3;
-  std::vector<int> ct3_kp, ct3_np;
+  // channels doubled): [W_hi | W_hi], and [W_lo | 0] as a second weight
+  // operand over the same A blocks; nullptr where that product stays on the
+  // SIMT units (with nu in float)
+  std::vector<__nv_bfloat16*> WT16x3, CT16s;
+  std::vector<int> cts_kp, cts_np;
+  std::vector<ConvSecondB> CTs_b2;
   double *xlo64 = nullptr, *xhi64 = nullptr;
   float *xlo32 = nullptr, *xhi32 = nullptr;
   double *C64 = nullptr, *negC64 = nullptr, *bL64 = nullptr;

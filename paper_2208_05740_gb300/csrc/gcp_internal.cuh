@@ -13,6 +13,7 @@
 // inside that row's gamma / E vectors.
 #pragma once
 
+#include <vector>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -30,16 +31,20 @@ struct LayerGeom {
   int kind, d_in, d_out;
   int c_in, h_in, w_in, c_out, h_out, w_out, k, stride, pad;
 };
-// The mixed-precision chain's products run as three bf16 terms concatenated
-// along K: operand [nu_hi | nu_lo | nu_hi] against weights [W_hi | W_hi | W_lo]
-// (hi = bf16(x), lo = bf16(x - hi)), i.e. nu_hi W_hi + nu_lo W_hi + nu_hi W_lo
-// in one tensor-core product with float accumulation.
-constexpr int kTerms = 3;
-// The geometry whose transposed product takes that operand: output channels
-// (the transposed product's source channels) times kTerms.
+// The mixed-precision chain's backward products run on three bf16 terms,
+// nu_hi W_hi + nu_lo W_hi + nu_hi W_lo (hi = bf16(x), lo = bf16(x - hi)), in
+// one tensor-core product with float accumulation. Dense layers concatenate
+// them along K: operand [nu_hi | nu_lo | nu_hi] against [W_hi | W_hi | W_lo]
+// (kDenseTerms planes). Convolutions stage the operand as twice the source
+// channels, [nu_hi | nu_lo] (kConvTerms planes), multiply each A block by
+// [W_hi | W_hi] and, as a second weight operand, by [W_lo | 0].
+constexpr int kDenseTerms = 3, kConvTerms = 2;
+constexpr int kMaxTerms = 3;
+// The geometry whose transposed product takes the convolution's operand:
+// output channels (the transposed product's source channels) times kConvTerms.
 inline LayerGeom split_geom(LayerGeom g) {
-  g.c_out *= kTerms;
-  g.d_out *= kTerms;
+  g.c_out *= kConvTerms;
+  g.d_out *= kConvTerms;
   return g;
 }
 
@@ -107,11 +112,12 @@ struct RelaxArgs {
   // Outputs of the mixed-precision chain (bf16 operands, T = float), each
   // written only where set: nu in T, for the products that stay on the SIMT
   // units and for identity skip connections (which would otherwise carry an
-  // operand rounding into y^(m) unaveraged); and nu's three-term operand, row
-  // r = [hi | lo | hi] with hi = bf16(nu) and lo = bf16(nu - hi), for the
-  // tensor-core products against [W_hi | W_hi | W_lo] (nu_out is then nullptr).
+  // operand rounding into y^(m) unaveraged); and nu's multi-term operand, row
+  // r = [hi | lo] (split_terms 2) or [hi | lo | hi] (3) with hi = bf16(nu) and
+  // lo = bf16(nu - hi), for the tensor-core products (nu_out is then nullptr).
   T* nu_full;           // [R, d]
-  Top* nu_split;        // [R, kTerms * d]
+  Top* nu_split;        // [R, split_terms * d]
+  int split_terms;
 };
 
 template <typename T, typename Top>
@@ -453,11 +459,20 @@ __host__ __device__ inline bool conv_plan(const LayerGeom& g, int dir, ConvPlan&
 // dir 0 out = conv(src) [R, d_out], dir 1 out = conv^T(src) [R, d_in]. Wp is
 // the weight packed for that direction's plan, [Np, Kp]. false = shape not
 // supported (use the SIMT convolution). flop_scale as for gemm_tc_bf16.
+constexpr int kConvMaxKb = 96;   // K blocks of 64 columns a plan may have with a second weight operand
+// b2 (optional): a second weight operand that each A block is also
+// multiplied by, the tiles of Wp2 [Np, 64 * nb2] listed per K block of the
+// plan in map (-1: none); its products are added to the same accumulator.
+struct ConvSecondB {
+  const __nv_bfloat16* W = nullptr;
+  int nb2 = 0;
+  std::vector<int8_t> map;
+};
 bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const __nv_bfloat16* Wp, int Kp, int Np,
-                  const __nv_bfloat16* src, float* out, double flop_scale = 1.0);
+                  const __nv_bfloat16* src, float* out, double flop_scale = 1.0, const ConvSecondB* b2 = nullptr);
 // Whether conv_tc_bf16 takes this plan at any row count (its staging fits
-// shared memory and its accumulators TMEM).
-bool conv_tc_fits(const LayerGeom& g, int dir, int Kp, int Np);
+// shared memory and its accumulators TMEM), with nb2 second-operand tiles.
+bool conv_tc_fits(const LayerGeom& g, int dir, int Kp, int Np, int nb2 = 0);
 
 template <typename T, typename Top>
 void relax_eval(cudaStream_t st, const RelaxArgs<T, Top>& a);

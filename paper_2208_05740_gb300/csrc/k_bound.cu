@@ -327,11 +327,11 @@ __device__ __forceinline__ void put_operand_v(Top* hi, float* lo, int64_t i, con
   }
 }
 
-// Three-term bf16 operand of the mixed-precision chain: hi = bf16(x) at p[i]
-// and p[i + 2d], lo = bf16(x - hi) at p[i + d] (hi + lo carries about 16
-// significant bits).
+// Multi-term bf16 operand of the mixed-precision chain: hi = bf16(x) at p[i]
+// (and at p[i + 2d] for three terms), lo = bf16(x - hi) at p[i + d] (hi + lo
+// carries about 16 significant bits).
 template <int V, typename Top, typename T>
-__device__ __forceinline__ void put_split_v(Top* p, int64_t i, int d, const T (&x)[V]) {
+__device__ __forceinline__ void put_split_v(Top* p, int64_t i, int d, const T (&x)[V], int terms) {
   if constexpr (std::is_same<Top, __nv_bfloat16>::value && std::is_same<T, float>::value) {
     float lo[V];
     __nv_bfloat16 h[V], l[V];
@@ -351,13 +351,13 @@ __device__ __forceinline__ void put_split_v(Top* p, int64_t i, int d, const T (&
       ul.y = *reinterpret_cast<const uint32_t*>(&l1);
       *reinterpret_cast<uint2*>(p + i) = uh;
       *reinterpret_cast<uint2*>(p + i + d) = ul;
-      *reinterpret_cast<uint2*>(p + i + 2 * d) = uh;
+      if (terms == 3) *reinterpret_cast<uint2*>(p + i + 2 * d) = uh;
     } else {
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         p[i + v] = h[v];
         p[i + d + v] = l[v];
-        p[i + 2 * d + v] = h[v];
+        if (terms == 3) p[i + 2 * d + v] = h[v];
       }
     }
   }
@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_eval(RelaxArgs<T, Top
           if (obj) term += (cl == 2 ? hu : (cl == 1 ? sq[v] : T(0))) - nu[v] * n.bj[v];
         }
         if (a.nu_out) put_operand_v<V, Top>(a.nu_out, a.nu_lo, ij, nu);
-        if (a.nu_split) put_split_v<V, Top>(a.nu_split, r * kTerms * a.d + w.j0, a.d, nu);
+        if (a.nu_split) put_split_v<V, Top>(a.nu_split, r * a.split_terms * a.d + w.j0, a.d, nu, a.split_terms);
         if (a.nu_full) stv<V>(a.nu_full + ij, nu);
         stv<V>(a.nuhat_out + ij, nh);
         if constexpr (PI) {
@@ -1370,10 +1370,12 @@ inline bool chk_csc(const CutCSC<T>& c, int d) {
 template <typename T, typename Top>
 void relax_eval(cudaStream_t st, const RelaxArgs<T, Top>& a) {
   if (a.R <= 0 || a.d <= 0) return;
+  if (a.nu_split && a.split_terms != 2 && a.split_terms != 3)
+    return (void)reg_check(nullptr, 1.0, "relax: split operand of 2 or 3 terms");
   char nm[48];
   snprintf(nm, sizeof nm, "relax_eval_%s%s", tsfx<T>(), sizeof(Top) == 2 ? "_bf16" : "");
   const double bytes = (double)a.R * a.d * (3.0 * sizeof(T) + (a.nu_out ? sizeof(Top) : 0) +
-                                            (a.nu_split ? kTerms * sizeof(Top) : 0.0) + (a.nu_full ? sizeof(T) : 0)) +
+                                            (a.nu_split ? a.split_terms * sizeof(Top) : 0.0) + (a.nu_full ? sizeof(T) : 0)) +
                        (double)a.R * (a.csc.n_entries + (a.d + 31) / 32) * sizeof(T);
   const double Rd = (double)a.R * a.d, tb = sizeof(T);
   if (!(reg_check(a.y, (a.y_per_spec ? (double)a.K : (double)a.R) * a.d * tb, "relax y") &
@@ -1382,7 +1384,7 @@ void relax_eval(cudaStream_t st, const RelaxArgs<T, Top>& a) {
         reg_check(a.alpha, Rd * tb, "alpha") & reg_check(a.beta, (double)a.M * a.R * tb, "beta") &
         reg_check(a.gamma, (a.csc.n_total ? (double)a.N * a.R : 0.0) * tb, "gamma") & chk_splits(a.sp, a.R, a.K, a.M) &
         chk_csc(a.csc, a.d) & reg_check(a.nu_out, a.nu_out ? Rd * sizeof(Top) : 0.0, "nu out") &
-        reg_check(a.nu_split, a.nu_split ? kTerms * Rd * sizeof(Top) : 0.0, "nu split") &
+        reg_check(a.nu_split, a.nu_split ? a.split_terms * Rd * sizeof(Top) : 0.0, "nu split") &
         reg_check(a.nu_lo, a.nu_lo ? Rd * 4.0 : 0.0, "nu lo") &
         reg_check(a.nuhat_out, Rd * tb, "nuhat out") & reg_check(a.theta, a.theta ? Rd * tb : 0.0, "theta") &
         reg_check(a.nu_full, a.nu_full ? Rd * tb : 0.0, "nu full") &

@@ -260,6 +260,131 @@ __global__ void __launch_bounds__(256) k_conv_T_tile(int64_t R, LayerGeom g, con
   }
 }
 
+// Row-staged forms of the two SIMT convolutions: the weights staged in shared
+// memory once per CTA, then one row at a time: the row's source map staged in
+// shared memory (read once from global memory), then kConvCT / kConvFT output
+// channels of one output pixel per work item, pixels fastest (a warp's pixels
+// share a phase, hence their taps). The sums run in the same order as the
+// kernels above, so every output is the same number.
+template <typename Tin, typename Tacc>
+__global__ void __launch_bounds__(256) k_conv_T_row(int64_t R, LayerGeom g, const Tin* __restrict__ W,
+                                                    const Tin* __restrict__ in, Tacc* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char conv_sm[];
+  Tacc* src = reinterpret_cast<Tacc*>(conv_sm);   // [d_out]
+  Tacc* ws = src + g.d_out;                       // [c_out, c_in, k, k]
+  const int s = g.stride, HW = g.h_in * g.w_in, HWo = g.h_out * g.w_out, ckk = g.c_in * g.k * g.k;
+  const int nct = (g.c_in + kConvCT - 1) / kConvCT, items = nct * HW;
+  for (int i = threadIdx.x; i < g.c_out * ckk; i += blockDim.x) ws[i] = load_as<Tacc>(W + i);
+  for (int64_t r = blockIdx.x; r < R; r += gridDim.x) {
+    __syncthreads();   // the previous row's items are done with src
+    for (int i = threadIdx.x; i < g.d_out; i += blockDim.x) src[i] = load_as<Tacc>(in + r * g.d_out + i);
+    __syncthreads();
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      const int c0 = (it / HW) * kConvCT;
+      int q = it - (c0 / kConvCT) * HW;   // position in phase order
+      int ph = 0, pw = 0, Wf = 1;
+      for (int f = 0; f < s * s; ++f) {
+        ph = f / s;
+        pw = f - ph * s;
+        const int Hf = ph < g.h_in ? (g.h_in - ph + s - 1) / s : 0;
+        Wf = pw < g.w_in ? (g.w_in - pw + s - 1) / s : 0;
+        if (q < Hf * Wf) break;
+        q -= Hf * Wf;
+      }
+      const int ih = ph + s * (q / Wf), iw = pw + s * (q % Wf);
+      const int rh = (ph + g.pad) % s, rw = (pw + g.pad) % s;
+      Tacc acc[kConvCT];
+#pragma unroll
+      for (int t = 0; t < kConvCT; ++t) acc[t] = Tacc(0);
+      for (int kh = rh; kh < g.k; kh += s) {
+        const int th = ih + g.pad - kh;
+        if (th < 0) break;
+        const int oh = th / s;
+        if (oh >= g.h_out) continue;
+        for (int kw = rw; kw < g.k; kw += s) {
+          const int tw = iw + g.pad - kw;
+          if (tw < 0) break;
+          const int ow = tw / s;
+          if (ow >= g.w_out) continue;
+          const int xo = oh * g.w_out + ow;
+          for (int o = 0; o < g.c_out; ++o) {
+            const Tacc v = src[o * HWo + xo];
+#pragma unroll
+            for (int t = 0; t < kConvCT; ++t) {
+              const int c = c0 + t < g.c_in ? c0 + t : g.c_in - 1;   // a valid address; not stored
+              acc[t] = fma(ws[o * ckk + (c * g.k + kh) * g.k + kw], v, acc[t]);
+            }
+          }
+        }
+      }
+      Tacc* orow = out + r * g.d_in + ih * g.w_in + iw;
+#pragma unroll
+      for (int t = 0; t < kConvCT; ++t)
+        if (c0 + t < g.c_in) orow[(int64_t)(c0 + t) * HW] = acc[t];
+    }
+  }
+}
+
+template <typename Tin, typename Tacc>
+__global__ void __launch_bounds__(256) k_conv_fwd_row(int64_t R, LayerGeom g, const Tin* __restrict__ W,
+                                                      const Tin* __restrict__ in, Tacc* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char conv_sm[];
+  Tacc* src = reinterpret_cast<Tacc*>(conv_sm);   // [d_in]
+  Tacc* ws = src + g.d_in;                        // [c_out, c_in, k, k]
+  const int HWo = g.h_out * g.w_out, ckk = g.c_in * g.k * g.k;
+  const int nct = (g.c_out + kConvFT - 1) / kConvFT, items = nct * HWo;
+  for (int i = threadIdx.x; i < g.c_out * ckk; i += blockDim.x) ws[i] = load_as<Tacc>(W + i);
+  for (int64_t r = blockIdx.x; r < R; r += gridDim.x) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.d_in; i += blockDim.x) src[i] = load_as<Tacc>(in + r * g.d_in + i);
+    __syncthreads();
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      const int o0 = (it / HWo) * kConvFT;
+      const int p2 = it - (o0 / kConvFT) * HWo;
+      const int oh = p2 / g.w_out, ow = p2 - oh * g.w_out;
+      Tacc acc[kConvFT];
+#pragma unroll
+      for (int t = 0; t < kConvFT; ++t) acc[t] = Tacc(0);
+      for (int c = 0; c < g.c_in; ++c)
+        for (int kh = 0; kh < g.k; ++kh) {
+          const int ih = oh * g.stride + kh - g.pad;
+          if (ih < 0 || ih >= g.h_in) continue;
+          for (int kw = 0; kw < g.k; ++kw) {
+            const int iw = ow * g.stride + kw - g.pad;
+            if (iw < 0 || iw >= g.w_in) continue;
+            const Tacc v = src[(c * g.h_in + ih) * g.w_in + iw];
+#pragma unroll
+            for (int t = 0; t < kConvFT; ++t) {
+              const int o = o0 + t < g.c_out ? o0 + t : g.c_out - 1;   // a valid address; not stored
+              acc[t] = fma(ws[o * ckk + (c * g.k + kh) * g.k + kw], v, acc[t]);
+            }
+          }
+        }
+      Tacc* orow = out + r * g.d_out + p2;
+#pragma unroll
+      for (int t = 0; t < kConvFT; ++t)
+        if (o0 + t < g.c_out) orow[(int64_t)(o0 + t) * HWo] = acc[t];
+    }
+  }
+}
+
+// Dynamic shared memory of a row-staged convolution, opted in once per kernel
+// (false: the row does not fit; use the tiled kernel).
+constexpr size_t kConvRowSmem = 96 * 1024;
+template <typename Kern>
+bool conv_row_smem(Kern kern, size_t bytes) {
+  if (bytes > kConvRowSmem) return false;
+  static bool attr = false;   // one static per kernel instantiation
+  if (!attr) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvRowSmem) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    attr = true;
+  }
+  return true;
+}
+
 // The transposed 1x1 convolution without padding (a residual block's
 // projection shortcut): out[r,c,ih,iw] = sum_o W[o,c] in[r,o,ih/s,iw/s] where s
 // divides ih and iw (and ih/s, iw/s lie in the source map), else 0. One thread
@@ -364,8 +489,12 @@ void conv_fwd(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, cons
   char nm[32];
   snprintf(nm, sizeof nm, "conv_fwd_%s", tname<Tin>());
   int tk = prof_begin(st, nm, 2.0 * R * conv_macs(g), (double)R * (g.d_in * sizeof(Tin) + g.d_out * sizeof(Tacc)));
-  k_conv_fwd_tile<Tin, Tacc><<<grid_for(R * (int64_t)((g.c_out + kConvFT - 1) / kConvFT) * g.h_out * g.w_out, 256),
-                               256, 0, st>>>(R, g, W, in, out);
+  const size_t row_bytes = ((size_t)g.d_in + (size_t)g.c_out * g.c_in * g.k * g.k) * sizeof(Tacc);
+  if (conv_row_smem(k_conv_fwd_row<Tin, Tacc>, row_bytes))
+    k_conv_fwd_row<Tin, Tacc><<<(unsigned)std::min<int64_t>(R, 152 * 8), 256, row_bytes, st>>>(R, g, W, in, out);
+  else
+    k_conv_fwd_tile<Tin, Tacc><<<grid_for(R * (int64_t)((g.c_out + kConvFT - 1) / kConvFT) * g.h_out * g.w_out, 256),
+                                 256, 0, st>>>(R, g, W, in, out);
   prof_end(st, tk);
 }
 
@@ -382,6 +511,11 @@ void conv_T(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const 
   int tk = prof_begin(st, nm, 2.0 * R * conv_macs(g), (double)R * (g.d_out * sizeof(Tin) + g.d_in * sizeof(Tacc)));
   if (g.k == 1 && g.pad == 0)
     k_conv_T_1x1<Tin, Tacc, false><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, nullptr, nullptr, nullptr);
+  else if (conv_row_smem(k_conv_T_row<Tin, Tacc>,
+                         ((size_t)g.d_out + (size_t)g.c_out * g.c_in * g.k * g.k) * sizeof(Tacc)))
+    k_conv_T_row<Tin, Tacc><<<(unsigned)std::min<int64_t>(R, 152 * 8), 256,
+                              ((size_t)g.d_out + (size_t)g.c_out * g.c_in * g.k * g.k) * sizeof(Tacc), st>>>(
+        R, g, W, in, out);
   else
     k_conv_T_tile<Tin, Tacc><<<grid_for(R * (int64_t)((g.c_in + kConvCT - 1) / kConvCT) * g.h_in * g.w_in, 256), 256, 0,
                                st>>>(R, g, W, in, out);

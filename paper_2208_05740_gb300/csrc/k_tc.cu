@@ -447,6 +447,12 @@ struct ConvTcArgs {
   const __nv_bfloat16* src;  // [R, Cs*Hs*Ws], channel-major (c, h, w)
   const __nv_bfloat16* Wp;   // [Np, Kp]
   float* out;                // [R, Co*Ho*Wo], channel-major
+  // optional second weight operand: K-block kb's A block is also multiplied
+  // by tile b2map[kb] (>= 0) of Wp2 [Np, 64 * nb2] and added (the low term of
+  // the weights, which reuses the A block built for the high term)
+  const __nv_bfloat16* Wp2;
+  int nb2;
+  int8_t b2map[kConvMaxKb];
 };
 
 // Roles of the 416 threads: warps 0-3 the epilogue (warp w reads TMEM lanes
@@ -459,10 +465,11 @@ constexpr int kConvStages = 4;   // A blocks in flight
 struct ConvSmem {
   int b_off, stg_off, tab_off, bar_off, total;
 };
-__host__ __device__ inline ConvSmem conv_smem_layout(int Kp, int Np, int stg_rows, int Ws, int Csp, int bufs) {
+__host__ __device__ inline ConvSmem conv_smem_layout(int Kp, int Np, int stg_rows, int Ws, int Csp, int bufs,
+                                                     int nb2 = 0) {
   ConvSmem L;
   L.b_off = kConvStages * kTileA;                          // after the A stages
-  L.stg_off = L.b_off + (Kp / 64) * Np * kRowBytes;        // weights: Kp/64 tiles of Np rows
+  L.stg_off = L.b_off + (Kp / 64 + nb2) * Np * kRowBytes;  // weights: Kp/64 (+ nb2) tiles of Np rows
   L.tab_off = (L.stg_off + bufs * stg_rows * Ws * Csp * 2 + 15) & ~15;
   L.bar_off = (L.tab_off + (Kp / 8) * 4 + 7) & ~7;         // chunk table: one word per 8 K columns
   // barriers: full/empty per A stage, full/empty per accumulator, abort flag, TMEM slot
@@ -653,7 +660,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   const ConvPlan& c = a.c;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const ConvSmem lay = conv_smem_layout(c.Kp, c.Np, a.stg_rows, c.Ws, c.Csp, a.stg_bufs);
+  const ConvSmem lay = conv_smem_layout(c.Kp, c.Np, a.stg_rows, c.Ws, c.Csp, a.stg_bufs, a.nb2);
   uint8_t* As = smem;
   uint8_t* Bs = smem + lay.b_off;
   __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(smem + lay.stg_off);
@@ -693,6 +700,14 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       const int kb = ch >> 3, j = ch & 7;
       const uint4 v = *reinterpret_cast<const uint4*>(a.Wp + (int64_t)n * c.Kp + ch * 8);
       *reinterpret_cast<uint4*>(Bs + kb * c.Np * kRowBytes + n * kRowBytes + ((j ^ (n & 7)) << 4)) = v;
+    }
+    // the second weight operand's tiles after the first's
+    const int chunks2 = a.nb2 * 8;
+    for (int idx = tid; idx < c.Np * chunks2; idx += kConvThreads) {
+      const int n = idx / chunks2, ch = idx - n * chunks2;
+      const int kb = ch >> 3, j = ch & 7;
+      const uint4 v = *reinterpret_cast<const uint4*>(a.Wp2 + (int64_t)n * chunks2 * 8 + ch * 8);
+      *reinterpret_cast<uint4*>(Bs + (c.Kp / 64 + kb) * c.Np * kRowBytes + n * kRowBytes + ((j ^ (n & 7)) << 4)) = v;
     }
   }
   // chunk table: for the 8 K columns of chunk x (a phase's k-block kb, chunk
@@ -839,6 +854,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
 #pragma unroll
             for (int k4 = 0; k4 < kRowBytes / 32; ++k4)
               umma<0>(acc, sdesc(ab + k4 * 32), sdesc(bb + k4 * 32), id, (kb | k4) != 0);
+            const int t2 = a.nb2 > 0 ? a.b2map[f.kb0 + kb] : -1;
+            if (t2 >= 0) {   // the same A block against the second weight operand
+              const uint32_t bb2 = smem_u32(Bs + (c.Kp / 64 + t2) * c.Np * kRowBytes);
+#pragma unroll
+              for (int k4 = 0; k4 < kRowBytes / 32; ++k4) umma<0>(acc, sdesc(ab + k4 * 32), sdesc(bb2 + k4 * 32), id, 1);
+            }
             umma_commit(&a_empty[sg]);   // the stage is free once these MMAs have read it
           }
         }
@@ -1180,9 +1201,10 @@ bool gemm_f64_slices(cudaStream_t st, int64_t M, int N, int K, const double* A, 
   return true;
 }
 
-bool conv_tc_fits(const LayerGeom& g, int dir, int Kp, int Np) {
+bool conv_tc_fits(const LayerGeom& g, int dir, int Kp, int Np, int nb2) {
   ConvPlan c;
   if (!conv_plan(g, dir, c) || c.Kp != Kp || c.Np != Np || Np > 256) return false;
+  if (nb2 > 0 && Kp / 64 > kConvMaxKb) return false;
   // the staging window grows with the row count until a tile spans whole
   // rows of every phase; a large row count gives the largest
   const int R = 1 << 16;
@@ -1197,11 +1219,11 @@ bool conv_tc_fits(const LayerGeom& g, int dir, int Kp, int Np) {
   }
   int tc = 32;
   while (tc < Np) tc <<= 1;
-  return conv_smem_layout(Kp, Np, std::max(rows, 1), c.Ws, c.Csp, 1).total <= 227 * 1024 && 2 * tc <= 512;
+  return conv_smem_layout(Kp, Np, std::max(rows, 1), c.Ws, c.Csp, 1, nb2).total <= 227 * 1024 && 2 * tc <= 512;
 }
 
 bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const __nv_bfloat16* Wp, int Kp, int Np,
-                  const __nv_bfloat16* src, float* out, double flop_scale) {
+                  const __nv_bfloat16* src, float* out, double flop_scale, const ConvSecondB* b2) {
   if (R <= 0) return true;
   ConvTcArgs a{};
   ConvPlan& c = a.c;
@@ -1237,10 +1259,16 @@ bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const
   }
   a.units = a.group == 2 ? c.f[0].ntiles + c.f[2].ntiles : tiles;
   a.stg_bufs = 2;
-  ConvSmem L = conv_smem_layout(Kp, Np, a.stg_rows, c.Ws, c.Csp, 2);
+  if (b2 && b2->nb2 > 0) {
+    if (Kp / 64 > kConvMaxKb || (int)b2->map.size() != Kp / 64 || !b2->W) return false;
+    a.Wp2 = b2->W;
+    a.nb2 = b2->nb2;
+    for (int q = 0; q < Kp / 64; ++q) a.b2map[q] = b2->map[q];
+  }
+  ConvSmem L = conv_smem_layout(Kp, Np, a.stg_rows, c.Ws, c.Csp, 2, a.nb2);
   if (L.total > 227 * 1024) {
     a.stg_bufs = 1;
-    L = conv_smem_layout(Kp, Np, a.stg_rows, c.Ws, c.Csp, 1);
+    L = conv_smem_layout(Kp, Np, a.stg_rows, c.Ws, c.Csp, 1, a.nb2);
   }
   if (L.total > 227 * 1024) return false;
   static std::mutex mu;
@@ -1265,6 +1293,7 @@ bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const
   a.out = out;
   const int src_dim = c.Cs * c.Hs * c.Ws, out_dim = c.Co * c.Ho * c.Wo;
   if (!(reg_check(src, (double)R * src_dim * 2, "conv src") & reg_check(Wp, (double)Np * Kp * 2, "conv W") &
+        reg_check(a.Wp2, a.nb2 ? (double)Np * 64 * a.nb2 * 2 : 0.0, "conv W2") &
         reg_check(out, (double)R * out_dim * 4, "conv out")))
     return true;  // reported by the caller's launch status
   int per_sm = 1;

@@ -55,3 +55,33 @@ def test_recomputed_nuhat_gives_identical_gradients_and_trajectory(monkeypatch, 
         # six 256-wide hidden layers: the stored copies (R x 1536) against three
         # recompute buffers of the widest layer (R x 3 x 256)
         assert mem_r < mem_s
+
+
+def test_budget_chooses_recompute_by_itself(monkeypatch):
+    """With GCP_NUHAT unset and a budget that holds the three widest-layer
+    buffers of the recomputing adjoint but not every layer's stored nuhat,
+    the library recomputes on its own: no GCP_EBUDGET, and the gradients equal
+    the stored run's bit for bit."""
+    inst = synth.mlp_256x6(n_sub=40, n_cuts=60)
+    g_s, _, _, mem_s = _run(monkeypatch, "store", inst, gcp.GCP_FP32, gcp.GCP_FP32)
+    g_r, _, _, mem_r = _run(monkeypatch, "recompute", inst, gcp.GCP_FP32, gcp.GCP_FP32)
+    monkeypatch.delenv("GCP_NUHAT", raising=False)
+    with gcp.Context(0) as probe:
+        net_id, cs = probe.load_instance(inst)
+        D = probe.duals_create(net_id, cs, inst.sub, gcp.GCP_FP32)
+        base = probe.mem_used()
+        probe.duals_free(D)
+    # everything the batch needs before the adjoint, plus the recomputing
+    # adjoint's workspace and half of what storing would add on top of it
+    budget = base + mem_r + (mem_s - mem_r) // 2
+    with gcp.Context(0, hbm_budget_bytes=budget) as ctx:
+        net_id, cs = ctx.load_instance(inst)
+        D = ctx.duals_create(net_id, cs, inst.sub, gcp.GCP_FP32)
+        rng = np.random.default_rng(4)
+        a, b, g = synth.random_duals(rng, inst, 0.1, 0.1)
+        ctx.duals_import(D, join_alpha(a), b, g)
+        grads = ctx.grad_batch(D, gcp.GCP_FP32)      # raises on GCP_EBUDGET
+        assert ctx.mem_used() <= budget
+        ctx.duals_free(D)
+    for x, y in zip(g_s, grads):
+        np.testing.assert_array_equal(x, y)
