@@ -743,6 +743,12 @@ gcp_status build_cutdev(Ctx& c, const Net& net, const CutSet* cs, CutDev& out) {
       if (j < net.dims[i]) run += cnt[poff[i] + j];
     }
   }
+  out.span4_max.assign(L, 0);
+  for (int i = 0; i < L; ++i)
+    for (int j0 = 0; j0 < net.dims[i]; j0 += 128) {
+      const int j1 = std::min(j0 + 128, net.dims[i]);
+      out.span4_max[i] = std::max(out.span4_max[i], cptr[poff[i] + j1] - cptr[poff[i] + j0]);
+    }
   for (int64_t q = 0; q < out.nnz; ++q) {
     const int64_t e = order[q];
     ccut[q] = cut_of[e];
@@ -1005,7 +1011,8 @@ template <typename T>
 CutCSC<T> csc_of(const Batch& b, int layer) {
   const CutDev& c = b.cuts;
   return CutCSC<T>{c.csc_ptr + c.poff[layer], c.csc_cut, c.csc_kind, TSel<T>::coef(c), c.csc_eid, c.csc_nrn,
-                   c.layer_nnz.empty() ? 0 : c.layer_nnz[layer], c.nnz};
+                   c.layer_nnz.empty() ? 0 : c.layer_nnz[layer], c.nnz,
+                   c.span4_max.empty() ? 0 : c.span4_max[layer]};
 }
 
 int64_t Batch::dmax() const {

@@ -93,6 +93,7 @@ struct CutDev {
   int32_t* csr_pos = nullptr;        // CSC position of each CSR entry
   std::vector<int64_t> poff;         // segment start of layer i in csc_ptr
   std::vector<int64_t> layer_nnz;    // entries per layer
+  std::vector<int32_t> span4_max;    // per layer: entries of the fullest 128-neuron span
   std::vector<void*> owned;
   bool pooled = false;               // blocks go back to the context's pool (serving batches)
   ~CutDev();

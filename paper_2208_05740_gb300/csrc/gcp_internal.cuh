@@ -59,6 +59,7 @@ struct CutCSC {
   const int32_t* nrn;   // neuron index of the entry within its layer
   int64_t n_entries;    // entries of this layer (host-side accounting only)
   int64_t n_total;      // entries of all layers (host-side validation only)
+  int max_span4;        // entries of this layer's fullest 128-neuron span (host-side launch choice only)
 };
 
 struct SplitsDev {

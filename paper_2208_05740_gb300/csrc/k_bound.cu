@@ -273,6 +273,9 @@ __device__ __forceinline__ void ldv(const T* p, T (&o)[V]) {      // read-only d
   if constexpr (V == 4 && sizeof(T) == 4) {
     const float4 q = __ldg(reinterpret_cast<const float4*>(p));
     o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+  } else if constexpr (V == 2 && sizeof(T) == 4) {
+    const float2 q = __ldg(reinterpret_cast<const float2*>(p));
+    o[0] = q.x; o[1] = q.y;
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) o[v] = __ldg(p + v);
@@ -283,6 +286,9 @@ __device__ __forceinline__ void ldv_rw(const T* p, T (&o)[V]) {   // also writte
   if constexpr (V == 4 && sizeof(T) == 4) {
     const float4 q = *reinterpret_cast<const float4*>(p);
     o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+  } else if constexpr (V == 2 && sizeof(T) == 4) {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    o[0] = q.x; o[1] = q.y;
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) o[v] = p[v];
@@ -292,6 +298,8 @@ template <int V, typename T>
 __device__ __forceinline__ void stv(T* p, const T (&o)[V]) {
   if constexpr (V == 4 && sizeof(T) == 4) {
     *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  } else if constexpr (V == 2 && sizeof(T) == 4) {
+    *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) p[v] = o[v];
@@ -321,6 +329,9 @@ __device__ __forceinline__ void put_operand_v(Top* hi, float* lo, int64_t i, con
     u.x = *reinterpret_cast<const uint32_t*>(&p0);
     u.y = *reinterpret_cast<const uint32_t*>(&p1);
     *reinterpret_cast<uint2*>(hi + i) = u;
+  } else if constexpr (std::is_same<Top, __nv_bfloat16>::value && V == 2) {
+    const __nv_bfloat162 p0 = __floats2bfloat162_rn(x[0], x[1]);
+    *reinterpret_cast<uint32_t*>(hi + i) = *reinterpret_cast<const uint32_t*>(&p0);
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) hi[i + v] = cvt_out<Top>(x[v]);
@@ -352,6 +363,12 @@ __device__ __forceinline__ void put_split_v(Top* p, int64_t i, int d, const T (&
       *reinterpret_cast<uint2*>(p + i) = uh;
       *reinterpret_cast<uint2*>(p + i + d) = ul;
       if (terms == 3) *reinterpret_cast<uint2*>(p + i + 2 * d) = uh;
+    } else if constexpr (V == 2) {
+      const __nv_bfloat162 h0 = __halves2bfloat162(h[0], h[1]), l0 = __halves2bfloat162(l[0], l[1]);
+      const uint32_t uh = *reinterpret_cast<const uint32_t*>(&h0), ul = *reinterpret_cast<const uint32_t*>(&l0);
+      *reinterpret_cast<uint32_t*>(p + i) = uh;
+      *reinterpret_cast<uint32_t*>(p + i + d) = ul;
+      if (terms == 3) *reinterpret_cast<uint32_t*>(p + i + 2 * d) = uh;
     } else {
 #pragma unroll
       for (int v = 0; v < V; ++v) {
@@ -441,6 +458,22 @@ struct SpanEntry {
   int maxrun;   // longest run of the batch (warp-uniform)
   T coef;
 };
+// Runs of a batch: lanes whose entries share a destination form a run of
+// consecutive lanes; the first lane of each run gets its length.
+template <typename T>
+__device__ __forceinline__ void entry_runs(SpanEntry<T>& en, int lane) {
+  const int prev = __shfl_up_sync(0xffffffffu, en.dest, 1);
+  const bool cont = lane > 0 && prev == en.dest;
+  const unsigned cm = __ballot_sync(0xffffffffu, cont);
+  // run length: this lane plus the continuation lanes right after it
+  int len = 1;
+  if (lane < 31) {
+    const unsigned after = cm >> (lane + 1), all = 0xffffffffu >> (lane + 1);
+    len += after == all ? 31 - lane : __ffs(~after) - 1;
+  }
+  en.run = cont ? 0 : len;
+  en.maxrun = __reduce_max_sync(0xffffffffu, en.run);
+}
 template <typename T, int V>
 __device__ __forceinline__ void span_entry(const CutCSC<T>& c, int N, int base, int b0, int ce, int lane,
                                            SpanEntry<T>& en, DevErr& er) {
@@ -460,17 +493,7 @@ __device__ __forceinline__ void span_entry(const CutCSC<T>& c, int N, int base, 
       en.dest = kind * 32 * V + nl;
     }
   }
-  const int prev = __shfl_up_sync(0xffffffffu, en.dest, 1);
-  const bool cont = lane > 0 && prev == en.dest;
-  const unsigned cm = __ballot_sync(0xffffffffu, cont);
-  // run length: this lane plus the continuation lanes right after it
-  int len = 1;
-  if (lane < 31) {
-    const unsigned after = cm >> (lane + 1), all = 0xffffffffu >> (lane + 1);
-    len += after == all ? 31 - lane : __ffs(~after) - 1;
-  }
-  en.run = cont ? 0 : len;
-  en.maxrun = __reduce_max_sync(0xffffffffu, en.run);
+  entry_runs(en, lane);
 }
 template <typename T>
 struct SpanCuts {
@@ -493,14 +516,20 @@ __device__ __forceinline__ void span_cuts(const CutCSC<T>& c, int N, int d, cons
 
 // acc[kind * 32V + neuron] += gamma-weighted entries of one batch; gv is
 // gamma[row, cut] of the lane's entry.
+// The first lane of a run starts from the destination's sum so far and the
+// run's later lanes are added one by one, so every destination adds its
+// entries in CSC order starting from 0, however they fall into batches: the
+// sums do not depend on the span width or on which entries share a batch.
 template <typename T>
 __device__ __forceinline__ void span_batch_sum(const SpanEntry<T>& en, T gv, T* acc) {
+  const bool head = en.run > 0 && en.cut >= 0;
   T v = en.cut >= 0 ? en.coef * gv : T(0);
+  if (head) v = acc[en.dest] + v;
   for (int q = 1; q < en.maxrun; ++q) {
     const T u = __shfl_down_sync(0xffffffffu, v, q);
     if (q < en.run) v += u;
   }
-  if (en.run > 0 && en.cut >= 0) acc[en.dest] += v;
+  if (head) acc[en.dest] = v;
   __syncwarp();
 }
 
@@ -536,6 +565,103 @@ __device__ __forceinline__ void span_cut_sums(const CutCSC<T>& c, const SpanCuts
   __syncwarp();
 }
 
+template <typename T, int V>
+__device__ __forceinline__ void span_zero(T* buf, int lane) {
+  T z[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) z[v] = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) stv<V>(buf + k * 32 * V + lane * V, z);
+  __syncwarp();
+}
+
+// The adjoint needs only the z sums s of its neurons (the x and xhat sums
+// enter through nuhat, which the relaxation stored). When the span's entries
+// are all cached (at most kSpanBatches batches) and at most kZBatches * 32 of
+// them are z entries, those are compacted, in their CSC order, into kZBatches
+// batches of their own: a row then stages and sums only them. Runs stay
+// contiguous, so each (z, neuron) sum still adds its entries in CSC order.
+constexpr int kZBatches = 2;
+template <typename T>
+struct SpanZ {
+  bool ok;                  // compacted (warp-uniform); else the full sums
+  int nb;                   // batches in use (warp-uniform)
+  SpanEntry<T> b[kZBatches];
+};
+// scratch: the warp's zeroed accumulator (3 * 32V elements of T), zeroed
+// again on return.
+template <typename T, int V>
+__device__ __forceinline__ void span_zcuts(const SpanCuts<T>& sc, const SpanWarp<V>& w, T* scratch, SpanZ<T>& z) {
+  constexpr int cap = (32 * V < 32 * kZBatches) ? 32 * V : 32 * kZBatches;   // 3 arrays of cap in 3 * 32V
+  int nz = 0;
+  unsigned mk[kSpanBatches];
+  int base[kSpanBatches];
+#pragma unroll
+  for (int q = 0; q < kSpanBatches; ++q) {
+    const SpanEntry<T>& en = sc.b[q];
+    const bool isz = sc.cb + 32 * q < sc.ce && en.cut >= 0 && en.dest >= 2 * 32 * V;
+    mk[q] = __ballot_sync(0xffffffffu, isz);
+    base[q] = nz;
+    nz += __popc(mk[q]);
+  }
+  z.ok = sc.ce - sc.cb <= 32 * kSpanBatches && nz <= cap;
+  z.nb = (nz + 31) / 32;
+#pragma unroll
+  for (int q = 0; q < kZBatches; ++q) {
+    z.b[q].cut = -1;
+    z.b[q].coef = T(0);
+    z.b[q].dest = -1 - w.lane;
+    z.b[q].run = 1;
+    z.b[q].maxrun = 1;
+  }
+  if (!z.ok) return;
+  int* zcut = reinterpret_cast<int*>(scratch);
+  int* zdst = zcut + cap;
+  T* zcoef = scratch + 2 * cap * sizeof(int) / sizeof(T);
+#pragma unroll
+  for (int q = 0; q < kSpanBatches; ++q) {
+    if ((mk[q] >> w.lane) & 1u) {
+      const int p = base[q] + __popc(mk[q] & ((1u << w.lane) - 1u));
+      zcut[p] = sc.b[q].cut;
+      zdst[p] = sc.b[q].dest;
+      zcoef[p] = sc.b[q].coef;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < kZBatches; ++q) {
+    const int p = 32 * q + w.lane;
+    if (p < nz) {
+      z.b[q].cut = zcut[p];
+      z.b[q].dest = zdst[p];
+      z.b[q].coef = zcoef[p];
+    }
+    entry_runs(z.b[q], w.lane);
+  }
+  __syncwarp();
+  span_zero<T, V>(scratch, w.lane);
+}
+
+// s of the lane's V neurons from the compacted z entries; gam[32q + lane]
+// holds gamma[row, cut] of the lane's entry in z batch q.
+template <typename T, int V>
+__device__ __forceinline__ void span_z_sums(const SpanZ<T>& z, const SpanWarp<V>& w, const T* gam, T* acc,
+                                            T (&s)[V]) {
+#pragma unroll
+  for (int v = 0; v < V; ++v) s[v] = T(0);
+  if (z.nb == 0) return;
+#pragma unroll
+  for (int q = 0; q < kZBatches; ++q)
+    if (q < z.nb) span_batch_sum(z.b[q], gam[32 * q + w.lane], acc);
+  T* a2 = acc + 64 * V + w.lane * V;
+  ldv_rw<V>(a2, s);
+  T zr[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) zr[v] = T(0);
+  stv<V>(a2, zr);
+  __syncwarp();
+}
+
 // E[r, e] = coef_e * value of the entry's (kind, neuron): x -> vx, xhat -> vh,
 // z -> vz, e the entry's CSC position (a span's entries are contiguous, so a
 // batch is one coalesced store). ev is the warp's staging buffer (3 * 32V).
@@ -562,15 +688,6 @@ __device__ __forceinline__ void span_cut_writes(const CutCSC<T>& c, const SpanCu
   __syncwarp();
 }
 
-template <typename T, int V>
-__device__ __forceinline__ void span_zero(T* buf, int lane) {
-  T z[V];
-#pragma unroll
-  for (int v = 0; v < V; ++v) z[v] = T(0);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) stv<V>(buf + k * 32 * V + lane * V, z);
-  __syncwarp();
-}
 
 // Objective partial of the row: the span covers the 32-neuron partial slots
 // V*c .. V*c + V - 1 of its layer; the first gets the sum, the others 0.
@@ -767,9 +884,19 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_adj(AdjArgs<T, Top> a
   SpanNeurons<T, V> n;
   DevErr er;
   SpanCuts<T> sc;
+  SpanZ<T> zc;
   auto scattered = [&](int k, int st) {
     T* sb = stage(st) + 5 * SPAN;
     const int64_t r = (int64_t)w.s * a.K + k;
+    if (zc.ok) {
+#pragma unroll
+      for (int q = 0; q < kZBatches; ++q) {
+        if (q >= zc.nb) break;
+        const bool ok = k < ke && zc.b[q].cut >= 0;
+        cp_async<sizeof(T)>(sb + 32 * q + w.lane, ok ? a.gamma + r * a.N + zc.b[q].cut : dummy, ok);
+      }
+      return;
+    }
 #pragma unroll
     for (int q = 0; q < kSpanBatches; ++q) {
       const bool ok = k < ke && sc.b[q].cut >= 0 && sc.cb + 32 * q < sc.ce;
@@ -779,6 +906,7 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_adj(AdjArgs<T, Top> a
   span_zero<T, V>(acc, w.lane);
   span_neurons<T, V>(w, a.lo, a.hi, a.bias, a.inv_ul, a.sp, a.M, a.layer, n);
   span_cuts<T, V>(a.csc, a.N, a.d, w, sc, er);
+  span_zcuts<T, V>(sc, w, acc, zc);
   // everything above reads static data only; the rows come from earlier kernels
   griddep_wait();
 #pragma unroll
@@ -801,8 +929,13 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_adj(AdjArgs<T, Top> a
       const int64_t r = (int64_t)w.s * a.K + k;
       const int64_t ij = r * a.d + w.j0;
       const T wr = a.seed ? __ldg(a.seed + r) : T(1);
-      T t[V], gg[V], sq[V];
-      span_cut_sums<T, V>(a.csc, sc, a.N, w, sb + 5 * SPAN, a.gamma + r * a.N, acc, t, gg, sq, er);
+      T sq[V];
+      if (zc.ok) {
+        span_z_sums<T, V>(zc, w, sb + 5 * SPAN, acc, sq);
+      } else {
+        T t[V], gg[V];
+        span_cut_sums<T, V>(a.csc, sc, a.N, w, sb + 5 * SPAN, a.gamma + r * a.N, acc, t, gg, sq, er);
+      }
       T nbv[V], nh[V], al[V], ma[V], va[V];
       ldv_rw<V>(sb + w.lane * V, nbv);
       ldv_rw<V>(sb + SPAN + w.lane * V, nh);
@@ -827,11 +960,9 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_adj(AdjArgs<T, Top> a
         const T nb = nbv[v] - wr * n.bj[v];   // dg/dnu^(i)
         const T h = nh[v], hi = n.hi[v], lo = n.lo[v], iv = n.iv[v];
         // local derivatives of nu and of the objective term h by case
-        T dnu_dnh = T(0), dh_dnh = T(0), dnu_ds = T(0), dh_ds = T(0);
-        if (n.cls[v] == 1) {                       // active
-          dnu_dnh = T(1);
-          dh_ds = wr;
-        } else if (PI && n.cls[v] == 2) {
+        const bool act1 = n.cls[v] == 1;           // active: nu = nuhat - t, h = s
+        T dnu_dnh = act1 ? T(1) : T(0), dh_dnh = T(0), dnu_ds = T(0), dh_ds = act1 ? wr : T(0);
+        if (PI && n.cls[v] == 2) {
           // pi = th C, q = u (C - pi) + l pi - s, h = l pi - max(q, 0), nu = pi - tau - t
           const T tc = tmin(tmax(th[v], T(0)), T(1));
           const bool pos = h > T(0);
@@ -841,16 +972,21 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_adj(AdjArgs<T, Top> a
           dh_dnh = pos ? wr * (lo * tc - (act ? hi * (T(1) - tc) + lo * tc : T(0))) : T(0);
           dh_ds = act ? wr : T(0);
           gt[v] = C * (nb + wr * (lo + (act ? hi - lo : T(0))));
-        } else if (n.cls[v] == 2) {
+        }
+        if constexpr (!PI) {
+          // unstable: the closed-form pi of Lemma A.1, computed for every
+          // neuron and selected by class (no divergent branches)
           const T p0 = (hi * h - sq[v]) * iv;
           const bool pos = h > T(0);
           const bool mid = pos && p0 > T(0) && p0 < h;          // pi* = p0
           const bool top = pos && !(p0 < h);                    // pi* = C; h = s when l C - s > 0
-          dnu_dnh = mid ? hi * iv : (top ? T(1) : (h < T(0) ? al[v] : T(0)));
-          dh_dnh = mid ? wr * lo * hi * iv : T(0);
-          dnu_ds = mid ? -iv : T(0);
-          dh_ds = mid ? -wr * lo * iv
-                      : (top ? (lo * h - sq[v] > T(0) ? wr : T(0)) : (pos ? T(0) : (sq[v] < T(0) ? wr : T(0))));
+          const bool un = n.cls[v] == 2;
+          const T hiv = hi * iv;
+          dnu_dnh = un ? (mid ? hiv : (top ? T(1) : (h < T(0) ? al[v] : T(0)))) : dnu_dnh;
+          dh_dnh = un && mid ? wr * lo * hiv : dh_dnh;
+          dnu_ds = un && mid ? -iv : dnu_ds;
+          const T zs = top ? (lo * h - sq[v] > T(0) ? wr : T(0)) : (pos ? T(0) : (sq[v] < T(0) ? wr : T(0)));
+          dh_ds = un ? (mid ? -wr * lo * iv : zs) : dh_ds;
         }
         ga[v] = n.cls[v] == 2 ? nb * (-tmax(-h, T(0))) : T(0);
         dnh[v] = nb * dnu_dnh + dh_dnh;
@@ -864,10 +1000,13 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_relax_adj(AdjArgs<T, Top> a
         } else if (n.unstable) {
 #pragma unroll
           for (int v = 0; v < V; ++v) {
-            if (n.cls[v] == 2) {
-              const T na = step_apply(a.st, al[v], ga[v], a.st.lr_a, ma[v], va[v]);
-              al[v] = tmin(tmax(na, T(0)), T(1));
-            }
+            // every neuron's step, kept for the unstable ones (no divergence)
+            T mv = ma[v], vv = va[v];
+            const T na = step_apply(a.st, al[v], ga[v], a.st.lr_a, mv, vv);
+            const bool un = n.cls[v] == 2;
+            al[v] = un ? tmin(tmax(na, T(0)), T(1)) : al[v];
+            ma[v] = un ? mv : ma[v];
+            va[v] = un ? vv : va[v];
           }
           stv<V>(a.alpha + ij, al);
           if (mode == 2) {
@@ -1319,9 +1458,21 @@ template <typename T>
 const char* tsfx() { return sizeof(T) == 8 ? "f64" : "f32"; }
 
 // Neurons per lane of the span kernels: 4 (16-byte vectors) for float chains
-// on layers whose width is a multiple of 4, else 1.
+// on layers whose width is a multiple of 4, unless a 128-neuron span of the
+// layer has more cut entries than the kSpanBatches batches a warp keeps in
+// registers (later batches reread their entries from memory every row): then
+// 2 (8-byte vectors, 64-neuron spans) when the width is even; else 1. The cut
+// sums add each destination's entries in CSC order whatever the span width,
+// so the choice changes no result.
 template <typename T>
 inline bool span_v4(int d) { return sizeof(T) == 4 && d % 4 == 0; }
+template <typename T>
+inline int span_vec(int d, int max_span4, bool al16_all, bool al8_all) {
+  if (sizeof(T) != 4) return 1;
+  const bool ok4 = d % 4 == 0 && al16_all, ok2 = d % 2 == 0 && al8_all;
+  if (ok4 && !(ok2 && max_span4 > 32 * kSpanBatches)) return 4;
+  return ok2 ? 2 : 1;
+}
 // A warp takes all K rows of its subdomain span, its setup (bounds, split
 // hits, cut entries) shared by the rows; a launch that would then leave the
 // GPU mostly idle (a small batch, where one warp's K rows in sequence are the
@@ -1333,6 +1484,7 @@ inline int row_split(int64_t S, int K, int spans) {
   return (int)std::min<int64_t>(K, (target + warps - 1) / warps);
 }
 inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+inline bool al8(const void* p) { return ((uintptr_t)p & 7) == 0; }
 
 // Launch a span kernel with its dynamic shared memory (the opt-in above 48 KB
 // is set once per kernel).
@@ -1365,6 +1517,21 @@ inline bool chk_csc(const CutCSC<T>& c, int d) {
          reg_check(c.nrn, c.n_total * 4.0, "csc nrn");
 }
 
+template <int V, typename T, typename Top>
+void launch_eval(cudaStream_t st, const RelaxArgs<T, Top>& a) {
+  if (a.theta)
+    launch_span(k_relax_eval<T, Top, V, true>, span_smem<T, V, 2, V, 3>(), span_blocks(a.R, a.K, a.d, V), st, a);
+  else
+    launch_span(k_relax_eval<T, Top, V, false>, span_smem<T, V, 2, V, 3>(), span_blocks(a.R, a.K, a.d, V), st, a);
+}
+template <int V, typename T, typename Top>
+void launch_adj(cudaStream_t st, const AdjArgs<T, Top>& a) {
+  if (a.theta)
+    launch_span(k_relax_adj<T, Top, V, true>, span_smem<T, V, 5, 0, 6>(), span_blocks(a.R, a.K, a.d, V), st, a);
+  else
+    launch_span(k_relax_adj<T, Top, V, false>, span_smem<T, V, 5, 0, 6>(), span_blocks(a.R, a.K, a.d, V), st, a);
+}
+
 // Algorithmic bytes per launch: every per-(row, neuron) array read or written
 // once, one gamma read (and E write) per cut entry and row, partial sums.
 template <typename T, typename Top>
@@ -1391,22 +1558,20 @@ void relax_eval(cudaStream_t st, const RelaxArgs<T, Top>& a) {
         (!a.obj_part || reg_check(a.obj_part, ((a.d + 31) / 32) * (double)a.R * tb, "obj part"))))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
+  const bool a16 = al16(a.y) && al16(a.alpha) && al16(a.lo) && al16(a.hi) && al16(a.bias) && al16(a.inv_ul) &&
+                   al16(a.nu_out) && al16(a.nu_lo) && al16(a.nuhat_out) && al16(a.theta) && al16(a.nu_full) &&
+                   (reinterpret_cast<uintptr_t>(a.nu_split) & 7) == 0;
+  const bool a8 = al8(a.y) && al8(a.alpha) && al8(a.lo) && al8(a.hi) && al8(a.bias) && al8(a.inv_ul) &&
+                  al8(a.nu_out) && al8(a.nu_lo) && al8(a.nuhat_out) && al8(a.theta) && al8(a.nu_full) &&
+                  (reinterpret_cast<uintptr_t>(a.nu_split) & 3) == 0;
+  const int V = span_vec<T>(a.d, a.csc.max_span4, a16, a8);
   if constexpr (sizeof(T) == 4) {
-    if (span_v4<T>(a.d) && al16(a.y) && al16(a.alpha) && al16(a.lo) && al16(a.hi) && al16(a.bias) &&
-        al16(a.inv_ul) && al16(a.nu_out) && al16(a.nu_lo) && al16(a.nuhat_out) && al16(a.theta) &&
-        al16(a.nu_full) && (reinterpret_cast<uintptr_t>(a.nu_split) & 7) == 0) {
-      if (a.theta)
-        launch_span(k_relax_eval<T, Top, 4, true>, span_smem<T, 4, 2, 4, 3>(), span_blocks(a.R, a.K, a.d, 4), st, a);
-      else
-        launch_span(k_relax_eval<T, Top, 4, false>, span_smem<T, 4, 2, 4, 3>(), span_blocks(a.R, a.K, a.d, 4), st, a);
-      prof_end(st, tk);
-      return;
-    }
+    if (V == 4) launch_eval<4>(st, a);
+    else if (V == 2) launch_eval<2>(st, a);
+    else launch_eval<1>(st, a);
+  } else {
+    launch_eval<1>(st, a);
   }
-  if (a.theta)
-    launch_span(k_relax_eval<T, Top, 1, true>, span_smem<T, 1, 2, 1, 3>(), span_blocks(a.R, a.K, a.d, 1), st, a);
-  else
-    launch_span(k_relax_eval<T, Top, 1, false>, span_smem<T, 1, 2, 1, 3>(), span_blocks(a.R, a.K, a.d, 1), st, a);
   prof_end(st, tk);
 }
 template <typename T, typename Top>
@@ -1441,22 +1606,20 @@ void relax_adjoint(cudaStream_t st, const AdjArgs<T, Top>& a) {
         reg_check(a.v_theta, (a.theta && m2) ? Rd * tb : 0.0, "v_theta")))
     return;
   int tk = prof_begin(st, nm, 0.0, bytes);
+  const bool a16 = al16(a.nubar) && al16(a.nuhat) && al16(a.alpha) && al16(a.m_alpha) && al16(a.v_alpha) &&
+                   al16(a.g_alpha) && al16(a.lo) && al16(a.hi) && al16(a.bias) && al16(a.inv_ul) && al16(a.a_out) &&
+                   al16(a.a_lo) && al16(a.theta) && al16(a.g_theta) && al16(a.m_theta) && al16(a.v_theta);
+  const bool a8 = al8(a.nubar) && al8(a.nuhat) && al8(a.alpha) && al8(a.m_alpha) && al8(a.v_alpha) &&
+                  al8(a.g_alpha) && al8(a.lo) && al8(a.hi) && al8(a.bias) && al8(a.inv_ul) && al8(a.a_out) &&
+                  al8(a.a_lo) && al8(a.theta) && al8(a.g_theta) && al8(a.m_theta) && al8(a.v_theta);
+  const int V = span_vec<T>(a.d, a.csc.max_span4, a16, a8);
   if constexpr (sizeof(T) == 4) {
-    if (span_v4<T>(a.d) && al16(a.nubar) && al16(a.nuhat) && al16(a.alpha) && al16(a.m_alpha) &&
-        al16(a.v_alpha) && al16(a.g_alpha) && al16(a.lo) && al16(a.hi) && al16(a.bias) && al16(a.inv_ul) &&
-        al16(a.a_out) && al16(a.a_lo) && al16(a.theta) && al16(a.g_theta) && al16(a.m_theta) && al16(a.v_theta)) {
-      if (a.theta)
-        launch_span(k_relax_adj<T, Top, 4, true>, span_smem<T, 4, 5, 0, 6>(), span_blocks(a.R, a.K, a.d, 4), st, a);
-      else
-        launch_span(k_relax_adj<T, Top, 4, false>, span_smem<T, 4, 5, 0, 6>(), span_blocks(a.R, a.K, a.d, 4), st, a);
-      prof_end(st, tk);
-      return;
-    }
+    if (V == 4) launch_adj<4>(st, a);
+    else if (V == 2) launch_adj<2>(st, a);
+    else launch_adj<1>(st, a);
+  } else {
+    launch_adj<1>(st, a);
   }
-  if (a.theta)
-    launch_span(k_relax_adj<T, Top, 1, true>, span_smem<T, 1, 5, 0, 6>(), span_blocks(a.R, a.K, a.d, 1), st, a);
-  else
-    launch_span(k_relax_adj<T, Top, 1, false>, span_smem<T, 1, 5, 0, 6>(), span_blocks(a.R, a.K, a.d, 1), st, a);
   prof_end(st, tk);
 }
 template <typename T, typename Top>

@@ -127,7 +127,7 @@ extern "C" gcp_status gcp_bound_dense_noalloc(int32_t n_layers, const int32_t* d
     a.inv_ul = nullptr;   // divide in the kernel
     a.alpha = alpha[i - 1];
     a.sp = sp;
-    a.csc = CutCSC<float>{csc_ptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0};
+    a.csc = CutCSC<float>{csc_ptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0};
     a.nu_out = nu;
     a.nuhat_out = nuhat;
     a.obj_part = part + (int64_t)poff * R;
@@ -139,7 +139,7 @@ extern "C" gcp_status gcp_bound_dense_noalloc(int32_t n_layers, const int32_t* d
   c.R = R; c.K = K; c.d0 = dims[0]; c.N = 0;
   c.y0 = (L == 1) ? y_last : y;
   c.x_lo = x_lo; c.x_hi = x_hi;
-  c.csc = CutCSC<float>{csc_ptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0};
+  c.csc = CutCSC<float>{csc_ptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0};
   c.obj_part = part + (int64_t)poff * R;
   concretize<float, float>(st, c);
   poff += (dims[0] + kChunk - 1) / kChunk;
