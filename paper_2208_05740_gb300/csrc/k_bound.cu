@@ -182,49 +182,99 @@ __device__ __forceinline__ void chunk_cuts(const CutCSC<T>& c, int N, int d, int
 }
 
 // Certification variant: round-to-nearest sums with their round-up absolute
-// sums and term counts (for Higham's bound), per kind.
+// sums and term counts (for Higham's bound), per kind. A batch holds 32
+// consecutive entries of the chunk, entry b0 + q on lane q; entries of one
+// (kind, neuron) form a run of lanes, whose first lane adds the run's terms
+// one by one to the warp's shared accumulator of that (kind, neuron), so each
+// sum is the recursive sum of its terms in CSC order (Higham's bound holds for
+// any order). acc: the warp's 3 * 32 sums, then 3 * 32 absolute sums, then
+// 3 * 32 counts, all zero on entry and again on return.
+constexpr int kCertAcc = 3 * 32 * 2 * 8 + 3 * 32 * 4;   // bytes per warp
 template <typename Tg>
 __device__ __forceinline__ void cut_sums_row_cert(const CutCSC<double>& c, const ChunkCuts<double>& cc,
                                                   const Tg* grow, int N, int lane, double (&sum)[3],
-                                                  double (&abs_)[3], int (&cnt_)[3]) {
+                                                  double (&abs_)[3], int (&cnt_)[3], unsigned char* acc) {
+  double* as = reinterpret_cast<double*>(acc);
+  double* aa = as + 96;
+  int* an = reinterpret_cast<int*>(aa + 96);
 #pragma unroll
   for (int q = 0; q < 3; ++q) { sum[q] = 0.0; abs_[q] = 0.0; cnt_[q] = 0; }
+  if (cc.cb == cc.ce) return;
   for (int b0 = cc.cb; b0 < cc.ce; b0 += 32) {
-    int kd = cc.kind, cut = cc.cut;
+    int kd = cc.kind, cut = cc.cut, nl = cc.nrn_lane;
     double cf = cc.coef;
     if (b0 != cc.cb) {
       const int e = b0 + lane;
-      kd = -1; cut = -1; cf = 0.0;
+      kd = -1; cut = -1; cf = 0.0; nl = 0;
       if (e < cc.ce) {
         cut = __ldg(c.cut + e);
         kd = __ldg(c.kind + e);
         cf = __ldg(c.coef + e);
-        if (cut < 0 || cut >= N) { dev_error(2, e, N); cut = -1; kd = -1; }
+        nl = (__ldg(c.nrn + e) & 31);
+        if (cut < 0 || cut >= N || kd < 0 || kd > 2) { dev_error(2, e, N); cut = -1; kd = -1; }
       }
     }
+    // the chunk's neurons are 32-aligned, so the neuron within the chunk is
+    // its index mod 32; lanes without an entry form runs of their own
+    const bool has = cut >= 0 && kd >= 0 && kd <= 2;
+    const int dest = has ? kd * 32 + nl : -1 - lane;   // in [0, 96) for an entry
     double val = 0.0, av = 0.0;
-    if (cut >= 0) {
+    if (has) {
       const double gv = (double)grow[cut];
       val = cf * gv;
       av = __dmul_ru(fabs(cf), fabs(gv));
     }
-    const int lo_e = max(cc.e0, b0), n = max(0, min(cc.e1, b0 + 32) - lo_e);
-    const int mx = __reduce_max_sync(0xffffffffu, n);
-    for (int q = 0; q < mx; ++q) {
-      const int src = (lo_e + q - b0) & 31;
-      const double v = __shfl_sync(0xffffffffu, val, src);
-      const double a = __shfl_sync(0xffffffffu, av, src);
-      const int kq = __shfl_sync(0xffffffffu, kd, src);
-      // selects per kind, not an indexed update: the sums stay in registers
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        const bool hit = q < n && kq == t;
-        sum[t] = hit ? sum[t] + v : sum[t];
-        abs_[t] = hit ? __dadd_ru(abs_[t], a) : abs_[t];
-        cnt_[t] += hit ? 1 : 0;
+    const int prev = __shfl_up_sync(0xffffffffu, dest, 1);
+    const bool cont = lane > 0 && prev == dest;
+    const unsigned cm = __ballot_sync(0xffffffffu, cont);
+    int len = 1;
+    if (lane < 31) {
+      const unsigned after = cm >> (lane + 1), all = 0xffffffffu >> (lane + 1);
+      len += after == all ? 31 - lane : __ffs(~after) - 1;
+    }
+    const int run = cont ? 0 : len;
+    const int maxrun = __reduce_max_sync(0xffffffffu, run);
+    const bool head = run > 0 && has;
+    if (head) {
+      val = as[dest] + val;
+      av = __dadd_ru(aa[dest], av);
+    }
+    for (int q = 1; q < maxrun; ++q) {
+      const double u = __shfl_down_sync(0xffffffffu, val, q);
+      const double ua = __shfl_down_sync(0xffffffffu, av, q);
+      if (q < run) {
+        val += u;
+        av = __dadd_ru(av, ua);
       }
     }
+    if (head) {
+      as[dest] = val;
+      aa[dest] = av;
+      an[dest] += run;
+    }
+    __syncwarp();
   }
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    sum[t] = as[t * 32 + lane];
+    abs_[t] = aa[t * 32 + lane];
+    cnt_[t] = an[t * 32 + lane];
+    as[t * 32 + lane] = 0.0;
+    aa[t * 32 + lane] = 0.0;
+    an[t * 32 + lane] = 0;
+  }
+  __syncwarp();
+}
+
+// zero a warp's certification accumulator
+__device__ __forceinline__ void cert_acc_zero(unsigned char* acc, int lane) {
+  double* as = reinterpret_cast<double*>(acc);
+  int* an = reinterpret_cast<int*>(as + 192);
+#pragma unroll
+  for (int t = 0; t < 6; ++t) as[t * 32 + lane] = 0.0;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) an[t * 32 + lane] = 0;
+  __syncwarp();
 }
 
 // One ascent step on x. Adam (Kingma & Ba): bias-corrected moments m, v are
@@ -1258,6 +1308,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_relax(CertArgs<
   const int slot = lane_split(a.sp, w.s, a.M, a.layer, w.c, w.lane, sign);
   ChunkCuts<double> cc;
   chunk_cuts(a.csc, a.N, a.d, w.c, w.lane, cc);
+  __shared__ __align__(16) unsigned char cacc_all[kWarpsPerBlock * kCertAcc];
+  unsigned char* cacc = cacc_all + (threadIdx.x >> 5) * kCertAcc;
+  cert_acc_zero(cacc, w.lane);
   // row-independent: the neuron's bounds after its split, 1/(u - l) (pi only
   // has to lie in [0, C] for the certificate to hold), and Higham's factors
   // for the sparse sums (the entry counts per kind do not depend on the row)
@@ -1275,7 +1328,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_relax(CertArgs<
     const int64_t r = (int64_t)w.s * a.K + k;
     double sum[3], abs_[3];
     int cnt_[3];
-    cut_sums_row_cert(a.csc, cc, a.gamma + r * a.N, a.N, w.lane, sum, abs_, cnt_);
+    cut_sums_row_cert(a.csc, cc, a.gamma + r * a.N, a.N, w.lane, sum, abs_, cnt_, cacc);
     double part = 0.0;
     if (w.on) {
     // sparse sums in round-to-nearest with their Higham error bounds
@@ -1360,12 +1413,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_conc(int64_t R,
   const int j = w.j;
   ChunkCuts<double> cc;
   chunk_cuts(csc, N, d0, w.c, w.lane, cc);
+  __shared__ __align__(16) unsigned char cacc_all[kWarpsPerBlock * kCertAcc];
+  unsigned char* cacc = cacc_all + (threadIdx.x >> 5) * kCertAcc;
+  cert_acc_zero(cacc, w.lane);
   double gh = 0.0;   // Higham's factor of the input neuron's cut sum (the same for every row)
   for (int k = 0; k < K; ++k) {
     const int64_t r = (int64_t)w.s * K + k;
     double sum[3], abs_[3];
     int cnt_[3];
-    cut_sums_row_cert(csc, cc, gamma + r * N, N, w.lane, sum, abs_, cnt_);
+    cut_sums_row_cert(csc, cc, gamma + r * N, N, w.lane, sum, abs_, cnt_, cacc);
     double part = 0.0;
     if (w.on) {
       const double h = sum[GCP_VAR_X];
