@@ -416,6 +416,14 @@ GCP_API gcp_status gcp_selftest_gemm_f64(int64_t M, int32_t N, int32_t K, const 
  * = none) are also bracketed by CUDA events on their own stream. */
 GCP_API gcp_status gcp_profile_start(const char* kernel_prefix);
 GCP_API gcp_status gcp_profile_stop(void);
+/* While profiling: every launch of the idempotent tensor-core GEMMs
+ * ("gemm_tc_tf32x3", "gemm_tc_bf16": they recompute their output from inputs
+ * they do not write) whose name starts with kernel_prefix is issued twice, in
+ * the same stream, so that the extra device time of a step over the launch
+ * count is the kernel's cost inside the stream, with no event between
+ * launches (NULL or "" = none; gcp_profile_stop clears it). The results do
+ * not change. */
+GCP_API gcp_status gcp_profile_repeat(const char* kernel_prefix);
 /* Totals since gcp_profile_start for the kernel called `name` (NULL = all):
  * launches, device time of the timed launches (ms), flops, bytes. Waits for
  * the timed launches to finish. */

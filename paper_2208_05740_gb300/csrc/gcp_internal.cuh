@@ -280,6 +280,10 @@ std::string take_device_error(cudaStream_t st);
 // Count a launch and, if its kernel is selected, bracket it with CUDA events.
 int prof_begin(cudaStream_t st, const char* name, double flops, double bytes);
 void prof_end(cudaStream_t st, int token);
+// Times a launch of an idempotent kernel (one that recomputes its outputs
+// from inputs it does not write) is issued: 2 while profiling with this
+// kernel selected by gcp_profile_repeat, else 1.
+int prof_repeats(const char* name);
 
 // ---------------------------------------------------------------- launchers
 // GEMM: C[M,N] = A[M,K] * B[N,K]^T, A row m read from row (a_mod ? m % a_mod : m).

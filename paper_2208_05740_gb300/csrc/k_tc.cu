@@ -998,7 +998,8 @@ bool gemm_tc_bf16(cudaStream_t st, int64_t M, int N, int K, const __nv_bfloat16*
     return true;  // reported by the caller's launch status
   int tk = prof_begin(st, "gemm_tc_bf16", flop_scale * 2.0 * M * N * K,
                       ((double)M * K + (double)N * K) * 2 + (double)M * N * 4);
-  const bool ok = launch_tc<0>(st, M, N, K, A, B, nullptr, C);
+  bool ok = true;
+  for (int rep = prof_repeats("gemm_tc_bf16"); rep > 0 && ok; --rep) ok = launch_tc<0>(st, M, N, K, A, B, nullptr, C);
   prof_end(st, tk);
   return ok;
 }
@@ -1011,7 +1012,8 @@ bool gemm_tc_tf32x3(cudaStream_t st, int64_t M, int N, int K, const float* A, co
         reg_check(Blo, (double)N * K * 4, "tc B lo") & reg_check(C, (double)M * N * 4, "tc C")))
     return true;
   int tk = prof_begin(st, "gemm_tc_tf32x3", 2.0 * M * N * K, (double)M * K * 4 + (double)N * K * 8 + (double)M * N * 4);
-  const bool ok = launch_tc<1>(st, M, N, K, A, B, Blo, C);
+  bool ok = true;
+  for (int rep = prof_repeats("gemm_tc_tf32x3"); rep > 0 && ok; --rep) ok = launch_tc<1>(st, M, N, K, A, B, Blo, C);
   prof_end(st, tk);
   return ok;
 }

@@ -29,6 +29,7 @@ std::string g_sel;
 std::vector<Pending> g_pend;
 std::vector<cudaEvent_t> g_pool;
 std::map<std::string, Agg> g_agg;
+std::string g_rep;   // idempotent kernels whose launches are issued twice
 
 cudaEvent_t take_event() {
   if (!g_pool.empty()) {
@@ -76,6 +77,12 @@ void prof_end(cudaStream_t st, int token) {
   if (token < (int)g_pend.size()) cudaEventRecord(g_pend[token].b, st);
 }
 
+int prof_repeats(const char* name) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_on || g_rep.empty()) return 1;
+  return strncmp(name, g_rep.c_str(), g_rep.size()) == 0 ? 2 : 1;
+}
+
 }  // namespace gcp
 
 using namespace gcp;
@@ -95,6 +102,13 @@ gcp_status gcp_profile_stop(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   drain_locked();
   g_on = false;
+  g_rep.clear();
+  return GCP_OK;
+}
+
+gcp_status gcp_profile_repeat(const char* kernel_prefix) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_rep = kernel_prefix ? kernel_prefix : "";
   return GCP_OK;
 }
 

@@ -28,7 +28,7 @@ EXPORTED = ["gcp_create", "gcp_destroy", "gcp_last_error", "gcp_set_stream", "gc
             "gcp_add_cuts", "gcp_duals_create", "gcp_duals_create_multi", "gcp_duals_shape", "gcp_duals_export", "gcp_duals_import",
             "gcp_duals_free", "gcp_duals_theta", "gcp_bound_batch", "gcp_grad_batch", "gcp_optimize_batch", "gcp_bound_device",
             "gcp_branch_picks",
-            "gcp_grad_device", "gcp_bound_dense_noalloc", "gcp_selftest_gemm", "gcp_selftest_gemm_f64", "gcp_profile_start", "gcp_profile_stop", "gcp_profile_query", "gcp_profile_report",
+            "gcp_grad_device", "gcp_bound_dense_noalloc", "gcp_selftest_gemm", "gcp_selftest_gemm_f64", "gcp_profile_start", "gcp_profile_stop", "gcp_profile_repeat", "gcp_profile_query", "gcp_profile_report",
             "gcp_serve_start", "gcp_serve_submit", "gcp_serve_poll", "gcp_serve_wait",
             "gcp_serve_final", "gcp_serve_stop"]
 
@@ -138,6 +138,7 @@ def lib():
             "gcp_selftest_gemm_f64": [I64, I32, I32, pd, pd, pd, C.POINTER(C.c_float), pd],
             "gcp_profile_start": [C.c_char_p],
             "gcp_profile_stop": [],
+            "gcp_profile_repeat": [C.c_char_p],
             "gcp_profile_query": [C.c_char_p, C.POINTER(I64), pd, pd, pd],
             "gcp_profile_report": [C.c_char_p, I64],
             "gcp_serve_start": [P, I32],
@@ -549,6 +550,13 @@ def profile_start(kernel_prefix: Optional[str] = None):
 
 def profile_stop():
     lib().gcp_profile_stop()
+
+
+def profile_repeat(kernel_prefix: Optional[str] = None):
+    """While profiling, issue every launch of the idempotent tensor-core GEMM
+    named by the prefix twice (its in-stream cost = the extra step time over
+    the launch count)."""
+    lib().gcp_profile_repeat(kernel_prefix.encode() if kernel_prefix else None)
 
 
 def profile_query(name: Optional[str] = None):
