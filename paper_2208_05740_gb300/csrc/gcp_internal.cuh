@@ -284,6 +284,10 @@ void prof_end(cudaStream_t st, int token);
 // from inputs it does not write) is issued: 2 while profiling with this
 // kernel selected by gcp_profile_repeat, else 1.
 int prof_repeats(const char* name);
+// Opts kernel `kern` in to `bytes` of dynamic shared memory on the current
+// device (once per kernel, device and size; kernels of the same type are told
+// apart by their address). False if the runtime refuses.
+bool smem_opt_in(const void* kern, size_t bytes);
 
 // ---------------------------------------------------------------- launchers
 // GEMM: C[M,N] = A[M,K] * B[N,K]^T, A row m read from row (a_mod ? m % a_mod : m).

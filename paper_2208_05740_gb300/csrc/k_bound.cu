@@ -27,6 +27,13 @@ constexpr int kWarpsPerBlock = 8;
 // Span kernels: small blocks (two warps) spread the subdomains' warps evenly
 // over the SMs; a block of eight left some SMs with half the warps of others.
 constexpr int kSpanWarps = 2;
+// The relaxation is capped at 72 registers (kEvalMinBlocks blocks of two
+// warps per SM; its shared memory allows 15), so a launch spreads each span's
+// rows over up to kEvalWarpsPerSM warps per SM: on the MLP's 2,048-warp
+// launches, two warps per span at 27 warps per SM instead of 13.5 measured
+// 47.3 against 48.3 ms per step.
+constexpr int kEvalMinBlocks = 14;
+constexpr int64_t kEvalWarpsPerSM = 26;
 
 __device__ __noinline__ void dev_error(unsigned long long code, long long idx, long long lim) {
   if (atomicCAS(&g_dev_err[0], 0ull, code) == 0ull) {
@@ -772,13 +779,13 @@ template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // Shared-memory layout of one warp (in elements of T): fixed buffers, then
-// kStages stages of ND dense rows of 32V, kSpanBatches x 32 gamma values and
+// NS stages of ND dense rows of 32V, kSpanBatches x 32 gamma values and
 // NB x 32 beta values.
-template <int V, int ND, int NB, int NFIX>
+template <int V, int ND, int NB, int NFIX, int NS = kStages>
 struct StageLayout {
   static constexpr int SPAN = 32 * V;
   static constexpr int STAGE = ND * SPAN + kSpanBatches * 32 + NB * 32;
-  static constexpr int WARP = NFIX * SPAN + kStages * STAGE;
+  static constexpr int WARP = NFIX * SPAN + NS * STAGE;
 };
 
 // ------------------------------------------------------------------ eval
@@ -786,7 +793,7 @@ struct StageLayout {
 // own (App. A's closing remark), read from a.theta, or written there from
 // Lemma A.1's closed form when a.theta_init is set.
 template <typename T, typename Top, int V, bool PI>
-__global__ void __launch_bounds__(kSpanWarps * 32) k_relax_eval(RelaxArgs<T, Top> a) {
+__global__ void __launch_bounds__(kSpanWarps * 32, kEvalMinBlocks) k_relax_eval(RelaxArgs<T, Top> a) {
   using Lay = StageLayout<V, 2, V, 3>;   // dense: y, alpha; fixed: acc
   constexpr int SPAN = Lay::SPAN, NS = kStages;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1189,9 +1196,9 @@ __global__ void __launch_bounds__(kSpanWarps * 32) k_concretize(ConcArgs<T, Top>
 }
 
 // dynamic shared memory of one block of the span kernels
-template <typename T, int V, int ND, int NB, int NFIX>
+template <typename T, int V, int ND, int NB, int NFIX, int NS = kStages>
 constexpr size_t span_smem() {
-  return (size_t)kSpanWarps * StageLayout<V, ND, NB, NFIX>::WARP * sizeof(T);
+  return (size_t)kSpanWarps * StageLayout<V, ND, NB, NFIX, NS>::WARP * sizeof(T);
 }
 
 // g[r] = c_k^T b^(L) - gamma_r^T d + sum of the partials. A warp takes 32
@@ -1534,29 +1541,25 @@ inline int span_vec(int d, int max_span4, bool al16_all, bool al8_all) {
 // GPU mostly idle (a small batch, where one warp's K rows in sequence are the
 // kernel's latency) spreads each span's rows over gridDim.z warps instead,
 // enough to bring the launch near 8 warps per SM.
-inline int row_split(int64_t S, int K, int spans) {
-  const int64_t warps = S * spans, target = 152 * 8;
+inline int row_split(int64_t S, int K, int spans, int64_t target = 152 * 8) {
+  const int64_t warps = S * spans;
   if (warps >= target || K <= 1) return 1;
   return (int)std::min<int64_t>(K, (target + warps - 1) / warps);
 }
 inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 inline bool al8(const void* p) { return ((uintptr_t)p & 7) == 0; }
 
-// Launch a span kernel with its dynamic shared memory (the opt-in above 48 KB
-// is set once per kernel).
+// Launch a span kernel with its dynamic shared memory (opted in above 48 KB).
 template <typename Kern, typename Args>
 void launch_span(Kern kern, size_t smem, dim3 grid, cudaStream_t st, const Args& a) {
-  static bool attr = false;   // one static per kernel instantiation
-  if (!attr) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  smem_opt_in(reinterpret_cast<const void*>(kern), smem);
   launch_pdl(kern, grid, dim3(kSpanWarps * 32), smem, st, a);
 }
-inline dim3 span_blocks(int64_t R, int K, int d, int V) {
+inline dim3 span_blocks(int64_t R, int K, int d, int V, int64_t target = 152 * 8) {
   const int64_t S = R / K;
   const int spans = (d + 32 * V - 1) / (32 * V);
-  return dim3((unsigned)((S + kSpanWarps - 1) / kSpanWarps), (unsigned)spans, (unsigned)row_split(S, K, spans));
+  return dim3((unsigned)((S + kSpanWarps - 1) / kSpanWarps), (unsigned)spans,
+              (unsigned)row_split(S, K, spans, target));
 }
 
 // host-side extent checks shared by the launchers
@@ -1575,17 +1578,19 @@ inline bool chk_csc(const CutCSC<T>& c, int d) {
 
 template <int V, typename T, typename Top>
 void launch_eval(cudaStream_t st, const RelaxArgs<T, Top>& a) {
+  const dim3 g = span_blocks(a.R, a.K, a.d, V, 152 * kEvalWarpsPerSM);
   if (a.theta)
-    launch_span(k_relax_eval<T, Top, V, true>, span_smem<T, V, 2, V, 3>(), span_blocks(a.R, a.K, a.d, V), st, a);
+    launch_span(k_relax_eval<T, Top, V, true>, span_smem<T, V, 2, V, 3>(), g, st, a);
   else
-    launch_span(k_relax_eval<T, Top, V, false>, span_smem<T, V, 2, V, 3>(), span_blocks(a.R, a.K, a.d, V), st, a);
+    launch_span(k_relax_eval<T, Top, V, false>, span_smem<T, V, 2, V, 3>(), g, st, a);
 }
 template <int V, typename T, typename Top>
 void launch_adj(cudaStream_t st, const AdjArgs<T, Top>& a) {
+  const dim3 g = span_blocks(a.R, a.K, a.d, V);
   if (a.theta)
-    launch_span(k_relax_adj<T, Top, V, true>, span_smem<T, V, 5, 0, 6>(), span_blocks(a.R, a.K, a.d, V), st, a);
+    launch_span(k_relax_adj<T, Top, V, true>, span_smem<T, V, 5, 0, 6>(), g, st, a);
   else
-    launch_span(k_relax_adj<T, Top, V, false>, span_smem<T, V, 5, 0, 6>(), span_blocks(a.R, a.K, a.d, V), st, a);
+    launch_span(k_relax_adj<T, Top, V, false>, span_smem<T, V, 5, 0, 6>(), g, st, a);
 }
 
 // Algorithmic bytes per launch: every per-(row, neuron) array read or written
@@ -1724,7 +1729,7 @@ void gather_gamma(cudaStream_t st, const GatherArgs<T>& a) {
   if (a.R <= 0 || (a.N <= 0 && nb == 0)) return;
   const double tb = sizeof(T), NR = (double)a.N * a.R, MR = (double)nb;
   const bool m0 = a.st.mode == 0, m2 = a.st.mode == 2;
-  if (!(reg_check(a.cut_ptr, a.N > 0 ? (a.N + 1) * 4.0 : 0.0, "cut ptr") & reg_check(a.pos, a.nnz * 4.0, "cut pos") &
+  if (!(reg_check(a.cut_ptr, a.N > 0 ? (a.N + 1) * 4.0 : 0.0, "cut ptr") & reg_check(a.pos, a.nnz * 4.0, "cut pos") & 
         reg_check(a.E, (double)a.nnz * a.R * tb, "E") &
         reg_check(a.d, a.N * tb, "d") & reg_check(a.seed, a.seed ? a.R * tb : 0.0, "seed") &
         reg_check(a.gamma, NR * tb, "gamma") & reg_check(a.g_gamma, m0 ? NR * tb : 0.0, "g_gamma") &

@@ -325,6 +325,100 @@ __global__ void __launch_bounds__(256) k_conv_T_row(int64_t R, LayerGeom g, cons
   }
 }
 
+// Float form of k_conv_T_row with two output pixels per work item: adjacent
+// pixels of one phase row (the same taps, source columns ow and ow + 1) share
+// each weight load, and the weights are staged as [c_out][k][k][4 * nct] so
+// one 16-byte load gives a tile's four channels. Each output adds the same
+// terms in the same order as k_conv_T_row (a skipped tap is a predicate), so
+// every output is the same number.
+constexpr int kConvTP = 2;   // pixels per work item
+template <typename Tin>
+__global__ void __launch_bounds__(256) k_conv_T_row2(int64_t R, LayerGeom g, const Tin* __restrict__ W,
+                                                     const Tin* __restrict__ in, float* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char conv_sm[];
+  const int s = g.stride, HW = g.h_in * g.w_in, HWo = g.h_out * g.w_out, kk = g.k * g.k;
+  const int nct = (g.c_in + kConvCT - 1) / kConvCT, C4 = nct * kConvCT;
+  float* ws = reinterpret_cast<float*>(conv_sm);   // [c_out][k][k][C4]
+  float* src = ws + (size_t)g.c_out * kk * C4;     // [d_out]
+  for (int i = threadIdx.x; i < g.c_out * kk * C4; i += blockDim.x) {
+    const int c = i % C4, tap = (i / C4) % kk, o = i / (C4 * kk);
+    ws[i] = c < g.c_in ? load_as<float>(W + (int64_t)o * g.c_in * kk + c * kk + tap) : 0.f;
+  }
+  // work items per channel tile: every phase's rows in groups of kConvTP pixels
+  int per_tile = 0;
+  for (int f = 0; f < s * s; ++f) {
+    const int ph = f / s, pw = f - ph * s;
+    const int Hf = ph < g.h_in ? (g.h_in - ph + s - 1) / s : 0, Wf = pw < g.w_in ? (g.w_in - pw + s - 1) / s : 0;
+    per_tile += Hf * ((Wf + kConvTP - 1) / kConvTP);
+  }
+  const int items = nct * per_tile;
+  for (int64_t r = blockIdx.x; r < R; r += gridDim.x) {
+    __syncthreads();   // the previous row's items are done with src
+    for (int i = threadIdx.x; i < g.d_out; i += blockDim.x) src[i] = load_as<float>(in + r * g.d_out + i);
+    __syncthreads();
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      const int ct = it / per_tile, c0 = ct * kConvCT;
+      int q = it - ct * per_tile;
+      int ph = 0, pw = 0, Wf = 1, G = 1;
+      for (int f = 0; f < s * s; ++f) {
+        ph = f / s;
+        pw = f - ph * s;
+        const int Hf = ph < g.h_in ? (g.h_in - ph + s - 1) / s : 0;
+        Wf = pw < g.w_in ? (g.w_in - pw + s - 1) / s : 0;
+        G = (Wf + kConvTP - 1) / kConvTP;
+        if (q < Hf * G) break;
+        q -= Hf * G;
+      }
+      const int i = q / G, j0 = (q - i * G) * kConvTP;
+      const int ih = ph + s * i, iw0 = pw + s * j0;
+      const int rh = (ph + g.pad) % s, rw = (pw + g.pad) % s;
+      float acc[kConvTP][kConvCT];
+#pragma unroll
+      for (int p = 0; p < kConvTP; ++p)
+#pragma unroll
+        for (int t = 0; t < kConvCT; ++t) acc[p][t] = 0.f;
+      for (int kh = rh; kh < g.k; kh += s) {
+        const int th = ih + g.pad - kh;
+        if (th < 0) break;
+        const int oh = th / s;
+        if (oh >= g.h_out) continue;
+        for (int kw = rw; kw < g.k; kw += s) {
+          // pixel p: iw = iw0 + s p, source column (iw + pad - kw) / s
+          const int tw0 = iw0 + g.pad - kw;
+          bool ok[kConvTP];
+          int xo[kConvTP];
+#pragma unroll
+          for (int p = 0; p < kConvTP; ++p) {
+            const int tw = tw0 + s * p;
+            ok[p] = j0 + p < Wf && tw >= 0 && tw / s < g.w_out;
+            xo[p] = ok[p] ? oh * g.w_out + tw / s : 0;
+          }
+          const float* wt = ws + (kh * g.k + kw) * C4 + c0;
+          for (int o = 0; o < g.c_out; ++o) {
+            const float4 w4 = *reinterpret_cast<const float4*>(wt + (size_t)o * kk * C4);
+            const float wv[kConvCT] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int p = 0; p < kConvTP; ++p) {
+              if (!ok[p]) continue;
+              const float v = src[o * HWo + xo[p]];
+#pragma unroll
+              for (int t = 0; t < kConvCT; ++t) acc[p][t] = fmaf(wv[t], v, acc[p][t]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < kConvTP; ++p) {
+        if (j0 + p >= Wf) continue;
+        float* orow = out + r * g.d_in + ih * g.w_in + iw0 + s * p;
+#pragma unroll
+        for (int t = 0; t < kConvCT; ++t)
+          if (c0 + t < g.c_in) orow[(int64_t)(c0 + t) * HW] = acc[p][t];
+      }
+    }
+  }
+}
+
 template <typename Tin, typename Tacc>
 __global__ void __launch_bounds__(256) k_conv_fwd_row(int64_t R, LayerGeom g, const Tin* __restrict__ W,
                                                       const Tin* __restrict__ in, Tacc* __restrict__ out) {
@@ -368,21 +462,76 @@ __global__ void __launch_bounds__(256) k_conv_fwd_row(int64_t R, LayerGeom g, co
   }
 }
 
+// Float form of k_conv_fwd_row with two adjacent output pixels (columns ow and
+// ow + 1 of one output row) per work item sharing each weight load, the
+// weights staged as [c_in][k][k][4 * nft] (one 16-byte load per tap gives a
+// tile's four output channels). The same terms are added in the same order
+// as k_conv_fwd_row, so every output is the same number.
+constexpr int kConvFP = 2;   // output pixels per work item
+template <typename Tin>
+__global__ void __launch_bounds__(256) k_conv_fwd_row2(int64_t R, LayerGeom g, const Tin* __restrict__ W,
+                                                       const Tin* __restrict__ in, float* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char conv_sm[];
+  const int HWo = g.h_out * g.w_out, kk = g.k * g.k;
+  const int nft = (g.c_out + kConvFT - 1) / kConvFT, O4 = nft * kConvFT;
+  float* ws = reinterpret_cast<float*>(conv_sm);   // [c_in][k][k][O4]
+  float* src = ws + (size_t)g.c_in * kk * O4;      // [d_in]
+  for (int i = threadIdx.x; i < g.c_in * kk * O4; i += blockDim.x) {
+    const int o = i % O4, tap = (i / O4) % kk, c = i / (O4 * kk);
+    ws[i] = o < g.c_out ? load_as<float>(W + (int64_t)o * g.c_in * kk + c * kk + tap) : 0.f;
+  }
+  const int G = (g.w_out + kConvFP - 1) / kConvFP;   // pixel groups per output row
+  const int per_tile = g.h_out * G, items = nft * per_tile;
+  for (int64_t r = blockIdx.x; r < R; r += gridDim.x) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.d_in; i += blockDim.x) src[i] = load_as<float>(in + r * g.d_in + i);
+    __syncthreads();
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      const int ft = it / per_tile, o0 = ft * kConvFT;
+      const int q = it - ft * per_tile, oh = q / G, ow0 = (q - oh * G) * kConvFP;
+      float acc[kConvFP][kConvFT];
+#pragma unroll
+      for (int p = 0; p < kConvFP; ++p)
+#pragma unroll
+        for (int t = 0; t < kConvFT; ++t) acc[p][t] = 0.f;
+      for (int c = 0; c < g.c_in; ++c)
+        for (int kh = 0; kh < g.k; ++kh) {
+          const int ih = oh * g.stride + kh - g.pad;
+          if (ih < 0 || ih >= g.h_in) continue;
+          const float* srow = src + (c * g.h_in + ih) * g.w_in;
+          const float* wt = ws + ((size_t)c * kk + kh * g.k) * O4 + o0;
+          for (int kw = 0; kw < g.k; ++kw) {
+            const float4 w4 = *reinterpret_cast<const float4*>(wt + kw * O4);
+            const float wv[kConvFT] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int p = 0; p < kConvFP; ++p) {
+              const int iw = (ow0 + p) * g.stride + kw - g.pad;
+              if (ow0 + p >= g.w_out || iw < 0 || iw >= g.w_in) continue;
+              const float v = srow[iw];
+#pragma unroll
+              for (int t = 0; t < kConvFT; ++t) acc[p][t] = fmaf(wv[t], v, acc[p][t]);
+            }
+          }
+        }
+#pragma unroll
+      for (int p = 0; p < kConvFP; ++p) {
+        if (ow0 + p >= g.w_out) continue;
+        float* orow = out + r * g.d_out + oh * g.w_out + ow0 + p;
+#pragma unroll
+        for (int t = 0; t < kConvFT; ++t)
+          if (o0 + t < g.c_out) orow[(int64_t)(o0 + t) * HWo] = acc[p][t];
+      }
+    }
+  }
+}
+
 // Dynamic shared memory of a row-staged convolution, opted in once per kernel
 // (false: the row does not fit; use the tiled kernel).
-constexpr size_t kConvRowSmem = 96 * 1024;
+constexpr size_t kConvRowSmem = 112 * 1024;   // two blocks per SM
 template <typename Kern>
 bool conv_row_smem(Kern kern, size_t bytes) {
   if (bytes > kConvRowSmem) return false;
-  static bool attr = false;   // one static per kernel instantiation
-  if (!attr) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvRowSmem) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
-    attr = true;
-  }
-  return true;
+  return smem_opt_in(reinterpret_cast<const void*>(kern), bytes);
 }
 
 // The transposed 1x1 convolution without padding (a residual block's
@@ -490,7 +639,12 @@ void conv_fwd(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, cons
   snprintf(nm, sizeof nm, "conv_fwd_%s", tname<Tin>());
   int tk = prof_begin(st, nm, 2.0 * R * conv_macs(g), (double)R * (g.d_in * sizeof(Tin) + g.d_out * sizeof(Tacc)));
   const size_t row_bytes = ((size_t)g.d_in + (size_t)g.c_out * g.c_in * g.k * g.k) * sizeof(Tacc);
-  if (conv_row_smem(k_conv_fwd_row<Tin, Tacc>, row_bytes))
+  const size_t row2_bytes =
+      ((size_t)g.d_in + (size_t)g.c_in * g.k * g.k * (size_t)(((g.c_out + kConvFT - 1) / kConvFT) * kConvFT)) * 4;
+  if (std::is_same<Tacc, float>::value && conv_row_smem(k_conv_fwd_row2<Tin>, row2_bytes))
+    k_conv_fwd_row2<Tin><<<(unsigned)std::min<int64_t>(R, 152 * 8), 256, row2_bytes, st>>>(
+        R, g, W, in, reinterpret_cast<float*>(out));
+  else if (conv_row_smem(k_conv_fwd_row<Tin, Tacc>, row_bytes))
     k_conv_fwd_row<Tin, Tacc><<<(unsigned)std::min<int64_t>(R, 152 * 8), 256, row_bytes, st>>>(R, g, W, in, out);
   else
     k_conv_fwd_tile<Tin, Tacc><<<grid_for(R * (int64_t)((g.c_out + kConvFT - 1) / kConvFT) * g.h_out * g.w_out, 256),
@@ -511,6 +665,13 @@ void conv_T(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const 
   int tk = prof_begin(st, nm, 2.0 * R * conv_macs(g), (double)R * (g.d_out * sizeof(Tin) + g.d_in * sizeof(Tacc)));
   if (g.k == 1 && g.pad == 0)
     k_conv_T_1x1<Tin, Tacc, false><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, nullptr, nullptr, nullptr);
+  else if (std::is_same<Tacc, float>::value &&
+           conv_row_smem(k_conv_T_row2<Tin>, ((size_t)g.d_out + (size_t)g.c_out * g.k * g.k *
+                                              (size_t)(((g.c_in + kConvCT - 1) / kConvCT) * kConvCT)) * 4))
+    k_conv_T_row2<Tin><<<(unsigned)std::min<int64_t>(R, 152 * 8), 256,
+                         ((size_t)g.d_out + (size_t)g.c_out * g.k * g.k *
+                          (size_t)(((g.c_in + kConvCT - 1) / kConvCT) * kConvCT)) * 4, st>>>(
+        R, g, W, in, reinterpret_cast<float*>(out));
   else if (conv_row_smem(k_conv_T_row<Tin, Tacc>,
                          ((size_t)g.d_out + (size_t)g.c_out * g.c_in * g.k * g.k) * sizeof(Tacc)))
     k_conv_T_row<Tin, Tacc><<<(unsigned)std::min<int64_t>(R, 152 * 8), 256,

@@ -77,6 +77,23 @@ void prof_end(cudaStream_t st, int token) {
   if (token < (int)g_pend.size()) cudaEventRecord(g_pend[token].b, st);
 }
 
+bool smem_opt_in(const void* kern, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> done;
+  if (bytes <= 48 * 1024) return true;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& have = done[{dev, kern}];
+  if (have >= bytes) return true;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  have = bytes;
+  return true;
+}
+
 int prof_repeats(const char* name) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_on || g_rep.empty()) return 1;
