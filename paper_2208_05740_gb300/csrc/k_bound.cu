@@ -1526,7 +1526,9 @@ const char* tsfx() { return sizeof(T) == 8 ? "f64" : "f32"; }
 // registers (later batches reread their entries from memory every row): then
 // 2 (8-byte vectors, 64-neuron spans) when the width is even; else 1. The cut
 // sums add each destination's entries in CSC order whatever the span width,
-// so the choice changes no result.
+// so the choice changes no dual, gradient or certified bound; only the float
+// chain's own objective partials (one per span, summed over its lanes) are
+// added in a tree that follows the span width.
 template <typename T>
 inline bool span_v4(int d) { return sizeof(T) == 4 && d % 4 == 0; }
 template <typename T>
