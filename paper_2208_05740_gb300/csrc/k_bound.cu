@@ -1330,6 +1330,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_relax(CertArgs<
     }
   }
   const double inv_ul = hi0 > lo0 ? 1.0 / (hi0 - lo0) : 0.0;
+  // whether the warp's neurons fall in more than one class (inactive,
+  // active, unstable): row-independent, warp-uniform
+  const unsigned cls_bits = w.on ? (hi0 <= 0.0 ? 1u : (lo0 >= 0.0 ? 2u : 4u)) : 0u;
+  const unsigned present = __reduce_or_sync(0xffffffffu, cls_bits);
+  const bool mixed = (present & (present - 1u)) != 0u;
   double gt = 0.0, gg_n = 0.0, gs_n = 0.0;
   for (int k = 0; k < a.K; ++k) {
     const int64_t r = (int64_t)w.s * a.K + k;
@@ -1365,18 +1370,19 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_relax(CertArgs<
     const double g_lo = __dsub_rd(gg, eg), g_hi = __dadd_ru(gg, eg);
     const double s_lo = __dsub_rd(sq, es);
     double nu;
-    if (hi <= 0.0) {
-      // inactive: xhat = z = 0; Lagrangian term (nu + t) x over x in [lo, hi]
-      nu = -t;
-      part = box_min_rd(__dadd_rd(nu, t_lo), __dadd_ru(nu, t_hi), lo, hi);
-    } else if (lo >= 0.0) {
-      // active: xhat = x, z = 1; term (nu + t - y + g) x plus s
-      nu = nh - t;
-      const double klo = __dadd_rd(__dadd_rd(__dadd_rd(nu, t_lo), -y_hi), g_lo);
-      const double khi = __dadd_ru(__dadd_ru(__dadd_ru(nu, t_hi), -y_lo), g_hi);
-      part = __dadd_rd(box_min_rd(klo, khi, lo, hi), s_lo);
-    } else {
-      // unstable: explicit duals pi, gamma_r = C - pi, tau, mu = M - tau (all >= 0)
+    if (mixed) {
+      // One formula for the three classes, the class choosing its terms by
+      // selects: a warp's lanes usually mix classes, and FP64 instructions,
+      // not memory, set this pass's time. Per class the result is the same
+      // number as the case-by-case form: the terms a class does not have are
+      // exact zeros added with directed rounding.
+      //   inactive (xhat = z = 0): (nu + t) x over x in [lo, hi], nu = -t;
+      //   active (xhat = x, z = 1): (nu + t - y + g) x plus s, nu = nuhat - t;
+      //   unstable: explicit duals pi, gamma_r = C - pi, tau, mu = M - tau (all
+      //   >= 0), nu = pi - tau - t; x: (nu + t + tau - pi) x over [lo, hi];
+      //   xhat: (-y + g - mu - tau + gamma_r + pi) xhat over [0, hi];
+      //   z: (-hi gamma_r - lo pi + s) z over [0, 1]; plus pi lo.
+      const bool inact = hi <= 0.0, act = !inact && lo >= 0.0, unst = !inact && !act;
       const double C = fmax(nh, 0.0), Mm = fmax(-nh, 0.0);
       const double p0 = (hi * C - sq) * inv_ul;
       // Lemma A.1's pi, or theta * C for directly optimised duals; either is
@@ -1386,19 +1392,56 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_certify_relax(CertArgs<
       const double al = fmin(fmax((double)a.alpha[r * a.d + j], 0.0), 1.0);
       const double tau = al * Mm;
       const double mu = Mm - tau;
-      nu = (pi - tau) - t;
-      // x: (nu + t + tau - pi) x over [lo, hi]
-      const double kx_lo = __dsub_rd(__dadd_rd(__dadd_rd(nu, t_lo), tau), pi);
-      const double kx_hi = __dsub_ru(__dadd_ru(__dadd_ru(nu, t_hi), tau), pi);
-      // xhat: (-y + g - mu - tau + gr + pi) xhat over [0, hi]
+      nu = inact ? -t : (act ? nh : pi - tau) - t;
+      // x's coefficient (nu + t) + A + B, rounded down and up
+      const double A_lo = act ? -y_hi : (unst ? tau : 0.0), A_hi = act ? -y_lo : (unst ? tau : 0.0);
+      const double B_lo = act ? g_lo : (unst ? -pi : 0.0), B_hi = act ? g_hi : (unst ? -pi : 0.0);
+      const double k_lo = __dadd_rd(__dadd_rd(__dadd_rd(nu, t_lo), A_lo), B_lo);
+      const double k_hi = __dadd_ru(__dadd_ru(__dadd_ru(nu, t_hi), A_hi), B_hi);
       double kh_lo = __dadd_rd(-y_hi, g_lo);
       kh_lo = __dadd_rd(__dsub_rd(__dsub_rd(kh_lo, mu), tau), __dadd_rd(gr, pi));
-      // z: (-hi gr - lo pi + s) z over [0, 1]
       const double kz_lo = __dadd_rd(__dadd_rd(-__dmul_ru(hi, gr), -__dmul_ru(lo, pi)), s_lo);
-      part = box_min_rd(kx_lo, kx_hi, lo, hi);
-      part = __dadd_rd(part, fmin(0.0, __dmul_rd(kh_lo, hi)));
-      part = __dadd_rd(part, fmin(0.0, kz_lo));
-      part = __dadd_rd(part, __dmul_rd(pi, lo));
+      part = box_min_rd(k_lo, k_hi, lo, hi);
+      part = __dadd_rd(part, act ? s_lo : (unst ? fmin(0.0, __dmul_rd(kh_lo, hi)) : 0.0));
+      part = __dadd_rd(part, unst ? fmin(0.0, kz_lo) : 0.0);
+      part = __dadd_rd(part, unst ? __dmul_rd(pi, lo) : 0.0);
+    } else {
+      // every lane of the warp in one class: that class's terms only
+      if (hi <= 0.0) {
+        // inactive: xhat = z = 0; Lagrangian term (nu + t) x over x in [lo, hi]
+        nu = -t;
+        part = box_min_rd(__dadd_rd(nu, t_lo), __dadd_ru(nu, t_hi), lo, hi);
+      } else if (lo >= 0.0) {
+        // active: xhat = x, z = 1; term (nu + t - y + g) x plus s
+        nu = nh - t;
+        const double klo = __dadd_rd(__dadd_rd(__dadd_rd(nu, t_lo), -y_hi), g_lo);
+        const double khi = __dadd_ru(__dadd_ru(__dadd_ru(nu, t_hi), -y_lo), g_hi);
+        part = __dadd_rd(box_min_rd(klo, khi, lo, hi), s_lo);
+      } else {
+        // unstable: explicit duals pi, gamma_r = C - pi, tau, mu = M - tau (all >= 0)
+        const double C = fmax(nh, 0.0), Mm = fmax(-nh, 0.0);
+        const double p0 = (hi * C - sq) * inv_ul;
+        // Lemma A.1's pi, or theta * C for directly optimised duals; either is
+        // in [0, C] (theta <= 1 and rounding is monotone), so gr >= 0
+        const double pi = a.theta ? fmin(fmax((double)a.theta[r * a.d + j], 0.0), 1.0) * C : fmin(fmax(p0, 0.0), C);
+        const double gr = C - pi;
+        const double al = fmin(fmax((double)a.alpha[r * a.d + j], 0.0), 1.0);
+        const double tau = al * Mm;
+        const double mu = Mm - tau;
+        nu = (pi - tau) - t;
+        // x: (nu + t + tau - pi) x over [lo, hi]
+        const double kx_lo = __dsub_rd(__dadd_rd(__dadd_rd(nu, t_lo), tau), pi);
+        const double kx_hi = __dsub_ru(__dadd_ru(__dadd_ru(nu, t_hi), tau), pi);
+        // xhat: (-y + g - mu - tau + gr + pi) xhat over [0, hi]
+        double kh_lo = __dadd_rd(-y_hi, g_lo);
+        kh_lo = __dadd_rd(__dsub_rd(__dsub_rd(kh_lo, mu), tau), __dadd_rd(gr, pi));
+        // z: (-hi gr - lo pi + s) z over [0, 1]
+        const double kz_lo = __dadd_rd(__dadd_rd(-__dmul_ru(hi, gr), -__dmul_ru(lo, pi)), s_lo);
+        part = box_min_rd(kx_lo, kx_hi, lo, hi);
+        part = __dadd_rd(part, fmin(0.0, __dmul_rd(kh_lo, hi)));
+        part = __dadd_rd(part, fmin(0.0, kz_lo));
+        part = __dadd_rd(part, __dmul_rd(pi, lo));
+      }
     }
     part = __dadd_rd(part, __dmul_rd(-nu, a.bias[j]));
     a.nu_out[r * a.d + j] = nu;
