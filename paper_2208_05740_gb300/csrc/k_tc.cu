@@ -194,7 +194,10 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
 template <int KIND>
 struct TcCfg {
   static constexpr int kStageBytes = KIND == 0 ? kTileA + kTileB : kTileA + 2 * kTileB;
-  static constexpr int kStages = 4;
+  // three-pass tf32: three stages (144 KB) leave room beside a CTA for the
+  // blocks of the next span kernel to start early (47.0 vs 47.4 ms per MLP
+  // step); the bf16 kernel keeps four (three measured slower)
+  static constexpr int kStages = KIND == 1 ? 3 : 4;
   static constexpr int kKElems = KIND == 0 ? 64 : 32;  // K elements per 128-byte row
   static constexpr uint32_t kFormat = KIND == 0 ? 1u : 2u;  // bf16 / tf32
   static constexpr int kAccCols = BN;
