@@ -325,6 +325,37 @@ __global__ void __launch_bounds__(256) k_conv_T_row(int64_t R, LayerGeom g, cons
   }
 }
 
+// Row staging of the float row kernels: with DB the next row's source map
+// streams into a second buffer (16-byte cp.async) while the block computes
+// on the current one; the row length is a multiple of 4 floats and the rows
+// are 16-byte aligned (checked by the launcher).
+__device__ __forceinline__ void row_async(float* dst, const float* src, int n) {
+  for (int i = threadIdx.x * 4; i < n; i += blockDim.x * 4) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst + i);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src + i) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void row_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+template <bool DB, typename Tin>
+__device__ __forceinline__ float* row_stage(float* buf, const Tin* in, int64_t r, int64_t R, int n, int iter) {
+  if constexpr (DB) {
+    float* cur = buf + (iter & 1) * n;
+    __syncthreads();   // the previous row's items are done with the other buffer
+    const int64_t rn = r + gridDim.x;
+    if (rn < R) row_async(buf + ((iter + 1) & 1) * n, reinterpret_cast<const float*>(in) + rn * n, n);
+    else asm volatile("cp.async.commit_group;\n" ::: "memory");
+    row_async_wait_prev();   // this row's copies (committed one iteration ago) are done
+    __syncthreads();
+    return cur;
+  } else {
+    __syncthreads();   // the previous row's items are done with buf
+    for (int i = threadIdx.x; i < n; i += blockDim.x) buf[i] = load_as<float>(in + r * n + i);
+    __syncthreads();
+    return buf;
+  }
+}
+
 // Float form of k_conv_T_row with two output pixels per work item: adjacent
 // pixels of one phase row (the same taps, source columns ow and ow + 1) share
 // each weight load, and the weights are staged as [c_out][k][k][4 * nct] so
@@ -332,14 +363,14 @@ __global__ void __launch_bounds__(256) k_conv_T_row(int64_t R, LayerGeom g, cons
 // terms in the same order as k_conv_T_row (a skipped tap is a predicate), so
 // every output is the same number.
 constexpr int kConvTP = 2;   // pixels per work item
-template <typename Tin>
+template <typename Tin, bool DB>
 __global__ void __launch_bounds__(256) k_conv_T_row2(int64_t R, LayerGeom g, const Tin* __restrict__ W,
                                                      const Tin* __restrict__ in, float* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char conv_sm[];
   const int s = g.stride, HW = g.h_in * g.w_in, HWo = g.h_out * g.w_out, kk = g.k * g.k;
   const int nct = (g.c_in + kConvCT - 1) / kConvCT, C4 = nct * kConvCT;
   float* ws = reinterpret_cast<float*>(conv_sm);   // [c_out][k][k][C4]
-  float* src = ws + (size_t)g.c_out * kk * C4;     // [d_out]
+  float* src = ws + (size_t)g.c_out * kk * C4;     // [d_out], twice with DB
   for (int i = threadIdx.x; i < g.c_out * kk * C4; i += blockDim.x) {
     const int c = i % C4, tap = (i / C4) % kk, o = i / (C4 * kk);
     ws[i] = c < g.c_in ? load_as<float>(W + (int64_t)o * g.c_in * kk + c * kk + tap) : 0.f;
@@ -352,10 +383,10 @@ __global__ void __launch_bounds__(256) k_conv_T_row2(int64_t R, LayerGeom g, con
     per_tile += Hf * ((Wf + kConvTP - 1) / kConvTP);
   }
   const int items = nct * per_tile;
-  for (int64_t r = blockIdx.x; r < R; r += gridDim.x) {
-    __syncthreads();   // the previous row's items are done with src
-    for (int i = threadIdx.x; i < g.d_out; i += blockDim.x) src[i] = load_as<float>(in + r * g.d_out + i);
-    __syncthreads();
+  if (DB && blockIdx.x < R) row_async(src, reinterpret_cast<const float*>(in) + blockIdx.x * (int64_t)g.d_out, g.d_out);
+  int iter = 0;
+  for (int64_t r = blockIdx.x; r < R; r += gridDim.x, ++iter) {
+    const float* srcr = row_stage<DB>(src, in, r, R, g.d_out, iter);
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
       const int ct = it / per_tile, c0 = ct * kConvCT;
       int q = it - ct * per_tile;
@@ -400,7 +431,7 @@ __global__ void __launch_bounds__(256) k_conv_T_row2(int64_t R, LayerGeom g, con
 #pragma unroll
             for (int p = 0; p < kConvTP; ++p) {
               if (!ok[p]) continue;
-              const float v = src[o * HWo + xo[p]];
+              const float v = srcr[o * HWo + xo[p]];
 #pragma unroll
               for (int t = 0; t < kConvCT; ++t) acc[p][t] = fmaf(wv[t], v, acc[p][t]);
             }
@@ -468,24 +499,24 @@ __global__ void __launch_bounds__(256) k_conv_fwd_row(int64_t R, LayerGeom g, co
 // tile's four output channels). The same terms are added in the same order
 // as k_conv_fwd_row, so every output is the same number.
 constexpr int kConvFP = 2;   // output pixels per work item
-template <typename Tin>
+template <typename Tin, bool DB>
 __global__ void __launch_bounds__(256) k_conv_fwd_row2(int64_t R, LayerGeom g, const Tin* __restrict__ W,
                                                        const Tin* __restrict__ in, float* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char conv_sm[];
   const int HWo = g.h_out * g.w_out, kk = g.k * g.k;
   const int nft = (g.c_out + kConvFT - 1) / kConvFT, O4 = nft * kConvFT;
   float* ws = reinterpret_cast<float*>(conv_sm);   // [c_in][k][k][O4]
-  float* src = ws + (size_t)g.c_in * kk * O4;      // [d_in]
+  float* src = ws + (size_t)g.c_in * kk * O4;      // [d_in], twice with DB
   for (int i = threadIdx.x; i < g.c_in * kk * O4; i += blockDim.x) {
     const int o = i % O4, tap = (i / O4) % kk, c = i / (O4 * kk);
     ws[i] = o < g.c_out ? load_as<float>(W + (int64_t)o * g.c_in * kk + c * kk + tap) : 0.f;
   }
   const int G = (g.w_out + kConvFP - 1) / kConvFP;   // pixel groups per output row
   const int per_tile = g.h_out * G, items = nft * per_tile;
-  for (int64_t r = blockIdx.x; r < R; r += gridDim.x) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < g.d_in; i += blockDim.x) src[i] = load_as<float>(in + r * g.d_in + i);
-    __syncthreads();
+  if (DB && blockIdx.x < R) row_async(src, reinterpret_cast<const float*>(in) + blockIdx.x * (int64_t)g.d_in, g.d_in);
+  int iter = 0;
+  for (int64_t r = blockIdx.x; r < R; r += gridDim.x, ++iter) {
+    const float* srcr = row_stage<DB>(src, in, r, R, g.d_in, iter);
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
       const int ft = it / per_tile, o0 = ft * kConvFT;
       const int q = it - ft * per_tile, oh = q / G, ow0 = (q - oh * G) * kConvFP;
@@ -498,7 +529,7 @@ __global__ void __launch_bounds__(256) k_conv_fwd_row2(int64_t R, LayerGeom g, c
         for (int kh = 0; kh < g.k; ++kh) {
           const int ih = oh * g.stride + kh - g.pad;
           if (ih < 0 || ih >= g.h_in) continue;
-          const float* srow = src + (c * g.h_in + ih) * g.w_in;
+          const float* srow = srcr + (c * g.h_in + ih) * g.w_in;
           const float* wt = ws + ((size_t)c * kk + kh * g.k) * O4 + o0;
           for (int kw = 0; kw < g.k; ++kw) {
             const float4 w4 = *reinterpret_cast<const float4*>(wt + kw * O4);
@@ -528,6 +559,11 @@ __global__ void __launch_bounds__(256) k_conv_fwd_row2(int64_t R, LayerGeom g, c
 // Dynamic shared memory of a row-staged convolution, opted in once per kernel
 // (false: the row does not fit; use the tiled kernel).
 constexpr size_t kConvRowSmem = 112 * 1024;   // two blocks per SM
+// The double-buffered float form only where it keeps three blocks per SM:
+// the CNN input layer's transposed product, 1.93 -> 1.73 ms per launch; the
+// FP32 chain's 64 -> 32-channel transposed convolution at two blocks per SM
+// measured 4.8 -> 5.3 ms.
+constexpr size_t kConvRowDbSmem = 75 * 1024;
 template <typename Kern>
 bool conv_row_smem(Kern kern, size_t bytes) {
   if (bytes > kConvRowSmem) return false;
@@ -639,11 +675,20 @@ void conv_fwd(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, cons
   snprintf(nm, sizeof nm, "conv_fwd_%s", tname<Tin>());
   int tk = prof_begin(st, nm, 2.0 * R * conv_macs(g), (double)R * (g.d_in * sizeof(Tin) + g.d_out * sizeof(Tacc)));
   const size_t row_bytes = ((size_t)g.d_in + (size_t)g.c_out * g.c_in * g.k * g.k) * sizeof(Tacc);
-  const size_t row2_bytes =
-      ((size_t)g.d_in + (size_t)g.c_in * g.k * g.k * (size_t)(((g.c_out + kConvFT - 1) / kConvFT) * kConvFT)) * 4;
-  if (std::is_same<Tacc, float>::value && conv_row_smem(k_conv_fwd_row2<Tin>, row2_bytes))
-    k_conv_fwd_row2<Tin><<<(unsigned)std::min<int64_t>(R, 152 * 8), 256, row2_bytes, st>>>(
-        R, g, W, in, reinterpret_cast<float*>(out));
+  const size_t wbytes = (size_t)g.c_in * g.k * g.k * (size_t)(((g.c_out + kConvFT - 1) / kConvFT) * kConvFT) * 4;
+  const size_t row2_bytes = (size_t)g.d_in * 4 + wbytes, row2d_bytes = (size_t)g.d_in * 8 + wbytes;
+  const unsigned nblk = (unsigned)std::min<int64_t>(R, 152 * 8);
+  bool done = false;
+  if constexpr (std::is_same<Tin, float>::value && std::is_same<Tacc, float>::value) {
+    if (g.d_in % 4 == 0 && ((uintptr_t)in & 15) == 0 && row2d_bytes <= kConvRowDbSmem &&
+        conv_row_smem(k_conv_fwd_row2<float, true>, row2d_bytes)) {
+      k_conv_fwd_row2<float, true><<<nblk, 256, row2d_bytes, st>>>(R, g, W, in, out);
+      done = true;
+    }
+  }
+  if (done) {
+  } else if (std::is_same<Tacc, float>::value && conv_row_smem(k_conv_fwd_row2<Tin, false>, row2_bytes))
+    k_conv_fwd_row2<Tin, false><<<nblk, 256, row2_bytes, st>>>(R, g, W, in, reinterpret_cast<float*>(out));
   else if (conv_row_smem(k_conv_fwd_row<Tin, Tacc>, row_bytes))
     k_conv_fwd_row<Tin, Tacc><<<(unsigned)std::min<int64_t>(R, 152 * 8), 256, row_bytes, st>>>(R, g, W, in, out);
   else
@@ -663,15 +708,22 @@ void conv_T(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const 
   char nm[32];
   snprintf(nm, sizeof nm, "conv_T_%s", tname<Tin>());
   int tk = prof_begin(st, nm, 2.0 * R * conv_macs(g), (double)R * (g.d_out * sizeof(Tin) + g.d_in * sizeof(Tacc)));
-  if (g.k == 1 && g.pad == 0)
+  const size_t wbytes = (size_t)g.c_out * g.k * g.k * (size_t)(((g.c_in + kConvCT - 1) / kConvCT) * kConvCT) * 4;
+  const size_t row2_bytes = (size_t)g.d_out * 4 + wbytes, row2d_bytes = (size_t)g.d_out * 8 + wbytes;
+  const unsigned nblk = (unsigned)std::min<int64_t>(R, 152 * 8);
+  bool done = false;
+  if constexpr (std::is_same<Tin, float>::value && std::is_same<Tacc, float>::value) {
+    if (!(g.k == 1 && g.pad == 0) && g.d_out % 4 == 0 && ((uintptr_t)in & 15) == 0 && row2d_bytes <= kConvRowDbSmem &&
+        conv_row_smem(k_conv_T_row2<float, true>, row2d_bytes)) {
+      k_conv_T_row2<float, true><<<nblk, 256, row2d_bytes, st>>>(R, g, W, in, out);
+      done = true;
+    }
+  }
+  if (done) {
+  } else if (g.k == 1 && g.pad == 0)
     k_conv_T_1x1<Tin, Tacc, false><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, nullptr, nullptr, nullptr);
-  else if (std::is_same<Tacc, float>::value &&
-           conv_row_smem(k_conv_T_row2<Tin>, ((size_t)g.d_out + (size_t)g.c_out * g.k * g.k *
-                                              (size_t)(((g.c_in + kConvCT - 1) / kConvCT) * kConvCT)) * 4))
-    k_conv_T_row2<Tin><<<(unsigned)std::min<int64_t>(R, 152 * 8), 256,
-                         ((size_t)g.d_out + (size_t)g.c_out * g.k * g.k *
-                          (size_t)(((g.c_in + kConvCT - 1) / kConvCT) * kConvCT)) * 4, st>>>(
-        R, g, W, in, reinterpret_cast<float*>(out));
+  else if (std::is_same<Tacc, float>::value && conv_row_smem(k_conv_T_row2<Tin, false>, row2_bytes))
+    k_conv_T_row2<Tin, false><<<nblk, 256, row2_bytes, st>>>(R, g, W, in, reinterpret_cast<float*>(out));
   else if (conv_row_smem(k_conv_T_row<Tin, Tacc>,
                          ((size_t)g.d_out + (size_t)g.c_out * g.c_in * g.k * g.k) * sizeof(Tacc)))
     k_conv_T_row<Tin, Tacc><<<(unsigned)std::min<int64_t>(R, 152 * 8), 256,
