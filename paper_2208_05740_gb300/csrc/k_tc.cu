@@ -191,21 +191,29 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
 
 // Stage layout: the A tile, then the B tile (KIND 1: and B_lo). KIND 1 keeps
 // A_hi | A_lo of each stage in TMEM columns kAccCols + s * 64 (32 each).
-template <int KIND>
+template <int KIND, int BNT = BN>
 struct TcCfg {
-  static constexpr int kStageBytes = KIND == 0 ? kTileA + kTileB : kTileA + 2 * kTileB;
+  static constexpr int kTileBt = BNT * kRowBytes;   // the B tile (BNT rows of 128 bytes)
+  static constexpr int kStageBytes = KIND == 0 ? kTileA + kTileBt : kTileA + 2 * kTileBt;
   // three-pass tf32: three stages (144 KB) leave room beside a CTA for the
   // blocks of the next span kernel to start early (47.0 vs 47.4 ms per MLP
   // step); the bf16 kernel keeps four (three measured slower)
   static constexpr int kStages = KIND == 1 ? 3 : 4;
   static constexpr int kKElems = KIND == 0 ? 64 : 32;  // K elements per 128-byte row
   static constexpr uint32_t kFormat = KIND == 0 ? 1u : 2u;  // bf16 / tf32
-  static constexpr int kAccCols = BN;
-  static constexpr int kTmemCols = KIND == 0 ? BN : 512;   // a power of two >= 128 + 4 * 64
+  static constexpr int kAccCols = BNT;
+  // KIND 1: A_hi | A_lo of stage s at TMEM columns kSplitCol + 64 s
+  static constexpr int kSplitCol = BNT <= 128 ? 128 : 256;
+  static constexpr int kTmemCols = KIND == 0 ? (BNT <= 128 ? 128 : 256) : 512;   // powers of two
   static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 };
-static_assert(TcCfg<1>::kAccCols + TcCfg<1>::kStages * 64 <= TcCfg<1>::kTmemCols, "TMEM columns");
+static_assert(TcCfg<1>::kSplitCol + TcCfg<1>::kStages * 64 <= TcCfg<1>::kTmemCols, "TMEM columns");
+static_assert(TcCfg<1, 224>::kSplitCol + TcCfg<1, 224>::kStages * 64 <= TcCfg<1, 224>::kTmemCols, "TMEM columns");
+static_assert(TcCfg<1, 224>::kSmem <= 227 * 1024, "shared memory of the 224-column tiles");
 static_assert(4 * 32 * BN * 4 <= TcCfg<0>::kStages * TcCfg<0>::kStageBytes, "epilogue staging fits the stages");
+static_assert(4 * 32 * (224 + 4) * 4 <= TcCfg<1, 224>::kStages * TcCfg<1, 224>::kStageBytes, "epilogue staging");
+static_assert(4 * 32 * (224 + 4) * 4 <= TcCfg<0, 224>::kStages * TcCfg<0, 224>::kStageBytes, "epilogue staging");
+static_assert(TcCfg<0, 224>::kAccCols <= TcCfg<0, 224>::kTmemCols && TcCfg<0, 224>::kSmem <= 227 * 1024, "bf16 224");
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -217,12 +225,13 @@ template <int KIND>
 constexpr int tc_threads() { return KIND == 1 ? 192 : 128; }
 constexpr int kSplitThreads = 128;
 
-template <int KIND>
+template <int KIND, int BNT = BN>
 __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
               const __grid_constant__ CUtensorMap tBlo, const __grid_constant__ CUtensorMap tC, int c_tma, int M,
               int N, int K, float* __restrict__ C) {
-  using Cfg = TcCfg<KIND>;
+  using Cfg = TcCfg<KIND, BNT>;
+  constexpr int kTileB = Cfg::kTileBt;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::kStages * Cfg::kStageBytes);
@@ -233,7 +242,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
 
   griddep_launch();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BNT;
   const int KT = (K + Cfg::kKElems - 1) / Cfg::kKElems;
 
   if (threadIdx.x == 0) {
@@ -302,7 +311,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
     // previous use have finished (the producer waited for them before the
     // TMA), so its TMEM columns are free.
     const int row = ((warp & 3) << 5) + lane;
-    const uint32_t trow = tmem + (static_cast<uint32_t>((warp & 3) << 5) << 16) + Cfg::kAccCols;
+    const uint32_t trow = tmem + (static_cast<uint32_t>((warp & 3) << 5) << 16) + Cfg::kSplitCol;
     for (int kt = 0; kt < KT; ++kt) {
       const int s = kt % Cfg::kStages;
       const uint32_t ph = (kt / Cfg::kStages) & 1;
@@ -329,7 +338,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: 4 K-steps of 32 bytes per stage, 1 or 3 passes each
-    constexpr uint32_t id = idesc(Cfg::kFormat, BM, BN);
+    constexpr uint32_t id = idesc(Cfg::kFormat, BM, BNT);
     bool ok = true;
     for (int kt = 0; kt < KT && ok; ++kt) {
       const int s = kt % Cfg::kStages;
@@ -343,7 +352,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
         const uint64_t db = sdesc(b + kk * 32);
         if constexpr (KIND == 1) {
           // A_hi, A_lo: 8 TMEM columns per K-step of 8 tf32 elements
-          const uint32_t ta = tmem + Cfg::kAccCols + s * 64 + kk * 8;
+          const uint32_t ta = tmem + Cfg::kSplitCol + s * 64 + kk * 8;
           const uint64_t db_lo = sdesc(b + kTileB + kk * 32);
           umma_tf32_ta(tmem, ta, db, id, (kt | kk) != 0);
           umma_tf32_ta(tmem, ta, db_lo, id, 1);
@@ -368,9 +377,9 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
   const bool ready = warp < 4 && mbar_wait_idle(done, 0);   // warps 4-5 (split only) skip the epilogue
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ready && c_tma) {
-    uint8_t* stg = smem + warp * (32 * BN * 4);
+    uint8_t* stg = smem + warp * (32 * BNT * 4);
 #pragma unroll 1
-    for (int c = 0; c < BN; c += 32) {
+    for (int c = 0; c < BNT; c += 32) {
       uint32_t r[32];
       tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c, r);
       uint8_t* row = stg + (c >> 5) * 4096 + lane * 128;
@@ -383,17 +392,17 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
     __syncwarp();
     if (lane == 0) {
       const int y = m0 + warp * 32;
-      for (int c = 0; c < BN / 32; ++c)
+      for (int c = 0; c < BNT / 32; ++c)
         if (y < M && n0 + 32 * c < N) tma_store_2d(&tC, stg + c * 4096, n0 + 32 * c, y);
       asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // staging read before the CTA ends
     }
     __syncwarp();
   } else if (ready) {
-    constexpr int kLd = BN + 4;   // padded row stride (floats): conflict-free float4 stores
+    constexpr int kLd = BNT + 4;   // padded row stride (floats): conflict-free float4 stores
     float* ct = reinterpret_cast<float*>(smem) + warp * 32 * kLd;
 #pragma unroll 1
-    for (int c = 0; c < BN; c += 32) {
+    for (int c = 0; c < BNT; c += 32) {
       uint32_t r[32];
       tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c, r);
 #pragma unroll
@@ -403,7 +412,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>(), 1)
                         __uint_as_float(r[q + 3]));
     }
     __syncwarp();
-    const int ncol = min(BN, N - n0);
+    const int ncol = min(BNT, N - n0);
 #pragma unroll 1
     for (int i = 0; i < 32; ++i) {
       const int row = m0 + warp * 32 + i;
@@ -960,28 +969,42 @@ bool make_map(CUtensorMap* m, const void* base, bool bf16, int64_t rows, int64_t
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int KIND>
-bool launch_tc(cudaStream_t st, int64_t M, int N, int K, const void* A, const void* B, const void* Blo, float* C,
-               int64_t lda = 0, int64_t ldb = 0) {
-  using Cfg = TcCfg<KIND>;
-  static std::once_flag attr_once;
-  std::call_once(attr_once, [] {
-    cudaFuncSetAttribute(k_gemm_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
-  });
+template <int KIND, int BNT>
+bool launch_tc_bn(cudaStream_t st, int64_t M, int N, int K, const void* A, const void* B, const void* Blo, float* C,
+                  int64_t lda, int64_t ldb) {
+  using Cfg = TcCfg<KIND, BNT>;
+  smem_opt_in(reinterpret_cast<const void*>(k_gemm_tc<KIND, BNT>), Cfg::kSmem);
   const bool bf = KIND == 0;
   CUtensorMap ta{}, tb{}, tblo{}, tc{};
-  if (!make_map(&ta, A, bf, M, K, BM, lda) || !make_map(&tb, B, bf, N, K, BN, ldb)) return false;
+  if (!make_map(&ta, A, bf, M, K, BM, lda) || !make_map(&tb, B, bf, N, K, BNT, ldb)) return false;
   if (KIND == 1) {
-    if (!make_map(&tblo, Blo, bf, N, K, BN, ldb)) return false;
+    if (!make_map(&tblo, Blo, bf, N, K, BNT, ldb)) return false;
   } else {
     tblo = tb;
   }
   // C through bulk tensor stores: 16-byte aligned base and row stride
   const int c_tma = (reinterpret_cast<uintptr_t>(C) & 15) == 0 && (N & 3) == 0 && make_map(&tc, C, false, M, N, 32);
-  dim3 grid((N + BN - 1) / BN, static_cast<unsigned>((M + BM - 1) / BM));
-  launch_pdl(k_gemm_tc<KIND>, grid, dim3(tc_threads<KIND>()), Cfg::kSmem, st, ta, tb, tblo, tc, c_tma,
+  dim3 grid((N + BNT - 1) / BNT, static_cast<unsigned>((M + BM - 1) / BM));
+  launch_pdl(k_gemm_tc<KIND, BNT>, grid, dim3(tc_threads<KIND>()), Cfg::kSmem, st, ta, tb, tblo, tc, c_tma,
              static_cast<int>(M), N, K, C);
   return true;
+}
+
+// Tile width of the GEMMs: 128 columns, or 224 where the
+// fewer waves of wider tiles take less time (a CTA's MMA time grows with its
+// width): the 9216 x 784 product onto the MLP's input layer runs 288 CTAs in
+// 1.9 waves instead of 504 in 3.3.
+inline int tc_tile_cols(int64_t M, int N) {
+  const int64_t rows = (M + BM - 1) / BM;
+  auto cost = [&](int bn) { return ((rows * ((N + bn - 1) / bn) + 151) / 152) * bn; };
+  return cost(224) < cost(128) ? 224 : 128;
+}
+
+template <int KIND>
+bool launch_tc(cudaStream_t st, int64_t M, int N, int K, const void* A, const void* B, const void* Blo, float* C,
+               int64_t lda = 0, int64_t ldb = 0) {
+  if (tc_tile_cols(M, N) == 224) return launch_tc_bn<KIND, 224>(st, M, N, K, A, B, Blo, C, lda, ldb);
+  return launch_tc_bn<KIND, BN>(st, M, N, K, A, B, Blo, C, lda, ldb);
 }
 
 }  // namespace

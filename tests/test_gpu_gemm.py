@@ -13,9 +13,12 @@ def g():
 
 
 SHAPES = [(128, 128, 64), (300, 200, 784), (9216, 256, 256), (257, 130, 40), (1, 16, 8), (640, 784, 256)]
+# shapes whose products take 224-column tiles (fewer waves):
+# the MLP's backward product onto its 784-wide input layer, and a ragged one
+WIDE = [(9216, 784, 256), (9100, 780, 104)]
 
 
-@pytest.mark.parametrize("M,N,K", SHAPES)
+@pytest.mark.parametrize("M,N,K", SHAPES + WIDE)
 def test_tcgen05_tf32x3_matches_float64(g, M, N, K):
     rng = np.random.default_rng(M + N + K)
     A = rng.normal(size=(M, K)).astype(np.float32)
@@ -28,7 +31,7 @@ def test_tcgen05_tf32x3_matches_float64(g, M, N, K):
     assert np.max(np.abs(C32 - ref) / np.maximum(scale, 1e-30)) < 4e-6
 
 
-@pytest.mark.parametrize("M,N,K", SHAPES)
+@pytest.mark.parametrize("M,N,K", SHAPES + WIDE)
 def test_tcgen05_bf16_matches_bf16_inputs(g, M, N, K):
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(7 * M + N + K)
