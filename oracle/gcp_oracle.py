@@ -546,42 +546,63 @@ def crown_root_bounds(net, x_lo, x_hi, block: int = 512):
     """Root intermediate bounds l, u of every hidden layer (Sec. 2, Eq. 1: the
     method takes them from a bound propagation such as CROWN or IBP).
 
-    Hidden layer 1: the interval image of the box under W^(1) x + b^(1).
-    Hidden layer i > 1: the network truncated after layer i's linear map, with
-    spec rows +e_j and -e_j over its neurons, bounded by this module's
-    Theorem 3.1 at the default duals (no cuts, no splits; R10's adaptive
-    slope) over the bounds already found for the layers below:
-    l_j = g(+e_j), u_j = -g(-e_j). That is CROWN. Plain feed-forward networks
-    (no skip connections).
+    Hidden layer 1: the interval image of the box under its affine map (W^(1),
+    plus the shortcut of a skip from the input). Hidden layer i > 1: the
+    network truncated after layer i's linear map, with spec rows +e_j and
+    -e_j over its neurons, bounded by this module's Theorem 3.1 at the
+    default duals (no cuts, no splits; R10's adaptive slope) over the bounds
+    already found for the layers below: l_j = g(+e_j), u_j = -g(-e_j). That is
+    CROWN. A skip connection into layer i (R11) stays in the truncated network,
+    restricted to the same rows j (the identity shortcut becomes the selection
+    of those rows).
     """
     layers = net.layers
-    if any(int(getattr(ly, "skip", 0)) for ly in layers):
-        raise ValueError("crown_root_bounds: skip connections are not handled")
     L = len(layers)
     dims = [layers[0].d_in] + [ly.d_out for ly in layers]
-    mats = [np.asarray(ly.W, np.float64) if ly.kind == DENSE else
-            conv_matrix(np.asarray(ly.W, np.float64), ly.in_shape, ly.out_shape, ly.stride, ly.pad) for ly in layers]
-    bias = [np.asarray(ly.b, np.float64) for ly in layers]
+
+    def lin(ly):
+        return (np.asarray(ly.W, np.float64) if ly.kind == DENSE else
+                conv_matrix(np.asarray(ly.W, np.float64), ly.in_shape, ly.out_shape, ly.stride, ly.pad))
+    mats = [lin(ly) for ly in layers]
+    skip = [int(getattr(ly, "skip", 0)) for ly in layers]
+    smap, bias = [], []
+    for ly, s_ in zip(layers, skip):
+        sc = getattr(ly, "shortcut", None) if s_ else None
+        smap.append(None if sc is None else lin(sc))
+        bias.append(np.asarray(ly.b, np.float64) + (np.asarray(sc.b, np.float64) if sc is not None else 0.0))
+
+    def rows_of(M, idx):
+        r = M[idx]
+        return r.toarray() if sp.issparse(r) else r
+
     x_lo = np.asarray(x_lo, np.float64)
     x_hi = np.asarray(x_hi, np.float64)
     c0, r0 = (x_hi + x_lo) / 2, (x_hi - x_lo) / 2
-    z = np.asarray(mats[0] @ c0).ravel() + bias[0]
-    rad = np.asarray(abs(mats[0]) @ r0).ravel()
+    M1 = mats[0]
+    if skip[0]:
+        # layer 1 may only add the input itself (xhat^(0) = x)
+        M1 = (M1.toarray() if sp.issparse(M1) else M1) + (np.eye(dims[0]) if smap[0] is None else
+                                                         (smap[0].toarray() if sp.issparse(smap[0]) else smap[0]))
+    z = np.asarray(M1 @ c0).ravel() + bias[0]
+    rad = np.asarray(abs(M1) @ r0).ravel()
     lo, hi = [z - rad], [z + rad]
     for i in range(2, L):
         li, ui = np.empty(dims[i]), np.empty(dims[i])
         for a in range(0, dims[i], block):
             idx = np.arange(a, min(dims[i], a + block))
             n = len(idx)
-            rows = mats[i - 1][idx]
-            rows = rows.toarray() if sp.issparse(rows) else rows
             dt = dims[:i] + [n]
+            s_i = skip[i - 1]
+            last_map = None
+            if s_i:
+                last_map = (np.eye(dims[i])[idx] if smap[i - 1] is None else rows_of(smap[i - 1], idx))
             none = [sp.csr_matrix((0, d)) for d in dt[:-1]]
-            P = Problem(i, dt, mats[:i - 1] + [rows], bias[:i - 1] + [bias[i - 1][idx]], x_lo, x_hi,
-                        np.concatenate([np.eye(n), -np.eye(n)]), lo, hi,
+            P = Problem(i, dt, mats[:i - 1] + [rows_of(mats[i - 1], idx)], bias[:i - 1] + [bias[i - 1][idx]],
+                        x_lo, x_hi, np.concatenate([np.eye(n), -np.eye(n)]), lo, hi,
                         [l[None, :] for l in lo], [h[None, :] for h in hi],
                         np.zeros(2, np.int64), np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0, np.int64),
-                        0, none, list(none), list(none), np.zeros(0), [0] * i, [None] * i)
+                        0, none, list(none), list(none), np.zeros(0), skip[:i - 1] + [s_i],
+                        smap[:i - 1] + [last_map])
             g = evaluate(P, default_duals(P))
             li[idx], ui[idx] = g[:n], -g[n:]
         lo.append(li)

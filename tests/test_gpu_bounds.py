@@ -166,3 +166,22 @@ def test_bounds_with_valid_cuts_are_sound_and_reduce_to_crown(ctx):
     wa = sum(float(np.sum(h - l)) for l, h in zip(la, ha))
     wc = sum(float(np.sum(h - l)) for l, h in zip(lc, hc))
     assert wc <= wa * (1 + 1e-3), (wc, wa)
+
+
+@pytest.mark.parametrize("make", [lambda: synth.mlp_residual(n_sub=1, n_cuts=0),
+                                  lambda: synth.cnn_resnet(n_sub=1, n_cuts=0)],
+                         ids=["mlp_residual", "resnet2b_shape"])
+def test_residual_crown_bounds_match_the_oracle(ctx, make):
+    """Skip connections (identity and 1x1 projection shortcuts) in the root
+    bounds: every hidden layer's certified CROWN bounds against the oracle's
+    CROWN (its truncated networks keep the skip, restricted to the bounded
+    rows), and sound on sampled inputs."""
+    inst = make()
+    lo, hi = ctx.intermediate_bounds(inst.net.layers, inst.x_lo, inst.x_hi)
+    olo, ohi = O.crown_root_bounds(inst.net, inst.x_lo, inst.x_hi)
+    for i, (a, b, c, d) in enumerate(zip(lo, hi, olo, ohi)):
+        assert_rel(a, c, 1e-9, f"layer {i + 1} lower vs oracle")
+        assert_rel(b, d, 1e-9, f"layer {i + 1} upper vs oracle")
+    for i, z in enumerate(_sampled_preacts(inst, 2000, 7)):
+        assert np.all(z >= lo[i] - 1e-9 * np.maximum(1, np.abs(z))), f"layer {i + 1} below the lower bound"
+        assert np.all(z <= hi[i] + 1e-9 * np.maximum(1, np.abs(z))), f"layer {i + 1} above the upper bound"

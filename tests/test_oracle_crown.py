@@ -96,3 +96,52 @@ def test_inside_interval_bounds():
     # strictly tighter somewhere past the first layer
     assert sum(float(np.sum(b - a)) for a, b in zip(L[1:], H[1:])) < \
         sum(float(np.sum(d - c)) for c, d in zip(IL[1:], IH[1:]))
+
+
+# ---- residual networks (a skip connection into a truncated layer, R11)
+
+def _res_net(seed):
+    inst = synth.mlp_residual(seed=seed, width=12, d0=6, blocks=2, d_out=3, eps=0.1, n_sub=1, n_cuts=0)
+    return inst.net, inst.x_lo, inst.x_hi
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_residual_bounds_are_sound_on_sampled_inputs(seed):
+    net, lo, hi = _res_net(seed)
+    L, H = crown_root_bounds(net, lo, hi)
+    X = synth.sample_box(np.random.default_rng(seed), lo, hi, 20000)
+    for i, z in enumerate(synth.forward_all(net, X)[:-1]):
+        assert np.all(z >= L[i] - 1e-12) and np.all(z <= H[i] + 1e-12), f"layer {i + 1}"
+
+
+def test_residual_bounds_inside_interval_bounds():
+    net, lo, hi = _res_net(13)
+    L, H = crown_root_bounds(net, lo, hi)
+    IL, IH = synth.interval_bounds(net, lo, hi)
+    for a, b, c, d in zip(L, H, IL, IH):
+        assert np.all(a >= c - 1e-12) and np.all(b <= d + 1e-12)
+    assert sum(float(np.sum(b - a)) for a, b in zip(L[1:], H[1:])) < \
+        sum(float(np.sum(d - c)) for c, d in zip(IL[1:], IH[1:]))
+
+
+def test_residual_skip_layer_bounds_do_not_beat_the_lp():
+    """Layer 3 carries the first block's skip (it adds xhat^(1)): its bounds are
+    at most as tight as the LP of the network truncated there with the skip."""
+    net, lo, hi = _res_net(14)
+    L, H = crown_root_bounds(net, lo, hi)
+    ly = net.layers[2]
+    assert int(ly.skip) == 2
+    empty = synth.Subdomains(np.zeros(2, np.int32), np.zeros(0, np.int16), np.zeros(0, np.int32),
+                             np.zeros(0, np.int8))
+    for j in range(0, ly.d_out, 3):
+        # the skip's identity restricted to row j: a one-row projection shortcut
+        sel = synth.Layer(synth.DENSE, np.eye(ly.d_out)[[j]], np.zeros(1), ly.in_shape, (1,))
+        import dataclasses
+        last = dataclasses.replace(ly, W=ly.W[[j]], b=ly.b[[j]], out_shape=(1,), shortcut=sel)
+        tr = synth.Instance("prefix", synth.Network(list(net.layers[:2]) + [last]), lo, hi,
+                            np.array([[1.0], [-1.0]]), L[:2], H[:2], empty, synth.Cuts.empty())
+        P = O.build_problem(tr)
+        lp_min = O.lp_value(P, 0, 0, with_cuts=False)
+        lp_max = -O.lp_value(P, 0, 1, with_cuts=False)
+        assert L[2][j] <= lp_min + 1e-7 * max(1.0, abs(lp_min))
+        assert H[2][j] >= lp_max - 1e-7 * max(1.0, abs(lp_max))
