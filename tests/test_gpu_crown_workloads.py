@@ -5,7 +5,8 @@ The root bounds here come from the oracle alone (tests/helpers.py,
 oracle_crown_bounds) and are fed to both sides. At the launch shapes the
 benchmark times -- MLP 784-256x6-10 with 1024 subdomains x 9 rows and 200
 cuts, 100 Adam steps in the FP32 chain; CNN 3x32x32 with 4096 subdomains x 9
-rows and 1000 cuts, 50 Adam steps in the BF16 chain -- sampled subdomains are
+rows and 1000 cuts, 50 Adam steps in the BF16 chain; the resnet2b-shaped residual CNN with
+2048 subdomains x 9 rows and 500 cuts, 20 Adam steps in the BF16 chain -- sampled subdomains are
 checked row by row against the oracle at the duals the GPU reached: the
 chain's bound (FP32 1e-5, BF16 1e-3) and the certified FP64 bound (1e-9).
 """
@@ -71,4 +72,16 @@ def test_full_size_cnn_on_crown_root_bounds_sampled_rows(ctx):
     D = ctx.duals_create(net_id, cs, inst.sub, gcp.GCP_FP32)
     bound, cert, err = ctx.optimize_batch(D, gcp.opt_params(50, gcp.GCP_ADAM, gcp.GCP_BF16, 1, **ADAM))
     _check_sampled(ctx, inst, D, bound, cert, [0, 2047, 4095], 1e-3, gcp.GCP_FP32, 1e-5)
+    ctx.duals_free(D)
+
+
+def test_full_size_resnet_on_crown_root_bounds_sampled_rows(ctx):
+    """The residual CNN (resnet2b shape) the benchmark's --workload resnet
+    times: 2048 subdomains x 9 rows, 500 cuts, 20 Adam steps in the BF16 chain,
+    on the oracle's CROWN root bounds through its skip connections."""
+    inst = synth.cnn_resnet(root_bounds=oracle_crown_bounds)
+    net_id, cs = ctx.load_instance(inst)
+    D = ctx.duals_create(net_id, cs, inst.sub, gcp.GCP_FP32)
+    bound, cert, err = ctx.optimize_batch(D, gcp.opt_params(20, gcp.GCP_ADAM, gcp.GCP_BF16, 1, **ADAM))
+    _check_sampled(ctx, inst, D, bound, cert, [0, 1000, 2047], 1e-3, gcp.GCP_FP32, 1e-5)
     ctx.duals_free(D)
