@@ -1299,23 +1299,12 @@ bool conv_tc_bf16(cudaStream_t st, int64_t R, const LayerGeom& g, int dir, const
     L = conv_smem_layout(Kp, Np, a.stg_rows, c.Ws, c.Csp, 1, a.nb2);
   }
   if (L.total > 227 * 1024) return false;
-  static std::mutex mu;
-  static int attr_bytes = 0;
-  static int n_sm = 0;
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    if (L.total > attr_bytes) {
-      if (cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) != cudaSuccess)
-        return false;
-      attr_bytes = L.total;
-    }
-    if (!n_sm) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-      if (n_sm <= 0) n_sm = 1;
-    }
-  }
+  // opted in per device and size
+  if (!smem_opt_in(reinterpret_cast<const void*>(k_conv_tc), (size_t)L.total)) return false;
+  int n_sm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (n_sm <= 0) n_sm = 1;
   a.src = src;
   a.Wp = Wp;
   a.out = out;
