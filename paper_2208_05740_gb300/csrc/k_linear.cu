@@ -363,7 +363,9 @@ __device__ __forceinline__ float* row_stage(float* buf, const Tin* in, int64_t r
 // terms in the same order as k_conv_T_row (a skipped tap is a predicate), so
 // every output is the same number. TP = 4 where there are several channel
 // tiles (the CNN's 64 -> 32-channel layer: 20% faster than TP = 2), 2 for a
-// single tile (its 3-channel input layer: 36% slower with TP = 4).
+// single tile (its 3-channel input layer: 36% slower with TP = 4). Work items
+// run channel tile fastest, as in k_conv_fwd_row2 (the 64 -> 32-channel layer
+// of the FP32 chain 6.1 -> 5.2 ms per launch).
 template <typename Tin, bool DB, int TP>
 __global__ void __launch_bounds__(256) k_conv_T_row2(int64_t R, LayerGeom g, const Tin* __restrict__ W,
                                                      const Tin* __restrict__ in, float* __restrict__ out) {
@@ -389,8 +391,8 @@ __global__ void __launch_bounds__(256) k_conv_T_row2(int64_t R, LayerGeom g, con
   for (int64_t r = blockIdx.x; r < R; r += gridDim.x, ++iter) {
     const float* srcr = row_stage<DB>(src, in, r, R, g.d_out, iter);
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
-      const int ct = it / per_tile, c0 = ct * kConvCT;
-      int q = it - ct * per_tile;
+      const int ct = it % nct, c0 = ct * kConvCT;
+      int q = it / nct;
       int ph = 0, pw = 0, Wf = 1, G = 1;
       for (int f = 0; f < s * s; ++f) {
         ph = f / s;
@@ -494,12 +496,17 @@ __global__ void __launch_bounds__(256) k_conv_fwd_row(int64_t R, LayerGeom g, co
   }
 }
 
-// Float form of k_conv_fwd_row with two adjacent output pixels (columns ow and
-// ow + 1 of one output row) per work item sharing each weight load, the
-// weights staged as [c_in][k][k][4 * nft] (one 16-byte load per tap gives a
-// tile's four output channels). The same terms are added in the same order
-// as k_conv_fwd_row, so every output is the same number.
-constexpr int kConvFP = 2;   // output pixels per work item
+// Float form of k_conv_fwd_row with kConvFP adjacent output pixels (columns
+// ow .. ow + kConvFP - 1 of one output row) per work item sharing each weight
+// load, the weights staged as [c_in][k][k][4 * nft] (one 16-byte load per tap
+// gives a tile's four output channels). Work items run channel tile fastest:
+// the lanes of a warp that share a pixel group read the same source words
+// (broadcasts), where pixel groups fastest put up to eight lanes of a stride-2
+// convolution on one shared-memory bank (CNN FP32 chain 1,825 -> 1,673 ms per
+// step); with that ordering four pixels per item beat two (1,621 -> 1,554 ms).
+// The same terms are added in the same order as k_conv_fwd_row, so every
+// output is the same number.
+constexpr int kConvFP = 4;   // output pixels per work item
 template <typename Tin, bool DB>
 __global__ void __launch_bounds__(256) k_conv_fwd_row2(int64_t R, LayerGeom g, const Tin* __restrict__ W,
                                                        const Tin* __restrict__ in, float* __restrict__ out) {
@@ -519,8 +526,8 @@ __global__ void __launch_bounds__(256) k_conv_fwd_row2(int64_t R, LayerGeom g, c
   for (int64_t r = blockIdx.x; r < R; r += gridDim.x, ++iter) {
     const float* srcr = row_stage<DB>(src, in, r, R, g.d_in, iter);
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
-      const int ft = it / per_tile, o0 = ft * kConvFT;
-      const int q = it - ft * per_tile, oh = q / G, ow0 = (q - oh * G) * kConvFP;
+      const int ft = it % nft, o0 = ft * kConvFT;
+      const int q = it / nft, oh = q / G, ow0 = (q - oh * G) * kConvFP;
       float acc[kConvFP][kConvFT];
 #pragma unroll
       for (int p = 0; p < kConvFP; ++p)
