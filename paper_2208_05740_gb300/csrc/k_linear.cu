@@ -362,8 +362,9 @@ __device__ __forceinline__ float* row_stage(float* buf, const Tin* in, int64_t r
 // so one 16-byte load gives a tile's four channels. Each output adds the same
 // terms in the same order as k_conv_T_row (a skipped tap is a predicate), so
 // every output is the same number. TP = 4 where there are several channel
-// tiles (the CNN's 64 -> 32-channel layer: 20% faster than TP = 2), 2 for a
-// single tile (its 3-channel input layer: 36% slower with TP = 4). Work items
+// tiles and enough items (conv_pixels; the CNN's 64 -> 32-channel layer: 20%
+// faster than TP = 2), 2 otherwise (its 3-channel input layer: 36% slower
+// with TP = 4). Work items
 // run channel tile fastest, as in k_conv_fwd_row2 (the 64 -> 32-channel layer
 // of the FP32 chain 6.1 -> 5.2 ms per launch).
 template <typename Tin, bool DB, int TP>
@@ -496,18 +497,18 @@ __global__ void __launch_bounds__(256) k_conv_fwd_row(int64_t R, LayerGeom g, co
   }
 }
 
-// Float form of k_conv_fwd_row with kConvFP adjacent output pixels (columns
-// ow .. ow + kConvFP - 1 of one output row) per work item sharing each weight
+// Float form of k_conv_fwd_row with FP adjacent output pixels (columns
+// ow .. ow + FP - 1 of one output row) per work item sharing each weight
 // load, the weights staged as [c_in][k][k][4 * nft] (one 16-byte load per tap
 // gives a tile's four output channels). Work items run channel tile fastest:
 // the lanes of a warp that share a pixel group read the same source words
 // (broadcasts), where pixel groups fastest put up to eight lanes of a stride-2
 // convolution on one shared-memory bank (CNN FP32 chain 1,825 -> 1,673 ms per
-// step); with that ordering four pixels per item beat two (1,621 -> 1,554 ms).
-// The same terms are added in the same order as k_conv_fwd_row, so every
-// output is the same number.
-constexpr int kConvFP = 4;   // output pixels per work item
-template <typename Tin, bool DB>
+// step); with that ordering four pixels per item beat two (1,621 -> 1,554 ms)
+// where a row still has an item for each of the block's threads
+// (conv_pixels). The same terms are added in the same order as
+// k_conv_fwd_row, so every output is the same number.
+template <typename Tin, bool DB, int FP>
 __global__ void __launch_bounds__(256) k_conv_fwd_row2(int64_t R, LayerGeom g, const Tin* __restrict__ W,
                                                        const Tin* __restrict__ in, float* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char conv_sm[];
@@ -519,7 +520,7 @@ __global__ void __launch_bounds__(256) k_conv_fwd_row2(int64_t R, LayerGeom g, c
     const int o = i % O4, tap = (i / O4) % kk, c = i / (O4 * kk);
     ws[i] = o < g.c_out ? load_as<float>(W + (int64_t)o * g.c_in * kk + c * kk + tap) : 0.f;
   }
-  const int G = (g.w_out + kConvFP - 1) / kConvFP;   // pixel groups per output row
+  const int G = (g.w_out + FP - 1) / FP;   // pixel groups per output row
   const int per_tile = g.h_out * G, items = nft * per_tile;
   if (DB && blockIdx.x < R) row_async(src, reinterpret_cast<const float*>(in) + blockIdx.x * (int64_t)g.d_in, g.d_in);
   int iter = 0;
@@ -527,10 +528,10 @@ __global__ void __launch_bounds__(256) k_conv_fwd_row2(int64_t R, LayerGeom g, c
     const float* srcr = row_stage<DB>(src, in, r, R, g.d_in, iter);
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
       const int ft = it % nft, o0 = ft * kConvFT;
-      const int q = it / nft, oh = q / G, ow0 = (q - oh * G) * kConvFP;
-      float acc[kConvFP][kConvFT];
+      const int q = it / nft, oh = q / G, ow0 = (q - oh * G) * FP;
+      float acc[FP][kConvFT];
 #pragma unroll
-      for (int p = 0; p < kConvFP; ++p)
+      for (int p = 0; p < FP; ++p)
 #pragma unroll
         for (int t = 0; t < kConvFT; ++t) acc[p][t] = 0.f;
       for (int c = 0; c < g.c_in; ++c)
@@ -543,7 +544,7 @@ __global__ void __launch_bounds__(256) k_conv_fwd_row2(int64_t R, LayerGeom g, c
             const float4 w4 = *reinterpret_cast<const float4*>(wt + kw * O4);
             const float wv[kConvFT] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-            for (int p = 0; p < kConvFP; ++p) {
+            for (int p = 0; p < FP; ++p) {
               const int iw = (ow0 + p) * g.stride + kw - g.pad;
               if (ow0 + p >= g.w_out || iw < 0 || iw >= g.w_in) continue;
               const float v = srow[iw];
@@ -553,7 +554,7 @@ __global__ void __launch_bounds__(256) k_conv_fwd_row2(int64_t R, LayerGeom g, c
           }
         }
 #pragma unroll
-      for (int p = 0; p < kConvFP; ++p) {
+      for (int p = 0; p < FP; ++p) {
         if (ow0 + p >= g.w_out) continue;
         float* orow = out + r * g.d_out + oh * g.w_out + ow0 + p;
 #pragma unroll
@@ -576,6 +577,28 @@ template <typename Kern>
 bool conv_row_smem(Kern kern, size_t bytes) {
   if (bytes > kConvRowSmem) return false;
   return smem_opt_in(reinterpret_cast<const void*>(kern), bytes);
+}
+
+// Pixels per work item of the row-staged float convolutions: four where the
+// row's items at four pixels still cover the block's 256 threads (and, for a
+// transposed product, the layer has several channel tiles), else two. The
+// residual network's 16-channel 8x8 layers have 64 items per row at four
+// pixels: with four, its FP32 chain measured 189 -> 224 ms per step.
+int conv_pixels(const LayerGeom& g, int dir) {
+  constexpr int kThreads = 256;
+  if (dir == 0) {
+    const int nft = (g.c_out + kConvFT - 1) / kConvFT;
+    return (int64_t)nft * g.h_out * ((g.w_out + 3) / 4) >= kThreads ? 4 : 2;
+  }
+  if (g.c_in <= kConvCT) return 2;
+  const int s = g.stride, nct = (g.c_in + kConvCT - 1) / kConvCT;
+  int64_t per_tile = 0;
+  for (int f = 0; f < s * s; ++f) {
+    const int ph = f / s, pw = f - ph * s;
+    const int Hf = ph < g.h_in ? (g.h_in - ph + s - 1) / s : 0, Wf = pw < g.w_in ? (g.w_in - pw + s - 1) / s : 0;
+    per_tile += (int64_t)Hf * ((Wf + 3) / 4);
+  }
+  return nct * per_tile >= kThreads ? 4 : 2;
 }
 
 // The transposed 1x1 convolution without padding (a residual block's
@@ -687,16 +710,23 @@ void conv_fwd(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, cons
   const size_t row2_bytes = (size_t)g.d_in * 4 + wbytes, row2d_bytes = (size_t)g.d_in * 8 + wbytes;
   const unsigned nblk = (unsigned)std::min<int64_t>(R, 152 * 8);
   bool done = false;
+  const int fp = conv_pixels(g, 0);
   if constexpr (std::is_same<Tin, float>::value && std::is_same<Tacc, float>::value) {
-    if (g.d_in % 4 == 0 && ((uintptr_t)in & 15) == 0 && row2d_bytes <= kConvRowDbSmem &&
-        conv_row_smem(k_conv_fwd_row2<float, true>, row2d_bytes)) {
-      k_conv_fwd_row2<float, true><<<nblk, 256, row2d_bytes, st>>>(R, g, W, in, out);
-      done = true;
+    if (g.d_in % 4 == 0 && ((uintptr_t)in & 15) == 0 && row2d_bytes <= kConvRowDbSmem) {
+      if (fp == 4 && conv_row_smem(k_conv_fwd_row2<float, true, 4>, row2d_bytes)) {
+        k_conv_fwd_row2<float, true, 4><<<nblk, 256, row2d_bytes, st>>>(R, g, W, in, out);
+        done = true;
+      } else if (fp == 2 && conv_row_smem(k_conv_fwd_row2<float, true, 2>, row2d_bytes)) {
+        k_conv_fwd_row2<float, true, 2><<<nblk, 256, row2d_bytes, st>>>(R, g, W, in, out);
+        done = true;
+      }
     }
   }
   if (done) {
-  } else if (std::is_same<Tacc, float>::value && conv_row_smem(k_conv_fwd_row2<Tin, false>, row2_bytes))
-    k_conv_fwd_row2<Tin, false><<<nblk, 256, row2_bytes, st>>>(R, g, W, in, reinterpret_cast<float*>(out));
+  } else if (std::is_same<Tacc, float>::value && fp == 4 && conv_row_smem(k_conv_fwd_row2<Tin, false, 4>, row2_bytes))
+    k_conv_fwd_row2<Tin, false, 4><<<nblk, 256, row2_bytes, st>>>(R, g, W, in, reinterpret_cast<float*>(out));
+  else if (std::is_same<Tacc, float>::value && conv_row_smem(k_conv_fwd_row2<Tin, false, 2>, row2_bytes))
+    k_conv_fwd_row2<Tin, false, 2><<<nblk, 256, row2_bytes, st>>>(R, g, W, in, reinterpret_cast<float*>(out));
   else if (conv_row_smem(k_conv_fwd_row<Tin, Tacc>, row_bytes))
     k_conv_fwd_row<Tin, Tacc><<<(unsigned)std::min<int64_t>(R, 152 * 8), 256, row_bytes, st>>>(R, g, W, in, out);
   else
@@ -719,10 +749,11 @@ void conv_T(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const 
   const size_t wbytes = (size_t)g.c_out * g.k * g.k * (size_t)(((g.c_in + kConvCT - 1) / kConvCT) * kConvCT) * 4;
   const size_t row2_bytes = (size_t)g.d_out * 4 + wbytes, row2d_bytes = (size_t)g.d_out * 8 + wbytes;
   const unsigned nblk = (unsigned)std::min<int64_t>(R, 152 * 8);
+  const int tp = conv_pixels(g, 1);
   bool done = false;
   if constexpr (std::is_same<Tin, float>::value && std::is_same<Tacc, float>::value) {
     if (!(g.k == 1 && g.pad == 0) && g.d_out % 4 == 0 && ((uintptr_t)in & 15) == 0 && row2d_bytes <= kConvRowDbSmem) {
-      if (g.c_in > kConvCT && conv_row_smem(k_conv_T_row2<float, true, 4>, row2d_bytes)) {
+      if (tp == 4 && conv_row_smem(k_conv_T_row2<float, true, 4>, row2d_bytes)) {
         k_conv_T_row2<float, true, 4><<<nblk, 256, row2d_bytes, st>>>(R, g, W, in, out);
         done = true;
       } else if (conv_row_smem(k_conv_T_row2<float, true, 2>, row2d_bytes)) {
@@ -734,8 +765,7 @@ void conv_T(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const 
   if (done) {
   } else if (g.k == 1 && g.pad == 0)
     k_conv_T_1x1<Tin, Tacc, false><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, nullptr, nullptr, nullptr);
-  else if (std::is_same<Tacc, float>::value && g.c_in > kConvCT &&
-           conv_row_smem(k_conv_T_row2<Tin, false, 4>, row2_bytes))
+  else if (std::is_same<Tacc, float>::value && tp == 4 && conv_row_smem(k_conv_T_row2<Tin, false, 4>, row2_bytes))
     k_conv_T_row2<Tin, false, 4><<<nblk, 256, row2_bytes, st>>>(R, g, W, in, reinterpret_cast<float*>(out));
   else if (std::is_same<Tacc, float>::value && conv_row_smem(k_conv_T_row2<Tin, false, 2>, row2_bytes))
     k_conv_T_row2<Tin, false, 2><<<nblk, 256, row2_bytes, st>>>(R, g, W, in, reinterpret_cast<float*>(out));
