@@ -583,22 +583,51 @@ bool conv_row_smem(Kern kern, size_t bytes) {
 // row's items at four pixels still cover the block's 256 threads (and, for a
 // transposed product, the layer has several channel tiles), else two. The
 // residual network's 16-channel 8x8 layers have 64 items per row at four
-// pixels: with four, its FP32 chain measured 189 -> 224 ms per step.
+// pixels: with four, its FP32 chain measured 189 -> 224 ms per step; with one
+// pixel per item (twice the items of two) 197 ms.
 int conv_pixels(const LayerGeom& g, int dir) {
   constexpr int kThreads = 256;
-  if (dir == 0) {
-    const int nft = (g.c_out + kConvFT - 1) / kConvFT;
-    return (int64_t)nft * g.h_out * ((g.w_out + 3) / 4) >= kThreads ? 4 : 2;
-  }
-  if (g.c_in <= kConvCT) return 2;
-  const int s = g.stride, nct = (g.c_in + kConvCT - 1) / kConvCT;
-  int64_t per_tile = 0;
-  for (int f = 0; f < s * s; ++f) {
-    const int ph = f / s, pw = f - ph * s;
-    const int Hf = ph < g.h_in ? (g.h_in - ph + s - 1) / s : 0, Wf = pw < g.w_in ? (g.w_in - pw + s - 1) / s : 0;
-    per_tile += (int64_t)Hf * ((Wf + 3) / 4);
-  }
-  return nct * per_tile >= kThreads ? 4 : 2;
+  auto items = [&](int P) -> int64_t {
+    if (dir == 0) return (int64_t)((g.c_out + kConvFT - 1) / kConvFT) * g.h_out * ((g.w_out + P - 1) / P);
+    const int s = g.stride;
+    int64_t per_tile = 0;
+    for (int f = 0; f < s * s; ++f) {
+      const int ph = f / s, pw = f - ph * s;
+      const int Hf = ph < g.h_in ? (g.h_in - ph + s - 1) / s : 0, Wf = pw < g.w_in ? (g.w_in - pw + s - 1) / s : 0;
+      per_tile += (int64_t)Hf * ((Wf + P - 1) / P);
+    }
+    return (int64_t)((g.c_in + kConvCT - 1) / kConvCT) * per_tile;
+  };
+  return items(4) >= kThreads && (dir == 0 || g.c_in > kConvCT) ? 4 : 2;
+}
+
+// Launch a row-staged float convolution with P = 2 or 4 pixels per item
+// (false: its shared memory could not be opted in).
+template <typename Tin, bool DB, int P>
+bool fwd_row2_p(cudaStream_t st, unsigned nblk, size_t bytes, int64_t R, const LayerGeom& g, const Tin* W,
+                const Tin* in, float* out) {
+  if (!conv_row_smem(k_conv_fwd_row2<Tin, DB, P>, bytes)) return false;
+  k_conv_fwd_row2<Tin, DB, P><<<nblk, 256, bytes, st>>>(R, g, W, in, out);
+  return true;
+}
+template <typename Tin, bool DB>
+bool fwd_row2(int P, cudaStream_t st, unsigned nblk, size_t bytes, int64_t R, const LayerGeom& g, const Tin* W,
+              const Tin* in, float* out) {
+  return P == 4 ? fwd_row2_p<Tin, DB, 4>(st, nblk, bytes, R, g, W, in, out)
+                : fwd_row2_p<Tin, DB, 2>(st, nblk, bytes, R, g, W, in, out);
+}
+template <typename Tin, bool DB, int P>
+bool T_row2_p(cudaStream_t st, unsigned nblk, size_t bytes, int64_t R, const LayerGeom& g, const Tin* W, const Tin* in,
+              float* out) {
+  if (!conv_row_smem(k_conv_T_row2<Tin, DB, P>, bytes)) return false;
+  k_conv_T_row2<Tin, DB, P><<<nblk, 256, bytes, st>>>(R, g, W, in, out);
+  return true;
+}
+template <typename Tin, bool DB>
+bool T_row2(int P, cudaStream_t st, unsigned nblk, size_t bytes, int64_t R, const LayerGeom& g, const Tin* W,
+            const Tin* in, float* out) {
+  return P == 4 ? T_row2_p<Tin, DB, 4>(st, nblk, bytes, R, g, W, in, out)
+                : T_row2_p<Tin, DB, 2>(st, nblk, bytes, R, g, W, in, out);
 }
 
 // The transposed 1x1 convolution without padding (a residual block's
@@ -712,22 +741,13 @@ void conv_fwd(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, cons
   bool done = false;
   const int fp = conv_pixels(g, 0);
   if constexpr (std::is_same<Tin, float>::value && std::is_same<Tacc, float>::value) {
-    if (g.d_in % 4 == 0 && ((uintptr_t)in & 15) == 0 && row2d_bytes <= kConvRowDbSmem) {
-      if (fp == 4 && conv_row_smem(k_conv_fwd_row2<float, true, 4>, row2d_bytes)) {
-        k_conv_fwd_row2<float, true, 4><<<nblk, 256, row2d_bytes, st>>>(R, g, W, in, out);
-        done = true;
-      } else if (fp == 2 && conv_row_smem(k_conv_fwd_row2<float, true, 2>, row2d_bytes)) {
-        k_conv_fwd_row2<float, true, 2><<<nblk, 256, row2d_bytes, st>>>(R, g, W, in, out);
-        done = true;
-      }
-    }
+    if (g.d_in % 4 == 0 && ((uintptr_t)in & 15) == 0 && row2d_bytes <= kConvRowDbSmem)
+      done = fwd_row2<float, true>(fp, st, nblk, row2d_bytes, R, g, W, in, out);
   }
+  if (!done && std::is_same<Tacc, float>::value)
+    done = fwd_row2<Tin, false>(fp, st, nblk, row2_bytes, R, g, W, in, reinterpret_cast<float*>(out));
   if (done) {
-  } else if (std::is_same<Tacc, float>::value && fp == 4 && conv_row_smem(k_conv_fwd_row2<Tin, false, 4>, row2_bytes))
-    k_conv_fwd_row2<Tin, false, 4><<<nblk, 256, row2_bytes, st>>>(R, g, W, in, reinterpret_cast<float*>(out));
-  else if (std::is_same<Tacc, float>::value && conv_row_smem(k_conv_fwd_row2<Tin, false, 2>, row2_bytes))
-    k_conv_fwd_row2<Tin, false, 2><<<nblk, 256, row2_bytes, st>>>(R, g, W, in, reinterpret_cast<float*>(out));
-  else if (conv_row_smem(k_conv_fwd_row<Tin, Tacc>, row_bytes))
+  } else if (conv_row_smem(k_conv_fwd_row<Tin, Tacc>, row_bytes))
     k_conv_fwd_row<Tin, Tacc><<<(unsigned)std::min<int64_t>(R, 152 * 8), 256, row_bytes, st>>>(R, g, W, in, out);
   else
     k_conv_fwd_tile<Tin, Tacc><<<grid_for(R * (int64_t)((g.c_out + kConvFT - 1) / kConvFT) * g.h_out * g.w_out, 256),
@@ -751,24 +771,16 @@ void conv_T(cudaStream_t st, int64_t R, const LayerGeom& g, const Tin* W, const 
   const unsigned nblk = (unsigned)std::min<int64_t>(R, 152 * 8);
   const int tp = conv_pixels(g, 1);
   bool done = false;
+  const bool k1x1 = g.k == 1 && g.pad == 0;
   if constexpr (std::is_same<Tin, float>::value && std::is_same<Tacc, float>::value) {
-    if (!(g.k == 1 && g.pad == 0) && g.d_out % 4 == 0 && ((uintptr_t)in & 15) == 0 && row2d_bytes <= kConvRowDbSmem) {
-      if (tp == 4 && conv_row_smem(k_conv_T_row2<float, true, 4>, row2d_bytes)) {
-        k_conv_T_row2<float, true, 4><<<nblk, 256, row2d_bytes, st>>>(R, g, W, in, out);
-        done = true;
-      } else if (conv_row_smem(k_conv_T_row2<float, true, 2>, row2d_bytes)) {
-        k_conv_T_row2<float, true, 2><<<nblk, 256, row2d_bytes, st>>>(R, g, W, in, out);
-        done = true;
-      }
-    }
+    if (!k1x1 && g.d_out % 4 == 0 && ((uintptr_t)in & 15) == 0 && row2d_bytes <= kConvRowDbSmem)
+      done = T_row2<float, true>(tp, st, nblk, row2d_bytes, R, g, W, in, out);
   }
+  if (!done && !k1x1 && std::is_same<Tacc, float>::value)
+    done = T_row2<Tin, false>(tp, st, nblk, row2_bytes, R, g, W, in, reinterpret_cast<float*>(out));
   if (done) {
-  } else if (g.k == 1 && g.pad == 0)
+  } else if (k1x1)
     k_conv_T_1x1<Tin, Tacc, false><<<grid_for(n, 256), 256, 0, st>>>(R, g, W, in, out, nullptr, nullptr, nullptr);
-  else if (std::is_same<Tacc, float>::value && tp == 4 && conv_row_smem(k_conv_T_row2<Tin, false, 4>, row2_bytes))
-    k_conv_T_row2<Tin, false, 4><<<nblk, 256, row2_bytes, st>>>(R, g, W, in, reinterpret_cast<float*>(out));
-  else if (std::is_same<Tacc, float>::value && conv_row_smem(k_conv_T_row2<Tin, false, 2>, row2_bytes))
-    k_conv_T_row2<Tin, false, 2><<<nblk, 256, row2_bytes, st>>>(R, g, W, in, reinterpret_cast<float*>(out));
   else if (conv_row_smem(k_conv_T_row<Tin, Tacc>,
                          ((size_t)g.d_out + (size_t)g.c_out * g.c_in * g.k * g.k) * sizeof(Tacc)))
     k_conv_T_row<Tin, Tacc><<<(unsigned)std::min<int64_t>(R, 152 * 8), 256,
