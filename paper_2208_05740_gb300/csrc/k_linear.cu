@@ -506,13 +506,18 @@ __global__ void __launch_bounds__(256) k_conv_fwd_row(int64_t R, LayerGeom g, co
 // convolution on one shared-memory bank (CNN FP32 chain 1,825 -> 1,673 ms per
 // step); with that ordering four pixels per item beat two (1,621 -> 1,554 ms)
 // where a row still has an item for each of the block's threads
-// (conv_pixels). The same terms are added in the same order as
+// (conv_pixels). KS = 3: the kernel size known at compile time and the tap
+// loops unrolled (the CNN FP32 chain's forward products 3.8 -> 3.0 ms per
+// launch; the BF16 chain's bf16-source input layer measured 8% slower, so it
+// keeps the general loops). The same terms are added in the same order as
 // k_conv_fwd_row, so every output is the same number.
-template <typename Tin, bool DB, int FP>
+template <typename Tin, bool DB, int FP, int KS>
 __global__ void __launch_bounds__(256) k_conv_fwd_row2(int64_t R, LayerGeom g, const Tin* __restrict__ W,
                                                        const Tin* __restrict__ in, float* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char conv_sm[];
-  const int HWo = g.h_out * g.w_out, kk = g.k * g.k;
+  const int K = KS ? KS : g.k;
+  constexpr int UK = KS ? KS : 1;
+  const int HWo = g.h_out * g.w_out, kk = K * K;
   const int nft = (g.c_out + kConvFT - 1) / kConvFT, O4 = nft * kConvFT;
   float* ws = reinterpret_cast<float*>(conv_sm);   // [c_in][k][k][O4]
   float* src = ws + (size_t)g.c_in * kk * O4;      // [d_in], twice with DB
@@ -535,12 +540,14 @@ __global__ void __launch_bounds__(256) k_conv_fwd_row2(int64_t R, LayerGeom g, c
 #pragma unroll
         for (int t = 0; t < kConvFT; ++t) acc[p][t] = 0.f;
       for (int c = 0; c < g.c_in; ++c)
-        for (int kh = 0; kh < g.k; ++kh) {
+#pragma unroll UK
+        for (int kh = 0; kh < K; ++kh) {
           const int ih = oh * g.stride + kh - g.pad;
           if (ih < 0 || ih >= g.h_in) continue;
           const float* srow = srcr + (c * g.h_in + ih) * g.w_in;
-          const float* wt = ws + ((size_t)c * kk + kh * g.k) * O4 + o0;
-          for (int kw = 0; kw < g.k; ++kw) {
+          const float* wt = ws + ((size_t)c * kk + kh * K) * O4 + o0;
+#pragma unroll UK
+          for (int kw = 0; kw < K; ++kw) {
             const float4 w4 = *reinterpret_cast<const float4*>(wt + kw * O4);
             const float wv[kConvFT] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
@@ -603,18 +610,21 @@ int conv_pixels(const LayerGeom& g, int dir) {
 
 // Launch a row-staged float convolution with P = 2 or 4 pixels per item
 // (false: its shared memory could not be opted in).
-template <typename Tin, bool DB, int P>
+template <typename Tin, bool DB, int P, int KS>
 bool fwd_row2_p(cudaStream_t st, unsigned nblk, size_t bytes, int64_t R, const LayerGeom& g, const Tin* W,
                 const Tin* in, float* out) {
-  if (!conv_row_smem(k_conv_fwd_row2<Tin, DB, P>, bytes)) return false;
-  k_conv_fwd_row2<Tin, DB, P><<<nblk, 256, bytes, st>>>(R, g, W, in, out);
+  if (!conv_row_smem(k_conv_fwd_row2<Tin, DB, P, KS>, bytes)) return false;
+  k_conv_fwd_row2<Tin, DB, P, KS><<<nblk, 256, bytes, st>>>(R, g, W, in, out);
   return true;
 }
 template <typename Tin, bool DB>
 bool fwd_row2(int P, cudaStream_t st, unsigned nblk, size_t bytes, int64_t R, const LayerGeom& g, const Tin* W,
               const Tin* in, float* out) {
-  return P == 4 ? fwd_row2_p<Tin, DB, 4>(st, nblk, bytes, R, g, W, in, out)
-                : fwd_row2_p<Tin, DB, 2>(st, nblk, bytes, R, g, W, in, out);
+  if (std::is_same<Tin, float>::value && g.k == 3)
+    return P == 4 ? fwd_row2_p<Tin, DB, 4, 3>(st, nblk, bytes, R, g, W, in, out)
+                  : fwd_row2_p<Tin, DB, 2, 3>(st, nblk, bytes, R, g, W, in, out);
+  return P == 4 ? fwd_row2_p<Tin, DB, 4, 0>(st, nblk, bytes, R, g, W, in, out)
+                : fwd_row2_p<Tin, DB, 2, 0>(st, nblk, bytes, R, g, W, in, out);
 }
 template <typename Tin, bool DB, int P>
 bool T_row2_p(cudaStream_t st, unsigned nblk, size_t bytes, int64_t R, const LayerGeom& g, const Tin* W, const Tin* in,
